@@ -1,0 +1,291 @@
+/*
+ * ddppo.h -- C ABI of the GB300 (sm_103a) DD-PPO rollout-then-update hot path.
+ *
+ * DD-PPO (arXiv:1911.00357) trains a PointGoal navigation agent with PPO in a
+ * synchronous collect-then-update loop (Sec. 3, Eq. 4; Fig. "distrib_rl"): each
+ * worker collects a rollout with its current policy, computes GAE advantages,
+ * and runs epochs x minibatches of the clipped-surrogate update (Sec. 2 Eq. 2,
+ * Sec. 4 "Training"). This library is one such worker on one GPU. The
+ * simulator is an occupancy-grid world with a ray-cast depth camera standing
+ * in for Habitat-Sim (Sec. 4 "Simulator+Datasets"), whose scenes and renderer
+ * are not available.
+ *
+ * Conventions for every entry point
+ *   - Return value: DDPPO_OK (0) or a negative DDPPO_E_* code. Nothing aborts,
+ *     throws or exits. ddppo_last_error() gives the message of the last failure
+ *     on the calling thread.
+ *   - Pointers marked [dev] are CUDA device pointers owned by the caller; the
+ *     library never frees them and never keeps them past the call (except the
+ *     buffers of a captured collect graph, see ddppo_collect). Pointers marked
+ *     [host] are host memory.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy default
+ *     stream. Work is enqueued asynchronously on it; results are ready when the
+ *     stream is synchronised. Entry points that enqueue work never allocate or
+ *     synchronise, so they can be captured into a CUDA graph, except where noted.
+ *   - Arrays are dense, row-major, time-major where a time axis exists.
+ *   - Units of the world: positions in u = 1e-4 m (int32), depth in metres.
+ *   - Errors detected on the device (an index outside a buffer, a capped wait
+ *     that ran out) do not trap: they set a sticky device status word that
+ *     ddppo_device_status() reads.
+ */
+#ifndef DDPPO_H
+#define DDPPO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DDPPO_OK 0
+#define DDPPO_E_ARG (-1)           /* null pointer, bad size, misaligned pointer        */
+#define DDPPO_E_CONFIG (-2)        /* unsupported configuration or shape                 */
+#define DDPPO_E_CUDA (-3)          /* a CUDA call or kernel launch failed                */
+#define DDPPO_E_DEVICE_BOUNDS (-4) /* a kernel caught an out-of-range index (sticky)     */
+#define DDPPO_E_TIMEOUT (-5)       /* a capped device loop ran out of iterations (sticky)*/
+#define DDPPO_E_STATE (-6)         /* call order: e.g. env_step before env_reset         */
+
+#define DDPPO_NSTATE 12   /* int32 slots of one agent state, see ddppo_env_state */
+#define DDPPO_NSTATS 8    /* floats of PPO statistics per minibatch              */
+#define DDPPO_NUM_ACTIONS 4
+
+typedef struct ddppo_ctx ddppo_ctx;
+
+/* Everything that fixes shapes and workspace sizes. Readings of the paper for
+ * the values it leaves open are listed per field. */
+typedef struct {
+  int32_t num_envs;       /* E: parallel environments of this worker (Sec. 4 "Training") */
+  /* world: procedural occupancy grids standing in for Gibson/MP3D scenes */
+  int32_t gen_kind;       /* 0: border + Bernoulli walls; 1: recursive rooms and doors     */
+  int32_t grid_min;       /* square grid side in cells; each episode draws a side          */
+  int32_t grid_max;       /*   grid_min * 2^j <= grid_max uniformly (equal: fixed side).   */
+                          /*   Sides must be multiples of 32 and at most 512.              */
+  float cell_m;           /* cell side in metres (0.25 or 0.1)                             */
+  float wall_density;     /* Bernoulli wall probability (gen_kind 0)                       */
+  float door_m;           /* door width in metres (gen_kind 1)                              */
+  int32_t min_room;       /* minimum room side in cells (gen_kind 1)                        */
+  int32_t max_steps;      /* episode step cap (500)                                         */
+  int32_t terminal_mode;  /* 0: +2.5 on success; 1: +2.5*SPL (Sec. 4 "Training")           */
+  /* depth camera (Sec. 4 "Agent": 256x256 depth; 90 degree field of view) */
+  int32_t depth_h, depth_w; /* rendered resolution; square, even, <= 1024                   */
+  int32_t pool2x2;        /* 1: 2x2 average pool before the encoder (App. "Visual Encoder") */
+  float cam_h_m;          /* camera height (0.88 m)                                          */
+  float ceil_h_m;         /* ceiling height (2.5 m)                                          */
+  float max_depth_m;      /* depth clip and normaliser (10 m)                                */
+  /* agent network (App. "Agent Design") */
+  int32_t net_kind;       /* 0: 3-layer conv 32/64/32 (8/4/3); 1: ResNet-18-style + GN      */
+  int32_t base_ch;        /* ResNet base width (32 or 64)                                    */
+  int32_t hidden;         /* LSTM hidden size and visual FC width (128 or 512)               */
+  int32_t lstm_layers;    /* 1 or 2                                                          */
+  int32_t precision;      /* 0: FP32 everywhere; 1: BF16 GEMM operands, FP32 accumulate      */
+  /* rollout / update shapes, used to size the workspace at creation */
+  int32_t rollout_T;      /* T: frames per env per rollout (128)                             */
+  int32_t minibatches;    /* PPO minibatches per epoch (E must divide evenly)                */
+  int32_t encoder_chunk;  /* max frames per encoder pass in the update (0: all at once)     */
+  uint64_t seed;          /* seeds the world (counter hash) and the initial weights          */
+} ddppo_config;
+
+/* Device views of one rollout (Sec. 4 "Training": T frames from each of E envs).
+ * Slot t of obs/goal/prev_a/masks/values is the observation the policy acts on
+ * at step t; slot T is the bootstrap observation. */
+typedef struct {
+  void* obs;            /* [dev] [T+1, E, 1, h, w]  encoder input, float (precision 0) or
+                           bf16 (precision 1); h = depth_h/(1+pool2x2), w likewise       */
+  float* goal;          /* [dev] [T+1, E, 3]  [r (m), cos theta, sin theta]               */
+  int32_t* prev_a;      /* [dev] [T+1, E]     previous action, 4 = start token             */
+  uint8_t* masks;       /* [dev] [T+1, E]     0 at an episode's first frame, else 1        */
+  int32_t* actions;     /* [dev] [T, E]                                                    */
+  float* logp;          /* [dev] [T, E]       log pi_old(a_t | o_t)                        */
+  float* values;        /* [dev] [T+1, E]     V(o_t); slot T bootstraps                    */
+  float* rewards;       /* [dev] [T, E]                                                    */
+  uint8_t* dones;       /* [dev] [T, E]       episode ended at step t                      */
+  float* info;          /* [dev] [T, E, 4]    success, spl, collided, episode steps; NULL ok*/
+  float* adv;           /* [dev] [T, E]       GAE advantages                               */
+  float* ret;           /* [dev] [T, E]       returns adv + V                              */
+  float* h0;            /* [dev] [L, E, hidden]  LSTM state before slot 0                  */
+  float* c0;            /* [dev] [L, E, hidden]                                            */
+  float* h;             /* [dev] [L, E, hidden]  running LSTM state (in/out)               */
+  float* c;             /* [dev] [L, E, hidden]                                            */
+  const float* uniforms;/* [dev] [T, E]  one U[0,1) draw per action sample                 */
+} ddppo_rollout;
+
+/* PPO hyper-parameters (Sec. 4 "Training": clip 0.2 by convention, 2 epochs x 2
+ * minibatches, Adam lr 2.5e-4, gamma 0.99, GAE tau 0.95, no advantage
+ * normalisation; value/entropy coefficients and grad clip are not stated). */
+typedef struct {
+  float clip;            /* epsilon of Eq. 2                          */
+  float lr;              /* Adam step size                            */
+  float value_coef;      /* c_v (0.5)                                 */
+  float entropy_coef;    /* c_e (0.01)                                */
+  float max_grad_norm;   /* global L2 clip (0.5); <= 0 disables       */
+  float beta1, beta2;    /* Adam (0.9, 0.999)                         */
+  float adam_eps;        /* Adam epsilon added to sqrt(v_hat) (1e-5)  */
+  int32_t epochs;        /* 2                                         */
+  int32_t minibatches;   /* 2; must equal the config's value          */
+  int32_t norm_adv;      /* 0 (the paper's choice) or 1               */
+  int32_t update_index;  /* seeds the per-epoch env permutation       */
+} ddppo_ppo_hparams;
+
+/* ---- lifetime --------------------------------------------------------------- */
+
+/* Create a worker on the current CUDA device. Allocates (cudaMalloc) the
+ * parameters (FP32, initialised from cfg->seed), Adam state, world state and all
+ * workspace for the shapes in cfg. Not capturable. *out is set on success only.
+ * Errors: E_ARG (null), E_CONFIG (unsupported shape), E_CUDA (allocation). */
+int ddppo_create(const ddppo_config* cfg, ddppo_ctx** out);
+
+/* Free everything ddppo_create allocated. Synchronises the device. NULL is a no-op. */
+int ddppo_destroy(ddppo_ctx* ctx);
+
+/* Message of the last failure on this thread ("" if none). Never NULL. */
+const char* ddppo_last_error(void);
+
+/* Sticky device status (DDPPO_OK or DDPPO_E_DEVICE_BOUNDS / DDPPO_E_TIMEOUT), read
+ * with a device-to-host copy that synchronises `stream`. code_out: [host]. */
+int ddppo_device_status(ddppo_ctx* ctx, int32_t* code_out, void* stream);
+
+/* ---- parameters -------------------------------------------------------------- */
+
+/* Number of FP32 parameters. The flat layout is the concatenation of the
+ * tensors below in PyTorch's natural layouts (conv [Cout, Cin, kh, kw], linear
+ * [out, in]), in this order:
+ *   net_kind 0: c1.w [32,1,8,8] c1.b [32] c2.w [64,32,4,4] c2.b [64] c3.w [32,64,3,3] c3.b [32]
+ *   net_kind 1: stem.w [c,1,7,7] stem.g [c] stem.b [c]; for each of the 8 BasicBlocks
+ *               (widths c,c,2c,2c,4c,4c,8c,8c; first of each width > c has stride 2):
+ *               c1.w n1.g n1.b c2.w n2.g n2.b [d.w (1x1) nd.g nd.b if it changes shape];
+ *               cmp.w [128,8c,3,3] cmp.g [128] cmp.b [128]
+ *   then vis.w [H, F] vis.b [H] (F = flattened encoder output, C-major order),
+ *   goal.w [32,3] goal.b [32], act.emb [5,32],
+ *   per LSTM layer l: w_ih [4H, In_l] w_hh [4H, H] b_ih [4H] b_hh [4H]
+ *               (In_0 = H + 64, In_l = H; gate order i, f, g, o),
+ *   actor.w [4,H] actor.b [4] critic.w [1,H] critic.b [1].
+ * n_out: [host]. */
+int ddppo_num_params(const ddppo_ctx* ctx, int64_t* n_out);
+
+/* Copy the FP32 master parameters out of / into the worker. flat: [dev] [n].
+ * n must equal ddppo_num_params. set_params also rebuilds the GEMM-layout
+ * weight copies and resets the Adam moments and step count to zero. */
+int ddppo_get_params(ddppo_ctx* ctx, float* flat, int64_t n, void* stream);
+int ddppo_set_params(ddppo_ctx* ctx, const float* flat, int64_t n, void* stream);
+
+/* Adam state: m, v [dev] [n] and the step count [host] (NULL to skip). */
+int ddppo_get_adam(ddppo_ctx* ctx, float* m, float* v, int64_t n, int64_t* step, void* stream);
+
+/* ---- environment (Sec. 4 "PointGoal Navigation", "Agent", "Training") -------- */
+
+/* Start episode 0 of every env: generate the scene, draw the goal (uniform free
+ * cell) and start (uniform among cells at geodesic >= 2 m; Sec. 4: random start
+ * position and orientation), compute the BFS geodesic field from the goal, and
+ * write the first observation: obs [dev] [E, 1, h, w] (pooled, / max_depth, in
+ * the precision's dtype) and goal [dev] [E, 3]. */
+int ddppo_env_reset(ddppo_ctx* ctx, void* obs, float* goal, void* stream);
+
+/* Apply actions [dev] [E] in {0 stop, 1 forward 0.25 m, 2 left 10 deg,
+ * 3 right 10 deg} (Sec. 4 "Agent"). Writes reward [dev] [E] (-delta geodesic -
+ * 0.01 per step, terminal bonus on success; Sec. 4 "Training"), done [dev] [E]
+ * (stop, or max_steps reached), info [dev] [E, 4] (success, SPL, collided,
+ * steps; NULL ok). An env whose episode ended starts its next episode at once
+ * and obs/goal [dev] are the new episode's first frame (auto-reset).
+ * Errors: E_ARG; E_STATE before env_reset; out-of-range actions are caught on
+ * the device (sticky E_DEVICE_BOUNDS) and treated as stop. */
+int ddppo_env_step(ddppo_ctx* ctx, const int32_t* actions, void* obs, float* goal, float* reward,
+                   uint8_t* done, float* info, void* stream);
+
+/* Parity / debugging views. state [dev] [E, DDPPO_NSTATE] int32: x, y (u),
+ * heading (0..35, 10 deg steps counter-clockwise from +x), steps, path length
+ * (u), previous geodesic (u), start geodesic l (u), goal x, goal y (u), episode,
+ * grid side (cells), collided. grids [dev] [E, grid_max^2] uint8 (1 = wall) and
+ * dists [dev] [E, grid_max^2] int32 (BFS cells from the goal, -1 unreachable)
+ * hold each env's current episode with row stride = its grid side.
+ * depth [dev] [E, depth_h, depth_w] float: the un-pooled depth image (metres) of
+ * the current state. Either pointer of env_grids may be NULL. */
+int ddppo_env_state(ddppo_ctx* ctx, int32_t* state, void* stream);
+int ddppo_env_grids(ddppo_ctx* ctx, uint8_t* grids, int32_t* dists, void* stream);
+int ddppo_env_depth(ddppo_ctx* ctx, float* depth, void* stream);
+
+/* Overwrite the agent states [dev] [E, DDPPO_NSTATE] (same layout as env_state)
+ * keeping the current scenes; for tests that place agents by hand. */
+int ddppo_env_set_state(ddppo_ctx* ctx, const int32_t* state, void* stream);
+
+/* ---- policy (App. "Agent Design") -------------------------------------------- */
+
+/* One inference step for all E envs: encoder -> FC -> concat(goal FC, previous
+ * action embedding) -> LSTM (state reset where masks == 0) -> softmax actor +
+ * critic; the action is a = min{k : CDF_k > u} for the caller's uniform u.
+ * obs [dev] [E,1,h,w] (dtype of the precision), goal [dev] [E,3], prev_a [dev]
+ * [E], masks [dev] [E], h/c [dev] [L,E,H] in/out, uniforms [dev] [E];
+ * action [dev] [E], logp [dev] [E], value [dev] [E]. */
+int ddppo_policy_act(ddppo_ctx* ctx, const void* obs, const float* goal, const int32_t* prev_a,
+                     const uint8_t* masks, float* h, float* c, const float* uniforms,
+                     int32_t* action, float* logp, float* value, void* stream);
+
+/* Forward over a [T, E] segment (T <= rollout_T, T*E <= rollout_T*num_envs/minibatches)
+ * from the LSTM state h0/c0 [dev] [L,E,H], keeping the activations for
+ * ddppo_policy_backward. Inputs as in policy_act with a leading T axis.
+ * logits [dev] [T,E,4], values [dev] [T,E]. */
+int ddppo_policy_evaluate(ddppo_ctx* ctx, int32_t T, int32_t E, const void* obs, const float* goal,
+                          const int32_t* prev_a, const uint8_t* masks, const float* h0,
+                          const float* c0, float* logits, float* values, void* stream);
+
+/* Backward of the last ddppo_policy_evaluate: hand-written gradients of the
+ * heads, the LSTM (back-propagation through time over the segment) and the
+ * encoder. dlogits [dev] [T,E,4], dvalues [dev] [T,E]; grad [dev] [n_params] is
+ * overwritten with d(sum dlogits*logits + dvalues*values)/d theta in the flat
+ * layout of ddppo_num_params. Errors: E_STATE without a preceding evaluate. */
+int ddppo_policy_backward(ddppo_ctx* ctx, const float* dlogits, const float* dvalues, float* grad,
+                          void* stream);
+
+/* ---- learning (Sec. 2 Eq. 1-2; Sec. 4 "Training") ----------------------------- */
+
+/* Generalised advantage estimation, one warp-level reverse scan per env:
+ *   delta_t = r_t + gamma (1 - d_t) V_{t+1} - V_t,  A_t = delta_t + gamma lam (1 - d_t) A_{t+1},
+ *   R_t = A_t + V_t.
+ * reward, adv, ret [dev] [T,E]; done [dev] [T,E] (nonzero = episode ended at t);
+ * value [dev] [T+1,E]. Stateless: needs no ctx. */
+int ddppo_gae(const float* reward, const uint8_t* done, const float* value, int32_t T, int32_t E,
+              float gamma, float lam, float* adv, float* ret, void* stream);
+
+/* PPO loss over n samples (Eq. 2 plus value and entropy terms):
+ *   L = -mean(min(rho A, clip(rho, 1-eps, 1+eps) A)) + c_v 0.5 mean((R-V)^2) - c_e mean(H)
+ * with rho = exp(log pi(a) - logp_old). logits [dev] [n,4], values, adv, ret,
+ * logp_old [dev] [n], actions [dev] [n]. Writes stats [dev] [DDPPO_NSTATS] = loss,
+ * policy loss, value loss, entropy, clip fraction, approx KL, 0, 0 and the exact
+ * gradients dlogits [dev] [n,4], dvalues [dev] [n]. Reductions are in a fixed
+ * order (deterministic). Stateless. */
+int ddppo_ppo_loss(int32_t n, const float* logits, const float* values, const int32_t* actions,
+                   const float* logp_old, const float* adv, const float* ret, float clip,
+                   float value_coef, float entropy_coef, float* stats, float* dlogits,
+                   float* dvalues, void* stream);
+
+/* One PPO update on a collected rollout (ro->adv/ret already filled by ddppo_gae):
+ * hp->epochs x hp->minibatches steps; minibatch k of epoch e holds the envs
+ * perm[k*E/mb, (k+1)*E/mb) of a Fisher-Yates permutation drawn from the counter
+ * hash (seed, update_index, epoch), with their full T-step sequences replayed
+ * from ro->h0/c0. Each step: forward, loss, hand-written backward, global-norm
+ * clip, Adam. stats [dev] [epochs*minibatches, DDPPO_NSTATS] (NULL ok): loss,
+ * policy loss, value loss, entropy, clip fraction, approx KL, grad norm, 0. */
+int ddppo_ppo_update(ddppo_ctx* ctx, const ddppo_rollout* ro, const ddppo_ppo_hparams* hp,
+                     float* stats, void* stream);
+
+/* Collect one rollout (Sec. 3: the collection stage of the synchronous loop):
+ * copy slot T of the previous rollout to slot 0 (first call: env_reset), save
+ * the LSTM state to h0/c0, then T times {policy_act on slot t -> env_step ->
+ * slot t+1}, then the bootstrap value V(o_T). With use_graph = 1 the T-step loop
+ * is captured once into a CUDA graph and replayed on later calls with the same
+ * rollout pointers (the first call with new pointers captures and is not itself
+ * capturable). */
+int ddppo_collect(ddppo_ctx* ctx, const ddppo_rollout* ro, int32_t use_graph, void* stream);
+
+/* Per-kernel-family timing of the calls enqueued while enabled (CUDA events on
+ * the launching stream). ddppo_timing_enable(ctx, 1) starts recording and
+ * clears the counters; ddppo_timing_read synchronises and returns, for family
+ * id (0: tensor-core / SIMT GEMM, 1: ray cast), the summed milliseconds, launch
+ * count and algorithmic work (FLOPs for GEMM, output bytes for the ray cast). */
+int ddppo_timing_enable(ddppo_ctx* ctx, int32_t on);
+int ddppo_timing_read(ddppo_ctx* ctx, int32_t family, double* ms, int64_t* launches, double* work);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DDPPO_H */

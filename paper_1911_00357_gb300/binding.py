@@ -1,0 +1,262 @@
+"""Thin ctypes binding of the C ABI in ``include/ddppo.h``.
+
+Functions carry the C names; each marshals torch tensors (device memory owned by
+the caller) into pointers and passes torch's current CUDA stream. All compute
+runs in the CUDA library; there is no fallback path: if the library or a GPU is
+missing, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+DDPPO_OK = 0
+ERRORS = {-1: "E_ARG", -2: "E_CONFIG", -3: "E_CUDA", -4: "E_DEVICE_BOUNDS", -5: "E_TIMEOUT",
+          -6: "E_STATE"}
+NSTATE = 12
+NSTATS = 8
+NUM_ACTIONS = 4
+
+
+class DDPPOError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+class Config(ctypes.Structure):
+    _fields_ = [
+        ("num_envs", ctypes.c_int32), ("gen_kind", ctypes.c_int32),
+        ("grid_min", ctypes.c_int32), ("grid_max", ctypes.c_int32),
+        ("cell_m", ctypes.c_float), ("wall_density", ctypes.c_float),
+        ("door_m", ctypes.c_float), ("min_room", ctypes.c_int32),
+        ("max_steps", ctypes.c_int32), ("terminal_mode", ctypes.c_int32),
+        ("depth_h", ctypes.c_int32), ("depth_w", ctypes.c_int32),
+        ("pool2x2", ctypes.c_int32), ("cam_h_m", ctypes.c_float),
+        ("ceil_h_m", ctypes.c_float), ("max_depth_m", ctypes.c_float),
+        ("net_kind", ctypes.c_int32), ("base_ch", ctypes.c_int32),
+        ("hidden", ctypes.c_int32), ("lstm_layers", ctypes.c_int32),
+        ("precision", ctypes.c_int32), ("rollout_T", ctypes.c_int32),
+        ("minibatches", ctypes.c_int32), ("encoder_chunk", ctypes.c_int32),
+        ("seed", ctypes.c_uint64),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Rollout(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_void_p) for n in (
+        "obs", "goal", "prev_a", "masks", "actions", "logp", "values", "rewards", "dones", "info",
+        "adv", "ret", "h0", "c0", "h", "c", "uniforms")]
+
+
+class PPOHParams(ctypes.Structure):
+    _fields_ = [
+        ("clip", ctypes.c_float), ("lr", ctypes.c_float), ("value_coef", ctypes.c_float),
+        ("entropy_coef", ctypes.c_float), ("max_grad_norm", ctypes.c_float),
+        ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("adam_eps", ctypes.c_float),
+        ("epochs", ctypes.c_int32), ("minibatches", ctypes.c_int32),
+        ("norm_adv", ctypes.c_int32), ("update_index", ctypes.c_int32),
+    ]
+
+
+def default_hparams(**kw) -> PPOHParams:
+    """Sec. 4 "Training": 2 epochs x 2 minibatches, Adam 2.5e-4, no advantage norm."""
+    d = dict(clip=0.2, lr=2.5e-4, value_coef=0.5, entropy_coef=0.01, max_grad_norm=0.5,
+             beta1=0.9, beta2=0.999, adam_eps=1e-5, epochs=2, minibatches=2, norm_adv=0,
+             update_index=0)
+    d.update(kw)
+    return PPOHParams(**d)
+
+
+_lib = None
+P = ctypes.c_void_p
+I32 = ctypes.c_int32
+I64 = ctypes.c_int64
+F32 = ctypes.c_float
+
+_SIGS = {
+    "ddppo_create": [P, P],
+    "ddppo_destroy": [P],
+    "ddppo_device_status": [P, P, P],
+    "ddppo_num_params": [P, P],
+    "ddppo_get_params": [P, P, I64, P],
+    "ddppo_set_params": [P, P, I64, P],
+    "ddppo_get_adam": [P, P, P, I64, P, P],
+    "ddppo_env_reset": [P, P, P, P],
+    "ddppo_env_step": [P, P, P, P, P, P, P, P],
+    "ddppo_env_state": [P, P, P],
+    "ddppo_env_set_state": [P, P, P],
+    "ddppo_env_grids": [P, P, P, P],
+    "ddppo_env_depth": [P, P, P],
+    "ddppo_policy_act": [P, P, P, P, P, P, P, P, P, P, P, P],
+    "ddppo_policy_evaluate": [P, I32, I32, P, P, P, P, P, P, P, P, P],
+    "ddppo_policy_backward": [P, P, P, P, P],
+    "ddppo_gae": [P, P, P, I32, I32, F32, F32, P, P, P],
+    "ddppo_ppo_loss": [I32, P, P, P, P, P, P, F32, F32, F32, P, P, P, P],
+    "ddppo_ppo_update": [P, P, P, P, P],
+    "ddppo_collect": [P, P, I32, P],
+    "ddppo_timing_enable": [P, I32],
+    "ddppo_timing_read": [P, I32, P, P, P],
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load (building first if needed) the CUDA library; raises if it cannot."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.ddppo_last_error.restype = ctypes.c_char_p
+        L.ddppo_last_error.argtypes = []
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_SIGS) + ["ddppo_last_error"]
+
+
+def _check(rc: int):
+    if rc != DDPPO_OK:
+        raise DDPPOError(rc, lib().ddppo_last_error().decode())
+
+
+def _p(t):
+    """Device pointer of a CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor):
+        return t
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _s(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+# ---- thin wrappers with the C names ----
+def ddppo_create(cfg: Config):
+    h = ctypes.c_void_p()
+    _check(lib().ddppo_create(ctypes.byref(cfg), ctypes.byref(h)))
+    return h
+
+
+def ddppo_destroy(h):
+    _check(lib().ddppo_destroy(h))
+
+
+def ddppo_device_status(h) -> int:
+    code = ctypes.c_int32()
+    _check(lib().ddppo_device_status(h, ctypes.byref(code), _s()))
+    return code.value
+
+
+def ddppo_num_params(h) -> int:
+    n = ctypes.c_int64()
+    _check(lib().ddppo_num_params(h, ctypes.byref(n)))
+    return n.value
+
+
+def ddppo_get_params(h, flat):
+    _check(lib().ddppo_get_params(h, _p(flat), flat.numel(), _s()))
+
+
+def ddppo_set_params(h, flat):
+    _check(lib().ddppo_set_params(h, _p(flat), flat.numel(), _s()))
+
+
+def ddppo_get_adam(h, m, v) -> int:
+    step = ctypes.c_int64()
+    _check(lib().ddppo_get_adam(h, _p(m), _p(v), m.numel(), ctypes.byref(step), _s()))
+    return step.value
+
+
+def ddppo_env_reset(h, obs, goal):
+    _check(lib().ddppo_env_reset(h, _p(obs), _p(goal), _s()))
+
+
+def ddppo_env_step(h, actions, obs, goal, reward, done, info=None):
+    _check(lib().ddppo_env_step(h, _p(actions), _p(obs), _p(goal), _p(reward), _p(done), _p(info),
+                                _s()))
+
+
+def ddppo_env_state(h, state):
+    _check(lib().ddppo_env_state(h, _p(state), _s()))
+
+
+def ddppo_env_set_state(h, state):
+    _check(lib().ddppo_env_set_state(h, _p(state), _s()))
+
+
+def ddppo_env_grids(h, grids=None, dists=None):
+    _check(lib().ddppo_env_grids(h, _p(grids), _p(dists), _s()))
+
+
+def ddppo_env_depth(h, depth):
+    _check(lib().ddppo_env_depth(h, _p(depth), _s()))
+
+
+def ddppo_policy_act(h, obs, goal, prev_a, masks, hs, cs, uniforms, action, logp, value):
+    _check(lib().ddppo_policy_act(h, _p(obs), _p(goal), _p(prev_a), _p(masks), _p(hs), _p(cs),
+                                  _p(uniforms), _p(action), _p(logp), _p(value), _s()))
+
+
+def ddppo_policy_evaluate(h, T, E, obs, goal, prev_a, masks, h0, c0, logits, values):
+    _check(lib().ddppo_policy_evaluate(h, T, E, _p(obs), _p(goal), _p(prev_a), _p(masks), _p(h0),
+                                       _p(c0), _p(logits), _p(values), _s()))
+
+
+def ddppo_policy_backward(h, dlogits, dvalues, grad):
+    _check(lib().ddppo_policy_backward(h, _p(dlogits), _p(dvalues), _p(grad), _s()))
+
+
+def ddppo_gae(reward, done, value, T, E, gamma, lam, adv, ret):
+    _check(lib().ddppo_gae(_p(reward), _p(done), _p(value), T, E, gamma, lam, _p(adv), _p(ret),
+                           _s()))
+
+
+def ddppo_ppo_loss(n, logits, values, actions, logp_old, adv, ret, clip, value_coef, entropy_coef,
+                   stats, dlogits, dvalues):
+    _check(lib().ddppo_ppo_loss(n, _p(logits), _p(values), _p(actions), _p(logp_old), _p(adv),
+                                _p(ret), clip, value_coef, entropy_coef, _p(stats), _p(dlogits),
+                                _p(dvalues), _s()))
+
+
+def ddppo_ppo_update(h, ro: Rollout, hp: PPOHParams, stats=None):
+    _check(lib().ddppo_ppo_update(h, ctypes.byref(ro), ctypes.byref(hp), _p(stats), _s()))
+
+
+def ddppo_collect(h, ro: Rollout, use_graph: bool = True):
+    _check(lib().ddppo_collect(h, ctypes.byref(ro), 1 if use_graph else 0, _s()))
+
+
+def ddppo_timing_enable(h, on: bool):
+    _check(lib().ddppo_timing_enable(h, 1 if on else 0))
+
+
+def ddppo_timing_read(h, family: int):
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    w = ctypes.c_double()
+    _check(lib().ddppo_timing_read(h, family, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
+    return ms.value, n.value, w.value

@@ -1,0 +1,242 @@
+// C ABI of the library (include/ddppo.h): argument checking, the worker context,
+// and the environment / GAE entry points. The network and update entry points are in
+// nn_abi.cu.
+#include <math.h>
+#include <stdio.h>
+
+#include <mutex>
+#include <string>
+
+#include "ctx.cuh"
+
+namespace ddppo {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+}  // namespace ddppo
+
+using namespace ddppo;
+
+#define ARG_CHECK(cond, msg)            \
+  do {                                  \
+    if (!(cond)) {                      \
+      set_error(std::string("ddppo: ") + msg); \
+      return DDPPO_E_ARG;               \
+    }                                   \
+  } while (0)
+#define CFG_CHECK(cond, msg)            \
+  do {                                  \
+    if (!(cond)) {                      \
+      set_error(std::string("ddppo config: ") + msg); \
+      return DDPPO_E_CONFIG;            \
+    }                                   \
+  } while (0)
+
+extern "C" const char* ddppo_last_error(void) { return g_last_error.c_str(); }
+
+static bool pow2_multiple(int a, int b) {
+  if (a <= 0 || b < a || b % a) return false;
+  int q = b / a;
+  return (q & (q - 1)) == 0;
+}
+
+static int validate(const ddppo_config* c) {
+  CFG_CHECK(c->num_envs >= 1 && c->num_envs <= (1 << 16), "num_envs must be in [1, 65536]");
+  CFG_CHECK(c->gen_kind == 0 || c->gen_kind == 1, "gen_kind must be 0 or 1");
+  CFG_CHECK(c->grid_min >= 32 && c->grid_max <= 512 && c->grid_min % 32 == 0 &&
+                pow2_multiple(c->grid_min, c->grid_max),
+            "grid sides must be multiples of 32 in [32, 512], grid_max = grid_min * 2^j");
+  CFG_CHECK(c->cell_m >= 0.01f && c->cell_m <= 1.0f, "cell_m must be in [0.01, 1]");
+  CFG_CHECK(c->wall_density >= 0.f && c->wall_density <= 1.f, "wall_density must be in [0, 1]");
+  CFG_CHECK(c->gen_kind == 0 || (c->min_room >= 2 && c->door_m > 0.f), "rooms need min_room >= 2");
+  CFG_CHECK(c->max_steps >= 1, "max_steps must be >= 1");
+  CFG_CHECK(c->terminal_mode == 0 || c->terminal_mode == 1, "terminal_mode must be 0 or 1");
+  CFG_CHECK(c->depth_h == c->depth_w && c->depth_w >= 32 && c->depth_w <= 1024 &&
+                c->depth_w % 32 == 0,
+            "depth must be square, a multiple of 32, at most 1024");
+  CFG_CHECK(c->pool2x2 == 0 || c->pool2x2 == 1, "pool2x2 must be 0 or 1");
+  CFG_CHECK(c->max_depth_m > 0.f && c->ceil_h_m > c->cam_h_m && c->cam_h_m > 0.f,
+            "camera must sit between floor and ceiling");
+  CFG_CHECK(c->net_kind == 0 || c->net_kind == 1, "net_kind must be 0 or 1");
+  CFG_CHECK(c->precision == 0 || c->precision == 1, "precision must be 0 (fp32) or 1 (bf16)");
+  CFG_CHECK(c->lstm_layers >= 1 && c->lstm_layers <= 4, "lstm_layers must be in [1, 4]");
+  CFG_CHECK(c->hidden >= 8 && c->hidden % 8 == 0 && c->hidden <= 2048,
+            "hidden must be a multiple of 8 in [8, 2048]");
+  CFG_CHECK(c->net_kind == 0 || (c->base_ch >= 4 && c->base_ch % 4 == 0 && c->base_ch <= 128),
+            "base_ch must be a multiple of 4 in [4, 128]");
+  CFG_CHECK(c->rollout_T >= 1 && c->rollout_T <= 4096, "rollout_T must be in [1, 4096]");
+  CFG_CHECK(c->minibatches >= 1 && c->num_envs % c->minibatches == 0,
+            "minibatches must divide num_envs");
+  CFG_CHECK(c->encoder_chunk >= 0, "encoder_chunk must be >= 0");
+  return DDPPO_OK;
+}
+
+static SimParams make_sim_params(const ddppo_config* c) {
+  SimParams p{};
+  p.E = c->num_envs;
+  p.gen_kind = c->gen_kind;
+  p.grid_min = c->grid_min;
+  p.grid_max = c->grid_max;
+  p.nsizes = 0;
+  for (int s = c->grid_min; s <= c->grid_max; s *= 2) ++p.nsizes;
+  p.cell_u = (int)llround((double)c->cell_m * 10000.0);
+  p.wall_thr24 = (uint32_t)floor((double)c->wall_density * 16777216.0);
+  p.door_cells = c->gen_kind == 1 ? (int)llround((double)c->door_m / (double)c->cell_m) : 1;
+  if (p.door_cells < 1) p.door_cells = 1;
+  p.min_room = c->min_room;
+  p.max_steps = c->max_steps;
+  p.terminal_mode = c->terminal_mode;
+  p.min_start_cells = (20000 + p.cell_u - 1) / p.cell_u;
+  p.H = c->depth_h;
+  p.W = c->depth_w;
+  p.pool = c->pool2x2;
+  p.obs_h = c->depth_h >> c->pool2x2;
+  p.obs_w = c->depth_w >> c->pool2x2;
+  p.cam_h = c->cam_h_m;
+  p.ceil_h = c->ceil_h_m;
+  p.max_depth = c->max_depth_m;
+  p.seed = c->seed;
+  p.max_segs = c->gen_kind == 1
+                   ? (c->grid_max - 2) * (c->grid_max - 2) / (c->min_room * c->min_room) + 1
+                   : 0;
+  p.bf16_obs = c->precision == 1;
+  return p;
+}
+
+template <class T>
+static int dmalloc(T** p, size_t n) {
+  if (n == 0) { *p = nullptr; return DDPPO_OK; }
+  DDPPO_CHECK_CUDA(cudaMalloc((void**)p, n * sizeof(T)));
+  return DDPPO_OK;
+}
+
+namespace ddppo {
+void ctx_free_world(ddppo_ctx* x) {
+  cudaFree(x->sb.grids); cudaFree(x->sb.bits); cudaFree(x->sb.dists); cudaFree(x->sb.states);
+  cudaFree(x->sb.segs); cudaFree(x->sb.need); cudaFree(x->sb.err);
+}
+}  // namespace ddppo
+
+extern "C" int ddppo_create(const ddppo_config* cfg, ddppo_ctx** out) {
+  ARG_CHECK(cfg != nullptr && out != nullptr, "ddppo_create: null argument");
+  DDPPO_TRY(validate(cfg));
+  ddppo_ctx* x = new ddppo_ctx();
+  x->cfg = *cfg;
+  x->sp = make_sim_params(cfg);
+  int rc = DDPPO_OK;
+  do {
+    if (cudaGetDevice(&x->device) != cudaSuccess) { set_error("no CUDA device"); rc = DDPPO_E_CUDA; break; }
+    if ((rc = sim_upload_tables()) != DDPPO_OK) break;
+    if ((rc = sim_configure(x->sp)) != DDPPO_OK) break;
+    const size_t E = cfg->num_envs, GM = (size_t)cfg->grid_max * cfg->grid_max;
+    if ((rc = dmalloc(&x->sb.grids, E * GM)) != DDPPO_OK) break;
+    if ((rc = dmalloc(&x->sb.bits, E * GM / 32)) != DDPPO_OK) break;
+    if ((rc = dmalloc(&x->sb.dists, E * GM)) != DDPPO_OK) break;
+    if ((rc = dmalloc(&x->sb.states, E * ST_N)) != DDPPO_OK) break;
+    if ((rc = dmalloc(&x->sb.segs, E * (size_t)x->sp.max_segs)) != DDPPO_OK) break;
+    if ((rc = dmalloc(&x->sb.need, E)) != DDPPO_OK) break;
+    if ((rc = dmalloc(&x->sb.err, 1)) != DDPPO_OK) break;
+    if (cudaMemset(x->sb.err, 0, sizeof(int32_t)) != cudaSuccess ||
+        cudaMemset(x->sb.need, 0, E) != cudaSuccess ||
+        cudaMemset(x->sb.states, 0, E * ST_N * sizeof(int32_t)) != cudaSuccess) {
+      set_error("cudaMemset failed"); rc = DDPPO_E_CUDA; break;
+    }
+    if ((rc = net_create(x)) != DDPPO_OK) break;
+    if (cudaDeviceSynchronize() != cudaSuccess) { set_error("create: device sync failed"); rc = DDPPO_E_CUDA; break; }
+  } while (0);
+  if (rc != DDPPO_OK) {
+    net_destroy(x);
+    ctx_free_world(x);
+    delete x;
+    return rc;
+  }
+  *out = x;
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_destroy(ddppo_ctx* x) {
+  if (!x) return DDPPO_OK;
+  cudaDeviceSynchronize();
+  net_destroy(x);
+  ctx_free_world(x);
+  delete x;
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_device_status(ddppo_ctx* x, int32_t* code_out, void* stream) {
+  ARG_CHECK(x && code_out, "device_status: null argument");
+  int32_t w = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  DDPPO_CHECK_CUDA(cudaMemcpyAsync(&w, x->sb.err, sizeof(w), cudaMemcpyDeviceToHost, s));
+  DDPPO_CHECK_CUDA(cudaStreamSynchronize(s));
+  if (w & ERRF_BOUNDS) *code_out = DDPPO_E_DEVICE_BOUNDS;
+  else if (w & ERRF_TIMEOUT) *code_out = DDPPO_E_TIMEOUT;
+  else if (w & ERRF_RESET) *code_out = DDPPO_E_CONFIG;
+  else *code_out = DDPPO_OK;
+  return DDPPO_OK;
+}
+
+// ---- environment ----
+extern "C" int ddppo_env_reset(ddppo_ctx* x, void* obs, float* goal, void* stream) {
+  ARG_CHECK(x && obs && goal, "env_reset: null argument");
+  ARG_CHECK(((uintptr_t)obs & 15) == 0 && ((uintptr_t)goal & 3) == 0, "env_reset: misaligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  DDPPO_TRY(launch_reset(x->sp, x->sb, true, s));
+  DDPPO_TRY(launch_render(x->sp, x->sb, obs, goal, nullptr, s));
+  x->env_ready = true;
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_env_step(ddppo_ctx* x, const int32_t* actions, void* obs, float* goal,
+                              float* reward, uint8_t* done, float* info, void* stream) {
+  ARG_CHECK(x && actions && obs && goal && reward && done, "env_step: null argument");
+  if (!x->env_ready) { set_error("env_step before env_reset"); return DDPPO_E_STATE; }
+  cudaStream_t s = (cudaStream_t)stream;
+  DDPPO_TRY(launch_step(x->sp, x->sb, actions, reward, done, info, s));
+  DDPPO_TRY(launch_reset(x->sp, x->sb, false, s));
+  DDPPO_TRY(launch_render(x->sp, x->sb, obs, goal, nullptr, s));
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_env_state(ddppo_ctx* x, int32_t* state, void* stream) {
+  ARG_CHECK(x && state, "env_state: null argument");
+  DDPPO_CHECK_CUDA(cudaMemcpyAsync(state, x->sb.states,
+                                   sizeof(int32_t) * ST_N * x->cfg.num_envs,
+                                   cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_env_set_state(ddppo_ctx* x, const int32_t* state, void* stream) {
+  ARG_CHECK(x && state, "env_set_state: null argument");
+  if (!x->env_ready) { set_error("env_set_state before env_reset"); return DDPPO_E_STATE; }
+  DDPPO_CHECK_CUDA(cudaMemcpyAsync(x->sb.states, state, sizeof(int32_t) * ST_N * x->cfg.num_envs,
+                                   cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_env_grids(ddppo_ctx* x, uint8_t* grids, int32_t* dists, void* stream) {
+  ARG_CHECK(x, "env_grids: null ctx");
+  const size_t n = (size_t)x->cfg.num_envs * x->cfg.grid_max * x->cfg.grid_max;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (grids)
+    DDPPO_CHECK_CUDA(cudaMemcpyAsync(grids, x->sb.grids, n, cudaMemcpyDeviceToDevice, s));
+  if (dists)
+    DDPPO_CHECK_CUDA(cudaMemcpyAsync(dists, x->sb.dists, n * 4, cudaMemcpyDeviceToDevice, s));
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_env_depth(ddppo_ctx* x, float* depth, void* stream) {
+  ARG_CHECK(x && depth, "env_depth: null argument");
+  if (!x->env_ready) { set_error("env_depth before env_reset"); return DDPPO_E_STATE; }
+  return launch_render(x->sp, x->sb, nullptr, nullptr, depth, (cudaStream_t)stream);
+}
+
+// ---- GAE ----
+extern "C" int ddppo_gae(const float* reward, const uint8_t* done, const float* value, int32_t T,
+                         int32_t E, float gamma, float lam, float* adv, float* ret, void* stream) {
+  ARG_CHECK(T >= 0 && E >= 0, "gae: negative size");
+  if (T == 0 || E == 0) return DDPPO_OK;
+  ARG_CHECK(reward && done && value && adv && ret, "gae: null argument");
+  return launch_gae(reward, done, value, T, E, gamma, lam, adv, ret, (cudaStream_t)stream);
+}

@@ -1,0 +1,81 @@
+// Internal declarations shared by the CUDA translation units of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/ddppo.h"
+
+namespace ddppo {
+
+// ---- error reporting (thread-local message, status codes of ddppo.h) ----
+void set_error(const std::string& msg);
+#define DDPPO_CHECK_CUDA(expr)                                                        \
+  do {                                                                                \
+    cudaError_t _e = (expr);                                                          \
+    if (_e != cudaSuccess) {                                                          \
+      ::ddppo::set_error(std::string(#expr) + ": " + cudaGetErrorString(_e));         \
+      return DDPPO_E_CUDA;                                                            \
+    }                                                                                 \
+  } while (0)
+#define DDPPO_CHECK_LAUNCH() DDPPO_CHECK_CUDA(cudaGetLastError())
+#define DDPPO_TRY(expr)              \
+  do {                               \
+    int _rc = (expr);                \
+    if (_rc != DDPPO_OK) return _rc; \
+  } while (0)
+
+// sticky device error word: bit flags
+enum : int32_t { ERRF_BOUNDS = 1, ERRF_TIMEOUT = 2, ERRF_RESET = 4 };
+
+// agent state slots (int32), same meaning as ddppo_env_state
+enum {
+  ST_X = 0, ST_Y, ST_HEAD, ST_STEPS, ST_PATH, ST_GEO_PREV, ST_GEO_START, ST_GOAL_X,
+  ST_GOAL_Y, ST_EPISODE, ST_GRID, ST_COLLIDED, ST_N
+};
+static_assert(ST_N == DDPPO_NSTATE, "state layout");
+
+// ---- world parameters passed to the simulator kernels by value ----
+struct SimParams {
+  int E;
+  int gen_kind;
+  int grid_min, grid_max, nsizes;
+  int cell_u;
+  uint32_t wall_thr24;
+  int door_cells, min_room;
+  int max_steps, terminal_mode;
+  int min_start_cells;  // ceil(2 m / cell)
+  int H, W, pool, obs_h, obs_w;
+  float cam_h, ceil_h, max_depth;
+  uint64_t seed;
+  int max_segs;
+  int bf16_obs;
+};
+
+struct SimBuffers {
+  uint8_t* grids;     // [E, gmax^2]
+  uint32_t* bits;     // [E, gmax^2/32] wall bits, row-major words
+  int32_t* dists;     // [E, gmax^2]
+  int32_t* states;    // [E, ST_N]
+  int4* segs;         // [E, max_segs] room walls (gen_kind 1)
+  uint8_t* need;      // [E] reset request
+  int32_t* err;       // [1] sticky
+};
+
+// host-side launchers (sim.cu)
+int sim_upload_tables();
+size_t reset_smem_bytes(const SimParams& p);
+int launch_reset(const SimParams& p, const SimBuffers& b, bool all, cudaStream_t s);
+int launch_step(const SimParams& p, const SimBuffers& b, const int32_t* actions, float* reward,
+                uint8_t* done, float* info, cudaStream_t s);
+int launch_render(const SimParams& p, const SimBuffers& b, void* obs, float* goal, float* depth_raw,
+                  cudaStream_t s);
+
+// rl.cu
+int launch_gae(const float* r, const uint8_t* d, const float* v, int T, int E, float gamma,
+               float lam, float* adv, float* ret, cudaStream_t s);
+
+}  // namespace ddppo

@@ -1,0 +1,155 @@
+// SIMT GEMM (the plain FP32 form, and the fallback shape path of the BF16 form) with
+// deterministic split-K, plus the dispatcher that routes bf16 operands to tcgen05.
+#include "gemm.cuh"
+
+namespace ddppo {
+
+template <typename T>
+__device__ __forceinline__ float ld_op(const T* p);
+template <>
+__device__ __forceinline__ float ld_op<float>(const float* p) { return __ldg(p); }
+template <>
+__device__ __forceinline__ float ld_op<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+
+constexpr int SB_M = 64, SB_N = 64, SB_K = 16;
+
+// 256 threads; thread (tx, ty) owns rows ty + 16 i and columns tx + 16 j, i, j < 4.
+template <typename T>
+__global__ void __launch_bounds__(256) gemm_simt_kernel(int M, int N, int K, const T* __restrict__ A,
+                                                        int lda, const T* __restrict__ B, int ldb,
+                                                        float* __restrict__ C, int ldc, int c_bf16,
+                                                        float beta, const float* __restrict__ bias,
+                                                        int relu, int kchunk,
+                                                        float* __restrict__ partial) {
+  __shared__ float As[SB_K][SB_M + 4];
+  __shared__ float Bs[SB_K][SB_N + 4];
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  const int m0 = blockIdx.y * SB_M, n0 = blockIdx.x * SB_N;
+  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+  float acc[4][4] = {};
+  const int lr = tid >> 2, lk = (tid & 3) * 4;  // loader: row lr, k lk..lk+3
+  for (int k0 = kbeg; k0 < kend; k0 += SB_K) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int k = k0 + lk + q;
+      const int m = m0 + lr, n = n0 + lr;
+      As[lk + q][lr] = (m < M && k < kend) ? ld_op(A + (size_t)m * lda + k) : 0.f;
+      Bs[lk + q][lr] = (n < N && k < kend) ? ld_op(B + (size_t)n * ldb + k) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < SB_K; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty + 16 * i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx + 16 * j;
+      if (n >= N) continue;
+      if (partial) {
+        partial[((size_t)blockIdx.z * M + m) * N + n] = acc[i][j];
+        continue;
+      }
+      float v = acc[i][j];
+      if (beta != 0.f) v += beta * C[(size_t)m * ldc + n];
+      if (bias) v += bias[n];
+      if (relu) v = fmaxf(v, 0.f);
+      if (c_bf16) ((__nv_bfloat16*)C)[(size_t)m * ldc + n] = __float2bfloat16_rn(v);
+      else C[(size_t)m * ldc + n] = v;
+    }
+  }
+}
+
+// C = beta*C + sum_z partial[z] (+ bias) (ReLU), summed in split order.
+__global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __restrict__ partial,
+                                     float* __restrict__ C, int ldc, int c_bf16, float beta,
+                                     const float* __restrict__ bias, int relu) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)M * N) return;
+  const int m = (int)(idx / N), n = (int)(idx % N);
+  float v = 0.f;
+  for (int z = 0; z < splits; ++z) v += partial[(size_t)z * M * N + idx];
+  if (beta != 0.f) v += beta * C[(size_t)m * ldc + n];
+  if (bias) v += bias[n];
+  if (relu) v = fmaxf(v, 0.f);
+  if (c_bf16) ((__nv_bfloat16*)C)[(size_t)m * ldc + n] = __float2bfloat16_rn(v);
+  else C[(size_t)m * ldc + n] = v;
+}
+
+static int gemm_simt(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t s) {
+  const int gm = (d.M + SB_M - 1) / SB_M, gn = (d.N + SB_N - 1) / SB_N;
+  int splits = 1;
+  const int tiles = gm * gn;
+  const int target = 2 * ws.num_sms;
+  if (tiles < target && d.K >= 4 * SB_K * 8) {
+    splits = (target + tiles - 1) / tiles;
+    splits = min(splits, d.K / (SB_K * 8));
+    const size_t per = (size_t)d.M * d.N;
+    if (per > 0) splits = (int)min((size_t)splits, ws.partial_elems / per);
+    if (splits < 2) splits = 1;
+  }
+  int kchunk = (d.K + splits - 1) / splits;
+  kchunk = (kchunk + SB_K - 1) / SB_K * SB_K;
+  splits = (d.K + kchunk - 1) / kchunk;
+  if (splits < 1) splits = 1;
+  float* partial = splits > 1 ? ws.partial : nullptr;
+  dim3 grid(gn, gm, splits);
+  if (op_bf16)
+    gemm_simt_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(
+        d.M, d.N, d.K, (const __nv_bfloat16*)d.A, d.lda, (const __nv_bfloat16*)d.B, d.ldb,
+        (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu, kchunk, partial);
+  else
+    gemm_simt_kernel<float><<<grid, 256, 0, s>>>(d.M, d.N, d.K, (const float*)d.A, d.lda,
+                                                 (const float*)d.B, d.ldb, (float*)d.C, d.ldc,
+                                                 d.c_bf16, d.beta, d.bias, d.relu, kchunk, partial);
+  DDPPO_CHECK_LAUNCH();
+  if (partial) {
+    const size_t n = (size_t)d.M * d.N;
+    splitk_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+        d.M, d.N, splits, partial, (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu);
+    DDPPO_CHECK_LAUNCH();
+  }
+  return DDPPO_OK;
+}
+
+int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t s,
+         KernelTimer* timer) {
+  if (d.M <= 0 || d.N <= 0) return DDPPO_OK;
+  if (d.K <= 0) {
+    set_error("gemm: K must be positive");
+    return DDPPO_E_CONFIG;
+  }
+  if (d.c_bf16 && d.beta != 0.f) {
+    set_error("gemm: bf16 output cannot accumulate");
+    return DDPPO_E_CONFIG;
+  }
+  const bool rec = timer && timer->on && timer->n + 2 <= 2 * 4096;
+  if (rec) cudaEventRecord(timer->ev[timer->n], s);
+  int rc;
+  if (op_bf16 && gemm_tc_supported(d)) rc = gemm_tc(d, ws, s);
+  else rc = gemm_simt(d, op_bf16, ws, s);
+  if (rec) {
+    cudaEventRecord(timer->ev[timer->n + 1], s);
+    timer->n += 2;
+    timer->flops += 2.0 * d.M * d.N * d.K;
+    timer->launches += 1;
+  }
+  return rc;
+}
+
+}  // namespace ddppo

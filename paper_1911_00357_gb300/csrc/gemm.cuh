@@ -1,0 +1,47 @@
+// GEMM interface used by every contraction of the agent network.
+//   C[M, N] = beta * C + A[M, K] * B[N, K]^T (+ bias[N]) (ReLU)
+// A and B are K-contiguous ("TN"), of the operand dtype (fp32 or bf16); C is fp32, or bf16
+// when c_bf16 (then beta must be 0). Accumulation is fp32.
+#pragma once
+
+#include "common.cuh"
+
+namespace ddppo {
+
+struct GemmDesc {
+  int M = 0, N = 0, K = 0;
+  const void* A = nullptr;
+  int lda = 0;
+  const void* B = nullptr;
+  int ldb = 0;
+  void* C = nullptr;
+  int ldc = 0;
+  int c_bf16 = 0;
+  float beta = 0.f;
+  const float* bias = nullptr;
+  int relu = 0;
+};
+
+struct GemmWorkspace {
+  float* partial = nullptr;  // split-K partial sums
+  size_t partial_elems = 0;
+  int num_sms = 152;
+};
+
+// timing of GEMM launches (family 0 of ddppo_timing_read)
+struct KernelTimer {
+  bool on = false;
+  int n = 0;
+  cudaEvent_t ev[2 * 4096];
+  double flops = 0.0;
+  int64_t launches = 0;
+};
+
+int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t s,
+         KernelTimer* timer = nullptr);
+
+// tcgen05 path (gemm_tc.cu); returns DDPPO_E_CONFIG when the shape is not supported
+int gemm_tc(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s);
+bool gemm_tc_supported(const GemmDesc& d);
+
+}  // namespace ddppo

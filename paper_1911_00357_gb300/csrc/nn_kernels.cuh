@@ -1,0 +1,141 @@
+// Launchers of the network's non-GEMM kernels (nn_kernels.cu). Activations are NHWC
+// fp32; "T" buffers are GEMM operands in the precision's dtype (fp32 or bf16).
+#pragma once
+
+#include "common.cuh"
+
+namespace ddppo {
+
+struct ConvGeom {
+  int N, H, W, C;       // input
+  int Ho, Wo, Cout;     // output
+  int k, s, p;          // square kernel, stride, padding
+  int K, Kp;            // k*k*C and its padded row length
+};
+
+// im2col: col[m, (ky*k + kx)*C + c] (m = (n, oy, ox)); zero beyond K. x_bf16 gives the
+// input's dtype, op_bf16 the output's.
+int launch_im2col(const ConvGeom& g, const void* x, bool x_bf16, void* col, bool op_bf16,
+                  bool transposed, cudaStream_t s);
+// col2im: dx[n, iy, ix, c] (+)= sum of dcol over the (ky, kx) that read it
+int launch_col2im(const ConvGeom& g, const float* dcol, float* dx, bool accumulate, cudaStream_t s);
+// out[c, r] = in[r, c]
+int launch_transpose(const void* in, bool in_bf16, void* out, bool out_bf16, int R, int Cc,
+                     int ld_in, cudaStream_t s);
+// fp32 -> op dtype copy (or plain copy)
+int launch_cast(const float* in, void* out, bool out_bf16, size_t n, cudaStream_t s);
+
+// GroupNorm with groups of 2 channels (C/2 groups), eps
+int launch_gn_stats(const float* z, int N, int HW, int C, float eps, float* mean, float* rstd,
+                    cudaStream_t s);
+// out = act(gn(z) + res) with res = 0, resid (fp32), or gn(zd) (a second normalised input)
+struct GNApply {
+  const float* z; const float* mean; const float* rstd; const float* gamma; const float* beta;
+  const float* resid;  // or null
+  const float* zd; const float* mean_d; const float* rstd_d; const float* gamma_d; const float* beta_d;
+  float* out; int relu;
+};
+int launch_gn_apply(const GNApply& a, int N, int HW, int C, cudaStream_t s);
+// GroupNorm backward: dy (fp32, grad of the GN output) -> dz (fp32 and/or op dtype),
+// per-image channel partials of dgamma/dbeta [N, C]
+int launch_gn_bwd(const float* dy, const float* z, const float* mean, const float* rstd,
+                  const float* gamma, int N, int HW, int C, float* dz32, void* dzop, bool op_bf16,
+                  float* dgamma_part, float* dbeta_part, cudaStream_t s);
+
+// dz = dy * (y > 0) written as fp32 (dz32) and/or op dtype (dzop); dy may equal dz32
+int launch_relu_bwd(const float* dy, const float* y, size_t n, float* dz32, void* dzop, bool op_bf16,
+                    cudaStream_t s);
+// dz += dy * (y > 0)   (used where a ReLU output feeds two consumers)
+int launch_add(float* dst, const float* src, size_t n, cudaStream_t s);
+
+int launch_maxpool_fwd(const float* x, int N, int H, int W, int C, float* y, uint8_t* arg,
+                       cudaStream_t s);
+int launch_maxpool_bwd(const float* dy, const uint8_t* arg, int N, int H, int W, int C, float* dx,
+                       cudaStream_t s);
+
+// out[c] (+)= sum_r in[r * ld + c], fixed summation order
+int launch_colsum(const float* in, int R, int Cc, int ld, float* out, bool accumulate,
+                  cudaStream_t s);
+
+// LSTM cell (gate order i, f, g, o). Step t of a [T, E] segment.
+struct LstmStep {
+  int E, H;
+  const float* gx;      // [E, 4H] input projection + both biases
+  const float* gh;      // [E, 4H] recurrent projection of the masked previous state
+  const float* c_prev;  // [E, H] (unmasked; mask m applied here)
+  const uint8_t* m;     // [E] mask of this step
+  const uint8_t* m_next;// [E] mask of the next step (null at the last)
+  float* gates;         // [E, 4H] post-activation i f g o
+  float* c;             // [E, H]
+  float* h;             // [E, H] fp32
+  void* y_op;           // [E, H] op dtype (layer output for the next layer / heads) or null
+  void* hm_next;        // [E, H] op dtype h * m_next (next recurrent GEMM operand) or null
+  bool op_bf16;
+};
+int launch_lstm_fwd(const LstmStep& a, cudaStream_t s);
+// hm = h0 * m (op dtype)
+int launch_mask_state(const float* h0, const uint8_t* m, int E, int H, void* hm, bool op_bf16,
+                      cudaStream_t s);
+
+struct LstmBack {
+  int E, H;
+  const float* gates; const float* c; const float* c_prev;  // forward values of step t
+  const uint8_t* m;         // mask of step t
+  const uint8_t* m_next;    // mask of step t+1 (applies to dh_rec / dc_carry) or null
+  const float* dh_above;    // [E, H]
+  const float* dh_rec;      // [E, H] dG_{t+1} W_hh (unmasked) or null at the last step
+  float* dc_carry;          // [E, H] in: dc_{t+1} f_{t+1} (unmasked); out: dc_t f_t
+  float* dg32;              // [E, 4H] fp32 dgates
+  void* dg_op;              // [E, 4H] op dtype dgates
+  bool op_bf16;
+};
+int launch_lstm_bwd(const LstmBack& a, cudaStream_t s);
+
+// heads: logits = h Wa^T + ba, value = h wv + bv (canonical fp32 weights)
+struct Heads {
+  int N, H;
+  const float* h;        // [N, H]
+  const float* Wa; const float* ba; const float* Wv; const float* bv;
+  float* logits;         // [N, 4] or null
+  float* value;          // [N]
+  // sampling (act): uniforms -> action, logp
+  const float* u; int32_t* action; float* logp;
+};
+int launch_heads_fwd(const Heads& a, cudaStream_t s);
+// dh[n] = dlogits[n] Wa + dvalue[n] wv ; weight grads via partials
+int launch_heads_bwd(int N, int H, const float* h, const float* Wa, const float* Wv,
+                     const float* dlogits, const float* dvalue, float* dh, float* gWa, float* gba,
+                     float* gWv, float* gbv, float* scratch, size_t scratch_elems, cudaStream_t s);
+
+// goal FC (3 -> 32) and action embedding (5 x 32) into columns [col0, col0+64) of x (op dtype)
+int launch_embed_fwd(int N, const float* goal, const int32_t* prev_a, const float* Wg,
+                     const float* bg, const float* Emb, void* x, int ldx, int col0, bool op_bf16,
+                     cudaStream_t s);
+int launch_embed_bwd(int N, const float* goal, const int32_t* prev_a, const float* dx, int lddx,
+                     int col0, float* gWg, float* gbg, float* gEmb, float* scratch,
+                     size_t scratch_elems, cudaStream_t s);
+// dv = dx[:, :H] * (v > 0) from the concatenated LSTM input gradient; v read from x (op dtype)
+int launch_vis_relu_bwd(int N, int H, const float* dx, int lddx, const void* x, int ldx,
+                        bool op_bf16, float* dv32, void* dvop, cudaStream_t s);
+
+// rows gather: out[t, j, :] = in[t, idx[j], :], rows of `bytes` bytes; idx null = identity
+int launch_gather_rows(const void* in, void* out, const int32_t* idx, int T, int Ein, int Eout,
+                       size_t bytes, cudaStream_t s);
+
+// weight preparation and gradient scatter between canonical and GEMM layouts
+int launch_conv_w_prep(const float* w, int cout, int cin, int k, int Kp, void* wg, void* wgT,
+                       bool op_bf16, cudaStream_t s);
+int launch_conv_w_grad(const float* dwg, int cout, int cin, int k, int Kp, float* dw,
+                       cudaStream_t s);
+// vis FC: canonical column j = c*HW + hw  <->  GEMM column hw*C + c
+int launch_vis_w_prep(const float* w, int H, int C, int HW, void* wg, void* wgT, bool op_bf16,
+                      cudaStream_t s);
+int launch_vis_w_grad(const float* dwg, int H, int C, int HW, float* dw, cudaStream_t s);
+int launch_add_vec(const float* a, const float* b, float* out, int n, cudaStream_t s);
+
+// deterministic parameter init from the counter hash
+int launch_init_uniform(float* p, size_t n, float lo, float hi, uint64_t seed, uint64_t stream,
+                        cudaStream_t s);
+int launch_fill(float* p, size_t n, float v, cudaStream_t s);
+
+}  // namespace ddppo

@@ -1,0 +1,173 @@
+"""GPU parity of the simulator (reset, step, ray-cast) and of GAE against the oracle.
+
+Bit-exact: scene grids, BFS distance fields, start/goal/heading, positions, headings,
+collisions, rewards (float32 bits), done flags, success and SPL. Depth: within 1e-4 m
+on >= 99.99% of pixels (a ray grazing an exact cell corner may differ; counted). GAE:
+within 1e-5 relative (absolute floor 1e-5) of the float64 recursion on the same
+float32 inputs.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import rl as OR
+from oracle import sim as OS
+from paper_1911_00357_gb300 import binding as B
+from paper_1911_00357_gb300.presets import make_config
+from tests import inputs as I
+from tests.gpu_util import Env, sim_config_from
+
+pytestmark = pytest.mark.gpu
+
+WORLDS = {
+    "bernoulli32": dict(preset="nature_fp32"),
+    "rooms128_pool": dict(preset="resnet", precision=0),
+    "rooms128_bf16": dict(preset="resnet", precision=1, num_envs=40),
+    "rooms_mixed": dict(preset="mixed_1024", num_envs=24, precision=0),
+    "bernoulli_mixed": dict(preset="nature_fp32", num_envs=40, grid_min=32, grid_max=128,
+                            depth_h=96, depth_w=96, terminal_mode=1, seed=7),
+}
+
+
+def _cfg(name):
+    d = dict(WORLDS[name])
+    return make_config(d.pop("preset"), **d)
+
+
+def _compare_world(env: Env, ref: OS.BatchSim, E: int):
+    st = env.get_state()
+    np.testing.assert_array_equal(st, ref.states)
+    grids, dists = env.get_grids()
+    for e in range(E):
+        g = int(st[e, OS.S_GRID])
+        np.testing.assert_array_equal(grids[e, :g * g].reshape(g, g), ref.grid(e))
+        np.testing.assert_array_equal(dists[e, :g * g].reshape(g, g), ref.dist(e))
+
+
+def _depth_mismatch(env: Env, ref: OS.BatchSim):
+    d_gpu = env.get_depth().astype(np.float64)
+    d_ref, g_ref = ref.render()
+    bad = np.abs(d_gpu - d_ref) > 1e-4
+    return int(bad.sum()), bad.size, d_ref, g_ref
+
+
+@pytest.mark.parametrize("world", list(WORLDS))
+def test_reset_parity(world):
+    cfg = _cfg(world)
+    env = Env(cfg)
+    try:
+        env.reset()
+        ref = OS.BatchSim(sim_config_from(cfg))
+        ref.reset()
+        _compare_world(env, ref, cfg.num_envs)
+        assert B.ddppo_device_status(env.h) == 0
+    finally:
+        env.close()
+
+
+@pytest.mark.parametrize("world", list(WORLDS))
+def test_step_and_depth_parity(world):
+    cfg = _cfg(world)
+    E = cfg.num_envs
+    env = Env(cfg)
+    try:
+        env.reset()
+        ref = OS.BatchSim(sim_config_from(cfg))
+        ref.reset()
+        K = 120
+        acts = I.random_actions(K, E, seed=11, p_stop=0.03)
+        bad_px, tot_px = 0, 0
+        scfg = sim_config_from(cfg)
+        pool = bool(cfg.pool2x2)
+        for t in range(K):
+            env.step(acts[t])
+            r, d, spl, info = ref.step(acts[t])
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(env.reward.cpu().numpy().view(np.uint32), r.view(np.uint32))
+            np.testing.assert_array_equal(env.done.cpu().numpy(), d)
+            gi = env.info.cpu().numpy()
+            np.testing.assert_array_equal(gi[:, 0], info[:, 0].astype(np.float32))
+            np.testing.assert_array_equal(gi[:, 1].view(np.uint32), spl.view(np.uint32))
+            np.testing.assert_array_equal(gi[:, 2], info[:, 1].astype(np.float32))
+            np.testing.assert_array_equal(gi[:, 3], info[:, 2].astype(np.float32))
+            np.testing.assert_array_equal(env.get_state(), ref.states)
+            if t % 30 == 0 or t == K - 1:
+                nb, n, d_ref, g_ref = _depth_mismatch(env, ref)
+                bad_px += nb
+                tot_px += n
+                # goal vector of the current (possibly auto-reset) episode
+                g = env.goal.cpu().numpy().astype(np.float64)
+                assert np.allclose(g[:, 0], g_ref[:, 0], rtol=2e-6, atol=1e-5)
+                assert np.allclose(g[:, 1:], g_ref[:, 1:], atol=2e-5)
+                # encoder input: pooled, normalised, cast
+                o_ref = OS.pool_obs(d_ref, pool, scfg.max_depth_m)
+                o = env.obs.float().cpu().numpy()[:, 0]
+                tol = (2.0 ** -8) * np.abs(o_ref) + 2e-5 if cfg.precision == 1 else 2e-5
+                ok = np.abs(o - o_ref) <= tol
+                assert ok.mean() >= 0.9999, (1 - ok.mean())
+        assert bad_px <= max(0, int(1e-4 * tot_px)), (bad_px, tot_px)
+        _compare_world(env, ref, E)
+        assert B.ddppo_device_status(env.h) == 0
+    finally:
+        env.close()
+
+
+def test_episodes_end_and_reset_inside_the_step():
+    """Stop everywhere: every env ends its episode, draws episode 1, and the new first
+    frame is what env_step returns (auto-reset)."""
+    cfg = make_config("nature_fp32", num_envs=8)
+    env = Env(cfg)
+    try:
+        env.reset()
+        ref = OS.BatchSim(sim_config_from(cfg))
+        ref.reset()
+        a = np.zeros(8, np.int32)
+        env.step(a)
+        r, d, spl, info = ref.step(a)
+        assert env.done.cpu().numpy().all() and d.all()
+        st = env.get_state()
+        assert (st[:, OS.S_EPISODE] >= 1).all() and (st[:, OS.S_STEPS] == 0).all()
+        np.testing.assert_array_equal(st, ref.states)
+    finally:
+        env.close()
+
+
+def test_invalid_action_sets_bounds_status():
+    cfg = make_config("nature_fp32", num_envs=4)
+    env = Env(cfg)
+    try:
+        env.reset()
+        assert B.ddppo_device_status(env.h) == 0
+        env.step(np.array([1, 7, 2, -1], np.int32))   # caught by the kernel's own range check
+        assert B.ddppo_device_status(env.h) == -4
+    finally:
+        env.close()
+
+
+def test_step_before_reset_is_a_state_error():
+    cfg = make_config("nature_fp32", num_envs=4)
+    env = Env(cfg)
+    try:
+        with pytest.raises(B.DDPPOError) as ei:
+            env.step(np.zeros(4, np.int32))
+        assert ei.value.code == -6
+    finally:
+        env.close()
+
+
+@pytest.mark.parametrize("T,E", [(1, 1), (128, 64), (33, 70), (32, 32), (5, 1000), (300, 3)])
+@pytest.mark.parametrize("lam", [0.95, 1.0, 0.0])
+def test_gae_parity(T, E, lam):
+    rng = np.random.default_rng(T * 1000 + E)
+    r = rng.normal(size=(T, E)).astype(np.float32)
+    d = (rng.random((T, E)) < 0.05).astype(np.uint8)
+    v = (3 * rng.normal(size=(T + 1, E))).astype(np.float32)
+    A_ref, R_ref = OR.gae(r, d, v, np.float32(0.99), np.float32(lam))
+    rt, dt, vt = (torch.from_numpy(x).cuda() for x in (r, d, v))
+    adv = torch.zeros(T, E, device="cuda")
+    ret = torch.zeros(T, E, device="cuda")
+    B.ddppo_gae(rt, dt, vt, T, E, 0.99, lam, adv, ret)
+    A = adv.cpu().numpy().astype(np.float64)
+    Rr = ret.cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(A - A_ref) <= 1e-5 * np.maximum(1.0, np.abs(A_ref)))
+    assert np.all(np.abs(Rr - R_ref) <= 1e-5 * np.maximum(1.0, np.abs(R_ref)))
