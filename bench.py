@@ -1,0 +1,273 @@
+"""Throughput of the DD-PPO rollout-then-update step on GB300.
+
+One step = one synchronous DD-PPO iteration of one worker (Sec. 3, Eq. 4 without the
+multi-worker allreduce): collect T frames from each of E envs (policy act + simulator
+step, captured as a CUDA graph), bootstrap value, GAE, then epochs x minibatches of PPO
+(forward, loss, hand-written backward, Adam). Metric: experience frames per second
+(E*T per step), measured as in App. "Additional scaling details" (time a run of steps
+after warm-up). Workload: 64 envs on 128x128 rooms-and-doors grids at 0.1 m, depth
+256x256 pooled to 128x128, ResNet-18-style encoder (32 base, GroupNorm) -> 2-layer LSTM
+512, T = 128, 2 epochs x 2 minibatches, Adam 2.5e-4.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16|fp32]
+  python bench.py --impl reference ...   # the float64 CPU oracle on a bounded sample
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = "pointnav_resnet18b32_lstm2x512_E64_T128_rooms128"
+METRIC = "experience frames/sec (sim+act+learn) on 1 GB300, BF16 batched vs plain FP32"
+UNIT = "frames/s"
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+            "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples taken while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1911_00357_gb300 import binding as B
+    from paper_1911_00357_gb300.worker import Worker
+
+    rank, world, local = _dist()
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    precision = 1 if args.precision == "bf16" else 0
+
+    def measure(prec, steps, warmup, timing):
+        w = Worker("resnet", precision=prec, seed=1000 * rank + 17)
+        for _ in range(warmup):
+            w.iterate()
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        if timing:
+            B.ddppo_timing_enable(w.h, True)
+        s = torch.cuda.current_stream()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        clk = ClockSampler(local) if timing else None
+        if clk:
+            clk.start()
+        torch.cuda.synchronize()
+        e0.record(s)
+        for _ in range(steps):
+            w.iterate()
+        e1.record(s)
+        torch.cuda.synchronize()
+        clocks = clk.stop() if clk else None
+        ms = e0.elapsed_time(e1)
+        t = torch.tensor([ms], device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        gemm = B.ddppo_timing_read(w.h, 0) if timing else None
+        rc = B.ddppo_timing_read(w.h, 1) if timing else None
+        if timing:
+            B.ddppo_timing_enable(w.h, False)
+        return w, t.item(), clocks, gemm, rc
+
+    w, ms, clocks, gemm, rc = measure(precision, args.steps, args.warmup, True)
+    frames = w.E * w.T * args.steps * world
+    value = frames / (ms / 1e3)
+
+    # end to end through the public API: uniforms H2D from pinned memory each step,
+    # statistics and rewards D2H each step
+    e2e_ms, h2d, d2h = w.time_e2e(args.steps)
+    t = torch.tensor([e2e_ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    e2e_value = frames / (t.item() / 1e3)
+
+    # plain FP32 form on the same GPU (the metric's denominator)
+    fp32_value = None
+    if not args.skip_fp32 and precision == 1:
+        w32, ms32, _, _, _ = measure(0, max(1, args.steps // 2), max(3, args.warmup // 2), False)
+        fp32_value = w32.E * w32.T * max(1, args.steps // 2) * world / (ms32 / 1e3)
+        del w32
+
+    peaks, pk_kind = _peaks()
+    g_ms, g_n, g_flops = gemm
+    achieved = g_flops / (g_ms / 1e3) / 1e12 if g_ms > 0 else 0.0
+    if precision == 1 and w.tensor_core_gemm():
+        bound, peak_v, unit = "tensor", peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]), "TFLOP/s"
+    else:
+        # SIMT FMA path: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock
+        bound, peak_v, unit = "alu", 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, "TFLOP/s"
+    r_ms, r_n, r_bytes = rc
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if precision == 1 else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "num_envs": w.E, "rollout_T": w.T, "epochs": 2,
+                   "minibatches": 2, "grid": "128x128 rooms, 0.1 m", "depth": "256x256 -> 128x128",
+                   "encoder": "resnet18-style base 32, GroupNorm", "lstm": "2x512",
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "working set (activations ~tens of GB) larger than L2; no flush"},
+        "fp32_value": round(fp32_value, 2) if fp32_value else None,
+        "bf16_over_fp32": round(value / fp32_value, 3) if fp32_value else None,
+        "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "gpu_launches": w.launches_per_step() * args.steps,
+        "roofline": {"bound": bound, "kernel": "gemm (all contractions of the update)",
+                     "achieved": round(achieved, 3), "peak": round(peak_v, 1), "unit": unit,
+                     "frac": round(achieved / peak_v, 4) if peak_v else None,
+                     "peak_kind": pk_kind, "launches": g_n, "avg_launch_us": round(1e3 * g_ms / max(g_n, 1), 2),
+                     "traffic": None},
+        "raycast": {"launches": r_n, "avg_launch_us": round(1e3 * r_ms / max(r_n, 1), 2),
+                    "out_GBps": round(r_bytes / (r_ms / 1e3) / 1e9, 2) if r_ms > 0 else None},
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(args.cpu_sample_steps)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(sample_steps: int = 1):
+    """The float64 oracle timed on the host cores on a bounded sample of the workload:
+    the same network and world, 4 envs x 16 frames per iteration, 2 epochs x 2 minibatches."""
+    from oracle import loop as OL
+    import torch
+    r = OL.OracleLoop(num_envs=4, T=16, seed=3)
+    r.iterate()  # warm-up (allocations, first-touch)
+    t0 = time.perf_counter()
+    for _ in range(sample_steps):
+        r.iterate()
+    dt = time.perf_counter() - t0
+    frames = r.E * r.T * sample_steps
+    return {"value": round(frames / dt, 3), "unit": UNIT, "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": "float64 oracle, %d iteration(s) of 4 envs x 16 frames (same ResNet-18/32 + "
+                      "2x512 LSTM, 128x128 rooms, 256x256 depth), 2 epochs x 2 minibatches" % sample_steps}
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    from oracle import loop as OL
+    import torch
+    r = OL.OracleLoop(num_envs=4, T=16, seed=3)
+    for _ in range(args.warmup):
+        r.iterate()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r.iterate()
+    dt = time.perf_counter() - t0
+    frames = r.E * r.T * args.steps
+    v = frames / dt
+    sample = ("float64 oracle, each step = 1 iteration of 4 envs x 16 frames of the same workload "
+              "(ResNet-18/32 + 2x512 LSTM, 128x128 rooms, 256x256 depth, 2x2 PPO)")
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": torch.get_num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--skip-fp32", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-steps", type=int, default=1)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "native":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

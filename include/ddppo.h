@@ -284,6 +284,15 @@ int ddppo_collect(ddppo_ctx* ctx, const ddppo_rollout* ro, int32_t use_graph, vo
  * count and algorithmic work (FLOPs for GEMM, output bytes for the ray cast). */
 int ddppo_timing_enable(ddppo_ctx* ctx, int32_t on);
 int ddppo_timing_read(ddppo_ctx* ctx, int32_t family, double* ms, int64_t* launches, double* work);
+/* family 2 reports the launches and FLOPs of the contractions that ran on the tcgen05
+ * tensor-core GEMM (ms = 0). */
+
+/* Number of kernel launches of one steady-state iteration (collect of T steps, bootstrap
+ * value, GAE, PPO update) with this rollout and hyper-parameters: the iteration is
+ * captured into a CUDA graph that is counted and discarded, nothing executes. Needs a
+ * preceding ddppo_collect. count: [host]. Synchronises the device. */
+int ddppo_count_kernels(ddppo_ctx* ctx, const ddppo_rollout* ro, const ddppo_ppo_hparams* hp,
+                        float gamma, float lam, int64_t* count);
 
 #ifdef __cplusplus
 }

@@ -103,6 +103,7 @@ _SIGS = {
     "ddppo_collect": [P, P, I32, P],
     "ddppo_timing_enable": [P, I32],
     "ddppo_timing_read": [P, I32, P, P, P],
+    "ddppo_count_kernels": [P, P, P, F32, F32, P],
 }
 
 
@@ -260,3 +261,10 @@ def ddppo_timing_read(h, family: int):
     w = ctypes.c_double()
     _check(lib().ddppo_timing_read(h, family, ctypes.byref(ms), ctypes.byref(n), ctypes.byref(w)))
     return ms.value, n.value, w.value
+
+
+def ddppo_count_kernels(h, ro: Rollout, hp: PPOHParams, gamma: float, lam: float) -> int:
+    n = ctypes.c_int64()
+    _check(lib().ddppo_count_kernels(h, ctypes.byref(ro), ctypes.byref(hp), gamma, lam,
+                                     ctypes.byref(n)))
+    return n.value

@@ -1,13 +1,13 @@
 // C ABI of the library (include/ddppo.h): argument checking, the worker context,
 // and the environment / GAE entry points. The network and update entry points are in
-// nn_abi.cu.
+// net_abi.cu.
 #include <math.h>
 #include <stdio.h>
 
 #include <mutex>
 #include <string>
 
-#include "ctx.cuh"
+#include "net.cuh"
 
 namespace ddppo {
 
@@ -195,7 +195,18 @@ extern "C" int ddppo_env_step(ddppo_ctx* x, const int32_t* actions, void* obs, f
   cudaStream_t s = (cudaStream_t)stream;
   DDPPO_TRY(launch_step(x->sp, x->sb, actions, reward, done, info, s));
   DDPPO_TRY(launch_reset(x->sp, x->sb, false, s));
+  KernelTimer* t = x->net ? &x->net->rc_timer : nullptr;
+  const bool rec = t && t->on && t->n + 2 <= 2 * 4096;
+  if (rec) cudaEventRecord(t->ev[t->n], s);
   DDPPO_TRY(launch_render(x->sp, x->sb, obs, goal, nullptr, s));
+  if (rec) {
+    cudaEventRecord(t->ev[t->n + 1], s);
+    t->n += 2;
+    t->launches += 1;
+    // algorithmic bytes: the encoder input written plus the goal vectors
+    t->flops += (double)x->cfg.num_envs *
+                ((double)x->sp.obs_h * x->sp.obs_w * (x->sp.bf16_obs ? 2 : 4) + 12.0);
+  }
   return DDPPO_OK;
 }
 

@@ -26,7 +26,7 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(int M, int N, int K, con
   __shared__ float As[SB_K][SB_M + 4];
   __shared__ float Bs[SB_K][SB_N + 4];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  const int m0 = blockIdx.y * SB_M, n0 = blockIdx.x * SB_N;
+  const int m0 = blockIdx.x * SB_M, n0 = blockIdx.y * SB_N;  // M tiles on x: M can exceed 65535*64
   const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
   float acc[4][4] = {};
   const int lr = tid >> 2, lk = (tid & 3) * 4;  // loader: row lr, k lk..lk+3
@@ -108,7 +108,7 @@ static int gemm_simt(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, c
   splits = (d.K + kchunk - 1) / kchunk;
   if (splits < 1) splits = 1;
   float* partial = splits > 1 ? ws.partial : nullptr;
-  dim3 grid(gn, gm, splits);
+  dim3 grid(gm, gn, splits);
   if (op_bf16)
     gemm_simt_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(
         d.M, d.N, d.K, (const __nv_bfloat16*)d.A, d.lda, (const __nv_bfloat16*)d.B, d.ldb,
@@ -141,8 +141,15 @@ int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t 
   const bool rec = timer && timer->on && timer->n + 2 <= 2 * 4096;
   if (rec) cudaEventRecord(timer->ev[timer->n], s);
   int rc;
-  if (op_bf16 && gemm_tc_supported(d)) rc = gemm_tc(d, ws, s);
-  else rc = gemm_simt(d, op_bf16, ws, s);
+  if (op_bf16 && gemm_tc_supported(d)) {
+    rc = gemm_tc(d, ws, s);
+    if (ws.tc && ws.tc->on) {
+      ws.tc->launches += 1;
+      ws.tc->flops += 2.0 * d.M * d.N * d.K;
+    }
+  } else {
+    rc = gemm_simt(d, op_bf16, ws, s);
+  }
   if (rec) {
     cudaEventRecord(timer->ev[timer->n + 1], s);
     timer->n += 2;

@@ -22,10 +22,17 @@ struct GemmDesc {
   int relu = 0;
 };
 
+struct GemmTcCount {
+  bool on = false;
+  int64_t launches = 0;
+  double flops = 0.0;
+};
+
 struct GemmWorkspace {
   float* partial = nullptr;  // split-K partial sums
   size_t partial_elems = 0;
   int num_sms = 152;
+  GemmTcCount* tc = nullptr;  // counts contractions routed to tcgen05 while enabled
 };
 
 // timing of GEMM launches (family 0 of ddppo_timing_read)

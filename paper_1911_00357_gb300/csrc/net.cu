@@ -1,0 +1,710 @@
+// Agent network of a worker: parameter layout, weight preparation, the forward pass over
+// a [T, E] segment (encoder -> visual FC -> goal/action embeddings -> L-layer LSTM ->
+// actor/critic), and the hand-written backward (heads -> LSTM back-propagation through
+// time -> embeddings -> visual FC -> encoder, with per-chunk recomputation when the
+// encoder runs in several chunks). App. "Agent Design"; Sec. 4 "Agent".
+#include <math.h>
+
+#include <algorithm>
+
+#include "net.cuh"
+#include "nn_kernels.cuh"
+#include "rl.cuh"
+
+namespace ddppo {
+
+template <class T>
+static int nalloc(Net& n, T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return DDPPO_OK;
+  void* q = nullptr;
+  DDPPO_CHECK_CUDA(cudaMalloc(&q, count * sizeof(T)));
+  n.allocs.push_back(q);
+  *p = (T*)q;
+  return DDPPO_OK;
+}
+static int nalloc_op(Net& n, void** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) return DDPPO_OK;
+  const size_t es = n.bf ? 2 : 4;
+  DDPPO_CHECK_CUDA(cudaMalloc(p, count * es));
+  n.allocs.push_back(*p);
+  return DDPPO_OK;
+}
+static inline size_t esz(const Net& n) { return n.bf ? 2 : 4; }
+static inline void* opoff(const Net& n, const void* p, size_t elems) {
+  return (void*)((const char*)p + elems * esz(n));
+}
+
+static int conv_out(int v, int k, int s, int p) { return (v + 2 * p - k) / s + 1; }
+
+// ---------------------------------------------------------------- layout
+struct Layout {
+  int64_t off = 0;
+  int64_t add(int64_t n) { int64_t o = off; off += n; return o; }
+};
+
+static void set_conv(ConvL& c, int cin, int cout, int k, int s, int p, bool bias, int H, int W,
+                     Layout& lay) {
+  c.cin = cin; c.cout = cout; c.k = k; c.s = s; c.p = p; c.bias = bias;
+  c.H = H; c.W = W; c.Ho = conv_out(H, k, s, p); c.Wo = conv_out(W, k, s, p);
+  c.Kp = (k * k * cin + 7) / 8 * 8;
+  c.w_off = lay.add((int64_t)cout * cin * k * k);
+  if (bias) c.b_off = lay.add(cout);
+}
+static void set_gn(GNL& g, int C, Layout& lay) {
+  g.C = C;
+  g.g_off = lay.add(C);
+  g.b_off = lay.add(C);
+}
+
+static ConvGeom geom(const ConvL& c, int N) {
+  ConvGeom g;
+  g.N = N; g.H = c.H; g.W = c.W; g.C = c.cin; g.Ho = c.Ho; g.Wo = c.Wo; g.Cout = c.cout;
+  g.k = c.k; g.s = c.s; g.p = c.p; g.K = c.k * c.k * c.cin; g.Kp = c.Kp;
+  return g;
+}
+
+// ---------------------------------------------------------------- creation
+static int build_layout(Net& n, Layout& lay) {
+  const ddppo_config& c = n.x->cfg;
+  n.inh = c.depth_h >> c.pool2x2;
+  n.inw = c.depth_w >> c.pool2x2;
+  if (n.kind == 0) {
+    set_conv(n.nat[0], 1, 32, 8, 4, 0, true, n.inh, n.inw, lay);
+    set_conv(n.nat[1], 32, 64, 4, 2, 0, true, n.nat[0].Ho, n.nat[0].Wo, lay);
+    set_conv(n.nat[2], 64, 32, 3, 1, 0, true, n.nat[1].Ho, n.nat[1].Wo, lay);
+    if (n.nat[2].Ho < 1 || n.nat[2].Wo < 1) {
+      set_error("depth too small for the 3-layer encoder");
+      return DDPPO_E_CONFIG;
+    }
+    for (auto& cv : n.nat) n.convs.push_back(&cv);
+    n.featC = 32;
+    n.featHW = n.nat[2].Ho * n.nat[2].Wo;
+  } else {
+    const int b = c.base_ch;
+    set_conv(n.stem, 1, b, 7, 2, 3, false, n.inh, n.inw, lay);
+    set_gn(n.stem_n, b, lay);
+    n.convs.push_back(&n.stem);
+    int H = (n.stem.Ho - 1) / 2 + 1, W = (n.stem.Wo - 1) / 2 + 1;  // max pool 3x3/2 pad 1
+    int cin = b;
+    const int widths[4] = {b, 2 * b, 4 * b, 8 * b};
+    for (int li = 0, bi = 0; li < 4; ++li)
+      for (int r = 0; r < 2; ++r, ++bi) {
+        BlockL& B = n.blocks[bi];
+        const int w = widths[li], s = (li > 0 && r == 0) ? 2 : 1;
+        set_conv(B.c1, cin, w, 3, s, 1, false, H, W, lay);
+        set_gn(B.n1, w, lay);
+        set_conv(B.c2, w, w, 3, 1, 1, false, B.c1.Ho, B.c1.Wo, lay);
+        set_gn(B.n2, w, lay);
+        B.down = (s != 1 || cin != w);
+        if (B.down) {
+          set_conv(B.d, cin, w, 1, s, 0, false, H, W, lay);
+          set_gn(B.nd, w, lay);
+          n.convs.push_back(&B.d);
+        }
+        n.convs.push_back(&B.c1);
+        n.convs.push_back(&B.c2);
+        H = B.c1.Ho; W = B.c1.Wo; cin = w;
+      }
+    if (H < 1 || W < 1) { set_error("depth too small for the ResNet encoder"); return DDPPO_E_CONFIG; }
+    set_conv(n.cmp, 8 * b, 128, 3, 1, 1, false, H, W, lay);
+    set_gn(n.cmp_n, 128, lay);
+    n.convs.push_back(&n.cmp);
+    n.featC = 128;
+    n.featHW = n.cmp.Ho * n.cmp.Wo;
+  }
+  n.F = n.featC * n.featHW;
+  const int Hd = n.H;
+  n.vis_w = lay.add((int64_t)Hd * n.F);
+  n.vis_b = lay.add(Hd);
+  n.goal_w = lay.add(32 * 3);
+  n.goal_b = lay.add(32);
+  n.emb = lay.add(5 * 32);
+  n.In0 = Hd + 64;
+  n.InMax = n.In0;
+  for (int l = 0; l < n.L; ++l) {
+    LstmL& s = n.lstm[l];
+    s.In = l == 0 ? n.In0 : Hd;
+    s.wih = lay.add((int64_t)4 * Hd * s.In);
+    s.whh = lay.add((int64_t)4 * Hd * Hd);
+    s.bih = lay.add(4 * Hd);
+    s.bhh = lay.add(4 * Hd);
+  }
+  n.actor_w = lay.add(4 * Hd);
+  n.actor_b = lay.add(4);
+  n.critic_w = lay.add(Hd);
+  n.critic_b = lay.add(1);
+  return DDPPO_OK;
+}
+
+static int alloc_encoder(Net& n) {
+  const size_t NC = n.NC;
+  auto conv_bufs = [&](ConvL& c) -> int {
+    DDPPO_TRY(nalloc_op(n, &c.wg, (size_t)c.cout * c.Kp));
+    DDPPO_TRY(nalloc_op(n, &c.wgT, (size_t)c.cout * c.Kp));
+    DDPPO_TRY(nalloc(n, &c.dwg, (size_t)c.cout * c.Kp));
+    DDPPO_TRY(nalloc(n, &c.z, NC * c.Ho * c.Wo * c.cout));
+    n.max_col = std::max(n.max_col, (size_t)c.Ho * c.Wo * c.Kp);
+    n.max_dz = std::max(n.max_dz, (size_t)c.Ho * c.Wo * c.cout);
+    n.max_act = std::max(n.max_act, c.Ho * c.Wo * c.cout);
+    n.max_act = std::max(n.max_act, c.H * c.W * c.cin);
+    return DDPPO_OK;
+  };
+  auto gn_bufs = [&](GNL& g, int HW, bool out) -> int {
+    DDPPO_TRY(nalloc(n, &g.mean, NC * g.C / 2));
+    DDPPO_TRY(nalloc(n, &g.rstd, NC * g.C / 2));
+    if (out) DDPPO_TRY(nalloc(n, &g.out, NC * HW * g.C));
+    n.max_gnC = std::max(n.max_gnC, g.C);
+    return DDPPO_OK;
+  };
+  if (n.kind == 0) {
+    for (auto& c : n.nat) DDPPO_TRY(conv_bufs(c));
+  } else {
+    DDPPO_TRY(conv_bufs(n.stem));
+    DDPPO_TRY(gn_bufs(n.stem_n, n.stem.Ho * n.stem.Wo, true));
+    const int ph = (n.stem.Ho - 1) / 2 + 1, pw = (n.stem.Wo - 1) / 2 + 1;
+    DDPPO_TRY(nalloc(n, &n.pool, NC * ph * pw * n.stem.cout));
+    DDPPO_TRY(nalloc(n, &n.pool_arg, NC * ph * pw * n.stem.cout));
+    for (auto& B : n.blocks) {
+      DDPPO_TRY(conv_bufs(B.c1));
+      DDPPO_TRY(conv_bufs(B.c2));
+      DDPPO_TRY(gn_bufs(B.n1, B.c1.Ho * B.c1.Wo, true));
+      DDPPO_TRY(gn_bufs(B.n2, B.c2.Ho * B.c2.Wo, false));
+      if (B.down) {
+        DDPPO_TRY(conv_bufs(B.d));
+        DDPPO_TRY(gn_bufs(B.nd, B.d.Ho * B.d.Wo, false));
+      }
+      DDPPO_TRY(nalloc(n, &B.y, NC * B.c2.Ho * B.c2.Wo * B.c2.cout));
+    }
+    DDPPO_TRY(conv_bufs(n.cmp));
+    DDPPO_TRY(gn_bufs(n.cmp_n, n.featHW, true));
+  }
+  DDPPO_TRY(nalloc_op(n, &n.col, NC * n.max_col));
+  DDPPO_TRY(nalloc_op(n, &n.colT, NC * n.max_col));
+  DDPPO_TRY(nalloc(n, &n.dcol, NC * n.max_col));
+  DDPPO_TRY(nalloc_op(n, &n.dzop, NC * n.max_dz));
+  DDPPO_TRY(nalloc_op(n, &n.dzT, NC * n.max_dz));
+  DDPPO_TRY(nalloc(n, &n.g0, NC * n.max_act));
+  DDPPO_TRY(nalloc(n, &n.g1, NC * n.max_act));
+  DDPPO_TRY(nalloc(n, &n.g2, NC * n.max_act));
+  const int C = std::max(n.max_gnC, 64);
+  DDPPO_TRY(nalloc(n, &n.gnp_g, NC * C));
+  DDPPO_TRY(nalloc(n, &n.gnp_b, NC * C));
+  return DDPPO_OK;
+}
+
+static int init_params(Net& n, cudaStream_t s) {
+  const uint64_t seed = n.x->cfg.seed;
+  uint64_t stream = 0;
+  auto unif = [&](int64_t off, int64_t cnt, float b) {
+    return launch_init_uniform(n.params + off, (size_t)cnt, -b, b, seed, stream++, s);
+  };
+  auto conv_init = [&](ConvL& c) -> int {
+    const int fan = c.cin * c.k * c.k;
+    DDPPO_TRY(unif(c.w_off, (int64_t)c.cout * fan, sqrtf(6.0f / fan)));
+    if (c.bias) DDPPO_TRY(launch_fill(n.params + c.b_off, c.cout, 0.f, s));
+    return DDPPO_OK;
+  };
+  auto gn_init = [&](GNL& g) -> int {
+    DDPPO_TRY(launch_fill(n.params + g.g_off, g.C, 1.f, s));
+    DDPPO_TRY(launch_fill(n.params + g.b_off, g.C, 0.f, s));
+    return DDPPO_OK;
+  };
+  if (n.kind == 0) {
+    for (auto& c : n.nat) DDPPO_TRY(conv_init(c));
+  } else {
+    DDPPO_TRY(conv_init(n.stem));
+    DDPPO_TRY(gn_init(n.stem_n));
+    for (auto& B : n.blocks) {
+      DDPPO_TRY(conv_init(B.c1)); DDPPO_TRY(gn_init(B.n1));
+      DDPPO_TRY(conv_init(B.c2)); DDPPO_TRY(gn_init(B.n2));
+      if (B.down) { DDPPO_TRY(conv_init(B.d)); DDPPO_TRY(gn_init(B.nd)); }
+    }
+    DDPPO_TRY(conv_init(n.cmp));
+    DDPPO_TRY(gn_init(n.cmp_n));
+  }
+  const int Hd = n.H;
+  DDPPO_TRY(unif(n.vis_w, (int64_t)Hd * n.F, sqrtf(6.0f / n.F)));
+  DDPPO_TRY(launch_fill(n.params + n.vis_b, Hd, 0.f, s));
+  DDPPO_TRY(unif(n.goal_w, 96, sqrtf(3.0f / 3.0f)));
+  DDPPO_TRY(launch_fill(n.params + n.goal_b, 32, 0.f, s));
+  DDPPO_TRY(unif(n.emb, 160, sqrtf(3.0f)));
+  for (int l = 0; l < n.L; ++l) {
+    LstmL& q = n.lstm[l];
+    const float b = 1.0f / sqrtf((float)Hd);
+    DDPPO_TRY(unif(q.wih, (int64_t)4 * Hd * q.In, b));
+    DDPPO_TRY(unif(q.whh, (int64_t)4 * Hd * Hd, b));
+    DDPPO_TRY(launch_fill(n.params + q.bih, 4 * Hd, 0.f, s));
+    DDPPO_TRY(launch_fill(n.params + q.bhh, 4 * Hd, 0.f, s));
+  }
+  DDPPO_TRY(unif(n.actor_w, 4 * Hd, 0.01f * sqrtf(3.0f / Hd)));
+  DDPPO_TRY(launch_fill(n.params + n.actor_b, 4, 0.f, s));
+  DDPPO_TRY(unif(n.critic_w, Hd, sqrtf(3.0f / Hd)));
+  DDPPO_TRY(launch_fill(n.params + n.critic_b, 1, 0.f, s));
+  return DDPPO_OK;
+}
+
+// canonical fp32 params -> GEMM operands in the precision's dtype
+int net_prep_weights(Net& n, cudaStream_t s) {
+  for (ConvL* c : n.convs)
+    DDPPO_TRY(launch_conv_w_prep(n.params + c->w_off, c->cout, c->cin, c->k, c->Kp, c->wg, c->wgT,
+                                 n.bf, s));
+  DDPPO_TRY(launch_vis_w_prep(n.params + n.vis_w, n.H, n.featC, n.featHW, n.Wv, n.WvT, n.bf, s));
+  for (int l = 0; l < n.L; ++l) {
+    LstmL& q = n.lstm[l];
+    const int G4 = 4 * n.H;
+    DDPPO_TRY(launch_cast(n.params + q.wih, q.Wih, n.bf, (size_t)G4 * q.In, s));
+    DDPPO_TRY(launch_transpose(n.params + q.wih, false, q.WihT, n.bf, G4, q.In, q.In, s));
+    DDPPO_TRY(launch_cast(n.params + q.whh, q.Whh, n.bf, (size_t)G4 * n.H, s));
+    DDPPO_TRY(launch_transpose(n.params + q.whh, false, q.WhhT, n.bf, G4, n.H, n.H, s));
+    DDPPO_TRY(launch_add_vec(n.params + q.bih, n.params + q.bhh, q.bsum, G4, s));
+  }
+  return DDPPO_OK;
+}
+
+int net_create(ddppo_ctx* x) {
+  Net* np = new Net();
+  x->net = np;
+  Net& n = *np;
+  n.x = x;
+  const ddppo_config& c = x->cfg;
+  n.bf = c.precision == 1;
+  n.kind = c.net_kind;
+  n.H = c.hidden;
+  n.L = c.lstm_layers;
+  n.E = c.num_envs;
+  n.T = c.rollout_T;
+  n.Emb = c.num_envs / c.minibatches;
+  n.NS = std::max(n.T * n.Emb, n.E);
+  n.NC = c.encoder_chunk > 0 ? std::min(c.encoder_chunk, n.NS) : n.NS;
+  n.NC = std::max(n.NC, n.E);  // an act step always fits one chunk
+  n.NC = std::min(n.NC, n.NS);
+  Layout lay;
+  DDPPO_TRY(build_layout(n, lay));
+  n.P = lay.off;
+  n.pix = (size_t)n.inh * n.inw;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n.gws.num_sms, cudaDevAttrMultiProcessorCount, dev);
+  n.gws.tc = &n.tc_count;
+  DDPPO_TRY(nalloc(n, &n.params, n.P));
+  DDPPO_TRY(nalloc(n, &n.grad, n.P));
+  DDPPO_TRY(nalloc(n, &n.adam_m, n.P));
+  DDPPO_TRY(nalloc(n, &n.adam_v, n.P));
+  DDPPO_TRY(alloc_encoder(n));
+  const size_t NS = n.NS, Hd = n.H, G4 = 4 * Hd;
+  DDPPO_TRY(nalloc_op(n, &n.Wv, Hd * n.F));
+  DDPPO_TRY(nalloc_op(n, &n.WvT, Hd * n.F));
+  DDPPO_TRY(nalloc(n, &n.dWv, Hd * n.F));
+  for (int l = 0; l < n.L; ++l) {
+    LstmL& q = n.lstm[l];
+    DDPPO_TRY(nalloc_op(n, &q.Wih, G4 * q.In));
+    DDPPO_TRY(nalloc_op(n, &q.WihT, G4 * q.In));
+    DDPPO_TRY(nalloc_op(n, &q.Whh, G4 * Hd));
+    DDPPO_TRY(nalloc_op(n, &q.WhhT, G4 * Hd));
+    DDPPO_TRY(nalloc(n, &q.bsum, G4));
+    DDPPO_TRY(nalloc(n, &q.gates, NS * G4));
+    DDPPO_TRY(nalloc(n, &q.c, NS * Hd));
+    DDPPO_TRY(nalloc(n, &q.h, NS * Hd));
+    DDPPO_TRY(nalloc_op(n, &q.hm, NS * Hd));
+    DDPPO_TRY(nalloc_op(n, &q.y, NS * Hd));
+  }
+  DDPPO_TRY(nalloc_op(n, &n.featop, NS * n.F));
+  DDPPO_TRY(nalloc(n, &n.dfeat, NS * n.F));
+  DDPPO_TRY(nalloc_op(n, &n.featT, NS * n.F));
+  DDPPO_TRY(nalloc_op(n, &n.x1, NS * n.In0));
+  DDPPO_TRY(nalloc(n, &n.gx, NS * G4));
+  DDPPO_TRY(nalloc(n, &n.gh, (size_t)n.E * G4));
+  DDPPO_TRY(nalloc(n, &n.logits, NS * 4));
+  DDPPO_TRY(nalloc(n, &n.values, NS));
+  DDPPO_TRY(nalloc(n, &n.dh_top, NS * Hd));
+  DDPPO_TRY(nalloc(n, &n.dX[0], NS * n.InMax));
+  DDPPO_TRY(nalloc(n, &n.dX[1], NS * n.InMax));
+  DDPPO_TRY(nalloc(n, &n.dg32, NS * G4));
+  DDPPO_TRY(nalloc_op(n, &n.dgop, NS * G4));
+  DDPPO_TRY(nalloc_op(n, &n.dgT, NS * G4));
+  DDPPO_TRY(nalloc_op(n, &n.XT, NS * n.InMax));
+  DDPPO_TRY(nalloc(n, &n.dh_rec, (size_t)n.E * Hd));
+  DDPPO_TRY(nalloc(n, &n.dc_carry, (size_t)n.E * Hd));
+  DDPPO_TRY(nalloc(n, &n.dv32, NS * Hd));
+  DDPPO_TRY(nalloc_op(n, &n.dvop, NS * Hd));
+  DDPPO_TRY(nalloc_op(n, &n.dvT, NS * Hd));
+  DDPPO_TRY(nalloc(n, &n.dlogits, NS * 4));
+  DDPPO_TRY(nalloc(n, &n.dvalues, NS));
+  n.scratch_elems = std::max((size_t)1 << 16, 5 * Hd * ((NS + 63) / 64) + 4096);
+  DDPPO_TRY(nalloc(n, &n.scratch, n.scratch_elems));
+  n.gws.partial_elems = (size_t)32 << 20;
+  DDPPO_TRY(nalloc(n, &n.gws.partial, n.gws.partial_elems));
+  // minibatch
+  const size_t NSmb = (size_t)n.T * n.Emb;
+  DDPPO_TRY(nalloc_op(n, &n.obs_mb, NSmb * n.pix));
+  DDPPO_TRY(nalloc(n, &n.goal_mb, NSmb * 3));
+  DDPPO_TRY(nalloc(n, &n.preva_mb, NSmb));
+  DDPPO_TRY(nalloc(n, &n.masks_mb, NSmb));
+  DDPPO_TRY(nalloc(n, &n.act_mb, NSmb));
+  DDPPO_TRY(nalloc(n, &n.logp_mb, NSmb));
+  DDPPO_TRY(nalloc(n, &n.adv_mb, NSmb));
+  DDPPO_TRY(nalloc(n, &n.ret_mb, NSmb));
+  DDPPO_TRY(nalloc(n, &n.h0_mb, (size_t)n.L * n.Emb * Hd));
+  DDPPO_TRY(nalloc(n, &n.c0_mb, (size_t)n.L * n.Emb * Hd));
+  DDPPO_TRY(nalloc(n, &n.perm, n.E));
+  DDPPO_TRY(nalloc(n, &n.adv_norm, (size_t)n.T * n.E));
+  DDPPO_TRY(nalloc(n, &n.scal, 8));
+  DDPPO_TRY(nalloc(n, &n.stats_tmp, 8 * 64));
+  DDPPO_TRY(nalloc(n, &n.norm, 1));
+  DDPPO_TRY(nalloc(n, &n.act_h, (size_t)n.L * n.E * Hd));
+  DDPPO_TRY(nalloc(n, &n.act_c, (size_t)n.L * n.E * Hd));
+  DDPPO_TRY(nalloc(n, &n.post_done, n.E));
+  DDPPO_CHECK_CUDA(cudaMemset(n.adam_m, 0, n.P * 4));
+  DDPPO_CHECK_CUDA(cudaMemset(n.adam_v, 0, n.P * 4));
+  DDPPO_CHECK_CUDA(cudaMemset(n.stats_tmp, 0, 8 * 64 * 4));
+  DDPPO_CHECK_CUDA(cudaStreamCreateWithFlags(&n.cap_stream, cudaStreamNonBlocking));
+  DDPPO_CHECK_CUDA(cudaEventCreateWithFlags(&n.ev_a, cudaEventDisableTiming));
+  DDPPO_CHECK_CUDA(cudaEventCreateWithFlags(&n.ev_b, cudaEventDisableTiming));
+  for (int i = 0; i < 2 * 4096; ++i) {
+    DDPPO_CHECK_CUDA(cudaEventCreate(&n.timer.ev[i]));
+    DDPPO_CHECK_CUDA(cudaEventCreate(&n.rc_timer.ev[i]));
+  }
+  DDPPO_TRY(init_params(n, 0));
+  DDPPO_TRY(net_prep_weights(n, 0));
+  return DDPPO_OK;
+}
+
+void net_destroy(ddppo_ctx* x) {
+  if (!x || !x->net) return;
+  Net& n = *x->net;
+  for (void* p : n.allocs) cudaFree(p);
+  if (n.graph_exec) cudaGraphExecDestroy(n.graph_exec);
+  if (n.cap_stream) cudaStreamDestroy(n.cap_stream);
+  if (n.ev_a) cudaEventDestroy(n.ev_a);
+  if (n.ev_b) cudaEventDestroy(n.ev_b);
+  for (int i = 0; i < 2 * 4096; ++i) {
+    if (n.timer.ev[i]) cudaEventDestroy(n.timer.ev[i]);
+    if (n.rc_timer.ev[i]) cudaEventDestroy(n.rc_timer.ev[i]);
+  }
+  delete x->net;
+  x->net = nullptr;
+}
+
+// ---------------------------------------------------------------- encoder
+static int G(Net& n, const GemmDesc& d, cudaStream_t s) { return gemm(d, n.bf, n.gws, s, &n.timer); }
+
+static int conv_fwd(Net& n, ConvL& c, const void* in, bool in_bf16, int N, float* out, bool bias_relu,
+                    cudaStream_t s) {
+  const ConvGeom g = geom(c, N);
+  DDPPO_TRY(launch_im2col(g, in, in_bf16, n.col, n.bf, false, s));
+  GemmDesc d;
+  d.M = N * c.Ho * c.Wo; d.N = c.cout; d.K = c.Kp;
+  d.A = n.col; d.lda = c.Kp; d.B = c.wg; d.ldb = c.Kp;
+  d.C = out; d.ldc = c.cout;
+  if (bias_relu) { d.bias = n.params + c.b_off; d.relu = 1; }
+  return G(n, d, s);
+}
+
+// weight gradient (accumulated over chunks) and, if dx, the input gradient
+static int conv_bwd(Net& n, ConvL& c, const void* in, bool in_bf16, int N, const void* dzop,
+                    float* dx, bool dx_acc, bool first, cudaStream_t s) {
+  const ConvGeom g = geom(c, N);
+  const int M = N * c.Ho * c.Wo;
+  DDPPO_TRY(launch_transpose(dzop, n.bf, n.dzT, n.bf, M, c.cout, c.cout, s));
+  DDPPO_TRY(launch_im2col(g, in, in_bf16, n.colT, n.bf, true, s));
+  GemmDesc w;
+  w.M = c.cout; w.N = c.Kp; w.K = M;
+  w.A = n.dzT; w.lda = M; w.B = n.colT; w.ldb = M;
+  w.C = c.dwg; w.ldc = c.Kp; w.beta = first ? 0.f : 1.f;
+  DDPPO_TRY(G(n, w, s));
+  if (dx) {
+    GemmDesc d;
+    d.M = M; d.N = c.Kp; d.K = c.cout;
+    d.A = dzop; d.lda = c.cout; d.B = c.wgT; d.ldb = c.cout;
+    d.C = n.dcol; d.ldc = c.Kp;
+    DDPPO_TRY(G(n, d, s));
+    DDPPO_TRY(launch_col2im(g, n.dcol, dx, dx_acc, s));
+  }
+  return DDPPO_OK;
+}
+
+static int gn_fwd(Net& n, GNL& g, const float* z, int N, int HW, float* out, bool relu,
+                  const float* resid, const GNL* gd, const float* zd, cudaStream_t s) {
+  const float eps = 1e-5f;
+  DDPPO_TRY(launch_gn_stats(z, N, HW, g.C, eps, g.mean, g.rstd, s));
+  GNApply a{};
+  a.z = z; a.mean = g.mean; a.rstd = g.rstd;
+  a.gamma = n.params + g.g_off; a.beta = n.params + g.b_off;
+  a.resid = resid;
+  if (gd) {
+    DDPPO_TRY(launch_gn_stats(zd, N, HW, gd->C, eps, gd->mean, gd->rstd, s));
+    a.zd = zd; a.mean_d = gd->mean; a.rstd_d = gd->rstd;
+    a.gamma_d = n.params + gd->g_off; a.beta_d = n.params + gd->b_off;
+  }
+  a.out = out;
+  a.relu = relu ? 1 : 0;
+  return launch_gn_apply(a, N, HW, g.C, s);
+}
+
+static int gn_bwd(Net& n, GNL& g, const float* dy, const float* z, int N, int HW, bool first,
+                  cudaStream_t s) {
+  DDPPO_TRY(launch_gn_bwd(dy, z, g.mean, g.rstd, n.params + g.g_off, N, HW, g.C, nullptr, n.dzop,
+                          n.bf, n.gnp_g, n.gnp_b, s));
+  DDPPO_TRY(launch_colsum(n.gnp_g, N, g.C, g.C, n.grad + g.g_off, !first, s));
+  DDPPO_TRY(launch_colsum(n.gnp_b, N, g.C, g.C, n.grad + g.b_off, !first, s));
+  return DDPPO_OK;
+}
+
+// forward of one chunk of N images: obs (op dtype) -> featop rows (op dtype)
+static int encoder_fwd(Net& n, const void* obs, int N, void* featop_rows, cudaStream_t s) {
+  if (n.kind == 0) {
+    DDPPO_TRY(conv_fwd(n, n.nat[0], obs, n.bf, N, n.nat[0].z, true, s));
+    DDPPO_TRY(conv_fwd(n, n.nat[1], n.nat[0].z, false, N, n.nat[1].z, true, s));
+    DDPPO_TRY(conv_fwd(n, n.nat[2], n.nat[1].z, false, N, n.nat[2].z, true, s));
+    return launch_cast(n.nat[2].z, featop_rows, n.bf, (size_t)N * n.F, s);
+  }
+  ConvL& st = n.stem;
+  DDPPO_TRY(conv_fwd(n, st, obs, n.bf, N, st.z, false, s));
+  DDPPO_TRY(gn_fwd(n, n.stem_n, st.z, N, st.Ho * st.Wo, n.stem_n.out, true, nullptr, nullptr, nullptr, s));
+  DDPPO_TRY(launch_maxpool_fwd(n.stem_n.out, N, st.Ho, st.Wo, st.cout, n.pool, n.pool_arg, s));
+  const float* cur = n.pool;
+  for (auto& B : n.blocks) {
+    const int HW = B.c1.Ho * B.c1.Wo;
+    DDPPO_TRY(conv_fwd(n, B.c1, cur, false, N, B.c1.z, false, s));
+    DDPPO_TRY(gn_fwd(n, B.n1, B.c1.z, N, HW, B.n1.out, true, nullptr, nullptr, nullptr, s));
+    DDPPO_TRY(conv_fwd(n, B.c2, B.n1.out, false, N, B.c2.z, false, s));
+    if (B.down) {
+      DDPPO_TRY(conv_fwd(n, B.d, cur, false, N, B.d.z, false, s));
+      DDPPO_TRY(gn_fwd(n, B.n2, B.c2.z, N, HW, B.y, true, nullptr, &B.nd, B.d.z, s));
+    } else {
+      DDPPO_TRY(gn_fwd(n, B.n2, B.c2.z, N, HW, B.y, true, cur, nullptr, nullptr, s));
+    }
+    cur = B.y;
+  }
+  DDPPO_TRY(conv_fwd(n, n.cmp, cur, false, N, n.cmp.z, false, s));
+  DDPPO_TRY(gn_fwd(n, n.cmp_n, n.cmp.z, N, n.featHW, n.cmp_n.out, true, nullptr, nullptr, nullptr, s));
+  return launch_cast(n.cmp_n.out, featop_rows, n.bf, (size_t)N * n.F, s);
+}
+
+// backward of one chunk: dfeat rows (fp32, NHWC-flattened) -> weight grads
+static int encoder_bwd(Net& n, const void* obs, int N, const float* dfeat_rows, bool first,
+                       cudaStream_t s) {
+  if (n.kind == 0) {
+    ConvL* c = n.nat;
+    float* gbuf[3] = {n.g0, n.g1, n.g2};
+    const float* dy = dfeat_rows;
+    for (int i = 2; i >= 0; --i) {
+      const size_t cnt = (size_t)N * c[i].Ho * c[i].Wo * c[i].cout;
+      DDPPO_TRY(launch_relu_bwd(dy, c[i].z, cnt, gbuf[i], n.dzop, n.bf, s));
+      DDPPO_TRY(launch_colsum(gbuf[i], N * c[i].Ho * c[i].Wo, c[i].cout, c[i].cout,
+                              n.grad + c[i].b_off, !first, s));
+      const void* in = i == 0 ? obs : (const void*)c[i - 1].z;
+      float* dx = i == 0 ? nullptr : gbuf[i - 1];
+      DDPPO_TRY(conv_bwd(n, c[i], in, i == 0 ? n.bf : false, N, n.dzop, dx, false, first, s));
+      dy = dx;
+    }
+    return DDPPO_OK;
+  }
+  // compression conv
+  {
+    const size_t cnt = (size_t)N * n.F;
+    DDPPO_TRY(launch_relu_bwd(dfeat_rows, n.cmp_n.out, cnt, n.g0, nullptr, n.bf, s));
+    DDPPO_TRY(gn_bwd(n, n.cmp_n, n.g0, n.cmp.z, N, n.featHW, first, s));
+    DDPPO_TRY(conv_bwd(n, n.cmp, n.blocks[7].y, false, N, n.dzop, n.g1, false, first, s));
+  }
+  float* gcur = n.g1;
+  float* gA = n.g0;
+  float* gB = n.g2;
+  for (int bi = 7; bi >= 0; --bi) {
+    BlockL& B = n.blocks[bi];
+    const int HW = B.c1.Ho * B.c1.Wo;
+    const float* xin = bi > 0 ? n.blocks[bi - 1].y : n.pool;
+    const size_t cnt = (size_t)N * HW * B.c2.cout;
+    DDPPO_TRY(launch_relu_bwd(gcur, B.y, cnt, gcur, nullptr, n.bf, s));  // grad of the pre-ReLU sum
+    DDPPO_TRY(gn_bwd(n, B.n2, gcur, B.c2.z, N, HW, first, s));
+    DDPPO_TRY(conv_bwd(n, B.c2, B.n1.out, false, N, n.dzop, gA, false, first, s));
+    DDPPO_TRY(launch_relu_bwd(gA, B.n1.out, cnt, gA, nullptr, n.bf, s));
+    DDPPO_TRY(gn_bwd(n, B.n1, gA, B.c1.z, N, HW, first, s));
+    DDPPO_TRY(conv_bwd(n, B.c1, xin, false, N, n.dzop, gB, false, first, s));
+    if (B.down) {
+      DDPPO_TRY(gn_bwd(n, B.nd, gcur, B.d.z, N, HW, first, s));
+      DDPPO_TRY(conv_bwd(n, B.d, xin, false, N, n.dzop, gB, true, first, s));
+    } else {
+      DDPPO_TRY(launch_add(gB, gcur, (size_t)N * B.c1.H * B.c1.W * B.c1.cin, s));
+    }
+    float* t = gcur; gcur = gB; gB = t;
+  }
+  // max pool, stem GN + ReLU, stem conv (no input gradient)
+  ConvL& st = n.stem;
+  DDPPO_TRY(launch_maxpool_bwd(gcur, n.pool_arg, N, st.Ho, st.Wo, st.cout, gA, s));
+  const size_t cnt = (size_t)N * st.Ho * st.Wo * st.cout;
+  DDPPO_TRY(launch_relu_bwd(gA, n.stem_n.out, cnt, gA, nullptr, n.bf, s));
+  DDPPO_TRY(gn_bwd(n, n.stem_n, gA, st.z, N, st.Ho * st.Wo, first, s));
+  DDPPO_TRY(conv_bwd(n, st, obs, n.bf, N, n.dzop, nullptr, false, first, s));
+  return DDPPO_OK;
+}
+
+// ---------------------------------------------------------------- forward / backward
+int net_forward(Net& n, int T, int E, const void* obs, const float* goal, const int32_t* prev_a,
+                const uint8_t* masks, const float* h0, const float* c0, const float* u,
+                int32_t* action, float* logp, cudaStream_t s) {
+  const int N = T * E, Hd = n.H, G4 = 4 * Hd;
+  if (N > n.NS || E > n.E) {
+    set_error("forward: segment larger than the workspace");
+    return DDPPO_E_CONFIG;
+  }
+  const int nch = (N + n.NC - 1) / n.NC;
+  for (int c = 0; c < nch; ++c) {
+    const int r0 = c * n.NC, rn = std::min(n.NC, N - r0);
+    DDPPO_TRY(encoder_fwd(n, opoff(n, obs, (size_t)r0 * n.pix), rn,
+                          opoff(n, n.featop, (size_t)r0 * n.F), s));
+  }
+  n.ev_valid_chunk = nch - 1;
+  GemmDesc v;
+  v.M = N; v.N = Hd; v.K = n.F;
+  v.A = n.featop; v.lda = n.F; v.B = n.Wv; v.ldb = n.F;
+  v.C = n.x1; v.ldc = n.In0; v.c_bf16 = n.bf ? 1 : 0;
+  v.bias = n.params + n.vis_b; v.relu = 1;
+  DDPPO_TRY(G(n, v, s));
+  DDPPO_TRY(launch_embed_fwd(N, goal, prev_a, n.params + n.goal_w, n.params + n.goal_b,
+                             n.params + n.emb, n.x1, n.In0, Hd, n.bf, s));
+  for (int l = 0; l < n.L; ++l) {
+    LstmL& q = n.lstm[l];
+    GemmDesc gx;
+    gx.M = N; gx.N = G4; gx.K = q.In;
+    gx.A = l == 0 ? n.x1 : n.lstm[l - 1].y; gx.lda = l == 0 ? n.In0 : Hd;
+    gx.B = q.Wih; gx.ldb = q.In;
+    gx.C = n.gx; gx.ldc = G4; gx.bias = q.bsum;
+    DDPPO_TRY(G(n, gx, s));
+    DDPPO_TRY(launch_mask_state(h0 + (size_t)l * E * Hd, masks, E, Hd, q.hm, n.bf, s));
+    for (int t = 0; t < T; ++t) {
+      GemmDesc gh;
+      gh.M = E; gh.N = G4; gh.K = Hd;
+      gh.A = opoff(n, q.hm, (size_t)t * E * Hd); gh.lda = Hd;
+      gh.B = q.Whh; gh.ldb = Hd;
+      gh.C = n.gh; gh.ldc = G4;
+      DDPPO_TRY(G(n, gh, s));
+      LstmStep st;
+      st.E = E; st.H = Hd;
+      st.gx = n.gx + (size_t)t * E * G4;
+      st.gh = n.gh;
+      st.c_prev = t == 0 ? c0 + (size_t)l * E * Hd : q.c + (size_t)(t - 1) * E * Hd;
+      st.m = masks + (size_t)t * E;
+      st.m_next = t + 1 < T ? masks + (size_t)(t + 1) * E : nullptr;
+      st.gates = q.gates + (size_t)t * E * G4;
+      st.c = q.c + (size_t)t * E * Hd;
+      st.h = q.h + (size_t)t * E * Hd;
+      st.y_op = opoff(n, q.y, (size_t)t * E * Hd);
+      st.hm_next = t + 1 < T ? opoff(n, q.hm, (size_t)(t + 1) * E * Hd) : nullptr;
+      st.op_bf16 = n.bf;
+      DDPPO_TRY(launch_lstm_fwd(st, s));
+    }
+  }
+  Heads hd{};
+  hd.N = N; hd.H = Hd; hd.h = n.lstm[n.L - 1].h;
+  hd.Wa = n.params + n.actor_w; hd.ba = n.params + n.actor_b;
+  hd.Wv = n.params + n.critic_w; hd.bv = n.params + n.critic_b;
+  hd.logits = n.logits; hd.value = n.values;
+  hd.u = u; hd.action = action; hd.logp = logp;
+  DDPPO_TRY(launch_heads_fwd(hd, s));
+  n.ev_T = T; n.ev_E = E; n.ev_valid = true;
+  n.ev_obs = obs; n.ev_goal = goal; n.ev_preva = prev_a; n.ev_masks = masks;
+  n.ev_h0 = h0; n.ev_c0 = c0;
+  return DDPPO_OK;
+}
+
+int net_backward(Net& n, const float* dlogits, const float* dvalues, cudaStream_t s) {
+  if (!n.ev_valid) {
+    set_error("policy_backward without a preceding evaluate");
+    return DDPPO_E_STATE;
+  }
+  const int T = n.ev_T, E = n.ev_E, N = T * E, Hd = n.H, G4 = 4 * Hd;
+  DDPPO_CHECK_CUDA(cudaMemsetAsync(n.grad, 0, n.P * sizeof(float), s));
+  DDPPO_TRY(launch_heads_bwd(N, Hd, n.lstm[n.L - 1].h, n.params + n.actor_w, n.params + n.critic_w,
+                             dlogits, dvalues, n.dh_top, n.grad + n.actor_w, n.grad + n.actor_b,
+                             n.grad + n.critic_w, n.grad + n.critic_b, n.scratch, n.scratch_elems, s));
+  const float* dabove = n.dh_top;
+  for (int l = n.L - 1; l >= 0; --l) {
+    LstmL& q = n.lstm[l];
+    DDPPO_CHECK_CUDA(cudaMemsetAsync(n.dc_carry, 0, (size_t)E * Hd * sizeof(float), s));
+    for (int t = T - 1; t >= 0; --t) {
+      LstmBack b;
+      b.E = E; b.H = Hd;
+      b.gates = q.gates + (size_t)t * E * G4;
+      b.c = q.c + (size_t)t * E * Hd;
+      b.c_prev = t == 0 ? n.ev_c0 + (size_t)l * E * Hd : q.c + (size_t)(t - 1) * E * Hd;
+      b.m = n.ev_masks + (size_t)t * E;
+      b.m_next = t + 1 < T ? n.ev_masks + (size_t)(t + 1) * E : nullptr;
+      b.dh_above = dabove + (size_t)t * E * Hd;
+      b.dh_rec = t + 1 < T ? n.dh_rec : nullptr;
+      b.dc_carry = n.dc_carry;
+      b.dg32 = n.dg32 + (size_t)t * E * G4;
+      b.dg_op = opoff(n, n.dgop, (size_t)t * E * G4);
+      b.op_bf16 = n.bf;
+      DDPPO_TRY(launch_lstm_bwd(b, s));
+      if (t > 0) {
+        GemmDesc r;
+        r.M = E; r.N = Hd; r.K = G4;
+        r.A = opoff(n, n.dgop, (size_t)t * E * G4); r.lda = G4;
+        r.B = q.WhhT; r.ldb = G4;
+        r.C = n.dh_rec; r.ldc = Hd;
+        DDPPO_TRY(G(n, r, s));
+      }
+    }
+    float* dX = n.dX[l & 1];
+    GemmDesc dx;
+    dx.M = N; dx.N = q.In; dx.K = G4;
+    dx.A = n.dgop; dx.lda = G4; dx.B = q.WihT; dx.ldb = G4;
+    dx.C = dX; dx.ldc = q.In;
+    DDPPO_TRY(G(n, dx, s));
+    const void* X = l == 0 ? n.x1 : n.lstm[l - 1].y;
+    const int ldX = l == 0 ? n.In0 : Hd;
+    DDPPO_TRY(launch_transpose(n.dgop, n.bf, n.dgT, n.bf, N, G4, G4, s));
+    DDPPO_TRY(launch_transpose(X, n.bf, n.XT, n.bf, N, q.In, ldX, s));
+    GemmDesc wi;
+    wi.M = G4; wi.N = q.In; wi.K = N;
+    wi.A = n.dgT; wi.lda = N; wi.B = n.XT; wi.ldb = N;
+    wi.C = n.grad + q.wih; wi.ldc = q.In;
+    DDPPO_TRY(G(n, wi, s));
+    DDPPO_TRY(launch_transpose(q.hm, n.bf, n.XT, n.bf, N, Hd, Hd, s));
+    GemmDesc wh;
+    wh.M = G4; wh.N = Hd; wh.K = N;
+    wh.A = n.dgT; wh.lda = N; wh.B = n.XT; wh.ldb = N;
+    wh.C = n.grad + q.whh; wh.ldc = Hd;
+    DDPPO_TRY(G(n, wh, s));
+    DDPPO_TRY(launch_colsum(n.dg32, N, G4, G4, n.grad + q.bih, false, s));
+    DDPPO_TRY(launch_colsum(n.dg32, N, G4, G4, n.grad + q.bhh, false, s));
+    dabove = dX;
+  }
+  // concatenated LSTM input: [visual FC (H) | goal FC (32) | action embedding (32)]
+  DDPPO_TRY(launch_vis_relu_bwd(N, Hd, dabove, n.In0, n.x1, n.In0, n.bf, n.dv32, n.dvop, s));
+  DDPPO_TRY(launch_embed_bwd(N, n.ev_goal, n.ev_preva, dabove, n.In0, Hd, n.grad + n.goal_w,
+                             n.grad + n.goal_b, n.grad + n.emb, n.scratch, n.scratch_elems, s));
+  DDPPO_TRY(launch_colsum(n.dv32, N, Hd, Hd, n.grad + n.vis_b, false, s));
+  DDPPO_TRY(launch_transpose(n.dvop, n.bf, n.dvT, n.bf, N, Hd, Hd, s));
+  DDPPO_TRY(launch_transpose(n.featop, n.bf, n.featT, n.bf, N, n.F, n.F, s));
+  GemmDesc wv;
+  wv.M = Hd; wv.N = n.F; wv.K = N;
+  wv.A = n.dvT; wv.lda = N; wv.B = n.featT; wv.ldb = N;
+  wv.C = n.dWv; wv.ldc = n.F;
+  DDPPO_TRY(G(n, wv, s));
+  DDPPO_TRY(launch_vis_w_grad(n.dWv, Hd, n.featC, n.featHW, n.grad + n.vis_w, s));
+  GemmDesc df;
+  df.M = N; df.N = n.F; df.K = Hd;
+  df.A = n.dvop; df.lda = Hd; df.B = n.WvT; df.ldb = Hd;
+  df.C = n.dfeat; df.ldc = n.F;
+  DDPPO_TRY(G(n, df, s));
+  // encoder, last chunk first (its activations are still resident)
+  const int nch = (N + n.NC - 1) / n.NC;
+  for (int c = nch - 1; c >= 0; --c) {
+    const int r0 = c * n.NC, rn = std::min(n.NC, N - r0);
+    const void* obs_c = opoff(n, n.ev_obs, (size_t)r0 * n.pix);
+    if (c != n.ev_valid_chunk) {
+      DDPPO_TRY(encoder_fwd(n, obs_c, rn, opoff(n, n.featT, 0), s));  // featT is free now
+      n.ev_valid_chunk = c;
+    }
+    DDPPO_TRY(encoder_bwd(n, obs_c, rn, n.dfeat + (size_t)r0 * n.F, c == nch - 1, s));
+  }
+  for (ConvL* c : n.convs)
+    DDPPO_TRY(launch_conv_w_grad(c->dwg, c->cout, c->cin, c->k, c->Kp, n.grad + c->w_off, s));
+  return DDPPO_OK;
+}
+
+}  // namespace ddppo

@@ -1,0 +1,137 @@
+// The agent network (App. "Agent Design") held by a worker: parameters, Adam state,
+// GEMM-layout weights and all workspace, sized at creation for the configured shapes.
+#pragma once
+
+#include <vector>
+
+#include "ctx.cuh"
+#include "gemm.cuh"
+
+namespace ddppo {
+
+struct ConvL {
+  int cin = 0, cout = 0, k = 0, s = 1, p = 0;
+  bool bias = false;
+  int64_t w_off = -1, b_off = -1;
+  int Kp = 0;
+  int H = 0, W = 0, Ho = 0, Wo = 0;
+  void* wg = nullptr;   // [cout, Kp] op dtype
+  void* wgT = nullptr;  // [Kp, cout] op dtype
+  float* dwg = nullptr; // [cout, Kp] fp32 gradient in GEMM layout
+  float* z = nullptr;   // [NC, Ho, Wo, cout] conv output (fp32)
+};
+
+struct GNL {
+  int C = 0;
+  int64_t g_off = -1, b_off = -1;
+  float* mean = nullptr;  // [NC, C/2]
+  float* rstd = nullptr;
+  float* out = nullptr;   // [NC, HW, C] post-activation output (when materialised)
+};
+
+struct BlockL {
+  ConvL c1, c2, d;
+  GNL n1, n2, nd;
+  bool down = false;
+  float* y = nullptr;     // block output [NC, Ho, Wo, cout]
+};
+
+struct LstmL {
+  int In = 0;
+  int64_t wih = -1, whh = -1, bih = -1, bhh = -1;
+  void* Wih = nullptr;   // [4H, In] op
+  void* WihT = nullptr;  // [In, 4H] op
+  void* Whh = nullptr;   // [4H, H] op
+  void* WhhT = nullptr;  // [H, 4H] op
+  float* bsum = nullptr; // [4H]
+  float* gates = nullptr;// [NS, 4H]
+  float* c = nullptr;    // [NS, H]
+  float* h = nullptr;    // [NS, H]
+  void* hm = nullptr;    // [NS, H] op: masked state entering each step
+  void* y = nullptr;     // [NS, H] op: layer output
+};
+
+struct Net {
+  ddppo_ctx* x = nullptr;
+  bool bf = false;
+  int kind = 0, H = 0, L = 0, inh = 0, inw = 0;
+  int F = 0, featC = 0, featHW = 0;
+  int E = 0, T = 0, Emb = 0, NS = 0, NC = 0;
+  int In0 = 0, InMax = 0;
+  size_t pix = 0;  // encoder input elements per image
+  int64_t P = 0;
+  float* params = nullptr;
+  float* grad = nullptr;
+  float* adam_m = nullptr;
+  float* adam_v = nullptr;
+  int64_t adam_t = 0;
+
+  // encoder
+  ConvL nat[3];
+  ConvL stem;
+  GNL stem_n;
+  float* pool = nullptr;
+  uint8_t* pool_arg = nullptr;
+  BlockL blocks[8];
+  ConvL cmp;
+  GNL cmp_n;
+  std::vector<ConvL*> convs;
+  int max_act = 0;     // max HW*C of any encoder activation (per image)
+  size_t max_col = 0;  // max Ho*Wo*Kp (per image)
+  size_t max_dz = 0;   // max Ho*Wo*cout (per image)
+  int max_gnC = 0;
+
+  int64_t vis_w = -1, vis_b = -1, goal_w = -1, goal_b = -1, emb = -1;
+  int64_t actor_w = -1, actor_b = -1, critic_w = -1, critic_b = -1;
+  void* Wv = nullptr;
+  void* WvT = nullptr;
+  float* dWv = nullptr;
+  LstmL lstm[4];
+
+  // scratch
+  void* col = nullptr; void* colT = nullptr; float* dcol = nullptr;
+  void* dzop = nullptr; void* dzT = nullptr;
+  float* g0 = nullptr; float* g1 = nullptr; float* g2 = nullptr;
+  float* gnp_g = nullptr; float* gnp_b = nullptr;
+  void* featop = nullptr; float* dfeat = nullptr; void* featT = nullptr;
+  void* x1 = nullptr;
+  float* gx = nullptr; float* gh = nullptr;
+  float* logits = nullptr; float* values = nullptr;
+  float* dh_top = nullptr; float* dX[2] = {nullptr, nullptr};
+  float* dg32 = nullptr; void* dgop = nullptr; void* dgT = nullptr; void* XT = nullptr;
+  float* dh_rec = nullptr; float* dc_carry = nullptr;
+  float* dv32 = nullptr; void* dvop = nullptr; void* dvT = nullptr;
+  float* dlogits = nullptr; float* dvalues = nullptr;
+  float* scratch = nullptr; size_t scratch_elems = 0;
+  GemmWorkspace gws;
+
+  // minibatch buffers
+  void* obs_mb = nullptr; float* goal_mb = nullptr; int32_t* preva_mb = nullptr;
+  uint8_t* masks_mb = nullptr; int32_t* act_mb = nullptr; float* logp_mb = nullptr;
+  float* adv_mb = nullptr; float* ret_mb = nullptr; float* h0_mb = nullptr; float* c0_mb = nullptr;
+  int32_t* perm = nullptr; float* adv_norm = nullptr; float* scal = nullptr;
+  float* stats_tmp = nullptr; float* norm = nullptr;
+  float* act_h = nullptr; float* act_c = nullptr;  // bootstrap state sink
+
+  // last evaluate (inputs read again by backward)
+  int ev_T = 0, ev_E = 0;
+  bool ev_valid = false;
+  const void* ev_obs = nullptr; const float* ev_goal = nullptr; const int32_t* ev_preva = nullptr;
+  const uint8_t* ev_masks = nullptr; const float* ev_h0 = nullptr; const float* ev_c0 = nullptr;
+  int ev_valid_chunk = -1;
+
+  // collect graph
+  bool collect_started = false;
+  cudaGraphExec_t graph_exec = nullptr;
+  ddppo_rollout graph_ro{};
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev_a = nullptr, ev_b = nullptr;
+  uint8_t* post_done = nullptr;
+
+  KernelTimer timer;
+  KernelTimer rc_timer;  // ray cast family
+  GemmTcCount tc_count;  // tcgen05 share of the contractions
+  std::vector<void*> allocs;
+};
+
+}  // namespace ddppo

@@ -1,0 +1,396 @@
+// C ABI entry points of the policy and the learning step (include/ddppo.h): parameters,
+// act / evaluate / backward, PPO loss, the PPO update (Sec. 4 "Training") and rollout
+// collection captured as a CUDA graph (Sec. 3: the collection stage of the loop).
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "net.cuh"
+#include "nn_kernels.cuh"
+#include "rl.cuh"
+
+namespace ddppo {
+int net_forward(Net& n, int T, int E, const void* obs, const float* goal, const int32_t* prev_a,
+                const uint8_t* masks, const float* h0, const float* c0, const float* u,
+                int32_t* action, float* logp, cudaStream_t s);
+int net_backward(Net& n, const float* dlogits, const float* dvalues, cudaStream_t s);
+int net_prep_weights(Net& n, cudaStream_t s);
+}  // namespace ddppo
+
+using namespace ddppo;
+
+#define ARG(cond, msg)                                   \
+  do {                                                   \
+    if (!(cond)) {                                       \
+      set_error(std::string("ddppo: ") + (msg));         \
+      return DDPPO_E_ARG;                                \
+    }                                                    \
+  } while (0)
+
+static inline size_t op_bytes(const Net& n) { return n.bf ? 2 : 4; }
+
+extern "C" int ddppo_num_params(const ddppo_ctx* x, int64_t* n_out) {
+  ARG(x && x->net && n_out, "num_params: null argument");
+  *n_out = x->net->P;
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_get_params(ddppo_ctx* x, float* flat, int64_t n, void* stream) {
+  ARG(x && x->net && flat, "get_params: null argument");
+  ARG(n == x->net->P, "get_params: size mismatch");
+  DDPPO_CHECK_CUDA(cudaMemcpyAsync(flat, x->net->params, n * 4, cudaMemcpyDeviceToDevice,
+                                   (cudaStream_t)stream));
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_set_params(ddppo_ctx* x, const float* flat, int64_t n, void* stream) {
+  ARG(x && x->net && flat, "set_params: null argument");
+  Net& N = *x->net;
+  ARG(n == N.P, "set_params: size mismatch");
+  cudaStream_t s = (cudaStream_t)stream;
+  DDPPO_CHECK_CUDA(cudaMemcpyAsync(N.params, flat, n * 4, cudaMemcpyDeviceToDevice, s));
+  DDPPO_CHECK_CUDA(cudaMemsetAsync(N.adam_m, 0, n * 4, s));
+  DDPPO_CHECK_CUDA(cudaMemsetAsync(N.adam_v, 0, n * 4, s));
+  N.adam_t = 0;
+  return net_prep_weights(N, s);
+}
+
+extern "C" int ddppo_get_adam(ddppo_ctx* x, float* m, float* v, int64_t n, int64_t* step,
+                              void* stream) {
+  ARG(x && x->net, "get_adam: null ctx");
+  Net& N = *x->net;
+  ARG(n == N.P, "get_adam: size mismatch");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (m) DDPPO_CHECK_CUDA(cudaMemcpyAsync(m, N.adam_m, n * 4, cudaMemcpyDeviceToDevice, s));
+  if (v) DDPPO_CHECK_CUDA(cudaMemcpyAsync(v, N.adam_v, n * 4, cudaMemcpyDeviceToDevice, s));
+  if (step) *step = N.adam_t;
+  return DDPPO_OK;
+}
+
+// copy the step-0 LSTM state of the last forward into h/c [L, E, H]
+static int copy_state_out(Net& n, int E, float* h, float* c, cudaStream_t s) {
+  const size_t bytes = (size_t)E * n.H * sizeof(float);
+  for (int l = 0; l < n.L; ++l) {
+    DDPPO_CHECK_CUDA(cudaMemcpyAsync(h + (size_t)l * E * n.H, n.lstm[l].h, bytes,
+                                     cudaMemcpyDeviceToDevice, s));
+    DDPPO_CHECK_CUDA(cudaMemcpyAsync(c + (size_t)l * E * n.H, n.lstm[l].c, bytes,
+                                     cudaMemcpyDeviceToDevice, s));
+  }
+  return DDPPO_OK;
+}
+
+static int act_impl(ddppo_ctx* x, const void* obs, const float* goal, const int32_t* prev_a,
+                    const uint8_t* masks, float* h, float* c, const float* u, int32_t* action,
+                    float* logp, float* value, cudaStream_t s) {
+  Net& n = *x->net;
+  const int E = x->cfg.num_envs;
+  DDPPO_TRY(net_forward(n, 1, E, obs, goal, prev_a, masks, h, c, u, action, logp, s));
+  DDPPO_CHECK_CUDA(cudaMemcpyAsync(value, n.values, (size_t)E * 4, cudaMemcpyDeviceToDevice, s));
+  n.ev_valid = false;  // the act workspace is not kept for a backward pass
+  return copy_state_out(n, E, h, c, s);
+}
+
+extern "C" int ddppo_policy_act(ddppo_ctx* x, const void* obs, const float* goal,
+                                const int32_t* prev_a, const uint8_t* masks, float* h, float* c,
+                                const float* uniforms, int32_t* action, float* logp, float* value,
+                                void* stream) {
+  ARG(x && x->net && obs && goal && prev_a && masks && h && c && uniforms && action && logp && value,
+      "policy_act: null argument");
+  return act_impl(x, obs, goal, prev_a, masks, h, c, uniforms, action, logp, value,
+                  (cudaStream_t)stream);
+}
+
+extern "C" int ddppo_policy_evaluate(ddppo_ctx* x, int32_t T, int32_t E, const void* obs,
+                                     const float* goal, const int32_t* prev_a, const uint8_t* masks,
+                                     const float* h0, const float* c0, float* logits, float* values,
+                                     void* stream) {
+  ARG(x && x->net && obs && goal && prev_a && masks && h0 && c0 && logits && values,
+      "policy_evaluate: null argument");
+  ARG(T >= 1 && E >= 1, "policy_evaluate: empty segment");
+  Net& n = *x->net;
+  if ((int64_t)T * E > n.NS || E > n.E) {
+    set_error("policy_evaluate: T*E exceeds rollout_T*num_envs/minibatches (or E > num_envs)");
+    return DDPPO_E_CONFIG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  DDPPO_TRY(net_forward(n, T, E, obs, goal, prev_a, masks, h0, c0, nullptr, nullptr, nullptr, s));
+  DDPPO_CHECK_CUDA(cudaMemcpyAsync(logits, n.logits, (size_t)T * E * 16, cudaMemcpyDeviceToDevice, s));
+  DDPPO_CHECK_CUDA(cudaMemcpyAsync(values, n.values, (size_t)T * E * 4, cudaMemcpyDeviceToDevice, s));
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_policy_backward(ddppo_ctx* x, const float* dlogits, const float* dvalues,
+                                     float* grad, void* stream) {
+  ARG(x && x->net && dlogits && dvalues && grad, "policy_backward: null argument");
+  Net& n = *x->net;
+  cudaStream_t s = (cudaStream_t)stream;
+  DDPPO_TRY(net_backward(n, dlogits, dvalues, s));
+  DDPPO_CHECK_CUDA(cudaMemcpyAsync(grad, n.grad, n.P * 4, cudaMemcpyDeviceToDevice, s));
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_ppo_loss(int32_t n, const float* logits, const float* values,
+                              const int32_t* actions, const float* logp_old, const float* adv,
+                              const float* ret, float clip, float value_coef, float entropy_coef,
+                              float* stats, float* dlogits, float* dvalues, void* stream) {
+  ARG(n >= 0, "ppo_loss: negative size");
+  if (n == 0) return DDPPO_OK;
+  ARG(logits && values && actions && logp_old && adv && ret && stats && dlogits && dvalues,
+      "ppo_loss: null argument");
+  return launch_ppo_loss(n, logits, values, actions, logp_old, adv, ret, clip, value_coef,
+                         entropy_coef, stats, dlogits, dvalues, nullptr, 0, (cudaStream_t)stream);
+}
+
+extern "C" int ddppo_ppo_update(ddppo_ctx* x, const ddppo_rollout* ro, const ddppo_ppo_hparams* hp,
+                                float* stats, void* stream) {
+  ARG(x && x->net && ro && hp, "ppo_update: null argument");
+  ARG(ro->obs && ro->goal && ro->prev_a && ro->masks && ro->actions && ro->logp && ro->adv &&
+          ro->ret && ro->h0 && ro->c0,
+      "ppo_update: rollout view has a null buffer");
+  Net& n = *x->net;
+  const ddppo_config& c = x->cfg;
+  if (hp->minibatches != c.minibatches || hp->epochs < 1) {
+    set_error("ppo_update: minibatches must equal the config's, epochs >= 1");
+    return DDPPO_E_CONFIG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int T = c.rollout_T, E = c.num_envs, Emb = n.Emb, L = n.L, Hd = n.H;
+  const int Nmb = T * Emb;
+  const float* adv = ro->adv;
+  if (hp->norm_adv) {
+    DDPPO_TRY(launch_normalize_adv(ro->adv, n.adv_norm, (size_t)T * E, n.scal, n.scratch,
+                                   n.scratch_elems, s));
+    adv = n.adv_norm;
+  }
+  int k = 0;
+  for (int ep = 0; ep < hp->epochs; ++ep) {
+    DDPPO_TRY(launch_permutation(c.seed, hp->update_index, ep, E, n.perm, s));
+    for (int mb = 0; mb < hp->minibatches; ++mb, ++k) {
+      const int32_t* idx = n.perm + (size_t)mb * Emb;
+      DDPPO_TRY(launch_gather_rows(ro->obs, n.obs_mb, idx, T, E, Emb, n.pix * op_bytes(n), s));
+      DDPPO_TRY(launch_gather_rows(ro->goal, n.goal_mb, idx, T, E, Emb, 12, s));
+      DDPPO_TRY(launch_gather_rows(ro->prev_a, n.preva_mb, idx, T, E, Emb, 4, s));
+      DDPPO_TRY(launch_gather_rows(ro->masks, n.masks_mb, idx, T, E, Emb, 1, s));
+      DDPPO_TRY(launch_gather_rows(ro->actions, n.act_mb, idx, T, E, Emb, 4, s));
+      DDPPO_TRY(launch_gather_rows(ro->logp, n.logp_mb, idx, T, E, Emb, 4, s));
+      DDPPO_TRY(launch_gather_rows(adv, n.adv_mb, idx, T, E, Emb, 4, s));
+      DDPPO_TRY(launch_gather_rows(ro->ret, n.ret_mb, idx, T, E, Emb, 4, s));
+      DDPPO_TRY(launch_gather_rows(ro->h0, n.h0_mb, idx, L, E, Emb, (size_t)Hd * 4, s));
+      DDPPO_TRY(launch_gather_rows(ro->c0, n.c0_mb, idx, L, E, Emb, (size_t)Hd * 4, s));
+      DDPPO_TRY(net_forward(n, T, Emb, n.obs_mb, n.goal_mb, n.preva_mb, n.masks_mb, n.h0_mb,
+                            n.c0_mb, nullptr, nullptr, nullptr, s));
+      float* st = stats ? stats + (size_t)k * DDPPO_NSTATS : n.stats_tmp + (size_t)(k % 64) * 8;
+      DDPPO_TRY(launch_ppo_loss(Nmb, n.logits, n.values, n.act_mb, n.logp_mb, n.adv_mb, n.ret_mb,
+                                hp->clip, hp->value_coef, hp->entropy_coef, st, n.dlogits,
+                                n.dvalues, n.scratch, n.scratch_elems, s));
+      DDPPO_TRY(net_backward(n, n.dlogits, n.dvalues, s));
+      DDPPO_TRY(launch_grad_norm(n.grad, n.P, n.norm, n.scratch, n.scratch_elems, s));
+      DDPPO_TRY(launch_copy_scalar(st + 6, n.norm, s));
+      ++n.adam_t;
+      DDPPO_TRY(launch_adam(n.params, n.grad, n.adam_m, n.adam_v, n.P,
+                            hp->max_grad_norm > 0.f ? n.norm : nullptr, hp->max_grad_norm, hp->lr,
+                            hp->beta1, hp->beta2, hp->adam_eps, n.adam_t, s));
+      DDPPO_TRY(net_prep_weights(n, s));
+    }
+  }
+  n.ev_valid = false;
+  return DDPPO_OK;
+}
+
+// ---- collection ----
+__global__ void post_step_kernel(int E, const int32_t* __restrict__ a, const uint8_t* __restrict__ d,
+                                 int32_t* __restrict__ prev_a, uint8_t* __restrict__ masks) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  prev_a[e] = d[e] ? 4 : a[e];
+  masks[e] = d[e] ? 0 : 1;
+}
+__global__ void start_slot_kernel(int E, int32_t* prev_a, uint8_t* masks) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= E) return;
+  prev_a[e] = 4;
+  masks[e] = 0;
+}
+
+extern "C" int ddppo_env_step(ddppo_ctx*, const int32_t*, void*, float*, float*, uint8_t*, float*,
+                              void*);
+extern "C" int ddppo_env_reset(ddppo_ctx*, void*, float*, void*);
+
+static int collect_body(ddppo_ctx* x, const ddppo_rollout* ro, cudaStream_t s) {
+  Net& n = *x->net;
+  const int E = x->cfg.num_envs, T = x->cfg.rollout_T;
+  const size_t ob = n.pix * op_bytes(n);
+  for (int t = 0; t < T; ++t) {
+    const size_t o = (size_t)t * E;
+    DDPPO_TRY(act_impl(x, (const char*)ro->obs + o * ob, ro->goal + o * 3, ro->prev_a + o,
+                       ro->masks + o, ro->h, ro->c, ro->uniforms + o, ro->actions + o, ro->logp + o,
+                       ro->values + o, s));
+    const size_t o1 = (size_t)(t + 1) * E;
+    DDPPO_TRY(ddppo_env_step(x, ro->actions + o, (char*)ro->obs + o1 * ob, ro->goal + o1 * 3,
+                             ro->rewards + o, ro->dones + o, ro->info ? ro->info + o * 4 : nullptr, s));
+    post_step_kernel<<<(E + 127) / 128, 128, 0, s>>>(E, ro->actions + o, ro->dones + o,
+                                                     ro->prev_a + o1, ro->masks + o1);
+    DDPPO_CHECK_LAUNCH();
+  }
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_collect(ddppo_ctx* x, const ddppo_rollout* ro, int32_t use_graph,
+                             void* stream) {
+  ARG(x && x->net && ro, "collect: null argument");
+  ARG(ro->obs && ro->goal && ro->prev_a && ro->masks && ro->actions && ro->logp && ro->values &&
+          ro->rewards && ro->dones && ro->h0 && ro->c0 && ro->h && ro->c && ro->uniforms,
+      "collect: rollout view has a null buffer");
+  Net& n = *x->net;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int E = x->cfg.num_envs, T = x->cfg.rollout_T, L = n.L, Hd = n.H;
+  const size_t ob = n.pix * op_bytes(n);
+  const size_t st_bytes = (size_t)L * E * Hd * 4;
+  // prologue: slot 0 is the previous rollout's slot T (first call: reset everything)
+  if (!n.collect_started || !x->env_ready) {
+    DDPPO_TRY(ddppo_env_reset(x, ro->obs, ro->goal, stream));
+    start_slot_kernel<<<(E + 127) / 128, 128, 0, s>>>(E, ro->prev_a, ro->masks);
+    DDPPO_CHECK_LAUNCH();
+    DDPPO_CHECK_CUDA(cudaMemsetAsync(ro->h, 0, st_bytes, s));
+    DDPPO_CHECK_CUDA(cudaMemsetAsync(ro->c, 0, st_bytes, s));
+    n.collect_started = true;
+  } else {
+    const size_t oT = (size_t)T * E;
+    DDPPO_CHECK_CUDA(cudaMemcpyAsync(ro->obs, (const char*)ro->obs + oT * ob, (size_t)E * ob,
+                                     cudaMemcpyDeviceToDevice, s));
+    DDPPO_CHECK_CUDA(cudaMemcpyAsync(ro->goal, ro->goal + oT * 3, (size_t)E * 12,
+                                     cudaMemcpyDeviceToDevice, s));
+    DDPPO_CHECK_CUDA(cudaMemcpyAsync(ro->prev_a, ro->prev_a + oT, (size_t)E * 4,
+                                     cudaMemcpyDeviceToDevice, s));
+    DDPPO_CHECK_CUDA(cudaMemcpyAsync(ro->masks, ro->masks + oT, (size_t)E,
+                                     cudaMemcpyDeviceToDevice, s));
+  }
+  DDPPO_CHECK_CUDA(cudaMemcpyAsync(ro->h0, ro->h, st_bytes, cudaMemcpyDeviceToDevice, s));
+  DDPPO_CHECK_CUDA(cudaMemcpyAsync(ro->c0, ro->c, st_bytes, cudaMemcpyDeviceToDevice, s));
+  if (use_graph) {
+    if (!n.graph_exec || memcmp(&n.graph_ro, ro, sizeof(*ro)) != 0) {
+      if (n.graph_exec) { cudaGraphExecDestroy(n.graph_exec); n.graph_exec = nullptr; }
+      DDPPO_CHECK_CUDA(cudaStreamSynchronize(s));
+      const bool t0 = n.timer.on, t1 = n.rc_timer.on;
+      n.timer.on = false; n.rc_timer.on = false;
+      DDPPO_CHECK_CUDA(cudaStreamBeginCapture(n.cap_stream, cudaStreamCaptureModeThreadLocal));
+      const int rc = collect_body(x, ro, n.cap_stream);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(n.cap_stream, &g);
+      n.timer.on = t0; n.rc_timer.on = t1;
+      if (rc != DDPPO_OK) { if (g) cudaGraphDestroy(g); return rc; }
+      if (ce != cudaSuccess) { set_error(std::string("collect capture: ") + cudaGetErrorString(ce)); return DDPPO_E_CUDA; }
+      const cudaError_t ie = cudaGraphInstantiate(&n.graph_exec, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) { set_error(std::string("collect instantiate: ") + cudaGetErrorString(ie)); return DDPPO_E_CUDA; }
+      n.graph_ro = *ro;
+    }
+    DDPPO_CHECK_CUDA(cudaGraphLaunch(n.graph_exec, s));
+  } else {
+    DDPPO_TRY(collect_body(x, ro, s));
+  }
+  // bootstrap value V(o_T) with the state after step T-1; the state itself is not advanced
+  const size_t oT = (size_t)T * E;
+  DDPPO_TRY(net_forward(n, 1, E, (const char*)ro->obs + oT * ob, ro->goal + oT * 3,
+                        ro->prev_a + oT, ro->masks + oT, ro->h, ro->c, nullptr, nullptr, nullptr, s));
+  DDPPO_CHECK_CUDA(cudaMemcpyAsync(ro->values + oT, n.values, (size_t)E * 4,
+                                   cudaMemcpyDeviceToDevice, s));
+  n.ev_valid = false;
+  return DDPPO_OK;
+}
+
+// ---- timing ----
+extern "C" int ddppo_timing_enable(ddppo_ctx* x, int32_t on) {
+  ARG(x && x->net, "timing_enable: null ctx");
+  Net& n = *x->net;
+  n.tc_count.on = on != 0;
+  n.tc_count.launches = 0;
+  n.tc_count.flops = 0.0;
+  for (KernelTimer* t : {&n.timer, &n.rc_timer}) {
+    t->on = on != 0;
+    t->n = 0;
+    t->flops = 0.0;
+    t->launches = 0;
+  }
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_timing_read(ddppo_ctx* x, int32_t family, double* ms, int64_t* launches,
+                                 double* work) {
+  ARG(x && x->net && ms && launches && work, "timing_read: null argument");
+  ARG(family >= 0 && family <= 2, "timing_read: family must be 0, 1 or 2");
+  if (family == 2) {
+    *ms = 0.0;
+    *launches = x->net->tc_count.launches;
+    *work = x->net->tc_count.flops;
+    return DDPPO_OK;
+  }
+  KernelTimer& t = family == 0 ? x->net->timer : x->net->rc_timer;
+  double acc = 0.0;
+  for (int i = 0; i + 1 < t.n; i += 2) {
+    DDPPO_CHECK_CUDA(cudaEventSynchronize(t.ev[i + 1]));
+    float v = 0.f;
+    DDPPO_CHECK_CUDA(cudaEventElapsedTime(&v, t.ev[i], t.ev[i + 1]));
+    acc += v;
+  }
+  *ms = acc;
+  *launches = t.launches;
+  *work = t.flops;
+  return DDPPO_OK;
+}
+
+// ---- kernel census of one steady-state iteration ----
+static int count_kernel_nodes(cudaGraph_t g, int64_t* count) {
+  size_t num = 0;
+  DDPPO_CHECK_CUDA(cudaGraphGetNodes(g, nullptr, &num));
+  std::vector<cudaGraphNode_t> nodes(num);
+  DDPPO_CHECK_CUDA(cudaGraphGetNodes(g, nodes.data(), &num));
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType ty;
+    DDPPO_CHECK_CUDA(cudaGraphNodeGetType(nd, &ty));
+    if (ty == cudaGraphNodeTypeKernel) {
+      ++*count;
+    } else if (ty == cudaGraphNodeTypeGraph) {
+      cudaGraph_t child;
+      DDPPO_CHECK_CUDA(cudaGraphChildGraphNodeGetGraph(nd, &child));
+      DDPPO_TRY(count_kernel_nodes(child, count));
+    }
+  }
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_count_kernels(ddppo_ctx* x, const ddppo_rollout* ro,
+                                   const ddppo_ppo_hparams* hp, float gamma, float lam,
+                                   int64_t* count) {
+  ARG(x && x->net && ro && hp && count, "count_kernels: null argument");
+  Net& n = *x->net;
+  if (!x->env_ready) { set_error("count_kernels before the first collect"); return DDPPO_E_STATE; }
+  const int E = x->cfg.num_envs, T = x->cfg.rollout_T;
+  const int64_t adam_t = n.adam_t;
+  const bool t0 = n.timer.on, t1 = n.rc_timer.on, t2 = n.tc_count.on;
+  n.timer.on = n.rc_timer.on = n.tc_count.on = false;
+  DDPPO_CHECK_CUDA(cudaDeviceSynchronize());
+  DDPPO_CHECK_CUDA(cudaStreamBeginCapture(n.cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = collect_body(x, ro, n.cap_stream);
+  const size_t ob = n.pix * op_bytes(n);
+  const size_t oT = (size_t)T * E;
+  if (rc == DDPPO_OK)
+    rc = net_forward(n, 1, E, (const char*)ro->obs + oT * ob, ro->goal + oT * 3, ro->prev_a + oT,
+                     ro->masks + oT, ro->h, ro->c, nullptr, nullptr, nullptr, n.cap_stream);
+  if (rc == DDPPO_OK)
+    rc = launch_gae(ro->rewards, ro->dones, ro->values, T, E, gamma, lam, ro->adv, ro->ret,
+                    n.cap_stream);
+  if (rc == DDPPO_OK) rc = ddppo_ppo_update(x, ro, hp, nullptr, n.cap_stream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ce = cudaStreamEndCapture(n.cap_stream, &g);
+  n.adam_t = adam_t;
+  n.timer.on = t0; n.rc_timer.on = t1; n.tc_count.on = t2;
+  n.ev_valid = false;
+  if (rc != DDPPO_OK) { if (g) cudaGraphDestroy(g); return rc; }
+  if (ce != cudaSuccess) { set_error(std::string("count capture: ") + cudaGetErrorString(ce)); return DDPPO_E_CUDA; }
+  *count = 0;
+  rc = count_kernel_nodes(g, count);
+  cudaGraphDestroy(g);
+  return rc;
+}

@@ -131,7 +131,7 @@ template <typename Ti, typename To>
 __global__ void transpose_kernel(const Ti* __restrict__ in, To* __restrict__ out, int R, int Cc,
                                  int ld_in) {
   __shared__ float tile[32][33];
-  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;  // rows on x: R can be in the millions
   for (int j = threadIdx.y; j < 32; j += blockDim.y) {
     const int r = r0 + j, c = c0 + threadIdx.x;
     tile[j][threadIdx.x] = (r < R && c < Cc) ? to_f(in[(size_t)r * ld_in + c]) : 0.f;
@@ -146,7 +146,7 @@ __global__ void transpose_kernel(const Ti* __restrict__ in, To* __restrict__ out
 int launch_transpose(const void* in, bool in_bf16, void* out, bool out_bf16, int R, int Cc,
                      int ld_in, cudaStream_t s) {
   if (R == 0 || Cc == 0) return DDPPO_OK;
-  dim3 grid((Cc + 31) / 32, (R + 31) / 32), blk(32, 8);
+  dim3 grid((R + 31) / 32, (Cc + 31) / 32), blk(32, 8);
   if (in_bf16 && out_bf16)
     transpose_kernel<__nv_bfloat16, __nv_bfloat16><<<grid, blk, 0, s>>>((const __nv_bfloat16*)in, (__nv_bfloat16*)out, R, Cc, ld_in);
   else if (in_bf16)

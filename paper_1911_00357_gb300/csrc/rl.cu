@@ -44,9 +44,8 @@ __global__ void __launch_bounds__(256) ppo_loss_kernel(int n, const float* __res
                                                        const float* __restrict__ ret, float clip,
                                                        float cv, float ce, float* dlogits,
                                                        float* dvalues, float* part) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  if (i < n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float lg[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) lg[q] = logits[(size_t)i * 4 + q];
@@ -77,21 +76,21 @@ __global__ void __launch_bounds__(256) ppo_loss_kernel(int n, const float* __res
     for (int q = 0; q < 4; ++q)
       dlogits[(size_t)i * 4 + q] = inv * (dlp * ((q == a ? 1.f : 0.f) - p[q]) + ce * p[q] * (lp[q] + H));
     dvalues[i] = inv * cv * (V - R);
-    acc[0] = -fminf(s1, s2);
-    acc[1] = 0.5f * (R - V) * (R - V);
-    acc[2] = H;
-    acc[3] = fabsf(rho - 1.f) > clip ? 1.f : 0.f;
-    acc[4] = logp_old[i] - lp[a];
+    acc[0] += -fminf(s1, s2);
+    acc[1] += 0.5f * (R - V) * (R - V);
+    acc[2] += H;
+    acc[3] += fabsf(rho - 1.f) > clip ? 1.f : 0.f;
+    acc[4] += logp_old[i] - lp[a];
   }
   block_partials<5>(acc, part);
 }
 
-__global__ void ppo_loss_final(int nb, int n, const float* __restrict__ part, float cv, float ce,
+__global__ void ppo_loss_final(int nb, int n, const float* part, float cv, float ce,
                                float* stats) {
   if (threadIdx.x != 0) return;
   float s[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   for (int b = 0; b < nb; ++b)
-    for (int k = 0; k < 5; ++k) s[k] += part[b * 5 + k];
+    for (int k = 0; k < 5; ++k) s[k] += part[b * 5 + k];  // read all partials before writing
   const float inv = 1.0f / (float)n;
   const float pol = s[0] * inv, vl = s[1] * inv, ent = s[2] * inv;
   stats[0] = pol + cv * vl - ce * ent;
@@ -100,6 +99,8 @@ __global__ void ppo_loss_final(int nb, int n, const float* __restrict__ part, fl
   stats[3] = ent;
   stats[4] = s[3] * inv;
   stats[5] = s[4] * inv;
+  stats[6] = 0.f;
+  stats[7] = 0.f;
 }
 
 int launch_ppo_loss(int n, const float* logits, const float* values, const int32_t* actions,
@@ -107,8 +108,11 @@ int launch_ppo_loss(int n, const float* logits, const float* values, const int32
                     float ce, float* stats, float* dlogits, float* dvalues, float* part,
                     size_t part_elems, cudaStream_t s) {
   if (n <= 0) return DDPPO_OK;
-  const int nb = (n + 255) / 256;
-  if ((size_t)nb * 5 > part_elems) { set_error("ppo_loss: scratch too small"); return DDPPO_E_CONFIG; }
+  // without scratch one block covers all samples and reduces into stats itself
+  int nb = part ? (n + 255) / 256 : 1;
+  if (nb > 1024) nb = 1024;
+  if (!part) part = stats;
+  else if ((size_t)nb * 5 > part_elems) { set_error("ppo_loss: scratch too small"); return DDPPO_E_CONFIG; }
   ppo_loss_kernel<<<nb, 256, 0, s>>>(n, logits, values, actions, logp_old, adv, ret, clip, cv, ce,
                                      dlogits, dvalues, part);
   DDPPO_CHECK_LAUNCH();
@@ -130,10 +134,8 @@ __global__ void __launch_bounds__(256) sumsq_partial(const float* __restrict__ x
 }
 __global__ void sum_final(int nb, const float* __restrict__ part, float* out, int mode, float scale) {
   if (threadIdx.x != 0) return;
-  double acc = 0.0;  // fixed order; the partials are fp32
   float s = 0.f;
-  for (int b = 0; b < nb; ++b) s += part[b];
-  (void)acc;
+  for (int b = 0; b < nb; ++b) s += part[b];  // fixed order
   if (mode == 0) out[0] = sqrtf(s);          // L2 norm
   else if (mode == 1) out[0] = s * scale;    // mean
   else out[0] = sqrtf(s * scale);            // population std
