@@ -258,6 +258,21 @@ int ddppo_ppo_loss(int32_t n, const float* logits, const float* values, const in
                    float value_coef, float entropy_coef, float* stats, float* dlogits,
                    float* dvalues, void* stream);
 
+/* The PPO loss of ddppo_ppo_loss (same arguments, same outputs) for callers that cannot
+ * allocate device memory where they need it, for instance inside a stream capture that
+ * forbids cudaMalloc or in a process whose device memory belongs to another allocator.
+ * The paper has no counterpart: this is a deployment variant. Samples are spread over
+ * one thread block per 256 (ddppo_ppo_loss uses one block); the per-block partial sums
+ * live in an 80 KiB array owned by the library, so nothing is allocated and no context
+ * is needed. n must be at most 1,048,576 (E_CONFIG otherwise). The first call on each
+ * device looks up the array's device address; make it before any stream capture. Every
+ * call shares the array, so calls that overlap on the GPU race. Each call overwrites the
+ * partials it uses; nothing needs clearing between calls. */
+int ddppo_ppo_loss_static(int32_t n, const float* logits, const float* values,
+                          const int32_t* actions, const float* logp_old, const float* adv,
+                          const float* ret, float clip, float value_coef, float entropy_coef,
+                          float* stats, float* dlogits, float* dvalues, void* stream);
+
 /* One PPO update on a collected rollout (ro->adv/ret already filled by ddppo_gae):
  * hp->epochs x hp->minibatches steps; minibatch k of epoch e holds the envs
  * perm[k*E/mb, (k+1)*E/mb) of a Fisher-Yates permutation drawn from the counter

@@ -99,6 +99,7 @@ _SIGS = {
     "ddppo_policy_backward": [P, P, P, P, P],
     "ddppo_gae": [P, P, P, I32, I32, F32, F32, P, P, P],
     "ddppo_ppo_loss": [I32, P, P, P, P, P, P, F32, F32, F32, P, P, P, P],
+    "ddppo_ppo_loss_static": [I32, P, P, P, P, P, P, F32, F32, F32, P, P, P, P],
     "ddppo_ppo_update": [P, P, P, P, P],
     "ddppo_collect": [P, P, I32, P],
     "ddppo_timing_enable": [P, I32],
@@ -241,6 +242,13 @@ def ddppo_ppo_loss(n, logits, values, actions, logp_old, adv, ret, clip, value_c
     _check(lib().ddppo_ppo_loss(n, _p(logits), _p(values), _p(actions), _p(logp_old), _p(adv),
                                 _p(ret), clip, value_coef, entropy_coef, _p(stats), _p(dlogits),
                                 _p(dvalues), _s()))
+
+
+def ddppo_ppo_loss_static(n, logits, values, actions, logp_old, adv, ret, clip, value_coef,
+                          entropy_coef, stats, dlogits, dvalues):
+    _check(lib().ddppo_ppo_loss_static(n, _p(logits), _p(values), _p(actions), _p(logp_old),
+                                       _p(adv), _p(ret), clip, value_coef, entropy_coef,
+                                       _p(stats), _p(dlogits), _p(dvalues), _s()))
 
 
 def ddppo_ppo_update(h, ro: Rollout, hp: PPOHParams, stats=None):

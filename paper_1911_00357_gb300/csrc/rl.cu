@@ -121,6 +121,19 @@ int launch_ppo_loss(int n, const float* logits, const float* values, const int32
   return DDPPO_OK;
 }
 
+int launch_ppo_loss_blocks(int n, const float* logits, const float* values, const int32_t* actions,
+                           const float* logp_old, const float* adv, const float* ret, float clip,
+                           float cv, float ce, float* stats, float* dlogits, float* dvalues,
+                           float* part, int nb, cudaStream_t s) {
+  if (n <= 0) return DDPPO_OK;
+  ppo_loss_kernel<<<nb, 256, 0, s>>>(n, logits, values, actions, logp_old, adv, ret, clip, cv, ce,
+                                     dlogits, dvalues, part);
+  DDPPO_CHECK_LAUNCH();
+  ppo_loss_final<<<1, 32, 0, s>>>(nb, n, part, cv, ce, stats);
+  DDPPO_CHECK_LAUNCH();
+  return DDPPO_OK;
+}
+
 // ---- sum of squares / sums, two-stage ----
 __global__ void __launch_bounds__(256) sumsq_partial(const float* __restrict__ x, size_t n,
                                                      float* part, int square, const float* shift) {

@@ -8,6 +8,11 @@ int launch_ppo_loss(int n, const float* logits, const float* values, const int32
                     const float* logp_old, const float* adv, const float* ret, float clip, float cv,
                     float ce, float* stats, float* dlogits, float* dvalues, float* part,
                     size_t part_elems, cudaStream_t s);
+// exactly nb blocks of 256 threads, partials part[nb * 5]
+int launch_ppo_loss_blocks(int n, const float* logits, const float* values, const int32_t* actions,
+                           const float* logp_old, const float* adv, const float* ret, float clip,
+                           float cv, float ce, float* stats, float* dlogits, float* dvalues,
+                           float* part, int nb, cudaStream_t s);
 int launch_grad_norm(const float* g, size_t n, float* norm_out, float* part, size_t part_elems,
                      cudaStream_t s);
 int launch_adam(float* p, const float* g, float* m, float* v, size_t n, const float* norm,
