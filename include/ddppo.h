@@ -292,6 +292,23 @@ int ddppo_ppo_update(ddppo_ctx* ctx, const ddppo_rollout* ro, const ddppo_ppo_hp
  * capturable). */
 int ddppo_collect(ddppo_ctx* ctx, const ddppo_rollout* ro, int32_t use_graph, void* stream);
 
+/* ---- contraction utility --------------------------------------------------------- */
+
+/* The GEMM every layer of the network runs on:
+ *   C[M, N] = beta * C + A[M, K] * B[N, K]^T (+ bias[N]) (then ReLU if relu)
+ * A, B [dev] row-major with K contiguous (leading dimensions lda, ldb >= K), of float
+ * (op_bf16 = 0, SIMT FMA) or bf16 (op_bf16 = 1; on sm_103a the tcgen05 tensor-core path
+ * with fp32 accumulation when the rows are 16-byte aligned). C [dev] row-major fp32, or
+ * bf16 when c_bf16 (then beta must be 0). bias [dev] [N] or NULL. status [dev] int32 or
+ * NULL receives the sticky timeout flag (2) of a bounded tensor-core wait. The first call
+ * per device allocates a split-K workspace (not capturable). */
+int ddppo_gemm(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const void* A, int32_t lda,
+               const void* B, int32_t ldb, void* C, int32_t ldc, int32_t c_bf16, float beta,
+               const float* bias, int32_t relu, int32_t* status, void* stream);
+/* Whether ddppo_gemm with these operands runs on the tensor cores (1) or SIMT (0). */
+int ddppo_gemm_backend(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const void* A,
+                       int32_t lda, const void* B, int32_t ldb, int32_t* tensor_cores);
+
 /* Per-kernel-family timing of the calls enqueued while enabled (CUDA events on
  * the launching stream). ddppo_timing_enable(ctx, 1) starts recording and
  * clears the counters; ddppo_timing_read synchronises and returns, for family

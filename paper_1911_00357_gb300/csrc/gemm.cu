@@ -118,12 +118,18 @@ static int gemm_simt(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, c
                                                  (const float*)d.B, d.ldb, (float*)d.C, d.ldc,
                                                  d.c_bf16, d.beta, d.bias, d.relu, kchunk, partial);
   DDPPO_CHECK_LAUNCH();
-  if (partial) {
-    const size_t n = (size_t)d.M * d.N;
-    splitk_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
-        d.M, d.N, splits, partial, (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu);
-    DDPPO_CHECK_LAUNCH();
-  }
+  if (partial)
+    DDPPO_TRY(launch_splitk_reduce(d.M, d.N, splits, partial, (float*)d.C, d.ldc, d.c_bf16, d.beta,
+                                   d.bias, d.relu, s));
+  return DDPPO_OK;
+}
+
+int launch_splitk_reduce(int M, int N, int splits, const float* partial, float* C, int ldc,
+                         int c_bf16, float beta, const float* bias, int relu, cudaStream_t s) {
+  const size_t n = (size_t)M * N;
+  splitk_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(M, N, splits, partial, C, ldc,
+                                                                   c_bf16, beta, bias, relu);
+  DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
 

@@ -33,6 +33,7 @@ struct GemmWorkspace {
   size_t partial_elems = 0;
   int num_sms = 152;
   GemmTcCount* tc = nullptr;  // counts contractions routed to tcgen05 while enabled
+  int32_t* err = nullptr;      // sticky device status word (timeout flag)
 };
 
 // timing of GEMM launches (family 0 of ddppo_timing_read)
@@ -46,6 +47,10 @@ struct KernelTimer {
 
 int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t s,
          KernelTimer* timer = nullptr);
+
+// C = beta*C + sum of `splits` partial [M, N] slices (+ bias) (ReLU), fixed order
+int launch_splitk_reduce(int M, int N, int splits, const float* partial, float* C, int ldc,
+                         int c_bf16, float beta, const float* bias, int relu, cudaStream_t s);
 
 // tcgen05 path (gemm_tc.cu); returns DDPPO_E_CONFIG when the shape is not supported
 int gemm_tc(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s);

@@ -1,10 +1,332 @@
-// tcgen05 BF16 GEMM (placeholder: shapes route to the SIMT kernel until it lands).
+// BF16 GEMM on the 5th-generation tensor cores (sm_103a): C[M,N] (+)= A[M,K] B[N,K]^T.
+//
+//   * TMA (cp.async.bulk.tensor.2d) stages 128x64 A tiles and BNx64 B tiles into shared
+//     memory in the 128-byte swizzled K-major layout; out-of-range rows/columns are
+//     zero-filled by the copy engine, so ragged M, N and K need no special path.
+//   * A 4-stage ring of mbarriers: "full" (TMA -> MMA, transaction bytes) and "empty"
+//     (MMA -> TMA, signalled by tcgen05.commit when the MMAs reading a stage retire).
+//   * One thread issues tcgen05.mma.cta_group::1.kind::f16 (M=128, N=BN, K=16 per
+//     instruction) accumulating in fp32 in tensor memory (BN columns of TMEM).
+//   * Epilogue: 4 warps each read their 32 TMEM lanes (rows) with tcgen05.ld.32x32b and
+//     apply beta/bias/ReLU, storing fp32 or bf16 -- or fp32 split-K partials that a
+//     fixed-order reduction combines.
+//   * Small-M problems (the per-step LSTM recurrences) are computed transposed (swap AB)
+//     so the 128-row MMA dimension covers the large side.
+// Every wait is bounded; a wait that runs out sets the sticky timeout flag and the CTA
+// drains and frees its tensor memory instead of hanging.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "gemm.cuh"
 
 namespace ddppo {
-bool gemm_tc_supported(const GemmDesc&) { return false; }
-int gemm_tc(const GemmDesc&, const GemmWorkspace&, cudaStream_t) {
-  set_error("tcgen05 GEMM not built");
-  return DDPPO_E_CONFIG;
+
+constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4, TC_THREADS = 128;
+constexpr uint32_t TC_SPIN_LIMIT = 1u << 22;
+
+struct TcSmem {
+  // stage buffers are carved from dynamic shared memory (1024-byte aligned)
+  uint64_t full[TC_STAGES];
+  uint64_t empty[TC_STAGES];
+  uint64_t done;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
 }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred P1;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, P1;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; on expiry marks the CTA aborted and raises the timeout flag
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                          int32_t* err) {
+  for (uint32_t i = 0; i < TC_SPIN_LIMIT; ++i) {
+    if (mbar_try(bar, parity)) return true;
+    if (*abort) return false;
+    // another CTA already timed out: give up at once instead of waiting out the limit
+    if ((i & 1023u) == 1023u && err && (*(volatile int32_t*)err & 2)) {
+      *abort = 1;
+      return false;
+    }
+  }
+  *abort = 1;
+  if (err) atomicOr(err, 2);
+  return false;
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4}], [%2];" ::"r"(smem_addr(dst)),
+      "l"((uint64_t)map), "r"(smem_addr(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;              // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset
+  d |= (uint64_t)1 << 46;              // descriptor version (tcgen05)
+  d |= (uint64_t)2 << 61;              // SWIZZLE_128B
+  return d;
+}
+
+// instruction descriptor, kind::f16: D f32, A/B bf16, both K-major
+__host__ __device__ constexpr uint32_t f16_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+                   int M, int N, int K, int kchunk, float* __restrict__ C, int ldc, int c_bf16,
+                   float beta, const float* __restrict__ bias, int relu, int trans_out,
+                   float* __restrict__ partial, int32_t* err) {
+  extern __shared__ __align__(1024) uint8_t dyn[];
+  __shared__ TcSmem ctl;
+  constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2;
+  uint8_t* base = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
+  uint8_t* sA = base;
+  uint8_t* sB = base + TC_STAGES * A_BYTES;
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
+  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+  const int nkb = (kend - kbeg + TC_BK - 1) / TC_BK;
+  volatile int* abort = &ctl.abort;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < TC_STAGES; ++s) {
+      mbar_init(&ctl.full[s], 1);
+      mbar_init(&ctl.empty[s], 1);
+    }
+    mbar_init(&ctl.done, 1);
+    ctl.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&ctl.tmem_base)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = ctl.tmem_base;
+
+  if (warp == 0 && lane == 0) {
+    // TMA producer
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % TC_STAGES;
+      const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+      if (!mbar_wait(&ctl.empty[s], ph ^ 1u, abort, err)) break;
+      mbar_expect_tx(&ctl.full[s], A_BYTES + B_BYTES);
+      const int k = kbeg + kb * TC_BK;
+      tma_load_2d(sA + s * A_BYTES, &mapA, &ctl.full[s], k, m0);
+      tma_load_2d(sB + s * B_BYTES, &mapB, &ctl.full[s], k, n0);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // MMA issuer
+    constexpr uint32_t idesc = f16_idesc(TC_BM, BN);
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % TC_STAGES;
+      const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+      if (!mbar_wait(&ctl.full[s], ph, abort, err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_addr(sA + s * A_BYTES), b0 = smem_addr(sB + s * B_BYTES);
+#pragma unroll
+      for (int k = 0; k < TC_BK / 16; ++k) {
+        const uint64_t da = sw128_desc(a0 + k * 32), db = sw128_desc(b0 + k * 32);
+        const uint32_t acc = (kb | k) ? 1u : 0u;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+            "l"(da), "l"(db), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_addr(&ctl.empty[s]))
+          : "memory");
+    }
+    // completion of every MMA issued so far
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_addr(&ctl.done))
+        : "memory");
+  }
+  __syncwarp();
+
+  // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31
+  const bool ok = mbar_wait(&ctl.done, 0, abort, err) && nkb > 0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+  for (int c0 = 0; c0 < BN; c0 += 32) {
+    uint32_t r[32];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    if (!ok || row >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      const int col = n0 + c0 + j;
+      if (col >= N) break;
+      float v = __uint_as_float(r[j]);
+      // (m, n) of the problem as the caller sees it
+      const int pm = trans_out ? col : row, pn = trans_out ? row : col;
+      if (partial) {
+        partial[((size_t)blockIdx.z * (trans_out ? N : M) + pm) * (trans_out ? M : N) + pn] = v;
+        continue;
+      }
+      const size_t o = (size_t)pm * ldc + pn;
+      if (beta != 0.f) v += beta * C[o];
+      if (bias) v += bias[pn];
+      if (relu) v = fmaxf(v, 0.f);
+      if (c_bf16) ((__nv_bfloat16*)C)[o] = __float2bfloat16_rn(v);
+      else C[o] = v;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+  }
+}
+
+// ---------------------------------------------------------------- host side
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  });
+  return fn;
+}
+
+// 2-D bf16 tensor [rows, cols] with row stride ld elements, box [box_rows, 64]
+static bool make_map(CUtensorMap* m, const void* ptr, int rows, int cols, int ld, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int BN>
+static size_t tc_smem() {
+  return (size_t)TC_STAGES * (TC_BM + BN) * TC_BK * 2 + 1024;
+}
+
+bool gemm_tc_supported(const GemmDesc& d) {
+  if (!encode_fn()) return false;
+  if (d.K < 16 || d.M < 1 || d.N < 1) return false;
+  if ((d.lda % 8) || (d.ldb % 8)) return false;  // 16-byte row strides for TMA
+  if (((uintptr_t)d.A & 15) || ((uintptr_t)d.B & 15)) return false;
+  if ((int64_t)d.M > (1ll << 31) - 1 || (int64_t)d.N > (1ll << 31) - 1) return false;
+  return true;
+}
+
+template <int BN>
+static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int K,
+                     const GemmDesc& d, int trans, const GemmWorkspace& ws, cudaStream_t s) {
+  static bool attr_done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !attr_done[dev]) {
+    DDPPO_CHECK_CUDA(cudaFuncSetAttribute(gemm_tc_kernel<BN>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)tc_smem<BN>()));
+    attr_done[dev] = true;
+  }
+  const int gm = (M + TC_BM - 1) / TC_BM, gn = (N + BN - 1) / BN;
+  const int tiles = gm * gn;
+  int splits = 1;
+  const int target = ws.num_sms;
+  if (tiles < target && K >= 8 * TC_BK) {
+    splits = min((target + tiles - 1) / tiles, K / (4 * TC_BK));
+    const size_t per = (size_t)M * N;
+    splits = (int)min((size_t)splits, ws.partial_elems / max(per, (size_t)1));
+    if (splits < 2) splits = 1;
+  }
+  int kchunk = (K + splits - 1) / splits;
+  kchunk = (kchunk + TC_BK - 1) / TC_BK * TC_BK;
+  splits = (K + kchunk - 1) / kchunk;
+  float* partial = splits > 1 ? ws.partial : nullptr;
+  dim3 grid(gm, gn, splits);
+  gemm_tc_kernel<BN><<<grid, TC_THREADS, tc_smem<BN>(), s>>>(
+      ma, mb, M, N, K, kchunk, (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu, trans,
+      partial, ws.err);
+  DDPPO_CHECK_LAUNCH();
+  if (partial)
+    DDPPO_TRY(launch_splitk_reduce(d.M, d.N, splits, partial, (float*)d.C, d.ldc, d.c_bf16, d.beta,
+                                   d.bias, d.relu, s));
+  return DDPPO_OK;
+}
+
+int gemm_tc(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s) {
+  // swap A and B when M is small: the MMA's 128-row side then covers N
+  const bool swap = d.M < TC_BM && d.N > d.M;
+  const void* A = swap ? d.B : d.A;
+  const void* Bm = swap ? d.A : d.B;
+  const int lda = swap ? d.ldb : d.lda, ldb = swap ? d.lda : d.ldb;
+  const int M = swap ? d.N : d.M, N = swap ? d.M : d.N;
+  const int BN = N > 64 ? 128 : 64;
+  CUtensorMap ma, mb;
+  if (!make_map(&ma, A, M, d.K, lda, TC_BM) || !make_map(&mb, Bm, N, d.K, ldb, BN)) {
+    set_error("gemm_tc: tensor map encoding failed");
+    return DDPPO_E_CUDA;
+  }
+  if (BN == 128) return launch_tc<128>(ma, mb, M, N, d.K, d, swap ? 1 : 0, ws, s);
+  return launch_tc<64>(ma, mb, M, N, d.K, d, swap ? 1 : 0, ws, s);
+}
+
 }  // namespace ddppo

@@ -288,6 +288,7 @@ int net_create(ddppo_ctx* x) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&n.gws.num_sms, cudaDevAttrMultiProcessorCount, dev);
   n.gws.tc = &n.tc_count;
+  n.gws.err = x->sb.err;
   DDPPO_TRY(nalloc(n, &n.params, n.P));
   DDPPO_TRY(nalloc(n, &n.grad, n.P));
   DDPPO_TRY(nalloc(n, &n.adam_m, n.P));

@@ -394,3 +394,39 @@ extern "C" int ddppo_count_kernels(ddppo_ctx* x, const ddppo_rollout* ro,
   cudaGraphDestroy(g);
   return rc;
 }
+
+// ---- stand-alone GEMM (the contraction every network layer uses) ----
+extern "C" int ddppo_gemm(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const void* A,
+                          int32_t lda, const void* B, int32_t ldb, void* C, int32_t ldc,
+                          int32_t c_bf16, float beta, const float* bias, int32_t relu,
+                          int32_t* status, void* stream) {
+  ARG(M >= 0 && N >= 0 && K >= 1, "gemm: bad sizes");
+  if (M == 0 || N == 0) return DDPPO_OK;
+  ARG(A && B && C, "gemm: null argument");
+  ARG(lda >= K && ldb >= K && ldc >= N, "gemm: leading dimension smaller than the row");
+  static float* partial[64] = {};
+  int dev = 0;
+  DDPPO_CHECK_CUDA(cudaGetDevice(&dev));
+  ARG(dev < 64, "gemm: device ordinal out of range");
+  const size_t elems = (size_t)16 << 20;
+  if (!partial[dev]) DDPPO_CHECK_CUDA(cudaMalloc(&partial[dev], elems * sizeof(float)));
+  GemmWorkspace ws;
+  ws.partial = partial[dev];
+  ws.partial_elems = elems;
+  cudaDeviceGetAttribute(&ws.num_sms, cudaDevAttrMultiProcessorCount, dev);
+  ws.err = status;
+  GemmDesc d;
+  d.M = M; d.N = N; d.K = K; d.A = A; d.lda = lda; d.B = B; d.ldb = ldb; d.C = C; d.ldc = ldc;
+  d.c_bf16 = c_bf16; d.beta = beta; d.bias = bias; d.relu = relu;
+  return gemm(d, op_bf16 != 0, ws, (cudaStream_t)stream, nullptr);
+}
+
+extern "C" int ddppo_gemm_backend(int32_t M, int32_t N, int32_t K, int32_t op_bf16,
+                                  const void* A, int32_t lda, const void* B, int32_t ldb,
+                                  int32_t* tensor_cores) {
+  ARG(tensor_cores, "gemm_backend: null argument");
+  GemmDesc d;
+  d.M = M; d.N = N; d.K = K; d.A = A; d.lda = lda; d.B = B; d.ldb = ldb;
+  *tensor_cores = (op_bf16 && gemm_tc_supported(d)) ? 1 : 0;
+  return DDPPO_OK;
+}
