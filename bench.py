@@ -114,7 +114,8 @@ def run_gpu(args):
     precision = 1 if args.precision == "bf16" else 0
 
     def measure(prec, steps, warmup, timing):
-        w = Worker("resnet", precision=prec, seed=1000 * rank + 17)
+        kw = {"rollout_T": args.rollout_T} if args.rollout_T else {}
+        w = Worker("resnet", precision=prec, seed=1000 * rank + 17, **kw)
         for _ in range(warmup):
             w.iterate()
         torch.cuda.synchronize()
@@ -140,14 +141,19 @@ def run_gpu(args):
         if world > 1:
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
         gemm = B.ddppo_timing_read(w.h, 0) if timing else None
-        rc = B.ddppo_timing_read(w.h, 1) if timing else None
+        tc = B.ddppo_timing_read(w.h, 2) if timing else None
         if timing:
             B.ddppo_timing_enable(w.h, False)
-        return w, t.item(), clocks, gemm, rc
+        return w, t.item(), clocks, gemm, tc
 
-    w, ms, clocks, gemm, rc = measure(precision, args.steps, args.warmup, True)
+    w, ms, clocks, gemm, tc = measure(precision, args.steps, args.warmup, True)
     frames = w.E * w.T * args.steps * world
     value = frames / (ms / 1e3)
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "ms_per_step": ms / args.steps}), flush=True)
+        return
+    rc = w.time_raycast(16)
 
     # end to end through the public API: uniforms H2D from pinned memory each step,
     # statistics and rewards D2H each step
@@ -167,7 +173,8 @@ def run_gpu(args):
     peaks, pk_kind = _peaks()
     g_ms, g_n, g_flops = gemm
     achieved = g_flops / (g_ms / 1e3) / 1e12 if g_ms > 0 else 0.0
-    if precision == 1 and w.tensor_core_gemm():
+    tc_flops_share = (tc[2] / gemm[2]) if gemm[2] > 0 else 0.0
+    if precision == 1 and tc[1] > 0:
         bound, peak_v, unit = "tensor", peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]), "TFLOP/s"
     else:
         # SIMT FMA path: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock
@@ -192,8 +199,9 @@ def run_gpu(args):
                      "achieved": round(achieved, 3), "peak": round(peak_v, 1), "unit": unit,
                      "frac": round(achieved / peak_v, 4) if peak_v else None,
                      "peak_kind": pk_kind, "launches": g_n, "avg_launch_us": round(1e3 * g_ms / max(g_n, 1), 2),
-                     "traffic": None},
+                     "tcgen05_flop_share": round(tc_flops_share, 4), "traffic": None},
         "raycast": {"launches": r_n, "avg_launch_us": round(1e3 * r_ms / max(r_n, 1), 2),
+                "kernel": "env_step render (TMA-staged DDA ray cast, 64 x 256x256 -> 128x128 bf16)",
                     "out_GBps": round(r_bytes / (r_ms / 1e3) / 1e9, 2) if r_ms > 0 else None},
         "clocks": clocks,
     }
@@ -260,8 +268,12 @@ def main():
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-steps", type=int, default=1)
+    ap.add_argument("--rollout-T", type=int, default=None,
+                    help="shorter rollout for profiler launch lists (not a bench value)")
+    ap.add_argument("--profile", action="store_true",
+                    help="timed steps only (for ncu); prints no bench line")
     args = ap.parse_args()
-    if args.warmup < 3 and args.impl == "native":
+    if args.warmup < 3 and args.impl == "native" and not args.profile:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)

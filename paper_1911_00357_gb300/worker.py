@@ -96,6 +96,23 @@ class Worker:
         d2h = self.stats.numel() * 4 + T * E * 4 + T * E
         return e0.elapsed_time(e1), h2d, d2h
 
+    def time_raycast(self, steps: int):
+        """Ray-cast launches of `steps` env steps run outside the collect graph, with the
+        library's event timer on the render kernel: (ms, launches, output bytes)."""
+        t = self.t
+        E = self.E
+        act = torch.randint(1, 4, (steps, E), dtype=torch.int32, device="cuda")
+        obs = torch.empty_like(t["obs"][0])
+        goal = torch.empty_like(t["goal"][0])
+        r = torch.empty(E, device="cuda")
+        d = torch.empty(E, dtype=torch.uint8, device="cuda")
+        B.ddppo_timing_enable(self.h, True)
+        for i in range(steps):
+            B.ddppo_env_step(self.h, act[i], obs, goal, r, d)
+        out = B.ddppo_timing_read(self.h, 1)
+        B.ddppo_timing_enable(self.h, False)
+        return out
+
     def launches_per_step(self) -> int:
         return B.ddppo_count_kernels(self.h, self.view, self.hp, self.gamma, self.lam)
 
