@@ -295,16 +295,19 @@ int ddppo_collect(ddppo_ctx* ctx, const ddppo_rollout* ro, int32_t use_graph, vo
 /* ---- contraction utility --------------------------------------------------------- */
 
 /* The GEMM every layer of the network runs on:
- *   C[M, N] = beta * C + A[M, K] * B[N, K]^T (+ bias[N]) (then ReLU if relu)
- * A, B [dev] row-major with K contiguous (leading dimensions lda, ldb >= K), of float
- * (op_bf16 = 0, SIMT FMA) or bf16 (op_bf16 = 1; on sm_103a the tcgen05 tensor-core path
- * with fp32 accumulation when the rows are 16-byte aligned). C [dev] row-major fp32, or
- * bf16 when c_bf16 (then beta must be 0). bias [dev] [N] or NULL. status [dev] int32 or
- * NULL receives the sticky timeout flag (2) of a bounded tensor-core wait. The first call
- * per device allocates a split-K workspace (not capturable). */
+ *   C[M, N] = beta * C + sum_k A(m, k) B(n, k) (+ bias[N]) (then ReLU if relu)
+ * A [dev] is [M, K] row-major (A(m,k) = A[m*lda + k], lda >= K) or, with a_t, stored
+ * [K, M] (A(m,k) = A[k*lda + m], lda >= M); B likewise with b_t ([N, K] or [K, N]).
+ * Operands are float (op_bf16 = 0, SIMT FMA) or bf16 (op_bf16 = 1; on sm_103a the
+ * tcgen05 tensor-core path with fp32 accumulation when rows are 16-byte aligned). C [dev]
+ * row-major fp32, or bf16 when c_bf16 (then beta must be 0). bias [dev] [N] or NULL.
+ * status [dev] int32 or NULL receives the sticky timeout flag (2) of a bounded
+ * tensor-core wait. The first call per device allocates a split-K workspace (not
+ * capturable). */
 int ddppo_gemm(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const void* A, int32_t lda,
-               const void* B, int32_t ldb, void* C, int32_t ldc, int32_t c_bf16, float beta,
-               const float* bias, int32_t relu, int32_t* status, void* stream);
+               int32_t a_t, const void* B, int32_t ldb, int32_t b_t, void* C, int32_t ldc,
+               int32_t c_bf16, float beta, const float* bias, int32_t relu, int32_t* status,
+               void* stream);
 /* Whether ddppo_gemm with these operands runs on the tensor cores (1) or SIMT (0). */
 int ddppo_gemm_backend(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const void* A,
                        int32_t lda, const void* B, int32_t ldb, int32_t* tensor_cores);

@@ -105,7 +105,7 @@ _SIGS = {
     "ddppo_timing_enable": [P, I32],
     "ddppo_timing_read": [P, I32, P, P, P],
     "ddppo_count_kernels": [P, P, P, F32, F32, P],
-    "ddppo_gemm": [I32, I32, I32, I32, P, I32, P, I32, P, I32, I32, F32, P, I32, P, P],
+    "ddppo_gemm": [I32, I32, I32, I32, P, I32, I32, P, I32, I32, P, I32, I32, F32, P, I32, P, P],
     "ddppo_gemm_backend": [I32, I32, I32, I32, P, I32, P, I32, P],
 }
 
@@ -281,17 +281,19 @@ def ddppo_count_kernels(h, ro: Rollout, hp: PPOHParams, gamma: float, lam: float
 
 
 def ddppo_gemm(A, B, C, beta=0.0, bias=None, relu=False, status=None, M=None, N=None, K=None,
-               lda=None, ldb=None, ldc=None):
-    """C = beta*C + A @ B^T (+ bias) (ReLU) on the library's GEMM (bf16 operands -> tcgen05)."""
-    M = A.shape[0] if M is None else M
-    N = B.shape[0] if N is None else N
-    K = A.shape[1] if K is None else K
+               lda=None, ldb=None, ldc=None, a_t=False, b_t=False):
+    """C = beta*C + A @ B^T (+ bias) (ReLU) on the library's GEMM (bf16 operands -> tcgen05).
+    With a_t the tensor A holds A^T ([K, M]); with b_t B holds B^T ([K, N])."""
+    M = (A.shape[1] if a_t else A.shape[0]) if M is None else M
+    N = (B.shape[1] if b_t else B.shape[0]) if N is None else N
+    K = (A.shape[0] if a_t else A.shape[1]) if K is None else K
     lda = A.stride(0) if lda is None else lda
     ldb = B.stride(0) if ldb is None else ldb
     ldc = C.stride(0) if ldc is None else ldc
     op_bf16 = 1 if A.dtype == torch.bfloat16 else 0
-    _check(lib().ddppo_gemm(M, N, K, op_bf16, ctypes.c_void_p(A.data_ptr()), lda,
-                            ctypes.c_void_p(B.data_ptr()), ldb, ctypes.c_void_p(C.data_ptr()), ldc,
+    _check(lib().ddppo_gemm(M, N, K, op_bf16, ctypes.c_void_p(A.data_ptr()), lda, 1 if a_t else 0,
+                            ctypes.c_void_p(B.data_ptr()), ldb, 1 if b_t else 0,
+                            ctypes.c_void_p(C.data_ptr()), ldc,
                             1 if C.dtype == torch.bfloat16 else 0, beta, _p(bias),
                             1 if relu else 0, _p(status), _s()))
 

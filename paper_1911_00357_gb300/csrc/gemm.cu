@@ -22,7 +22,8 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(int M, int N, int K, con
                                                         float* __restrict__ C, int ldc, int c_bf16,
                                                         float beta, const float* __restrict__ bias,
                                                         int relu, int kchunk,
-                                                        float* __restrict__ partial) {
+                                                        float* __restrict__ partial, int a_t,
+                                                        int b_t) {
   __shared__ float As[SB_K][SB_M + 4];
   __shared__ float Bs[SB_K][SB_N + 4];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -35,8 +36,10 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(int M, int N, int K, con
     for (int q = 0; q < 4; ++q) {
       const int k = k0 + lk + q;
       const int m = m0 + lr, n = n0 + lr;
-      As[lk + q][lr] = (m < M && k < kend) ? ld_op(A + (size_t)m * lda + k) : 0.f;
-      Bs[lk + q][lr] = (n < N && k < kend) ? ld_op(B + (size_t)n * ldb + k) : 0.f;
+      As[lk + q][lr] = (m < M && k < kend)
+                           ? ld_op(A + (a_t ? (size_t)k * lda + m : (size_t)m * lda + k)) : 0.f;
+      Bs[lk + q][lr] = (n < N && k < kend)
+                           ? ld_op(B + (b_t ? (size_t)k * ldb + n : (size_t)n * ldb + k)) : 0.f;
     }
     __syncthreads();
 #pragma unroll
@@ -112,11 +115,12 @@ static int gemm_simt(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, c
   if (op_bf16)
     gemm_simt_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(
         d.M, d.N, d.K, (const __nv_bfloat16*)d.A, d.lda, (const __nv_bfloat16*)d.B, d.ldb,
-        (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu, kchunk, partial);
+        (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu, kchunk, partial, d.a_t, d.b_t);
   else
     gemm_simt_kernel<float><<<grid, 256, 0, s>>>(d.M, d.N, d.K, (const float*)d.A, d.lda,
                                                  (const float*)d.B, d.ldb, (float*)d.C, d.ldc,
-                                                 d.c_bf16, d.beta, d.bias, d.relu, kchunk, partial);
+                                                 d.c_bf16, d.beta, d.bias, d.relu, kchunk, partial,
+                                                 d.a_t, d.b_t);
   DDPPO_CHECK_LAUNCH();
   if (partial)
     DDPPO_TRY(launch_splitk_reduce(d.M, d.N, splits, partial, (float*)d.C, d.ldc, d.c_bf16, d.beta,

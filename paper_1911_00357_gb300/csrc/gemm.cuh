@@ -1,7 +1,9 @@
 // GEMM interface used by every contraction of the agent network.
-//   C[M, N] = beta * C + A[M, K] * B[N, K]^T (+ bias[N]) (ReLU)
-// A and B are K-contiguous ("TN"), of the operand dtype (fp32 or bf16); C is fp32, or bf16
-// when c_bf16 (then beta must be 0). Accumulation is fp32.
+//   C[M, N] = beta * C + sum_k A(m, k) B(n, k) (+ bias[N]) (ReLU)
+// A(m, k) = A[m * lda + k] (K-contiguous), or A[k * lda + m] when a_t ("MN-major": the
+// weight gradients read activations and output gradients as they are stored, [rows][C]).
+// B likewise with b_t. Operands are of the operand dtype (fp32 or bf16); C is fp32, or
+// bf16 when c_bf16 (then beta must be 0). Accumulation is fp32.
 #pragma once
 
 #include "common.cuh"
@@ -20,6 +22,8 @@ struct GemmDesc {
   float beta = 0.f;
   const float* bias = nullptr;
   int relu = 0;
+  int a_t = 0;  // A stored [K][M]
+  int b_t = 0;  // B stored [K][N]
 };
 
 struct GemmTcCount {

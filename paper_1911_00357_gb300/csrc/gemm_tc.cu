@@ -87,7 +87,9 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart
+// shared-memory matrix descriptors, 128-byte swizzle.
+// K-major tile: rows of 64 K-elements (128 B), 8-row groups 1024 B apart (SBO); the K
+// offset of an MMA within the swizzle atom is added to the start address.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr >> 4) & 0x3FFF);
@@ -97,11 +99,22 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
   d |= (uint64_t)2 << 61;              // SWIZZLE_128B
   return d;
 }
+// MN-major tile: rows of 64 MN-elements (128 B), one row per K index; blocks of 64 MN
+// columns are 64 rows (8 KiB) apart (LBO); 8-row K groups 1024 B apart (SBO).
+__device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)(8192 >> 4) << 16;    // leading byte offset: next 64-wide MN block
+  d |= (uint64_t)(1024 >> 4) << 32;    // stride byte offset: next 8-row K group
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
 
-// instruction descriptor, kind::f16: D f32, A/B bf16, both K-major
-__host__ __device__ constexpr uint32_t f16_idesc(int M, int N) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
-         ((uint32_t)(M >> 4) << 24);
+// instruction descriptor, kind::f16: D f32, A/B bf16; a_mn / b_mn select MN-major operands
+__host__ __device__ constexpr uint32_t f16_idesc(int M, int N, int a_mn = 0, int b_mn = 0) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(a_mn & 1) << 15) |
+         ((uint32_t)(b_mn & 1) << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
 template <int BN>
@@ -109,7 +122,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    int M, int N, int K, int kchunk, float* __restrict__ C, int ldc, int c_bf16,
                    float beta, const float* __restrict__ bias, int relu, int trans_out,
-                   float* __restrict__ partial, int32_t* err) {
+                   float* __restrict__ partial, int32_t* err, int a_mn, int b_mn) {
   extern __shared__ __align__(1024) uint8_t dyn[];
   __shared__ TcSmem ctl;
   constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2;
@@ -151,12 +164,23 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       if (!mbar_wait(&ctl.empty[s], ph ^ 1u, abort, err)) break;
       mbar_expect_tx(&ctl.full[s], A_BYTES + B_BYTES);
       const int k = kbeg + kb * TC_BK;
-      tma_load_2d(sA + s * A_BYTES, &mapA, &ctl.full[s], k, m0);
-      tma_load_2d(sB + s * B_BYTES, &mapB, &ctl.full[s], k, n0);
+      if (a_mn) {
+        tma_load_2d(sA + s * A_BYTES, &mapA, &ctl.full[s], m0, k);
+        tma_load_2d(sA + s * A_BYTES + 8192, &mapA, &ctl.full[s], m0 + 64, k);
+      } else {
+        tma_load_2d(sA + s * A_BYTES, &mapA, &ctl.full[s], k, m0);
+      }
+      if (b_mn) {
+#pragma unroll
+        for (int j = 0; j < BN / 64; ++j)
+          tma_load_2d(sB + s * B_BYTES + j * 8192, &mapB, &ctl.full[s], n0 + 64 * j, k);
+      } else {
+        tma_load_2d(sB + s * B_BYTES, &mapB, &ctl.full[s], k, n0);
+      }
     }
   } else if (warp == 1 && lane == 0) {
     // MMA issuer
-    constexpr uint32_t idesc = f16_idesc(TC_BM, BN);
+    const uint32_t idesc = f16_idesc(TC_BM, BN, a_mn, b_mn);
     for (int kb = 0; kb < nkb; ++kb) {
       const int s = kb % TC_STAGES;
       const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
@@ -165,7 +189,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       const uint32_t a0 = smem_addr(sA + s * A_BYTES), b0 = smem_addr(sB + s * B_BYTES);
 #pragma unroll
       for (int k = 0; k < TC_BK / 16; ++k) {
-        const uint64_t da = sw128_desc(a0 + k * 32), db = sw128_desc(b0 + k * 32);
+        // K-major: +32 B per 16-element K step inside the swizzle row; MN-major: +2 K groups
+        const uint64_t da = a_mn ? sw128_mn_desc(a0 + k * 2048) : sw128_desc(a0 + k * 32);
+        const uint64_t db = b_mn ? sw128_mn_desc(b0 + k * 2048) : sw128_desc(b0 + k * 32);
         const uint32_t acc = (kb | k) ? 1u : 0u;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -248,13 +274,13 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// 2-D bf16 tensor [rows, cols] with row stride ld elements, box [box_rows, 64]
+// 2-D bf16 tensor [rows, cols] with row stride ld elements, box [box_rows, 64 columns]
 static bool make_map(CUtensorMap* m, const void* ptr, int rows, int cols, int ld, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-  cuuint32_t box[2] = {(cuuint32_t)TC_BK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {64u, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box,
             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
@@ -277,7 +303,8 @@ bool gemm_tc_supported(const GemmDesc& d) {
 
 template <int BN>
 static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int K,
-                     const GemmDesc& d, int trans, const GemmWorkspace& ws, cudaStream_t s) {
+                     const GemmDesc& d, int trans, int a_mn, int b_mn, const GemmWorkspace& ws,
+                     cudaStream_t s) {
   static bool attr_done[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -304,7 +331,7 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
   dim3 grid(gm, gn, splits);
   gemm_tc_kernel<BN><<<grid, TC_THREADS, tc_smem<BN>(), s>>>(
       ma, mb, M, N, K, kchunk, (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu, trans,
-      partial, ws.err);
+      partial, ws.err, a_mn, b_mn);
   DDPPO_CHECK_LAUNCH();
   if (partial)
     DDPPO_TRY(launch_splitk_reduce(d.M, d.N, splits, partial, (float*)d.C, d.ldc, d.c_bf16, d.beta,
@@ -318,15 +345,20 @@ int gemm_tc(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s) {
   const void* A = swap ? d.B : d.A;
   const void* Bm = swap ? d.A : d.B;
   const int lda = swap ? d.ldb : d.lda, ldb = swap ? d.lda : d.ldb;
+  const int a_mn = swap ? d.b_t : d.a_t, b_mn = swap ? d.a_t : d.b_t;
   const int M = swap ? d.N : d.M, N = swap ? d.M : d.N;
   const int BN = N > 64 ? 128 : 64;
   CUtensorMap ma, mb;
-  if (!make_map(&ma, A, M, d.K, lda, TC_BM) || !make_map(&mb, Bm, N, d.K, ldb, BN)) {
+  // K-major operand: [rows = M|N, cols = K] boxes of 128|BN rows x 64 K;
+  // MN-major operand: [rows = K, cols = M|N] boxes of 64 K rows x 64 columns
+  const bool okA = a_mn ? make_map(&ma, A, d.K, M, lda, TC_BK) : make_map(&ma, A, M, d.K, lda, TC_BM);
+  const bool okB = b_mn ? make_map(&mb, Bm, d.K, N, ldb, TC_BK) : make_map(&mb, Bm, N, d.K, ldb, BN);
+  if (!okA || !okB) {
     set_error("gemm_tc: tensor map encoding failed");
     return DDPPO_E_CUDA;
   }
-  if (BN == 128) return launch_tc<128>(ma, mb, M, N, d.K, d, swap ? 1 : 0, ws, s);
-  return launch_tc<64>(ma, mb, M, N, d.K, d, swap ? 1 : 0, ws, s);
+  if (BN == 128) return launch_tc<128>(ma, mb, M, N, d.K, d, swap ? 1 : 0, a_mn, b_mn, ws, s);
+  return launch_tc<64>(ma, mb, M, N, d.K, d, swap ? 1 : 0, a_mn, b_mn, ws, s);
 }
 
 }  // namespace ddppo

@@ -181,10 +181,8 @@ static int alloc_encoder(Net& n) {
     DDPPO_TRY(gn_bufs(n.cmp_n, n.featHW, true));
   }
   DDPPO_TRY(nalloc_op(n, &n.col, NC * n.max_col));
-  DDPPO_TRY(nalloc_op(n, &n.colT, NC * n.max_col));
   DDPPO_TRY(nalloc(n, &n.dcol, NC * n.max_col));
   DDPPO_TRY(nalloc_op(n, &n.dzop, NC * n.max_dz));
-  DDPPO_TRY(nalloc_op(n, &n.dzT, NC * n.max_dz));
   DDPPO_TRY(nalloc(n, &n.g0, NC * n.max_act));
   DDPPO_TRY(nalloc(n, &n.g1, NC * n.max_act));
   DDPPO_TRY(nalloc(n, &n.g2, NC * n.max_act));
@@ -324,13 +322,10 @@ int net_create(ddppo_ctx* x) {
   DDPPO_TRY(nalloc(n, &n.dX[1], NS * n.InMax));
   DDPPO_TRY(nalloc(n, &n.dg32, NS * G4));
   DDPPO_TRY(nalloc_op(n, &n.dgop, NS * G4));
-  DDPPO_TRY(nalloc_op(n, &n.dgT, NS * G4));
-  DDPPO_TRY(nalloc_op(n, &n.XT, NS * n.InMax));
   DDPPO_TRY(nalloc(n, &n.dh_rec, (size_t)n.E * Hd));
   DDPPO_TRY(nalloc(n, &n.dc_carry, (size_t)n.E * Hd));
   DDPPO_TRY(nalloc(n, &n.dv32, NS * Hd));
   DDPPO_TRY(nalloc_op(n, &n.dvop, NS * Hd));
-  DDPPO_TRY(nalloc_op(n, &n.dvT, NS * Hd));
   DDPPO_TRY(nalloc(n, &n.dlogits, NS * 4));
   DDPPO_TRY(nalloc(n, &n.dvalues, NS));
   n.scratch_elems = std::max((size_t)1 << 16, 5 * Hd * ((NS + 63) / 64) + 4096);
@@ -403,16 +398,18 @@ static int conv_fwd(Net& n, ConvL& c, const void* in, bool in_bf16, int N, float
   return G(n, d, s);
 }
 
-// weight gradient (accumulated over chunks) and, if dx, the input gradient
+// weight gradient (accumulated over chunks) and, if dx, the input gradient.
+//   dW[co, kk] += sum_m dz[m, co] col[m, kk]   (both operands read as stored: MN-major)
+//   dcol[m, kk] = sum_co dz[m, co] W[co, kk]   then col2im
 static int conv_bwd(Net& n, ConvL& c, const void* in, bool in_bf16, int N, const void* dzop,
                     float* dx, bool dx_acc, bool first, cudaStream_t s) {
   const ConvGeom g = geom(c, N);
   const int M = N * c.Ho * c.Wo;
-  DDPPO_TRY(launch_transpose(dzop, n.bf, n.dzT, n.bf, M, c.cout, c.cout, s));
-  DDPPO_TRY(launch_im2col(g, in, in_bf16, n.colT, n.bf, true, s));
+  DDPPO_TRY(launch_im2col(g, in, in_bf16, n.col, n.bf, false, s));
   GemmDesc w;
   w.M = c.cout; w.N = c.Kp; w.K = M;
-  w.A = n.dzT; w.lda = M; w.B = n.colT; w.ldb = M;
+  w.A = dzop; w.lda = c.cout; w.a_t = 1;
+  w.B = n.col; w.ldb = c.Kp; w.b_t = 1;
   w.C = c.dwg; w.ldc = c.Kp; w.beta = first ? 0.f : 1.f;
   DDPPO_TRY(G(n, w, s));
   if (dx) {
@@ -657,17 +654,15 @@ int net_backward(Net& n, const float* dlogits, const float* dvalues, cudaStream_
     DDPPO_TRY(G(n, dx, s));
     const void* X = l == 0 ? n.x1 : n.lstm[l - 1].y;
     const int ldX = l == 0 ? n.In0 : Hd;
-    DDPPO_TRY(launch_transpose(n.dgop, n.bf, n.dgT, n.bf, N, G4, G4, s));
-    DDPPO_TRY(launch_transpose(X, n.bf, n.XT, n.bf, N, q.In, ldX, s));
+    // dW_ih[g, i] = sum_n dG[n, g] X[n, i]; dW_hh[g, j] = sum_n dG[n, g] Hm[n, j]
     GemmDesc wi;
     wi.M = G4; wi.N = q.In; wi.K = N;
-    wi.A = n.dgT; wi.lda = N; wi.B = n.XT; wi.ldb = N;
+    wi.A = n.dgop; wi.lda = G4; wi.a_t = 1; wi.B = X; wi.ldb = ldX; wi.b_t = 1;
     wi.C = n.grad + q.wih; wi.ldc = q.In;
     DDPPO_TRY(G(n, wi, s));
-    DDPPO_TRY(launch_transpose(q.hm, n.bf, n.XT, n.bf, N, Hd, Hd, s));
     GemmDesc wh;
     wh.M = G4; wh.N = Hd; wh.K = N;
-    wh.A = n.dgT; wh.lda = N; wh.B = n.XT; wh.ldb = N;
+    wh.A = n.dgop; wh.lda = G4; wh.a_t = 1; wh.B = q.hm; wh.ldb = Hd; wh.b_t = 1;
     wh.C = n.grad + q.whh; wh.ldc = Hd;
     DDPPO_TRY(G(n, wh, s));
     DDPPO_TRY(launch_colsum(n.dg32, N, G4, G4, n.grad + q.bih, false, s));
@@ -679,11 +674,9 @@ int net_backward(Net& n, const float* dlogits, const float* dvalues, cudaStream_
   DDPPO_TRY(launch_embed_bwd(N, n.ev_goal, n.ev_preva, dabove, n.In0, Hd, n.grad + n.goal_w,
                              n.grad + n.goal_b, n.grad + n.emb, n.scratch, n.scratch_elems, s));
   DDPPO_TRY(launch_colsum(n.dv32, N, Hd, Hd, n.grad + n.vis_b, false, s));
-  DDPPO_TRY(launch_transpose(n.dvop, n.bf, n.dvT, n.bf, N, Hd, Hd, s));
-  DDPPO_TRY(launch_transpose(n.featop, n.bf, n.featT, n.bf, N, n.F, n.F, s));
-  GemmDesc wv;
+  GemmDesc wv;  // dWv[h, f] = sum_n dv[n, h] feat[n, f]
   wv.M = Hd; wv.N = n.F; wv.K = N;
-  wv.A = n.dvT; wv.lda = N; wv.B = n.featT; wv.ldb = N;
+  wv.A = n.dvop; wv.lda = Hd; wv.a_t = 1; wv.B = n.featop; wv.ldb = n.F; wv.b_t = 1;
   wv.C = n.dWv; wv.ldc = n.F;
   DDPPO_TRY(G(n, wv, s));
   DDPPO_TRY(launch_vis_w_grad(n.dWv, Hd, n.featC, n.featHW, n.grad + n.vis_w, s));
@@ -698,7 +691,7 @@ int net_backward(Net& n, const float* dlogits, const float* dvalues, cudaStream_
     const int r0 = c * n.NC, rn = std::min(n.NC, N - r0);
     const void* obs_c = opoff(n, n.ev_obs, (size_t)r0 * n.pix);
     if (c != n.ev_valid_chunk) {
-      DDPPO_TRY(encoder_fwd(n, obs_c, rn, opoff(n, n.featT, 0), s));  // featT is free now
+      DDPPO_TRY(encoder_fwd(n, obs_c, rn, n.featT, s));  // feature rows are not needed again
       n.ev_valid_chunk = c;
     }
     DDPPO_TRY(encoder_bwd(n, obs_c, rn, n.dfeat + (size_t)r0 * n.F, c == nch - 1, s));

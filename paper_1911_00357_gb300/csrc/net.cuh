@@ -89,8 +89,8 @@ struct Net {
   LstmL lstm[4];
 
   // scratch
-  void* col = nullptr; void* colT = nullptr; float* dcol = nullptr;
-  void* dzop = nullptr; void* dzT = nullptr;
+  void* col = nullptr; float* dcol = nullptr;
+  void* dzop = nullptr;
   float* g0 = nullptr; float* g1 = nullptr; float* g2 = nullptr;
   float* gnp_g = nullptr; float* gnp_b = nullptr;
   void* featop = nullptr; float* dfeat = nullptr; void* featT = nullptr;
@@ -98,9 +98,9 @@ struct Net {
   float* gx = nullptr; float* gh = nullptr;
   float* logits = nullptr; float* values = nullptr;
   float* dh_top = nullptr; float* dX[2] = {nullptr, nullptr};
-  float* dg32 = nullptr; void* dgop = nullptr; void* dgT = nullptr; void* XT = nullptr;
+  float* dg32 = nullptr; void* dgop = nullptr;
   float* dh_rec = nullptr; float* dc_carry = nullptr;
-  float* dv32 = nullptr; void* dvop = nullptr; void* dvT = nullptr;
+  float* dv32 = nullptr; void* dvop = nullptr;
   float* dlogits = nullptr; float* dvalues = nullptr;
   float* scratch = nullptr; size_t scratch_elems = 0;
   GemmWorkspace gws;

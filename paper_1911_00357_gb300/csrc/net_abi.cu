@@ -397,13 +397,14 @@ extern "C" int ddppo_count_kernels(ddppo_ctx* x, const ddppo_rollout* ro,
 
 // ---- stand-alone GEMM (the contraction every network layer uses) ----
 extern "C" int ddppo_gemm(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const void* A,
-                          int32_t lda, const void* B, int32_t ldb, void* C, int32_t ldc,
-                          int32_t c_bf16, float beta, const float* bias, int32_t relu,
-                          int32_t* status, void* stream) {
+                          int32_t lda, int32_t a_t, const void* B, int32_t ldb, int32_t b_t,
+                          void* C, int32_t ldc, int32_t c_bf16, float beta, const float* bias,
+                          int32_t relu, int32_t* status, void* stream) {
   ARG(M >= 0 && N >= 0 && K >= 1, "gemm: bad sizes");
   if (M == 0 || N == 0) return DDPPO_OK;
   ARG(A && B && C, "gemm: null argument");
-  ARG(lda >= K && ldb >= K && ldc >= N, "gemm: leading dimension smaller than the row");
+  ARG(lda >= (a_t ? M : K) && ldb >= (b_t ? N : K) && ldc >= N,
+      "gemm: leading dimension smaller than the row");
   static float* partial[64] = {};
   int dev = 0;
   DDPPO_CHECK_CUDA(cudaGetDevice(&dev));
@@ -418,6 +419,7 @@ extern "C" int ddppo_gemm(int32_t M, int32_t N, int32_t K, int32_t op_bf16, cons
   GemmDesc d;
   d.M = M; d.N = N; d.K = K; d.A = A; d.lda = lda; d.B = B; d.ldb = ldb; d.C = C; d.ldc = ldc;
   d.c_bf16 = c_bf16; d.beta = beta; d.bias = bias; d.relu = relu;
+  d.a_t = a_t ? 1 : 0; d.b_t = b_t ? 1 : 0;
   return gemm(d, op_bf16 != 0, ws, (cudaStream_t)stream, nullptr);
 }
 

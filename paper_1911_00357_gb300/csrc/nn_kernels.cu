@@ -74,13 +74,63 @@ static unsigned grid_for(size_t total) {
   return (unsigned)b;
 }
 
+// Vectorised forward-layout im2col for C % 8 == 0: one thread per (row m, tap, 8-channel
+// group); 8 channels are read (two float4 or one 16-byte bf16 load) and written with one
+// 16-byte (bf16) or two (fp32) stores, so index decoding happens once per 8 elements and
+// consecutive threads touch consecutive bytes.
+template <typename Ti, typename To>
+__global__ void im2col_vec_kernel(ConvGeom g, const Ti* __restrict__ x, To* __restrict__ col) {
+  const int C8 = g.C >> 3, taps = g.k * g.k;
+  const size_t total = (size_t)g.N * g.Ho * g.Wo * taps * C8;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int c8 = (int)(idx % C8);
+    const size_t q = idx / C8;
+    const int tap = (int)(q % taps);
+    const size_t m = q / taps;
+    const int ky = tap / g.k, kx = tap - ky * g.k;
+    const int ox = (int)(m % g.Wo), oy = (int)((m / g.Wo) % g.Ho), n = (int)(m / ((size_t)g.Wo * g.Ho));
+    const int iy = oy * g.s - g.p + ky, ix = ox * g.s - g.p + kx;
+    float v[8];
+    if (iy >= 0 && iy < g.H && ix >= 0 && ix < g.W) {
+      const Ti* src = x + (((size_t)n * g.H + iy) * g.W + ix) * g.C + c8 * 8;
+      if constexpr (sizeof(Ti) == 4) {
+        const float4 a = *(const float4*)src, b = *(const float4*)(src + 4);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+      } else {
+        const uint4 u = *(const uint4*)src;
+        const __nv_bfloat16* h = (const __nv_bfloat16*)&u;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) v[i] = __bfloat162float(h[i]);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = 0.f;
+    }
+    To* dst = col + m * g.Kp + (size_t)tap * g.C + c8 * 8;
+    if constexpr (sizeof(To) == 2) {
+      uint4 u;
+      __nv_bfloat16* h = (__nv_bfloat16*)&u;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) h[i] = __float2bfloat16_rn(v[i]);
+      *(uint4*)dst = u;
+    } else {
+      *(float4*)dst = make_float4(v[0], v[1], v[2], v[3]);
+      *(float4*)(dst + 4) = make_float4(v[4], v[5], v[6], v[7]);
+    }
+  }
+}
+
 int launch_im2col(const ConvGeom& g, const void* x, bool x_bf16, void* col, bool op_bf16,
                   bool transposed, cudaStream_t s) {
   const size_t total = (size_t)g.N * g.Ho * g.Wo * g.Kp;
   if (total == 0) return DDPPO_OK;
-  const unsigned gb = grid_for(total);
+  const bool vec = !transposed && g.C % 8 == 0 && g.Kp == g.K && g.Kp % 8 == 0 &&
+                   ((uintptr_t)x & 15) == 0 && ((uintptr_t)col & 15) == 0;
+  const unsigned gb = grid_for(vec ? total / 8 : total);
 #define IM2COL_CASE(TI, TO)                                                                   \
-  if (transposed) im2colT_kernel<TI, TO><<<gb, 256, 0, s>>>(g, (const TI*)x, (TO*)col);      \
+  if (vec) im2col_vec_kernel<TI, TO><<<gb, 256, 0, s>>>(g, (const TI*)x, (TO*)col);           \
+  else if (transposed) im2colT_kernel<TI, TO><<<gb, 256, 0, s>>>(g, (const TI*)x, (TO*)col);  \
   else im2col_kernel<TI, TO><<<gb, 256, 0, s>>>(g, (const TI*)x, (TO*)col);
   if (x_bf16 && op_bf16) { IM2COL_CASE(__nv_bfloat16, __nv_bfloat16) }
   else if (x_bf16) { IM2COL_CASE(__nv_bfloat16, float) }
@@ -118,10 +168,52 @@ __global__ void col2im_kernel(ConvGeom g, const float* __restrict__ dcol, float*
   }
 }
 
+// vectorised col2im for C % 8 == 0: one thread per (pixel, 8-channel group)
+__global__ void col2im_vec_kernel(ConvGeom g, const float* __restrict__ dcol, float* __restrict__ dx,
+                                  int accumulate) {
+  const int C8 = g.C >> 3;
+  const size_t total = (size_t)g.N * g.H * g.W * C8;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int c8 = (int)(idx % C8);
+    const size_t pix = idx / C8;
+    const int ix = (int)(pix % g.W), iy = (int)((pix / g.W) % g.H), n = (int)(pix / ((size_t)g.W * g.H));
+    float a[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int ky = 0; ky < g.k; ++ky) {
+      const int ty = iy + g.p - ky;
+      if (ty < 0 || ty % g.s) continue;
+      const int oy = ty / g.s;
+      if (oy >= g.Ho) continue;
+      for (int kx = 0; kx < g.k; ++kx) {
+        const int tx = ix + g.p - kx;
+        if (tx < 0 || tx % g.s) continue;
+        const int ox = tx / g.s;
+        if (ox >= g.Wo) continue;
+        const float* src = dcol + (((size_t)n * g.Ho + oy) * g.Wo + ox) * g.Kp +
+                           (size_t)(ky * g.k + kx) * g.C + c8 * 8;
+        const float4 u = *(const float4*)src, w = *(const float4*)(src + 4);
+        a[0] += u.x; a[1] += u.y; a[2] += u.z; a[3] += u.w;
+        a[4] += w.x; a[5] += w.y; a[6] += w.z; a[7] += w.w;
+      }
+    }
+    float* d = dx + pix * g.C + c8 * 8;
+    if (accumulate) {
+      const float4 u = *(const float4*)d, w = *(const float4*)(d + 4);
+      a[0] += u.x; a[1] += u.y; a[2] += u.z; a[3] += u.w;
+      a[4] += w.x; a[5] += w.y; a[6] += w.z; a[7] += w.w;
+    }
+    *(float4*)d = make_float4(a[0], a[1], a[2], a[3]);
+    *(float4*)(d + 4) = make_float4(a[4], a[5], a[6], a[7]);
+  }
+}
+
 int launch_col2im(const ConvGeom& g, const float* dcol, float* dx, bool accumulate, cudaStream_t s) {
   const size_t total = (size_t)g.N * g.H * g.W * g.C;
   if (total == 0) return DDPPO_OK;
-  col2im_kernel<<<grid_for(total), 256, 0, s>>>(g, dcol, dx, accumulate ? 1 : 0);
+  if (g.C % 8 == 0 && g.Kp % 4 == 0 && ((uintptr_t)dcol & 15) == 0 && ((uintptr_t)dx & 15) == 0)
+    col2im_vec_kernel<<<grid_for(total / 8), 256, 0, s>>>(g, dcol, dx, accumulate ? 1 : 0);
+  else
+    col2im_kernel<<<grid_for(total), 256, 0, s>>>(g, dcol, dx, accumulate ? 1 : 0);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }

@@ -50,6 +50,31 @@ def test_gemm_parity(M, N, K, dtype):
         assert B.ddppo_gemm_backend(A, Bm)
 
 
+TRANS_SHAPES = [(32, 288, 24576), (64, 576, 4100), (2048, 576, 1000), (2048, 512, 4096),
+                (512, 2048, 64), (37, 56, 3000), (300, 200, 136)]
+
+
+@pytest.mark.parametrize("M,N,K", TRANS_SHAPES)
+@pytest.mark.parametrize("a_t,b_t", [(1, 1), (1, 0), (0, 1)])
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float32])
+def test_gemm_mn_major_operands(M, N, K, a_t, b_t, dtype):
+    """Operands stored [K, M] / [K, N] (the weight-gradient contractions)."""
+    g = torch.Generator(device="cuda").manual_seed(M + 3 * N + 7 * K + a_t + 2 * b_t)
+    A = torch.randn(M, K, device="cuda", generator=g).to(dtype)
+    Bm = torch.randn(N, K, device="cuda", generator=g).to(dtype)
+    At = A.t().contiguous() if a_t else A
+    Bt = Bm.t().contiguous() if b_t else Bm
+    C = torch.zeros(M, N, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.ddppo_gemm(At, Bt, C, status=st, a_t=bool(a_t), b_t=bool(b_t))
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    ref = _ref(A, Bm, None, 0.0, None, False)
+    tol = 1e-5 * np.sqrt(K) * 4.0
+    err = (C.double().cpu() - ref).abs().max().item()
+    assert err <= tol, (err, tol)
+
+
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float32])
 def test_gemm_epilogue_and_strides(dtype):
     M, N, K = 300, 200, 136
