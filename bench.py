@@ -173,7 +173,7 @@ def run_gpu(args):
     peaks, pk_kind = _peaks()
     g_ms, g_n, g_flops = gemm
     achieved = g_flops / (g_ms / 1e3) / 1e12 if g_ms > 0 else 0.0
-    tc_flops_share = (tc[2] / gemm[2]) if gemm[2] > 0 else 0.0
+    tc_flops_share = (tc[2] / tc[0]) if tc[0] > 0 else 0.0
     if precision == 1 and tc[1] > 0:
         bound, peak_v, unit = "tensor", peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]), "TFLOP/s"
     else:

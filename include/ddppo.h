@@ -320,7 +320,7 @@ int ddppo_gemm_backend(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const v
 int ddppo_timing_enable(ddppo_ctx* ctx, int32_t on);
 int ddppo_timing_read(ddppo_ctx* ctx, int32_t family, double* ms, int64_t* launches, double* work);
 /* family 2 reports the launches and FLOPs of the contractions that ran on the tcgen05
- * tensor-core GEMM (ms = 0). */
+ * tensor-core GEMM; its `ms` slot carries the FLOPs of all contractions while enabled. */
 
 /* Number of kernel launches of one steady-state iteration (collect of T steps, bootstrap
  * value, GAE, PPO update) with this rollout and hyper-parameters: the iteration is

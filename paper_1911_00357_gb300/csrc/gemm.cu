@@ -149,6 +149,7 @@ int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t 
     return DDPPO_E_CONFIG;
   }
   const bool rec = timer && timer->on && timer->n + 2 <= 2 * 4096;
+  if (timer && timer->on) timer->flops_all += 2.0 * d.M * d.N * d.K;
   if (rec) cudaEventRecord(timer->ev[timer->n], s);
   int rc;
   if (op_bf16 && gemm_tc_supported(d)) {

@@ -45,8 +45,9 @@ struct KernelTimer {
   bool on = false;
   int n = 0;
   cudaEvent_t ev[2 * 4096];
-  double flops = 0.0;
+  double flops = 0.0;      // work of the launches that carry events
   int64_t launches = 0;
+  double flops_all = 0.0;  // work of every launch while enabled
 };
 
 int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t s,

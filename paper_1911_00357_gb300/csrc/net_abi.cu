@@ -311,6 +311,7 @@ extern "C" int ddppo_timing_enable(ddppo_ctx* x, int32_t on) {
     t->on = on != 0;
     t->n = 0;
     t->flops = 0.0;
+    t->flops_all = 0.0;
     t->launches = 0;
   }
   return DDPPO_OK;
@@ -321,7 +322,8 @@ extern "C" int ddppo_timing_read(ddppo_ctx* x, int32_t family, double* ms, int64
   ARG(x && x->net && ms && launches && work, "timing_read: null argument");
   ARG(family >= 0 && family <= 2, "timing_read: family must be 0, 1 or 2");
   if (family == 2) {
-    *ms = 0.0;
+    // tcgen05 launches; ms carries the FLOPs of every GEMM launch (tensor core or not)
+    *ms = x->net->timer.flops_all;
     *launches = x->net->tc_count.launches;
     *work = x->net->tc_count.flops;
     return DDPPO_OK;
