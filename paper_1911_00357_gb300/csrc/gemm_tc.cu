@@ -24,6 +24,7 @@
 namespace ddppo {
 
 constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4, TC_THREADS = 128;
+constexpr int TC_EPI_PITCH = 33;  // floats per staged row (bank-conflict-free transpose)
 constexpr uint32_t TC_SPIN_LIMIT = 1u << 22;
 
 struct TcSmem {
@@ -122,13 +123,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    int M, int N, int K, int kchunk, float* __restrict__ C, int ldc, int c_bf16,
                    float beta, const float* __restrict__ bias, int relu, int trans_out,
-                   float* __restrict__ partial, int32_t* err, int a_mn, int b_mn) {
+                   float* __restrict__ partial, int32_t* err, int a_mn, int b_mn, int stages) {
   extern __shared__ __align__(1024) uint8_t dyn[];
   __shared__ TcSmem ctl;
   constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2;
   uint8_t* base = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = base;
-  uint8_t* sB = base + TC_STAGES * A_BYTES;
+  uint8_t* sB = base + stages * A_BYTES;
+  float* stage_out = (float*)(sB + stages * B_BYTES) + (threadIdx.x >> 5) * 32 * TC_EPI_PITCH;
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   volatile int* abort = &ctl.abort;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < TC_STAGES; ++s) {
+    for (int s = 0; s < stages; ++s) {
       mbar_init(&ctl.full[s], 1);
       mbar_init(&ctl.empty[s], 1);
     }
@@ -159,8 +161,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 0 && lane == 0) {
     // TMA producer
     for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % TC_STAGES;
-      const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+      const int s = kb % stages;
+      const uint32_t ph = (uint32_t)(kb / stages) & 1u;
       if (!mbar_wait(&ctl.empty[s], ph ^ 1u, abort, err)) break;
       mbar_expect_tx(&ctl.full[s], A_BYTES + B_BYTES);
       const int k = kbeg + kb * TC_BK;
@@ -182,8 +184,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // MMA issuer
     const uint32_t idesc = f16_idesc(TC_BM, BN, a_mn, b_mn);
     for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % TC_STAGES;
-      const uint32_t ph = (uint32_t)(kb / TC_STAGES) & 1u;
+      const int s = kb % stages;
+      const uint32_t ph = (uint32_t)(kb / stages) & 1u;
       if (!mbar_wait(&ctl.full[s], ph, abort, err)) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a0 = smem_addr(sA + s * A_BYTES), b0 = smem_addr(sB + s * B_BYTES);
@@ -213,10 +215,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   __syncwarp();
 
-  // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31
+  // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31. Each 32-column chunk is read
+  // with tcgen05.ld (thread = row) and, unless the output is transposed, staged through
+  // shared memory so that every warp store writes one contiguous row segment.
   const bool ok = mbar_wait(&ctl.done, 0, abort, err) && nkb > 0;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int row = m0 + warp * 32 + lane;
+  const int Mo = trans_out ? N : M, No = trans_out ? M : N;  // caller's output shape
 #pragma unroll 1
   for (int c0 = 0; c0 < BN; c0 += 32) {
     uint32_t r[32];
@@ -231,25 +236,53 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    if (!ok || row >= M) continue;
+    if (!ok || n0 + c0 >= N) continue;
+    if (trans_out) {
+      // caller element (col, row): for a fixed j the 32 lanes write 32 consecutive columns
+      if (row >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      const int col = n0 + c0 + j;
-      if (col >= N) break;
-      float v = __uint_as_float(r[j]);
-      // (m, n) of the problem as the caller sees it
-      const int pm = trans_out ? col : row, pn = trans_out ? row : col;
+      for (int j = 0; j < 32; ++j) {
+        const int col = n0 + c0 + j;
+        if (col >= N) break;
+        float v = __uint_as_float(r[j]);
+        if (partial) {
+          partial[((size_t)blockIdx.z * Mo + col) * No + row] = v;
+          continue;
+        }
+        const size_t o = (size_t)col * ldc + row;
+        if (beta != 0.f) v += beta * C[o];
+        if (bias) v += bias[row];
+        if (relu) v = fmaxf(v, 0.f);
+        if (c_bf16) ((__nv_bfloat16*)C)[o] = __float2bfloat16_rn(v);
+        else C[o] = v;
+      }
+      continue;
+    }
+    // stage the warp's 32x32 chunk (row = lane), then store row by row: lane = column
+#pragma unroll
+    for (int j = 0; j < 32; ++j) stage_out[lane * TC_EPI_PITCH + j] = __uint_as_float(r[j]);
+    __syncwarp();
+    const int col = n0 + c0 + lane;
+    const bool cin = col < N;
+    const float bv = (bias && cin) ? bias[col] : 0.f;
+#pragma unroll 4
+    for (int i = 0; i < 32; ++i) {
+      const int rr = m0 + warp * 32 + i;
+      if (rr >= M) break;
+      float v = stage_out[i * TC_EPI_PITCH + lane];
+      if (!cin) continue;
       if (partial) {
-        partial[((size_t)blockIdx.z * (trans_out ? N : M) + pm) * (trans_out ? M : N) + pn] = v;
+        partial[((size_t)blockIdx.z * Mo + rr) * No + col] = v;
         continue;
       }
-      const size_t o = (size_t)pm * ldc + pn;
+      const size_t o = (size_t)rr * ldc + col;
       if (beta != 0.f) v += beta * C[o];
-      if (bias) v += bias[pn];
+      v += bv;
       if (relu) v = fmaxf(v, 0.f);
       if (c_bf16) ((__nv_bfloat16*)C)[o] = __float2bfloat16_rn(v);
       else C[o] = v;
     }
+    __syncwarp();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -288,8 +321,8 @@ static bool make_map(CUtensorMap* m, const void* ptr, int rows, int cols, int ld
 }
 
 template <int BN>
-static size_t tc_smem() {
-  return (size_t)TC_STAGES * (TC_BM + BN) * TC_BK * 2 + 1024;
+static size_t tc_smem(int stages) {
+  return (size_t)stages * (TC_BM + BN) * TC_BK * 2 + 4 * 32 * TC_EPI_PITCH * 4 + 1024;
 }
 
 bool gemm_tc_supported(const GemmDesc& d) {
@@ -311,7 +344,7 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
   if (dev < 64 && !attr_done[dev]) {
     DDPPO_CHECK_CUDA(cudaFuncSetAttribute(gemm_tc_kernel<BN>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)tc_smem<BN>()));
+                                          (int)tc_smem<BN>(TC_STAGES)));
     attr_done[dev] = true;
   }
   const int gm = (M + TC_BM - 1) / TC_BM, gn = (N + BN - 1) / BN;
@@ -328,10 +361,14 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
   kchunk = (kchunk + TC_BK - 1) / TC_BK * TC_BK;
   splits = (K + kchunk - 1) / kchunk;
   float* partial = splits > 1 ? ws.partial : nullptr;
+  // pipeline depth: enough stages to cover the K loop, at most 4; shallow pipelines leave
+  // room for more CTAs per SM, whose epilogues then overlap other CTAs' loads
+  const int nkb = (kchunk + TC_BK - 1) / TC_BK;
+  const int stages = nkb >= 4 ? TC_STAGES : (nkb <= 2 ? 2 : 3);
   dim3 grid(gm, gn, splits);
-  gemm_tc_kernel<BN><<<grid, TC_THREADS, tc_smem<BN>(), s>>>(
+  gemm_tc_kernel<BN><<<grid, TC_THREADS, tc_smem<BN>(stages), s>>>(
       ma, mb, M, N, K, kchunk, (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu, trans,
-      partial, ws.err, a_mn, b_mn);
+      partial, ws.err, a_mn, b_mn, stages);
   DDPPO_CHECK_LAUNCH();
   if (partial)
     DDPPO_TRY(launch_splitk_reduce(d.M, d.N, splits, partial, (float*)d.C, d.ldc, d.c_bf16, d.beta,
