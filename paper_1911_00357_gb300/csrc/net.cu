@@ -145,6 +145,13 @@ static int alloc_encoder(Net& n) {
     DDPPO_TRY(nalloc_op(n, &c.wgT, (size_t)c.cout * c.Kp));
     DDPPO_TRY(nalloc(n, &c.dwg, (size_t)c.cout * c.Kp));
     DDPPO_TRY(nalloc(n, &c.z, NC * c.Ho * c.Wo * c.cout));
+    // a stride-1 'same' convolution's input gradient is a convolution of its output
+    // gradient with the flipped, channel-swapped kernel: no col2im round trip
+    c.dgrad_as_conv = c.s == 1 && c.k % 2 == 1 && c.p == c.k / 2 && c.cout % 8 == 0;
+    if (c.dgrad_as_conv) {
+      DDPPO_TRY(nalloc_op(n, &c.wgR, (size_t)c.cin * c.k * c.k * c.cout));
+      n.max_col = std::max(n.max_col, (size_t)c.H * c.W * c.k * c.k * c.cout);
+    }
     n.max_col = std::max(n.max_col, (size_t)c.Ho * c.Wo * c.Kp);
     n.max_dz = std::max(n.max_dz, (size_t)c.Ho * c.Wo * c.cout);
     n.max_act = std::max(n.max_act, c.Ho * c.Wo * c.cout);
@@ -245,9 +252,12 @@ static int init_params(Net& n, cudaStream_t s) {
 
 // canonical fp32 params -> GEMM operands in the precision's dtype
 int net_prep_weights(Net& n, cudaStream_t s) {
-  for (ConvL* c : n.convs)
+  for (ConvL* c : n.convs) {
     DDPPO_TRY(launch_conv_w_prep(n.params + c->w_off, c->cout, c->cin, c->k, c->Kp, c->wg, c->wgT,
                                  n.bf, s));
+    if (c->dgrad_as_conv)
+      DDPPO_TRY(launch_conv_w_flip(n.params + c->w_off, c->cout, c->cin, c->k, c->wgR, n.bf, s));
+  }
   DDPPO_TRY(launch_vis_w_prep(n.params + n.vis_w, n.H, n.featC, n.featHW, n.Wv, n.WvT, n.bf, s));
   for (int l = 0; l < n.L; ++l) {
     LstmL& q = n.lstm[l];
@@ -412,7 +422,18 @@ static int conv_bwd(Net& n, ConvL& c, const void* in, bool in_bf16, int N, const
   w.B = n.col; w.ldb = c.Kp; w.b_t = 1;
   w.C = c.dwg; w.ldc = c.Kp; w.beta = first ? 0.f : 1.f;
   DDPPO_TRY(G(n, w, s));
-  if (dx) {
+  if (dx && c.dgrad_as_conv) {
+    // dx = conv(dz, flipped kernel): im2col of dz (C = cout) then one GEMM into dx
+    ConvGeom gd;
+    gd.N = N; gd.H = c.Ho; gd.W = c.Wo; gd.C = c.cout; gd.Ho = c.H; gd.Wo = c.W; gd.Cout = c.cin;
+    gd.k = c.k; gd.s = 1; gd.p = c.p; gd.K = c.k * c.k * c.cout; gd.Kp = gd.K;
+    DDPPO_TRY(launch_im2col(gd, dzop, n.bf, n.col, n.bf, false, s));
+    GemmDesc d;
+    d.M = N * c.H * c.W; d.N = c.cin; d.K = gd.K;
+    d.A = n.col; d.lda = gd.K; d.B = c.wgR; d.ldb = gd.K;
+    d.C = dx; d.ldc = c.cin; d.beta = dx_acc ? 1.f : 0.f;
+    DDPPO_TRY(G(n, d, s));
+  } else if (dx) {
     GemmDesc d;
     d.M = M; d.N = c.Kp; d.K = c.cout;
     d.A = dzop; d.lda = c.cout; d.B = c.wgT; d.ldb = c.cout;

@@ -16,7 +16,9 @@ struct ConvL {
   int Kp = 0;
   int H = 0, W = 0, Ho = 0, Wo = 0;
   void* wg = nullptr;   // [cout, Kp] op dtype
-  void* wgT = nullptr;  // [Kp, cout] op dtype
+  void* wgT = nullptr;  // [Kp, cout] op dtype (dgrad through col2im)
+  void* wgR = nullptr;  // [cin, k*k*cout] op dtype: flipped, channel-swapped kernel (stride-1 dgrad)
+  bool dgrad_as_conv = false;
   float* dwg = nullptr; // [cout, Kp] fp32 gradient in GEMM layout
   float* z = nullptr;   // [NC, Ho, Wo, cout] conv output (fp32)
 };

@@ -877,6 +877,25 @@ int launch_conv_w_prep(const float* w, int cout, int cin, int k, int Kp, void* w
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
+__global__ void conv_w_flip_kernel(const float* __restrict__ w, int cout, int cin, int k, void* wr,
+                                   int bf) {
+  const size_t total = (size_t)cin * k * k * cout;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int co = (int)(idx % cout);
+    const int tap = (int)((idx / cout) % (k * k));
+    const int ci = (int)(idx / ((size_t)cout * k * k));
+    const int ky = tap / k, kx = tap % k;
+    st_op(wr, idx, w[(((size_t)co * cin + ci) * k + (k - 1 - ky)) * k + (k - 1 - kx)], bf);
+  }
+}
+int launch_conv_w_flip(const float* w, int cout, int cin, int k, void* wr, bool op_bf16,
+                       cudaStream_t s) {
+  conv_w_flip_kernel<<<grid_for((size_t)cin * k * k * cout), 256, 0, s>>>(w, cout, cin, k, wr,
+                                                                          op_bf16 ? 1 : 0);
+  DDPPO_CHECK_LAUNCH();
+  return DDPPO_OK;
+}
 __global__ void conv_w_grad_kernel(const float* __restrict__ dwg, int cout, int cin, int k, int Kp,
                                    float* __restrict__ dw) {
   const size_t total = (size_t)cout * cin * k * k;

@@ -125,6 +125,10 @@ int launch_gather_rows(const void* in, void* out, const int32_t* idx, int T, int
 // weight preparation and gradient scatter between canonical and GEMM layouts
 int launch_conv_w_prep(const float* w, int cout, int cin, int k, int Kp, void* wg, void* wgT,
                        bool op_bf16, cudaStream_t s);
+// wr[ci, (ky*k + kx)*cout + co] = w[co, ci, k-1-ky, k-1-kx]: the kernel of the input
+// gradient of a stride-1 'same' convolution, itself a convolution of the output gradient
+int launch_conv_w_flip(const float* w, int cout, int cin, int k, void* wr, bool op_bf16,
+                       cudaStream_t s);
 int launch_conv_w_grad(const float* dwg, int cout, int cin, int k, int Kp, float* dw,
                        cudaStream_t s);
 // vis FC: canonical column j = c*HW + hw  <->  GEMM column hw*C + c
