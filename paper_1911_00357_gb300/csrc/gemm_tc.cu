@@ -23,7 +23,7 @@
 
 namespace ddppo {
 
-constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4, TC_THREADS = 128;
+constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4;
 constexpr int TC_EPI_PITCH = 33;  // floats per staged row (bank-conflict-free transpose)
 constexpr uint32_t TC_SPIN_LIMIT = 1u << 22;
 
@@ -118,24 +118,29 @@ __host__ __device__ constexpr uint32_t f16_idesc(int M, int N, int a_mn = 0, int
          ((uint32_t)(b_mn & 1) << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// Persistent, warp-specialised kernel. Warp 0 streams (tile, k-block) stages through the
+// shared-memory ring with TMA; warp 1 issues the MMAs of a tile into one of two TMEM
+// accumulators; warps 2..5 drain the other accumulator (tcgen05.ld -> smem transpose ->
+// coalesced stores), so one tile's epilogue overlaps the next tile's loads and MMAs.
+// Tiles are (m, n, split) triples walked with stride gridDim.x.
+constexpr int TC_PTHREADS = 192;
+
 template <int BN>
-__global__ void __launch_bounds__(TC_THREADS, 1)
+__global__ void __launch_bounds__(TC_PTHREADS, 1)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    int M, int N, int K, int kchunk, float* __restrict__ C, int ldc, int c_bf16,
                    float beta, const float* __restrict__ bias, int relu, int trans_out,
-                   float* __restrict__ partial, int32_t* err, int a_mn, int b_mn, int stages) {
+                   float* __restrict__ partial, int32_t* err, int a_mn, int b_mn, int stages,
+                   int tiles_m, int tiles_n, int splits) {
   extern __shared__ __align__(1024) uint8_t dyn[];
   __shared__ TcSmem ctl;
+  __shared__ uint64_t acc_full[2], acc_empty[2];
   constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2;
   uint8_t* base = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = base;
   uint8_t* sB = base + stages * A_BYTES;
-  float* stage_out = (float*)(sB + stages * B_BYTES) + (threadIdx.x >> 5) * 32 * TC_EPI_PITCH;
-
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * TC_BM, n0 = blockIdx.y * BN;
-  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
-  const int nkb = (kend - kbeg + TC_BK - 1) / TC_BK;
+  const int ntiles = tiles_m * tiles_n * splits;
   volatile int* abort = &ctl.abort;
 
   if (threadIdx.x == 0) {
@@ -143,14 +148,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       mbar_init(&ctl.full[s], 1);
       mbar_init(&ctl.empty[s], 1);
     }
-    mbar_init(&ctl.done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+    }
     ctl.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_addr(&ctl.tmem_base)),
-                 "r"(BN));
+                 "r"(2 * BN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -158,137 +166,167 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = ctl.tmem_base;
 
-  if (warp == 0 && lane == 0) {
-    // TMA producer
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % stages;
-      const uint32_t ph = (uint32_t)(kb / stages) & 1u;
-      if (!mbar_wait(&ctl.empty[s], ph ^ 1u, abort, err)) break;
-      mbar_expect_tx(&ctl.full[s], A_BYTES + B_BYTES);
-      const int k = kbeg + kb * TC_BK;
-      if (a_mn) {
-        tma_load_2d(sA + s * A_BYTES, &mapA, &ctl.full[s], m0, k);
-        tma_load_2d(sA + s * A_BYTES + 8192, &mapA, &ctl.full[s], m0 + 64, k);
-      } else {
-        tma_load_2d(sA + s * A_BYTES, &mapA, &ctl.full[s], k, m0);
-      }
-      if (b_mn) {
+  if (warp == 0) {
+    if (lane == 0) {
+      // TMA producer over every (tile, k-block) of this CTA
+      uint32_t it = 0;
+      for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
+        const int tm = t % tiles_m, tn = (t / tiles_m) % tiles_n, z = t / (tiles_m * tiles_n);
+        const int m0 = tm * TC_BM, n0 = tn * BN;
+        const int kbeg = z * kchunk, kend = min(K, kbeg + kchunk);
+        const int nkb = (kend - kbeg + TC_BK - 1) / TC_BK;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % stages;
+          const uint32_t ph = (it / stages) & 1u;
+          if (!mbar_wait(&ctl.empty[s], ph ^ 1u, abort, err)) break;
+          mbar_expect_tx(&ctl.full[s], A_BYTES + B_BYTES);
+          const int k = kbeg + kb * TC_BK;
+          if (a_mn) {
+            tma_load_2d(sA + s * A_BYTES, &mapA, &ctl.full[s], m0, k);
+            tma_load_2d(sA + s * A_BYTES + 8192, &mapA, &ctl.full[s], m0 + 64, k);
+          } else {
+            tma_load_2d(sA + s * A_BYTES, &mapA, &ctl.full[s], k, m0);
+          }
+          if (b_mn) {
 #pragma unroll
-        for (int j = 0; j < BN / 64; ++j)
-          tma_load_2d(sB + s * B_BYTES + j * 8192, &mapB, &ctl.full[s], n0 + 64 * j, k);
-      } else {
-        tma_load_2d(sB + s * B_BYTES, &mapB, &ctl.full[s], k, n0);
+            for (int j = 0; j < BN / 64; ++j)
+              tma_load_2d(sB + s * B_BYTES + j * 8192, &mapB, &ctl.full[s], n0 + 64 * j, k);
+          } else {
+            tma_load_2d(sB + s * B_BYTES, &mapB, &ctl.full[s], k, n0);
+          }
+        }
       }
     }
-  } else if (warp == 1 && lane == 0) {
-    // MMA issuer
-    const uint32_t idesc = f16_idesc(TC_BM, BN, a_mn, b_mn);
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % stages;
-      const uint32_t ph = (uint32_t)(kb / stages) & 1u;
-      if (!mbar_wait(&ctl.full[s], ph, abort, err)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_addr(sA + s * A_BYTES), b0 = smem_addr(sB + s * B_BYTES);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // MMA issuer
+      const uint32_t idesc = f16_idesc(TC_BM, BN, a_mn, b_mn);
+      uint32_t it = 0, ti = 0;
+      for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++ti) {
+        const int z = t / (tiles_m * tiles_n);
+        const int kbeg = z * kchunk, kend = min(K, kbeg + kchunk);
+        const int nkb = (kend - kbeg + TC_BK - 1) / TC_BK;
+        const uint32_t buf = ti & 1u, bph = (ti >> 1) & 1u;
+        if (!mbar_wait(&acc_empty[buf], bph ^ 1u, abort, err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dacc = tmem + buf * BN;
+        for (int kb = 0; kb < nkb; ++kb, ++it) {
+          const int s = it % stages;
+          const uint32_t ph = (it / stages) & 1u;
+          if (!mbar_wait(&ctl.full[s], ph, abort, err)) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_addr(sA + s * A_BYTES), b0 = smem_addr(sB + s * B_BYTES);
 #pragma unroll
-      for (int k = 0; k < TC_BK / 16; ++k) {
-        // K-major: +32 B per 16-element K step inside the swizzle row; MN-major: +2 K groups
-        const uint64_t da = a_mn ? sw128_mn_desc(a0 + k * 2048) : sw128_desc(a0 + k * 32);
-        const uint64_t db = b_mn ? sw128_mn_desc(b0 + k * 2048) : sw128_desc(b0 + k * 32);
-        const uint32_t acc = (kb | k) ? 1u : 0u;
+          for (int k = 0; k < TC_BK / 16; ++k) {
+            const uint64_t da = a_mn ? sw128_mn_desc(a0 + k * 2048) : sw128_desc(a0 + k * 32);
+            const uint64_t db = b_mn ? sw128_mn_desc(b0 + k * 2048) : sw128_desc(b0 + k * 32);
+            const uint32_t acc = (kb | k) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\t"
+                "setp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dacc),
+                "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                : "memory");
+          }
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  smem_addr(&ctl.empty[s]))
+              : "memory");
+        }
         asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "setp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-            "l"(da), "l"(db), "r"(idesc), "r"(acc)
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_addr(&acc_full[buf]))
             : "memory");
       }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_addr(&ctl.empty[s]))
-          : "memory");
     }
-    // completion of every MMA issued so far
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-            smem_addr(&ctl.done))
-        : "memory");
-  }
-  __syncwarp();
-
-  // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31. Each 32-column chunk is read
-  // with tcgen05.ld (thread = row) and, unless the output is transposed, staged through
-  // shared memory so that every warp store writes one contiguous row segment.
-  const bool ok = mbar_wait(&ctl.done, 0, abort, err) && nkb > 0;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const int row = m0 + warp * 32 + lane;
-  const int Mo = trans_out ? N : M, No = trans_out ? M : N;  // caller's output shape
+  } else {
+    // epilogue warps 2..5: warp w reads TMEM lanes 32 (w % 4) .. +31
+    const int q = warp & 3;
+    float* stage_out = (float*)(sB + stages * B_BYTES) + q * 32 * TC_EPI_PITCH;
+    const int Mo = trans_out ? N : M, No = trans_out ? M : N;
+    uint32_t ti = 0;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++ti) {
+      const int tm = t % tiles_m, tn = (t / tiles_m) % tiles_n, z = t / (tiles_m * tiles_n);
+      const int m0 = tm * TC_BM, n0 = tn * BN;
+      const uint32_t buf = ti & 1u, bph = (ti >> 1) & 1u;
+      const bool ok = mbar_wait(&acc_full[buf], bph, abort, err);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int row = m0 + q * 32 + lane;
 #pragma unroll 1
-  for (int c0 = 0; c0 < BN; c0 += 32) {
-    uint32_t r[32];
-    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-          "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-          "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    if (!ok || n0 + c0 >= N) continue;
-    if (trans_out) {
-      // caller element (col, row): for a fixed j the 32 lanes write 32 consecutive columns
-      if (row >= M) continue;
+      for (int c0 = 0; c0 < BN; c0 += 32) {
+        uint32_t r[32];
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * BN + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+            "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+              "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+              "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+              "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (!ok || n0 + c0 >= N) continue;
+        if (trans_out) {
+          if (row >= M) continue;
 #pragma unroll
-      for (int j = 0; j < 32; ++j) {
-        const int col = n0 + c0 + j;
-        if (col >= N) break;
-        float v = __uint_as_float(r[j]);
-        if (partial) {
-          partial[((size_t)blockIdx.z * Mo + col) * No + row] = v;
+          for (int j = 0; j < 32; ++j) {
+            const int col = n0 + c0 + j;
+            if (col >= N) break;
+            float v = __uint_as_float(r[j]);
+            if (partial) {
+              partial[((size_t)z * Mo + col) * No + row] = v;
+              continue;
+            }
+            const size_t o = (size_t)col * ldc + row;
+            if (beta != 0.f) v += beta * C[o];
+            if (bias) v += bias[row];
+            if (relu) v = fmaxf(v, 0.f);
+            if (c_bf16) ((__nv_bfloat16*)C)[o] = __float2bfloat16_rn(v);
+            else C[o] = v;
+          }
           continue;
         }
-        const size_t o = (size_t)col * ldc + row;
-        if (beta != 0.f) v += beta * C[o];
-        if (bias) v += bias[row];
-        if (relu) v = fmaxf(v, 0.f);
-        if (c_bf16) ((__nv_bfloat16*)C)[o] = __float2bfloat16_rn(v);
-        else C[o] = v;
-      }
-      continue;
-    }
-    // stage the warp's 32x32 chunk (row = lane), then store row by row: lane = column
 #pragma unroll
-    for (int j = 0; j < 32; ++j) stage_out[lane * TC_EPI_PITCH + j] = __uint_as_float(r[j]);
-    __syncwarp();
-    const int col = n0 + c0 + lane;
-    const bool cin = col < N;
-    const float bv = (bias && cin) ? bias[col] : 0.f;
+        for (int j = 0; j < 32; ++j) stage_out[lane * TC_EPI_PITCH + j] = __uint_as_float(r[j]);
+        __syncwarp();
+        const int col = n0 + c0 + lane;
+        const bool cin = col < N;
+        const float bv = (bias && cin) ? bias[col] : 0.f;
 #pragma unroll 4
-    for (int i = 0; i < 32; ++i) {
-      const int rr = m0 + warp * 32 + i;
-      if (rr >= M) break;
-      float v = stage_out[i * TC_EPI_PITCH + lane];
-      if (!cin) continue;
-      if (partial) {
-        partial[((size_t)blockIdx.z * Mo + rr) * No + col] = v;
-        continue;
+        for (int i = 0; i < 32; ++i) {
+          const int rr = m0 + q * 32 + i;
+          if (rr >= M) break;
+          float v = stage_out[i * TC_EPI_PITCH + lane];
+          if (!cin) continue;
+          if (partial) {
+            partial[((size_t)z * Mo + rr) * No + col] = v;
+            continue;
+          }
+          const size_t o = (size_t)rr * ldc + col;
+          if (beta != 0.f) v += beta * C[o];
+          v += bv;
+          if (relu) v = fmaxf(v, 0.f);
+          if (c_bf16) ((__nv_bfloat16*)C)[o] = __float2bfloat16_rn(v);
+          else C[o] = v;
+        }
+        __syncwarp();
       }
-      const size_t o = (size_t)rr * ldc + col;
-      if (beta != 0.f) v += beta * C[o];
-      v += bv;
-      if (relu) v = fmaxf(v, 0.f);
-      if (c_bf16) ((__nv_bfloat16*)C)[o] = __float2bfloat16_rn(v);
-      else C[o] = v;
+      // the accumulator may be overwritten by the next tile
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(&acc_empty[buf]))
+                     : "memory");
+      }
+      if (!ok) break;
     }
-    __syncwarp();
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
   }
 }
 
@@ -361,14 +399,15 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
   kchunk = (kchunk + TC_BK - 1) / TC_BK * TC_BK;
   splits = (K + kchunk - 1) / kchunk;
   float* partial = splits > 1 ? ws.partial : nullptr;
-  // pipeline depth: enough stages to cover the K loop, at most 4; shallow pipelines leave
-  // room for more CTAs per SM, whose epilogues then overlap other CTAs' loads
-  const int nkb = (kchunk + TC_BK - 1) / TC_BK;
-  const int stages = nkb >= 4 ? TC_STAGES : (nkb <= 2 ? 2 : 3);
-  dim3 grid(gm, gn, splits);
-  gemm_tc_kernel<BN><<<grid, TC_THREADS, tc_smem<BN>(stages), s>>>(
+  // persistent grid: one CTA per SM (a second where shared memory allows), each walking
+  // tiles with stride gridDim.x; the ring is deep enough to stream across tile boundaries
+  const int stages = BN == 64 ? 3 : TC_STAGES;  // BN = 64: two CTAs fit one SM
+  const int per_sm = tc_smem<BN>(stages) <= 110 * 1024 ? 2 : 1;
+  const int ntiles = gm * gn * splits;
+  const int grid = min(ntiles, ws.num_sms * per_sm);
+  gemm_tc_kernel<BN><<<grid, TC_PTHREADS, tc_smem<BN>(stages), s>>>(
       ma, mb, M, N, K, kchunk, (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu, trans,
-      partial, ws.err, a_mn, b_mn, stages);
+      partial, ws.err, a_mn, b_mn, stages, gm, gn, splits);
   DDPPO_CHECK_LAUNCH();
   if (partial)
     DDPPO_TRY(launch_splitk_reduce(d.M, d.N, splits, partial, (float*)d.C, d.ldc, d.c_bf16, d.beta,

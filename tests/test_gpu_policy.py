@@ -39,8 +39,9 @@ NETS = {
 }
 
 
-def _cfg(name, E, T, precision, mb=1):
+def _cfg(name, E, T, precision, mb=1, **kw):
     d = dict(NETS[name])
+    d.update(kw)
     pre = d.pop("preset")
     return make_config(pre, num_envs=E, rollout_T=T, minibatches=mb, precision=precision, **d)
 
@@ -93,11 +94,14 @@ def _rel_close(a, b, rtol, name=""):
     return err
 
 
-@pytest.mark.parametrize("name,T,E", [("nature_small", 5, 3), ("resnet_small", 4, 5),
-                                      ("nature_full", 3, 4), ("resnet_full", 2, 3)])
+@pytest.mark.parametrize("name,T,E,chunk", [("nature_small", 5, 3, 0), ("resnet_small", 4, 5, 0),
+                                            ("nature_full", 3, 4, 0), ("resnet_full", 2, 3, 0),
+                                            ("resnet_small", 4, 5, 6), ("nature_small", 5, 3, 4)])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_evaluate_and_backward_parity(name, T, E, precision):
-    cfg = _cfg(name, E, T, precision)
+def test_evaluate_and_backward_parity(name, T, E, chunk, precision):
+    """chunk > 0 runs the encoder in chunks of that many frames (ragged last chunk); the
+    backward then recomputes every chunk but the last before back-propagating it."""
+    cfg = _cfg(name, E, T, precision, encoder_chunk=chunk)
     net = Net(cfg, seed=1)
     try:
         mb = I.minibatch(net.ncfg, T=T, E=E, seed=2)
