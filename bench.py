@@ -105,6 +105,7 @@ def run_gpu(args):
     import torch.distributed as dist
 
     from paper_1911_00357_gb300 import binding as B
+    from paper_1911_00357_gb300.dist import aggregate
     from paper_1911_00357_gb300.worker import Worker
 
     rank, world, local = _dist()
@@ -137,18 +138,15 @@ def run_gpu(args):
         torch.cuda.synchronize()
         clocks = clk.stop() if clk else None
         ms = e0.elapsed_time(e1)
-        t = torch.tensor([ms], device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
         gemm = B.ddppo_timing_read(w.h, 0) if timing else None
         tc = B.ddppo_timing_read(w.h, 2) if timing else None
+        per_launch = B.ddppo_timing_launches(w.h, 0) if timing else None
         if timing:
             B.ddppo_timing_enable(w.h, False)
-        return w, t.item(), clocks, gemm, tc
+        return w, ms, clocks, gemm, tc, per_launch
 
-    w, ms, clocks, gemm, tc = measure(precision, args.steps, args.warmup, True)
-    frames = w.E * w.T * args.steps * world
-    value = frames / (ms / 1e3)
+    w, ms_local, clocks, gemm, tc, per_launch = measure(precision, args.steps, args.warmup, True)
+    value, ms, frames = aggregate(w.E * w.T * args.steps, ms_local, torch.device("cuda"))
     if args.profile:
         if rank == 0:
             print(json.dumps({"profile_run": True, "ms_per_step": ms / args.steps}), flush=True)
@@ -158,27 +156,37 @@ def run_gpu(args):
     # end to end through the public API: uniforms H2D from pinned memory each step,
     # statistics and rewards D2H each step
     e2e_ms, h2d, d2h = w.time_e2e(args.steps)
-    t = torch.tensor([e2e_ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    e2e_value = frames / (t.item() / 1e3)
+    e2e_value, _, _ = aggregate(w.E * w.T * args.steps, e2e_ms, torch.device("cuda"))
 
     # plain FP32 form on the same GPU (the metric's denominator)
     fp32_value = None
     if not args.skip_fp32 and precision == 1:
-        w32, ms32, _, _, _ = measure(0, max(1, args.steps // 2), max(3, args.warmup // 2), False)
-        fp32_value = w32.E * w32.T * max(1, args.steps // 2) * world / (ms32 / 1e3)
-        del w32
+        k32 = max(1, args.steps // 2)
+        w32, ms32, _, _, _, _ = measure(0, k32, max(3, args.warmup // 2), False)
+        fp32_value, _, _ = aggregate(w32.E * w32.T * k32, ms32, torch.device("cuda"))
+        w32.close()
 
     peaks, pk_kind = _peaks()
     g_ms, g_n, g_flops = gemm
-    achieved = g_flops / (g_ms / 1e3) / 1e12 if g_ms > 0 else 0.0
     tc_flops_share = (tc[2] / tc[0]) if tc[0] > 0 else 0.0
     if precision == 1 and tc[1] > 0:
-        bound, peak_v, unit = "tensor", peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]), "TFLOP/s"
+        compute, cunit = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]), "tensor"
     else:
         # SIMT FMA path: 152 SMs x 128 FP32 lanes x 2 FLOP x max SM clock
-        bound, peak_v, unit = "alu", 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, "TFLOP/s"
+        compute, cunit = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12, "alu"
+    hbm = peaks["hbm_gbs"]
+    # each launch's own roofline time: max(FLOP / compute peak, bytes / HBM peak)
+    l_ms, l_fl, l_by = per_launch
+    t_act = sum(l_ms) / 1e3
+    t_c = sum(f / (compute * 1e12) for f, b in zip(l_fl, l_by) if f / (compute * 1e12) >= b / (hbm * 1e9))
+    t_m = sum(b / (hbm * 1e9) for f, b in zip(l_fl, l_by) if f / (compute * 1e12) < b / (hbm * 1e9))
+    mixed_frac = (t_c + t_m) / t_act if t_act > 0 else None
+    if t_m >= t_c:
+        bound, unit, peak_v = "hbm", "GB/s", hbm
+        achieved = sum(l_by) / t_act / 1e9 if t_act > 0 else 0.0
+    else:
+        bound, unit, peak_v = cunit, "TFLOP/s", compute
+        achieved = sum(l_fl) / t_act / 1e12 if t_act > 0 else 0.0
     r_ms, r_n, r_bytes = rc
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
@@ -199,7 +207,10 @@ def run_gpu(args):
                      "achieved": round(achieved, 3), "peak": round(peak_v, 1), "unit": unit,
                      "frac": round(achieved / peak_v, 4) if peak_v else None,
                      "peak_kind": pk_kind, "launches": g_n, "avg_launch_us": round(1e3 * g_ms / max(g_n, 1), 2),
-                     "tcgen05_flop_share": round(tc_flops_share, 4), "traffic": None},
+                     "tcgen05_flop_share": round(tc_flops_share, 4),
+                     "achieved_tflops": round(g_flops / (g_ms / 1e3) / 1e12, 2) if g_ms > 0 else None,
+                     "frac_of_per_launch_roofline": round(mixed_frac, 4) if mixed_frac else None,
+                     "traffic": None},
         "raycast": {"launches": r_n, "avg_launch_us": round(1e3 * r_ms / max(r_n, 1), 2),
                 "kernel": "env_step render (TMA-staged DDA ray cast, 64 x 256x256 -> 128x128 bf16)",
                     "out_GBps": round(r_bytes / (r_ms / 1e3) / 1e9, 2) if r_ms > 0 else None},

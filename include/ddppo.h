@@ -322,6 +322,14 @@ int ddppo_timing_read(ddppo_ctx* ctx, int32_t family, double* ms, int64_t* launc
 /* family 2 reports the launches and FLOPs of the contractions that ran on the tcgen05
  * tensor-core GEMM; its `ms` slot carries the FLOPs of all contractions while enabled. */
 
+/* Per-launch records of the timed launches of a family since ddppo_timing_enable: event
+ * time ms[i], work[i] (FLOPs for family 0, output bytes for 1) and the algorithmic HBM
+ * bytes[i] (operands read once, result written once). Arrays [host] of cap entries (any
+ * may be NULL); count [host] receives the number of records (at most 4096 per family).
+ * Synchronises on the recorded events. */
+int ddppo_timing_launches(ddppo_ctx* ctx, int32_t family, double* ms, double* work, double* bytes,
+                          int64_t cap, int64_t* count);
+
 /* Number of kernel launches of one steady-state iteration (collect of T steps, bootstrap
  * value, GAE, PPO update) with this rollout and hyper-parameters: the iteration is
  * captured into a CUDA graph that is counted and discarded, nothing executes. Needs a

@@ -107,6 +107,7 @@ _SIGS = {
     "ddppo_count_kernels": [P, P, P, F32, F32, P],
     "ddppo_gemm": [I32, I32, I32, I32, P, I32, I32, P, I32, I32, P, I32, I32, F32, P, I32, P, P],
     "ddppo_gemm_backend": [I32, I32, I32, I32, P, I32, P, I32, P],
+    "ddppo_timing_launches": [P, I32, P, P, P, I64, P],
 }
 
 
@@ -305,3 +306,15 @@ def ddppo_gemm_backend(A, B) -> bool:
                                     ctypes.c_void_p(A.data_ptr()), A.stride(0),
                                     ctypes.c_void_p(B.data_ptr()), B.stride(0), ctypes.byref(t)))
     return bool(t.value)
+
+
+def ddppo_timing_launches(h, family: int):
+    """Per-launch (ms, work, bytes) lists of the timed launches of a kernel family."""
+    n = ctypes.c_int64()
+    _check(lib().ddppo_timing_launches(h, family, None, None, None, 0, ctypes.byref(n)))
+    cap = n.value
+    ms = (ctypes.c_double * max(cap, 1))()
+    wk = (ctypes.c_double * max(cap, 1))()
+    by = (ctypes.c_double * max(cap, 1))()
+    _check(lib().ddppo_timing_launches(h, family, ms, wk, by, cap, ctypes.byref(n)))
+    return list(ms)[:cap], list(wk)[:cap], list(by)[:cap]

@@ -114,7 +114,7 @@ static int dmalloc(T** p, size_t n) {
 namespace ddppo {
 void ctx_free_world(ddppo_ctx* x) {
   cudaFree(x->sb.grids); cudaFree(x->sb.bits); cudaFree(x->sb.dists); cudaFree(x->sb.states);
-  cudaFree(x->sb.segs); cudaFree(x->sb.need); cudaFree(x->sb.err);
+  cudaFree(x->sb.segs); cudaFree(x->sb.need); cudaFree(x->sb.err); cudaFree(x->sb.work);
 }
 }  // namespace ddppo
 
@@ -137,6 +137,13 @@ extern "C" int ddppo_create(const ddppo_config* cfg, ddppo_ctx** out) {
     if ((rc = dmalloc(&x->sb.segs, E * (size_t)x->sp.max_segs)) != DDPPO_OK) break;
     if ((rc = dmalloc(&x->sb.need, E)) != DDPPO_OK) break;
     if ((rc = dmalloc(&x->sb.err, 1)) != DDPPO_OK) break;
+    if ((rc = dmalloc(&x->sb.work, 2)) != DDPPO_OK) break;
+    if (cudaMemset(x->sb.work, 0, 2 * sizeof(int32_t)) != cudaSuccess) { set_error("cudaMemset failed"); rc = DDPPO_E_CUDA; break; }
+    {
+      int nsm = 152;
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, x->device);
+      x->env_grid = env_step_grid(x->sp, nsm);
+    }
     if (cudaMemset(x->sb.err, 0, sizeof(int32_t)) != cudaSuccess ||
         cudaMemset(x->sb.need, 0, E) != cudaSuccess ||
         cudaMemset(x->sb.states, 0, E * ST_N * sizeof(int32_t)) != cudaSuccess) {
@@ -193,19 +200,20 @@ extern "C" int ddppo_env_step(ddppo_ctx* x, const int32_t* actions, void* obs, f
   ARG_CHECK(x && actions && obs && goal && reward && done, "env_step: null argument");
   if (!x->env_ready) { set_error("env_step before env_reset"); return DDPPO_E_STATE; }
   cudaStream_t s = (cudaStream_t)stream;
-  DDPPO_TRY(launch_step(x->sp, x->sb, actions, reward, done, info, s));
-  DDPPO_TRY(launch_reset(x->sp, x->sb, false, s));
   KernelTimer* t = x->net ? &x->net->rc_timer : nullptr;
   const bool rec = t && t->on && t->n + 2 <= 2 * 4096;
   if (rec) cudaEventRecord(t->ev[t->n], s);
-  DDPPO_TRY(launch_render(x->sp, x->sb, obs, goal, nullptr, s));
+  DDPPO_TRY(launch_env_step(x->sp, x->sb, x->env_grid, actions, obs, goal, reward, done, info, s));
   if (rec) {
     cudaEventRecord(t->ev[t->n + 1], s);
+    // algorithmic bytes: the encoder input written plus the goal vectors
+    const double out = (double)x->cfg.num_envs *
+                       ((double)x->sp.obs_h * x->sp.obs_w * (x->sp.bf16_obs ? 2 : 4) + 12.0);
+    t->work[t->n / 2] = out;
+    t->bytes[t->n / 2] = out;
     t->n += 2;
     t->launches += 1;
-    // algorithmic bytes: the encoder input written plus the goal vectors
-    t->flops += (double)x->cfg.num_envs *
-                ((double)x->sp.obs_h * x->sp.obs_w * (x->sp.bf16_obs ? 2 : 4) + 12.0);
+    t->flops += out;
   }
   return DDPPO_OK;
 }

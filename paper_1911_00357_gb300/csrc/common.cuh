@@ -63,6 +63,7 @@ struct SimBuffers {
   int4* segs;         // [E, max_segs] room walls (gen_kind 1)
   uint8_t* need;      // [E] reset request
   int32_t* err;       // [1] sticky
+  int32_t* work;      // [2] persistent env-step work counter, CTAs finished (self re-arming)
 };
 
 // host-side launchers (sim.cu)
@@ -73,6 +74,11 @@ int launch_step(const SimParams& p, const SimBuffers& b, const int32_t* actions,
                 uint8_t* done, float* info, cudaStream_t s);
 int launch_render(const SimParams& p, const SimBuffers& b, void* obs, float* goal, float* depth_raw,
                   cudaStream_t s);
+// fused persistent step + auto-reset + render over all envs
+int launch_env_step(const SimParams& p, const SimBuffers& b, int grid, const int32_t* actions,
+                    void* obs, float* goal, float* reward, uint8_t* done, float* info,
+                    cudaStream_t s);
+int env_step_grid(const SimParams& p, int num_sms);
 
 // rl.cu
 int launch_gae(const float* r, const uint8_t* d, const float* v, int T, int E, float gamma,

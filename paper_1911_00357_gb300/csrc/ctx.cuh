@@ -17,5 +17,6 @@ struct ddppo_ctx {
   ddppo::SimBuffers sb{};
   int device = 0;
   bool env_ready = false;
+  int env_grid = 1;  // CTAs of the persistent env-step kernel
   ddppo::Net* net = nullptr;
 };

@@ -163,6 +163,11 @@ int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t 
   }
   if (rec) {
     cudaEventRecord(timer->ev[timer->n + 1], s);
+    const double es = op_bf16 ? 2.0 : 4.0, cs = d.c_bf16 ? 2.0 : 4.0;
+    timer->work[timer->n / 2] = 2.0 * d.M * d.N * d.K;
+    // operands read once, result written once (and read when accumulating)
+    timer->bytes[timer->n / 2] = ((double)d.M * d.K + (double)d.N * d.K) * es +
+                                 (double)d.M * d.N * cs * (d.beta != 0.f ? 2.0 : 1.0);
     timer->n += 2;
     timer->flops += 2.0 * d.M * d.N * d.K;
     timer->launches += 1;

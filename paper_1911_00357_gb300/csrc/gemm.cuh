@@ -45,6 +45,8 @@ struct KernelTimer {
   bool on = false;
   int n = 0;
   cudaEvent_t ev[2 * 4096];
+  double work[4096];       // per timed launch: FLOPs (GEMM) or output bytes (ray cast)
+  double bytes[4096];      // per timed launch: algorithmic HBM bytes
   double flops = 0.0;      // work of the launches that carry events
   int64_t launches = 0;
   double flops_all = 0.0;  // work of every launch while enabled

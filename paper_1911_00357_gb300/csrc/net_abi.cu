@@ -434,3 +434,21 @@ extern "C" int ddppo_gemm_backend(int32_t M, int32_t N, int32_t K, int32_t op_bf
   *tensor_cores = (op_bf16 && gemm_tc_supported(d)) ? 1 : 0;
   return DDPPO_OK;
 }
+
+extern "C" int ddppo_timing_launches(ddppo_ctx* x, int32_t family, double* ms, double* work,
+                                     double* bytes, int64_t cap, int64_t* count) {
+  ARG(x && x->net && count, "timing_launches: null argument");
+  ARG(family == 0 || family == 1, "timing_launches: family must be 0 or 1");
+  KernelTimer& t = family == 0 ? x->net->timer : x->net->rc_timer;
+  const int64_t n = t.n / 2;
+  *count = n;
+  for (int64_t i = 0; i < n && i < cap; ++i) {
+    float v = 0.f;
+    DDPPO_CHECK_CUDA(cudaEventSynchronize(t.ev[2 * i + 1]));
+    DDPPO_CHECK_CUDA(cudaEventElapsedTime(&v, t.ev[2 * i], t.ev[2 * i + 1]));
+    if (ms) ms[i] = v;
+    if (work) work[i] = t.work[i];
+    if (bytes) bytes[i] = t.bytes[i];
+  }
+  return DDPPO_OK;
+}

@@ -121,10 +121,61 @@ __global__ void im2col_vec_kernel(ConvGeom g, const Ti* __restrict__ x, To* __re
   }
 }
 
+// Single-channel input (the first convolution on the depth image): one thread per output
+// row, assembling 8 taps at a time into one 16-byte (bf16) or two (fp32) stores; adjacent
+// threads write adjacent rows, so a warp writes one contiguous stretch of the col matrix.
+template <typename Ti, typename To>
+__global__ void im2col_c1_kernel(ConvGeom g, const Ti* __restrict__ x, To* __restrict__ col) {
+  const size_t rows = (size_t)g.N * g.Ho * g.Wo;
+  for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < rows;
+       m += (size_t)gridDim.x * blockDim.x) {
+    const int ox = (int)(m % g.Wo), oy = (int)((m / g.Wo) % g.Ho), n = (int)(m / ((size_t)g.Wo * g.Ho));
+    const Ti* img = x + (size_t)n * g.H * g.W;
+    To* dst = col + m * g.Kp;
+    for (int k0 = 0; k0 < g.Kp; k0 += 8) {
+      float v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int kk = k0 + q;
+        float t = 0.f;
+        if (kk < g.K) {
+          const int ky = kk / g.k, kx = kk - ky * g.k;
+          const int iy = oy * g.s - g.p + ky, ix = ox * g.s - g.p + kx;
+          if (iy >= 0 && iy < g.H && ix >= 0 && ix < g.W) t = to_f(img[(size_t)iy * g.W + ix]);
+        }
+        v[q] = t;
+      }
+      if constexpr (sizeof(To) == 2) {
+        uint4 u;
+        __nv_bfloat16* h = (__nv_bfloat16*)&u;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) h[q] = __float2bfloat16_rn(v[q]);
+        *(uint4*)(dst + k0) = u;
+      } else {
+        *(float4*)(dst + k0) = make_float4(v[0], v[1], v[2], v[3]);
+        *(float4*)(dst + k0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
+      }
+    }
+  }
+}
+
 int launch_im2col(const ConvGeom& g, const void* x, bool x_bf16, void* col, bool op_bf16,
                   bool transposed, cudaStream_t s) {
   const size_t total = (size_t)g.N * g.Ho * g.Wo * g.Kp;
   if (total == 0) return DDPPO_OK;
+  if (!transposed && g.C == 1 && g.Kp % 8 == 0 && ((uintptr_t)col & 15) == 0) {
+    const unsigned gb = grid_for((size_t)g.N * g.Ho * g.Wo);
+    if (x_bf16 && op_bf16)
+      im2col_c1_kernel<__nv_bfloat16, __nv_bfloat16><<<gb, 256, 0, s>>>(g, (const __nv_bfloat16*)x, (__nv_bfloat16*)col);
+    else if (x_bf16)
+      im2col_c1_kernel<__nv_bfloat16, float><<<gb, 256, 0, s>>>(g, (const __nv_bfloat16*)x, (float*)col);
+    else if (op_bf16)
+      im2col_c1_kernel<float, __nv_bfloat16><<<gb, 256, 0, s>>>(g, (const float*)x, (__nv_bfloat16*)col);
+    else
+      im2col_c1_kernel<float, float><<<gb, 256, 0, s>>>(g, (const float*)x, (float*)col);
+    DDPPO_CHECK_LAUNCH();
+    return DDPPO_OK;
+  }
   const bool vec = !transposed && g.C % 8 == 0 && g.Kp == g.K && g.Kp % 8 == 0 &&
                    ((uintptr_t)x & 15) == 0 && ((uintptr_t)col & 15) == 0;
   const unsigned gb = grid_for(vec ? total / 8 : total);

@@ -186,11 +186,10 @@ size_t reset_smem_bytes(const SimParams& p) {
   return 4 * words * sizeof(uint32_t) + 256 * 4 * sizeof(int) + 32 * sizeof(int);
 }
 
-__global__ void __launch_bounds__(RESET_THREADS) reset_kernel(SimParams p, SimBuffers b, int all) {
-  const int e = blockIdx.x;
-  if (e >= p.E) return;
-  if (!all && !b.need[e]) return;
-  extern __shared__ __align__(16) uint32_t smem[];
+// Block-wide reset of env e (all = 1: episode 0, else the next episode). smem holds
+// reset_smem_bytes(p) bytes.
+__device__ void reset_env_block(const SimParams& p, const SimBuffers& b, int e, int all,
+                                uint32_t* smem) {
   const int WMAX = p.grid_max * p.grid_max / 32;
   uint32_t* Fw = smem;
   uint32_t* Vw = Fw + WMAX;
@@ -303,6 +302,14 @@ __global__ void __launch_bounds__(RESET_THREADS) reset_kernel(SimParams p, SimBu
   }
 }
 
+__global__ void __launch_bounds__(RESET_THREADS) reset_kernel(SimParams p, SimBuffers b, int all) {
+  const int e = blockIdx.x;
+  if (e >= p.E) return;
+  if (!all && !b.need[e]) return;
+  extern __shared__ __align__(16) uint32_t smem[];
+  reset_env_block(p, b, e, all, smem);
+}
+
 int launch_reset(const SimParams& p, const SimBuffers& b, bool all, cudaStream_t s) {
   reset_kernel<<<p.E, RESET_THREADS, reset_smem_bytes(p), s>>>(p, b, all ? 1 : 0);
   DDPPO_CHECK_LAUNCH();
@@ -345,11 +352,10 @@ __device__ bool segment_blocked(const uint8_t* grid, int g, int cs, int x0, int 
   return false;
 }
 
-__global__ void step_kernel(SimParams p, SimBuffers b, const int32_t* __restrict__ actions,
-                            float* __restrict__ reward, uint8_t* __restrict__ done,
-                            float* __restrict__ info) {
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= p.E) return;
+// one env step (thread-level); returns 1 when the episode ended
+__device__ int step_env(const SimParams& p, const SimBuffers& b, int e,
+                        const int32_t* __restrict__ actions, float* __restrict__ reward,
+                        uint8_t* __restrict__ done, float* __restrict__ info) {
   int32_t* st = b.states + (size_t)ST_N * e;
   const uint8_t* grid = b.grids + (size_t)p.grid_max * p.grid_max * e;
   const int32_t* dist = b.dists + (size_t)p.grid_max * p.grid_max * e;
@@ -398,6 +404,15 @@ __global__ void step_kernel(SimParams p, SimBuffers b, const int32_t* __restrict
     info[4 * e + 2] = (float)collided;
     info[4 * e + 3] = (float)steps;
   }
+  return finished;
+}
+
+__global__ void step_kernel(SimParams p, SimBuffers b, const int32_t* __restrict__ actions,
+                            float* __restrict__ reward, uint8_t* __restrict__ done,
+                            float* __restrict__ info) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= p.E) return;
+  step_env(p, b, e, actions, reward, done, info);
 }
 
 int launch_step(const SimParams& p, const SimBuffers& b, const int32_t* actions, float* reward,
@@ -413,22 +428,21 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__global__ void render_kernel(SimParams p, SimBuffers b, void* __restrict__ obs,
-                              float* __restrict__ goal, float* __restrict__ depth_raw) {
-  extern __shared__ __align__(128) uint32_t sbits[];
-  __shared__ __align__(8) uint64_t mbar;
-  const int e = blockIdx.x, i = threadIdx.x;
+// Render env e with the whole block: TMA bulk copy of the bit-packed grid into smem (the
+// mbarrier `bar` completes phase `phase`), then one column ray per thread (looping when
+// the image is wider than the block), depth against the analytic planes, the optional
+// 2x2 pool, normalisation and cast; thread 0 writes the goal vector.
+__device__ void render_env_block(const SimParams& p, const SimBuffers& b, int e,
+                                 void* __restrict__ obs, float* __restrict__ goal,
+                                 float* __restrict__ depth_raw, uint32_t* sbits, uint64_t* mbar,
+                                 uint32_t phase) {
+  const int tid = threadIdx.x;
   const int32_t* st = b.states + (size_t)ST_N * e;
   const int g = st[ST_GRID];
   const int WMAX = p.grid_max * p.grid_max / 32;
   const uint32_t bytes = (uint32_t)(g * g / 8);
-  const uint32_t bar = smem_u32(&mbar);
-  if (i == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  if (i == 0) {
+  const uint32_t bar = smem_u32(mbar);
+  if (tid == 0) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                  : "memory");
     asm volatile(
@@ -437,42 +451,24 @@ __global__ void render_kernel(SimParams p, SimBuffers b, void* __restrict__ obs,
         "l"(b.bits + (size_t)WMAX * e), "r"(bytes), "r"(bar)
         : "memory");
   }
-  // bounded wait on phase 0 of the barrier
   uint32_t ok = 0;
   for (int it = 0; it < (1 << 24) && !ok; ++it) {
     asm volatile(
         "{\n\t.reg .pred P1;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], 0;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
         "selp.b32 %0, 1, 0, P1;\n\t}"
         : "=r"(ok)
-        : "r"(bar)
+        : "r"(bar), "r"(phase)
         : "memory");
   }
   if (!ok) set_err(b.err, ERRF_TIMEOUT);  // keep going: every later access stays in bounds
-
   const int cs = p.cell_u;
   const int k = st[ST_HEAD];
   const float c = c_cos[k], s = c_sin[k];
   const float px = (float)st[ST_X], py = (float)st[ST_Y];
-  // column ray: forward + x_i * right, right = (sin, -cos)
-  const float xi = (float)(2 * i + 1) / (float)p.W - 1.0f;
-  const float dx = c + xi * s, dy = s - xi * c;
-  int cx = st[ST_X] / cs, cy = st[ST_Y] / cs;
-  const int sx = dx > 0.f ? 1 : (dx < 0.f ? -1 : 0);
-  const int sy = dy > 0.f ? 1 : (dy < 0.f ? -1 : 0);
-  float t = INFINITY;
   const int R = g >> 5;
-  for (int it = 0; it < 8 * g + 8; ++it) {
-    const float tx = sx ? ((float)((cx + (sx > 0)) * cs) - px) / dx : INFINITY;
-    const float ty = sy ? ((float)((cy + (sy > 0)) * cs) - py) / dy : INFINITY;
-    float tc;
-    if (tx <= ty) { cx += sx; tc = tx; } else { cy += sy; tc = ty; }
-    if (cx < 0 || cy < 0 || cx >= g || cy >= g) break;
-    if ((sbits[cy * R + (cx >> 5)] >> (cx & 31)) & 1u) { t = tc; break; }
-  }
-  const float tw = t * 1e-4f;  // metres
   const float up = p.ceil_h - p.cam_h, H = (float)p.H;
-  if (i == 0 && goal) {
+  if (tid == 0 && goal) {
     const float gx = (float)(st[ST_GOAL_X] - st[ST_X]) * 1e-4f;
     const float gy = (float)(st[ST_GOAL_Y] - st[ST_Y]) * 1e-4f;
     const float f = gx * c + gy * s, l = -gx * s + gy * c;
@@ -483,39 +479,127 @@ __global__ void render_kernel(SimParams p, SimBuffers b, void* __restrict__ obs,
   }
   float* raw = depth_raw ? depth_raw + (size_t)e * p.H * p.W : nullptr;
   const float inv_max = 1.0f / p.max_depth;
-  for (int j = 0; j < p.H; j += 2) {
-    float d2[2];
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-      const float yj = 1.0f - (float)(2 * (j + q) + 1) / H;
-      const float tp = yj > 0.f ? up / yj : p.cam_h / (-yj);
-      float d = fminf(tw, tp);
-      d = fminf(d, p.max_depth);
-      d = fmaxf(d, 0.0f);
-      d2[q] = d;
-      if (raw) raw[(size_t)(j + q) * p.W + i] = d;
+  for (int i = tid; i < p.W; i += blockDim.x) {
+    // column ray: forward + x_i * right, right = (sin, -cos)
+    const float xi = (float)(2 * i + 1) / (float)p.W - 1.0f;
+    const float dx = c + xi * s, dy = s - xi * c;
+    int cx = st[ST_X] / cs, cy = st[ST_Y] / cs;
+    const int sx = dx > 0.f ? 1 : (dx < 0.f ? -1 : 0);
+    const int sy = dy > 0.f ? 1 : (dy < 0.f ? -1 : 0);
+    float t = INFINITY;
+    for (int it = 0; it < 8 * g + 8; ++it) {
+      const float tx = sx ? ((float)((cx + (sx > 0)) * cs) - px) / dx : INFINITY;
+      const float ty = sy ? ((float)((cy + (sy > 0)) * cs) - py) / dy : INFINITY;
+      float tc;
+      if (tx <= ty) { cx += sx; tc = tx; } else { cy += sy; tc = ty; }
+      if (cx < 0 || cy < 0 || cx >= g || cy >= g) break;
+      if ((sbits[cy * R + (cx >> 5)] >> (cx & 31)) & 1u) { t = tc; break; }
     }
-    if (obs) {
-      if (p.pool) {
-        const float sum = d2[0] + d2[1];
-        const float other = __shfl_xor_sync(0xffffffffu, sum, 1);
-        if ((i & 1) == 0) {
-          const float v = (sum + other) * 0.25f * inv_max;
-          const size_t o = ((size_t)e * p.obs_h + (j >> 1)) * p.obs_w + (i >> 1);
-          if (p.bf16_obs) ((__nv_bfloat16*)obs)[o] = __float2bfloat16_rn(v);
-          else ((float*)obs)[o] = v;
-        }
-      } else {
+    const float tw = t * 1e-4f;  // metres
+    for (int j = 0; j < p.H; j += 2) {
+      float d2[2];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const size_t o = ((size_t)e * p.obs_h + j + q) * p.obs_w + i;
-          const float v = d2[q] * inv_max;
-          if (p.bf16_obs) ((__nv_bfloat16*)obs)[o] = __float2bfloat16_rn(v);
-          else ((float*)obs)[o] = v;
+      for (int q = 0; q < 2; ++q) {
+        const float yj = 1.0f - (float)(2 * (j + q) + 1) / H;
+        const float tp = yj > 0.f ? up / yj : p.cam_h / (-yj);
+        float d = fminf(tw, tp);
+        d = fminf(d, p.max_depth);
+        d = fmaxf(d, 0.0f);
+        d2[q] = d;
+        if (raw) raw[(size_t)(j + q) * p.W + i] = d;
+      }
+      if (obs) {
+        if (p.pool) {
+          const float sum = d2[0] + d2[1];
+          const float other = __shfl_xor_sync(0xffffffffu, sum, 1);
+          if ((i & 1) == 0) {
+            const float v = (sum + other) * 0.25f * inv_max;
+            const size_t o = ((size_t)e * p.obs_h + (j >> 1)) * p.obs_w + (i >> 1);
+            if (p.bf16_obs) ((__nv_bfloat16*)obs)[o] = __float2bfloat16_rn(v);
+            else ((float*)obs)[o] = v;
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const size_t o = ((size_t)e * p.obs_h + j + q) * p.obs_w + i;
+            const float v = d2[q] * inv_max;
+            if (p.bf16_obs) ((__nv_bfloat16*)obs)[o] = __float2bfloat16_rn(v);
+            else ((float*)obs)[o] = v;
+          }
         }
       }
     }
   }
+}
+
+__global__ void render_kernel(SimParams p, SimBuffers b, void* __restrict__ obs,
+                              float* __restrict__ goal, float* __restrict__ depth_raw) {
+  extern __shared__ __align__(128) uint32_t sbits[];
+  __shared__ __align__(8) uint64_t mbar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  render_env_block(p, b, blockIdx.x, obs, goal, depth_raw, sbits, &mbar, 0);
+}
+
+// One persistent launch for the whole env step: CTAs take envs from an atomic work
+// counter (so a CTA stuck on an expensive reset -- a BFS over a 512x512 grid -- does not
+// hold up the others), and per env do: step (thread 0); if the episode ended, the
+// block-wide reset of the next episode; the TMA-staged render of the new frame. The last
+// CTA to finish re-arms the counter for the next launch (graph replays included).
+__global__ void __launch_bounds__(RESET_THREADS)
+    env_step_persistent_kernel(SimParams p, SimBuffers b, const int32_t* __restrict__ actions,
+                               void* __restrict__ obs, float* __restrict__ goal,
+                               float* __restrict__ reward, uint8_t* __restrict__ done,
+                               float* __restrict__ info) {
+  extern __shared__ __align__(128) uint32_t smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ int s_env, s_fin;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  uint32_t phase = 0;
+  for (int guard = 0; guard <= p.E; ++guard) {
+    if (tid == 0) s_env = atomicAdd(&b.work[0], 1);
+    __syncthreads();
+    const int e = s_env;
+    if (e >= p.E) break;
+    if (tid == 0) s_fin = step_env(p, b, e, actions, reward, done, info);
+    __syncthreads();
+    if (s_fin) {
+      reset_env_block(p, b, e, 0, smem);
+      // the new wall bits were written through the generic proxy; the TMA copy that
+      // reads them next goes through the async proxy
+      asm volatile("fence.proxy.async.global;" ::: "memory");
+    }
+    __syncthreads();
+    render_env_block(p, b, e, obs, goal, nullptr, smem, &mbar, phase);
+    phase ^= 1u;
+    __syncthreads();  // smem is reused by the next env
+  }
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&b.work[1], 1) == (int)gridDim.x - 1) {
+      b.work[0] = 0;
+      b.work[1] = 0;
+      __threadfence();
+    }
+  }
+}
+
+int launch_env_step(const SimParams& p, const SimBuffers& b, int grid, const int32_t* actions,
+                    void* obs, float* goal, float* reward, uint8_t* done, float* info,
+                    cudaStream_t s) {
+  const size_t smem = max(reset_smem_bytes(p), (size_t)p.grid_max * p.grid_max / 8);
+  env_step_persistent_kernel<<<grid, RESET_THREADS, smem, s>>>(p, b, actions, obs, goal, reward,
+                                                               done, info);
+  DDPPO_CHECK_LAUNCH();
+  return DDPPO_OK;
 }
 
 int launch_render(const SimParams& p, const SimBuffers& b, void* obs, float* goal, float* depth_raw,
@@ -536,6 +620,20 @@ int sim_configure(const SimParams& p) {
   const size_t gs = (size_t)p.grid_max * p.grid_max / 8;
   DDPPO_CHECK_CUDA(cudaFuncSetAttribute(render_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)gs));
+  const size_t ps = rs > gs ? rs : gs;
+  DDPPO_CHECK_CUDA(cudaFuncSetAttribute(env_step_persistent_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps));
   return DDPPO_OK;
+}
+
+int env_step_grid(const SimParams& p, int num_sms) {
+  const size_t rs = reset_smem_bytes(p), gs = (size_t)p.grid_max * p.grid_max / 8;
+  int per_sm = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, env_step_persistent_kernel,
+                                                    RESET_THREADS, rs > gs ? rs : gs) !=
+          cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  const int g = per_sm * num_sms;
+  return g < p.E ? g : p.E;
 }
 }  // namespace ddppo
