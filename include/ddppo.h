@@ -312,6 +312,13 @@ int ddppo_gemm(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const void* A, 
 int ddppo_gemm_backend(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const void* A,
                        int32_t lda, const void* B, int32_t ldb, int32_t* tensor_cores);
 
+/* Tile-shape autotuner of the tensor-core GEMM (precision 1): on by default. The first
+ * time a contraction shape is seen outside a stream capture, each candidate (N tile 64 or
+ * 128, ring depth 2-4, split-K or not) runs on a scratch output and the fastest is kept;
+ * ddppo_collect runs one act step outside its capture for this. on = 0 freezes the table
+ * (new shapes use the fixed heuristic). tuned_shapes [host] (NULL ok): table size. */
+int ddppo_autotune(ddppo_ctx* ctx, int32_t on, int64_t* tuned_shapes);
+
 /* Per-kernel-family timing of the calls enqueued while enabled (CUDA events on
  * the launching stream). ddppo_timing_enable(ctx, 1) starts recording and
  * clears the counters; ddppo_timing_read synchronises and returns, for family

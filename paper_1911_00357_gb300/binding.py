@@ -108,6 +108,7 @@ _SIGS = {
     "ddppo_gemm": [I32, I32, I32, I32, P, I32, I32, P, I32, I32, P, I32, I32, F32, P, I32, P, P],
     "ddppo_gemm_backend": [I32, I32, I32, I32, P, I32, P, I32, P],
     "ddppo_timing_launches": [P, I32, P, P, P, I64, P],
+    "ddppo_autotune": [P, I32, P],
 }
 
 
@@ -318,3 +319,9 @@ def ddppo_timing_launches(h, family: int):
     by = (ctypes.c_double * max(cap, 1))()
     _check(lib().ddppo_timing_launches(h, family, ms, wk, by, cap, ctypes.byref(n)))
     return list(ms)[:cap], list(wk)[:cap], list(by)[:cap]
+
+
+def ddppo_autotune(h, on: bool = True) -> int:
+    n = ctypes.c_int64()
+    _check(lib().ddppo_autotune(h, 1 if on else 0, ctypes.byref(n)))
+    return n.value

@@ -32,12 +32,22 @@ struct GemmTcCount {
   double flops = 0.0;
 };
 
+// Tile-shape autotuner of the tcgen05 GEMM: the first time a contraction shape is seen
+// (outside stream capture), every candidate configuration runs into a scratch output and
+// the fastest is kept for the life of the worker.
+struct TcTuner;
+TcTuner* tc_tuner_create(size_t scratch_bytes);
+void tc_tuner_destroy(TcTuner* t);
+void tc_tuner_enable(TcTuner* t, bool on);
+int64_t tc_tuner_shapes(const TcTuner* t);
+
 struct GemmWorkspace {
   float* partial = nullptr;  // split-K partial sums
   size_t partial_elems = 0;
   int num_sms = 152;
   GemmTcCount* tc = nullptr;  // counts contractions routed to tcgen05 while enabled
   int32_t* err = nullptr;      // sticky device status word (timeout flag)
+  TcTuner* tuner = nullptr;    // tile-shape autotuner (null: fixed heuristic)
 };
 
 // timing of GEMM launches (family 0 of ddppo_timing_read)

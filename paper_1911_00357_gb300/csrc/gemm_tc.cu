@@ -17,7 +17,11 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <chrono>
+#include <map>
 #include <mutex>
+#include <tuple>
+#include <vector>
 
 #include "gemm.cuh"
 
@@ -372,10 +376,53 @@ bool gemm_tc_supported(const GemmDesc& d) {
   return true;
 }
 
+struct TcCfg {
+  int bn = 64;       // N tile: 64 or 128
+  int stages = 3;    // shared-memory ring depth: 2..4
+  int split = 0;     // 0: split K when the grid would be short of SMs; 1: never split
+};
+
+struct TcTuner {
+  bool on = true;
+  std::map<std::tuple<int, int, int, int, int, int, int>, TcCfg> table;
+  void* scratch = nullptr;  // trial output
+  size_t scratch_bytes = 0;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+};
+
+TcTuner* tc_tuner_create(size_t scratch_bytes) {
+  TcTuner* t = new TcTuner();
+  if (cudaMalloc(&t->scratch, scratch_bytes) != cudaSuccess) {
+    t->scratch = nullptr;
+    scratch_bytes = 0;
+  }
+  t->scratch_bytes = scratch_bytes;
+  cudaEventCreate(&t->e0);
+  cudaEventCreate(&t->e1);
+  return t;
+}
+void tc_tuner_destroy(TcTuner* t) {
+  if (!t) return;
+  if (t->scratch) cudaFree(t->scratch);
+  if (t->e0) cudaEventDestroy(t->e0);
+  if (t->e1) cudaEventDestroy(t->e1);
+  delete t;
+}
+void tc_tuner_enable(TcTuner* t, bool on) { if (t) t->on = on; }
+int64_t tc_tuner_shapes(const TcTuner* t) { return t ? (int64_t)t->table.size() : 0; }
+
+static TcCfg default_cfg(int N) {
+  TcCfg c;
+  c.bn = N > 64 ? 128 : 64;
+  c.stages = c.bn == 64 ? 3 : TC_STAGES;  // BN = 64: two CTAs fit one SM
+  c.split = 0;
+  return c;
+}
+
 template <int BN>
 static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int K,
                      const GemmDesc& d, int trans, int a_mn, int b_mn, const GemmWorkspace& ws,
-                     cudaStream_t s) {
+                     const TcCfg& cfg, cudaStream_t s) {
   static bool attr_done[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -389,7 +436,7 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
   const int tiles = gm * gn;
   int splits = 1;
   const int target = ws.num_sms;
-  if (tiles < target && K >= 8 * TC_BK) {
+  if (cfg.split == 0 && tiles < target && K >= 8 * TC_BK) {
     splits = min((target + tiles - 1) / tiles, K / (4 * TC_BK));
     const size_t per = (size_t)M * N;
     splits = (int)min((size_t)splits, ws.partial_elems / max(per, (size_t)1));
@@ -399,9 +446,9 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
   kchunk = (kchunk + TC_BK - 1) / TC_BK * TC_BK;
   splits = (K + kchunk - 1) / kchunk;
   float* partial = splits > 1 ? ws.partial : nullptr;
-  // persistent grid: one CTA per SM (a second where shared memory allows), each walking
-  // tiles with stride gridDim.x; the ring is deep enough to stream across tile boundaries
-  const int stages = BN == 64 ? 3 : TC_STAGES;  // BN = 64: two CTAs fit one SM
+  // persistent grid: one CTA per SM (two where shared memory allows), each walking tiles
+  // with stride gridDim.x; the ring streams across tile boundaries
+  const int stages = cfg.stages;
   const int per_sm = tc_smem<BN>(stages) <= 110 * 1024 ? 2 : 1;
   const int ntiles = gm * gn * splits;
   const int grid = min(ntiles, ws.num_sms * per_sm);
@@ -415,7 +462,7 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
   return DDPPO_OK;
 }
 
-int gemm_tc(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s) {
+static int run_cfg(const GemmDesc& d, const GemmWorkspace& ws, const TcCfg& cfg, cudaStream_t s) {
   // swap A and B when M is small: the MMA's 128-row side then covers N
   const bool swap = d.M < TC_BM && d.N > d.M;
   const void* A = swap ? d.B : d.A;
@@ -423,7 +470,7 @@ int gemm_tc(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s) {
   const int lda = swap ? d.ldb : d.lda, ldb = swap ? d.lda : d.ldb;
   const int a_mn = swap ? d.b_t : d.a_t, b_mn = swap ? d.a_t : d.b_t;
   const int M = swap ? d.N : d.M, N = swap ? d.M : d.N;
-  const int BN = N > 64 ? 128 : 64;
+  const int BN = cfg.bn;
   CUtensorMap ma, mb;
   // K-major operand: [rows = M|N, cols = K] boxes of 128|BN rows x 64 K;
   // MN-major operand: [rows = K, cols = M|N] boxes of 64 K rows x 64 columns
@@ -433,8 +480,64 @@ int gemm_tc(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s) {
     set_error("gemm_tc: tensor map encoding failed");
     return DDPPO_E_CUDA;
   }
-  if (BN == 128) return launch_tc<128>(ma, mb, M, N, d.K, d, swap ? 1 : 0, a_mn, b_mn, ws, s);
-  return launch_tc<64>(ma, mb, M, N, d.K, d, swap ? 1 : 0, a_mn, b_mn, ws, s);
+  if (BN == 128) return launch_tc<128>(ma, mb, M, N, d.K, d, swap ? 1 : 0, a_mn, b_mn, ws, cfg, s);
+  return launch_tc<64>(ma, mb, M, N, d.K, d, swap ? 1 : 0, a_mn, b_mn, ws, cfg, s);
+}
+
+// time every candidate on a scratch output (beta = 0, same operands); keep the fastest
+static TcCfg tune(const GemmDesc& d, const GemmWorkspace& ws, TcTuner& t, cudaStream_t s) {
+  const bool swap = d.M < TC_BM && d.N > d.M;
+  const int Nk = swap ? d.M : d.N;
+  std::vector<TcCfg> cands;
+  for (int bn : {64, 128}) {
+    if (bn == 128 && Nk <= 64) continue;
+    for (int st = 2; st <= 4; ++st)
+      for (int sp = 0; sp <= 1; ++sp) {
+        TcCfg c;
+        c.bn = bn; c.stages = st; c.split = sp;
+        cands.push_back(c);
+      }
+  }
+  GemmDesc trial = d;
+  trial.C = t.scratch;
+  trial.ldc = d.N;
+  trial.beta = 0.f;
+  TcCfg best = default_cfg(Nk);
+  float best_ms = 1e30f;
+  for (const TcCfg& c : cands) {
+    if (run_cfg(trial, ws, c, s) != DDPPO_OK) continue;  // warm-up
+    cudaEventRecord(t.e0, s);
+    for (int r = 0; r < 3; ++r) run_cfg(trial, ws, c, s);
+    cudaEventRecord(t.e1, s);
+    if (cudaEventSynchronize(t.e1) != cudaSuccess) continue;
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, t.e0, t.e1);
+    if (ms < best_ms) { best_ms = ms; best = c; }
+  }
+  return best;
+}
+
+int gemm_tc(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s) {
+  const bool swap = d.M < TC_BM && d.N > d.M;
+  TcCfg cfg = default_cfg(swap ? d.M : d.N);
+  TcTuner* t = ws.tuner;
+  if (t && t->on) {
+    const auto key = std::make_tuple(d.M, d.N, d.K, d.a_t * 2 + d.b_t, d.c_bf16,
+                                     d.beta != 0.f ? 1 : 0, d.lda * 8 + d.ldb);
+    auto it = t->table.find(key);
+    if (it != t->table.end()) {
+      cfg = it->second;
+    } else {
+      cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+      cudaStreamIsCapturing(s, &cs);
+      const size_t need = (size_t)d.M * d.N * (d.c_bf16 ? 2 : 4);
+      if (cs == cudaStreamCaptureStatusNone && t->scratch && need <= t->scratch_bytes) {
+        cfg = tune(d, ws, *t, s);
+        t->table[key] = cfg;
+      }
+    }
+  }
+  return run_cfg(d, ws, cfg, s);
 }
 
 }  // namespace ddppo

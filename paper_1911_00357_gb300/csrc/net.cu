@@ -342,6 +342,7 @@ int net_create(ddppo_ctx* x) {
   DDPPO_TRY(nalloc(n, &n.scratch, n.scratch_elems));
   n.gws.partial_elems = (size_t)32 << 20;
   DDPPO_TRY(nalloc(n, &n.gws.partial, n.gws.partial_elems));
+  if (n.bf) n.gws.tuner = tc_tuner_create((size_t)256 << 20);
   // minibatch
   const size_t NSmb = (size_t)n.T * n.Emb;
   DDPPO_TRY(nalloc_op(n, &n.obs_mb, NSmb * n.pix));
@@ -380,6 +381,7 @@ int net_create(ddppo_ctx* x) {
 void net_destroy(ddppo_ctx* x) {
   if (!x || !x->net) return;
   Net& n = *x->net;
+  tc_tuner_destroy(n.gws.tuner);
   for (void* p : n.allocs) cudaFree(p);
   if (n.graph_exec) cudaGraphExecDestroy(n.graph_exec);
   if (n.cap_stream) cudaStreamDestroy(n.cap_stream);

@@ -270,6 +270,13 @@ extern "C" int ddppo_collect(ddppo_ctx* x, const ddppo_rollout* ro, int32_t use_
   DDPPO_CHECK_CUDA(cudaMemcpyAsync(ro->c0, ro->c, st_bytes, cudaMemcpyDeviceToDevice, s));
   if (use_graph) {
     if (!n.graph_exec || memcmp(&n.graph_ro, ro, sizeof(*ro)) != 0) {
+      // one act step outside the capture (state into scratch buffers) so that the GEMM
+      // autotuner sees the act shapes before they are frozen into the graph
+      if (n.gws.tuner) {
+        DDPPO_TRY(net_forward(n, 1, E, ro->obs, ro->goal, ro->prev_a, ro->masks, ro->h, ro->c,
+                              ro->uniforms, (int32_t*)n.perm, n.dvalues, s));
+        n.ev_valid = false;
+      }
       if (n.graph_exec) { cudaGraphExecDestroy(n.graph_exec); n.graph_exec = nullptr; }
       DDPPO_CHECK_CUDA(cudaStreamSynchronize(s));
       const bool t0 = n.timer.on, t1 = n.rc_timer.on;
@@ -450,5 +457,12 @@ extern "C" int ddppo_timing_launches(ddppo_ctx* x, int32_t family, double* ms, d
     if (work) work[i] = t.work[i];
     if (bytes) bytes[i] = t.bytes[i];
   }
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_autotune(ddppo_ctx* x, int32_t on, int64_t* tuned_shapes) {
+  ARG(x && x->net, "autotune: null ctx");
+  tc_tuner_enable(x->net->gws.tuner, on != 0);
+  if (tuned_shapes) *tuned_shapes = tc_tuner_shapes(x->net->gws.tuner);
   return DDPPO_OK;
 }
