@@ -82,7 +82,8 @@ typedef struct {
   /* rollout / update shapes, used to size the workspace at creation */
   int32_t rollout_T;      /* T: frames per env per rollout (128)                             */
   int32_t minibatches;    /* PPO minibatches per epoch (E must divide evenly)                */
-  int32_t encoder_chunk;  /* max frames per encoder pass in the update (0: all at once)     */
+  int32_t encoder_chunk;  /* max frames per encoder pass in the update (0: min(all, 8192));
+                             larger minibatches run in chunks, recomputed for the backward */
   uint64_t seed;          /* seeds the world (counter hash) and the initial weights          */
 } ddppo_config;
 

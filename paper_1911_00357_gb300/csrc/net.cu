@@ -285,7 +285,9 @@ int net_create(ddppo_ctx* x) {
   n.T = c.rollout_T;
   n.Emb = c.num_envs / c.minibatches;
   n.NS = std::max(n.T * n.Emb, n.E);
-  n.NC = c.encoder_chunk > 0 ? std::min(c.encoder_chunk, n.NS) : n.NS;
+  // encoder pass size: the whole minibatch when it fits the automatic cap (8192 frames,
+  // ~30 GB of activations for the 32-base ResNet), else chunks with recomputation
+  n.NC = c.encoder_chunk > 0 ? std::min(c.encoder_chunk, n.NS) : std::min(n.NS, 8192);
   n.NC = std::max(n.NC, n.E);  // an act step always fits one chunk
   n.NC = std::min(n.NC, n.NS);
   Layout lay;

@@ -29,11 +29,10 @@ PRESETS = {
                        lstm_layers=2, rollout_T=128, minibatches=2, precision=1),
     "wide_256": dict(num_envs=256, gen_kind=1, grid_min=128, grid_max=128, cell_m=0.1,
                      depth_h=256, depth_w=256, pool2x2=1, net_kind=1, base_ch=64, hidden=512,
-                     lstm_layers=2, rollout_T=128, minibatches=2, precision=1),
+                     lstm_layers=2, rollout_T=128, minibatches=2, precision=1, encoder_chunk=4096),
     "scale_4096": dict(num_envs=4096, gen_kind=1, grid_min=128, grid_max=128, cell_m=0.1,
                        depth_h=256, depth_w=256, pool2x2=1, net_kind=1, base_ch=32, hidden=512,
-                       lstm_layers=2, rollout_T=128, minibatches=4, precision=1,
-                       encoder_chunk=8192),
+                       lstm_layers=2, rollout_T=128, minibatches=4, precision=1),
 }
 
 
