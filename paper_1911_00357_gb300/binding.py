@@ -109,6 +109,7 @@ _SIGS = {
     "ddppo_gemm_backend": [I32, I32, I32, I32, P, I32, P, I32, P],
     "ddppo_timing_launches": [P, I32, P, P, P, I64, P],
     "ddppo_autotune": [P, I32, P],
+    "ddppo_conv2d": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, P, P],
 }
 
 
@@ -325,3 +326,11 @@ def ddppo_autotune(h, on: bool = True) -> int:
     n = ctypes.c_int64()
     _check(lib().ddppo_autotune(h, 1 if on else 0, ctypes.byref(n)))
     return n.value
+
+
+def ddppo_conv2d(x, w, y, k: int, stride: int, pad: int, status=None):
+    """y = conv(x, w) on the implicit-im2col tensor-core path. x NHWC bf16 [N, H, W, C];
+    w bf16 [Cout, k*k*C] (K ordered ky, kx, c); y fp32 [N, Ho, Wo, Cout]."""
+    N, H, W, C = x.shape
+    _check(lib().ddppo_conv2d(N, H, W, C, w.shape[0], k, stride, pad, _p(x), _p(w), _p(y),
+                              _p(status), _s()))

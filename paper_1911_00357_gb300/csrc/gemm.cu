@@ -148,11 +148,15 @@ int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t 
     set_error("gemm: bf16 output cannot accumulate");
     return DDPPO_E_CONFIG;
   }
+  if (d.conv && !(op_bf16 && gemm_conv_supported(*d.conv, d.A))) {
+    set_error("gemm: implicit convolution not supported for this shape");
+    return DDPPO_E_CONFIG;
+  }
   const bool rec = timer && timer->on && timer->n + 2 <= 2 * 4096;
   if (timer && timer->on) timer->flops_all += 2.0 * d.M * d.N * d.K;
   if (rec) cudaEventRecord(timer->ev[timer->n], s);
   int rc;
-  if (op_bf16 && gemm_tc_supported(d)) {
+  if (op_bf16 && (d.conv || gemm_tc_supported(d))) {
     rc = gemm_tc(d, ws, s);
     if (ws.tc && ws.tc->on) {
       ws.tc->launches += 1;
@@ -165,8 +169,11 @@ int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t 
     cudaEventRecord(timer->ev[timer->n + 1], s);
     const double es = op_bf16 ? 2.0 : 4.0, cs = d.c_bf16 ? 2.0 : 4.0;
     timer->work[timer->n / 2] = 2.0 * d.M * d.N * d.K;
-    // operands read once, result written once (and read when accumulating)
-    timer->bytes[timer->n / 2] = ((double)d.M * d.K + (double)d.N * d.K) * es +
+    // operands read once, result written once (and read when accumulating); an implicit
+    // convolution reads its input tensor, not the M x K patch matrix
+    const double a_elems = d.conv ? (double)d.conv->N * d.conv->H * d.conv->W * d.conv->C
+                                  : (double)d.M * d.K;
+    timer->bytes[timer->n / 2] = (a_elems + (double)d.N * d.K) * es +
                                  (double)d.M * d.N * cs * (d.beta != 0.f ? 2.0 : 1.0);
     timer->n += 2;
     timer->flops += 2.0 * d.M * d.N * d.K;

@@ -10,8 +10,16 @@
 
 namespace ddppo {
 
+// A convolution whose GEMM A operand is gathered from its NHWC bf16 input by the
+// tensor-core kernel itself (implicit im2col): row m = output pixel, column
+// (ky*k + kx)*C + c. K = k*k*C; B is the [Cout, K] weight matrix.
+struct ConvShape {
+  int N = 0, H = 0, W = 0, C = 0, Ho = 0, Wo = 0, k = 0, s = 1, p = 0;
+};
+
 struct GemmDesc {
   int M = 0, N = 0, K = 0;
+  const ConvShape* conv = nullptr;  // non-null: A is the convolution input (NHWC bf16)
   const void* A = nullptr;
   int lda = 0;
   const void* B = nullptr;
@@ -72,5 +80,8 @@ int launch_splitk_reduce(int M, int N, int splits, const float* partial, float* 
 // tcgen05 path (gemm_tc.cu); returns DDPPO_E_CONFIG when the shape is not supported
 int gemm_tc(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s);
 bool gemm_tc_supported(const GemmDesc& d);
+// whether the implicit-im2col path covers this convolution (C % 32 == 0, output rows that
+// tile 128-pixel blocks, 16-byte aligned input)
+bool gemm_conv_supported(const ConvShape& c, const void* input);
 
 }  // namespace ddppo

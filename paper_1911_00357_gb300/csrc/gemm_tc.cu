@@ -92,6 +92,36 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                            int c1, int c2, int c3) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4, %5, %6}], [%2];" ::"r"(smem_addr(dst)),
+      "l"((uint64_t)map), "r"(smem_addr(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+      : "memory");
+}
+
+// K-major tile with 64-byte rows (32 bf16 K-elements), 64-byte swizzle: 8-row groups
+// 512 B apart; used by the implicit convolution when C = 32
+__device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;              // SWIZZLE_64B
+  return d;
+}
+
+// implicit-im2col parameters of a convolution A operand (passed by value to the kernel)
+struct ConvA {
+  int on = 0;
+  int C = 0, cbw = 64;       // input channels, channels per K-block (64 or 32)
+  int k = 1, s = 1, p = 0;
+  int Ho = 1, Wo = 1;
+  int hi = 1;                // output rows per 128-pixel tile (or Ho when a tile spans images)
+};
+
 // shared-memory matrix descriptors, 128-byte swizzle.
 // K-major tile: rows of 64 K-elements (128 B), 8-row groups 1024 B apart (SBO); the K
 // offset of an MMA within the swizzle atom is added to the start address.
@@ -135,7 +165,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 1)
                    int M, int N, int K, int kchunk, float* __restrict__ C, int ldc, int c_bf16,
                    float beta, const float* __restrict__ bias, int relu, int trans_out,
                    float* __restrict__ partial, int32_t* err, int a_mn, int b_mn, int stages,
-                   int tiles_m, int tiles_n, int splits) {
+                   int tiles_m, int tiles_n, int splits, ConvA ca) {
   extern __shared__ __align__(1024) uint8_t dyn[];
   __shared__ TcSmem ctl;
   __shared__ uint64_t acc_full[2], acc_empty[2];
@@ -173,18 +203,35 @@ __global__ void __launch_bounds__(TC_PTHREADS, 1)
   if (warp == 0) {
     if (lane == 0) {
       // TMA producer over every (tile, k-block) of this CTA
+      const int kstep = ca.on ? ca.cbw : TC_BK;
+      const uint32_t tx = (uint32_t)(TC_BM + BN) * kstep * 2;
       uint32_t it = 0;
       for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
         const int tm = t % tiles_m, tn = (t / tiles_m) % tiles_n, z = t / (tiles_m * tiles_n);
         const int m0 = tm * TC_BM, n0 = tn * BN;
         const int kbeg = z * kchunk, kend = min(K, kbeg + kchunk);
-        const int nkb = (kend - kbeg + TC_BK - 1) / TC_BK;
+        const int nkb = (kend - kbeg + kstep - 1) / kstep;
+        int img = 0, oy0 = 0;
+        if (ca.on) {
+          const int pix = ca.Ho * ca.Wo;
+          img = m0 / pix;
+          oy0 = (m0 - img * pix) / ca.Wo;
+        }
         for (int kb = 0; kb < nkb; ++kb, ++it) {
           const int s = it % stages;
           const uint32_t ph = (it / stages) & 1u;
           if (!mbar_wait(&ctl.empty[s], ph ^ 1u, abort, err)) break;
-          mbar_expect_tx(&ctl.full[s], A_BYTES + B_BYTES);
-          const int k = kbeg + kb * TC_BK;
+          mbar_expect_tx(&ctl.full[s], tx);
+          const int k = kbeg + kb * kstep;
+          if (ca.on) {
+            // A: the input box of this filter tap and channel block (zero outside the image)
+            const int tap = k / ca.C, c0 = k - tap * ca.C;
+            const int ky = tap / ca.k, kx = tap - ky * ca.k;
+            tma_load_4d(sA + s * A_BYTES, &mapA, &ctl.full[s], c0, kx - ca.p, oy0 * ca.s - ca.p + ky,
+                        img);
+            tma_load_2d(sB + s * B_BYTES, &mapB, &ctl.full[s], k, n0);
+            continue;
+          }
           if (a_mn) {
             tma_load_2d(sA + s * A_BYTES, &mapA, &ctl.full[s], m0, k);
             tma_load_2d(sA + s * A_BYTES + 8192, &mapA, &ctl.full[s], m0 + 64, k);
@@ -205,11 +252,13 @@ __global__ void __launch_bounds__(TC_PTHREADS, 1)
     if (lane == 0) {
       // MMA issuer
       const uint32_t idesc = f16_idesc(TC_BM, BN, a_mn, b_mn);
+      const int kstep = ca.on ? ca.cbw : TC_BK;
+      const bool sw64 = ca.on && ca.cbw == 32;
       uint32_t it = 0, ti = 0;
       for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++ti) {
         const int z = t / (tiles_m * tiles_n);
         const int kbeg = z * kchunk, kend = min(K, kbeg + kchunk);
-        const int nkb = (kend - kbeg + TC_BK - 1) / TC_BK;
+        const int nkb = (kend - kbeg + kstep - 1) / kstep;
         const uint32_t buf = ti & 1u, bph = (ti >> 1) & 1u;
         if (!mbar_wait(&acc_empty[buf], bph ^ 1u, abort, err)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -220,10 +269,15 @@ __global__ void __launch_bounds__(TC_PTHREADS, 1)
           if (!mbar_wait(&ctl.full[s], ph, abort, err)) break;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t a0 = smem_addr(sA + s * A_BYTES), b0 = smem_addr(sB + s * B_BYTES);
-#pragma unroll
-          for (int k = 0; k < TC_BK / 16; ++k) {
-            const uint64_t da = a_mn ? sw128_mn_desc(a0 + k * 2048) : sw128_desc(a0 + k * 32);
-            const uint64_t db = b_mn ? sw128_mn_desc(b0 + k * 2048) : sw128_desc(b0 + k * 32);
+          for (int k = 0; k < kstep / 16; ++k) {
+            uint64_t da, db;
+            if (sw64) {
+              da = sw64_desc(a0 + k * 32);
+              db = sw64_desc(b0 + k * 32);
+            } else {
+              da = a_mn ? sw128_mn_desc(a0 + k * 2048) : sw128_desc(a0 + k * 32);
+              db = b_mn ? sw128_mn_desc(b0 + k * 2048) : sw128_desc(b0 + k * 32);
+            }
             const uint32_t acc = (kb | k) ? 1u : 0u;
             asm volatile(
                 "{\n\t.reg .pred p;\n\t"
@@ -362,6 +416,52 @@ static bool make_map(CUtensorMap* m, const void* ptr, int rows, int cols, int ld
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// bf16 [rows, cols] with row stride ld, box [box_rows, box_cols], given swizzle
+static bool make_map_sw(CUtensorMap* m, const void* ptr, int rows, int cols, int ld, int box_rows,
+                        int box_cols, CUtensorMapSwizzle sw) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)box_cols, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// NHWC bf16 input as a 4-D tensor [C, W, H, N]; one box = the cbw channels of the
+// (hi or Ho) x Wo output pixels of a tile, sampled with the convolution stride
+static bool make_conv_map(CUtensorMap* m, const void* x, const ConvShape& c, const ConvA& ca) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const int ni = (c.Ho * c.Wo >= TC_BM) ? 1 : TC_BM / (c.Ho * c.Wo);
+  cuuint64_t dims[4] = {(cuuint64_t)c.C, (cuuint64_t)c.W, (cuuint64_t)c.H, (cuuint64_t)c.N};
+  cuuint64_t strides[3] = {(cuuint64_t)c.C * 2, (cuuint64_t)c.W * c.C * 2,
+                           (cuuint64_t)c.H * c.W * c.C * 2};
+  cuuint32_t box[4] = {(cuuint32_t)ca.cbw, (cuuint32_t)(c.Wo * c.s), (cuuint32_t)(ca.hi * c.s),
+                       (cuuint32_t)ni};
+  cuuint32_t estr[4] = {1, (cuuint32_t)c.s, (cuuint32_t)c.s, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(x), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE,
+            ca.cbw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool gemm_conv_supported(const ConvShape& c, const void* input) {
+  if (!encode_fn()) return false;
+  if (c.C % 32 || c.C <= 0 || ((uintptr_t)input & 15)) return false;
+  if (TC_BM % c.Wo || c.Wo * c.s > 256) return false;
+  const int pix = c.Ho * c.Wo;
+  if (pix >= TC_BM) {
+    const int hi = TC_BM / c.Wo;
+    if (c.Ho % hi || hi * c.s > 256) return false;
+  } else {
+    if (TC_BM % pix || c.Ho * c.s > 256) return false;
+  }
+  return c.k >= 1 && c.s >= 1 && c.s <= 8;
+}
+
 template <int BN>
 static size_t tc_smem(int stages) {
   return (size_t)stages * (TC_BM + BN) * TC_BK * 2 + 4 * 32 * TC_EPI_PITCH * 4 + 1024;
@@ -422,7 +522,7 @@ static TcCfg default_cfg(int N) {
 template <int BN>
 static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int K,
                      const GemmDesc& d, int trans, int a_mn, int b_mn, const GemmWorkspace& ws,
-                     const TcCfg& cfg, cudaStream_t s) {
+                     const TcCfg& cfg, const ConvA& ca, cudaStream_t s) {
   static bool attr_done[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -442,8 +542,9 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
     splits = (int)min((size_t)splits, ws.partial_elems / max(per, (size_t)1));
     if (splits < 2) splits = 1;
   }
+  const int kstep = ca.on ? ca.cbw : TC_BK;
   int kchunk = (K + splits - 1) / splits;
-  kchunk = (kchunk + TC_BK - 1) / TC_BK * TC_BK;
+  kchunk = (kchunk + kstep - 1) / kstep * kstep;
   splits = (K + kchunk - 1) / kchunk;
   float* partial = splits > 1 ? ws.partial : nullptr;
   // persistent grid: one CTA per SM (two where shared memory allows), each walking tiles
@@ -454,7 +555,7 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
   const int grid = min(ntiles, ws.num_sms * per_sm);
   gemm_tc_kernel<BN><<<grid, TC_PTHREADS, tc_smem<BN>(stages), s>>>(
       ma, mb, M, N, K, kchunk, (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu, trans,
-      partial, ws.err, a_mn, b_mn, stages, gm, gn, splits);
+      partial, ws.err, a_mn, b_mn, stages, gm, gn, splits, ca);
   DDPPO_CHECK_LAUNCH();
   if (partial)
     DDPPO_TRY(launch_splitk_reduce(d.M, d.N, splits, partial, (float*)d.C, d.ldc, d.c_bf16, d.beta,
@@ -463,6 +564,24 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
 }
 
 static int run_cfg(const GemmDesc& d, const GemmWorkspace& ws, const TcCfg& cfg, cudaStream_t s) {
+  if (d.conv) {
+    const ConvShape& c = *d.conv;
+    ConvA ca;
+    ca.on = 1;
+    ca.C = c.C;
+    ca.cbw = c.C % 64 == 0 ? 64 : 32;
+    ca.k = c.k; ca.s = c.s; ca.p = c.p; ca.Ho = c.Ho; ca.Wo = c.Wo;
+    ca.hi = c.Ho * c.Wo >= TC_BM ? TC_BM / c.Wo : c.Ho;
+    const CUtensorMapSwizzle sw = ca.cbw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    CUtensorMap ma, mb;
+    if (!make_conv_map(&ma, d.A, c, ca) ||
+        !make_map_sw(&mb, d.B, d.N, d.K, d.ldb, cfg.bn, ca.cbw, sw)) {
+      set_error("gemm_tc: convolution tensor map encoding failed");
+      return DDPPO_E_CUDA;
+    }
+    if (cfg.bn == 128) return launch_tc<128>(ma, mb, d.M, d.N, d.K, d, 0, 0, 0, ws, cfg, ca, s);
+    return launch_tc<64>(ma, mb, d.M, d.N, d.K, d, 0, 0, 0, ws, cfg, ca, s);
+  }
   // swap A and B when M is small: the MMA's 128-row side then covers N
   const bool swap = d.M < TC_BM && d.N > d.M;
   const void* A = swap ? d.B : d.A;
@@ -480,13 +599,14 @@ static int run_cfg(const GemmDesc& d, const GemmWorkspace& ws, const TcCfg& cfg,
     set_error("gemm_tc: tensor map encoding failed");
     return DDPPO_E_CUDA;
   }
-  if (BN == 128) return launch_tc<128>(ma, mb, M, N, d.K, d, swap ? 1 : 0, a_mn, b_mn, ws, cfg, s);
-  return launch_tc<64>(ma, mb, M, N, d.K, d, swap ? 1 : 0, a_mn, b_mn, ws, cfg, s);
+  const ConvA none;
+  if (BN == 128) return launch_tc<128>(ma, mb, M, N, d.K, d, swap ? 1 : 0, a_mn, b_mn, ws, cfg, none, s);
+  return launch_tc<64>(ma, mb, M, N, d.K, d, swap ? 1 : 0, a_mn, b_mn, ws, cfg, none, s);
 }
 
 // time every candidate on a scratch output (beta = 0, same operands); keep the fastest
 static TcCfg tune(const GemmDesc& d, const GemmWorkspace& ws, TcTuner& t, cudaStream_t s) {
-  const bool swap = d.M < TC_BM && d.N > d.M;
+  const bool swap = !d.conv && d.M < TC_BM && d.N > d.M;
   const int Nk = swap ? d.M : d.N;
   std::vector<TcCfg> cands;
   for (int bn : {64, 128}) {
@@ -518,12 +638,12 @@ static TcCfg tune(const GemmDesc& d, const GemmWorkspace& ws, TcTuner& t, cudaSt
 }
 
 int gemm_tc(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s) {
-  const bool swap = d.M < TC_BM && d.N > d.M;
+  const bool swap = !d.conv && d.M < TC_BM && d.N > d.M;
   TcCfg cfg = default_cfg(swap ? d.M : d.N);
   TcTuner* t = ws.tuner;
   if (t && t->on) {
-    const auto key = std::make_tuple(d.M, d.N, d.K, d.a_t * 2 + d.b_t, d.c_bf16,
-                                     d.beta != 0.f ? 1 : 0, d.lda * 8 + d.ldb);
+    const auto key = std::make_tuple(d.M, d.N, d.K, d.a_t * 2 + d.b_t + (d.conv ? 4 + 8 * d.conv->s : 0),
+                                     d.c_bf16, d.beta != 0.f ? 1 : 0, d.lda * 8 + d.ldb);
     auto it = t->table.find(key);
     if (it != t->table.end()) {
       cfg = it->second;

@@ -172,6 +172,7 @@ static int alloc_encoder(Net& n) {
     DDPPO_TRY(gn_bufs(n.stem_n, n.stem.Ho * n.stem.Wo, true));
     const int ph = (n.stem.Ho - 1) / 2 + 1, pw = (n.stem.Wo - 1) / 2 + 1;
     DDPPO_TRY(nalloc(n, &n.pool, NC * ph * pw * n.stem.cout));
+    if (n.bf) DDPPO_TRY(nalloc(n, &n.pool_bf, NC * ph * pw * n.stem.cout));
     DDPPO_TRY(nalloc(n, &n.pool_arg, NC * ph * pw * n.stem.cout));
     for (auto& B : n.blocks) {
       DDPPO_TRY(conv_bufs(B.c1));
@@ -183,6 +184,10 @@ static int alloc_encoder(Net& n) {
         DDPPO_TRY(gn_bufs(B.nd, B.d.Ho * B.d.Wo, false));
       }
       DDPPO_TRY(nalloc(n, &B.y, NC * B.c2.Ho * B.c2.Wo * B.c2.cout));
+      if (n.bf) {
+        DDPPO_TRY(nalloc(n, &B.y_bf, NC * B.c2.Ho * B.c2.Wo * B.c2.cout));
+        DDPPO_TRY(nalloc(n, &B.n1.out_bf, NC * B.c1.Ho * B.c1.Wo * B.c1.cout));
+      }
     }
     DDPPO_TRY(conv_bufs(n.cmp));
     DDPPO_TRY(gn_bufs(n.cmp_n, n.featHW, true));
@@ -400,15 +405,31 @@ void net_destroy(ddppo_ctx* x) {
 // ---------------------------------------------------------------- encoder
 static int G(Net& n, const GemmDesc& d, cudaStream_t s) { return gemm(d, n.bf, n.gws, s, &n.timer); }
 
+static ConvShape conv_shape(const ConvL& c, int N) {
+  ConvShape cs;
+  cs.N = N; cs.H = c.H; cs.W = c.W; cs.C = c.cin; cs.Ho = c.Ho; cs.Wo = c.Wo;
+  cs.k = c.k; cs.s = c.s; cs.p = c.p;
+  return cs;
+}
+
+// forward convolution. in_bf (bf16 NHWC copy of the input, BF16 form) lets the tensor-core
+// GEMM gather the patches itself; otherwise im2col materialises them first
 static int conv_fwd(Net& n, ConvL& c, const void* in, bool in_bf16, int N, float* out, bool bias_relu,
-                    cudaStream_t s) {
-  const ConvGeom g = geom(c, N);
-  DDPPO_TRY(launch_im2col(g, in, in_bf16, n.col, n.bf, false, s));
+                    cudaStream_t s, const __nv_bfloat16* in_bf = nullptr) {
   GemmDesc d;
   d.M = N * c.Ho * c.Wo; d.N = c.cout; d.K = c.Kp;
-  d.A = n.col; d.lda = c.Kp; d.B = c.wg; d.ldb = c.Kp;
+  d.B = c.wg; d.ldb = c.Kp;
   d.C = out; d.ldc = c.cout;
   if (bias_relu) { d.bias = n.params + c.b_off; d.relu = 1; }
+  const ConvShape cs = conv_shape(c, N);
+  if (n.bf && in_bf && c.Kp == c.k * c.k * c.cin && gemm_conv_supported(cs, in_bf)) {
+    d.conv = &cs;
+    d.A = in_bf; d.lda = d.K;
+    return G(n, d, s);
+  }
+  const ConvGeom g = geom(c, N);
+  DDPPO_TRY(launch_im2col(g, in, in_bf16, n.col, n.bf, false, s));
+  d.A = n.col; d.lda = c.Kp;
   return G(n, d, s);
 }
 
@@ -416,10 +437,12 @@ static int conv_fwd(Net& n, ConvL& c, const void* in, bool in_bf16, int N, float
 //   dW[co, kk] += sum_m dz[m, co] col[m, kk]   (both operands read as stored: MN-major)
 //   dcol[m, kk] = sum_co dz[m, co] W[co, kk]   then col2im
 static int conv_bwd(Net& n, ConvL& c, const void* in, bool in_bf16, int N, const void* dzop,
-                    float* dx, bool dx_acc, bool first, cudaStream_t s) {
+                    float* dx, bool dx_acc, bool first, cudaStream_t s,
+                    const __nv_bfloat16* in_bf = nullptr) {
   const ConvGeom g = geom(c, N);
   const int M = N * c.Ho * c.Wo;
-  DDPPO_TRY(launch_im2col(g, in, in_bf16, n.col, n.bf, false, s));
+  if (in_bf) DDPPO_TRY(launch_im2col(g, in_bf, true, n.col, n.bf, false, s));
+  else DDPPO_TRY(launch_im2col(g, in, in_bf16, n.col, n.bf, false, s));
   GemmDesc w;
   w.M = c.cout; w.N = c.Kp; w.K = M;
   w.A = dzop; w.lda = c.cout; w.a_t = 1;
@@ -431,11 +454,20 @@ static int conv_bwd(Net& n, ConvL& c, const void* in, bool in_bf16, int N, const
     ConvGeom gd;
     gd.N = N; gd.H = c.Ho; gd.W = c.Wo; gd.C = c.cout; gd.Ho = c.H; gd.Wo = c.W; gd.Cout = c.cin;
     gd.k = c.k; gd.s = 1; gd.p = c.p; gd.K = c.k * c.k * c.cout; gd.Kp = gd.K;
-    DDPPO_TRY(launch_im2col(gd, dzop, n.bf, n.col, n.bf, false, s));
     GemmDesc d;
     d.M = N * c.H * c.W; d.N = c.cin; d.K = gd.K;
-    d.A = n.col; d.lda = gd.K; d.B = c.wgR; d.ldb = gd.K;
+    d.B = c.wgR; d.ldb = gd.K;
     d.C = dx; d.ldc = c.cin; d.beta = dx_acc ? 1.f : 0.f;
+    ConvShape cs;
+    cs.N = N; cs.H = c.Ho; cs.W = c.Wo; cs.C = c.cout; cs.Ho = c.H; cs.Wo = c.W;
+    cs.k = c.k; cs.s = 1; cs.p = c.p;
+    if (n.bf && gemm_conv_supported(cs, dzop)) {
+      d.conv = &cs;  // the output gradient (bf16 NHWC) is gathered by the GEMM itself
+      d.A = dzop; d.lda = d.K;
+    } else {
+      DDPPO_TRY(launch_im2col(gd, dzop, n.bf, n.col, n.bf, false, s));
+      d.A = n.col; d.lda = gd.K;
+    }
     DDPPO_TRY(G(n, d, s));
   } else if (dx) {
     GemmDesc d;
@@ -449,7 +481,8 @@ static int conv_bwd(Net& n, ConvL& c, const void* in, bool in_bf16, int N, const
 }
 
 static int gn_fwd(Net& n, GNL& g, const float* z, int N, int HW, float* out, bool relu,
-                  const float* resid, const GNL* gd, const float* zd, cudaStream_t s) {
+                  const float* resid, const GNL* gd, const float* zd, cudaStream_t s,
+                  __nv_bfloat16* out_bf = nullptr) {
   const float eps = 1e-5f;
   DDPPO_TRY(launch_gn_stats(z, N, HW, g.C, eps, g.mean, g.rstd, s));
   GNApply a{};
@@ -462,6 +495,7 @@ static int gn_fwd(Net& n, GNL& g, const float* z, int N, int HW, float* out, boo
     a.gamma_d = n.params + gd->g_off; a.beta_d = n.params + gd->b_off;
   }
   a.out = out;
+  a.out_bf = out_bf;
   a.relu = relu ? 1 : 0;
   return launch_gn_apply(a, N, HW, g.C, s);
 }
@@ -486,22 +520,26 @@ static int encoder_fwd(Net& n, const void* obs, int N, void* featop_rows, cudaSt
   ConvL& st = n.stem;
   DDPPO_TRY(conv_fwd(n, st, obs, n.bf, N, st.z, false, s));
   DDPPO_TRY(gn_fwd(n, n.stem_n, st.z, N, st.Ho * st.Wo, n.stem_n.out, true, nullptr, nullptr, nullptr, s));
-  DDPPO_TRY(launch_maxpool_fwd(n.stem_n.out, N, st.Ho, st.Wo, st.cout, n.pool, n.pool_arg, s));
+  DDPPO_TRY(launch_maxpool_fwd(n.stem_n.out, N, st.Ho, st.Wo, st.cout, n.pool, n.pool_arg,
+                               n.pool_bf, s));
   const float* cur = n.pool;
+  const __nv_bfloat16* cur_bf = n.pool_bf;
   for (auto& B : n.blocks) {
     const int HW = B.c1.Ho * B.c1.Wo;
-    DDPPO_TRY(conv_fwd(n, B.c1, cur, false, N, B.c1.z, false, s));
-    DDPPO_TRY(gn_fwd(n, B.n1, B.c1.z, N, HW, B.n1.out, true, nullptr, nullptr, nullptr, s));
-    DDPPO_TRY(conv_fwd(n, B.c2, B.n1.out, false, N, B.c2.z, false, s));
+    DDPPO_TRY(conv_fwd(n, B.c1, cur, false, N, B.c1.z, false, s, cur_bf));
+    DDPPO_TRY(gn_fwd(n, B.n1, B.c1.z, N, HW, B.n1.out, true, nullptr, nullptr, nullptr, s,
+                     B.n1.out_bf));
+    DDPPO_TRY(conv_fwd(n, B.c2, B.n1.out, false, N, B.c2.z, false, s, B.n1.out_bf));
     if (B.down) {
-      DDPPO_TRY(conv_fwd(n, B.d, cur, false, N, B.d.z, false, s));
-      DDPPO_TRY(gn_fwd(n, B.n2, B.c2.z, N, HW, B.y, true, nullptr, &B.nd, B.d.z, s));
+      DDPPO_TRY(conv_fwd(n, B.d, cur, false, N, B.d.z, false, s, cur_bf));
+      DDPPO_TRY(gn_fwd(n, B.n2, B.c2.z, N, HW, B.y, true, nullptr, &B.nd, B.d.z, s, B.y_bf));
     } else {
-      DDPPO_TRY(gn_fwd(n, B.n2, B.c2.z, N, HW, B.y, true, cur, nullptr, nullptr, s));
+      DDPPO_TRY(gn_fwd(n, B.n2, B.c2.z, N, HW, B.y, true, cur, nullptr, nullptr, s, B.y_bf));
     }
     cur = B.y;
+    cur_bf = B.y_bf;
   }
-  DDPPO_TRY(conv_fwd(n, n.cmp, cur, false, N, n.cmp.z, false, s));
+  DDPPO_TRY(conv_fwd(n, n.cmp, cur, false, N, n.cmp.z, false, s, cur_bf));
   DDPPO_TRY(gn_fwd(n, n.cmp_n, n.cmp.z, N, n.featHW, n.cmp_n.out, true, nullptr, nullptr, nullptr, s));
   return launch_cast(n.cmp_n.out, featop_rows, n.bf, (size_t)N * n.F, s);
 }
@@ -530,7 +568,8 @@ static int encoder_bwd(Net& n, const void* obs, int N, const float* dfeat_rows, 
     const size_t cnt = (size_t)N * n.F;
     DDPPO_TRY(launch_relu_bwd(dfeat_rows, n.cmp_n.out, cnt, n.g0, nullptr, n.bf, s));
     DDPPO_TRY(gn_bwd(n, n.cmp_n, n.g0, n.cmp.z, N, n.featHW, first, s));
-    DDPPO_TRY(conv_bwd(n, n.cmp, n.blocks[7].y, false, N, n.dzop, n.g1, false, first, s));
+    DDPPO_TRY(conv_bwd(n, n.cmp, n.blocks[7].y, false, N, n.dzop, n.g1, false, first, s,
+                       n.blocks[7].y_bf));
   }
   float* gcur = n.g1;
   float* gA = n.g0;
@@ -539,16 +578,17 @@ static int encoder_bwd(Net& n, const void* obs, int N, const float* dfeat_rows, 
     BlockL& B = n.blocks[bi];
     const int HW = B.c1.Ho * B.c1.Wo;
     const float* xin = bi > 0 ? n.blocks[bi - 1].y : n.pool;
+    const __nv_bfloat16* xin_bf = bi > 0 ? n.blocks[bi - 1].y_bf : n.pool_bf;
     const size_t cnt = (size_t)N * HW * B.c2.cout;
     DDPPO_TRY(launch_relu_bwd(gcur, B.y, cnt, gcur, nullptr, n.bf, s));  // grad of the pre-ReLU sum
     DDPPO_TRY(gn_bwd(n, B.n2, gcur, B.c2.z, N, HW, first, s));
-    DDPPO_TRY(conv_bwd(n, B.c2, B.n1.out, false, N, n.dzop, gA, false, first, s));
+    DDPPO_TRY(conv_bwd(n, B.c2, B.n1.out, false, N, n.dzop, gA, false, first, s, B.n1.out_bf));
     DDPPO_TRY(launch_relu_bwd(gA, B.n1.out, cnt, gA, nullptr, n.bf, s));
     DDPPO_TRY(gn_bwd(n, B.n1, gA, B.c1.z, N, HW, first, s));
-    DDPPO_TRY(conv_bwd(n, B.c1, xin, false, N, n.dzop, gB, false, first, s));
+    DDPPO_TRY(conv_bwd(n, B.c1, xin, false, N, n.dzop, gB, false, first, s, xin_bf));
     if (B.down) {
       DDPPO_TRY(gn_bwd(n, B.nd, gcur, B.d.z, N, HW, first, s));
-      DDPPO_TRY(conv_bwd(n, B.d, xin, false, N, n.dzop, gB, true, first, s));
+      DDPPO_TRY(conv_bwd(n, B.d, xin, false, N, n.dzop, gB, true, first, s, xin_bf));
     } else {
       DDPPO_TRY(launch_add(gB, gcur, (size_t)N * B.c1.H * B.c1.W * B.c1.cin, s));
     }

@@ -29,6 +29,7 @@ struct GNL {
   float* mean = nullptr;  // [NC, C/2]
   float* rstd = nullptr;
   float* out = nullptr;   // [NC, HW, C] post-activation output (when materialised)
+  __nv_bfloat16* out_bf = nullptr;  // its bf16 copy (BF16 form: the next conv's TMA operand)
 };
 
 struct BlockL {
@@ -36,6 +37,7 @@ struct BlockL {
   GNL n1, n2, nd;
   bool down = false;
   float* y = nullptr;     // block output [NC, Ho, Wo, cout]
+  __nv_bfloat16* y_bf = nullptr;  // its bf16 copy (BF16 form)
 };
 
 struct LstmL {
@@ -73,6 +75,7 @@ struct Net {
   ConvL stem;
   GNL stem_n;
   float* pool = nullptr;
+  __nv_bfloat16* pool_bf = nullptr;
   uint8_t* pool_arg = nullptr;
   BlockL blocks[8];
   ConvL cmp;

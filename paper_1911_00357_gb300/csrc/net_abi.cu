@@ -466,3 +466,37 @@ extern "C" int ddppo_autotune(ddppo_ctx* x, int32_t on, int64_t* tuned_shapes) {
   if (tuned_shapes) *tuned_shapes = tc_tuner_shapes(x->net->gws.tuner);
   return DDPPO_OK;
 }
+
+// ---- stand-alone convolution on the implicit-im2col tensor-core path ----
+extern "C" int ddppo_conv2d(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, int32_t k,
+                            int32_t stride, int32_t pad, const void* x, const void* w, float* y,
+                            int32_t* status, void* stream) {
+  ARG(N >= 1 && H >= 1 && W >= 1 && C >= 1 && Cout >= 1 && k >= 1 && stride >= 1 && pad >= 0,
+      "conv2d: bad sizes");
+  ARG(x && w && y, "conv2d: null argument");
+  ConvShape c;
+  c.N = N; c.H = H; c.W = W; c.C = C; c.k = k; c.s = stride; c.p = pad;
+  c.Ho = (H + 2 * pad - k) / stride + 1;
+  c.Wo = (W + 2 * pad - k) / stride + 1;
+  ARG(c.Ho >= 1 && c.Wo >= 1, "conv2d: empty output");
+  if (!gemm_conv_supported(c, x)) {
+    set_error("conv2d: shape not covered by the implicit-im2col path");
+    return DDPPO_E_CONFIG;
+  }
+  int dev = 0;
+  DDPPO_CHECK_CUDA(cudaGetDevice(&dev));
+  GemmWorkspace ws;
+  static float* partial[64] = {};
+  ARG(dev < 64, "conv2d: device ordinal out of range");
+  const size_t elems = (size_t)16 << 20;
+  if (!partial[dev]) DDPPO_CHECK_CUDA(cudaMalloc(&partial[dev], elems * sizeof(float)));
+  ws.partial = partial[dev];
+  ws.partial_elems = elems;
+  cudaDeviceGetAttribute(&ws.num_sms, cudaDevAttrMultiProcessorCount, dev);
+  ws.err = status;
+  GemmDesc d;
+  d.M = N * c.Ho * c.Wo; d.N = Cout; d.K = k * k * C;
+  d.conv = &c; d.A = x; d.lda = d.K; d.B = w; d.ldb = d.K;
+  d.C = y; d.ldc = Cout;
+  return gemm(d, true, ws, (cudaStream_t)stream, nullptr);
+}

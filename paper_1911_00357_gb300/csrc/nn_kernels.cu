@@ -390,6 +390,7 @@ __global__ void gn_apply_kernel(GNApply a, int N, int HW, int C) {
     if (a.zd) v += (a.zd[idx] - a.mean_d[ng]) * a.rstd_d[ng] * a.gamma_d[c] + a.beta_d[c];
     if (a.relu) v = fmaxf(v, 0.f);
     a.out[idx] = v;
+    if (a.out_bf) a.out_bf[idx] = __float2bfloat16_rn(v);
   }
 }
 
@@ -492,7 +493,8 @@ int launch_add(float* dst, const float* src, size_t n, cudaStream_t s) {
 
 // ---------------------------------------------------------------- max pool 3x3 / 2, pad 1
 __global__ void maxpool_fwd_kernel(const float* __restrict__ x, int N, int H, int W, int C,
-                                   float* __restrict__ y, uint8_t* __restrict__ arg) {
+                                   float* __restrict__ y, uint8_t* __restrict__ arg,
+                                   __nv_bfloat16* __restrict__ y_bf) {
   const int Ho = (H + 2 - 3) / 2 + 1, Wo = (W + 2 - 3) / 2 + 1;
   const size_t total = (size_t)N * Ho * Wo * C;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -513,15 +515,16 @@ __global__ void maxpool_fwd_kernel(const float* __restrict__ x, int N, int H, in
       }
     }
     y[idx] = best;
+    if (y_bf) y_bf[idx] = __float2bfloat16_rn(best);
     arg[idx] = (uint8_t)bi;
   }
 }
 int launch_maxpool_fwd(const float* x, int N, int H, int W, int C, float* y, uint8_t* arg,
-                       cudaStream_t s) {
+                       __nv_bfloat16* y_bf, cudaStream_t s) {
   const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1;
   const size_t total = (size_t)N * Ho * Wo * C;
   if (!total) return DDPPO_OK;
-  maxpool_fwd_kernel<<<grid_for(total), 256, 0, s>>>(x, N, H, W, C, y, arg);
+  maxpool_fwd_kernel<<<grid_for(total), 256, 0, s>>>(x, N, H, W, C, y, arg, y_bf);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }

@@ -34,6 +34,7 @@ struct GNApply {
   const float* resid;  // or null
   const float* zd; const float* mean_d; const float* rstd_d; const float* gamma_d; const float* beta_d;
   float* out; int relu;
+  __nv_bfloat16* out_bf;  // optional bf16 copy of out (the next convolution's TMA operand)
 };
 int launch_gn_apply(const GNApply& a, int N, int HW, int C, cudaStream_t s);
 // GroupNorm backward: dy (fp32, grad of the GN output) -> dz (fp32 and/or op dtype),
@@ -49,7 +50,7 @@ int launch_relu_bwd(const float* dy, const float* y, size_t n, float* dz32, void
 int launch_add(float* dst, const float* src, size_t n, cudaStream_t s);
 
 int launch_maxpool_fwd(const float* x, int N, int H, int W, int C, float* y, uint8_t* arg,
-                       cudaStream_t s);
+                       __nv_bfloat16* y_bf, cudaStream_t s);
 int launch_maxpool_bwd(const float* dy, const uint8_t* arg, int N, int H, int W, int C, float* dx,
                        cudaStream_t s);
 
