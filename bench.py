@@ -117,8 +117,15 @@ def run_gpu(args):
     def measure(prec, steps, warmup, timing):
         kw = {"rollout_T": args.rollout_T} if args.rollout_T else {}
         w = Worker("resnet", precision=prec, seed=1000 * rank + 17, **kw)
+        cache = args.tune_cache if prec == 1 else None
+        if cache and os.path.exists(cache):
+            with open(cache, "rb") as f:
+                B.ddppo_autotune_import(w.h, f.read())
         for _ in range(warmup):
             w.iterate()
+        if cache and not os.path.exists(cache) and rank == 0:
+            with open(cache, "wb") as f:
+                f.write(B.ddppo_autotune_export(w.h))
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
@@ -283,6 +290,9 @@ def main():
                     help="shorter rollout for profiler launch lists (not a bench value)")
     ap.add_argument("--profile", action="store_true",
                     help="timed steps only (for ncu); prints no bench line")
+    ap.add_argument("--tune-cache", default=None,
+                    help="GEMM tuning table: loaded if the file exists, else written after the "
+                         "warm-up (a profiled run then launches the plain run's configurations)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "native" and not args.profile:
         args.warmup = 3

@@ -330,6 +330,17 @@ int ddppo_gemm_backend(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const v
  * (new shapes use the fixed heuristic). tuned_shapes [host] (NULL ok): table size. */
 int ddppo_autotune(ddppo_ctx* ctx, int32_t on, int64_t* tuned_shapes);
 
+/* Save and restore the autotuner's table (a tuning cache), so that a later process --
+ * for instance one run under a profiler, whose serialised launches would distort the
+ * trial timings -- launches the same configurations without re-tuning.
+ * export: buf [host] (NULL: size query) of cap bytes; size [host] receives the image's
+ *   byte count; DDPPO_E_CONFIG when buf is non-NULL and cap < size.
+ * import: buf [host] of size bytes from an export (same library version); its entries
+ *   replace equal shapes; DDPPO_E_CONFIG on a malformed image or when precision is 0
+ *   (no tensor-core GEMM). The image is plain int32 words in host byte order. */
+int ddppo_autotune_export(ddppo_ctx* ctx, void* buf, size_t cap, size_t* size);
+int ddppo_autotune_import(ddppo_ctx* ctx, const void* buf, size_t size);
+
 /* Per-kernel-family timing of the calls enqueued while enabled (CUDA events on
  * the launching stream). ddppo_timing_enable(ctx, 1) starts recording and
  * clears the counters; ddppo_timing_read synchronises and returns, for family

@@ -109,6 +109,8 @@ _SIGS = {
     "ddppo_gemm_backend": [I32, I32, I32, I32, P, I32, P, I32, P],
     "ddppo_timing_launches": [P, I32, P, P, P, I64, P],
     "ddppo_autotune": [P, I32, P],
+    "ddppo_autotune_export": [P, P, ctypes.c_size_t, P],
+    "ddppo_autotune_import": [P, P, ctypes.c_size_t],
     "ddppo_conv2d": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, P, P],
 }
 
@@ -326,6 +328,20 @@ def ddppo_autotune(h, on: bool = True) -> int:
     n = ctypes.c_int64()
     _check(lib().ddppo_autotune(h, 1 if on else 0, ctypes.byref(n)))
     return n.value
+
+
+def ddppo_autotune_export(h) -> bytes:
+    """The autotuner's table as a byte image (a tuning cache)."""
+    n = ctypes.c_size_t()
+    _check(lib().ddppo_autotune_export(h, None, 0, ctypes.byref(n)))
+    buf = ctypes.create_string_buffer(n.value)
+    _check(lib().ddppo_autotune_export(h, buf, n.value, ctypes.byref(n)))
+    return buf.raw[:n.value]
+
+
+def ddppo_autotune_import(h, image: bytes) -> None:
+    buf = ctypes.create_string_buffer(bytes(image), len(image))
+    _check(lib().ddppo_autotune_import(h, buf, len(image)))
 
 
 def ddppo_conv2d(x, w, y, k: int, stride: int, pad: int, status=None):

@@ -48,6 +48,10 @@ TcTuner* tc_tuner_create(size_t scratch_bytes);
 void tc_tuner_destroy(TcTuner* t);
 void tc_tuner_enable(TcTuner* t, bool on);
 int64_t tc_tuner_shapes(const TcTuner* t);
+// serialise the table into buf (returns the bytes needed; writes only when cap suffices)
+size_t tc_tuner_export(const TcTuner* t, void* buf, size_t cap);
+// merge a serialised table (entries replace equal keys)
+int tc_tuner_import(TcTuner* t, const void* buf, size_t size);
 
 struct GemmWorkspace {
   float* partial = nullptr;  // split-K partial sums

@@ -511,6 +511,49 @@ void tc_tuner_destroy(TcTuner* t) {
 void tc_tuner_enable(TcTuner* t, bool on) { if (t) t->on = on; }
 int64_t tc_tuner_shapes(const TcTuner* t) { return t ? (int64_t)t->table.size() : 0; }
 
+// table image: int32 words {magic, version, count} then count records of 7 key words and
+// 3 configuration words (N tile, ring depth, split policy)
+static const int32_t kTuneMagic = 0x54544444, kTuneVersion = 1, kTuneRec = 10;
+
+size_t tc_tuner_export(const TcTuner* t, void* buf, size_t cap) {
+  const size_t cnt = t ? t->table.size() : 0;
+  const size_t need = (3 + cnt * kTuneRec) * sizeof(int32_t);
+  if (!buf || cap < need) return need;
+  int32_t* w = (int32_t*)buf;
+  w[0] = kTuneMagic; w[1] = kTuneVersion; w[2] = (int32_t)cnt;
+  int32_t* r = w + 3;
+  if (t)
+    for (const auto& kv : t->table) {
+      const auto& k = kv.first;
+      r[0] = std::get<0>(k); r[1] = std::get<1>(k); r[2] = std::get<2>(k); r[3] = std::get<3>(k);
+      r[4] = std::get<4>(k); r[5] = std::get<5>(k); r[6] = std::get<6>(k);
+      r[7] = kv.second.bn; r[8] = kv.second.stages; r[9] = kv.second.split;
+      r += kTuneRec;
+    }
+  return need;
+}
+
+int tc_tuner_import(TcTuner* t, const void* buf, size_t size) {
+  if (!t) { set_error("autotune import: no tuner (precision 0)"); return DDPPO_E_CONFIG; }
+  const int32_t* w = (const int32_t*)buf;
+  if (!buf || size < 3 * sizeof(int32_t) || w[0] != kTuneMagic || w[1] != kTuneVersion || w[2] < 0 ||
+      size != (3 + (size_t)w[2] * kTuneRec) * sizeof(int32_t)) {
+    set_error("autotune import: not a tuning table image of this version");
+    return DDPPO_E_CONFIG;
+  }
+  const int32_t* r = w + 3;
+  for (int32_t i = 0; i < w[2]; ++i, r += kTuneRec) {
+    TcCfg c;
+    c.bn = r[7]; c.stages = r[8]; c.split = r[9];
+    if ((c.bn != 64 && c.bn != 128) || c.stages < 2 || c.stages > TC_STAGES || (c.split != 0 && c.split != 1)) {
+      set_error("autotune import: bad configuration record");
+      return DDPPO_E_CONFIG;
+    }
+    t->table[std::make_tuple(r[0], r[1], r[2], r[3], r[4], r[5], r[6])] = c;
+  }
+  return DDPPO_OK;
+}
+
 static TcCfg default_cfg(int N) {
   TcCfg c;
   c.bn = N > 64 ? 128 : 64;

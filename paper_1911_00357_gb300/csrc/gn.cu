@@ -1,0 +1,382 @@
+// GroupNorm with groups of two channels (C/2 groups per image), the normalisation of the
+// ResNet encoder's convolutions (Sec. 4 replaces BatchNorm by GroupNorm). Activations are
+// NHWC fp32 [N, HW, C].
+//
+// The statistics and the backward reductions split every image over S blocks (a grid of
+// S x N) so that a small batch -- the 64 frames of one rollout step -- still covers every
+// SM. Each thread owns V consecutive channels (V = 4, or 2 when C % 4 != 0) of one pixel
+// row and loads them as one vector. Blocks write per-channel partial sums; the last block
+// of an image to finish (a per-image arrival counter, re-armed by that block) combines the
+// S partials in block order, so every result is deterministic. The element-wise passes
+// (normalise + residual + ReLU, and the input gradient) are vectorised the same way.
+#include <algorithm>
+
+#include "nn_kernels.cuh"
+
+namespace ddppo {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+template <int V>
+__device__ __forceinline__ void ldv(const float* p, float (&v)[V]) {
+  if constexpr (V == 4) {
+    const float4 t = *reinterpret_cast<const float4*>(p);
+    v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+  } else {
+    const float2 t = *reinterpret_cast<const float2*>(p);
+    v[0] = t.x; v[1] = t.y;
+  }
+}
+template <int V>
+__device__ __forceinline__ void stv(float* p, const float (&v)[V]) {
+  if constexpr (V == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  else *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+}
+__device__ __forceinline__ uint32_t pack_bf2(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+template <int V>
+__device__ __forceinline__ void stv_bf(__nv_bfloat16* p, const float (&v)[V]) {
+  if constexpr (V == 4) *reinterpret_cast<uint2*>(p) = make_uint2(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]));
+  else *reinterpret_cast<uint32_t*>(p) = pack_bf2(v[0], v[1]);
+}
+template <int V>
+__device__ __forceinline__ void stv_op(void* p, size_t i, const float (&v)[V], bool bf) {
+  if (bf) stv_bf<V>((__nv_bfloat16*)p + i, v);
+  else stv<V>((float*)p + i, v);
+}
+
+// threads of the block: R = C / V per pixel row, P rows per pass
+__host__ __device__ inline int rows_per_pass(int C, int V) {
+  const int R = C / V;
+  return R >= kThreads ? 1 : kThreads / R;
+}
+
+// sums the per-thread pair (a[v], b[v]) over the P rows of the block for every channel,
+// in row order; results for channel c at out[2c], out[2c + 1]. sh holds blockDim x 2V.
+template <int V>
+__device__ __forceinline__ void block_pair_sums(const float (&a)[V], const float (&b)[V], float* sh,
+                                                int C, float* out) {
+  const int R = C / V, P = blockDim.x / R;
+  for (int v = 0; v < V; ++v) {
+    sh[threadIdx.x * 2 * V + v] = a[v];
+    sh[threadIdx.x * 2 * V + V + v] = b[v];
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    const int cv = c / V, v = c % V;
+    float sa = 0.f, sb = 0.f;
+    for (int r = 0; r < P; ++r) {
+      const float* q = sh + (size_t)(r * R + cv) * 2 * V;
+      sa += q[v];
+      sb += q[V + v];
+    }
+    out[2 * c] = sa;
+    out[2 * c + 1] = sb;
+  }
+}
+
+// true in exactly one block per image: the last to arrive after writing its partials
+__device__ __forceinline__ bool last_of_image(int* cnt, int S, int* flag) {
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) *flag = atomicAdd(cnt, 1) == S - 1;
+  __syncthreads();
+  if (!*flag) return false;
+  __threadfence();
+  return true;
+}
+
+// ---- statistics: shifted sums about the image's first pixel, combined in double ----
+template <int V>
+__global__ void __launch_bounds__(kThreads) gn_stats_kernel(const float* __restrict__ z, int HW, int C,
+                                                            int S, float eps, float* __restrict__ part,
+                                                            int* __restrict__ cnt, float* __restrict__ mean,
+                                                            float* __restrict__ rstd) {
+  extern __shared__ float sh[];
+  __shared__ int flag;
+  const int R = C / V, P = blockDim.x / R;
+  const int n = blockIdx.y, sb = blockIdx.x;
+  const int cv = threadIdx.x % R, pr = threadIdx.x / R, c0 = cv * V;
+  const int chunk = (HW + S - 1) / S, pb = sb * chunk, pe = min(HW, pb + chunk);
+  const float* zi = z + (size_t)n * HW * C;
+  float K[V], s1[V], s2[V];
+  ldv<V>(zi + c0, K);
+#pragma unroll
+  for (int v = 0; v < V; ++v) s1[v] = s2[v] = 0.f;
+  for (int p = pb + pr; p < pe; p += P) {
+    float x[V];
+    ldv<V>(zi + (size_t)p * C + c0, x);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const float d = x[v] - K[v];
+      s1[v] += d;
+      s2[v] += d * d;
+    }
+  }
+  float* pp = part + ((size_t)n * S + sb) * C * 2;
+  block_pair_sums<V>(s1, s2, sh, C, pp);
+  if (!last_of_image(cnt + n, S, &flag)) return;
+  const int G = C / 2;
+  const double inv = 1.0 / HW;
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    double m[2], M2[2];
+    for (int j = 0; j < 2; ++j) {
+      const int c = 2 * g + j;
+      double a = 0.0, b = 0.0;
+      for (int t = 0; t < S; ++t) {
+        const float* q = part + ((size_t)n * S + t) * C * 2 + 2 * c;
+        a += (double)__ldcg(q);
+        b += (double)__ldcg(q + 1);
+      }
+      m[j] = (double)zi[c] + a * inv;   // the same shift every block used
+      M2[j] = b - a * a * inv;
+    }
+    const double dm = m[0] - m[1];
+    double var = (M2[0] + M2[1] + 0.5 * HW * dm * dm) / (2.0 * HW);
+    if (var < 0.0) var = 0.0;
+    mean[(size_t)n * G + g] = (float)(0.5 * (m[0] + m[1]));
+    rstd[(size_t)n * G + g] = 1.0f / sqrtf((float)var + eps);
+  }
+  if (threadIdx.x == 0) cnt[n] = 0;  // re-arm for the next launch on this stream
+}
+
+// ---- out = act(gn(z) + res) ----
+template <int V>
+__global__ void __launch_bounds__(kThreads) gn_apply_kernel(GNApply a, int HW, int C) {
+  const int R = C / V, G = C / 2;
+  const int n = blockIdx.y;
+  const int per = HW * R;
+  const size_t ib = (size_t)n * HW * C;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per; i += gridDim.x * blockDim.x) {
+    const int cv = i % R, c0 = cv * V;
+    const size_t o = ib + (size_t)i * V;
+    float x[V], gm[V], bt[V];
+    ldv<V>(a.z + o, x);
+    ldv<V>(a.gamma + c0, gm);
+    ldv<V>(a.beta + c0, bt);
+    const float* mu = a.mean + (size_t)n * G + c0 / 2;
+    const float* rs = a.rstd + (size_t)n * G + c0 / 2;
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = (x[v] - mu[v / 2]) * rs[v / 2] * gm[v] + bt[v];
+    if (a.resid) {
+      float r[V];
+      ldv<V>(a.resid + o, r);
+#pragma unroll
+      for (int v = 0; v < V; ++v) x[v] += r[v];
+    }
+    if (a.zd) {
+      float d[V], gd[V], bd[V];
+      ldv<V>(a.zd + o, d);
+      ldv<V>(a.gamma_d + c0, gd);
+      ldv<V>(a.beta_d + c0, bd);
+      const float* mud = a.mean_d + (size_t)n * G + c0 / 2;
+      const float* rsd = a.rstd_d + (size_t)n * G + c0 / 2;
+#pragma unroll
+      for (int v = 0; v < V; ++v) x[v] += (d[v] - mud[v / 2]) * rsd[v / 2] * gd[v] + bd[v];
+    }
+    if (a.relu) {
+#pragma unroll
+      for (int v = 0; v < V; ++v) x[v] = fmaxf(x[v], 0.f);
+    }
+    if (a.out) stv<V>(a.out + o, x);
+    if (a.out_bf) stv_bf<V>(a.out_bf + o, x);
+  }
+}
+
+// ---- backward reductions: g = dy (masked by relu_y > 0), xhat = (z - mu) rstd;
+//      per image and channel sum(g) and sum(g xhat); group means of gamma-weighted sums ----
+template <int V>
+__global__ void __launch_bounds__(kThreads) gn_bwd_reduce_kernel(GNBack b, int HW, int C, int S,
+                                                                 float* __restrict__ part,
+                                                                 int* __restrict__ cnt) {
+  extern __shared__ float sh[];
+  __shared__ int flag;
+  const int R = C / V, P = blockDim.x / R, G = C / 2;
+  const int n = blockIdx.y, sb = blockIdx.x;
+  const int cv = threadIdx.x % R, pr = threadIdx.x / R, c0 = cv * V;
+  const int chunk = (HW + S - 1) / S, pb = sb * chunk, pe = min(HW, pb + chunk);
+  const size_t ib = (size_t)n * HW * C;
+  float mu[V], rs[V], sg[V], sgx[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    mu[v] = b.mean[(size_t)n * G + (c0 + v) / 2];
+    rs[v] = b.rstd[(size_t)n * G + (c0 + v) / 2];
+    sg[v] = sgx[v] = 0.f;
+  }
+  for (int p = pb + pr; p < pe; p += P) {
+    const size_t o = ib + (size_t)p * C + c0;
+    float d[V], x[V];
+    ldv<V>(b.dy + o, d);
+    ldv<V>(b.z + o, x);
+    if (b.relu_y) {
+      float y[V];
+      ldv<V>(b.relu_y + o, y);
+#pragma unroll
+      for (int v = 0; v < V; ++v) d[v] = y[v] > 0.f ? d[v] : 0.f;
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      sg[v] += d[v];
+      sgx[v] += d[v] * ((x[v] - mu[v]) * rs[v]);
+    }
+  }
+  float* pp = part + ((size_t)n * S + sb) * C * 2;
+  block_pair_sums<V>(sg, sgx, sh, C, pp);
+  if (!last_of_image(cnt + n, S, &flag)) return;
+  // per-channel totals (block order), then the group means of gamma-weighted sums
+  float* tot = sh;  // [C][2], reusing the reduction buffer after the barrier below
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    float a = 0.f, e = 0.f;
+    for (int t = 0; t < S; ++t) {
+      const float* q = part + ((size_t)n * S + t) * C * 2 + 2 * c;
+      a += __ldcg(q);
+      e += __ldcg(q + 1);
+    }
+    tot[2 * c] = a;
+    tot[2 * c + 1] = e;
+    b.dbeta_part[(size_t)n * C + c] = a;
+    b.dgamma_part[(size_t)n * C + c] = e;
+  }
+  __syncthreads();
+  const float inv = 1.0f / (float)(2 * HW);
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    const float g0 = b.gamma[2 * g], g1 = b.gamma[2 * g + 1];
+    b.m1[(size_t)n * G + g] = (tot[4 * g] * g0 + tot[4 * g + 2] * g1) * inv;
+    b.m2[(size_t)n * G + g] = (tot[4 * g + 1] * g0 + tot[4 * g + 3] * g1) * inv;
+  }
+  if (threadIdx.x == 0) cnt[n] = 0;
+}
+
+// ---- dz = rstd (g gamma - m1 - xhat m2); optionally g itself (the masked gradient) ----
+template <int V>
+__global__ void __launch_bounds__(kThreads) gn_bwd_apply_kernel(GNBack b, int HW, int C) {
+  const int R = C / V, G = C / 2;
+  const int n = blockIdx.y;
+  const int per = HW * R;
+  const size_t ib = (size_t)n * HW * C;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per; i += gridDim.x * blockDim.x) {
+    const int c0 = (i % R) * V;
+    const size_t o = ib + (size_t)i * V;
+    float d[V], x[V], gm[V], r[V];
+    ldv<V>(b.dy + o, d);
+    ldv<V>(b.z + o, x);
+    ldv<V>(b.gamma + c0, gm);
+    if (b.relu_y) {
+      float y[V];
+      ldv<V>(b.relu_y + o, y);
+#pragma unroll
+      for (int v = 0; v < V; ++v) d[v] = y[v] > 0.f ? d[v] : 0.f;
+      if (b.g_out) stv<V>(b.g_out + o, d);
+    }
+    const size_t gi = (size_t)n * G + c0 / 2;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const float mu = b.mean[gi + v / 2], rs = b.rstd[gi + v / 2];
+      const float xh = (x[v] - mu) * rs;
+      r[v] = rs * (d[v] * gm[v] - b.m1[gi + v / 2] - xh * b.m2[gi + v / 2]);
+    }
+    if (b.dz32) stv<V>(b.dz32 + o, r);
+    if (b.dzop) stv_op<V>(b.dzop, o, r, b.op_bf16);
+  }
+}
+
+int num_sms_cached() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+      sms = 1;
+  }
+  return sms;
+}
+
+bool gn_shape_ok(int C) { return C >= 2 && C % 2 == 0 && C / (C % 4 == 0 ? 4 : 2) <= kThreads; }
+
+// blocks per image: enough for ~8 blocks per SM overall, at least one pixel pass each
+int gn_split(int N, int HW, int C, const GnScratch& w) {
+  const int V = C % 4 == 0 ? 4 : 2;
+  const int P = rows_per_pass(C, V);
+  const int want = (8 * num_sms_cached() + N - 1) / N;
+  int S = std::min(want, (HW + P - 1) / P);
+  S = std::min(S, 64);
+  S = std::max(S, 1);
+  while (S > 1 && (size_t)N * S * C * 2 > w.part_elems) --S;
+  return S;
+}
+
+unsigned apply_blocks(int N, int HW, int C, int V) {
+  const long per = (long)HW * (C / V);
+  const int want = (8 * num_sms_cached() + N - 1) / N;
+  long bx = (per + kThreads - 1) / kThreads;
+  bx = std::min<long>(bx, std::max(want, 1));
+  return (unsigned)std::max<long>(bx, 1);
+}
+
+int threads_for(int C, int V) {
+  const int R = C / V;
+  return R * rows_per_pass(C, V);
+}
+
+}  // namespace
+
+size_t gn_part_elems(int max_images, int max_C) {
+  return (size_t)(max_images + 8 * num_sms_cached() + 64) * max_C * 2;
+}
+
+int launch_gn_stats(const float* z, int N, int HW, int C, float eps, float* mean, float* rstd,
+                    const GnScratch& w, cudaStream_t s) {
+  if (!N || !HW) return DDPPO_OK;
+  if (!gn_shape_ok(C) || N > w.max_images || N > 65535) {
+    set_error("gn: unsupported channel count or too many images for the scratch");
+    return DDPPO_E_CONFIG;
+  }
+  const int V = C % 4 == 0 ? 4 : 2;
+  const int S = gn_split(N, HW, C, w);
+  const int th = threads_for(C, V);
+  const size_t smem = (size_t)th * 2 * V * sizeof(float);
+  const dim3 grid(S, N);
+  if (V == 4) gn_stats_kernel<4><<<grid, th, smem, s>>>(z, HW, C, S, eps, w.part, w.cnt, mean, rstd);
+  else gn_stats_kernel<2><<<grid, th, smem, s>>>(z, HW, C, S, eps, w.part, w.cnt, mean, rstd);
+  DDPPO_CHECK_LAUNCH();
+  return DDPPO_OK;
+}
+
+int launch_gn_apply(const GNApply& a, int N, int HW, int C, cudaStream_t s) {
+  if (!N || !HW) return DDPPO_OK;
+  if (!gn_shape_ok(C) || N > 65535) { set_error("gn: unsupported shape"); return DDPPO_E_CONFIG; }
+  const int V = C % 4 == 0 ? 4 : 2;
+  const dim3 grid(apply_blocks(N, HW, C, V), N);
+  if (V == 4) gn_apply_kernel<4><<<grid, kThreads, 0, s>>>(a, HW, C);
+  else gn_apply_kernel<2><<<grid, kThreads, 0, s>>>(a, HW, C);
+  DDPPO_CHECK_LAUNCH();
+  return DDPPO_OK;
+}
+
+int launch_gn_bwd(const GNBack& b, int N, int HW, int C, const GnScratch& w, cudaStream_t s) {
+  if (!N || !HW) return DDPPO_OK;
+  if (!gn_shape_ok(C) || N > w.max_images || N > 65535) {
+    set_error("gn: unsupported channel count or too many images for the scratch");
+    return DDPPO_E_CONFIG;
+  }
+  const int V = C % 4 == 0 ? 4 : 2;
+  const int S = gn_split(N, HW, C, w);
+  const int th = threads_for(C, V);
+  const size_t smem = std::max((size_t)th * 2 * V, (size_t)2 * C) * sizeof(float);
+  const dim3 grid(S, N);
+  if (V == 4) gn_bwd_reduce_kernel<4><<<grid, th, smem, s>>>(b, HW, C, S, w.part, w.cnt);
+  else gn_bwd_reduce_kernel<2><<<grid, th, smem, s>>>(b, HW, C, S, w.part, w.cnt);
+  DDPPO_CHECK_LAUNCH();
+  const dim3 ga(apply_blocks(N, HW, C, V), N);
+  if (V == 4) gn_bwd_apply_kernel<4><<<ga, kThreads, 0, s>>>(b, HW, C);
+  else gn_bwd_apply_kernel<2><<<ga, kThreads, 0, s>>>(b, HW, C);
+  DDPPO_CHECK_LAUNCH();
+  return DDPPO_OK;
+}
+
+}  // namespace ddppo

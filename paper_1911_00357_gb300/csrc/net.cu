@@ -201,6 +201,15 @@ static int alloc_encoder(Net& n) {
   const int C = std::max(n.max_gnC, 64);
   DDPPO_TRY(nalloc(n, &n.gnp_g, NC * C));
   DDPPO_TRY(nalloc(n, &n.gnp_b, NC * C));
+  if (n.kind == 1) {
+    n.gnw.max_images = (int)NC;
+    n.gnw.part_elems = gn_part_elems((int)NC, C);
+    DDPPO_TRY(nalloc(n, &n.gnw.part, n.gnw.part_elems));
+    DDPPO_TRY(nalloc(n, &n.gnw.cnt, NC));
+    DDPPO_CHECK_CUDA(cudaMemset(n.gnw.cnt, 0, NC * sizeof(int)));
+    DDPPO_TRY(nalloc(n, &n.gn_m1, NC * C / 2));
+    DDPPO_TRY(nalloc(n, &n.gn_m2, NC * C / 2));
+  }
   return DDPPO_OK;
 }
 
@@ -484,13 +493,13 @@ static int gn_fwd(Net& n, GNL& g, const float* z, int N, int HW, float* out, boo
                   const float* resid, const GNL* gd, const float* zd, cudaStream_t s,
                   __nv_bfloat16* out_bf = nullptr) {
   const float eps = 1e-5f;
-  DDPPO_TRY(launch_gn_stats(z, N, HW, g.C, eps, g.mean, g.rstd, s));
+  DDPPO_TRY(launch_gn_stats(z, N, HW, g.C, eps, g.mean, g.rstd, n.gnw, s));
   GNApply a{};
   a.z = z; a.mean = g.mean; a.rstd = g.rstd;
   a.gamma = n.params + g.g_off; a.beta = n.params + g.b_off;
   a.resid = resid;
   if (gd) {
-    DDPPO_TRY(launch_gn_stats(zd, N, HW, gd->C, eps, gd->mean, gd->rstd, s));
+    DDPPO_TRY(launch_gn_stats(zd, N, HW, gd->C, eps, gd->mean, gd->rstd, n.gnw, s));
     a.zd = zd; a.mean_d = gd->mean; a.rstd_d = gd->rstd;
     a.gamma_d = n.params + gd->g_off; a.beta_d = n.params + gd->b_off;
   }
@@ -500,10 +509,17 @@ static int gn_fwd(Net& n, GNL& g, const float* z, int N, int HW, float* out, boo
   return launch_gn_apply(a, N, HW, g.C, s);
 }
 
+// GroupNorm backward into n.dzop (op dtype). relu_y: the output of the ReLU that followed
+// the normalisation (its mask is applied to dy here); g_out receives the masked gradient.
 static int gn_bwd(Net& n, GNL& g, const float* dy, const float* z, int N, int HW, bool first,
-                  cudaStream_t s) {
-  DDPPO_TRY(launch_gn_bwd(dy, z, g.mean, g.rstd, n.params + g.g_off, N, HW, g.C, nullptr, n.dzop,
-                          n.bf, n.gnp_g, n.gnp_b, s));
+                  cudaStream_t s, const float* relu_y = nullptr, float* g_out = nullptr) {
+  GNBack b{};
+  b.dy = dy; b.relu_y = relu_y; b.g_out = g_out;
+  b.z = z; b.mean = g.mean; b.rstd = g.rstd; b.gamma = n.params + g.g_off;
+  b.m1 = n.gn_m1; b.m2 = n.gn_m2;
+  b.dzop = n.dzop; b.op_bf16 = n.bf;
+  b.dgamma_part = n.gnp_g; b.dbeta_part = n.gnp_b;
+  DDPPO_TRY(launch_gn_bwd(b, N, HW, g.C, n.gnw, s));
   DDPPO_TRY(launch_colsum(n.gnp_g, N, g.C, g.C, n.grad + g.g_off, !first, s));
   DDPPO_TRY(launch_colsum(n.gnp_b, N, g.C, g.C, n.grad + g.b_off, !first, s));
   return DDPPO_OK;
@@ -564,13 +580,10 @@ static int encoder_bwd(Net& n, const void* obs, int N, const float* dfeat_rows, 
     return DDPPO_OK;
   }
   // compression conv
-  {
-    const size_t cnt = (size_t)N * n.F;
-    DDPPO_TRY(launch_relu_bwd(dfeat_rows, n.cmp_n.out, cnt, n.g0, nullptr, n.bf, s));
-    DDPPO_TRY(gn_bwd(n, n.cmp_n, n.g0, n.cmp.z, N, n.featHW, first, s));
-    DDPPO_TRY(conv_bwd(n, n.cmp, n.blocks[7].y, false, N, n.dzop, n.g1, false, first, s,
-                       n.blocks[7].y_bf));
-  }
+  DDPPO_TRY(gn_bwd(n, n.cmp_n, dfeat_rows, n.cmp.z, N, n.featHW, first, s, n.cmp_n.out));
+  DDPPO_TRY(conv_bwd(n, n.cmp, n.blocks[7].y, false, N, n.dzop, n.g1, false, first, s,
+                     n.blocks[7].y_bf));
+  // residual blocks, last to first. gcur: gradient of the block output (before its ReLU)
   float* gcur = n.g1;
   float* gA = n.g0;
   float* gB = n.g2;
@@ -579,27 +592,24 @@ static int encoder_bwd(Net& n, const void* obs, int N, const float* dfeat_rows, 
     const int HW = B.c1.Ho * B.c1.Wo;
     const float* xin = bi > 0 ? n.blocks[bi - 1].y : n.pool;
     const __nv_bfloat16* xin_bf = bi > 0 ? n.blocks[bi - 1].y_bf : n.pool_bf;
-    const size_t cnt = (size_t)N * HW * B.c2.cout;
-    DDPPO_TRY(launch_relu_bwd(gcur, B.y, cnt, gcur, nullptr, n.bf, s));  // grad of the pre-ReLU sum
-    DDPPO_TRY(gn_bwd(n, B.n2, gcur, B.c2.z, N, HW, first, s));
+    // the ReLU after the sum masks gcur; with an identity skip the masked gradient is
+    // kept (written back in place) and the first conv's input gradient accumulates onto it
+    DDPPO_TRY(gn_bwd(n, B.n2, gcur, B.c2.z, N, HW, first, s, B.y, B.down ? nullptr : gcur));
     DDPPO_TRY(conv_bwd(n, B.c2, B.n1.out, false, N, n.dzop, gA, false, first, s, B.n1.out_bf));
-    DDPPO_TRY(launch_relu_bwd(gA, B.n1.out, cnt, gA, nullptr, n.bf, s));
-    DDPPO_TRY(gn_bwd(n, B.n1, gA, B.c1.z, N, HW, first, s));
-    DDPPO_TRY(conv_bwd(n, B.c1, xin, false, N, n.dzop, gB, false, first, s, xin_bf));
+    DDPPO_TRY(gn_bwd(n, B.n1, gA, B.c1.z, N, HW, first, s, B.n1.out));
     if (B.down) {
-      DDPPO_TRY(gn_bwd(n, B.nd, gcur, B.d.z, N, HW, first, s));
+      DDPPO_TRY(conv_bwd(n, B.c1, xin, false, N, n.dzop, gB, false, first, s, xin_bf));
+      DDPPO_TRY(gn_bwd(n, B.nd, gcur, B.d.z, N, HW, first, s, B.y));
       DDPPO_TRY(conv_bwd(n, B.d, xin, false, N, n.dzop, gB, true, first, s, xin_bf));
+      float* t = gcur; gcur = gB; gB = t;
     } else {
-      DDPPO_TRY(launch_add(gB, gcur, (size_t)N * B.c1.H * B.c1.W * B.c1.cin, s));
+      DDPPO_TRY(conv_bwd(n, B.c1, xin, false, N, n.dzop, gcur, true, first, s, xin_bf));
     }
-    float* t = gcur; gcur = gB; gB = t;
   }
   // max pool, stem GN + ReLU, stem conv (no input gradient)
   ConvL& st = n.stem;
   DDPPO_TRY(launch_maxpool_bwd(gcur, n.pool_arg, N, st.Ho, st.Wo, st.cout, gA, s));
-  const size_t cnt = (size_t)N * st.Ho * st.Wo * st.cout;
-  DDPPO_TRY(launch_relu_bwd(gA, n.stem_n.out, cnt, gA, nullptr, n.bf, s));
-  DDPPO_TRY(gn_bwd(n, n.stem_n, gA, st.z, N, st.Ho * st.Wo, first, s));
+  DDPPO_TRY(gn_bwd(n, n.stem_n, gA, st.z, N, st.Ho * st.Wo, first, s, n.stem_n.out));
   DDPPO_TRY(conv_bwd(n, st, obs, n.bf, N, n.dzop, nullptr, false, first, s));
   return DDPPO_OK;
 }

@@ -6,6 +6,7 @@
 
 #include "ctx.cuh"
 #include "gemm.cuh"
+#include "nn_kernels.cuh"
 
 namespace ddppo {
 
@@ -98,6 +99,8 @@ struct Net {
   void* dzop = nullptr;
   float* g0 = nullptr; float* g1 = nullptr; float* g2 = nullptr;
   float* gnp_g = nullptr; float* gnp_b = nullptr;
+  GnScratch gnw;                              // GroupNorm partial sums + arrival counters
+  float* gn_m1 = nullptr; float* gn_m2 = nullptr;  // [NC, C/2] backward group means
   void* featop = nullptr; float* dfeat = nullptr; void* featT = nullptr;
   void* x1 = nullptr;
   float* gx = nullptr; float* gh = nullptr;

@@ -467,6 +467,18 @@ extern "C" int ddppo_autotune(ddppo_ctx* x, int32_t on, int64_t* tuned_shapes) {
   return DDPPO_OK;
 }
 
+extern "C" int ddppo_autotune_export(ddppo_ctx* x, void* buf, size_t cap, size_t* size) {
+  ARG(x && x->net && size, "autotune_export: null argument");
+  *size = tc_tuner_export(x->net->gws.tuner, buf, cap);
+  ARG(!buf || cap >= *size, "autotune_export: buffer too small");
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_autotune_import(ddppo_ctx* x, const void* buf, size_t size) {
+  ARG(x && x->net && buf, "autotune_import: null argument");
+  return tc_tuner_import(x->net->gws.tuner, buf, size);
+}
+
 // ---- stand-alone convolution on the implicit-im2col tensor-core path ----
 extern "C" int ddppo_conv2d(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, int32_t k,
                             int32_t stride, int32_t pad, const void* x, const void* w, float* y,

@@ -324,145 +324,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 // t % C and reads pixels t / C, t / C + blockDim / C, ... -- consecutive threads read
 // consecutive channels of a pixel (coalesced). Two passes (mean, then the centred second
 // moment); per-channel sums combine in shared memory in a fixed order.
-__device__ __forceinline__ void block_channel_sums(float v, float* sh, int C, float* out_c) {
-  // sh: [blockDim] ; out_c: [C] sums over the threads owning each channel
-  sh[threadIdx.x] = v;
-  __syncthreads();
-  if ((int)threadIdx.x < C) {
-    float t = 0.f;
-    for (int j = threadIdx.x; j < (int)blockDim.x; j += C) t += sh[j];
-    out_c[threadIdx.x] = t;
-  }
-  __syncthreads();
-}
 
-__global__ void gn_stats_kernel(const float* __restrict__ z, int N, int HW, int C, float eps,
-                                float* __restrict__ mean, float* __restrict__ rstd) {
-  extern __shared__ float gsh[];
-  float* sh = gsh;                  // [blockDim]
-  float* cs = gsh + blockDim.x;     // [C]
-  float* gm = cs + C;               // [C/2] group means
-  const int n = blockIdx.x, c = threadIdx.x % C, p0 = threadIdx.x / C, ps = blockDim.x / C;
-  const float* zi = z + (size_t)n * HW * C;
-  float acc = 0.f;
-  for (int p = p0; p < HW; p += ps) acc += zi[(size_t)p * C + c];
-  block_channel_sums(acc, sh, C, cs);
-  const int G = C / 2;
-  const float inv = 1.0f / (float)(2 * HW);
-  if ((int)threadIdx.x < G) gm[threadIdx.x] = (cs[2 * threadIdx.x] + cs[2 * threadIdx.x + 1]) * inv;
-  __syncthreads();
-  const float mu = gm[c >> 1];
-  float q = 0.f;
-  for (int p = p0; p < HW; p += ps) {
-    const float d = zi[(size_t)p * C + c] - mu;
-    q += d * d;
-  }
-  block_channel_sums(q, sh, C, cs);
-  if ((int)threadIdx.x < G) {
-    const float var = (cs[2 * threadIdx.x] + cs[2 * threadIdx.x + 1]) * inv;
-    mean[(size_t)n * G + threadIdx.x] = gm[threadIdx.x];
-    rstd[(size_t)n * G + threadIdx.x] = 1.0f / sqrtf(var + eps);
-  }
-}
-
-static int gn_threads(int C) { return C > 256 ? C : 256; }
-
-int launch_gn_stats(const float* z, int N, int HW, int C, float eps, float* mean, float* rstd,
-                    cudaStream_t s) {
-  if (!N) return DDPPO_OK;
-  const int th = gn_threads(C);
-  if (C > 1024 || th % C) { set_error("gn: channel count must divide the block"); return DDPPO_E_CONFIG; }
-  gn_stats_kernel<<<N, th, (th + C + C / 2) * sizeof(float), s>>>(z, N, HW, C, eps, mean, rstd);
-  DDPPO_CHECK_LAUNCH();
-  return DDPPO_OK;
-}
-
-__global__ void gn_apply_kernel(GNApply a, int N, int HW, int C) {
-  const size_t total = (size_t)N * HW * C;
-  const int G = C / 2;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (size_t)gridDim.x * blockDim.x) {
-    const int c = (int)(idx % C);
-    const int n = (int)(idx / ((size_t)HW * C));
-    const int ng = n * G + c / 2;
-    float v = (a.z[idx] - a.mean[ng]) * a.rstd[ng] * a.gamma[c] + a.beta[c];
-    if (a.resid) v += a.resid[idx];
-    if (a.zd) v += (a.zd[idx] - a.mean_d[ng]) * a.rstd_d[ng] * a.gamma_d[c] + a.beta_d[c];
-    if (a.relu) v = fmaxf(v, 0.f);
-    a.out[idx] = v;
-    if (a.out_bf) a.out_bf[idx] = __float2bfloat16_rn(v);
-  }
-}
-
-int launch_gn_apply(const GNApply& a, int N, int HW, int C, cudaStream_t s) {
-  const size_t total = (size_t)N * HW * C;
-  if (!total) return DDPPO_OK;
-  gn_apply_kernel<<<grid_for(total), 256, 0, s>>>(a, N, HW, C);
-  DDPPO_CHECK_LAUNCH();
-  return DDPPO_OK;
-}
-
-// GroupNorm backward, one block per image (same thread layout as the statistics):
-//   xhat = (z - mu) rstd ; dxhat = dy gamma
-//   dz = rstd (dxhat - mean_g(dxhat) - xhat mean_g(dxhat xhat))
-//   dgamma_part[n, c] = sum dy xhat ; dbeta_part[n, c] = sum dy
-__global__ void gn_bwd_kernel(const float* __restrict__ dy, const float* __restrict__ z,
-                              const float* __restrict__ mean, const float* __restrict__ rstd,
-                              const float* __restrict__ gamma, int N, int HW, int C,
-                              float* __restrict__ dz32, void* dzop, int bf,
-                              float* __restrict__ dgp, float* __restrict__ dbp) {
-  extern __shared__ float gsh[];
-  float* sh = gsh;
-  float* cs = gsh + blockDim.x;   // [C]
-  float* m1 = cs + C;             // [C/2] mean_g(dxhat)
-  float* m2 = m1 + C / 2;         // [C/2] mean_g(dxhat xhat)
-  const int n = blockIdx.x, c = threadIdx.x % C, p0 = threadIdx.x / C, ps = blockDim.x / C;
-  const int G = C / 2;
-  const size_t base = (size_t)n * HW * C;
-  const float mu = mean[(size_t)n * G + (c >> 1)], rs = rstd[(size_t)n * G + (c >> 1)];
-  const float gc = gamma[c];
-  float s_dy = 0.f, s_dyx = 0.f;
-  for (int p = p0; p < HW; p += ps) {
-    const size_t o = base + (size_t)p * C + c;
-    const float d = dy[o], xh = (z[o] - mu) * rs;
-    s_dy += d;
-    s_dyx += d * xh;
-  }
-  const float inv = 1.0f / (float)(2 * HW);
-  block_channel_sums(s_dy, sh, C, cs);
-  if ((int)threadIdx.x < C) dbp[(size_t)n * C + threadIdx.x] = cs[threadIdx.x];
-  if ((int)threadIdx.x < G)
-    m1[threadIdx.x] = (cs[2 * threadIdx.x] * gamma[2 * threadIdx.x] +
-                       cs[2 * threadIdx.x + 1] * gamma[2 * threadIdx.x + 1]) * inv;
-  __syncthreads();
-  block_channel_sums(s_dyx, sh, C, cs);
-  if ((int)threadIdx.x < C) dgp[(size_t)n * C + threadIdx.x] = cs[threadIdx.x];
-  if ((int)threadIdx.x < G)
-    m2[threadIdx.x] = (cs[2 * threadIdx.x] * gamma[2 * threadIdx.x] +
-                       cs[2 * threadIdx.x + 1] * gamma[2 * threadIdx.x + 1]) * inv;
-  __syncthreads();
-  const float a1 = m1[c >> 1], a2 = m2[c >> 1];
-  for (int p = p0; p < HW; p += ps) {
-    const size_t o = base + (size_t)p * C + c;
-    const float xh = (z[o] - mu) * rs;
-    const float r = rs * (dy[o] * gc - a1 - xh * a2);
-    if (dz32) dz32[o] = r;
-    if (dzop) st_op(dzop, o, r, bf);
-  }
-}
-
-int launch_gn_bwd(const float* dy, const float* z, const float* mean, const float* rstd,
-                  const float* gamma, int N, int HW, int C, float* dz32, void* dzop, bool op_bf16,
-                  float* dgamma_part, float* dbeta_part, cudaStream_t s) {
-  if (!N) return DDPPO_OK;
-  const int th = gn_threads(C);
-  if (C > 1024 || th % C) { set_error("gn: channel count must divide the block"); return DDPPO_E_CONFIG; }
-  gn_bwd_kernel<<<N, th, (th + 2 * C) * sizeof(float), s>>>(dy, z, mean, rstd, gamma, N, HW, C,
-                                                           dz32, dzop, op_bf16 ? 1 : 0,
-                                                           dgamma_part, dbeta_part);
-  DDPPO_CHECK_LAUNCH();
-  return DDPPO_OK;
-}
 
 // ---------------------------------------------------------------- ReLU backward, add
 __global__ void relu_bwd_kernel(const float* dy, const float* __restrict__ y, size_t n, float* dz32,

@@ -25,10 +25,21 @@ int launch_transpose(const void* in, bool in_bf16, void* out, bool out_bf16, int
 // fp32 -> op dtype copy (or plain copy)
 int launch_cast(const float* in, void* out, bool out_bf16, size_t n, cudaStream_t s);
 
-// GroupNorm with groups of 2 channels (C/2 groups), eps
+// GroupNorm with groups of 2 channels (C/2 groups), split over several blocks per image
+// (gn.cu). Scratch shared by the launches of one stream: partial sums and per-image
+// arrival counters (zero at allocation; every launch leaves them zero).
+struct GnScratch {
+  float* part = nullptr;  // gn_part_elems(max_images, max_C) floats
+  size_t part_elems = 0;
+  int* cnt = nullptr;     // [max_images], zeroed once
+  int max_images = 0;
+};
+size_t gn_part_elems(int max_images, int max_C);
+// C even, C / V <= 256 (V = 4 when C % 4 == 0, else 2): C <= 1024
 int launch_gn_stats(const float* z, int N, int HW, int C, float eps, float* mean, float* rstd,
-                    cudaStream_t s);
-// out = act(gn(z) + res) with res = 0, resid (fp32), or gn(zd) (a second normalised input)
+                    const GnScratch& w, cudaStream_t s);
+// out = act(gn(z) + res) with res = 0, resid (fp32), or gn(zd) (a second normalised input);
+// out (fp32) and out_bf (bf16) each optional
 struct GNApply {
   const float* z; const float* mean; const float* rstd; const float* gamma; const float* beta;
   const float* resid;  // or null
@@ -37,11 +48,19 @@ struct GNApply {
   __nv_bfloat16* out_bf;  // optional bf16 copy of out (the next convolution's TMA operand)
 };
 int launch_gn_apply(const GNApply& a, int N, int HW, int C, cudaStream_t s);
-// GroupNorm backward: dy (fp32, grad of the GN output) -> dz (fp32 and/or op dtype),
-// per-image channel partials of dgamma/dbeta [N, C]
-int launch_gn_bwd(const float* dy, const float* z, const float* mean, const float* rstd,
-                  const float* gamma, int N, int HW, int C, float* dz32, void* dzop, bool op_bf16,
-                  float* dgamma_part, float* dbeta_part, cudaStream_t s);
+// GroupNorm backward. g = dy, masked by (relu_y > 0) when relu_y is given (the ReLU that
+// followed the normalisation); g_out (optional, with relu_y) receives g.
+//   dz = rstd (g gamma - m1 - xhat m2), m1 / m2 the group means of gamma g and gamma g xhat;
+//   dgamma_part[n, c] = sum g xhat, dbeta_part[n, c] = sum g (per image).
+// m1, m2: [N, C/2] scratch. dz32 (fp32) and dzop (op dtype) each optional.
+struct GNBack {
+  const float* dy; const float* relu_y; float* g_out;
+  const float* z; const float* mean; const float* rstd; const float* gamma;
+  float* m1; float* m2;
+  float* dz32; void* dzop; bool op_bf16;
+  float* dgamma_part; float* dbeta_part;
+};
+int launch_gn_bwd(const GNBack& b, int N, int HW, int C, const GnScratch& w, cudaStream_t s);
 
 // dz = dy * (y > 0) written as fp32 (dz32) and/or op dtype (dzop); dy may equal dz32
 int launch_relu_bwd(const float* dy, const float* y, size_t n, float* dz32, void* dzop, bool op_bf16,
