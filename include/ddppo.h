@@ -319,6 +319,18 @@ int ddppo_gemm(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const void* A, 
 int ddppo_conv2d(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, int32_t k,
                  int32_t stride, int32_t pad, const void* x, const void* w, float* y,
                  int32_t* status, void* stream);
+/* The weight gradient of that convolution without an im2col matrix (the backward pass of
+ * Sec. 4's encoder): dw[co, (ky*k + kx)*C + c] = beta dw + sum over n, oy, ox of
+ * dy[n, oy, ox, co] x[n, oy*s - p + ky, ox*s - p + kx, c] (zero outside the image).
+ * The GEMM's reduction runs over output pixels in 64-pixel blocks, each gathered per
+ * filter tap with a 4-D TMA copy. x [dev] NHWC bf16 [N, H, W, C]; dy [dev] bf16
+ * [N, Ho, Wo, Cout]; dw [dev] fp32 [Cout, k*k*C]. Requires C == 32 or C % 64 == 0,
+ * Cout % 8 == 0, an output width dividing 64 and whole 64-pixel blocks (Ho*Wo a multiple
+ * of 64 made of whole rows, or a divisor of 64); E_CONFIG otherwise. status and the
+ * workspace as for ddppo_conv2d. */
+int ddppo_conv2d_wgrad(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, int32_t k,
+                       int32_t stride, int32_t pad, const void* x, const void* dy, float* dw,
+                       float beta, int32_t* status, void* stream);
 /* Whether ddppo_gemm with these operands runs on the tensor cores (1) or SIMT (0). */
 int ddppo_gemm_backend(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const void* A,
                        int32_t lda, const void* B, int32_t ldb, int32_t* tensor_cores);

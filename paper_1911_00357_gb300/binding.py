@@ -112,6 +112,7 @@ _SIGS = {
     "ddppo_autotune_export": [P, P, ctypes.c_size_t, P],
     "ddppo_autotune_import": [P, P, ctypes.c_size_t],
     "ddppo_conv2d": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, P, P],
+    "ddppo_conv2d_wgrad": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, F32, P, P],
 }
 
 
@@ -342,6 +343,15 @@ def ddppo_autotune_export(h) -> bytes:
 def ddppo_autotune_import(h, image: bytes) -> None:
     buf = ctypes.create_string_buffer(bytes(image), len(image))
     _check(lib().ddppo_autotune_import(h, buf, len(image)))
+
+
+def ddppo_conv2d_wgrad(x, dy, dw, k: int, stride: int, pad: int, beta: float = 0.0, status=None):
+    """dw (+)= the weight gradient of conv(x, w) for output gradient dy, on the implicit
+    weight-gradient path. x NHWC bf16 [N, H, W, C]; dy bf16 [N, Ho, Wo, Cout];
+    dw fp32 [Cout, k*k*C] (K ordered ky, kx, c)."""
+    N, H, W, C = x.shape
+    _check(lib().ddppo_conv2d_wgrad(N, H, W, C, dy.shape[3], k, stride, pad, _p(x), _p(dy), _p(dw),
+                                    beta, _p(status), _s()))
 
 
 def ddppo_conv2d(x, w, y, k: int, stride: int, pad: int, status=None):

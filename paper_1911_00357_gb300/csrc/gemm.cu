@@ -152,11 +152,18 @@ int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t 
     set_error("gemm: implicit convolution not supported for this shape");
     return DDPPO_E_CONFIG;
   }
+  if (d.convw && !(op_bf16 && !d.conv && d.a_t && d.lda == d.M && d.lda % 8 == 0 && !d.c_bf16 && !d.bias && !d.relu &&
+                   d.N == d.convw->k * d.convw->k * d.convw->C &&
+                   d.K == d.convw->N * d.convw->Ho * d.convw->Wo &&
+                   gemm_convw_supported(*d.convw, d.B, d.A))) {
+    set_error("gemm: implicit weight gradient not supported for this shape");
+    return DDPPO_E_CONFIG;
+  }
   const bool rec = timer && timer->on && timer->n + 2 <= 2 * 4096;
   if (timer && timer->on) timer->flops_all += 2.0 * d.M * d.N * d.K;
   if (rec) cudaEventRecord(timer->ev[timer->n], s);
   int rc;
-  if (op_bf16 && (d.conv || gemm_tc_supported(d))) {
+  if (op_bf16 && (d.conv || d.convw || gemm_tc_supported(d))) {
     rc = gemm_tc(d, ws, s);
     if (ws.tc && ws.tc->on) {
       ws.tc->launches += 1;
@@ -171,9 +178,11 @@ int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t 
     timer->work[timer->n / 2] = 2.0 * d.M * d.N * d.K;
     // operands read once, result written once (and read when accumulating); an implicit
     // convolution reads its input tensor, not the M x K patch matrix
-    const double a_elems = d.conv ? (double)d.conv->N * d.conv->H * d.conv->W * d.conv->C
-                                  : (double)d.M * d.K;
-    timer->bytes[timer->n / 2] = (a_elems + (double)d.N * d.K) * es +
+    const ConvShape* cv = d.conv ? d.conv : d.convw;
+    const double in_elems = cv ? (double)cv->N * cv->H * cv->W * cv->C : 0.0;
+    const double a_elems = d.conv ? in_elems : (double)d.M * d.K;
+    const double b_elems = d.convw ? in_elems : (double)d.N * d.K;
+    timer->bytes[timer->n / 2] = (a_elems + b_elems) * es +
                                  (double)d.M * d.N * cs * (d.beta != 0.f ? 2.0 : 1.0);
     timer->n += 2;
     timer->flops += 2.0 * d.M * d.N * d.K;

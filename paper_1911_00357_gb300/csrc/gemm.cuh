@@ -20,6 +20,10 @@ struct ConvShape {
 struct GemmDesc {
   int M = 0, N = 0, K = 0;
   const ConvShape* conv = nullptr;  // non-null: A is the convolution input (NHWC bf16)
+  // non-null: the weight gradient of a convolution, dW[co, (ky, kx, c)] (+)= sum over output
+  // pixels m of dz[m, co] x[m shifted by (ky, kx), c]: M = cout, N = k*k*C, K = pixels,
+  // A = dz stored [K][M] (a_t = 1, lda = M), B = the convolution input (NHWC bf16)
+  const ConvShape* convw = nullptr;
   const void* A = nullptr;
   int lda = 0;
   const void* B = nullptr;
@@ -87,5 +91,7 @@ bool gemm_tc_supported(const GemmDesc& d);
 // whether the implicit-im2col path covers this convolution (C % 32 == 0, output rows that
 // tile 128-pixel blocks, 16-byte aligned input)
 bool gemm_conv_supported(const ConvShape& c, const void* input);
+// the implicit weight-gradient gather (64-pixel K blocks) handles this shape
+bool gemm_convw_supported(const ConvShape& c, const void* input, const void* dz);
 
 }  // namespace ddppo

@@ -113,14 +113,30 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
   return d;
 }
 
-// implicit-im2col parameters of a convolution A operand (passed by value to the kernel)
+// implicit-im2col parameters of a convolution A operand (passed by value to the kernel).
+// on = 1: forward / input-gradient convolution, A = [output pixels, (tap, channel)] K-major,
+//         one box of cbw channels x 128 pixels per K block;
+// on = 2: weight gradient, A = [(tap, channel), output pixels] MN-major: per 64-pixel K
+//         block, 128 / cbw boxes of 64 pixels x cbw channels (one per tap / channel block).
 struct ConvA {
   int on = 0;
   int C = 0, cbw = 64;       // input channels, channels per K-block (64 or 32)
   int k = 1, s = 1, p = 0;
   int Ho = 1, Wo = 1;
-  int hi = 1;                // output rows per 128-pixel tile (or Ho when a tile spans images)
+  int hi = 1;                // output rows per pixel block (or Ho when a block spans images)
 };
+
+// MN-major tile with 64-byte rows (32 MN-elements), 64-byte swizzle: blocks of 32 MN
+// columns 64 rows (4 KiB) apart (LBO), 8-row K groups 512 B apart (SBO)
+__device__ __forceinline__ uint64_t sw64_mn_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)(4096 >> 4) << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
 
 // shared-memory matrix descriptors, 128-byte swizzle.
 // K-major tile: rows of 64 K-elements (128 B), 8-row groups 1024 B apart (SBO); the K
@@ -203,16 +219,23 @@ __global__ void __launch_bounds__(TC_PTHREADS, 1)
   if (warp == 0) {
     if (lane == 0) {
       // TMA producer over every (tile, k-block) of this CTA
-      const int kstep = ca.on ? ca.cbw : TC_BK;
-      const uint32_t tx = (uint32_t)(TC_BM + BN) * kstep * 2;
+      const int kstep = ca.on == 1 ? ca.cbw : TC_BK;
+      uint32_t tx = (uint32_t)(TC_BM + BN) * kstep * 2;
       uint32_t it = 0;
       for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
         const int tm = t % tiles_m, tn = (t / tiles_m) % tiles_n, z = t / (tiles_m * tiles_n);
         const int m0 = tm * TC_BM, n0 = tn * BN;
         const int kbeg = z * kchunk, kend = min(K, kbeg + kchunk);
         const int nkb = (kend - kbeg + kstep - 1) / kstep;
+        // weight gradient: boxes of this tile's (tap, channel) rows that exist (rows >= M
+        // are left unloaded; their accumulator rows are never stored)
+        int nbox = 0;
+        if (ca.on == 2) {
+          nbox = min(TC_BM / ca.cbw, (M - m0 + ca.cbw - 1) / ca.cbw);
+          tx = (uint32_t)BN * TC_BK * 2 + (uint32_t)nbox * 64 * ca.cbw * 2;
+        }
         int img = 0, oy0 = 0;
-        if (ca.on) {
+        if (ca.on == 1) {
           const int pix = ca.Ho * ca.Wo;
           img = m0 / pix;
           oy0 = (m0 - img * pix) / ca.Wo;
@@ -223,6 +246,21 @@ __global__ void __launch_bounds__(TC_PTHREADS, 1)
           if (!mbar_wait(&ctl.empty[s], ph ^ 1u, abort, err)) break;
           mbar_expect_tx(&ctl.full[s], tx);
           const int k = kbeg + kb * kstep;
+          if (ca.on == 2) {
+            const int pix = ca.Ho * ca.Wo;
+            const int im = k / pix, oy = (k - im * pix) / ca.Wo;
+            for (int j = 0; j < nbox; ++j) {
+              const int kk = m0 + j * ca.cbw;
+              const int tap = kk / ca.C, c0 = kk - tap * ca.C;
+              const int ky = tap / ca.k, kx = tap - ky * ca.k;
+              tma_load_4d(sA + s * A_BYTES + j * (64 * ca.cbw * 2), &mapA, &ctl.full[s], c0,
+                          kx - ca.p, oy * ca.s - ca.p + ky, im);
+            }
+#pragma unroll
+            for (int j = 0; j < BN / 64; ++j)
+              tma_load_2d(sB + s * B_BYTES + j * 8192, &mapB, &ctl.full[s], n0 + 64 * j, k);
+            continue;
+          }
           if (ca.on) {
             // A: the input box of this filter tap and channel block (zero outside the image)
             const int tap = k / ca.C, c0 = k - tap * ca.C;
@@ -252,8 +290,9 @@ __global__ void __launch_bounds__(TC_PTHREADS, 1)
     if (lane == 0) {
       // MMA issuer
       const uint32_t idesc = f16_idesc(TC_BM, BN, a_mn, b_mn);
-      const int kstep = ca.on ? ca.cbw : TC_BK;
-      const bool sw64 = ca.on && ca.cbw == 32;
+      const int kstep = ca.on == 1 ? ca.cbw : TC_BK;
+      const bool sw64 = ca.on == 1 && ca.cbw == 32;
+      const bool a_sw64_mn = ca.on == 2 && ca.cbw == 32;
       uint32_t it = 0, ti = 0;
       for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x, ++ti) {
         const int z = t / (tiles_m * tiles_n);
@@ -274,6 +313,9 @@ __global__ void __launch_bounds__(TC_PTHREADS, 1)
             if (sw64) {
               da = sw64_desc(a0 + k * 32);
               db = sw64_desc(b0 + k * 32);
+            } else if (a_sw64_mn) {
+              da = sw64_mn_desc(a0 + k * 1024);
+              db = sw128_mn_desc(b0 + k * 2048);
             } else {
               da = a_mn ? sw128_mn_desc(a0 + k * 2048) : sw128_desc(a0 + k * 32);
               db = b_mn ? sw128_mn_desc(b0 + k * 2048) : sw128_desc(b0 + k * 32);
@@ -448,6 +490,47 @@ static bool make_conv_map(CUtensorMap* m, const void* x, const ConvShape& c, con
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// weight-gradient gather: 64-pixel K blocks of whole output rows (or whole images)
+static bool convw_geom(const ConvShape& c, int* hi, int* ni) {
+  if (c.Wo < 1 || c.Ho < 1 || 64 % c.Wo) return false;
+  const int pix = c.Ho * c.Wo;
+  if (pix >= 64) {
+    *hi = 64 / c.Wo;
+    *ni = 1;
+    if (c.Ho % *hi) return false;
+  } else {
+    if (64 % pix) return false;
+    *hi = c.Ho;
+    *ni = 64 / pix;
+  }
+  return *hi * c.s <= 256 && c.Wo * c.s <= 256;
+}
+
+static bool make_convw_map(CUtensorMap* m, const void* x, const ConvShape& c, int cbw) {
+  auto fn = encode_fn();
+  int hi = 0, ni = 0;
+  if (!fn || !convw_geom(c, &hi, &ni)) return false;
+  cuuint64_t dims[4] = {(cuuint64_t)c.C, (cuuint64_t)c.W, (cuuint64_t)c.H, (cuuint64_t)c.N};
+  cuuint64_t strides[3] = {(cuuint64_t)c.C * 2, (cuuint64_t)c.W * c.C * 2,
+                           (cuuint64_t)c.H * c.W * c.C * 2};
+  cuuint32_t box[4] = {(cuuint32_t)cbw, (cuuint32_t)(c.Wo * c.s), (cuuint32_t)(hi * c.s),
+                       (cuuint32_t)ni};
+  cuuint32_t estr[4] = {1, (cuuint32_t)c.s, (cuuint32_t)c.s, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(x), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE,
+            cbw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+bool gemm_convw_supported(const ConvShape& c, const void* input, const void* dz) {
+  if (!encode_fn()) return false;
+  if (!(c.C == 32 || (c.C > 0 && c.C % 64 == 0))) return false;
+  if (((uintptr_t)input & 15) || ((uintptr_t)dz & 15)) return false;
+  if (c.k < 1 || c.s < 1 || c.s > 8 || c.N < 1) return false;
+  int hi = 0, ni = 0;
+  return convw_geom(c, &hi, &ni);
+}
+
 bool gemm_conv_supported(const ConvShape& c, const void* input) {
   if (!encode_fn()) return false;
   if (c.C % 32 || c.C <= 0 || ((uintptr_t)input & 15)) return false;
@@ -513,7 +596,7 @@ int64_t tc_tuner_shapes(const TcTuner* t) { return t ? (int64_t)t->table.size() 
 
 // table image: int32 words {magic, version, count} then count records of 7 key words and
 // 3 configuration words (N tile, ring depth, split policy)
-static const int32_t kTuneMagic = 0x54544444, kTuneVersion = 1, kTuneRec = 10;
+static const int32_t kTuneMagic = 0x54544444, kTuneVersion = 2, kTuneRec = 10;
 
 size_t tc_tuner_export(const TcTuner* t, void* buf, size_t cap) {
   const size_t cnt = t ? t->table.size() : 0;
@@ -585,7 +668,7 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
     splits = (int)min((size_t)splits, ws.partial_elems / max(per, (size_t)1));
     if (splits < 2) splits = 1;
   }
-  const int kstep = ca.on ? ca.cbw : TC_BK;
+  const int kstep = ca.on == 1 ? ca.cbw : TC_BK;
   int kchunk = (K + splits - 1) / splits;
   kchunk = (kchunk + kstep - 1) / kstep * kstep;
   splits = (K + kchunk - 1) / kchunk;
@@ -607,6 +690,23 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
 }
 
 static int run_cfg(const GemmDesc& d, const GemmWorkspace& ws, const TcCfg& cfg, cudaStream_t s) {
+  if (d.convw) {
+    // computed transposed: M' = (tap, channel) rows gathered from the input (MN-major),
+    // N' = output channels from dz [pixels][cout] (MN-major); stored as dW[co][kk]
+    const ConvShape& c = *d.convw;
+    ConvA ca;
+    ca.on = 2;
+    ca.C = c.C;
+    ca.cbw = c.C == 32 ? 32 : 64;
+    ca.k = c.k; ca.s = c.s; ca.p = c.p; ca.Ho = c.Ho; ca.Wo = c.Wo;
+    CUtensorMap ma, mb;
+    if (!make_convw_map(&ma, d.B, c, ca.cbw) || !make_map(&mb, d.A, d.K, d.M, d.lda, TC_BK)) {
+      set_error("gemm_tc: weight-gradient tensor map encoding failed");
+      return DDPPO_E_CUDA;
+    }
+    if (cfg.bn == 128) return launch_tc<128>(ma, mb, d.N, d.M, d.K, d, 1, 1, 1, ws, cfg, ca, s);
+    return launch_tc<64>(ma, mb, d.N, d.M, d.K, d, 1, 1, 1, ws, cfg, ca, s);
+  }
   if (d.conv) {
     const ConvShape& c = *d.conv;
     ConvA ca;
@@ -649,7 +749,7 @@ static int run_cfg(const GemmDesc& d, const GemmWorkspace& ws, const TcCfg& cfg,
 
 // time every candidate on a scratch output (beta = 0, same operands); keep the fastest
 static TcCfg tune(const GemmDesc& d, const GemmWorkspace& ws, TcTuner& t, cudaStream_t s) {
-  const bool swap = !d.conv && d.M < TC_BM && d.N > d.M;
+  const bool swap = d.convw || (!d.conv && d.M < TC_BM && d.N > d.M);
   const int Nk = swap ? d.M : d.N;
   std::vector<TcCfg> cands;
   for (int bn : {64, 128}) {
@@ -681,11 +781,14 @@ static TcCfg tune(const GemmDesc& d, const GemmWorkspace& ws, TcTuner& t, cudaSt
 }
 
 int gemm_tc(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s) {
-  const bool swap = !d.conv && d.M < TC_BM && d.N > d.M;
+  const bool swap = d.convw || (!d.conv && d.M < TC_BM && d.N > d.M);
   TcCfg cfg = default_cfg(swap ? d.M : d.N);
   TcTuner* t = ws.tuner;
   if (t && t->on) {
-    const auto key = std::make_tuple(d.M, d.N, d.K, d.a_t * 2 + d.b_t + (d.conv ? 4 + 8 * d.conv->s : 0),
+    const ConvShape* cv = d.conv ? d.conv : d.convw;
+    const int mode = d.a_t * 2 + d.b_t + (d.conv ? 4 : 0) + (d.convw ? 128 : 0) +
+                     (cv ? 8 * cv->s + 256 * cv->Wo + 65536 * cv->k : 0);
+    const auto key = std::make_tuple(d.M, d.N, d.K, mode,
                                      d.c_bf16, d.beta != 0.f ? 1 : 0, d.lda * 8 + d.ldb);
     auto it = t->table.find(key);
     if (it != t->table.end()) {

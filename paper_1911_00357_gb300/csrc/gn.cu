@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(kThreads) gn_stats_kernel(const float* __restr
   ldv<V>(zi + c0, K);
 #pragma unroll
   for (int v = 0; v < V; ++v) s1[v] = s2[v] = 0.f;
+#pragma unroll 4
   for (int p = pb + pr; p < pe; p += P) {
     float x[V];
     ldv<V>(zi + (size_t)p * C + c0, x);
@@ -120,6 +121,10 @@ __global__ void __launch_bounds__(kThreads) gn_stats_kernel(const float* __restr
   float* pp = part + ((size_t)n * S + sb) * C * 2;
   block_pair_sums<V>(s1, s2, sh, C, pp);
   if (!last_of_image(cnt + n, S, &flag)) return;
+  // the image's S x C x 2 partials, staged in shared memory with all loads in flight
+  const float* pim = part + (size_t)n * S * C * 2;
+  for (int i = threadIdx.x; i < S * C * 2; i += blockDim.x) sh[i] = __ldcg(pim + i);
+  __syncthreads();
   const int G = C / 2;
   const double inv = 1.0 / HW;
   for (int g = threadIdx.x; g < G; g += blockDim.x) {
@@ -128,9 +133,8 @@ __global__ void __launch_bounds__(kThreads) gn_stats_kernel(const float* __restr
       const int c = 2 * g + j;
       double a = 0.0, b = 0.0;
       for (int t = 0; t < S; ++t) {
-        const float* q = part + ((size_t)n * S + t) * C * 2 + 2 * c;
-        a += (double)__ldcg(q);
-        b += (double)__ldcg(q + 1);
+        a += (double)sh[(t * C + c) * 2];
+        b += (double)sh[(t * C + c) * 2 + 1];
       }
       m[j] = (double)zi[c] + a * inv;   // the same shift every block used
       M2[j] = b - a * a * inv;
@@ -207,6 +211,7 @@ __global__ void __launch_bounds__(kThreads) gn_bwd_reduce_kernel(GNBack b, int H
     rs[v] = b.rstd[(size_t)n * G + (c0 + v) / 2];
     sg[v] = sgx[v] = 0.f;
   }
+#pragma unroll 4
   for (int p = pb + pr; p < pe; p += P) {
     const size_t o = ib + (size_t)p * C + c0;
     float d[V], x[V];
@@ -228,14 +233,15 @@ __global__ void __launch_bounds__(kThreads) gn_bwd_reduce_kernel(GNBack b, int H
   block_pair_sums<V>(sg, sgx, sh, C, pp);
   if (!last_of_image(cnt + n, S, &flag)) return;
   // per-channel totals (block order), then the group means of gamma-weighted sums
-  float* tot = sh;  // [C][2], reusing the reduction buffer after the barrier below
+  const float* pim = part + (size_t)n * S * C * 2;
+  for (int i = threadIdx.x; i < S * C * 2; i += blockDim.x) sh[i] = __ldcg(pim + i);
   __syncthreads();
+  float* tot = sh + S * C * 2;  // [C][2]
   for (int c = threadIdx.x; c < C; c += blockDim.x) {
     float a = 0.f, e = 0.f;
     for (int t = 0; t < S; ++t) {
-      const float* q = part + ((size_t)n * S + t) * C * 2 + 2 * c;
-      a += __ldcg(q);
-      e += __ldcg(q + 1);
+      a += sh[(t * C + c) * 2];
+      e += sh[(t * C + c) * 2 + 1];
     }
     tot[2 * c] = a;
     tot[2 * c + 1] = e;
@@ -305,6 +311,7 @@ int gn_split(int N, int HW, int C, const GnScratch& w) {
   const int want = (8 * num_sms_cached() + N - 1) / N;
   int S = std::min(want, (HW + P - 1) / P);
   S = std::min(S, 64);
+  S = std::min(S, std::max(1, 4096 / C));  // the combine stages S x C x 2 floats in shared memory
   S = std::max(S, 1);
   while (S > 1 && (size_t)N * S * C * 2 > w.part_elems) --S;
   return S;
@@ -339,7 +346,7 @@ int launch_gn_stats(const float* z, int N, int HW, int C, float eps, float* mean
   const int V = C % 4 == 0 ? 4 : 2;
   const int S = gn_split(N, HW, C, w);
   const int th = threads_for(C, V);
-  const size_t smem = (size_t)th * 2 * V * sizeof(float);
+  const size_t smem = std::max((size_t)th * 2 * V, (size_t)S * C * 2) * sizeof(float);
   const dim3 grid(S, N);
   if (V == 4) gn_stats_kernel<4><<<grid, th, smem, s>>>(z, HW, C, S, eps, w.part, w.cnt, mean, rstd);
   else gn_stats_kernel<2><<<grid, th, smem, s>>>(z, HW, C, S, eps, w.part, w.cnt, mean, rstd);
@@ -367,7 +374,7 @@ int launch_gn_bwd(const GNBack& b, int N, int HW, int C, const GnScratch& w, cud
   const int V = C % 4 == 0 ? 4 : 2;
   const int S = gn_split(N, HW, C, w);
   const int th = threads_for(C, V);
-  const size_t smem = std::max((size_t)th * 2 * V, (size_t)2 * C) * sizeof(float);
+  const size_t smem = std::max((size_t)th * 2 * V, (size_t)(S + 1) * C * 2) * sizeof(float);
   const dim3 grid(S, N);
   if (V == 4) gn_bwd_reduce_kernel<4><<<grid, th, smem, s>>>(b, HW, C, S, w.part, w.cnt);
   else gn_bwd_reduce_kernel<2><<<grid, th, smem, s>>>(b, HW, C, S, w.part, w.cnt);

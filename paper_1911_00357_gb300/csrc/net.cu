@@ -450,13 +450,21 @@ static int conv_bwd(Net& n, ConvL& c, const void* in, bool in_bf16, int N, const
                     const __nv_bfloat16* in_bf = nullptr) {
   const ConvGeom g = geom(c, N);
   const int M = N * c.Ho * c.Wo;
-  if (in_bf) DDPPO_TRY(launch_im2col(g, in_bf, true, n.col, n.bf, false, s));
-  else DDPPO_TRY(launch_im2col(g, in, in_bf16, n.col, n.bf, false, s));
   GemmDesc w;
   w.M = c.cout; w.N = c.Kp; w.K = M;
   w.A = dzop; w.lda = c.cout; w.a_t = 1;
-  w.B = n.col; w.ldb = c.Kp; w.b_t = 1;
   w.C = c.dwg; w.ldc = c.Kp; w.beta = first ? 0.f : 1.f;
+  const ConvShape cs = conv_shape(c, N);
+  const void* x_bf = in_bf ? (const void*)in_bf : (in_bf16 ? in : nullptr);
+  if (n.bf && x_bf && c.Kp == c.k * c.k * c.cin && c.cout % 8 == 0 &&
+      gemm_convw_supported(cs, x_bf, dzop)) {
+    w.convw = &cs;  // the GEMM gathers the shifted input rows itself
+    w.B = x_bf;
+  } else {
+    if (in_bf) DDPPO_TRY(launch_im2col(g, in_bf, true, n.col, n.bf, false, s));
+    else DDPPO_TRY(launch_im2col(g, in, in_bf16, n.col, n.bf, false, s));
+    w.B = n.col; w.ldb = c.Kp; w.b_t = 1;
+  }
   DDPPO_TRY(G(n, w, s));
   if (dx && c.dgrad_as_conv) {
     // dx = conv(dz, flipped kernel): im2col of dz (C = cout) then one GEMM into dx

@@ -480,35 +480,67 @@ extern "C" int ddppo_autotune_import(ddppo_ctx* x, const void* buf, size_t size)
 }
 
 // ---- stand-alone convolution on the implicit-im2col tensor-core path ----
-extern "C" int ddppo_conv2d(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, int32_t k,
-                            int32_t stride, int32_t pad, const void* x, const void* w, float* y,
-                            int32_t* status, void* stream) {
-  ARG(N >= 1 && H >= 1 && W >= 1 && C >= 1 && Cout >= 1 && k >= 1 && stride >= 1 && pad >= 0,
-      "conv2d: bad sizes");
-  ARG(x && w && y, "conv2d: null argument");
-  ConvShape c;
-  c.N = N; c.H = H; c.W = W; c.C = C; c.k = k; c.s = stride; c.p = pad;
-  c.Ho = (H + 2 * pad - k) / stride + 1;
-  c.Wo = (W + 2 * pad - k) / stride + 1;
-  ARG(c.Ho >= 1 && c.Wo >= 1, "conv2d: empty output");
-  if (!gemm_conv_supported(c, x)) {
-    set_error("conv2d: shape not covered by the implicit-im2col path");
-    return DDPPO_E_CONFIG;
-  }
+static int standalone_ws(GemmWorkspace* ws, int32_t* status) {
   int dev = 0;
   DDPPO_CHECK_CUDA(cudaGetDevice(&dev));
-  GemmWorkspace ws;
   static float* partial[64] = {};
   ARG(dev < 64, "conv2d: device ordinal out of range");
   const size_t elems = (size_t)16 << 20;
   if (!partial[dev]) DDPPO_CHECK_CUDA(cudaMalloc(&partial[dev], elems * sizeof(float)));
-  ws.partial = partial[dev];
-  ws.partial_elems = elems;
-  cudaDeviceGetAttribute(&ws.num_sms, cudaDevAttrMultiProcessorCount, dev);
-  ws.err = status;
+  ws->partial = partial[dev];
+  ws->partial_elems = elems;
+  cudaDeviceGetAttribute(&ws->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  ws->err = status;
+  return DDPPO_OK;
+}
+
+static int conv_args(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, int32_t k,
+                     int32_t stride, int32_t pad, ConvShape* c) {
+  ARG(N >= 1 && H >= 1 && W >= 1 && C >= 1 && Cout >= 1 && k >= 1 && stride >= 1 && pad >= 0,
+      "conv2d: bad sizes");
+  c->N = N; c->H = H; c->W = W; c->C = C; c->k = k; c->s = stride; c->p = pad;
+  c->Ho = (H + 2 * pad - k) / stride + 1;
+  c->Wo = (W + 2 * pad - k) / stride + 1;
+  ARG(c->Ho >= 1 && c->Wo >= 1, "conv2d: empty output");
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_conv2d(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, int32_t k,
+                            int32_t stride, int32_t pad, const void* x, const void* w, float* y,
+                            int32_t* status, void* stream) {
+  ConvShape c;
+  DDPPO_TRY(conv_args(N, H, W, C, Cout, k, stride, pad, &c));
+  ARG(x && w && y, "conv2d: null argument");
+  if (!gemm_conv_supported(c, x)) {
+    set_error("conv2d: shape not covered by the implicit-im2col path");
+    return DDPPO_E_CONFIG;
+  }
+  GemmWorkspace ws;
+  DDPPO_TRY(standalone_ws(&ws, status));
   GemmDesc d;
   d.M = N * c.Ho * c.Wo; d.N = Cout; d.K = k * k * C;
   d.conv = &c; d.A = x; d.lda = d.K; d.B = w; d.ldb = d.K;
   d.C = y; d.ldc = Cout;
+  return gemm(d, true, ws, (cudaStream_t)stream, nullptr);
+}
+
+extern "C" int ddppo_conv2d_wgrad(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout,
+                                  int32_t k, int32_t stride, int32_t pad, const void* x,
+                                  const void* dy, float* dw, float beta, int32_t* status,
+                                  void* stream) {
+  ConvShape c;
+  DDPPO_TRY(conv_args(N, H, W, C, Cout, k, stride, pad, &c));
+  ARG(x && dy && dw, "conv2d_wgrad: null argument");
+  if (Cout % 8 || !gemm_convw_supported(c, x, dy)) {
+    set_error("conv2d_wgrad: shape not covered by the implicit weight-gradient path");
+    return DDPPO_E_CONFIG;
+  }
+  GemmWorkspace ws;
+  DDPPO_TRY(standalone_ws(&ws, status));
+  GemmDesc d;
+  d.M = Cout; d.N = k * k * C; d.K = N * c.Ho * c.Wo;
+  d.A = dy; d.lda = Cout; d.a_t = 1;
+  d.convw = &c; d.B = x;
+  d.C = dw; d.ldc = d.N; d.beta = beta;
   return gemm(d, true, ws, (cudaStream_t)stream, nullptr);
 }

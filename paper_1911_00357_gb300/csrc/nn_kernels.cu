@@ -2,6 +2,8 @@
 // transforms, GroupNorm (Wu & He 2018) with C/2 groups, max pool, the LSTM cell and its
 // backward, actor/critic heads with inverse-CDF sampling, goal/action embeddings, and the
 // canonical <-> GEMM weight layouts. All reductions run in a fixed order.
+#include <algorithm>
+
 #include "nn_kernels.cuh"
 
 namespace ddppo {
@@ -126,35 +128,37 @@ __global__ void im2col_vec_kernel(ConvGeom g, const Ti* __restrict__ x, To* __re
 // threads write adjacent rows, so a warp writes one contiguous stretch of the col matrix.
 template <typename Ti, typename To>
 __global__ void im2col_c1_kernel(ConvGeom g, const Ti* __restrict__ x, To* __restrict__ col) {
-  const size_t rows = (size_t)g.N * g.Ho * g.Wo;
-  for (size_t m = (size_t)blockIdx.x * blockDim.x + threadIdx.x; m < rows;
-       m += (size_t)gridDim.x * blockDim.x) {
-    const int ox = (int)(m % g.Wo), oy = (int)((m / g.Wo) % g.Ho), n = (int)(m / ((size_t)g.Wo * g.Ho));
-    const Ti* img = x + (size_t)n * g.H * g.W;
-    To* dst = col + m * g.Kp;
-    for (int k0 = 0; k0 < g.Kp; k0 += 8) {
-      float v[8];
+  const int nck = g.Kp / 8;                     // 8-tap chunks per row
+  const int per_img = g.Ho * g.Wo * nck;        // chunks of one image
+  const int n = blockIdx.y;
+  const Ti* img = x + (size_t)n * g.H * g.W;
+  To* dst_img = col + (size_t)n * g.Ho * g.Wo * g.Kp;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per_img; i += gridDim.x * blockDim.x) {
+    const int ck = i % nck, m = i / nck;
+    const int ox = m % g.Wo, oy = m / g.Wo;
+    const int k0 = ck * 8;
+    float v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int kk = k0 + q;
-        float t = 0.f;
-        if (kk < g.K) {
-          const int ky = kk / g.k, kx = kk - ky * g.k;
-          const int iy = oy * g.s - g.p + ky, ix = ox * g.s - g.p + kx;
-          if (iy >= 0 && iy < g.H && ix >= 0 && ix < g.W) t = to_f(img[(size_t)iy * g.W + ix]);
-        }
-        v[q] = t;
+    for (int q = 0; q < 8; ++q) {
+      const int kk = k0 + q;
+      float t = 0.f;
+      if (kk < g.K) {
+        const int ky = kk / g.k, kx = kk - ky * g.k;
+        const int iy = oy * g.s - g.p + ky, ix = ox * g.s - g.p + kx;
+        if (iy >= 0 && iy < g.H && ix >= 0 && ix < g.W) t = to_f(img[iy * g.W + ix]);
       }
-      if constexpr (sizeof(To) == 2) {
-        uint4 u;
-        __nv_bfloat16* h = (__nv_bfloat16*)&u;
+      v[q] = t;
+    }
+    To* dst = dst_img + (size_t)m * g.Kp + k0;
+    if constexpr (sizeof(To) == 2) {
+      uint4 u;
+      __nv_bfloat16* h = (__nv_bfloat16*)&u;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) h[q] = __float2bfloat16_rn(v[q]);
-        *(uint4*)(dst + k0) = u;
-      } else {
-        *(float4*)(dst + k0) = make_float4(v[0], v[1], v[2], v[3]);
-        *(float4*)(dst + k0 + 4) = make_float4(v[4], v[5], v[6], v[7]);
-      }
+      for (int q = 0; q < 8; ++q) h[q] = __float2bfloat16_rn(v[q]);
+      *(uint4*)dst = u;
+    } else {
+      *(float4*)dst = make_float4(v[0], v[1], v[2], v[3]);
+      *(float4*)(dst + 4) = make_float4(v[4], v[5], v[6], v[7]);
     }
   }
 }
@@ -163,8 +167,11 @@ int launch_im2col(const ConvGeom& g, const void* x, bool x_bf16, void* col, bool
                   bool transposed, cudaStream_t s) {
   const size_t total = (size_t)g.N * g.Ho * g.Wo * g.Kp;
   if (total == 0) return DDPPO_OK;
-  if (!transposed && g.C == 1 && g.Kp % 8 == 0 && ((uintptr_t)col & 15) == 0) {
-    const unsigned gb = grid_for((size_t)g.N * g.Ho * g.Wo);
+  if (!transposed && g.C == 1 && g.Kp % 8 == 0 && ((uintptr_t)col & 15) == 0 && g.N <= 65535 &&
+      (int64_t)g.Ho * g.Wo * g.Kp < (1ll << 31) && (int64_t)g.H * g.W < (1ll << 31)) {
+    const long per = (long)g.Ho * g.Wo * (g.Kp / 8);
+    const dim3 gb((unsigned)std::max<long>(1, std::min<long>((per + 255) / 256,
+                                                             (8l * 152 + g.N - 1) / g.N)), g.N);
     if (x_bf16 && op_bf16)
       im2col_c1_kernel<__nv_bfloat16, __nv_bfloat16><<<gb, 256, 0, s>>>(g, (const __nv_bfloat16*)x, (__nv_bfloat16*)col);
     else if (x_bf16)
@@ -381,12 +388,54 @@ __global__ void maxpool_fwd_kernel(const float* __restrict__ x, int N, int H, in
     arg[idx] = (uint8_t)bi;
   }
 }
+// 4 channels per thread (C % 4 == 0): float4 loads and stores, 32-bit index decoding
+__global__ void maxpool_fwd4_kernel(const float* __restrict__ x, int H, int W, int C,
+                                    float* __restrict__ y, uint8_t* __restrict__ arg,
+                                    __nv_bfloat16* __restrict__ y_bf) {
+  const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1, C4 = C / 4;
+  const int n = blockIdx.y, per = Ho * Wo * C4;
+  const float* xi = x + (size_t)n * H * W * C;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per; i += gridDim.x * blockDim.x) {
+    const int c4 = i % C4, pix = i / C4;
+    const int ox = pix % Wo, oy = pix / Wo;
+    float b[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    int bi[4] = {0, 0, 0, 0};
+    for (int ky = 0; ky < 3; ++ky) {
+      const int iy = oy * 2 - 1 + ky;
+      if (iy < 0 || iy >= H) continue;
+      for (int kx = 0; kx < 3; ++kx) {
+        const int ix = ox * 2 - 1 + kx;
+        if (ix < 0 || ix >= W) continue;
+        const float4 v = *reinterpret_cast<const float4*>(xi + ((size_t)iy * W + ix) * C + c4 * 4);
+        const float vv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (vv[q] > b[q]) { b[q] = vv[q]; bi[q] = ky * 3 + kx; }
+      }
+    }
+    const size_t o = (size_t)n * per * 4 + (size_t)i * 4;
+    *reinterpret_cast<float4*>(y + o) = make_float4(b[0], b[1], b[2], b[3]);
+    if (y_bf) {
+      __nv_bfloat162 h0 = __floats2bfloat162_rn(b[0], b[1]), h1 = __floats2bfloat162_rn(b[2], b[3]);
+      *reinterpret_cast<uint2*>(y_bf + o) =
+          make_uint2(*reinterpret_cast<uint32_t*>(&h0), *reinterpret_cast<uint32_t*>(&h1));
+    }
+    *reinterpret_cast<uchar4*>(arg + o) = make_uchar4(bi[0], bi[1], bi[2], bi[3]);
+  }
+}
+
 int launch_maxpool_fwd(const float* x, int N, int H, int W, int C, float* y, uint8_t* arg,
                        __nv_bfloat16* y_bf, cudaStream_t s) {
   const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1;
   const size_t total = (size_t)N * Ho * Wo * C;
   if (!total) return DDPPO_OK;
-  maxpool_fwd_kernel<<<grid_for(total), 256, 0, s>>>(x, N, H, W, C, y, arg, y_bf);
+  if (C % 4 == 0 && N <= 65535 && (int64_t)Ho * Wo * C < (1ll << 31)) {
+    const long per = (long)Ho * Wo * (C / 4);
+    const dim3 gb((unsigned)std::max<long>(1, std::min<long>((per + 255) / 256, (8l * 152 + N - 1) / N)), N);
+    maxpool_fwd4_kernel<<<gb, 256, 0, s>>>(x, H, W, C, y, arg, y_bf);
+  } else {
+    maxpool_fwd_kernel<<<grid_for(total), 256, 0, s>>>(x, N, H, W, C, y, arg, y_bf);
+  }
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -417,11 +466,51 @@ __global__ void maxpool_bwd_kernel(const float* __restrict__ dy, const uint8_t* 
     dx[idx] = acc;
   }
 }
+__global__ void maxpool_bwd4_kernel(const float* __restrict__ dy, const uint8_t* __restrict__ arg,
+                                    int H, int W, int C, float* __restrict__ dx) {
+  const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1, C4 = C / 4;
+  const int n = blockIdx.y, per = H * W * C4;
+  const size_t ob = (size_t)n * Ho * Wo * C;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per; i += gridDim.x * blockDim.x) {
+    const int c4 = i % C4, pix = i / C4;
+    const int ix = pix % W, iy = pix / W;
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int ky = 0; ky < 3; ++ky) {
+      const int ty = iy + 1 - ky;
+      if (ty < 0 || (ty & 1)) continue;
+      const int oy = ty >> 1;
+      if (oy >= Ho) continue;
+      for (int kx = 0; kx < 3; ++kx) {
+        const int tx = ix + 1 - kx;
+        if (tx < 0 || (tx & 1)) continue;
+        const int ox = tx >> 1;
+        if (ox >= Wo) continue;
+        const size_t o = ob + ((size_t)oy * Wo + ox) * C + c4 * 4;
+        const uchar4 a4 = *reinterpret_cast<const uchar4*>(arg + o);
+        const float4 d4 = *reinterpret_cast<const float4*>(dy + o);
+        const int t = ky * 3 + kx;
+        if (a4.x == t) acc[0] += d4.x;
+        if (a4.y == t) acc[1] += d4.y;
+        if (a4.z == t) acc[2] += d4.z;
+        if (a4.w == t) acc[3] += d4.w;
+      }
+    }
+    *reinterpret_cast<float4*>(dx + (size_t)n * per * 4 + (size_t)i * 4) =
+        make_float4(acc[0], acc[1], acc[2], acc[3]);
+  }
+}
+
 int launch_maxpool_bwd(const float* dy, const uint8_t* arg, int N, int H, int W, int C, float* dx,
                        cudaStream_t s) {
   const size_t total = (size_t)N * H * W * C;
   if (!total) return DDPPO_OK;
-  maxpool_bwd_kernel<<<grid_for(total), 256, 0, s>>>(dy, arg, N, H, W, C, dx);
+  if (C % 4 == 0 && N <= 65535 && (int64_t)H * W * C < (1ll << 31)) {
+    const long per = (long)H * W * (C / 4);
+    const dim3 gb((unsigned)std::max<long>(1, std::min<long>((per + 255) / 256, (8l * 152 + N - 1) / N)), N);
+    maxpool_bwd4_kernel<<<gb, 256, 0, s>>>(dy, arg, H, W, C, dx);
+  } else {
+    maxpool_bwd_kernel<<<grid_for(total), 256, 0, s>>>(dy, arg, N, H, W, C, dx);
+  }
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }

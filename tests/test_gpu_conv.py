@@ -54,3 +54,51 @@ def test_unsupported_shape_is_rejected():
     with pytest.raises(B.DDPPOError) as ei:
         B.ddppo_conv2d(x, w, y, 3, 1, 1)
     assert ei.value.code == -2
+
+
+# (N, H, W, C, Cout, k, s, p) for the weight gradient: 64-pixel K blocks of whole rows or
+# whole images; C = 32 (64-byte swizzled MN-major boxes) and C % 64 == 0 (128-byte)
+WGRAD_SHAPES = [
+    (3, 32, 32, 32, 32, 3, 1, 1),     # layer-1 shape: 2 output rows per K block, 4 boxes per tile
+    (2, 32, 32, 32, 64, 3, 2, 1),     # stride 2 (16x16 outputs)
+    (5, 16, 16, 64, 64, 3, 1, 1),     # 2 boxes (taps) per 128-row tile
+    (3, 16, 16, 64, 128, 3, 2, 1),    # 8x8 outputs: one image per K block
+    (9, 8, 8, 128, 128, 3, 1, 1),
+    (7, 8, 8, 128, 256, 3, 2, 1),     # 4x4 outputs: 4 images per K block, ragged image tail
+    (6, 4, 4, 256, 128, 3, 1, 1),     # ragged (tap, channel) tile: 2304 = 18 x 128
+    (4, 16, 16, 64, 128, 1, 2, 0),    # 1x1 stride-2 shortcut
+    (2, 64, 64, 32, 32, 3, 1, 1),     # 64-wide rows: one row per K block
+    (70, 32, 32, 32, 32, 3, 1, 1),    # long reduction (split K)
+]
+
+
+@pytest.mark.parametrize("N,H,W,C,Co,k,s,p", WGRAD_SHAPES)
+def test_implicit_wgrad_parity(N, H, W, C, Co, k, s, p):
+    g = torch.Generator(device="cuda").manual_seed(N * 17 + C * 5 + Co + 3 * k + s)
+    x = torch.randn(N, H, W, C, device="cuda", generator=g).to(torch.bfloat16)
+    Ho, Wo = (H + 2 * p - k) // s + 1, (W + 2 * p - k) // s + 1
+    dy = torch.randn(N, Ho, Wo, Co, device="cuda", generator=g).to(torch.bfloat16)
+    dw0 = torch.randn(Co, k * k * C, device="cuda", generator=g)
+    dw = dw0.clone()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.ddppo_conv2d_wgrad(x, dy, dw, k, s, p, beta=1.0, status=st)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    # float64 weight gradient of the same bf16 values through autograd of conv2d
+    xd = x.double().cpu().permute(0, 3, 1, 2)
+    wd = torch.zeros(Co, C, k, k, dtype=torch.float64, requires_grad=True)
+    out = F.conv2d(xd, wd, stride=s, padding=p)
+    out.backward(dy.double().cpu().permute(0, 3, 1, 2))
+    ref = wd.grad.permute(0, 2, 3, 1).reshape(Co, k * k * C) + dw0.double().cpu()
+    red = N * Ho * Wo
+    err = (dw.double().cpu() - ref).abs().max().item()
+    assert err <= 4e-5 * np.sqrt(red) * 4, err
+
+
+def test_wgrad_unsupported_shape_is_rejected():
+    x = torch.zeros(2, 15, 15, 32, device="cuda", dtype=torch.bfloat16)   # 15-wide output
+    dy = torch.zeros(2, 15, 15, 32, device="cuda", dtype=torch.bfloat16)
+    dw = torch.zeros(32, 9 * 32, device="cuda")
+    with pytest.raises(B.DDPPOError) as ei:
+        B.ddppo_conv2d_wgrad(x, dy, dw, 3, 1, 1)
+    assert ei.value.code == -2
