@@ -193,6 +193,15 @@ int ddppo_env_reset(ddppo_ctx* ctx, void* obs, float* goal, void* stream);
 int ddppo_env_step(ddppo_ctx* ctx, const int32_t* actions, void* obs, float* goal, float* reward,
                    uint8_t* done, float* info, void* stream);
 
+/* Generate, ahead of time, the next episode of every env that has none prepared (scene,
+ * geodesic field and start state, exactly as env_step's auto-reset would draw them) into
+ * the env's second scene slot; an env_step that ends an episode then adopts the prepared
+ * slot instead of generating it. Meant for a second stream, overlapping the policy's
+ * forward pass (ddppo_collect does this); it must not overlap env_reset, env_step or
+ * env_set_state of the same context. Results are identical with or without it.
+ * Errors: E_STATE before env_reset. */
+int ddppo_env_prefetch(ddppo_ctx* ctx, void* stream);
+
 /* Parity / debugging views. state [dev] [E, DDPPO_NSTATE] int32: x, y (u),
  * heading (0..35, 10 deg steps counter-clockwise from +x), steps, path length
  * (u), previous geodesic (u), start geodesic l (u), goal x, goal y (u), episode,
@@ -206,7 +215,8 @@ int ddppo_env_grids(ddppo_ctx* ctx, uint8_t* grids, int32_t* dists, void* stream
 int ddppo_env_depth(ddppo_ctx* ctx, float* depth, void* stream);
 
 /* Overwrite the agent states [dev] [E, DDPPO_NSTATE] (same layout as env_state)
- * keeping the current scenes; for tests that place agents by hand. */
+ * keeping the current scenes; for tests that place agents by hand. Discards prepared
+ * next episodes (they were drawn for the replaced episode counters). */
 int ddppo_env_set_state(ddppo_ctx* ctx, const int32_t* state, void* stream);
 
 /* ---- policy (App. "Agent Design") -------------------------------------------- */

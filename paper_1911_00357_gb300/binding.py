@@ -90,6 +90,7 @@ _SIGS = {
     "ddppo_get_adam": [P, P, P, I64, P, P],
     "ddppo_env_reset": [P, P, P, P],
     "ddppo_env_step": [P, P, P, P, P, P, P, P],
+    "ddppo_env_prefetch": [P, P],
     "ddppo_env_state": [P, P, P],
     "ddppo_env_set_state": [P, P, P],
     "ddppo_env_grids": [P, P, P, P],
@@ -208,6 +209,11 @@ def ddppo_env_reset(h, obs, goal):
 def ddppo_env_step(h, actions, obs, goal, reward, done, info=None):
     _check(lib().ddppo_env_step(h, _p(actions), _p(obs), _p(goal), _p(reward), _p(done), _p(info),
                                 _s()))
+
+
+def ddppo_env_prefetch(h, stream=None):
+    """Prepare the next episode of every env (see the header); stream: a torch stream."""
+    _check(lib().ddppo_env_prefetch(h, _s(stream)))
 
 
 def ddppo_env_state(h, state):

@@ -114,7 +114,11 @@ static int dmalloc(T** p, size_t n) {
 namespace ddppo {
 void ctx_free_world(ddppo_ctx* x) {
   cudaFree(x->sb.grids); cudaFree(x->sb.bits); cudaFree(x->sb.dists); cudaFree(x->sb.states);
+  cudaFree(x->sb.pend); cudaFree(x->sb.slot); cudaFree(x->sb.ready);
   cudaFree(x->sb.segs); cudaFree(x->sb.need); cudaFree(x->sb.err); cudaFree(x->sb.work);
+  if (x->ev_fork) cudaEventDestroy(x->ev_fork);
+  if (x->ev_join) cudaEventDestroy(x->ev_join);
+  if (x->side) cudaStreamDestroy(x->side);
 }
 }  // namespace ddppo
 
@@ -130,19 +134,32 @@ extern "C" int ddppo_create(const ddppo_config* cfg, ddppo_ctx** out) {
     if ((rc = sim_upload_tables()) != DDPPO_OK) break;
     if ((rc = sim_configure(x->sp)) != DDPPO_OK) break;
     const size_t E = cfg->num_envs, GM = (size_t)cfg->grid_max * cfg->grid_max;
-    if ((rc = dmalloc(&x->sb.grids, E * GM)) != DDPPO_OK) break;
-    if ((rc = dmalloc(&x->sb.bits, E * GM / 32)) != DDPPO_OK) break;
-    if ((rc = dmalloc(&x->sb.dists, E * GM)) != DDPPO_OK) break;
+    if ((rc = dmalloc(&x->sb.grids, 2 * E * GM)) != DDPPO_OK) break;
+    if ((rc = dmalloc(&x->sb.bits, 2 * E * GM / 32)) != DDPPO_OK) break;
+    if ((rc = dmalloc(&x->sb.dists, 2 * E * GM)) != DDPPO_OK) break;
     if ((rc = dmalloc(&x->sb.states, E * ST_N)) != DDPPO_OK) break;
+    if ((rc = dmalloc(&x->sb.pend, E * ST_N)) != DDPPO_OK) break;
+    if ((rc = dmalloc(&x->sb.slot, E)) != DDPPO_OK) break;
+    if ((rc = dmalloc(&x->sb.ready, E)) != DDPPO_OK) break;
+    if (cudaMemset(x->sb.slot, 0, E) != cudaSuccess || cudaMemset(x->sb.ready, 0, E) != cudaSuccess) {
+      set_error("cudaMemset failed"); rc = DDPPO_E_CUDA; break;
+    }
+    if (cudaStreamCreateWithFlags(&x->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&x->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      set_error("stream/event creation failed"); rc = DDPPO_E_CUDA; break;
+    }
     if ((rc = dmalloc(&x->sb.segs, E * (size_t)x->sp.max_segs)) != DDPPO_OK) break;
     if ((rc = dmalloc(&x->sb.need, E)) != DDPPO_OK) break;
     if ((rc = dmalloc(&x->sb.err, 1)) != DDPPO_OK) break;
-    if ((rc = dmalloc(&x->sb.work, 2)) != DDPPO_OK) break;
-    if (cudaMemset(x->sb.work, 0, 2 * sizeof(int32_t)) != cudaSuccess) { set_error("cudaMemset failed"); rc = DDPPO_E_CUDA; break; }
+    if ((rc = dmalloc(&x->sb.work, 4)) != DDPPO_OK) break;
+    if (cudaMemset(x->sb.work, 0, 4 * sizeof(int32_t)) != cudaSuccess) { set_error("cudaMemset failed"); rc = DDPPO_E_CUDA; break; }
     {
       int nsm = 152;
       cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, x->device);
       x->env_grid = env_step_grid(x->sp, nsm);
+      // half the SMs at most: the prefetch runs beside the policy's forward pass
+      x->prefetch_grid = std::max(1, std::min(cfg->num_envs, nsm / 2));
     }
     if (cudaMemset(x->sb.err, 0, sizeof(int32_t)) != cudaSuccess ||
         cudaMemset(x->sb.need, 0, E) != cudaSuccess ||
@@ -218,6 +235,12 @@ extern "C" int ddppo_env_step(ddppo_ctx* x, const int32_t* actions, void* obs, f
   return DDPPO_OK;
 }
 
+extern "C" int ddppo_env_prefetch(ddppo_ctx* x, void* stream) {
+  ARG_CHECK(x, "env_prefetch: null ctx");
+  if (!x->env_ready) { set_error("env_prefetch before env_reset"); return DDPPO_E_STATE; }
+  return launch_env_prefetch(x->sp, x->sb, x->prefetch_grid, (cudaStream_t)stream);
+}
+
 extern "C" int ddppo_env_state(ddppo_ctx* x, int32_t* state, void* stream) {
   ARG_CHECK(x && state, "env_state: null argument");
   DDPPO_CHECK_CUDA(cudaMemcpyAsync(state, x->sb.states,
@@ -231,18 +254,15 @@ extern "C" int ddppo_env_set_state(ddppo_ctx* x, const int32_t* state, void* str
   if (!x->env_ready) { set_error("env_set_state before env_reset"); return DDPPO_E_STATE; }
   DDPPO_CHECK_CUDA(cudaMemcpyAsync(x->sb.states, state, sizeof(int32_t) * ST_N * x->cfg.num_envs,
                                    cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  // prepared next episodes were drawn for the replaced episode counters
+  DDPPO_CHECK_CUDA(cudaMemsetAsync(x->sb.ready, 0, x->cfg.num_envs, (cudaStream_t)stream));
   return DDPPO_OK;
 }
 
 extern "C" int ddppo_env_grids(ddppo_ctx* x, uint8_t* grids, int32_t* dists, void* stream) {
   ARG_CHECK(x, "env_grids: null ctx");
-  const size_t n = (size_t)x->cfg.num_envs * x->cfg.grid_max * x->cfg.grid_max;
-  cudaStream_t s = (cudaStream_t)stream;
-  if (grids)
-    DDPPO_CHECK_CUDA(cudaMemcpyAsync(grids, x->sb.grids, n, cudaMemcpyDeviceToDevice, s));
-  if (dists)
-    DDPPO_CHECK_CUDA(cudaMemcpyAsync(dists, x->sb.dists, n * 4, cudaMemcpyDeviceToDevice, s));
-  return DDPPO_OK;
+  if (!grids && !dists) return DDPPO_OK;
+  return launch_copy_current(x->sp, x->sb, grids, dists, (cudaStream_t)stream);
 }
 
 extern "C" int ddppo_env_depth(ddppo_ctx* x, float* depth, void* stream) {

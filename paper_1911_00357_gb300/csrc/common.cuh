@@ -55,15 +55,20 @@ struct SimParams {
   int bf16_obs;
 };
 
+// Every env owns two scene slots: the current episode's and the next one's, which the
+// prefetch kernel generates ahead of time (off the critical path of the rollout).
 struct SimBuffers {
-  uint8_t* grids;     // [E, gmax^2]
-  uint32_t* bits;     // [E, gmax^2/32] wall bits, row-major words
-  int32_t* dists;     // [E, gmax^2]
+  uint8_t* grids;     // [2, E, gmax^2]
+  uint32_t* bits;     // [2, E, gmax^2/32] wall bits, row-major words
+  int32_t* dists;     // [2, E, gmax^2]
   int32_t* states;    // [E, ST_N]
+  int32_t* pend;      // [E, ST_N] start state of the prepared next episode
+  uint8_t* slot;      // [E] slot of the current episode
+  uint8_t* ready;     // [E] 1: the other slot holds the next episode (start state in pend)
   int4* segs;         // [E, max_segs] room walls (gen_kind 1)
   uint8_t* need;      // [E] reset request
   int32_t* err;       // [1] sticky
-  int32_t* work;      // [2] persistent env-step work counter, CTAs finished (self re-arming)
+  int32_t* work;      // [4] env-step and prefetch work counters + CTAs finished (self re-arming)
 };
 
 // host-side launchers (sim.cu)
@@ -79,6 +84,11 @@ int launch_env_step(const SimParams& p, const SimBuffers& b, int grid, const int
                     void* obs, float* goal, float* reward, uint8_t* done, float* info,
                     cudaStream_t s);
 int env_step_grid(const SimParams& p, int num_sms);
+// generate the next episode of every env whose other slot is not ready yet
+int launch_env_prefetch(const SimParams& p, const SimBuffers& b, int grid, cudaStream_t s);
+// copy the current slot's grids / distance fields of every env to dense [E, gmax^2] buffers
+int launch_copy_current(const SimParams& p, const SimBuffers& b, uint8_t* grids, int32_t* dists,
+                        cudaStream_t s);
 
 // rl.cu
 int launch_gae(const float* r, const uint8_t* d, const float* v, int T, int E, float gamma,

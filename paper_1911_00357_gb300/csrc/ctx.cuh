@@ -18,5 +18,8 @@ struct ddppo_ctx {
   int device = 0;
   bool env_ready = false;
   int env_grid = 1;  // CTAs of the persistent env-step kernel
+  int prefetch_grid = 1;  // CTAs of the next-episode prefetch kernel
+  cudaStream_t side = nullptr;  // prefetch stream (forked from and joined to the rollout stream)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   ddppo::Net* net = nullptr;
 };

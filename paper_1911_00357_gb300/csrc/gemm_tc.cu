@@ -17,6 +17,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <chrono>
 #include <map>
 #include <mutex>
@@ -27,7 +28,7 @@
 
 namespace ddppo {
 
-constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 4;
+constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 16;  // TC_STAGES: deepest ring
 constexpr int TC_EPI_PITCH = 33;  // floats per staged row (bank-conflict-free transpose)
 constexpr uint32_t TC_SPIN_LIMIT = 1u << 22;
 
@@ -185,7 +186,9 @@ __global__ void __launch_bounds__(TC_PTHREADS, 1)
   extern __shared__ __align__(1024) uint8_t dyn[];
   __shared__ TcSmem ctl;
   __shared__ uint64_t acc_full[2], acc_empty[2];
-  constexpr uint32_t A_BYTES = TC_BM * TC_BK * 2, B_BYTES = BN * TC_BK * 2;
+  // stage sizes follow the K extent of one ring slot (32 channels for narrow convolutions)
+  const int kslot = ca.on == 1 ? ca.cbw : TC_BK;
+  const uint32_t A_BYTES = TC_BM * kslot * 2, B_BYTES = BN * kslot * 2;
   uint8_t* base = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = base;
   uint8_t* sB = base + stages * A_BYTES;
@@ -545,9 +548,20 @@ bool gemm_conv_supported(const ConvShape& c, const void* input) {
   return c.k >= 1 && c.s >= 1 && c.s <= 8;
 }
 
+constexpr size_t TC_SMEM_MAX = 225 * 1024;  // dynamic part, below the 227 KiB opt-in limit
 template <int BN>
-static size_t tc_smem(int stages) {
-  return (size_t)stages * (TC_BM + BN) * TC_BK * 2 + 4 * 32 * TC_EPI_PITCH * 4 + 1024;
+static size_t tc_smem(int stages, int kslot) {
+  return (size_t)stages * (TC_BM + BN) * kslot * 2 + 4 * 32 * TC_EPI_PITCH * 4 + 1024;
+}
+static size_t tc_smem_bn(int bn, int stages, int kslot) {
+  return bn == 128 ? tc_smem<128>(stages, kslot) : tc_smem<64>(stages, kslot);
+}
+// deepest ring within a budget (two CTAs per SM for BN = 64, one for BN = 128)
+static int ring_for(int bn, int kslot) {
+  const size_t budget = bn == 64 ? 110 * 1024 : 200 * 1024;
+  int st = TC_STAGES;
+  while (st > 2 && tc_smem_bn(bn, st, kslot) > budget) --st;
+  return st;
 }
 
 bool gemm_tc_supported(const GemmDesc& d) {
@@ -561,7 +575,7 @@ bool gemm_tc_supported(const GemmDesc& d) {
 
 struct TcCfg {
   int bn = 64;       // N tile: 64 or 128
-  int stages = 3;    // shared-memory ring depth: 2..4
+  int stages = 3;    // shared-memory ring depth: 2..TC_STAGES
   int split = 0;     // 0: split K when the grid would be short of SMs; 1: never split
 };
 
@@ -596,7 +610,7 @@ int64_t tc_tuner_shapes(const TcTuner* t) { return t ? (int64_t)t->table.size() 
 
 // table image: int32 words {magic, version, count} then count records of 7 key words and
 // 3 configuration words (N tile, ring depth, split policy)
-static const int32_t kTuneMagic = 0x54544444, kTuneVersion = 2, kTuneRec = 10;
+static const int32_t kTuneMagic = 0x54544444, kTuneVersion = 4, kTuneRec = 10;
 
 size_t tc_tuner_export(const TcTuner* t, void* buf, size_t cap) {
   const size_t cnt = t ? t->table.size() : 0;
@@ -637,10 +651,15 @@ int tc_tuner_import(TcTuner* t, const void* buf, size_t size) {
   return DDPPO_OK;
 }
 
-static TcCfg default_cfg(int N) {
+static int kslot_of(const GemmDesc& d) {
+  if (d.conv) return d.conv->C % 64 == 0 ? 64 : 32;
+  return TC_BK;
+}
+
+static TcCfg default_cfg(int N, int kslot) {
   TcCfg c;
   c.bn = N > 64 ? 128 : 64;
-  c.stages = c.bn == 64 ? 3 : TC_STAGES;  // BN = 64: two CTAs fit one SM
+  c.stages = std::min(ring_for(c.bn, kslot), c.bn == 64 ? 3 : 4);
   c.split = 0;
   return c;
 }
@@ -655,7 +674,7 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
   if (dev < 64 && !attr_done[dev]) {
     DDPPO_CHECK_CUDA(cudaFuncSetAttribute(gemm_tc_kernel<BN>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)tc_smem<BN>(TC_STAGES)));
+                                          (int)TC_SMEM_MAX));
     attr_done[dev] = true;
   }
   const int gm = (M + TC_BM - 1) / TC_BM, gn = (N + BN - 1) / BN;
@@ -669,6 +688,10 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
     if (splits < 2) splits = 1;
   }
   const int kstep = ca.on == 1 ? ca.cbw : TC_BK;
+  if (tc_smem<BN>(cfg.stages, kstep) > TC_SMEM_MAX || cfg.stages < 2 || cfg.stages > TC_STAGES) {
+    set_error("gemm_tc: ring depth exceeds shared memory");
+    return DDPPO_E_CONFIG;
+  }
   int kchunk = (K + splits - 1) / splits;
   kchunk = (kchunk + kstep - 1) / kstep * kstep;
   splits = (K + kchunk - 1) / kchunk;
@@ -676,10 +699,10 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
   // persistent grid: one CTA per SM (two where shared memory allows), each walking tiles
   // with stride gridDim.x; the ring streams across tile boundaries
   const int stages = cfg.stages;
-  const int per_sm = tc_smem<BN>(stages) <= 110 * 1024 ? 2 : 1;
+  const int per_sm = tc_smem<BN>(stages, kstep) <= 110 * 1024 ? 2 : 1;
   const int ntiles = gm * gn * splits;
   const int grid = min(ntiles, ws.num_sms * per_sm);
-  gemm_tc_kernel<BN><<<grid, TC_PTHREADS, tc_smem<BN>(stages), s>>>(
+  gemm_tc_kernel<BN><<<grid, TC_PTHREADS, tc_smem<BN>(stages, kstep), s>>>(
       ma, mb, M, N, K, kchunk, (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu, trans,
       partial, ws.err, a_mn, b_mn, stages, gm, gn, splits, ca);
   DDPPO_CHECK_LAUNCH();
@@ -751,21 +774,24 @@ static int run_cfg(const GemmDesc& d, const GemmWorkspace& ws, const TcCfg& cfg,
 static TcCfg tune(const GemmDesc& d, const GemmWorkspace& ws, TcTuner& t, cudaStream_t s) {
   const bool swap = d.convw || (!d.conv && d.M < TC_BM && d.N > d.M);
   const int Nk = swap ? d.M : d.N;
+  const int kslot = kslot_of(d);
   std::vector<TcCfg> cands;
   for (int bn : {64, 128}) {
     if (bn == 128 && Nk <= 64) continue;
-    for (int st = 2; st <= 4; ++st)
+    for (int st : {2, 3, 4}) {
+      if (tc_smem_bn(bn, st, kslot) > TC_SMEM_MAX) continue;
       for (int sp = 0; sp <= 1; ++sp) {
         TcCfg c;
         c.bn = bn; c.stages = st; c.split = sp;
         cands.push_back(c);
       }
+    }
   }
   GemmDesc trial = d;
   trial.C = t.scratch;
   trial.ldc = d.N;
   trial.beta = 0.f;
-  TcCfg best = default_cfg(Nk);
+  TcCfg best = default_cfg(Nk, kslot);
   float best_ms = 1e30f;
   for (const TcCfg& c : cands) {
     if (run_cfg(trial, ws, c, s) != DDPPO_OK) continue;  // warm-up
@@ -782,7 +808,7 @@ static TcCfg tune(const GemmDesc& d, const GemmWorkspace& ws, TcTuner& t, cudaSt
 
 int gemm_tc(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s) {
   const bool swap = d.convw || (!d.conv && d.M < TC_BM && d.N > d.M);
-  TcCfg cfg = default_cfg(swap ? d.M : d.N);
+  TcCfg cfg = default_cfg(swap ? d.M : d.N, kslot_of(d));
   TcTuner* t = ws.tuner;
   if (t && t->on) {
     const ConvShape* cv = d.conv ? d.conv : d.convw;

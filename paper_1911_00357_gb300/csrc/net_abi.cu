@@ -221,17 +221,29 @@ static int collect_body(ddppo_ctx* x, const ddppo_rollout* ro, cudaStream_t s) {
   Net& n = *x->net;
   const int E = x->cfg.num_envs, T = x->cfg.rollout_T;
   const size_t ob = n.pix * op_bytes(n);
+  // the next episodes of the envs are generated on a side stream while the policy acts:
+  //   act(t) | prefetch(t-1)  ->  env_step(t)  ->  act(t+1) | prefetch(t) ...
+  auto fork_prefetch = [&]() -> int {
+    DDPPO_CHECK_CUDA(cudaEventRecord(x->ev_fork, s));
+    DDPPO_CHECK_CUDA(cudaStreamWaitEvent(x->side, x->ev_fork, 0));
+    DDPPO_TRY(launch_env_prefetch(x->sp, x->sb, x->prefetch_grid, x->side));
+    DDPPO_CHECK_CUDA(cudaEventRecord(x->ev_join, x->side));
+    return DDPPO_OK;
+  };
+  DDPPO_TRY(fork_prefetch());
   for (int t = 0; t < T; ++t) {
     const size_t o = (size_t)t * E;
     DDPPO_TRY(act_impl(x, (const char*)ro->obs + o * ob, ro->goal + o * 3, ro->prev_a + o,
                        ro->masks + o, ro->h, ro->c, ro->uniforms + o, ro->actions + o, ro->logp + o,
                        ro->values + o, s));
+    DDPPO_CHECK_CUDA(cudaStreamWaitEvent(s, x->ev_join, 0));
     const size_t o1 = (size_t)(t + 1) * E;
     DDPPO_TRY(ddppo_env_step(x, ro->actions + o, (char*)ro->obs + o1 * ob, ro->goal + o1 * 3,
                              ro->rewards + o, ro->dones + o, ro->info ? ro->info + o * 4 : nullptr, s));
     post_step_kernel<<<(E + 127) / 128, 128, 0, s>>>(E, ro->actions + o, ro->dones + o,
                                                      ro->prev_a + o1, ro->masks + o1);
     DDPPO_CHECK_LAUNCH();
+    if (t + 1 < T) DDPPO_TRY(fork_prefetch());
   }
   return DDPPO_OK;
 }

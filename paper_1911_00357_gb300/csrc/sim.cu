@@ -19,6 +19,8 @@
 // depth and the goal vector are FP32.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace ddppo {
@@ -65,6 +67,14 @@ enum : uint32_t { SM_GRID = 1, SM_ROOMS = 2, SM_GOAL = 3, SM_START = 4, SM_HEAD 
 __device__ __forceinline__ int grid_side(const SimParams& p, int env, int64_t ep) {
   if (p.nsizes <= 1) return p.grid_min;
   return p.grid_min << uni(chash(p.seed, env, ep, SM_SIZE, 0), (uint32_t)p.nsizes);
+}
+
+// scene buffers of env e in slot sl (0 / 1)
+__device__ __forceinline__ size_t slot_index(const SimParams& p, int e, int sl) {
+  return (size_t)sl * p.E + e;
+}
+__device__ __forceinline__ size_t cur_index(const SimParams& p, const SimBuffers& b, int e) {
+  return slot_index(p, e, b.slot[e]);
 }
 
 __device__ __forceinline__ void set_err(int32_t* err, int32_t f) {
@@ -186,10 +196,13 @@ size_t reset_smem_bytes(const SimParams& p) {
   return 4 * words * sizeof(uint32_t) + 256 * 4 * sizeof(int) + 32 * sizeof(int);
 }
 
-// Block-wide reset of env e (all = 1: episode 0, else the next episode). smem holds
-// reset_smem_bytes(p) bytes.
-__device__ void reset_env_block(const SimParams& p, const SimBuffers& b, int e, int all,
-                                uint32_t* smem) {
+// Block-wide generation of an episode of env e into scene slot sl: the scene of episode
+// `episode` (or of the next ones, up to 8 draws, when a scene has no valid start), its
+// BFS geodesic field, and the start state written to st_out. smem holds
+// reset_smem_bytes(p) bytes. Callers read whatever they need of the env's state before
+// the call; st_out may be the env's own state.
+__device__ void gen_episode(const SimParams& p, const SimBuffers& b, int e, int64_t episode, int sl,
+                            int32_t* st, uint32_t* smem) {
   const int WMAX = p.grid_max * p.grid_max / 32;
   uint32_t* Fw = smem;
   uint32_t* Vw = Fw + WMAX;
@@ -201,12 +214,11 @@ __device__ void reset_env_block(const SimParams& p, const SimBuffers& b, int e, 
 
   const int tid = threadIdx.x, nt = blockDim.x;
   const size_t GM = (size_t)p.grid_max * p.grid_max;
-  uint8_t* grid = b.grids + GM * e;
-  uint32_t* bits = b.bits + (size_t)WMAX * e;
-  int32_t* dist = b.dists + GM * e;
-  int32_t* st = b.states + (size_t)ST_N * e;
-  int64_t episode = all ? 0 : (int64_t)st[ST_EPISODE] + 1;
-  __syncthreads();  // every thread has read the old episode before thread 0 may rewrite it
+  const size_t si_ = slot_index(p, e, sl);
+  uint8_t* grid = b.grids + GM * si_;
+  uint32_t* bits = b.bits + (size_t)WMAX * si_;
+  int32_t* dist = b.dists + GM * si_;
+  __syncthreads();  // every thread has read the caller's state before thread 0 may rewrite it
 
   for (int tries = 0; tries < 8; ++tries, ++episode) {
     const int g = grid_side(p, e, episode);
@@ -302,12 +314,42 @@ __device__ void reset_env_block(const SimParams& p, const SimBuffers& b, int e, 
   }
 }
 
+// the episode that follows env e's current one: the prepared slot when ready, else
+// generated now into the other slot
+__device__ void next_episode(const SimParams& p, const SimBuffers& b, int e, uint32_t* smem) {
+  int32_t* st = b.states + (size_t)ST_N * e;
+  const int tid = threadIdx.x;
+  const int ready = b.ready[e], sl = b.slot[e];
+  const int64_t ep = (int64_t)st[ST_EPISODE] + 1;
+  __syncthreads();
+  if (ready) {
+    if (tid < ST_N) st[tid] = b.pend[(size_t)ST_N * e + tid];
+  } else {
+    gen_episode(p, b, e, ep, sl ^ 1, st, smem);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    b.slot[e] = (uint8_t)(sl ^ 1);
+    b.ready[e] = 0;
+  }
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(RESET_THREADS) reset_kernel(SimParams p, SimBuffers b, int all) {
   const int e = blockIdx.x;
   if (e >= p.E) return;
   if (!all && !b.need[e]) return;
   extern __shared__ __align__(16) uint32_t smem[];
-  reset_env_block(p, b, e, all, smem);
+  if (all) {
+    gen_episode(p, b, e, 0, 0, b.states + (size_t)ST_N * e, smem);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      b.slot[e] = 0;
+      b.ready[e] = 0;
+    }
+  } else {
+    next_episode(p, b, e, smem);
+  }
 }
 
 int launch_reset(const SimParams& p, const SimBuffers& b, bool all, cudaStream_t s) {
@@ -357,8 +399,9 @@ __device__ int step_env(const SimParams& p, const SimBuffers& b, int e,
                         const int32_t* __restrict__ actions, float* __restrict__ reward,
                         uint8_t* __restrict__ done, float* __restrict__ info) {
   int32_t* st = b.states + (size_t)ST_N * e;
-  const uint8_t* grid = b.grids + (size_t)p.grid_max * p.grid_max * e;
-  const int32_t* dist = b.dists + (size_t)p.grid_max * p.grid_max * e;
+  const size_t ci = cur_index(p, b, e);
+  const uint8_t* grid = b.grids + (size_t)p.grid_max * p.grid_max * ci;
+  const int32_t* dist = b.dists + (size_t)p.grid_max * p.grid_max * ci;
   int a = actions[e];
   if (a < 0 || a > 3) { set_err(b.err, ERRF_BOUNDS); a = 0; }
   const int g = st[ST_GRID], cs = p.cell_u;
@@ -448,7 +491,7 @@ __device__ void render_env_block(const SimParams& p, const SimBuffers& b, int e,
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
             smem_u32(sbits)),
-        "l"(b.bits + (size_t)WMAX * e), "r"(bytes), "r"(bar)
+        "l"(b.bits + (size_t)WMAX * cur_index(p, b, e)), "r"(bytes), "r"(bar)
         : "memory");
   }
   uint32_t ok = 0;
@@ -572,8 +615,8 @@ __global__ void __launch_bounds__(RESET_THREADS)
     if (tid == 0) s_fin = step_env(p, b, e, actions, reward, done, info);
     __syncthreads();
     if (s_fin) {
-      reset_env_block(p, b, e, 0, smem);
-      // the new wall bits were written through the generic proxy; the TMA copy that
+      next_episode(p, b, e, smem);
+      // new wall bits may have been written through the generic proxy; the TMA copy that
       // reads them next goes through the async proxy
       asm volatile("fence.proxy.async.global;" ::: "memory");
     }
@@ -590,6 +633,63 @@ __global__ void __launch_bounds__(RESET_THREADS)
       __threadfence();
     }
   }
+}
+
+// Prefetch: CTAs take envs from a second self-re-arming work counter and generate the
+// next episode of every env whose other slot is not ready. Runs beside the policy's
+// forward pass; the next env step adopts the prepared slot instead of generating it.
+__global__ void __launch_bounds__(RESET_THREADS) env_prefetch_kernel(SimParams p, SimBuffers b) {
+  extern __shared__ __align__(128) uint32_t smem[];
+  __shared__ int s_env;
+  const int tid = threadIdx.x;
+  for (int guard = 0; guard <= p.E; ++guard) {
+    if (tid == 0) s_env = atomicAdd(&b.work[2], 1);
+    __syncthreads();
+    const int e = s_env;
+    __syncthreads();
+    if (e >= p.E) break;
+    if (b.ready[e]) continue;
+    const int32_t* st = b.states + (size_t)ST_N * e;
+    const int64_t ep = (int64_t)st[ST_EPISODE] + 1;
+    gen_episode(p, b, e, ep, b.slot[e] ^ 1, b.pend + (size_t)ST_N * e, smem);
+    __syncthreads();
+    if (tid == 0) b.ready[e] = 1;
+  }
+  if (tid == 0) {
+    __threadfence();
+    if (atomicAdd(&b.work[3], 1) == (int)gridDim.x - 1) {
+      b.work[2] = 0;
+      b.work[3] = 0;
+      __threadfence();
+    }
+  }
+}
+
+int launch_env_prefetch(const SimParams& p, const SimBuffers& b, int grid, cudaStream_t s) {
+  env_prefetch_kernel<<<grid, RESET_THREADS, reset_smem_bytes(p), s>>>(p, b);
+  DDPPO_CHECK_LAUNCH();
+  return DDPPO_OK;
+}
+
+__global__ void copy_current_kernel(SimParams p, SimBuffers b, uint8_t* __restrict__ grids,
+                                    int32_t* __restrict__ dists) {
+  const int e = blockIdx.y;
+  const size_t GM = (size_t)p.grid_max * p.grid_max, ci = cur_index(p, b, e);
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < GM;
+       i += (size_t)gridDim.x * blockDim.x) {
+    if (grids) grids[GM * e + i] = b.grids[GM * ci + i];
+    if (dists) dists[GM * e + i] = b.dists[GM * ci + i];
+  }
+}
+
+int launch_copy_current(const SimParams& p, const SimBuffers& b, uint8_t* grids, int32_t* dists,
+                        cudaStream_t s) {
+  if (p.E > 65535) { set_error("env_grids: too many envs"); return DDPPO_E_CONFIG; }
+  const size_t GM = (size_t)p.grid_max * p.grid_max;
+  const unsigned bx = (unsigned)std::min<size_t>((GM + 255) / 256, 64);
+  copy_current_kernel<<<dim3(bx, p.E), 256, 0, s>>>(p, b, grids, dists);
+  DDPPO_CHECK_LAUNCH();
+  return DDPPO_OK;
 }
 
 int launch_env_step(const SimParams& p, const SimBuffers& b, int grid, const int32_t* actions,
@@ -623,6 +723,8 @@ int sim_configure(const SimParams& p) {
   const size_t ps = rs > gs ? rs : gs;
   DDPPO_CHECK_CUDA(cudaFuncSetAttribute(env_step_persistent_kernel,
                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ps));
+  DDPPO_CHECK_CUDA(cudaFuncSetAttribute(env_prefetch_kernel,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs));
   return DDPPO_OK;
 }
 

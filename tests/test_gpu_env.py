@@ -112,6 +112,42 @@ def test_step_and_depth_parity(world):
         env.close()
 
 
+@pytest.mark.parametrize("world", ["rooms128_bf16", "rooms_mixed", "bernoulli_mixed"])
+def test_prefetched_episodes_match_the_oracle(world):
+    """Next episodes generated ahead of time on a second stream (as the rollout does)
+    give the same worlds, rewards, dones and frames as generating them at the reset.
+    A high stop rate makes most steps end some episodes."""
+    cfg = _cfg(world)
+    E = cfg.num_envs
+    env = Env(cfg)
+    side = torch.cuda.Stream()
+    main = torch.cuda.current_stream()
+    try:
+        env.reset()
+        ref = OS.BatchSim(sim_config_from(cfg))
+        ref.reset()
+        K = 48
+        acts = I.random_actions(K, E, seed=23, p_stop=0.3)
+        for t in range(K):
+            if t % 3 != 2:   # some steps run without a prefetch: those resets are generated in place
+                side.wait_stream(main)
+                B.ddppo_env_prefetch(env.h, side)
+                main.wait_stream(side)
+            env.step(acts[t])
+            r, d, spl, info = ref.step(acts[t])
+            torch.cuda.synchronize()
+            np.testing.assert_array_equal(env.reward.cpu().numpy().view(np.uint32), r.view(np.uint32))
+            np.testing.assert_array_equal(env.done.cpu().numpy(), d)
+            np.testing.assert_array_equal(env.get_state(), ref.states)
+        assert int(ref.states[:, OS.S_EPISODE].sum()) >= E   # resets did happen
+        nb, n, _, _ = _depth_mismatch(env, ref)
+        assert nb <= max(0, int(1e-4 * n)), (nb, n)
+        _compare_world(env, ref, E)
+        assert B.ddppo_device_status(env.h) == 0
+    finally:
+        env.close()
+
+
 def test_episodes_end_and_reset_inside_the_step():
     """Stop everywhere: every env ends its episode, draws episode 1, and the new first
     frame is what env_step returns (auto-reset)."""
