@@ -177,7 +177,7 @@ __host__ __device__ constexpr uint32_t f16_idesc(int M, int N, int a_mn = 0, int
 constexpr int TC_PTHREADS = 192;
 
 template <int BN>
-__global__ void __launch_bounds__(TC_PTHREADS, 1)
+__global__ void __launch_bounds__(TC_PTHREADS, 2)
     gemm_tc_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                    int M, int N, int K, int kchunk, float* __restrict__ C, int ldc, int c_bf16,
                    float beta, const float* __restrict__ bias, int relu, int trans_out,
@@ -186,6 +186,8 @@ __global__ void __launch_bounds__(TC_PTHREADS, 1)
   extern __shared__ __align__(1024) uint8_t dyn[];
   __shared__ TcSmem ctl;
   __shared__ uint64_t acc_full[2], acc_empty[2];
+  // epilogue staging, one 32 x 32 block per epilogue warp (static: known to be shared memory)
+  __shared__ float epi_stage[4][32 * TC_EPI_PITCH];
   // stage sizes follow the K extent of one ring slot (32 channels for narrow convolutions)
   const int kslot = ca.on == 1 ? ca.cbw : TC_BK;
   const uint32_t A_BYTES = TC_BM * kslot * 2, B_BYTES = BN * kslot * 2;
@@ -345,7 +347,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 1)
   } else {
     // epilogue warps 2..5: warp w reads TMEM lanes 32 (w % 4) .. +31
     const int q = warp & 3;
-    float* stage_out = (float*)(sB + stages * B_BYTES) + q * 32 * TC_EPI_PITCH;
+    float* stage_out = epi_stage[q];
     const int Mo = trans_out ? N : M, No = trans_out ? M : N;
     uint32_t ti = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++ti) {
@@ -357,6 +359,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 1)
       const int row = m0 + q * 32 + lane;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
+        if (n0 + c0 >= N) break;  // columns past N: nothing to read or store
         uint32_t r[32];
         const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * BN + (uint32_t)c0;
         asm volatile(
@@ -369,7 +372,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 1)
               "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
             : "r"(taddr));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (!ok || n0 + c0 >= N) continue;
+        if (!ok) continue;
         if (trans_out) {
           if (row >= M) continue;
 #pragma unroll
@@ -390,30 +393,49 @@ __global__ void __launch_bounds__(TC_PTHREADS, 1)
           }
           continue;
         }
+        // transpose through shared memory: lane l then owns column c0 + l of the 32 rows,
+        // so every store instruction writes 32 consecutive values of one row
 #pragma unroll
         for (int j = 0; j < 32; ++j) stage_out[lane * TC_EPI_PITCH + j] = __uint_as_float(r[j]);
         __syncwarp();
         const int col = n0 + c0 + lane;
         const bool cin = col < N;
         const float bv = (bias && cin) ? bias[col] : 0.f;
-#pragma unroll 4
-        for (int i = 0; i < 32; ++i) {
-          const int rr = m0 + q * 32 + i;
-          if (rr >= M) break;
-          float v = stage_out[i * TC_EPI_PITCH + lane];
-          if (!cin) continue;
+        const int nrows = min(32, M - (m0 + q * 32));
+        // eight rows at a time: the shared-memory loads of a group are all in flight before
+        // its global stores
+#pragma unroll 1
+        for (int i0 = 0; i0 < 32; i0 += 8) {
+          float v[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) v[k] = stage_out[(i0 + k) * TC_EPI_PITCH + lane];
+          if (!cin || i0 >= nrows) continue;
           if (partial) {
-            partial[((size_t)z * Mo + rr) * No + col] = v;
+            float* pz = partial + ((size_t)z * Mo + m0 + q * 32 + i0) * No + col;
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              if (i0 + k < nrows) pz[(size_t)k * No] = v[k];
             continue;
           }
-          const size_t o = (size_t)rr * ldc + col;
-          if (beta != 0.f) v += beta * C[o];
-          v += bv;
-          if (relu) v = fmaxf(v, 0.f);
-          if (c_bf16) ((__nv_bfloat16*)C)[o] = __float2bfloat16_rn(v);
-          else C[o] = v;
+          const size_t o0 = (size_t)(m0 + q * 32 + i0) * ldc + col;
+          if (beta != 0.f) {
+            float cv[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) cv[k] = i0 + k < nrows ? C[o0 + (size_t)k * ldc] : 0.f;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) v[k] += beta * cv[k];
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            float x = v[k] + bv;
+            if (relu) x = fmaxf(x, 0.f);
+            if (i0 + k < nrows) {
+              if (c_bf16) ((__nv_bfloat16*)C)[o0 + (size_t)k * ldc] = __float2bfloat16_rn(x);
+              else C[o0 + (size_t)k * ldc] = x;
+            }
+          }
         }
-        __syncwarp();
+        __syncwarp();  // the next chunk rewrites stage_out
       }
       // the accumulator may be overwritten by the next tile
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -548,17 +570,20 @@ bool gemm_conv_supported(const ConvShape& c, const void* input) {
   return c.k >= 1 && c.s >= 1 && c.s <= 8;
 }
 
-constexpr size_t TC_SMEM_MAX = 225 * 1024;  // dynamic part, below the 227 KiB opt-in limit
+// dynamic part; the static part (barriers, 17 KiB epilogue staging) makes up the rest of
+// the 227 KiB opt-in limit
+constexpr size_t TC_SMEM_MAX = 205 * 1024;
+constexpr size_t TC_SMEM_TWO_PER_SM = 95 * 1024;  // dynamic bytes that still fit two CTAs per SM
 template <int BN>
 static size_t tc_smem(int stages, int kslot) {
-  return (size_t)stages * (TC_BM + BN) * kslot * 2 + 4 * 32 * TC_EPI_PITCH * 4 + 1024;
+  return (size_t)stages * (TC_BM + BN) * kslot * 2 + 1024;
 }
 static size_t tc_smem_bn(int bn, int stages, int kslot) {
   return bn == 128 ? tc_smem<128>(stages, kslot) : tc_smem<64>(stages, kslot);
 }
 // deepest ring within a budget (two CTAs per SM for BN = 64, one for BN = 128)
 static int ring_for(int bn, int kslot) {
-  const size_t budget = bn == 64 ? 110 * 1024 : 200 * 1024;
+  const size_t budget = bn == 64 ? TC_SMEM_TWO_PER_SM : TC_SMEM_MAX;
   int st = TC_STAGES;
   while (st > 2 && tc_smem_bn(bn, st, kslot) > budget) --st;
   return st;
@@ -699,7 +724,7 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
   // persistent grid: one CTA per SM (two where shared memory allows), each walking tiles
   // with stride gridDim.x; the ring streams across tile boundaries
   const int stages = cfg.stages;
-  const int per_sm = tc_smem<BN>(stages, kstep) <= 110 * 1024 ? 2 : 1;
+  const int per_sm = tc_smem<BN>(stages, kstep) <= TC_SMEM_TWO_PER_SM ? 2 : 1;
   const int ntiles = gm * gn * splits;
   const int grid = min(ntiles, ws.num_sms * per_sm);
   gemm_tc_kernel<BN><<<grid, TC_PTHREADS, tc_smem<BN>(stages, kstep), s>>>(
