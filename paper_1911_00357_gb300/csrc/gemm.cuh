@@ -15,6 +15,7 @@ namespace ddppo {
 // (ky*k + kx)*C + c. K = k*k*C; B is the [Cout, K] weight matrix.
 struct ConvShape {
   int N = 0, H = 0, W = 0, C = 0, Ho = 0, Wo = 0, k = 0, s = 1, p = 0;
+  int Cout = 0;  // output channels (0: unknown; the halo path then stays off)
 };
 
 struct GemmDesc {

@@ -31,6 +31,10 @@ namespace ddppo {
 constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 16;  // TC_STAGES: deepest ring
 constexpr int TC_EPI_PITCH = 33;  // floats per staged row (bank-conflict-free transpose)
 constexpr uint32_t TC_SPIN_LIMIT = 1u << 22;
+// dynamic part; the static part (barriers, 17 KiB epilogue staging) makes up the rest of
+// the 227 KiB opt-in limit
+constexpr size_t TC_SMEM_MAX = 205 * 1024;
+constexpr size_t TC_SMEM_TWO_PER_SM = 94 * 1024;  // dynamic bytes that still fit two CTAs per SM
 
 struct TcSmem {
   // stage buffers are carved from dynamic shared memory (1024-byte aligned)
@@ -119,13 +123,46 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
 //         one box of cbw channels x 128 pixels per K block;
 // on = 2: weight gradient, A = [(tap, channel), output pixels] MN-major: per 64-pixel K
 //         block, 128 / cbw boxes of 64 pixels x cbw channels (one per tap / channel block).
+// on = 3: halo (stride-1 'same' convolution): per channel block ONE box of the input (the
+//         tile's output rows plus the filter's halo, rows of pitch Wp = W + 2p) is staged,
+//         and every filter tap reads it as a row-shifted view. Tile rows are "anchors" on
+//         the Wp-pitch grid; anchors outside the image are computed and discarded.
 struct ConvA {
   int on = 0;
   int C = 0, cbw = 64;       // input channels, channels per K-block (64 or 32)
   int k = 1, s = 1, p = 0;
   int Ho = 1, Wo = 1;
   int hi = 1;                // output rows per pixel block (or Ho when a block spans images)
+  // halo mode
+  int N = 1, H = 1, W = 1;   // images and their (input = output) size
+  int Wp = 1, Hh = 1;        // anchor row pitch W + 2p, anchor rows per image H + 2p
+  int ni = 0;                // images per tile (small images), or 0: tiles within one image
+  int tpi = 1;               // tiles per image when ni == 0
+  int rows_box = 1;          // rows of the halo box (per image)
+  int tiles_m = 1;
+  uint32_t halo_bytes = 0;   // stride of the two halo stages in shared memory
+  uint32_t box_bytes = 0;    // bytes one halo box delivers
 };
+
+// output row of anchor r of halo-mode tile tm, or -1 when the anchor is not an output pixel
+__device__ __forceinline__ long long halo_out_row(const ConvA& ca, int tm, int r) {
+  int img, y, x;
+  if (ca.ni) {
+    const int per = ca.Hh * ca.Wp;
+    const int i = r / per, rem = r - i * per;
+    if (i >= ca.ni) return -1;
+    img = tm * ca.ni + i;
+    y = rem / ca.Wp;
+    x = rem - y * ca.Wp;
+  } else {
+    img = tm / ca.tpi;
+    const int a = (tm - img * ca.tpi) * 128 + r;
+    y = a / ca.Wp;
+    x = a - y * ca.Wp;
+  }
+  if (img >= ca.N || y >= ca.H || x >= ca.W) return -1;
+  return ((long long)img * ca.H + y) * ca.W + x;
+}
 
 // MN-major tile with 64-byte rows (32 MN-elements), 64-byte swizzle: blocks of 32 MN
 // columns 64 rows (4 KiB) apart (LBO), 8-row K groups 512 B apart (SBO)
@@ -188,12 +225,14 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
   __shared__ uint64_t acc_full[2], acc_empty[2];
   // epilogue staging, one 32 x 32 block per epilogue warp (static: known to be shared memory)
   __shared__ float epi_stage[4][32 * TC_EPI_PITCH];
-  // stage sizes follow the K extent of one ring slot (32 channels for narrow convolutions)
-  const int kslot = ca.on == 1 ? ca.cbw : TC_BK;
-  const uint32_t A_BYTES = TC_BM * kslot * 2, B_BYTES = BN * kslot * 2;
+  // stage sizes follow the K extent of one ring slot (32 channels for narrow convolutions);
+  // the halo mode has a ring of `stages` halo boxes (A) and all the weights resident (B)
+  const bool halo = ca.on == 3;
+  const int kslot = (ca.on == 1 || halo) ? ca.cbw : TC_BK;
+  const uint32_t A_BYTES = halo ? ca.halo_bytes : TC_BM * kslot * 2, B_BYTES = BN * kslot * 2;
   uint8_t* base = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = base;
-  uint8_t* sB = base + stages * A_BYTES;
+  uint8_t* sB = base + stages * A_BYTES;  // halo mode: the resident weights
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = tiles_m * tiles_n * splits;
   volatile int* abort = &ctl.abort;
@@ -203,6 +242,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
       mbar_init(&ctl.full[s], 1);
       mbar_init(&ctl.empty[s], 1);
     }
+    mbar_init(&ctl.done, 1);  // halo mode: resident weights landed
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
@@ -221,7 +261,87 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = ctl.tmem_base;
 
-  if (warp == 0) {
+  if (warp == 0 && halo) {
+    if (lane == 0) {
+      // halo producer: the weights of every (tap, channel block) once, resident for the
+      // whole kernel; then per (tile, channel block) one input box through the ring
+      const int nkk = ca.k * ca.k, ncb = ca.C / ca.cbw;
+      const uint32_t wbox = (uint32_t)BN * ca.cbw * 2;
+      mbar_expect_tx(&ctl.done, wbox * nkk * ncb);
+      for (int tap = 0; tap < nkk; ++tap)
+        for (int cb = 0; cb < ncb; ++cb)
+          tma_load_2d(sB + (tap * ncb + cb) * wbox, &mapB, &ctl.done, tap * ca.C + cb * ca.cbw, 0);
+      uint32_t hit = 0;
+      for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
+        const int tm = t % tiles_m, z = t / (tiles_m * tiles_n);
+        int img, ybase;
+        if (ca.ni) {
+          img = tm * ca.ni;
+          ybase = -ca.p;
+        } else {
+          img = tm / ca.tpi;
+          ybase = ((tm - img * ca.tpi) * TC_BM) / ca.Wp - ca.p;
+        }
+        const int cb_end = min(ca.C, z * kchunk + kchunk);
+        for (int c0 = z * kchunk; c0 < cb_end; c0 += ca.cbw, ++hit) {
+          const int hs = hit % stages;
+          if (!mbar_wait(&ctl.empty[hs], ((hit / stages) & 1u) ^ 1u, abort, err)) break;
+          mbar_expect_tx(&ctl.full[hs], ca.box_bytes);
+          tma_load_4d(sA + hs * A_BYTES, &mapA, &ctl.full[hs], c0, -ca.p, ybase, img);
+        }
+      }
+    }
+  } else if (warp == 1 && halo) {
+    if (lane == 0) {
+      // halo MMA issuer: tap (ky, kx) reads the staged box from row off + ky Wp + kx on
+      const uint32_t idesc = f16_idesc(TC_BM, BN, 0, 0);
+      const int nkk = ca.k * ca.k, ncb = ca.C / ca.cbw, rb = ca.cbw * 2;
+      const uint32_t wbox = (uint32_t)BN * ca.cbw * 2;
+      const bool wok = mbar_wait(&ctl.done, 0u, abort, err);
+      uint32_t hit = 0, ti = 0;
+      for (int t = blockIdx.x; t < ntiles && wok && !*abort; t += gridDim.x, ++ti) {
+        const int tm = t % tiles_m, z = t / (tiles_m * tiles_n);
+        const int off = ca.ni ? 0 : ((tm % ca.tpi) * TC_BM) % ca.Wp;
+        const uint32_t buf = ti & 1u, bph = (ti >> 1) & 1u;
+        if (!mbar_wait(&acc_empty[buf], bph ^ 1u, abort, err)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t dacc = tmem + buf * BN;
+        uint32_t acc = 0;
+        const int cb_end = min(ca.C, z * kchunk + kchunk);
+        for (int c0 = z * kchunk; c0 < cb_end; c0 += ca.cbw, ++hit) {
+          const int hs = hit % stages;
+          if (!mbar_wait(&ctl.full[hs], (hit / stages) & 1u, abort, err)) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t h0 = smem_addr(sA + hs * A_BYTES);
+          const int cb = c0 / ca.cbw;
+          for (int tap = 0; tap < nkk; ++tap) {
+            const int ky = tap / ca.k, kx = tap - ky * ca.k;
+            const uint32_t arow = h0 + (uint32_t)(off + ky * ca.Wp + kx) * rb;
+            const uint32_t b0 = smem_addr(sB + (tap * ncb + cb) * wbox);
+            for (int kq = 0; kq < ca.cbw / 16; ++kq) {
+              const uint64_t da = ca.cbw == 32 ? sw64_desc(arow + kq * 32) : sw128_desc(arow + kq * 32);
+              const uint64_t db = ca.cbw == 32 ? sw64_desc(b0 + kq * 32) : sw128_desc(b0 + kq * 32);
+              asm volatile(
+                  "{\n\t.reg .pred p;\n\t"
+                  "setp.ne.b32 p, %4, 0;\n\t"
+                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dacc),
+                  "l"(da), "l"(db), "r"(idesc), "r"(acc)
+                  : "memory");
+              acc = 1u;
+            }
+          }
+          asm volatile(
+              "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                  smem_addr(&ctl.empty[hs]))
+              : "memory");
+        }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_addr(&acc_full[buf]))
+            : "memory");
+      }
+    }
+  } else if (warp == 0) {
     if (lane == 0) {
       // TMA producer over every (tile, k-block) of this CTA
       const int kstep = ca.on == 1 ? ca.cbw : TC_BK;
@@ -357,6 +477,9 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
       const bool ok = mbar_wait(&acc_full[buf], bph, abort, err);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const int row = m0 + q * 32 + lane;
+      // halo mode: output row of this lane's tile row, computed once per tile and handed to
+      // the row loop by shuffles
+      const long long my_orow = halo ? halo_out_row(ca, tm, q * 32 + lane) : 0;
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         if (n0 + c0 >= N) break;  // columns past N: nothing to read or store
@@ -401,6 +524,37 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
         const int col = n0 + c0 + lane;
         const bool cin = col < N;
         const float bv = (bias && cin) ? bias[col] : 0.f;
+        if (halo) {
+#pragma unroll 1
+          for (int i0 = 0; i0 < 32; i0 += 8) {
+            float v[8];
+            long long orows[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              v[k] = stage_out[(i0 + k) * TC_EPI_PITCH + lane];
+              orows[k] = __shfl_sync(0xffffffffu, my_orow, i0 + k);
+            }
+            if (!cin) continue;
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const long long orow = orows[k];
+              if (orow < 0) continue;
+              float x = v[k];
+              if (partial) {
+                partial[((size_t)z * Mo + orow) * No + col] = x;
+                continue;
+              }
+              const size_t o = (size_t)orow * ldc + col;
+              if (beta != 0.f) x += beta * C[o];
+              x += bv;
+              if (relu) x = fmaxf(x, 0.f);
+              if (c_bf16) ((__nv_bfloat16*)C)[o] = __float2bfloat16_rn(x);
+              else C[o] = x;
+            }
+          }
+          __syncwarp();
+          continue;
+        }
         const int nrows = min(32, M - (m0 + q * 32));
         // eight rows at a time: the shared-memory loads of a group are all in flight before
         // its global stores
@@ -515,6 +669,76 @@ static bool make_conv_map(CUtensorMap* m, const void* x, const ConvShape& c, con
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// Halo-mode geometry of a stride-1 'same' convolution (odd k, p = k / 2, C = 32 or a
+// multiple of 64). Fills ca when non-null; false when the shape is not covered.
+static int halo_bn(int cout) { return cout <= 32 ? 32 : cout <= 64 ? 64 : cout <= 128 ? 128 : 0; }
+constexpr size_t TC_HALO_WEIGHTS_MAX = 96 * 1024;  // resident weights of one halo convolution
+
+// Taken for 32-channel inputs, where the 4-D gather moves 64-byte rows once per filter tap;
+// with 64 or more channels the resident weights leave room for one CTA per SM and the
+// gather path is faster.
+static bool halo_geom(const ConvShape& c, ConvA* ca) {
+  if (c.s != 1 || c.k % 2 == 0 || c.p != c.k / 2 || c.C != 32) return false;
+  if (c.Ho != c.H || c.Wo != c.W) return false;
+  const int bn = halo_bn(c.Cout);
+  if (!bn) return false;
+  const size_t wbytes = (size_t)bn * c.k * c.k * c.C * 2;
+  if (wbytes > TC_HALO_WEIGHTS_MAX) return false;
+  const int Wp = c.W + 2 * c.p, Hh = c.H + 2 * c.p, per = Hh * Wp;
+  const int cbw = c.C == 32 ? 32 : 64, rb = cbw * 2;
+  int ni, tpi, rows_box, rows_need;
+  if (per <= TC_BM) {
+    ni = TC_BM / per;
+    tpi = 1;
+    rows_box = Hh;
+    rows_need = TC_BM + (c.k - 1) * (Wp + 1);
+  } else {
+    ni = 0;
+    tpi = (c.H * Wp + TC_BM - 1) / TC_BM;
+    // rows of the box: enough for the farthest row read from the largest in-row offset
+    rows_box = (Wp - 1 + TC_BM - 1 + (c.k - 1) * (Wp + 1)) / Wp + 1;
+    rows_need = Wp - 1 + TC_BM + (c.k - 1) * (Wp + 1);
+  }
+  if (Wp > 256 || rows_box > 256) return false;
+  const int box_rows = rows_box * Wp * (ni ? ni : 1);
+  const int rows_alloc = std::max(box_rows, rows_need);
+  const uint32_t halo_bytes = (uint32_t)(((size_t)rows_alloc * rb + 1023) / 1024 * 1024);
+  if (2 * (size_t)halo_bytes + wbytes + 1024 > TC_SMEM_MAX) return false;
+  if (ca) {
+    ca->on = 3;
+    ca->C = c.C; ca->cbw = cbw; ca->k = c.k; ca->s = 1; ca->p = c.p;
+    ca->Ho = c.Ho; ca->Wo = c.Wo;
+    ca->N = c.N; ca->H = c.H; ca->W = c.W; ca->Wp = Wp; ca->Hh = Hh;
+    ca->ni = ni; ca->tpi = tpi; ca->rows_box = rows_box;
+    ca->tiles_m = ni ? (c.N + ni - 1) / ni : c.N * tpi;
+    ca->halo_bytes = halo_bytes;
+    ca->box_bytes = (uint32_t)box_rows * rb;
+  }
+  return true;
+}
+
+// shared memory of a halo-mode launch: the box ring and the resident weights
+static size_t halo_smem(const ConvA& ca, int bn, int stages) {
+  return (size_t)stages * ca.halo_bytes + (size_t)bn * ca.k * ca.k * ca.C * 2 + 1024;
+}
+
+// NHWC bf16 input as [C, W, H, N]; one box = the halo of a tile: cbw channels x Wp columns
+// (from x = -p) x rows_box rows x (ni or 1) images, zero outside the image
+static bool make_halo_map(CUtensorMap* m, const void* x, const ConvShape& c, const ConvA& ca) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[4] = {(cuuint64_t)c.C, (cuuint64_t)c.W, (cuuint64_t)c.H, (cuuint64_t)c.N};
+  cuuint64_t strides[3] = {(cuuint64_t)c.C * 2, (cuuint64_t)c.W * c.C * 2,
+                           (cuuint64_t)c.H * c.W * c.C * 2};
+  cuuint32_t box[4] = {(cuuint32_t)ca.cbw, (cuuint32_t)ca.Wp, (cuuint32_t)ca.rows_box,
+                       (cuuint32_t)(ca.ni ? ca.ni : 1)};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(x), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE,
+            ca.cbw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // weight-gradient gather: 64-pixel K blocks of whole output rows (or whole images)
 static bool convw_geom(const ConvShape& c, int* hi, int* ni) {
   if (c.Wo < 1 || c.Ho < 1 || 64 % c.Wo) return false;
@@ -556,9 +780,9 @@ bool gemm_convw_supported(const ConvShape& c, const void* input, const void* dz)
   return convw_geom(c, &hi, &ni);
 }
 
-bool gemm_conv_supported(const ConvShape& c, const void* input) {
-  if (!encode_fn()) return false;
-  if (c.C % 32 || c.C <= 0 || ((uintptr_t)input & 15)) return false;
+// the 4-D gather path: whole output rows per 128-pixel tile (or whole images per tile)
+static bool gather_ok(const ConvShape& c) {
+  if (c.C % 32 || c.C <= 0) return false;
   if (TC_BM % c.Wo || c.Wo * c.s > 256) return false;
   const int pix = c.Ho * c.Wo;
   if (pix >= TC_BM) {
@@ -570,10 +794,11 @@ bool gemm_conv_supported(const ConvShape& c, const void* input) {
   return c.k >= 1 && c.s >= 1 && c.s <= 8;
 }
 
-// dynamic part; the static part (barriers, 17 KiB epilogue staging) makes up the rest of
-// the 227 KiB opt-in limit
-constexpr size_t TC_SMEM_MAX = 205 * 1024;
-constexpr size_t TC_SMEM_TWO_PER_SM = 95 * 1024;  // dynamic bytes that still fit two CTAs per SM
+bool gemm_conv_supported(const ConvShape& c, const void* input) {
+  if (!encode_fn() || ((uintptr_t)input & 15)) return false;
+  return halo_geom(c, nullptr) || gather_ok(c);
+}
+
 template <int BN>
 static size_t tc_smem(int stages, int kslot) {
   return (size_t)stages * (TC_BM + BN) * kslot * 2 + 1024;
@@ -599,9 +824,10 @@ bool gemm_tc_supported(const GemmDesc& d) {
 }
 
 struct TcCfg {
-  int bn = 64;       // N tile: 64 or 128
+  int bn = 64;       // N tile: 32 (halo convolutions), 64 or 128
   int stages = 3;    // shared-memory ring depth: 2..TC_STAGES
   int split = 0;     // 0: split K when the grid would be short of SMs; 1: never split
+  int halo = 0;      // convolution through the halo path (1) or the 4-D gather (0)
 };
 
 struct TcTuner {
@@ -634,8 +860,8 @@ void tc_tuner_enable(TcTuner* t, bool on) { if (t) t->on = on; }
 int64_t tc_tuner_shapes(const TcTuner* t) { return t ? (int64_t)t->table.size() : 0; }
 
 // table image: int32 words {magic, version, count} then count records of 7 key words and
-// 3 configuration words (N tile, ring depth, split policy)
-static const int32_t kTuneMagic = 0x54544444, kTuneVersion = 4, kTuneRec = 10;
+// 4 configuration words (N tile, ring depth, split policy, halo path)
+static const int32_t kTuneMagic = 0x54544444, kTuneVersion = 6, kTuneRec = 11;
 
 size_t tc_tuner_export(const TcTuner* t, void* buf, size_t cap) {
   const size_t cnt = t ? t->table.size() : 0;
@@ -650,6 +876,7 @@ size_t tc_tuner_export(const TcTuner* t, void* buf, size_t cap) {
       r[0] = std::get<0>(k); r[1] = std::get<1>(k); r[2] = std::get<2>(k); r[3] = std::get<3>(k);
       r[4] = std::get<4>(k); r[5] = std::get<5>(k); r[6] = std::get<6>(k);
       r[7] = kv.second.bn; r[8] = kv.second.stages; r[9] = kv.second.split;
+      r[10] = kv.second.halo;
       r += kTuneRec;
     }
   return need;
@@ -666,8 +893,9 @@ int tc_tuner_import(TcTuner* t, const void* buf, size_t size) {
   const int32_t* r = w + 3;
   for (int32_t i = 0; i < w[2]; ++i, r += kTuneRec) {
     TcCfg c;
-    c.bn = r[7]; c.stages = r[8]; c.split = r[9];
-    if ((c.bn != 64 && c.bn != 128) || c.stages < 2 || c.stages > TC_STAGES || (c.split != 0 && c.split != 1)) {
+    c.bn = r[7]; c.stages = r[8]; c.split = r[9]; c.halo = r[10];
+    if ((c.bn != 32 && c.bn != 64 && c.bn != 128) || c.stages < 2 || c.stages > TC_STAGES - 2 ||
+        (c.split != 0 && c.split != 1) || (c.halo != 0 && c.halo != 1)) {
       set_error("autotune import: bad configuration record");
       return DDPPO_E_CONFIG;
     }
@@ -702,32 +930,37 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
                                           (int)TC_SMEM_MAX));
     attr_done[dev] = true;
   }
-  const int gm = (M + TC_BM - 1) / TC_BM, gn = (N + BN - 1) / BN;
+  const bool halo = ca.on == 3;
+  const int gm = halo ? ca.tiles_m : (M + TC_BM - 1) / TC_BM, gn = (N + BN - 1) / BN;
   const int tiles = gm * gn;
+  // split-K: over K elements, or over channel blocks in the halo mode (every block runs all
+  // filter taps)
+  const int kstep = (ca.on == 1 || halo) ? ca.cbw : TC_BK;
+  const int Ksplit = halo ? ca.C : K;
   int splits = 1;
   const int target = ws.num_sms;
-  if (cfg.split == 0 && tiles < target && K >= 8 * TC_BK) {
-    splits = min((target + tiles - 1) / tiles, K / (4 * TC_BK));
-    const size_t per = (size_t)M * N;
+  if (cfg.split == 0 && tiles < target && (halo ? Ksplit >= 2 * kstep : K >= 8 * TC_BK)) {
+    splits = min((target + tiles - 1) / tiles, halo ? Ksplit / kstep : K / (4 * TC_BK));
+    const size_t per = (size_t)d.M * d.N;
     splits = (int)min((size_t)splits, ws.partial_elems / max(per, (size_t)1));
     if (splits < 2) splits = 1;
   }
-  const int kstep = ca.on == 1 ? ca.cbw : TC_BK;
-  if (tc_smem<BN>(cfg.stages, kstep) > TC_SMEM_MAX || cfg.stages < 2 || cfg.stages > TC_STAGES) {
+  const size_t smem = halo ? halo_smem(ca, BN, cfg.stages) : tc_smem<BN>(cfg.stages, kstep);
+  if (smem > TC_SMEM_MAX || cfg.stages < 2 || cfg.stages > TC_STAGES - 2) {
     set_error("gemm_tc: ring depth exceeds shared memory");
     return DDPPO_E_CONFIG;
   }
-  int kchunk = (K + splits - 1) / splits;
+  int kchunk = (Ksplit + splits - 1) / splits;
   kchunk = (kchunk + kstep - 1) / kstep * kstep;
-  splits = (K + kchunk - 1) / kchunk;
+  splits = (Ksplit + kchunk - 1) / kchunk;
   float* partial = splits > 1 ? ws.partial : nullptr;
   // persistent grid: one CTA per SM (two where shared memory allows), each walking tiles
   // with stride gridDim.x; the ring streams across tile boundaries
   const int stages = cfg.stages;
-  const int per_sm = tc_smem<BN>(stages, kstep) <= TC_SMEM_TWO_PER_SM ? 2 : 1;
+  const int per_sm = smem <= TC_SMEM_TWO_PER_SM ? 2 : 1;
   const int ntiles = gm * gn * splits;
   const int grid = min(ntiles, ws.num_sms * per_sm);
-  gemm_tc_kernel<BN><<<grid, TC_PTHREADS, tc_smem<BN>(stages, kstep), s>>>(
+  gemm_tc_kernel<BN><<<grid, TC_PTHREADS, smem, s>>>(
       ma, mb, M, N, K, kchunk, (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu, trans,
       partial, ws.err, a_mn, b_mn, stages, gm, gn, splits, ca);
   DDPPO_CHECK_LAUNCH();
@@ -754,6 +987,25 @@ static int run_cfg(const GemmDesc& d, const GemmWorkspace& ws, const TcCfg& cfg,
     }
     if (cfg.bn == 128) return launch_tc<128>(ma, mb, d.N, d.M, d.K, d, 1, 1, 1, ws, cfg, ca, s);
     return launch_tc<64>(ma, mb, d.N, d.M, d.K, d, 1, 1, 1, ws, cfg, ca, s);
+  }
+  if (d.conv && (cfg.halo || !gather_ok(*d.conv)) && halo_geom(*d.conv, nullptr)) {
+    const ConvShape& c = *d.conv;
+    ConvA ca;
+    halo_geom(c, &ca);
+    const CUtensorMapSwizzle sw = ca.cbw == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    const int bn = halo_bn(c.Cout);  // one N tile: the weights stay resident
+    if (c.Cout != d.N) {
+      set_error("gemm_tc: convolution output channels disagree with N");
+      return DDPPO_E_CONFIG;
+    }
+    CUtensorMap ma, mb;
+    if (!make_halo_map(&ma, d.A, c, ca) || !make_map_sw(&mb, d.B, d.N, d.K, d.ldb, bn, ca.cbw, sw)) {
+      set_error("gemm_tc: halo convolution tensor map encoding failed");
+      return DDPPO_E_CUDA;
+    }
+    if (bn == 32) return launch_tc<32>(ma, mb, d.M, d.N, d.K, d, 0, 0, 0, ws, cfg, ca, s);
+    if (bn == 128) return launch_tc<128>(ma, mb, d.M, d.N, d.K, d, 0, 0, 0, ws, cfg, ca, s);
+    return launch_tc<64>(ma, mb, d.M, d.N, d.K, d, 0, 0, 0, ws, cfg, ca, s);
   }
   if (d.conv) {
     const ConvShape& c = *d.conv;
@@ -800,23 +1052,38 @@ static TcCfg tune(const GemmDesc& d, const GemmWorkspace& ws, TcTuner& t, cudaSt
   const bool swap = d.convw || (!d.conv && d.M < TC_BM && d.N > d.M);
   const int Nk = swap ? d.M : d.N;
   const int kslot = kslot_of(d);
+  const bool hal = d.conv && halo_geom(*d.conv, nullptr);
+  const bool gat = !d.conv || gather_ok(*d.conv);
   std::vector<TcCfg> cands;
-  for (int bn : {64, 128}) {
-    if (bn == 128 && Nk <= 64) continue;
-    for (int st : {2, 3, 4}) {
-      if (tc_smem_bn(bn, st, kslot) > TC_SMEM_MAX) continue;
-      for (int sp = 0; sp <= 1; ++sp) {
-        TcCfg c;
-        c.bn = bn; c.stages = st; c.split = sp;
-        cands.push_back(c);
+  if (gat)
+    for (int bn : {64, 128}) {
+      if (bn == 128 && Nk <= 64) continue;
+      for (int st : {2, 3, 4}) {
+        if (tc_smem_bn(bn, st, kslot) > TC_SMEM_MAX) continue;
+        for (int sp = 0; sp <= 1; ++sp) {
+          TcCfg c;
+          c.bn = bn; c.stages = st; c.split = sp;
+          cands.push_back(c);
+        }
       }
     }
-  }
+  if (hal)
+    for (int st : {2, 3, 4})
+      for (int sp = 0; sp <= 1; ++sp) {
+        TcCfg c;
+        c.bn = halo_bn(d.conv->Cout); c.stages = st; c.split = sp; c.halo = 1;
+        cands.push_back(c);
+      }
   GemmDesc trial = d;
   trial.C = t.scratch;
   trial.ldc = d.N;
   trial.beta = 0.f;
   TcCfg best = default_cfg(Nk, kslot);
+  if (hal && !gat) {
+    best.bn = halo_bn(d.conv->Cout);
+    best.stages = 2;
+    best.halo = 1;
+  }
   float best_ms = 1e30f;
   for (const TcCfg& c : cands) {
     if (run_cfg(trial, ws, c, s) != DDPPO_OK) continue;  // warm-up
@@ -834,6 +1101,15 @@ static TcCfg tune(const GemmDesc& d, const GemmWorkspace& ws, TcTuner& t, cudaSt
 int gemm_tc(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s) {
   const bool swap = d.convw || (!d.conv && d.M < TC_BM && d.N > d.M);
   TcCfg cfg = default_cfg(swap ? d.M : d.N, kslot_of(d));
+  if (d.conv && !gather_ok(*d.conv) && halo_geom(*d.conv, nullptr)) {
+    ConvA ca;
+    halo_geom(*d.conv, &ca);
+    cfg.halo = 1;
+    cfg.bn = halo_bn(d.conv->Cout);
+    cfg.stages = 2;  // halo boxes in flight: as many as fit two CTAs per SM, else 2
+    for (int st = 4; st > 2; --st)
+      if (halo_smem(ca, cfg.bn, st) <= TC_SMEM_TWO_PER_SM) { cfg.stages = st; break; }
+  }
   TcTuner* t = ws.tuner;
   if (t && t->on) {
     const ConvShape* cv = d.conv ? d.conv : d.convw;

@@ -418,6 +418,7 @@ static ConvShape conv_shape(const ConvL& c, int N) {
   ConvShape cs;
   cs.N = N; cs.H = c.H; cs.W = c.W; cs.C = c.cin; cs.Ho = c.Ho; cs.Wo = c.Wo;
   cs.k = c.k; cs.s = c.s; cs.p = c.p;
+  cs.Cout = c.cout;
   return cs;
 }
 
@@ -477,7 +478,7 @@ static int conv_bwd(Net& n, ConvL& c, const void* in, bool in_bf16, int N, const
     d.C = dx; d.ldc = c.cin; d.beta = dx_acc ? 1.f : 0.f;
     ConvShape cs;
     cs.N = N; cs.H = c.Ho; cs.W = c.Wo; cs.C = c.cout; cs.Ho = c.H; cs.Wo = c.W;
-    cs.k = c.k; cs.s = 1; cs.p = c.p;
+    cs.k = c.k; cs.s = 1; cs.p = c.p; cs.Cout = c.cin;
     if (n.bf && gemm_conv_supported(cs, dzop)) {
       d.conv = &cs;  // the output gradient (bf16 NHWC) is gathered by the GEMM itself
       d.A = dzop; d.lda = d.K;

@@ -26,6 +26,17 @@ SHAPES = [
     (2, 64, 64, 32, 32, 3, 1, 1),     # 64-wide rows
     (3, 32, 32, 96, 64, 3, 1, 1),     # C = 96: 32-channel K-blocks
     (33, 8, 8, 256, 256, 3, 1, 1),    # many tiles
+    # stride-1 'same' convolutions of 32-channel inputs take the halo path: one input
+    # box per tile, every tap a row-shifted view of it; odd widths and sizes that no
+    # tile divides
+    (3, 15, 15, 32, 32, 3, 1, 1),     # 17-wide anchor rows, tiles straddle rows
+    (4, 7, 7, 32, 64, 3, 1, 1),       # 9x9 anchors: one image per tile
+    (5, 5, 5, 32, 32, 3, 1, 1),       # 7x7 anchors: two images per tile, ragged last tile
+    (3, 12, 20, 32, 32, 3, 1, 1),     # non-square
+    (2, 16, 16, 32, 32, 5, 1, 2),     # 5x5 filter, halo of two
+    (3, 9, 9, 32, 64, 1, 1, 0),       # 1x1 filter
+    (3, 8, 16, 64, 32, 3, 1, 1),      # 64 channels: 4-D gather path
+    (2, 16, 16, 64, 64, 5, 1, 2),     # 5x5, 64 channels: 4-D gather path
 ]
 
 
@@ -48,11 +59,12 @@ def test_implicit_conv_parity(N, H, W, C, Co, k, s, p):
 
 
 def test_unsupported_shape_is_rejected():
-    x = torch.zeros(2, 15, 15, 32, device="cuda", dtype=torch.bfloat16)   # 15-wide output
+    # stride 2 (no halo path) with a 15-wide output (no whole rows per 128-pixel tile)
+    x = torch.zeros(2, 30, 30, 32, device="cuda", dtype=torch.bfloat16)
     w = torch.zeros(32, 9 * 32, device="cuda", dtype=torch.bfloat16)
     y = torch.zeros(2, 15, 15, 32, device="cuda")
     with pytest.raises(B.DDPPOError) as ei:
-        B.ddppo_conv2d(x, w, y, 3, 1, 1)
+        B.ddppo_conv2d(x, w, y, 3, 2, 1)
     assert ei.value.code == -2
 
 

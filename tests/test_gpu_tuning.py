@@ -22,7 +22,7 @@ def test_tuning_cache_round_trip():
         n1 = B.ddppo_autotune(w1.h, True)
         assert n1 > 0
         image = B.ddppo_autotune_export(w1.h)
-        assert len(image) == 4 * (3 + 10 * n1)
+        assert len(image) == 4 * (3 + 11 * n1)
         B.ddppo_autotune_import(w2.h, image)
         assert B.ddppo_autotune(w2.h, True) == n1
         w2.iterate()
