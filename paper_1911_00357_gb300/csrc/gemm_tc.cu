@@ -937,18 +937,20 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
   // filter taps)
   const int kstep = (ca.on == 1 || halo) ? ca.cbw : TC_BK;
   const int Ksplit = halo ? ca.C : K;
+  const size_t smem = halo ? halo_smem(ca, BN, cfg.stages) : tc_smem<BN>(cfg.stages, kstep);
+  if (smem > TC_SMEM_MAX || cfg.stages < 2 || cfg.stages > TC_STAGES - 2) {
+    set_error("gemm_tc: ring depth exceeds shared memory");
+    return DDPPO_E_CONFIG;
+  }
+  const int per_sm = smem <= TC_SMEM_TWO_PER_SM ? 2 : 1;
+  // split K until every resident CTA slot has a tile
   int splits = 1;
-  const int target = ws.num_sms;
+  const int target = ws.num_sms * per_sm;
   if (cfg.split == 0 && tiles < target && (halo ? Ksplit >= 2 * kstep : K >= 8 * TC_BK)) {
     splits = min((target + tiles - 1) / tiles, halo ? Ksplit / kstep : K / (4 * TC_BK));
     const size_t per = (size_t)d.M * d.N;
     splits = (int)min((size_t)splits, ws.partial_elems / max(per, (size_t)1));
     if (splits < 2) splits = 1;
-  }
-  const size_t smem = halo ? halo_smem(ca, BN, cfg.stages) : tc_smem<BN>(cfg.stages, kstep);
-  if (smem > TC_SMEM_MAX || cfg.stages < 2 || cfg.stages > TC_STAGES - 2) {
-    set_error("gemm_tc: ring depth exceeds shared memory");
-    return DDPPO_E_CONFIG;
   }
   int kchunk = (Ksplit + splits - 1) / splits;
   kchunk = (kchunk + kstep - 1) / kstep * kstep;
@@ -957,7 +959,6 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
   // persistent grid: one CTA per SM (two where shared memory allows), each walking tiles
   // with stride gridDim.x; the ring streams across tile boundaries
   const int stages = cfg.stages;
-  const int per_sm = smem <= TC_SMEM_TWO_PER_SM ? 2 : 1;
   const int ntiles = gm * gn * splits;
   const int grid = min(ntiles, ws.num_sms * per_sm);
   gemm_tc_kernel<BN><<<grid, TC_PTHREADS, smem, s>>>(
