@@ -163,7 +163,9 @@ int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t 
   if (timer && timer->on) timer->flops_all += 2.0 * d.M * d.N * d.K;
   if (rec) cudaEventRecord(timer->ev[timer->n], s);
   int rc;
-  if (op_bf16 && (d.conv || d.convw || gemm_tc_supported(d))) {
+  if (op_bf16 && gemm_small_supported(d)) {
+    rc = gemm_small(d, s);  // latency-bound small-M shapes: no tensor-memory pipeline
+  } else if (op_bf16 && (d.conv || d.convw || gemm_tc_supported(d))) {
     rc = gemm_tc(d, ws, s);
     if (ws.tc && ws.tc->on) {
       ws.tc->launches += 1;

@@ -92,6 +92,9 @@ bool gemm_tc_supported(const GemmDesc& d);
 // whether the implicit-im2col path covers this convolution (C % 32 == 0, output rows that
 // tile 128-pixel blocks, 16-byte aligned input)
 bool gemm_conv_supported(const ConvShape& c, const void* input);
+// small-M BF16 contraction (gemm_small.cu): M <= 64, both operands K-major, K % 16 == 0
+bool gemm_small_supported(const GemmDesc& d);
+int gemm_small(const GemmDesc& d, cudaStream_t s);
 // the implicit weight-gradient gather (64-pixel K blocks) handles this shape
 bool gemm_convw_supported(const ConvShape& c, const void* input, const void* dz);
 

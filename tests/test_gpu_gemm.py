@@ -17,6 +17,8 @@ SHAPES = [
     (128, 128, 64), (256, 256, 128), (129, 65, 72), (1000, 300, 520), (37, 2048, 512),
     (5, 1152, 128), (64, 2048, 512), (4096, 32, 288), (32, 288, 24576), (128, 1152, 4096),
     (3, 7, 40), (200, 17, 16), (8192, 512, 2048),
+    # M <= 64 with K % 16 == 0: the small-M kernel (LSTM recurrences of one rollout step)
+    (32, 512, 2048), (1, 64, 16), (64, 33, 48), (17, 100, 32), (64, 2048, 576),
 ]
 
 
@@ -76,8 +78,9 @@ def test_gemm_mn_major_operands(M, N, K, a_t, b_t, dtype):
 
 
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float32])
-def test_gemm_epilogue_and_strides(dtype):
-    M, N, K = 300, 200, 136
+@pytest.mark.parametrize("M", [300, 40])   # 40: the small-M kernel
+def test_gemm_epilogue_and_strides(dtype, M):
+    N, K = 200, 144
     g = torch.Generator(device="cuda").manual_seed(5)
     Abig = torch.randn(M, K + 24, device="cuda", generator=g).to(dtype)   # lda = K + 24
     A = Abig[:, :K]
