@@ -129,8 +129,6 @@ def run_gpu(args):
         torch.cuda.synchronize()
         if world > 1:
             dist.barrier()
-        if timing:
-            B.ddppo_timing_enable(w.h, True)
         s = torch.cuda.current_stream()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -145,10 +143,16 @@ def run_gpu(args):
         torch.cuda.synchronize()
         clocks = clk.stop() if clk else None
         ms = e0.elapsed_time(e1)
-        gemm = B.ddppo_timing_read(w.h, 0) if timing else None
-        tc = B.ddppo_timing_read(w.h, 2) if timing else None
-        per_launch = B.ddppo_timing_launches(w.h, 0) if timing else None
-        if timing:
+        gemm = tc = per_launch = None
+        if timing and not args.profile:
+            # per-launch records of the contractions, from one more step outside the timed
+            # region (recording them runs the update uncaptured)
+            B.ddppo_timing_enable(w.h, True)
+            w.iterate()
+            torch.cuda.synchronize()
+            gemm = B.ddppo_timing_read(w.h, 0)
+            tc = B.ddppo_timing_read(w.h, 2)
+            per_launch = B.ddppo_timing_launches(w.h, 0)
             B.ddppo_timing_enable(w.h, False)
         return w, ms, clocks, gemm, tc, per_launch
 

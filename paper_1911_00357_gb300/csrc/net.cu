@@ -383,6 +383,8 @@ int net_create(ddppo_ctx* x) {
   DDPPO_CHECK_CUDA(cudaMemset(n.adam_v, 0, n.P * 4));
   DDPPO_CHECK_CUDA(cudaMemset(n.stats_tmp, 0, 8 * 64 * 4));
   DDPPO_CHECK_CUDA(cudaStreamCreateWithFlags(&n.cap_stream, cudaStreamNonBlocking));
+  DDPPO_TRY(nalloc(n, &n.d_steps, 2));
+  DDPPO_CHECK_CUDA(cudaMemset(n.d_steps, 0, 2 * sizeof(int64_t)));
   DDPPO_CHECK_CUDA(cudaEventCreateWithFlags(&n.ev_a, cudaEventDisableTiming));
   DDPPO_CHECK_CUDA(cudaEventCreateWithFlags(&n.ev_b, cudaEventDisableTiming));
   for (int i = 0; i < 2 * 4096; ++i) {
@@ -400,6 +402,7 @@ void net_destroy(ddppo_ctx* x) {
   tc_tuner_destroy(n.gws.tuner);
   for (void* p : n.allocs) cudaFree(p);
   if (n.graph_exec) cudaGraphExecDestroy(n.graph_exec);
+  if (n.upd_exec) cudaGraphExecDestroy(n.upd_exec);
   if (n.cap_stream) cudaStreamDestroy(n.cap_stream);
   if (n.ev_a) cudaEventDestroy(n.ev_a);
   if (n.ev_b) cudaEventDestroy(n.ev_b);

@@ -132,6 +132,15 @@ struct Net {
   bool collect_started = false;
   cudaGraphExec_t graph_exec = nullptr;
   ddppo_rollout graph_ro{};
+  // captured PPO update: replayed while its rollout view, statistics buffer and
+  // hyper-parameters (other than the update index) are unchanged
+  cudaGraphExec_t upd_exec = nullptr;
+  ddppo_rollout upd_ro{};
+  ddppo_ppo_hparams upd_hp{};
+  const float* upd_stats = nullptr;
+  bool upd_tuned = false;        // one uncaptured update has run (the autotuner saw its shapes)
+  bool upd_no_graph = false;     // kernel census: run the update uncaptured
+  int64_t* d_steps = nullptr;    // [2] device: update index, Adam steps before this update
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   uint8_t* post_done = nullptr;

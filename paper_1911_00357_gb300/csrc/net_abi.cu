@@ -142,19 +142,17 @@ extern "C" int ddppo_ppo_loss(int32_t n, const float* logits, const float* value
                          entropy_coef, stats, dlogits, dvalues, nullptr, 0, (cudaStream_t)stream);
 }
 
-extern "C" int ddppo_ppo_update(ddppo_ctx* x, const ddppo_rollout* ro, const ddppo_ppo_hparams* hp,
-                                float* stats, void* stream) {
-  ARG(x && x->net && ro && hp, "ppo_update: null argument");
-  ARG(ro->obs && ro->goal && ro->prev_a && ro->masks && ro->actions && ro->logp && ro->adv &&
-          ro->ret && ro->h0 && ro->c0,
-      "ppo_update: rollout view has a null buffer");
+__global__ void set_steps_kernel(int64_t* d, int64_t update_index, int64_t adam_t) {
+  d[0] = update_index;
+  d[1] = adam_t;
+}
+
+// one PPO update (epochs x minibatches) on stream s; the update index and the Adam step
+// count are read from n.d_steps, so the same launches replay for every update
+static int update_body(ddppo_ctx* x, const ddppo_rollout* ro, const ddppo_ppo_hparams* hp,
+                       float* stats, cudaStream_t s) {
   Net& n = *x->net;
   const ddppo_config& c = x->cfg;
-  if (hp->minibatches != c.minibatches || hp->epochs < 1) {
-    set_error("ppo_update: minibatches must equal the config's, epochs >= 1");
-    return DDPPO_E_CONFIG;
-  }
-  cudaStream_t s = (cudaStream_t)stream;
   const int T = c.rollout_T, E = c.num_envs, Emb = n.Emb, L = n.L, Hd = n.H;
   const int Nmb = T * Emb;
   const float* adv = ro->adv;
@@ -165,7 +163,7 @@ extern "C" int ddppo_ppo_update(ddppo_ctx* x, const ddppo_rollout* ro, const ddp
   }
   int k = 0;
   for (int ep = 0; ep < hp->epochs; ++ep) {
-    DDPPO_TRY(launch_permutation(c.seed, hp->update_index, ep, E, n.perm, s));
+    DDPPO_TRY(launch_permutation(c.seed, n.d_steps, ep, E, n.perm, s));
     for (int mb = 0; mb < hp->minibatches; ++mb, ++k) {
       const int32_t* idx = n.perm + (size_t)mb * Emb;
       DDPPO_TRY(launch_gather_rows(ro->obs, n.obs_mb, idx, T, E, Emb, n.pix * op_bytes(n), s));
@@ -187,13 +185,72 @@ extern "C" int ddppo_ppo_update(ddppo_ctx* x, const ddppo_rollout* ro, const ddp
       DDPPO_TRY(net_backward(n, n.dlogits, n.dvalues, s));
       DDPPO_TRY(launch_grad_norm(n.grad, n.P, n.norm, n.scratch, n.scratch_elems, s));
       DDPPO_TRY(launch_copy_scalar(st + 6, n.norm, s));
-      ++n.adam_t;
       DDPPO_TRY(launch_adam(n.params, n.grad, n.adam_m, n.adam_v, n.P,
                             hp->max_grad_norm > 0.f ? n.norm : nullptr, hp->max_grad_norm, hp->lr,
-                            hp->beta1, hp->beta2, hp->adam_eps, n.adam_t, s));
+                            hp->beta1, hp->beta2, hp->adam_eps, n.d_steps + 1, k + 1, s));
       DDPPO_TRY(net_prep_weights(n, s));
     }
   }
+  return DDPPO_OK;
+}
+
+static bool same_hparams(const ddppo_ppo_hparams& a, const ddppo_ppo_hparams& b) {
+  ddppo_ppo_hparams x = a, y = b;
+  x.update_index = 0;
+  y.update_index = 0;
+  return memcmp(&x, &y, sizeof(x)) == 0;
+}
+
+extern "C" int ddppo_ppo_update(ddppo_ctx* x, const ddppo_rollout* ro, const ddppo_ppo_hparams* hp,
+                                float* stats, void* stream) {
+  ARG(x && x->net && ro && hp, "ppo_update: null argument");
+  ARG(ro->obs && ro->goal && ro->prev_a && ro->masks && ro->actions && ro->logp && ro->adv &&
+          ro->ret && ro->h0 && ro->c0,
+      "ppo_update: rollout view has a null buffer");
+  Net& n = *x->net;
+  const ddppo_config& c = x->cfg;
+  if (hp->minibatches != c.minibatches || hp->epochs < 1) {
+    set_error("ppo_update: minibatches must equal the config's, epochs >= 1");
+    return DDPPO_E_CONFIG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  // this update's index and the Adam steps taken so far, as device scalars (kernel
+  // arguments: valid inside a caller's capture too)
+  set_steps_kernel<<<1, 1, 0, s>>>(n.d_steps, hp->update_index, n.adam_t);
+  DDPPO_CHECK_LAUNCH();
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  DDPPO_CHECK_CUDA(cudaStreamIsCapturing(s, &cs));
+  // the update is ~10K launches, most of them small: replaying it as one graph removes
+  // the host launch cost. Timed runs (per-launch event records), kernel census and a
+  // caller's own capture run it directly; so does the first update (the autotuner times
+  // its contraction shapes outside any capture).
+  const bool use_graph = n.upd_tuned && !n.upd_no_graph && !n.timer.on && !n.rc_timer.on &&
+                         cs == cudaStreamCaptureStatusNone;
+  if (use_graph) {
+    const bool same = n.upd_exec && memcmp(&n.upd_ro, ro, sizeof(*ro)) == 0 &&
+                      same_hparams(n.upd_hp, *hp) && n.upd_stats == stats;
+    if (!same) {
+      if (n.upd_exec) { cudaGraphExecDestroy(n.upd_exec); n.upd_exec = nullptr; }
+      DDPPO_CHECK_CUDA(cudaStreamSynchronize(s));
+      DDPPO_CHECK_CUDA(cudaStreamBeginCapture(n.cap_stream, cudaStreamCaptureModeThreadLocal));
+      const int rc = update_body(x, ro, hp, stats, n.cap_stream);
+      cudaGraph_t g = nullptr;
+      const cudaError_t ce = cudaStreamEndCapture(n.cap_stream, &g);
+      if (rc != DDPPO_OK) { if (g) cudaGraphDestroy(g); return rc; }
+      if (ce != cudaSuccess) { set_error(std::string("update capture: ") + cudaGetErrorString(ce)); return DDPPO_E_CUDA; }
+      const cudaError_t ie = cudaGraphInstantiate(&n.upd_exec, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) { n.upd_exec = nullptr; set_error(std::string("update instantiate: ") + cudaGetErrorString(ie)); return DDPPO_E_CUDA; }
+      n.upd_ro = *ro;
+      n.upd_hp = *hp;
+      n.upd_stats = stats;
+    }
+    DDPPO_CHECK_CUDA(cudaGraphLaunch(n.upd_exec, s));
+  } else {
+    DDPPO_TRY(update_body(x, ro, hp, stats, s));
+    if (cs == cudaStreamCaptureStatusNone) n.upd_tuned = true;
+  }
+  n.adam_t += (int64_t)hp->epochs * hp->minibatches;
   n.ev_valid = false;
   return DDPPO_OK;
 }
@@ -389,6 +446,7 @@ extern "C" int ddppo_count_kernels(ddppo_ctx* x, const ddppo_rollout* ro,
   if (!x->env_ready) { set_error("count_kernels before the first collect"); return DDPPO_E_STATE; }
   const int E = x->cfg.num_envs, T = x->cfg.rollout_T;
   const int64_t adam_t = n.adam_t;
+  n.upd_no_graph = true;
   const bool t0 = n.timer.on, t1 = n.rc_timer.on, t2 = n.tc_count.on;
   n.timer.on = n.rc_timer.on = n.tc_count.on = false;
   DDPPO_CHECK_CUDA(cudaDeviceSynchronize());
@@ -406,6 +464,7 @@ extern "C" int ddppo_count_kernels(ddppo_ctx* x, const ddppo_rollout* ro,
   cudaGraph_t g = nullptr;
   const cudaError_t ce = cudaStreamEndCapture(n.cap_stream, &g);
   n.adam_t = adam_t;
+  n.upd_no_graph = false;
   n.timer.on = t0; n.rc_timer.on = t1; n.tc_count.on = t2;
   n.ev_valid = false;
   if (rc != DDPPO_OK) { if (g) cudaGraphDestroy(g); return rc; }

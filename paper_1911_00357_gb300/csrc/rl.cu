@@ -172,10 +172,19 @@ int launch_grad_norm(const float* g, size_t n, float* norm_out, float* part, siz
   return DDPPO_OK;
 }
 
+// Adam step t = *t_dev + t_off (bias corrections 1 - beta^t computed once per block)
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
                             float* __restrict__ v, size_t n, const float* __restrict__ norm,
-                            float max_norm, float lr, float b1, float b2, float eps, float bc1,
-                            float bc2) {
+                            float max_norm, float lr, float b1, float b2, float eps,
+                            const int64_t* __restrict__ t_dev, int t_off) {
+  __shared__ float s_bc[2];
+  if (threadIdx.x == 0) {
+    const double t = (double)(*t_dev + t_off);
+    s_bc[0] = (float)(1.0 - pow((double)b1, t));
+    s_bc[1] = (float)(1.0 - pow((double)b2, t));
+  }
+  __syncthreads();
+  const float bc1 = s_bc[0], bc2 = s_bc[1];
   float coef = 1.f;
   if (norm && max_norm > 0.f) coef = fminf(1.f, max_norm / (norm[0] + 1e-6f));
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -189,12 +198,12 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
 }
 
 int launch_adam(float* p, const float* g, float* m, float* v, size_t n, const float* norm,
-                float max_norm, float lr, float b1, float b2, float eps, int64_t t, cudaStream_t s) {
-  const float bc1 = (float)(1.0 - pow((double)b1, (double)t));
-  const float bc2 = (float)(1.0 - pow((double)b2, (double)t));
+                float max_norm, float lr, float b1, float b2, float eps, const int64_t* t_dev,
+                int t_off, cudaStream_t s) {
   size_t b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
-  adam_kernel<<<(unsigned)b, 256, 0, s>>>(p, g, m, v, n, norm, max_norm, lr, b1, b2, eps, bc1, bc2);
+  adam_kernel<<<(unsigned)b, 256, 0, s>>>(p, g, m, v, n, norm, max_norm, lr, b1, b2, eps, t_dev,
+                                          t_off);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -206,8 +215,10 @@ __device__ __forceinline__ uint64_t sm64r(uint64_t z) {
   z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
   return z ^ (z >> 31);
 }
-__global__ void perm_kernel(uint64_t seed, int64_t update, int64_t epoch, int E, int32_t* perm) {
+__global__ void perm_kernel(uint64_t seed, const int64_t* __restrict__ update_dev, int64_t epoch,
+                            int E, int32_t* perm) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const int64_t update = *update_dev;
   for (int i = 0; i < E; ++i) perm[i] = i;
   uint64_t k = sm64r(seed);
   k = sm64r(k + 0);
@@ -221,9 +232,9 @@ __global__ void perm_kernel(uint64_t seed, int64_t update, int64_t epoch, int E,
     perm[j] = t;
   }
 }
-int launch_permutation(uint64_t seed, int64_t update, int64_t epoch, int E, int32_t* perm,
-                       cudaStream_t s) {
-  perm_kernel<<<1, 32, 0, s>>>(seed, update, epoch, E, perm);
+int launch_permutation(uint64_t seed, const int64_t* update_dev, int64_t epoch, int E,
+                       int32_t* perm, cudaStream_t s) {
+  perm_kernel<<<1, 32, 0, s>>>(seed, update_dev, epoch, E, perm);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
