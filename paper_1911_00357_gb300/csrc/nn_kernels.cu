@@ -163,10 +163,73 @@ __global__ void im2col_c1_kernel(ConvGeom g, const Ti* __restrict__ x, To* __res
   }
 }
 
+// Single-channel im2col with compile-time filter geometry (the 7x7 / stride 2 / pad 3
+// stem): one block per (image, RB output rows). The input rows those outputs read are
+// staged once in shared memory with the zero padding materialised, then every thread
+// assembles 8 consecutive taps of one output pixel and writes them with one 16-byte
+// (bf16) or two (fp32) stores; consecutive threads write consecutive bytes.
+template <typename Ti, typename To, int KS, int S, int P, int RB>
+__global__ void __launch_bounds__(256) im2col_stem_kernel(ConvGeom g, const Ti* __restrict__ x,
+                                                          To* __restrict__ col) {
+  constexpr int KK = KS * KS, KP = (KK + 7) / 8 * 8, NCK = KP / 8, ROWS = (RB - 1) * S + KS;
+  extern __shared__ float tile[];  // [ROWS][W + 2P]
+  const int n = blockIdx.y, oy0 = blockIdx.x * RB;
+  const int Wp = g.W + 2 * P;
+  const Ti* img = x + (size_t)n * g.H * g.W;
+  const int iy0 = oy0 * S - P;
+  for (int i = threadIdx.x; i < ROWS * Wp; i += blockDim.x) {
+    const int r = i / Wp, c = i - r * Wp;
+    const int iy = iy0 + r, ix = c - P;
+    tile[i] = (iy >= 0 && iy < g.H && ix >= 0 && ix < g.W) ? to_f(img[iy * g.W + ix]) : 0.f;
+  }
+  __syncthreads();
+  const int rows = min(RB, g.Ho - oy0);
+  const int items = rows * g.Wo * NCK;
+  To* dst0 = col + ((size_t)n * g.Ho + oy0) * g.Wo * KP;
+  for (int i = threadIdx.x; i < items; i += blockDim.x) {
+    const int ck = i % NCK, px = i / NCK;
+    const int r = px / g.Wo, ox = px - r * g.Wo;
+    const float* base = tile + (r * S) * Wp + ox * S;
+    float v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int kk = ck * 8 + q;
+      const int ky = kk / KS, kx = kk - ky * KS;
+      v[q] = kk < KK ? base[ky * Wp + kx] : 0.f;
+    }
+    To* dst = dst0 + (size_t)px * KP + ck * 8;
+    if constexpr (sizeof(To) == 2) {
+      uint4 u;
+      __nv_bfloat16* h = (__nv_bfloat16*)&u;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) h[q] = __float2bfloat16_rn(v[q]);
+      *(uint4*)dst = u;
+    } else {
+      *(float4*)dst = make_float4(v[0], v[1], v[2], v[3]);
+      *(float4*)(dst + 4) = make_float4(v[4], v[5], v[6], v[7]);
+    }
+  }
+}
+
 int launch_im2col(const ConvGeom& g, const void* x, bool x_bf16, void* col, bool op_bf16,
                   bool transposed, cudaStream_t s) {
   const size_t total = (size_t)g.N * g.Ho * g.Wo * g.Kp;
   if (total == 0) return DDPPO_OK;
+  if (!transposed && g.C == 1 && g.k == 7 && g.s == 2 && g.p == 3 && g.Kp == 56 &&
+      ((uintptr_t)col & 15) == 0 && g.N <= 65535 && g.W <= 900) {
+    constexpr int RB = 4;
+    const dim3 gb((unsigned)((g.Ho + RB - 1) / RB), (unsigned)g.N);
+    const size_t smem = (size_t)((RB - 1) * 2 + 7) * (g.W + 6) * sizeof(float);
+#define STEM_CASE(TI, TO) \
+    im2col_stem_kernel<TI, TO, 7, 2, 3, RB><<<gb, 256, smem, s>>>(g, (const TI*)x, (TO*)col);
+    if (x_bf16 && op_bf16) { STEM_CASE(__nv_bfloat16, __nv_bfloat16) }
+    else if (x_bf16) { STEM_CASE(__nv_bfloat16, float) }
+    else if (op_bf16) { STEM_CASE(float, __nv_bfloat16) }
+    else { STEM_CASE(float, float) }
+#undef STEM_CASE
+    DDPPO_CHECK_LAUNCH();
+    return DDPPO_OK;
+  }
   if (!transposed && g.C == 1 && g.Kp % 8 == 0 && ((uintptr_t)col & 15) == 0 && g.N <= 65535 &&
       (int64_t)g.Ho * g.Wo * g.Kp < (1ll << 31) && (int64_t)g.H * g.W < (1ll << 31)) {
     const long per = (long)g.Ho * g.Wo * (g.Kp / 8);
