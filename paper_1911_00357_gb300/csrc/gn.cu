@@ -191,6 +191,49 @@ __global__ void __launch_bounds__(kThreads) gn_apply_kernel(GNApply a, int HW, i
   }
 }
 
+// dy of one V-channel group at pixel p of image n when the normalisation fed a ReLU and
+// the 3x3 / stride-2 / pad-1 max pool: the pool gradients whose argmax is this pixel,
+// masked by the recomputed ReLU (x is z of the same pixel)
+template <int V>
+__device__ __forceinline__ void pooled_dy(const GNBack& b, int n, int p, int c0, int C,
+                                          const float (&x)[V], const float (&mu)[V],
+                                          const float (&rs)[V], float (&d)[V]) {
+  const int iy = p / b.W, ix = p - iy * b.W;
+#pragma unroll
+  for (int v = 0; v < V; ++v) d[v] = 0.f;
+  for (int ky = 0; ky < 3; ++ky) {
+    const int ty = iy + 1 - ky;
+    if (ty < 0 || (ty & 1)) continue;
+    const int oy = ty >> 1;
+    if (oy >= b.Hq) continue;
+    for (int kx = 0; kx < 3; ++kx) {
+      const int tx = ix + 1 - kx;
+      if (tx < 0 || (tx & 1)) continue;
+      const int ox = tx >> 1;
+      if (ox >= b.Wq) continue;
+      const size_t q = (((size_t)n * b.Hq + oy) * b.Wq + ox) * C + c0;
+      const int t = ky * 3 + kx;
+      if constexpr (V == 4) {
+        const uchar4 a4 = *reinterpret_cast<const uchar4*>(b.pool_arg + q);
+        const float4 g4 = *reinterpret_cast<const float4*>(b.pool_dy + q);
+        if (a4.x == t) d[0] += g4.x;
+        if (a4.y == t) d[1] += g4.y;
+        if (a4.z == t) d[2] += g4.z;
+        if (a4.w == t) d[3] += g4.w;
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v)
+          if (b.pool_arg[q + v] == t) d[v] += b.pool_dy[q + v];
+      }
+    }
+  }
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    const float y = (x[v] - mu[v]) * rs[v] * b.gamma[c0 + v] + b.beta[c0 + v];
+    if (!(y > 0.f)) d[v] = 0.f;
+  }
+}
+
 // ---- backward reductions: g = dy (masked by relu_y > 0), xhat = (z - mu) rstd;
 //      per image and channel sum(g) and sum(g xhat); group means of gamma-weighted sums ----
 template <int V>
@@ -215,8 +258,9 @@ __global__ void __launch_bounds__(kThreads) gn_bwd_reduce_kernel(GNBack b, int H
   for (int p = pb + pr; p < pe; p += P) {
     const size_t o = ib + (size_t)p * C + c0;
     float d[V], x[V];
-    ldv<V>(b.dy + o, d);
     ldv<V>(b.z + o, x);
+    if (b.pool_dy) pooled_dy<V>(b, n, p, c0, C, x, mu, rs, d);
+    else ldv<V>(b.dy + o, d);
     if (b.relu_y) {
       float y[V];
       ldv<V>(b.relu_y + o, y);
@@ -269,9 +313,19 @@ __global__ void __launch_bounds__(kThreads) gn_bwd_apply_kernel(GNBack b, int HW
     const int c0 = (i % R) * V;
     const size_t o = ib + (size_t)i * V;
     float d[V], x[V], gm[V], r[V];
-    ldv<V>(b.dy + o, d);
     ldv<V>(b.z + o, x);
     ldv<V>(b.gamma + c0, gm);
+    if (b.pool_dy) {
+      float mu4[V], rs4[V];
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        mu4[v] = b.mean[(size_t)n * G + (c0 + v) / 2];
+        rs4[v] = b.rstd[(size_t)n * G + (c0 + v) / 2];
+      }
+      pooled_dy<V>(b, n, i / R, c0, C, x, mu4, rs4, d);
+    } else {
+      ldv<V>(b.dy + o, d);
+    }
     if (b.relu_y) {
       float y[V];
       ldv<V>(b.relu_y + o, y);
@@ -382,6 +436,66 @@ int launch_gn_bwd(const GNBack& b, int N, int HW, int C, const GnScratch& w, cud
   const dim3 ga(apply_blocks(N, HW, C, V), N);
   if (V == 4) gn_bwd_apply_kernel<4><<<ga, kThreads, 0, s>>>(b, HW, C);
   else gn_bwd_apply_kernel<2><<<ga, kThreads, 0, s>>>(b, HW, C);
+  DDPPO_CHECK_LAUNCH();
+  return DDPPO_OK;
+}
+
+// ---- GroupNorm apply + ReLU + 3x3 / stride-2 / pad-1 max pool (4 channels per thread) ----
+__global__ void __launch_bounds__(kThreads) gn_relu_maxpool_kernel(GNApply a, int H, int W, int C,
+                                                                   float* __restrict__ pool,
+                                                                   __nv_bfloat16* __restrict__ pool_bf,
+                                                                   uint8_t* __restrict__ arg) {
+  const int Hq = (H - 1) / 2 + 1, Wq = (W - 1) / 2 + 1, C4 = C / 4, G = C / 2;
+  const int n = blockIdx.y, per = Hq * Wq * C4;
+  const float* zi = a.z + (size_t)n * H * W * C;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per; i += gridDim.x * blockDim.x) {
+    const int c4 = i % C4, pix = i / C4, c0 = c4 * 4;
+    const int ox = pix % Wq, oy = pix / Wq;
+    float gm[4], bt[4], mu[4], rs[4];
+    ldv<4>(a.gamma + c0, gm);
+    ldv<4>(a.beta + c0, bt);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      mu[v] = a.mean[(size_t)n * G + (c0 + v) / 2];
+      rs[v] = a.rstd[(size_t)n * G + (c0 + v) / 2];
+    }
+    float best[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    int bi[4] = {0, 0, 0, 0};
+    for (int ky = 0; ky < 3; ++ky) {
+      const int iy = oy * 2 - 1 + ky;
+      if (iy < 0 || iy >= H) continue;
+      for (int kx = 0; kx < 3; ++kx) {
+        const int ix = ox * 2 - 1 + kx;
+        if (ix < 0 || ix >= W) continue;
+        float x[4];
+        ldv<4>(zi + ((size_t)iy * W + ix) * C + c0, x);
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const float y = fmaxf((x[v] - mu[v]) * rs[v] * gm[v] + bt[v], 0.f);
+          if (y > best[v]) { best[v] = y; bi[v] = ky * 3 + kx; }
+        }
+      }
+    }
+    const size_t o = (size_t)n * per * 4 + (size_t)i * 4;
+    stv<4>(pool + o, best);
+    if (pool_bf) stv_bf<4>(pool_bf + o, best);
+    *reinterpret_cast<uchar4*>(arg + o) = make_uchar4(bi[0], bi[1], bi[2], bi[3]);
+  }
+}
+
+int launch_gn_relu_maxpool(const GNApply& a, int N, int H, int W, int C, float* pool,
+                           __nv_bfloat16* pool_bf, uint8_t* arg, cudaStream_t s) {
+  if (!N) return DDPPO_OK;
+  const int Hq = (H - 1) / 2 + 1, Wq = (W - 1) / 2 + 1;
+  if (C % 4 || N > 65535 || (int64_t)Hq * Wq * C >= (1ll << 31)) {
+    set_error("gn_relu_maxpool: unsupported shape");
+    return DDPPO_E_CONFIG;
+  }
+  const long per = (long)Hq * Wq * (C / 4);
+  const dim3 gb((unsigned)std::max<long>(1, std::min<long>((per + kThreads - 1) / kThreads,
+                                                           (8l * num_sms_cached() + N - 1) / N)),
+                N);
+  gn_relu_maxpool_kernel<<<gb, kThreads, 0, s>>>(a, H, W, C, pool, pool_bf, arg);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }

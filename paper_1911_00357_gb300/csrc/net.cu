@@ -169,7 +169,8 @@ static int alloc_encoder(Net& n) {
     for (auto& c : n.nat) DDPPO_TRY(conv_bufs(c));
   } else {
     DDPPO_TRY(conv_bufs(n.stem));
-    DDPPO_TRY(gn_bufs(n.stem_n, n.stem.Ho * n.stem.Wo, true));
+    // the stem's full-resolution activation is only stored when its pool is not fused
+    DDPPO_TRY(gn_bufs(n.stem_n, n.stem.Ho * n.stem.Wo, n.stem.cout % 4 != 0));
     const int ph = (n.stem.Ho - 1) / 2 + 1, pw = (n.stem.Wo - 1) / 2 + 1;
     DDPPO_TRY(nalloc(n, &n.pool, NC * ph * pw * n.stem.cout));
     if (n.bf) DDPPO_TRY(nalloc(n, &n.pool_bf, NC * ph * pw * n.stem.cout));
@@ -547,9 +548,22 @@ static int encoder_fwd(Net& n, const void* obs, int N, void* featop_rows, cudaSt
   }
   ConvL& st = n.stem;
   DDPPO_TRY(conv_fwd(n, st, obs, n.bf, N, st.z, false, s));
-  DDPPO_TRY(gn_fwd(n, n.stem_n, st.z, N, st.Ho * st.Wo, n.stem_n.out, true, nullptr, nullptr, nullptr, s));
-  DDPPO_TRY(launch_maxpool_fwd(n.stem_n.out, N, st.Ho, st.Wo, st.cout, n.pool, n.pool_arg,
-                               n.pool_bf, s));
+  if (st.cout % 4 == 0) {
+    // GroupNorm + ReLU + max pool in one pass: the full-resolution activation is never
+    // stored (the backward recomputes its ReLU mask from z)
+    DDPPO_TRY(launch_gn_stats(st.z, N, st.Ho * st.Wo, st.cout, 1e-5f, n.stem_n.mean, n.stem_n.rstd,
+                              n.gnw, s));
+    GNApply a{};
+    a.z = st.z; a.mean = n.stem_n.mean; a.rstd = n.stem_n.rstd;
+    a.gamma = n.params + n.stem_n.g_off; a.beta = n.params + n.stem_n.b_off;
+    a.relu = 1;
+    DDPPO_TRY(launch_gn_relu_maxpool(a, N, st.Ho, st.Wo, st.cout, n.pool, n.pool_bf, n.pool_arg, s));
+  } else {
+    DDPPO_TRY(gn_fwd(n, n.stem_n, st.z, N, st.Ho * st.Wo, n.stem_n.out, true, nullptr, nullptr,
+                     nullptr, s));
+    DDPPO_TRY(launch_maxpool_fwd(n.stem_n.out, N, st.Ho, st.Wo, st.cout, n.pool, n.pool_arg,
+                                 n.pool_bf, s));
+  }
   const float* cur = n.pool;
   const __nv_bfloat16* cur_bf = n.pool_bf;
   for (auto& B : n.blocks) {
@@ -620,8 +634,24 @@ static int encoder_bwd(Net& n, const void* obs, int N, const float* dfeat_rows, 
   }
   // max pool, stem GN + ReLU, stem conv (no input gradient)
   ConvL& st = n.stem;
-  DDPPO_TRY(launch_maxpool_bwd(gcur, n.pool_arg, N, st.Ho, st.Wo, st.cout, gA, s));
-  DDPPO_TRY(gn_bwd(n, n.stem_n, gA, st.z, N, st.Ho * st.Wo, first, s, n.stem_n.out));
+  if (st.cout % 4 == 0) {
+    // the pool gradient routed through the argmax and the recomputed ReLU mask, inside
+    // the GroupNorm backward (no full-resolution gradient tensor)
+    GNBack b{};
+    b.z = st.z; b.mean = n.stem_n.mean; b.rstd = n.stem_n.rstd;
+    b.gamma = n.params + n.stem_n.g_off; b.beta = n.params + n.stem_n.b_off;
+    b.m1 = n.gn_m1; b.m2 = n.gn_m2;
+    b.dzop = n.dzop; b.op_bf16 = n.bf;
+    b.dgamma_part = n.gnp_g; b.dbeta_part = n.gnp_b;
+    b.pool_dy = gcur; b.pool_arg = n.pool_arg;
+    b.H = st.Ho; b.W = st.Wo; b.Hq = (st.Ho - 1) / 2 + 1; b.Wq = (st.Wo - 1) / 2 + 1;
+    DDPPO_TRY(launch_gn_bwd(b, N, st.Ho * st.Wo, st.cout, n.gnw, s));
+    DDPPO_TRY(launch_colsum(n.gnp_g, N, st.cout, st.cout, n.grad + n.stem_n.g_off, !first, s));
+    DDPPO_TRY(launch_colsum(n.gnp_b, N, st.cout, st.cout, n.grad + n.stem_n.b_off, !first, s));
+  } else {
+    DDPPO_TRY(launch_maxpool_bwd(gcur, n.pool_arg, N, st.Ho, st.Wo, st.cout, gA, s));
+    DDPPO_TRY(gn_bwd(n, n.stem_n, gA, st.z, N, st.Ho * st.Wo, first, s, n.stem_n.out));
+  }
   DDPPO_TRY(conv_bwd(n, st, obs, n.bf, N, n.dzop, nullptr, false, first, s));
   return DDPPO_OK;
 }

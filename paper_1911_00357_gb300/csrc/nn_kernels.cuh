@@ -59,8 +59,18 @@ struct GNBack {
   float* m1; float* m2;
   float* dz32; void* dzop; bool op_bf16;
   float* dgamma_part; float* dbeta_part;
+  // optional: the normalisation fed a ReLU and a 3x3 / stride-2 / pad-1 max pool. Then dy
+  // is the pool's output gradient pool_dy [N, Hq, Wq, C] routed through pool_arg (the
+  // argmax taps), and the ReLU mask is recomputed from z (relu_y unused). H x W = HW.
+  const float* pool_dy; const uint8_t* pool_arg; int H, W, Hq, Wq;
+  const float* beta;  // GroupNorm shift (needed to recompute the ReLU mask)
 };
 int launch_gn_bwd(const GNBack& b, int N, int HW, int C, const GnScratch& w, cudaStream_t s);
+// GroupNorm apply + ReLU + 3x3 / stride-2 / pad-1 max pool in one pass: pool (fp32),
+// pool_bf (bf16, optional), arg (argmax tap) of [N, Hq, Wq, C]; the full-resolution
+// activation is not written. C % 4 == 0.
+int launch_gn_relu_maxpool(const GNApply& a, int N, int H, int W, int C, float* pool,
+                           __nv_bfloat16* pool_bf, uint8_t* arg, cudaStream_t s);
 
 // dz = dy * (y > 0) written as fp32 (dz32) and/or op dtype (dzop); dy may equal dz32
 int launch_relu_bwd(const float* dy, const float* y, size_t n, float* dz32, void* dzop, bool op_bf16,
