@@ -345,6 +345,13 @@ int ddppo_conv2d_wgrad(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout,
 int ddppo_gemm_backend(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const void* A,
                        int32_t lda, const void* B, int32_t ldb, int32_t* tensor_cores);
 
+/* The PPO update (ddppo_ppo_update) is recorded once as a CUDA graph (after its first,
+ * directly launched run) and replayed while its rollout view, statistics buffer and
+ * hyper-parameters other than update_index stay the same; GEMM timing, when enabled, is
+ * recorded inside the graph. on = 0 launches every update directly (debugging); results
+ * are bit-identical either way. */
+int ddppo_update_graph(ddppo_ctx* ctx, int32_t on);
+
 /* Tile-shape autotuner of the tensor-core GEMM (precision 1): on by default. The first
  * time a contraction shape is seen outside a stream capture, each candidate (N tile 64 or
  * 128, ring depth 2-4, split-K or not) runs on a scratch output and the fastest is kept;

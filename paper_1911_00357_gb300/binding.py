@@ -110,6 +110,7 @@ _SIGS = {
     "ddppo_gemm_backend": [I32, I32, I32, I32, P, I32, P, I32, P],
     "ddppo_timing_launches": [P, I32, P, P, P, I64, P],
     "ddppo_autotune": [P, I32, P],
+    "ddppo_update_graph": [P, I32],
     "ddppo_autotune_export": [P, P, ctypes.c_size_t, P],
     "ddppo_autotune_import": [P, P, ctypes.c_size_t],
     "ddppo_conv2d": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, P, P],
@@ -329,6 +330,10 @@ def ddppo_timing_launches(h, family: int):
     by = (ctypes.c_double * max(cap, 1))()
     _check(lib().ddppo_timing_launches(h, family, ms, wk, by, cap, ctypes.byref(n)))
     return list(ms)[:cap], list(wk)[:cap], list(by)[:cap]
+
+
+def ddppo_update_graph(h, on: bool = True) -> None:
+    _check(lib().ddppo_update_graph(h, 1 if on else 0))
 
 
 def ddppo_autotune(h, on: bool = True) -> int:

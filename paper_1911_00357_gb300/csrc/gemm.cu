@@ -161,7 +161,14 @@ int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t 
   }
   const bool rec = timer && timer->on && timer->n + 2 <= 2 * 4096;
   if (timer && timer->on) timer->flops_all += 2.0 * d.M * d.N * d.K;
-  if (rec) cudaEventRecord(timer->ev[timer->n], s);
+  // inside a stream capture the records are external: they become event nodes of the graph
+  unsigned rec_flags = cudaEventRecordDefault;
+  if (rec) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+      rec_flags = cudaEventRecordExternal;
+    cudaEventRecordWithFlags(timer->ev[timer->n], s, rec_flags);
+  }
   int rc;
   if (op_bf16 && gemm_small_supported(d)) {
     rc = gemm_small(d, s);  // latency-bound small-M shapes: no tensor-memory pipeline
@@ -175,7 +182,7 @@ int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t 
     rc = gemm_simt(d, op_bf16, ws, s);
   }
   if (rec) {
-    cudaEventRecord(timer->ev[timer->n + 1], s);
+    cudaEventRecordWithFlags(timer->ev[timer->n + 1], s, rec_flags);
     const double es = op_bf16 ? 2.0 : 4.0, cs = d.c_bf16 ? 2.0 : 4.0;
     timer->work[timer->n / 2] = 2.0 * d.M * d.N * d.K;
     // operands read once, result written once (and read when accumulating); an implicit

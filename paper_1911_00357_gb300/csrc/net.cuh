@@ -139,7 +139,14 @@ struct Net {
   ddppo_ppo_hparams upd_hp{};
   const float* upd_stats = nullptr;
   bool upd_tuned = false;        // one uncaptured update has run (the autotuner saw its shapes)
+  // GEMM timing captured into the graph: the timer records the graph's launches add, and
+  // the first record index they use
+  bool upd_timed = false;
+  int upd_t_n0 = 0, upd_t_dn = 0;
+  double upd_t_flops = 0.0, upd_t_flops_all = 0.0, upd_tc_flops = 0.0;
+  int64_t upd_t_launches = 0, upd_tc_launches = 0;
   bool upd_no_graph = false;     // kernel census: run the update uncaptured
+  bool upd_graph_on = true;      // caller's choice (ddppo_update_graph)
   int64_t* d_steps = nullptr;    // [2] device: update index, Adam steps before this update
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;

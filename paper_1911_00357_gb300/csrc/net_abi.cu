@@ -221,17 +221,23 @@ extern "C" int ddppo_ppo_update(ddppo_ctx* x, const ddppo_rollout* ro, const ddp
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   DDPPO_CHECK_CUDA(cudaStreamIsCapturing(s, &cs));
   // the update is ~10K launches, most of them small: replaying it as one graph removes
-  // the host launch cost. Timed runs (per-launch event records), kernel census and a
-  // caller's own capture run it directly; so does the first update (the autotuner times
-  // its contraction shapes outside any capture).
-  const bool use_graph = n.upd_tuned && !n.upd_no_graph && !n.timer.on && !n.rc_timer.on &&
+  // the host launch cost. The kernel census and a caller's own capture run it directly;
+  // so does the first update (the autotuner times its contraction shapes outside any
+  // capture).
+  const bool use_graph = n.upd_tuned && n.upd_graph_on && !n.upd_no_graph &&
                          cs == cudaStreamCaptureStatusNone;
   if (use_graph) {
+    // with GEMM timing on, the graph carries the timer's event records (as event nodes);
+    // it is valid while the timer's next record index is the one it was captured at
+    const bool timed = n.timer.on;
     const bool same = n.upd_exec && memcmp(&n.upd_ro, ro, sizeof(*ro)) == 0 &&
-                      same_hparams(n.upd_hp, *hp) && n.upd_stats == stats;
+                      same_hparams(n.upd_hp, *hp) && n.upd_stats == stats && n.upd_timed == timed &&
+                      (!timed || n.upd_t_n0 == n.timer.n);
     if (!same) {
       if (n.upd_exec) { cudaGraphExecDestroy(n.upd_exec); n.upd_exec = nullptr; }
       DDPPO_CHECK_CUDA(cudaStreamSynchronize(s));
+      const KernelTimer t0 = n.timer;
+      const GemmTcCount c0 = n.tc_count;
       DDPPO_CHECK_CUDA(cudaStreamBeginCapture(n.cap_stream, cudaStreamCaptureModeThreadLocal));
       const int rc = update_body(x, ro, hp, stats, n.cap_stream);
       cudaGraph_t g = nullptr;
@@ -244,8 +250,30 @@ extern "C" int ddppo_ppo_update(ddppo_ctx* x, const ddppo_rollout* ro, const ddp
       n.upd_ro = *ro;
       n.upd_hp = *hp;
       n.upd_stats = stats;
+      n.upd_timed = timed;
+      // what the capture added to the host-side counters; replays add it again
+      n.upd_t_n0 = t0.n;
+      n.upd_t_dn = n.timer.n - t0.n;
+      n.upd_t_flops = n.timer.flops - t0.flops;
+      n.upd_t_flops_all = n.timer.flops_all - t0.flops_all;
+      n.upd_t_launches = n.timer.launches - t0.launches;
+      n.upd_tc_flops = n.tc_count.flops - c0.flops;
+      n.upd_tc_launches = n.tc_count.launches - c0.launches;
+      n.timer.n = t0.n; n.timer.flops = t0.flops; n.timer.flops_all = t0.flops_all;
+      n.timer.launches = t0.launches;
+      n.tc_count.flops = c0.flops; n.tc_count.launches = c0.launches;
     }
     DDPPO_CHECK_CUDA(cudaGraphLaunch(n.upd_exec, s));
+    if (timed) {
+      n.timer.n += n.upd_t_dn;
+      n.timer.flops += n.upd_t_flops;
+      n.timer.flops_all += n.upd_t_flops_all;
+      n.timer.launches += n.upd_t_launches;
+      if (n.tc_count.on) {
+        n.tc_count.flops += n.upd_tc_flops;
+        n.tc_count.launches += n.upd_tc_launches;
+      }
+    }
   } else {
     DDPPO_TRY(update_body(x, ro, hp, stats, s));
     if (cs == cudaStreamCaptureStatusNone) n.upd_tuned = true;
@@ -528,6 +556,12 @@ extern "C" int ddppo_timing_launches(ddppo_ctx* x, int32_t family, double* ms, d
     if (work) work[i] = t.work[i];
     if (bytes) bytes[i] = t.bytes[i];
   }
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_update_graph(ddppo_ctx* x, int32_t on) {
+  ARG(x && x->net, "update_graph: null ctx");
+  x->net->upd_graph_on = on != 0;
   return DDPPO_OK;
 }
 

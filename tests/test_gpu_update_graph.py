@@ -1,7 +1,8 @@
 """The PPO update replays as one CUDA graph after its first (uncaptured) run. The captured
 and the directly launched update run the same kernels in the same order, so three
 rollout-then-update iterations give bit-identical parameters, Adam moments, statistics
-and rollouts; a changed hyper-parameter re-captures."""
+and rollouts; a changed hyper-parameter re-captures. GEMM timing recorded inside the
+graph reports one record per contraction launch."""
 import pytest
 import torch
 
@@ -30,7 +31,7 @@ def test_captured_update_matches_direct_launches():
     try:
         for w in (wa, wb):
             B.ddppo_autotune(w.h, False)   # same contraction configurations on both
-        B.ddppo_timing_enable(wb.h, True)  # per-launch timing: wb's updates stay uncaptured
+        B.ddppo_update_graph(wb.h, False)  # wb launches every update directly
         for it in range(3):
             wa.iterate()
             wb.iterate()
@@ -47,6 +48,18 @@ def test_captured_update_matches_direct_launches():
         wa.iterate()
         after, _, _, _ = _state(wa)
         assert torch.equal(before, after)       # lr = 0: Adam leaves the parameters unchanged
+        # per-launch timing inside the captured update: same launch count as the direct path
+        for w in (wa, wb):
+            B.ddppo_timing_enable(w.h, True)
+            w.iterate()
+            torch.cuda.synchronize()
+        na = B.ddppo_timing_read(wa.h, 0)
+        nb = B.ddppo_timing_read(wb.h, 0)
+        assert na[1] == nb[1] > 0 and na[0] > 0
+        ms_a, _, _ = B.ddppo_timing_launches(wa.h, 0)
+        assert len(ms_a) == nb[1] and min(ms_a) > 0
+        for w in (wa, wb):
+            B.ddppo_timing_enable(w.h, False)
         assert B.ddppo_device_status(wa.h) == 0 and B.ddppo_device_status(wb.h) == 0
     finally:
         wa.close()
