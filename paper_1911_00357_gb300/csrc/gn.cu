@@ -191,49 +191,6 @@ __global__ void __launch_bounds__(kThreads) gn_apply_kernel(GNApply a, int HW, i
   }
 }
 
-// dy of one V-channel group at pixel p of image n when the normalisation fed a ReLU and
-// the 3x3 / stride-2 / pad-1 max pool: the pool gradients whose argmax is this pixel,
-// masked by the recomputed ReLU (x is z of the same pixel)
-template <int V>
-__device__ __forceinline__ void pooled_dy(const GNBack& b, int n, int p, int c0, int C,
-                                          const float (&x)[V], const float (&mu)[V],
-                                          const float (&rs)[V], float (&d)[V]) {
-  const int iy = p / b.W, ix = p - iy * b.W;
-#pragma unroll
-  for (int v = 0; v < V; ++v) d[v] = 0.f;
-  for (int ky = 0; ky < 3; ++ky) {
-    const int ty = iy + 1 - ky;
-    if (ty < 0 || (ty & 1)) continue;
-    const int oy = ty >> 1;
-    if (oy >= b.Hq) continue;
-    for (int kx = 0; kx < 3; ++kx) {
-      const int tx = ix + 1 - kx;
-      if (tx < 0 || (tx & 1)) continue;
-      const int ox = tx >> 1;
-      if (ox >= b.Wq) continue;
-      const size_t q = (((size_t)n * b.Hq + oy) * b.Wq + ox) * C + c0;
-      const int t = ky * 3 + kx;
-      if constexpr (V == 4) {
-        const uchar4 a4 = *reinterpret_cast<const uchar4*>(b.pool_arg + q);
-        const float4 g4 = *reinterpret_cast<const float4*>(b.pool_dy + q);
-        if (a4.x == t) d[0] += g4.x;
-        if (a4.y == t) d[1] += g4.y;
-        if (a4.z == t) d[2] += g4.z;
-        if (a4.w == t) d[3] += g4.w;
-      } else {
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-          if (b.pool_arg[q + v] == t) d[v] += b.pool_dy[q + v];
-      }
-    }
-  }
-#pragma unroll
-  for (int v = 0; v < V; ++v) {
-    const float y = (x[v] - mu[v]) * rs[v] * b.gamma[c0 + v] + b.beta[c0 + v];
-    if (!(y > 0.f)) d[v] = 0.f;
-  }
-}
-
 // ---- backward reductions: g = dy (masked by relu_y > 0), xhat = (z - mu) rstd;
 //      per image and channel sum(g) and sum(g xhat); group means of gamma-weighted sums ----
 template <int V>
@@ -259,8 +216,12 @@ __global__ void __launch_bounds__(kThreads) gn_bwd_reduce_kernel(GNBack b, int H
     const size_t o = ib + (size_t)p * C + c0;
     float d[V], x[V];
     ldv<V>(b.z + o, x);
-    if (b.pool_dy) pooled_dy<V>(b, n, p, c0, C, x, mu, rs, d);
-    else ldv<V>(b.dy + o, d);
+    ldv<V>(b.dy + o, d);
+    if (b.relu_from_z) {
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        if (!((x[v] - mu[v]) * rs[v] * b.gamma[c0 + v] + b.beta[c0 + v] > 0.f)) d[v] = 0.f;
+    }
     if (b.relu_y) {
       float y[V];
       ldv<V>(b.relu_y + o, y);
@@ -315,16 +276,13 @@ __global__ void __launch_bounds__(kThreads) gn_bwd_apply_kernel(GNBack b, int HW
     float d[V], x[V], gm[V], r[V];
     ldv<V>(b.z + o, x);
     ldv<V>(b.gamma + c0, gm);
-    if (b.pool_dy) {
-      float mu4[V], rs4[V];
+    ldv<V>(b.dy + o, d);
+    if (b.relu_from_z) {
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        mu4[v] = b.mean[(size_t)n * G + (c0 + v) / 2];
-        rs4[v] = b.rstd[(size_t)n * G + (c0 + v) / 2];
+        const size_t gq = (size_t)n * G + (c0 + v) / 2;
+        if (!((x[v] - b.mean[gq]) * b.rstd[gq] * gm[v] + b.beta[c0 + v] > 0.f)) d[v] = 0.f;
       }
-      pooled_dy<V>(b, n, i / R, c0, C, x, mu4, rs4, d);
-    } else {
-      ldv<V>(b.dy + o, d);
     }
     if (b.relu_y) {
       float y[V];

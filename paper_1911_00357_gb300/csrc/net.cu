@@ -635,16 +635,17 @@ static int encoder_bwd(Net& n, const void* obs, int N, const float* dfeat_rows, 
   // max pool, stem GN + ReLU, stem conv (no input gradient)
   ConvL& st = n.stem;
   if (st.cout % 4 == 0) {
-    // the pool gradient routed through the argmax and the recomputed ReLU mask, inside
-    // the GroupNorm backward (no full-resolution gradient tensor)
+    // the max-pool gradient scattered once; the GroupNorm backward recomputes the ReLU
+    // mask from z (the full-resolution activation was never stored)
+    DDPPO_TRY(launch_maxpool_bwd(gcur, n.pool_arg, N, st.Ho, st.Wo, st.cout, gA, s));
     GNBack b{};
+    b.dy = gA;
     b.z = st.z; b.mean = n.stem_n.mean; b.rstd = n.stem_n.rstd;
     b.gamma = n.params + n.stem_n.g_off; b.beta = n.params + n.stem_n.b_off;
+    b.relu_from_z = 1;
     b.m1 = n.gn_m1; b.m2 = n.gn_m2;
     b.dzop = n.dzop; b.op_bf16 = n.bf;
     b.dgamma_part = n.gnp_g; b.dbeta_part = n.gnp_b;
-    b.pool_dy = gcur; b.pool_arg = n.pool_arg;
-    b.H = st.Ho; b.W = st.Wo; b.Hq = (st.Ho - 1) / 2 + 1; b.Wq = (st.Wo - 1) / 2 + 1;
     DDPPO_TRY(launch_gn_bwd(b, N, st.Ho * st.Wo, st.cout, n.gnw, s));
     DDPPO_TRY(launch_colsum(n.gnp_g, N, st.cout, st.cout, n.grad + n.stem_n.g_off, !first, s));
     DDPPO_TRY(launch_colsum(n.gnp_b, N, st.cout, st.cout, n.grad + n.stem_n.b_off, !first, s));

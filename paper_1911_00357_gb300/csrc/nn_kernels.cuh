@@ -59,11 +59,9 @@ struct GNBack {
   float* m1; float* m2;
   float* dz32; void* dzop; bool op_bf16;
   float* dgamma_part; float* dbeta_part;
-  // optional: the normalisation fed a ReLU and a 3x3 / stride-2 / pad-1 max pool. Then dy
-  // is the pool's output gradient pool_dy [N, Hq, Wq, C] routed through pool_arg (the
-  // argmax taps), and the ReLU mask is recomputed from z (relu_y unused). H x W = HW.
-  const float* pool_dy; const uint8_t* pool_arg; int H, W, Hq, Wq;
-  const float* beta;  // GroupNorm shift (needed to recompute the ReLU mask)
+  // optional: the ReLU after the normalisation was not stored; its mask is recomputed
+  // from z (relu_y unused, beta = the GroupNorm shift)
+  int relu_from_z; const float* beta;
 };
 int launch_gn_bwd(const GNBack& b, int N, int HW, int C, const GnScratch& w, cudaStream_t s);
 // GroupNorm apply + ReLU + 3x3 / stride-2 / pad-1 max pool in one pass: pool (fp32),
