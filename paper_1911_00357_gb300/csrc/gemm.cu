@@ -155,7 +155,8 @@ int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t 
   if (d.convw && !(op_bf16 && !d.conv && d.a_t && d.lda == d.M && d.lda % 8 == 0 && !d.c_bf16 && !d.bias && !d.relu &&
                    d.N == d.convw->k * d.convw->k * d.convw->C &&
                    d.K == d.convw->N * d.convw->Ho * d.convw->Wo &&
-                   gemm_convw_supported(*d.convw, d.B, d.A))) {
+                   (conv_wgrad_halo_ok(*d.convw, d.B, d.A) ||
+                    gemm_convw_supported(*d.convw, d.B, d.A)))) {
     set_error("gemm: implicit weight gradient not supported for this shape");
     return DDPPO_E_CONFIG;
   }
@@ -172,6 +173,8 @@ int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t 
   int rc;
   if (op_bf16 && gemm_small_supported(d)) {
     rc = gemm_small(d, s);  // latency-bound small-M shapes: no tensor-memory pipeline
+  } else if (op_bf16 && d.convw && conv_wgrad_halo_ok(*d.convw, d.B, d.A)) {
+    rc = conv_wgrad_halo(*d.convw, d.B, d.A, (float*)d.C, d.ldc, d.beta, ws, s);
   } else if (op_bf16 && (d.conv || d.convw || gemm_tc_supported(d))) {
     rc = gemm_tc(d, ws, s);
     if (ws.tc && ws.tc->on) {

@@ -92,6 +92,11 @@ bool gemm_tc_supported(const GemmDesc& d);
 // whether the implicit-im2col path covers this convolution (C % 32 == 0, output rows that
 // tile 128-pixel blocks, 16-byte aligned input)
 bool gemm_conv_supported(const ConvShape& c, const void* input);
+// weight gradient of a 3x3 / stride-1 / pad-1 convolution, 32 -> 32 channels, through
+// staged halo boxes (gemm_tc.cu): dw[co, (ky*3+kx)*32 + c] (+)= ...; x, dz NHWC bf16
+bool conv_wgrad_halo_ok(const ConvShape& c, const void* x, const void* dz);
+int conv_wgrad_halo(const ConvShape& c, const void* x, const void* dz, float* dw, int ldw, float beta,
+                    const GemmWorkspace& ws, cudaStream_t s);
 // small-M BF16 contraction (gemm_small.cu): M <= 64, both operands K-major, K % 16 == 0
 bool gemm_small_supported(const GemmDesc& d);
 int gemm_small(const GemmDesc& d, cudaStream_t s);

@@ -1134,4 +1134,246 @@ int gemm_tc(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s) {
   return run_cfg(d, ws, cfg, s);
 }
 
+// ---------------------------------------------------------------- halo weight gradient
+// Weight gradient of a 3x3 / stride-1 / pad-1 convolution of a 32-channel input into 32
+// output channels (the first ResNet stage):
+//   dW[co, (ky, kx, c)] = sum over output pixels a of dz[a, co] x[a + (ky - 1, kx - 1), c].
+// Work unit: RB whole rows of one image, as Wp = W + 2 "anchors" per row (anchors x >= W
+// carry dz = 0: the dz box reads past the row end, where TMA fills zeros). Per unit one box
+// of dz (RB rows x Wp) and one box of the input with its halo (RB + 3 rows x Wp, from
+// x = -1, y = y0 - 1, plus one row) are staged, both 64-byte swizzled, rows = anchors. Per 16-anchor
+// K step and filter row ky one MMA (M = 128, N = 32) computes the three kx taps at once:
+// the A operand is MN-major (channels contiguous) and its four 32-channel atoms sit one
+// 64-byte row apart (leading byte offset 64), so atom j reads the input shifted by j
+// anchors -- tap kx = j (the fourth is discarded). Three TMEM accumulators (ky) of 32
+// columns collect every unit a CTA takes; each CTA writes its partial sums once and a
+// fixed-order reduction adds the CTAs.
+constexpr int WH_THREADS = 128;
+constexpr int WH_STAGES = 3;
+
+__device__ __forceinline__ uint64_t sw64_mn_desc_lbo(uint32_t saddr, uint32_t lbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
+__global__ void __launch_bounds__(WH_THREADS, 1)
+    wgrad_halo_kernel(const __grid_constant__ CUtensorMap mapX, const __grid_constant__ CUtensorMap mapDZ,
+                      int Wp, int RB, int nrb, int nunits, uint32_t x_bytes, uint32_t dz_bytes,
+                      uint32_t x_stride, uint32_t dz_stride, int stages, float* __restrict__ part,
+                      int32_t* err) {
+  extern __shared__ __align__(1024) uint8_t dyn[];
+  __shared__ uint64_t full[WH_STAGES], empty[WH_STAGES], done;
+  __shared__ uint32_t tmem_base;
+  __shared__ int abort_flag;
+  uint8_t* base = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
+  uint8_t* sX = base;
+  uint8_t* sD = base + stages * x_stride;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  volatile int* abort = &abort_flag;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < stages; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(&done, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_addr(&tmem_base)),
+                 "r"(128));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = tmem_base;
+  const int kq = RB * Wp / 16;
+  const bool has_work = (int)blockIdx.x < nunits;
+
+  if (warp == 0 && lane == 0) {
+    uint32_t it = 0;
+    for (int u = blockIdx.x; u < nunits && !*abort; u += gridDim.x, ++it) {
+      const int s = it % stages;
+      if (!mbar_wait(&empty[s], ((it / stages) & 1u) ^ 1u, abort, err)) break;
+      const int img = u / nrb, y0 = (u - img * nrb) * RB;
+      mbar_expect_tx(&full[s], x_bytes + dz_bytes);
+      tma_load_4d(sX + s * x_stride, &mapX, &full[s], 0, -1, y0 - 1, img);
+      tma_load_4d(sD + s * dz_stride, &mapDZ, &full[s], 0, 0, y0, img);
+    }
+  } else if (warp == 1 && lane == 0) {
+    const uint32_t idesc = f16_idesc(TC_BM, 32, 1, 1);
+    uint32_t it = 0;
+    for (int u = blockIdx.x; u < nunits && !*abort; u += gridDim.x, ++it) {
+      const int s = it % stages;
+      if (!mbar_wait(&full[s], (it / stages) & 1u, abort, err)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t x0 = smem_addr(sX + s * x_stride), d0 = smem_addr(sD + s * dz_stride);
+      for (int k = 0; k < kq; ++k) {
+        const uint64_t db = sw64_mn_desc_lbo(d0 + (uint32_t)k * 16 * 64, 4096);
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky) {
+          const uint64_t da = sw64_mn_desc_lbo(x0 + (uint32_t)(ky * Wp + k * 16) * 64, 64);
+          const uint32_t acc = (it | k) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\t"
+              "setp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem + ky * 32),
+              "l"(da), "l"(db), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_addr(&empty[s]))
+          : "memory");
+    }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+            smem_addr(&done))
+        : "memory");
+  }
+  __syncwarp();
+  // epilogue: warp w holds TMEM rows 32 w .. 32 w + 31 = tap kx = w, channel c = lane
+  const bool ok = has_work ? mbar_wait(&done, 0u, abort, err) : true;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp < 3) {
+#pragma unroll 1
+    for (int ky = 0; ky < 3; ++ky) {
+      uint32_t r[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ky * 32);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+          "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+            "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+            "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+            "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float* dst = part + ((((size_t)blockIdx.x * 3 + ky) * 3 + warp) * 32 + lane) * 32;
+#pragma unroll
+      for (int j = 0; j < 32; j += 4)
+        *reinterpret_cast<float4*>(dst + j) =
+            (has_work && ok) ? make_float4(__uint_as_float(r[j]), __uint_as_float(r[j + 1]),
+                                           __uint_as_float(r[j + 2]), __uint_as_float(r[j + 3]))
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));
+  }
+}
+
+// dw[co, (ky*3 + kx)*32 + c] = beta dw + sum over CTAs (in order) of part[cta][ky][kx][c][co]
+__global__ void wgrad_halo_reduce_kernel(const float* __restrict__ part, int nctas, float* __restrict__ dw,
+                                         int ldw, float beta) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 32 * 288) return;
+  const int co = i / 288, kk = i - co * 288;
+  const int tap = kk / 32, c = kk - tap * 32;
+  const int ky = tap / 3, kx = tap - ky * 3;
+  float v = 0.f;
+  for (int t = 0; t < nctas; ++t) v += part[((((size_t)t * 3 + ky) * 3 + kx) * 32 + c) * 32 + co];
+  const size_t o = (size_t)co * ldw + kk;
+  dw[o] = beta != 0.f ? beta * dw[o] + v : v;
+}
+
+// unit rows (RB), anchor pitch (Wp), stage strides and ring depth of the halo weight
+// gradient; false when the shape is not covered or two stages do not fit
+struct WgradHalo {
+  int RB = 0, Wp = 0, stages = 0;
+  uint32_t x_bytes = 0, dz_bytes = 0, x_stride = 0, dz_stride = 0;
+  size_t smem = 0;
+};
+static bool wgrad_halo_geom(const ConvShape& c, WgradHalo* g) {
+  if (c.C != 32 || c.Cout != 32 || c.k != 3 || c.s != 1 || c.p != 1 || c.Ho != c.H || c.Wo != c.W)
+    return false;
+  g->Wp = c.W + 2;
+  if (g->Wp > 256) return false;
+  int r = 1;
+  while ((r * g->Wp) % 16 || r * g->Wp < 128) ++r;
+  if (r + 3 > 256) return false;
+  g->RB = r;
+  // input box: the unit's rows, the filter halo above and below, and one more row -- the
+  // tap atoms of the last K step read up to 3 anchors past the halo rows, and those
+  // anchors (dz = 0 there) must meet finite values, never stale shared memory
+  g->x_bytes = 64u * g->Wp * (r + 3);
+  g->dz_bytes = 64u * g->Wp * r;
+  g->x_stride = (g->x_bytes + 1023) / 1024 * 1024;
+  g->dz_stride = (g->dz_bytes + 1023) / 1024 * 1024;
+  for (int st = WH_STAGES; st >= 2; --st) {
+    g->stages = st;
+    g->smem = (size_t)st * (g->x_stride + g->dz_stride) + 1024;
+    if (g->smem <= TC_SMEM_MAX) return true;
+  }
+  return false;
+}
+
+bool conv_wgrad_halo_ok(const ConvShape& c, const void* x, const void* dz) {
+  WgradHalo g;
+  return encode_fn() && !((uintptr_t)x & 15) && !((uintptr_t)dz & 15) && wgrad_halo_geom(c, &g);
+}
+
+int conv_wgrad_halo(const ConvShape& c, const void* x, const void* dz, float* dw, int ldw, float beta,
+                    const GemmWorkspace& ws, cudaStream_t s) {
+  WgradHalo g;
+  if (!wgrad_halo_geom(c, &g)) {
+    set_error("wgrad_halo: unsupported shape");
+    return DDPPO_E_CONFIG;
+  }
+  const int RB = g.RB, Wp = g.Wp;
+  auto fn = encode_fn();
+  CUtensorMap mx, md;
+  cuuint64_t dims[4] = {32, (cuuint64_t)c.W, (cuuint64_t)c.H, (cuuint64_t)c.N};
+  cuuint64_t strides[3] = {64, (cuuint64_t)c.W * 64, (cuuint64_t)c.H * c.W * 64};
+  cuuint32_t boxx[4] = {32, (cuuint32_t)Wp, (cuuint32_t)(RB + 3), 1};
+  cuuint32_t boxd[4] = {32, (cuuint32_t)Wp, (cuuint32_t)RB, 1};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  if (!fn ||
+      fn(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(x), dims, strides, boxx, estr,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+      fn(&md, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<void*>(dz), dims, strides, boxd, estr,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS) {
+    set_error("wgrad_halo: tensor map encoding failed");
+    return DDPPO_E_CUDA;
+  }
+  const int nrb = (c.H + RB - 1) / RB;
+  const int nunits = c.N * nrb;
+  int grid = std::min(nunits, ws.num_sms);
+  const size_t per = (size_t)3 * 3 * 32 * 32;
+  grid = (int)std::min<size_t>((size_t)grid, ws.partial_elems / per);
+  if (grid < 1) {
+    set_error("wgrad_halo: split-K workspace too small");
+    return DDPPO_E_CONFIG;
+  }
+  static bool attr_done[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !attr_done[dev]) {
+    DDPPO_CHECK_CUDA(cudaFuncSetAttribute(wgrad_halo_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)TC_SMEM_MAX));
+    attr_done[dev] = true;
+  }
+  wgrad_halo_kernel<<<grid, WH_THREADS, g.smem, s>>>(mx, md, Wp, RB, nrb, nunits, g.x_bytes,
+                                                     g.dz_bytes, g.x_stride, g.dz_stride, g.stages,
+                                                     ws.partial, ws.err);
+  DDPPO_CHECK_LAUNCH();
+  wgrad_halo_reduce_kernel<<<(32 * 288 + 255) / 256, 256, 0, s>>>(ws.partial, grid, dw, ldw, beta);
+  DDPPO_CHECK_LAUNCH();
+  return DDPPO_OK;
+}
+
 }  // namespace ddppo

@@ -462,7 +462,7 @@ static int conv_bwd(Net& n, ConvL& c, const void* in, bool in_bf16, int N, const
   const ConvShape cs = conv_shape(c, N);
   const void* x_bf = in_bf ? (const void*)in_bf : (in_bf16 ? in : nullptr);
   if (n.bf && x_bf && c.Kp == c.k * c.k * c.cin && c.cout % 8 == 0 &&
-      gemm_convw_supported(cs, x_bf, dzop)) {
+      (conv_wgrad_halo_ok(cs, x_bf, dzop) || gemm_convw_supported(cs, x_bf, dzop))) {
     w.convw = &cs;  // the GEMM gathers the shifted input rows itself
     w.B = x_bf;
   } else {

@@ -637,7 +637,8 @@ extern "C" int ddppo_conv2d_wgrad(int32_t N, int32_t H, int32_t W, int32_t C, in
   ConvShape c;
   DDPPO_TRY(conv_args(N, H, W, C, Cout, k, stride, pad, &c));
   ARG(x && dy && dw, "conv2d_wgrad: null argument");
-  if (Cout % 8 || !gemm_convw_supported(c, x, dy)) {
+  c.Cout = Cout;
+  if (Cout % 8 || !(conv_wgrad_halo_ok(c, x, dy) || gemm_convw_supported(c, x, dy))) {
     set_error("conv2d_wgrad: shape not covered by the implicit weight-gradient path");
     return DDPPO_E_CONFIG;
   }

@@ -69,7 +69,8 @@ def test_unsupported_shape_is_rejected():
 
 
 # (N, H, W, C, Cout, k, s, p) for the weight gradient: 64-pixel K blocks of whole rows or
-# whole images; C = 32 (64-byte swizzled MN-major boxes) and C % 64 == 0 (128-byte)
+# whole images; C = 32 (64-byte swizzled MN-major boxes) and C % 64 == 0 (128-byte);
+# 3x3 / stride-1 / 32 -> 32 shapes take the halo weight gradient
 WGRAD_SHAPES = [
     (3, 32, 32, 32, 32, 3, 1, 1),     # layer-1 shape: 2 output rows per K block, 4 boxes per tile
     (2, 32, 32, 32, 64, 3, 2, 1),     # stride 2 (16x16 outputs)
@@ -81,6 +82,11 @@ WGRAD_SHAPES = [
     (4, 16, 16, 64, 128, 1, 2, 0),    # 1x1 stride-2 shortcut
     (2, 64, 64, 32, 32, 3, 1, 1),     # 64-wide rows: one row per K block
     (70, 32, 32, 32, 32, 3, 1, 1),    # long reduction (split K)
+    # 3x3 / stride 1, 32 -> 32 channels: the halo weight gradient (whole-row units of Wp
+    # anchors, three taps per MMA); widths that no 64-pixel block divides
+    (3, 15, 15, 32, 32, 3, 1, 1),
+    (2, 7, 9, 32, 32, 3, 1, 1),
+    (5, 33, 20, 32, 32, 3, 1, 1),
 ]
 
 
@@ -108,9 +114,10 @@ def test_implicit_wgrad_parity(N, H, W, C, Co, k, s, p):
 
 
 def test_wgrad_unsupported_shape_is_rejected():
-    x = torch.zeros(2, 15, 15, 32, device="cuda", dtype=torch.bfloat16)   # 15-wide output
+    # stride 2 (no halo path) with a 15-wide output (no whole rows per 64-pixel block)
+    x = torch.zeros(2, 30, 30, 32, device="cuda", dtype=torch.bfloat16)
     dy = torch.zeros(2, 15, 15, 32, device="cuda", dtype=torch.bfloat16)
     dw = torch.zeros(32, 9 * 32, device="cuda")
     with pytest.raises(B.DDPPOError) as ei:
-        B.ddppo_conv2d_wgrad(x, dy, dw, 3, 1, 1)
+        B.ddppo_conv2d_wgrad(x, dy, dw, 3, 2, 1)
     assert ei.value.code == -2
