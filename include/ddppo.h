@@ -319,16 +319,20 @@ int ddppo_gemm(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const void* A, 
                int32_t a_t, const void* B, int32_t ldb, int32_t b_t, void* C, int32_t ldc,
                int32_t c_bf16, float beta, const float* bias, int32_t relu, int32_t* status,
                void* stream);
-/* A convolution on the tensor cores without an im2col matrix: the GEMM kernel gathers
- * each K-block of the input patch matrix with one 4-D TMA copy of the input (filter tap
- * shifts the box, the stride is the copy's traversal stride, zero padding is the copy's
- * out-of-bounds fill). x [dev] NHWC bf16 [N, H, W, C]; w [dev] bf16 [Cout, k*k*C] with K
- * ordered (ky, kx, c); y [dev] fp32 NHWC [N, Ho, Wo, Cout]. Requires C % 32 == 0 and an
- * output width dividing 128 (whole output rows per 128-pixel tile); E_CONFIG otherwise.
- * status as for ddppo_gemm. The first call per device allocates a split-K workspace. */
+/* A convolution on the tensor cores without an im2col matrix (the encoder of Sec. 4):
+ * y = beta y + conv(x, w). Either the GEMM kernel gathers each K-block of the input patch
+ * matrix with one 4-D TMA copy of the input (filter tap shifts the box, the stride is the
+ * copy's traversal stride, zero padding is the copy's out-of-bounds fill), or, for
+ * stride-1 'same' convolutions of 32-channel inputs, each 128-pixel tile stages one input
+ * box with its filter halo and every tap reads it through a row-shifted operand view.
+ * x [dev] NHWC bf16 [N, H, W, C]; w [dev] bf16 [Cout, k*k*C] with K ordered (ky, kx, c);
+ * y [dev] fp32 NHWC [N, Ho, Wo, Cout] (read when beta != 0). Requires C % 32 == 0 and an
+ * output width dividing 128 (whole output rows per 128-pixel tile), or stride 1, odd k,
+ * p = k / 2, C == 32, Cout <= 128 and W + 2p <= 256; E_CONFIG otherwise. status as for
+ * ddppo_gemm. The first call per device allocates a split-K workspace. */
 int ddppo_conv2d(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, int32_t k,
                  int32_t stride, int32_t pad, const void* x, const void* w, float* y,
-                 int32_t* status, void* stream);
+                 float beta, int32_t* status, void* stream);
 /* The weight gradient of that convolution without an im2col matrix (the backward pass of
  * Sec. 4's encoder): dw[co, (ky*k + kx)*C + c] = beta dw + sum over n, oy, ox of
  * dy[n, oy, ox, co] x[n, oy*s - p + ky, ox*s - p + kx, c] (zero outside the image).

@@ -113,7 +113,7 @@ _SIGS = {
     "ddppo_update_graph": [P, I32],
     "ddppo_autotune_export": [P, P, ctypes.c_size_t, P],
     "ddppo_autotune_import": [P, P, ctypes.c_size_t],
-    "ddppo_conv2d": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, P, P],
+    "ddppo_conv2d": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, F32, P, P],
     "ddppo_conv2d_wgrad": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, F32, P, P],
 }
 
@@ -365,9 +365,9 @@ def ddppo_conv2d_wgrad(x, dy, dw, k: int, stride: int, pad: int, beta: float = 0
                                     beta, _p(status), _s()))
 
 
-def ddppo_conv2d(x, w, y, k: int, stride: int, pad: int, status=None):
-    """y = conv(x, w) on the implicit-im2col tensor-core path. x NHWC bf16 [N, H, W, C];
-    w bf16 [Cout, k*k*C] (K ordered ky, kx, c); y fp32 [N, Ho, Wo, Cout]."""
+def ddppo_conv2d(x, w, y, k: int, stride: int, pad: int, beta: float = 0.0, status=None):
+    """y = beta y + conv(x, w) on the implicit-im2col tensor-core path. x NHWC bf16
+    [N, H, W, C]; w bf16 [Cout, k*k*C] (K ordered ky, kx, c); y fp32 [N, Ho, Wo, Cout]."""
     N, H, W, C = x.shape
     _check(lib().ddppo_conv2d(N, H, W, C, w.shape[0], k, stride, pad, _p(x), _p(w), _p(y),
-                              _p(status), _s()))
+                              beta, _p(status), _s()))

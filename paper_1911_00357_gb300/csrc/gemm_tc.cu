@@ -535,6 +535,11 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
               orows[k] = __shfl_sync(0xffffffffu, my_orow, i0 + k);
             }
             if (!cin) continue;
+            // accumulated output: the group's eight loads are issued before its stores
+            float cv[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k)
+              cv[k] = (beta != 0.f && !partial && orows[k] >= 0) ? C[(size_t)orows[k] * ldc + col] : 0.f;
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
               const long long orow = orows[k];
@@ -545,7 +550,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
                 continue;
               }
               const size_t o = (size_t)orow * ldc + col;
-              if (beta != 0.f) x += beta * C[o];
+              if (beta != 0.f) x += beta * cv[k];
               x += bv;
               if (relu) x = fmaxf(x, 0.f);
               if (c_bf16) ((__nv_bfloat16*)C)[o] = __float2bfloat16_rn(x);

@@ -612,7 +612,7 @@ static int conv_args(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, i
 
 extern "C" int ddppo_conv2d(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, int32_t k,
                             int32_t stride, int32_t pad, const void* x, const void* w, float* y,
-                            int32_t* status, void* stream) {
+                            float beta, int32_t* status, void* stream) {
   ConvShape c;
   DDPPO_TRY(conv_args(N, H, W, C, Cout, k, stride, pad, &c));
   ARG(x && w && y, "conv2d: null argument");
@@ -626,7 +626,7 @@ extern "C" int ddppo_conv2d(int32_t N, int32_t H, int32_t W, int32_t C, int32_t 
   GemmDesc d;
   d.M = N * c.Ho * c.Wo; d.N = Cout; d.K = k * k * C;
   d.conv = &c; d.A = x; d.lda = d.K; d.B = w; d.ldb = d.K;
-  d.C = y; d.ldc = Cout;
+  d.C = y; d.ldc = Cout; d.beta = beta;
   return gemm(d, true, ws, (cudaStream_t)stream, nullptr);
 }
 

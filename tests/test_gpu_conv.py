@@ -58,6 +58,35 @@ def test_implicit_conv_parity(N, H, W, C, Co, k, s, p):
     assert err <= 4e-5 * np.sqrt(k * k * C), err
 
 
+# y = beta y + conv(x, w): the accumulating form the encoder backward uses for the
+# identity-skip input gradient (halo path: per-row output addresses; gather path)
+BETA_SHAPES = [
+    (3, 15, 15, 32, 32, 3, 1, 1),     # halo, tiles straddle rows
+    (5, 5, 5, 32, 32, 3, 1, 1),       # halo, two images per tile
+    (2, 30, 30, 32, 32, 3, 1, 1),     # halo only (no whole rows per 128-pixel tile)
+    (3, 16, 16, 64, 64, 3, 1, 1),     # 4-D gather path
+]
+
+
+@pytest.mark.parametrize("N,H,W,C,Co,k,s,p", BETA_SHAPES)
+def test_implicit_conv_beta_parity(N, H, W, C, Co, k, s, p):
+    g = torch.Generator(device="cuda").manual_seed(N * 17 + H + C + Co)
+    x = torch.randn(N, H, W, C, device="cuda", generator=g).to(torch.bfloat16)
+    wt = (torch.randn(Co, C, k, k, device="cuda", generator=g) / np.sqrt(C * k * k)).to(torch.bfloat16)
+    wg = wt.permute(0, 2, 3, 1).contiguous().reshape(Co, k * k * C)
+    Ho, Wo = (H + 2 * p - k) // s + 1, (W + 2 * p - k) // s + 1
+    y0 = torch.randn(N, Ho, Wo, Co, device="cuda", generator=g)
+    y = y0.clone()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.ddppo_conv2d(x, wg, y, k, s, p, beta=0.5, status=st)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    ref = F.conv2d(x.double().cpu().permute(0, 3, 1, 2), wt.double().cpu(), stride=s, padding=p)
+    ref = ref.permute(0, 2, 3, 1) + 0.5 * y0.double().cpu()
+    err = (y.double().cpu() - ref).abs().max().item()
+    assert err <= 4e-5 * np.sqrt(k * k * C) + 1e-6, err
+
+
 def test_unsupported_shape_is_rejected():
     # stride 2 (no halo path) with a 15-wide output (no whole rows per 128-pixel tile)
     x = torch.zeros(2, 30, 30, 32, device="cuda", dtype=torch.bfloat16)
