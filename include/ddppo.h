@@ -78,7 +78,11 @@ typedef struct {
   int32_t base_ch;        /* ResNet base width (32 or 64)                                    */
   int32_t hidden;         /* LSTM hidden size and visual FC width (128 or 512)               */
   int32_t lstm_layers;    /* 1 or 2                                                          */
-  int32_t precision;      /* 0: FP32 everywhere; 1: BF16 GEMM operands, FP32 accumulate      */
+  int32_t precision;      /* 0: FP32 everywhere; 1: BF16 GEMM operands, FP32 accumulate;
+                             2: as 1, but act-time (inference) encoder convolutions after the
+                             stem take E4M3 operands with per-tensor scales (weights: amax /
+                             448 at each weight refresh; activations: delayed, 2 amax / 448
+                             of the previous act pass). Needs net_kind 1 and 64 | base_ch  */
   /* rollout / update shapes, used to size the workspace at creation */
   int32_t rollout_T;      /* T: frames per env per rollout (128)                             */
   int32_t minibatches;    /* PPO minibatches per epoch (E must divide evenly)                */
@@ -92,7 +96,7 @@ typedef struct {
  * at step t; slot T is the bootstrap observation. */
 typedef struct {
   void* obs;            /* [dev] [T+1, E, 1, h, w]  encoder input, float (precision 0) or
-                           bf16 (precision 1); h = depth_h/(1+pool2x2), w likewise       */
+                           bf16 (precision 1, 2); h = depth_h/(1+pool2x2), w likewise       */
   float* goal;          /* [dev] [T+1, E, 3]  [r (m), cos theta, sin theta]               */
   int32_t* prev_a;      /* [dev] [T+1, E]     previous action, 4 = start token             */
   uint8_t* masks;       /* [dev] [T+1, E]     0 at an episode's first frame, else 1        */
@@ -345,6 +349,26 @@ int ddppo_conv2d(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, int32
 int ddppo_conv2d_wgrad(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, int32_t k,
                        int32_t stride, int32_t pad, const void* x, const void* dy, float* dw,
                        float beta, int32_t* status, void* stream);
+/* E4M3 contractions (FP8 inference, config "Precision" of the paper-shaped workloads).
+ * ddppo_quantize_e4m3: per-tensor quantisation of n values x [dev] (fp32, or bf16 when
+ * x_bf16): scale [dev] float = amax(|x|) / 448 (1 when every x is 0); q [dev] uint8 [n] =
+ * e4m3(x / scale), rounded to nearest even, saturating at +-448.
+ * ddppo_gemm_e4m3: C[M, N] = beta C + sa sb sum_k A[m, k] B[n, k] (+ bias) (ReLU), A and B
+ * E4M3 K-major with K, lda, ldb even and 16-byte aligned rows (16 | lda, ldb), sa = *scale_a,
+ * sb = *scale_b [dev] (NULL reads 1); C fp32. tcgen05 kind::f8f6f4, fp32 accumulation.
+ * ddppo_conv2d_e4m3: ddppo_conv2d with E4M3 x [dev] NHWC and w [dev] [Cout, k*k*C], y =
+ * beta y + sx sw conv(x, w); C a multiple of 64 (gather path) or C = 64 with stride 1 and
+ * p = k / 2 (halo path). All three: E_CONFIG for unsupported shapes, status as ddppo_gemm. */
+int ddppo_quantize_e4m3(const void* x, int32_t x_bf16, int64_t n, void* q, float* scale,
+                        void* stream);
+int ddppo_gemm_e4m3(int32_t M, int32_t N, int32_t K, const void* A, int32_t lda, const void* B,
+                    int32_t ldb, const float* scale_a, const float* scale_b, float* C, int32_t ldc,
+                    float beta, const float* bias, int32_t relu, int32_t* status, void* stream);
+int ddppo_conv2d_e4m3(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, int32_t k,
+                      int32_t stride, int32_t pad, const void* x, const void* w,
+                      const float* scale_x, const float* scale_w, float* y, float beta,
+                      int32_t* status, void* stream);
+
 /* Whether ddppo_gemm with these operands runs on the tensor cores (1) or SIMT (0). */
 int ddppo_gemm_backend(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const void* A,
                        int32_t lda, const void* B, int32_t ldb, int32_t* tensor_cores);

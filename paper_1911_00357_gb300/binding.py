@@ -115,6 +115,9 @@ _SIGS = {
     "ddppo_autotune_import": [P, P, ctypes.c_size_t],
     "ddppo_conv2d": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, F32, P, P],
     "ddppo_conv2d_wgrad": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, F32, P, P],
+    "ddppo_quantize_e4m3": [P, I32, I64, P, P, P],
+    "ddppo_gemm_e4m3": [I32, I32, I32, P, I32, P, I32, P, P, P, I32, F32, P, I32, P, P],
+    "ddppo_conv2d_e4m3": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, P, P, F32, P, P],
 }
 
 
@@ -354,6 +357,35 @@ def ddppo_autotune_export(h) -> bytes:
 def ddppo_autotune_import(h, image: bytes) -> None:
     buf = ctypes.create_string_buffer(bytes(image), len(image))
     _check(lib().ddppo_autotune_import(h, buf, len(image)))
+
+
+def ddppo_quantize_e4m3(x, q, scale):
+    """Per-tensor E4M3 quantisation: scale[0] = amax|x| / 448 (1 when x is all zero),
+    q = e4m3(x / scale) as uint8 codes. x fp32 or bf16 (any shape), q uint8 (same numel),
+    scale fp32 [1]; all CUDA tensors."""
+    assert q.dtype == torch.uint8 and q.numel() == x.numel()
+    _check(lib().ddppo_quantize_e4m3(_p(x), 1 if x.dtype == torch.bfloat16 else 0, x.numel(),
+                                     _p(q), _p(scale), _s()))
+
+
+def ddppo_gemm_e4m3(A, B, C, scale_a=None, scale_b=None, beta: float = 0.0, bias=None,
+                    relu: bool = False, status=None):
+    """C (+)= scale_a scale_b A B^T with A [M, K], B [N, K] E4M3 codes (uint8 or
+    torch.float8_e4m3fn), C fp32 [M, N]; scales fp32 [1] CUDA tensors or None."""
+    M, K = A.shape
+    N = B.shape[0]
+    _check(lib().ddppo_gemm_e4m3(M, N, K, _p(A), A.stride(0), _p(B), B.stride(0), _p(scale_a),
+                                 _p(scale_b), _p(C), C.stride(0), beta, _p(bias), 1 if relu else 0,
+                                 _p(status), _s()))
+
+
+def ddppo_conv2d_e4m3(x, w, y, k: int, stride: int, pad: int, scale_x=None, scale_w=None,
+                      beta: float = 0.0, status=None):
+    """y = beta y + scale_x scale_w conv(x, w): x NHWC E4M3 [N, H, W, C], w E4M3
+    [Cout, k*k*C] (K ordered ky, kx, c), y fp32 [N, Ho, Wo, Cout]."""
+    N, H, W, C = x.shape
+    _check(lib().ddppo_conv2d_e4m3(N, H, W, C, w.shape[0], k, stride, pad, _p(x), _p(w),
+                                   _p(scale_x), _p(scale_w), _p(y), beta, _p(status), _s()))
 
 
 def ddppo_conv2d_wgrad(x, dy, dw, k: int, stride: int, pad: int, beta: float = 0.0, status=None):

@@ -59,7 +59,10 @@ static int validate(const ddppo_config* c) {
   CFG_CHECK(c->max_depth_m > 0.f && c->ceil_h_m > c->cam_h_m && c->cam_h_m > 0.f,
             "camera must sit between floor and ceiling");
   CFG_CHECK(c->net_kind == 0 || c->net_kind == 1, "net_kind must be 0 or 1");
-  CFG_CHECK(c->precision == 0 || c->precision == 1, "precision must be 0 (fp32) or 1 (bf16)");
+  CFG_CHECK(c->precision >= 0 && c->precision <= 2,
+            "precision must be 0 (fp32), 1 (bf16) or 2 (fp8 inference, bf16 training)");
+  CFG_CHECK(c->precision != 2 || (c->net_kind == 1 && c->base_ch % 64 == 0),
+            "fp8 inference needs the ResNet encoder with a base width that is a multiple of 64");
   CFG_CHECK(c->lstm_layers >= 1 && c->lstm_layers <= 4, "lstm_layers must be in [1, 4]");
   CFG_CHECK(c->hidden >= 8 && c->hidden % 8 == 0 && c->hidden <= 2048,
             "hidden must be a multiple of 8 in [8, 2048]");
@@ -100,7 +103,7 @@ static SimParams make_sim_params(const ddppo_config* c) {
   p.max_segs = c->gen_kind == 1
                    ? (c->grid_max - 2) * (c->grid_max - 2) / (c->min_room * c->min_room) + 1
                    : 0;
-  p.bf16_obs = c->precision == 1;
+  p.bf16_obs = c->precision >= 1;
   return p;
 }
 

@@ -137,6 +137,37 @@ int launch_splitk_reduce(int M, int N, int splits, const float* partial, float* 
   return DDPPO_OK;
 }
 
+// E4M3 operands on the tensor cores. The kernel's layouts are byte layouts (a 128-byte
+// operand row is 64 bf16 or 128 E4M3 values, and one MMA consumes 32 bytes of K either
+// way), so the contraction runs on the 16-bit view of its operands: K, the leading
+// dimensions and a convolution's channels count E4M3 pairs, and only the MMA kind and the
+// epilogue's scale differ from the bf16 form.
+static int gemm_fp8(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s) {
+  if (d.convw || d.a_t || d.b_t || (d.K % 2) || (d.lda % 2) || (d.ldb % 2) ||
+      (d.conv && (d.conv->C % 2))) {
+    set_error("gemm: E4M3 operands must be K-major with even K, leading dimensions and channels");
+    return DDPPO_E_CONFIG;
+  }
+  GemmDesc p = d;
+  p.K = d.K / 2;
+  p.lda = d.lda / 2;
+  p.ldb = d.ldb / 2;
+  ConvShape cp;
+  if (d.conv) {
+    cp = *d.conv;
+    cp.C = d.conv->C / 2;
+    p.conv = &cp;
+    if (!gemm_conv_supported(cp, p.A)) {
+      set_error("gemm: E4M3 convolution needs 64 | C (or C = 64 on the halo path)");
+      return DDPPO_E_CONFIG;
+    }
+  } else if (!gemm_tc_supported(p)) {
+    set_error("gemm: E4M3 operands need 16-byte aligned rows and K >= 32");
+    return DDPPO_E_CONFIG;
+  }
+  return gemm_tc(p, ws, s);
+}
+
 int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t s,
          KernelTimer* timer) {
   if (d.M <= 0 || d.N <= 0) return DDPPO_OK;
@@ -144,11 +175,15 @@ int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t 
     set_error("gemm: K must be positive");
     return DDPPO_E_CONFIG;
   }
+  if (d.fp8 && (!op_bf16 || d.c_bf16)) {
+    set_error("gemm: E4M3 operands need the tensor-core path and an fp32 output");
+    return DDPPO_E_CONFIG;
+  }
   if (d.c_bf16 && d.beta != 0.f) {
     set_error("gemm: bf16 output cannot accumulate");
     return DDPPO_E_CONFIG;
   }
-  if (d.conv && !(op_bf16 && gemm_conv_supported(*d.conv, d.A))) {
+  if (d.conv && !d.fp8 && !(op_bf16 && gemm_conv_supported(*d.conv, d.A))) {
     set_error("gemm: implicit convolution not supported for this shape");
     return DDPPO_E_CONFIG;
   }
@@ -171,7 +206,13 @@ int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t 
     cudaEventRecordWithFlags(timer->ev[timer->n], s, rec_flags);
   }
   int rc;
-  if (op_bf16 && gemm_small_supported(d)) {
+  if (d.fp8) {
+    rc = gemm_fp8(d, ws, s);
+    if (ws.tc && ws.tc->on) {
+      ws.tc->launches += 1;
+      ws.tc->flops += 2.0 * d.M * d.N * d.K;
+    }
+  } else if (op_bf16 && gemm_small_supported(d)) {
     rc = gemm_small(d, s);  // latency-bound small-M shapes: no tensor-memory pipeline
   } else if (op_bf16 && d.convw && conv_wgrad_halo_ok(*d.convw, d.B, d.A)) {
     rc = conv_wgrad_halo(*d.convw, d.B, d.A, (float*)d.C, d.ldc, d.beta, ws, s);
@@ -186,7 +227,7 @@ int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t 
   }
   if (rec) {
     cudaEventRecordWithFlags(timer->ev[timer->n + 1], s, rec_flags);
-    const double es = op_bf16 ? 2.0 : 4.0, cs = d.c_bf16 ? 2.0 : 4.0;
+    const double es = d.fp8 ? 1.0 : op_bf16 ? 2.0 : 4.0, cs = d.c_bf16 ? 2.0 : 4.0;
     timer->work[timer->n / 2] = 2.0 * d.M * d.N * d.K;
     // operands read once, result written once (and read when accumulating); an implicit
     // convolution reads its input tensor, not the M x K patch matrix

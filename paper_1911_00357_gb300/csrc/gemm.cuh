@@ -37,6 +37,12 @@ struct GemmDesc {
   int relu = 0;
   int a_t = 0;  // A stored [K][M]
   int b_t = 0;  // B stored [K][N]
+  // fp8: A and B hold E4M3 values, both K-major (K, lda, ldb and a convolution's C count
+  // E4M3 elements); the product is multiplied by *scale_a * *scale_b (device scalars, null
+  // reads as 1) before beta, bias and ReLU
+  int fp8 = 0;
+  const float* scale_a = nullptr;
+  const float* scale_b = nullptr;
 };
 
 struct GemmTcCount {

@@ -206,6 +206,32 @@ __host__ __device__ constexpr uint32_t f16_idesc(int M, int N, int a_mn = 0, int
          ((uint32_t)(b_mn & 1) << 16) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// instruction descriptor, kind::f8f6f4: D f32, A/B E4M3 (format code 0), both K-major
+__host__ __device__ constexpr uint32_t f8_idesc(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+// one MMA of the tile into TMEM: bf16 x bf16 (K = 16) or E4M3 x E4M3 (K = 32). Either way
+// it consumes 32 bytes of every operand row, so the shared-memory layouts and descriptors
+// are the same; acc = 0 overwrites the accumulator
+__device__ __forceinline__ void tc_mma(uint32_t dacc, uint64_t da, uint64_t db, uint32_t idesc,
+                                       uint32_t acc, int fp8) {
+  if (fp8)
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(dacc),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+  else
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dacc),
+        "l"(da), "l"(db), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
 // Persistent, warp-specialised kernel. Warp 0 streams (tile, k-block) stages through the
 // shared-memory ring with TMA; warp 1 issues the MMAs of a tile into one of two TMEM
 // accumulators; warps 2..5 drain the other accumulator (tcgen05.ld -> smem transpose ->
@@ -219,7 +245,8 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
                    int M, int N, int K, int kchunk, float* __restrict__ C, int ldc, int c_bf16,
                    float beta, const float* __restrict__ bias, int relu, int trans_out,
                    float* __restrict__ partial, int32_t* err, int a_mn, int b_mn, int stages,
-                   int tiles_m, int tiles_n, int splits, ConvA ca) {
+                   int tiles_m, int tiles_n, int splits, ConvA ca, int fp8,
+                   const float* __restrict__ scale_a, const float* __restrict__ scale_b) {
   extern __shared__ __align__(1024) uint8_t dyn[];
   __shared__ TcSmem ctl;
   __shared__ uint64_t acc_full[2], acc_empty[2];
@@ -294,7 +321,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
   } else if (warp == 1 && halo) {
     if (lane == 0) {
       // halo MMA issuer: tap (ky, kx) reads the staged box from row off + ky Wp + kx on
-      const uint32_t idesc = f16_idesc(TC_BM, BN, 0, 0);
+      const uint32_t idesc = fp8 ? f8_idesc(TC_BM, BN) : f16_idesc(TC_BM, BN, 0, 0);
       const int nkk = ca.k * ca.k, ncb = ca.C / ca.cbw, rb = ca.cbw * 2;
       const uint32_t wbox = (uint32_t)BN * ca.cbw * 2;
       const bool wok = mbar_wait(&ctl.done, 0u, abort, err);
@@ -321,12 +348,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
             for (int kq = 0; kq < ca.cbw / 16; ++kq) {
               const uint64_t da = ca.cbw == 32 ? sw64_desc(arow + kq * 32) : sw128_desc(arow + kq * 32);
               const uint64_t db = ca.cbw == 32 ? sw64_desc(b0 + kq * 32) : sw128_desc(b0 + kq * 32);
-              asm volatile(
-                  "{\n\t.reg .pred p;\n\t"
-                  "setp.ne.b32 p, %4, 0;\n\t"
-                  "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dacc),
-                  "l"(da), "l"(db), "r"(idesc), "r"(acc)
-                  : "memory");
+              tc_mma(dacc, da, db, idesc, acc, fp8);
               acc = 1u;
             }
           }
@@ -414,7 +436,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
   } else if (warp == 1) {
     if (lane == 0) {
       // MMA issuer
-      const uint32_t idesc = f16_idesc(TC_BM, BN, a_mn, b_mn);
+      const uint32_t idesc = fp8 ? f8_idesc(TC_BM, BN) : f16_idesc(TC_BM, BN, a_mn, b_mn);
       const int kstep = ca.on == 1 ? ca.cbw : TC_BK;
       const bool sw64 = ca.on == 1 && ca.cbw == 32;
       const bool a_sw64_mn = ca.on == 2 && ca.cbw == 32;
@@ -446,12 +468,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
               db = b_mn ? sw128_mn_desc(b0 + k * 2048) : sw128_desc(b0 + k * 32);
             }
             const uint32_t acc = (kb | k) ? 1u : 0u;
-            asm volatile(
-                "{\n\t.reg .pred p;\n\t"
-                "setp.ne.b32 p, %4, 0;\n\t"
-                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dacc),
-                "l"(da), "l"(db), "r"(idesc), "r"(acc)
-                : "memory");
+            tc_mma(dacc, da, db, idesc, acc, fp8);
           }
           asm volatile(
               "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -469,6 +486,8 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
     const int q = warp & 3;
     float* stage_out = epi_stage[q];
     const int Mo = trans_out ? N : M, No = trans_out ? M : N;
+    // per-tensor scales of E4M3 operands (exactly 1 otherwise)
+    const float alpha = (scale_a ? *scale_a : 1.f) * (scale_b ? *scale_b : 1.f);
     uint32_t ti = 0;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++ti) {
       const int tm = t % tiles_m, tn = (t / tiles_m) % tiles_n, z = t / (tiles_m * tiles_n);
@@ -502,7 +521,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
           for (int j = 0; j < 32; ++j) {
             const int col = n0 + c0 + j;
             if (col >= N) break;
-            float v = __uint_as_float(r[j]);
+            float v = __uint_as_float(r[j]) * alpha;
             if (partial) {
               partial[((size_t)z * Mo + col) * No + row] = v;
               continue;
@@ -520,6 +539,10 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
         // so every store instruction writes 32 consecutive values of one row
 #pragma unroll
         for (int j = 0; j < 32; ++j) stage_out[lane * TC_EPI_PITCH + j] = __uint_as_float(r[j]);
+        if (fp8) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) stage_out[lane * TC_EPI_PITCH + j] *= alpha;
+        }
         __syncwarp();
         const int col = n0 + c0 + lane;
         const bool cin = col < N;
@@ -536,10 +559,12 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
             }
             if (!cin) continue;
             // accumulated output: the group's eight loads are issued before its stores
-            float cv[8];
+            float cv[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (beta != 0.f && !partial) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k)
-              cv[k] = (beta != 0.f && !partial && orows[k] >= 0) ? C[(size_t)orows[k] * ldc + col] : 0.f;
+              for (int k = 0; k < 8; ++k)
+                if (orows[k] >= 0) cv[k] = C[(size_t)orows[k] * ldc + col];
+            }
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
               const long long orow = orows[k];
@@ -968,7 +993,7 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
   const int grid = min(ntiles, ws.num_sms * per_sm);
   gemm_tc_kernel<BN><<<grid, TC_PTHREADS, smem, s>>>(
       ma, mb, M, N, K, kchunk, (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu, trans,
-      partial, ws.err, a_mn, b_mn, stages, gm, gn, splits, ca);
+      partial, ws.err, a_mn, b_mn, stages, gm, gn, splits, ca, d.fp8, d.scale_a, d.scale_b);
   DDPPO_CHECK_LAUNCH();
   if (partial)
     DDPPO_TRY(launch_splitk_reduce(d.M, d.N, splits, partial, (float*)d.C, d.ldc, d.c_bf16, d.beta,
@@ -1121,8 +1146,8 @@ int gemm_tc(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s) {
     const ConvShape* cv = d.conv ? d.conv : d.convw;
     const int mode = d.a_t * 2 + d.b_t + (d.conv ? 4 : 0) + (d.convw ? 128 : 0) +
                      (cv ? 8 * cv->s + 256 * cv->Wo + 65536 * cv->k : 0);
-    const auto key = std::make_tuple(d.M, d.N, d.K, mode,
-                                     d.c_bf16, d.beta != 0.f ? 1 : 0, d.lda * 8 + d.ldb);
+    const auto key = std::make_tuple(d.M, d.N, d.K, mode, d.c_bf16 + 2 * d.fp8,
+                                     d.beta != 0.f ? 1 : 0, d.lda * 8 + d.ldb);
     auto it = t->table.find(key);
     if (it != t->table.end()) {
       cfg = it->second;

@@ -43,6 +43,30 @@ __device__ __forceinline__ void stv_bf(__nv_bfloat16* p, const float (&v)[V]) {
   if constexpr (V == 4) *reinterpret_cast<uint2*>(p) = make_uint2(pack_bf2(v[0], v[1]), pack_bf2(v[2], v[3]));
   else *reinterpret_cast<uint32_t*>(p) = pack_bf2(v[0], v[1]);
 }
+
+// E4M3 codes of v / sc (saturating), V consecutive bytes
+template <int V>
+__device__ __forceinline__ void stv_e4m3(uint8_t* p, const float (&v)[V], float sc) {
+  uint32_t w = 0;
+#pragma unroll
+  for (int j = 0; j < V; ++j) w |= (uint32_t)e4m3_sat(v[j] / sc) << (8 * j);
+  if (V == 4) *reinterpret_cast<uint32_t*>(p) = w;
+  else *reinterpret_cast<uint16_t*>(p) = (uint16_t)w;
+}
+
+// the block's largest m folded into *amax (one atomic per block; every thread calls it)
+__device__ __forceinline__ void block_amax(float m, unsigned* amax) {
+  __shared__ float wm[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b = fmaxf(b, wm[w]);
+    atomicMax(amax, __float_as_uint(b));
+  }
+}
 template <int V>
 __device__ __forceinline__ void stv_op(void* p, size_t i, const float (&v)[V], bool bf) {
   if (bf) stv_bf<V>((__nv_bfloat16*)p + i, v);
@@ -155,6 +179,8 @@ __global__ void __launch_bounds__(kThreads) gn_apply_kernel(GNApply a, int HW, i
   const int n = blockIdx.y;
   const int per = HW * R;
   const size_t ib = (size_t)n * HW * C;
+  const float f8s = a.out_f8 ? *a.f8_scale : 1.f;
+  float f8m = 0.f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per; i += gridDim.x * blockDim.x) {
     const int cv = i % R, c0 = cv * V;
     const size_t o = ib + (size_t)i * V;
@@ -188,7 +214,13 @@ __global__ void __launch_bounds__(kThreads) gn_apply_kernel(GNApply a, int HW, i
     }
     if (a.out) stv<V>(a.out + o, x);
     if (a.out_bf) stv_bf<V>(a.out_bf + o, x);
+    if (a.out_f8) {
+      stv_e4m3<V>(a.out_f8 + o, x, f8s);
+#pragma unroll
+      for (int v = 0; v < V; ++v) f8m = fmaxf(f8m, fabsf(x[v]));
+    }
   }
+  if (a.out_f8) block_amax(f8m, a.f8_amax);
 }
 
 // ---- backward reductions: g = dy (masked by relu_y > 0), xhat = (z - mu) rstd;
@@ -406,6 +438,8 @@ __global__ void __launch_bounds__(kThreads) gn_relu_maxpool_kernel(GNApply a, in
   const int Hq = (H - 1) / 2 + 1, Wq = (W - 1) / 2 + 1, C4 = C / 4, G = C / 2;
   const int n = blockIdx.y, per = Hq * Wq * C4;
   const float* zi = a.z + (size_t)n * H * W * C;
+  const float f8s = a.out_f8 ? *a.f8_scale : 1.f;
+  float f8m = 0.f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per; i += gridDim.x * blockDim.x) {
     const int c4 = i % C4, pix = i / C4, c0 = c4 * 4;
     const int ox = pix % Wq, oy = pix / Wq;
@@ -437,8 +471,14 @@ __global__ void __launch_bounds__(kThreads) gn_relu_maxpool_kernel(GNApply a, in
     const size_t o = (size_t)n * per * 4 + (size_t)i * 4;
     stv<4>(pool + o, best);
     if (pool_bf) stv_bf<4>(pool_bf + o, best);
+    if (a.out_f8) {
+      stv_e4m3<4>(a.out_f8 + o, best, f8s);
+#pragma unroll
+      for (int v = 0; v < 4; ++v) f8m = fmaxf(f8m, best[v]);
+    }
     *reinterpret_cast<uchar4*>(arg + o) = make_uchar4(bi[0], bi[1], bi[2], bi[3]);
   }
+  if (a.out_f8) block_amax(f8m, a.f8_amax);
 }
 
 int launch_gn_relu_maxpool(const GNApply& a, int N, int H, int W, int C, float* pool,

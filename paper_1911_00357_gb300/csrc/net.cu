@@ -138,6 +138,42 @@ static int build_layout(Net& n, Layout& lay) {
   return DDPPO_OK;
 }
 
+// FP8 inference buffers: E4M3 copies of the act-time convolution inputs (E images), E4M3
+// weights of every convolution whose input channels are a multiple of 64, and the scale /
+// absolute-maximum slots (activations first, then weights)
+static int alloc_f8(Net& n, int pool_hw) {
+  const size_t E = n.E;
+  int slot = 0;
+  n.pool_slot = slot++;
+  DDPPO_TRY(nalloc(n, &n.pool_f8, E * pool_hw * n.stem.cout));
+  for (auto& B : n.blocks) {
+    B.n1.f8_slot = slot++;
+    B.y_slot = slot++;
+    DDPPO_TRY(nalloc(n, &B.n1.out_f8, E * B.c1.Ho * B.c1.Wo * B.c1.cout));
+    DDPPO_TRY(nalloc(n, &B.y_f8, E * B.c2.Ho * B.c2.Wo * B.c2.cout));
+  }
+  n.f8_act_slots = slot;
+  std::vector<ConvL*> wq;
+  for (ConvL* c : n.convs)
+    if (c->cin % 64 == 0 && c->Kp == c->k * c->k * c->cin) wq.push_back(c);
+  n.f8_slots = slot + (int)wq.size();
+  DDPPO_TRY(nalloc(n, &n.f8_scale, (size_t)n.f8_slots));
+  DDPPO_TRY(nalloc(n, &n.f8_amax, (size_t)n.f8_slots));
+  for (ConvL* c : wq) {
+    DDPPO_TRY(nalloc(n, &c->wg8, (size_t)c->cout * c->Kp));
+    c->w8_scale = n.f8_scale + slot;
+    c->w8_amax = n.f8_amax + slot;
+    ++slot;
+  }
+  // first act pass: activations carried at scale 1/8 (|x| up to 56); later passes use the
+  // previous pass's maxima
+  std::vector<float> init(n.f8_slots, 1.f);
+  for (int i = 0; i < n.f8_act_slots; ++i) init[i] = 0.125f;
+  DDPPO_CHECK_CUDA(cudaMemcpy(n.f8_scale, init.data(), init.size() * 4, cudaMemcpyHostToDevice));
+  DDPPO_CHECK_CUDA(cudaMemset(n.f8_amax, 0, (size_t)n.f8_slots * 4));
+  return DDPPO_OK;
+}
+
 static int alloc_encoder(Net& n) {
   const size_t NC = n.NC;
   auto conv_bufs = [&](ConvL& c) -> int {
@@ -192,6 +228,7 @@ static int alloc_encoder(Net& n) {
     }
     DDPPO_TRY(conv_bufs(n.cmp));
     DDPPO_TRY(gn_bufs(n.cmp_n, n.featHW, true));
+    if (n.f8) DDPPO_TRY(alloc_f8(n, ph * pw));
   }
   DDPPO_TRY(nalloc_op(n, &n.col, NC * n.max_col));
   DDPPO_TRY(nalloc(n, &n.dcol, NC * n.max_col));
@@ -273,6 +310,17 @@ int net_prep_weights(Net& n, cudaStream_t s) {
     if (c->dgrad_as_conv)
       DDPPO_TRY(launch_conv_w_flip(n.params + c->w_off, c->cout, c->cin, c->k, c->wgR, n.bf, s));
   }
+  if (n.f8) {
+    // per-tensor E4M3 weights from the bf16 GEMM layout
+    const int na = n.f8_act_slots;
+    DDPPO_CHECK_CUDA(cudaMemsetAsync(n.f8_amax + na, 0, (size_t)(n.f8_slots - na) * 4, s));
+    for (ConvL* c : n.convs) {
+      if (!c->wg8) continue;
+      const size_t cnt = (size_t)c->cout * c->Kp;
+      DDPPO_TRY(launch_amax(c->wg, true, cnt, c->w8_amax, s));
+      DDPPO_TRY(launch_quant_e4m3(c->wg, true, cnt, c->w8_amax, c->w8_scale, c->wg8, s));
+    }
+  }
   DDPPO_TRY(launch_vis_w_prep(n.params + n.vis_w, n.H, n.featC, n.featHW, n.Wv, n.WvT, n.bf, s));
   for (int l = 0; l < n.L; ++l) {
     LstmL& q = n.lstm[l];
@@ -292,7 +340,8 @@ int net_create(ddppo_ctx* x) {
   Net& n = *np;
   n.x = x;
   const ddppo_config& c = x->cfg;
-  n.bf = c.precision == 1;
+  n.bf = c.precision >= 1;
+  n.f8 = c.precision == 2;
   n.kind = c.net_kind;
   n.H = c.hidden;
   n.L = c.lstm_layers;
@@ -429,13 +478,23 @@ static ConvShape conv_shape(const ConvL& c, int N) {
 // forward convolution. in_bf (bf16 NHWC copy of the input, BF16 form) lets the tensor-core
 // GEMM gather the patches itself; otherwise im2col materialises them first
 static int conv_fwd(Net& n, ConvL& c, const void* in, bool in_bf16, int N, float* out, bool bias_relu,
-                    cudaStream_t s, const __nv_bfloat16* in_bf = nullptr) {
+                    cudaStream_t s, const __nv_bfloat16* in_bf = nullptr,
+                    const uint8_t* in_f8 = nullptr, const float* in_scale = nullptr) {
   GemmDesc d;
   d.M = N * c.Ho * c.Wo; d.N = c.cout; d.K = c.Kp;
   d.B = c.wg; d.ldb = c.Kp;
   d.C = out; d.ldc = c.cout;
   if (bias_relu) { d.bias = n.params + c.b_off; d.relu = 1; }
   const ConvShape cs = conv_shape(c, N);
+  if (in_f8 && c.wg8) {
+    // FP8 inference: E4M3 input and weights, the product rescaled in the epilogue
+    d.conv = &cs;
+    d.fp8 = 1;
+    d.A = in_f8; d.lda = d.K;
+    d.B = c.wg8;
+    d.scale_a = in_scale; d.scale_b = c.w8_scale;
+    return G(n, d, s);
+  }
   if (n.bf && in_bf && c.Kp == c.k * c.k * c.cin && gemm_conv_supported(cs, in_bf)) {
     d.conv = &cs;
     d.A = in_bf; d.lda = d.K;
@@ -504,7 +563,7 @@ static int conv_bwd(Net& n, ConvL& c, const void* in, bool in_bf16, int N, const
 
 static int gn_fwd(Net& n, GNL& g, const float* z, int N, int HW, float* out, bool relu,
                   const float* resid, const GNL* gd, const float* zd, cudaStream_t s,
-                  __nv_bfloat16* out_bf = nullptr) {
+                  __nv_bfloat16* out_bf = nullptr, uint8_t* out_f8 = nullptr, int f8_slot = -1) {
   const float eps = 1e-5f;
   DDPPO_TRY(launch_gn_stats(z, N, HW, g.C, eps, g.mean, g.rstd, n.gnw, s));
   GNApply a{};
@@ -518,6 +577,11 @@ static int gn_fwd(Net& n, GNL& g, const float* z, int N, int HW, float* out, boo
   }
   a.out = out;
   a.out_bf = out_bf;
+  if (out_f8) {
+    a.out_f8 = out_f8;
+    a.f8_scale = n.f8_scale + f8_slot;
+    a.f8_amax = n.f8_amax + f8_slot;
+  }
   a.relu = relu ? 1 : 0;
   return launch_gn_apply(a, N, HW, g.C, s);
 }
@@ -538,8 +602,11 @@ static int gn_bwd(Net& n, GNL& g, const float* dy, const float* z, int N, int HW
   return DDPPO_OK;
 }
 
-// forward of one chunk of N images: obs (op dtype) -> featop rows (op dtype)
-static int encoder_fwd(Net& n, const void* obs, int N, void* featop_rows, cudaStream_t s) {
+// forward of one chunk of N images: obs (op dtype) -> featop rows (op dtype). f8: the
+// act-time pass of FP8 inference (N <= E): every convolution after the stem reads E4M3
+// copies of its input and weights; the activation scales advance once per pass
+static int encoder_fwd(Net& n, const void* obs, int N, void* featop_rows, cudaStream_t s,
+                       bool f8 = false) {
   if (n.kind == 0) {
     DDPPO_TRY(conv_fwd(n, n.nat[0], obs, n.bf, N, n.nat[0].z, true, s));
     DDPPO_TRY(conv_fwd(n, n.nat[1], n.nat[0].z, false, N, n.nat[1].z, true, s));
@@ -557,7 +624,13 @@ static int encoder_fwd(Net& n, const void* obs, int N, void* featop_rows, cudaSt
     a.z = st.z; a.mean = n.stem_n.mean; a.rstd = n.stem_n.rstd;
     a.gamma = n.params + n.stem_n.g_off; a.beta = n.params + n.stem_n.b_off;
     a.relu = 1;
-    DDPPO_TRY(launch_gn_relu_maxpool(a, N, st.Ho, st.Wo, st.cout, n.pool, n.pool_bf, n.pool_arg, s));
+    if (f8) {
+      a.out_f8 = n.pool_f8;
+      a.f8_scale = n.f8_scale + n.pool_slot;
+      a.f8_amax = n.f8_amax + n.pool_slot;
+    }
+    DDPPO_TRY(launch_gn_relu_maxpool(a, N, st.Ho, st.Wo, st.cout, n.pool, f8 ? nullptr : n.pool_bf,
+                                     n.pool_arg, s));
   } else {
     DDPPO_TRY(gn_fwd(n, n.stem_n, st.z, N, st.Ho * st.Wo, n.stem_n.out, true, nullptr, nullptr,
                      nullptr, s));
@@ -565,24 +638,34 @@ static int encoder_fwd(Net& n, const void* obs, int N, void* featop_rows, cudaSt
                                  n.pool_bf, s));
   }
   const float* cur = n.pool;
-  const __nv_bfloat16* cur_bf = n.pool_bf;
+  const __nv_bfloat16* cur_bf = f8 ? nullptr : n.pool_bf;
+  const uint8_t* cur_f8 = f8 ? n.pool_f8 : nullptr;
+  const float* cur_sc = f8 ? n.f8_scale + n.pool_slot : nullptr;
   for (auto& B : n.blocks) {
     const int HW = B.c1.Ho * B.c1.Wo;
-    DDPPO_TRY(conv_fwd(n, B.c1, cur, false, N, B.c1.z, false, s, cur_bf));
+    DDPPO_TRY(conv_fwd(n, B.c1, cur, false, N, B.c1.z, false, s, cur_bf, cur_f8, cur_sc));
     DDPPO_TRY(gn_fwd(n, B.n1, B.c1.z, N, HW, B.n1.out, true, nullptr, nullptr, nullptr, s,
-                     B.n1.out_bf));
-    DDPPO_TRY(conv_fwd(n, B.c2, B.n1.out, false, N, B.c2.z, false, s, B.n1.out_bf));
+                     f8 ? nullptr : B.n1.out_bf, f8 ? B.n1.out_f8 : nullptr, B.n1.f8_slot));
+    DDPPO_TRY(conv_fwd(n, B.c2, B.n1.out, false, N, B.c2.z, false, s, f8 ? nullptr : B.n1.out_bf,
+                       f8 ? B.n1.out_f8 : nullptr, f8 ? n.f8_scale + B.n1.f8_slot : nullptr));
+    uint8_t* y_f8 = f8 ? B.y_f8 : nullptr;
+    __nv_bfloat16* y_bf = f8 ? nullptr : B.y_bf;
     if (B.down) {
-      DDPPO_TRY(conv_fwd(n, B.d, cur, false, N, B.d.z, false, s, cur_bf));
-      DDPPO_TRY(gn_fwd(n, B.n2, B.c2.z, N, HW, B.y, true, nullptr, &B.nd, B.d.z, s, B.y_bf));
+      DDPPO_TRY(conv_fwd(n, B.d, cur, false, N, B.d.z, false, s, cur_bf, cur_f8, cur_sc));
+      DDPPO_TRY(gn_fwd(n, B.n2, B.c2.z, N, HW, B.y, true, nullptr, &B.nd, B.d.z, s, y_bf, y_f8,
+                       B.y_slot));
     } else {
-      DDPPO_TRY(gn_fwd(n, B.n2, B.c2.z, N, HW, B.y, true, cur, nullptr, nullptr, s, B.y_bf));
+      DDPPO_TRY(gn_fwd(n, B.n2, B.c2.z, N, HW, B.y, true, cur, nullptr, nullptr, s, y_bf, y_f8,
+                       B.y_slot));
     }
     cur = B.y;
-    cur_bf = B.y_bf;
+    cur_bf = y_bf;
+    cur_f8 = y_f8;
+    cur_sc = f8 ? n.f8_scale + B.y_slot : nullptr;
   }
-  DDPPO_TRY(conv_fwd(n, n.cmp, cur, false, N, n.cmp.z, false, s, cur_bf));
+  DDPPO_TRY(conv_fwd(n, n.cmp, cur, false, N, n.cmp.z, false, s, cur_bf, cur_f8, cur_sc));
   DDPPO_TRY(gn_fwd(n, n.cmp_n, n.cmp.z, N, n.featHW, n.cmp_n.out, true, nullptr, nullptr, nullptr, s));
+  if (f8) DDPPO_TRY(launch_f8_scale_update(n.f8_scale, n.f8_amax, n.f8_act_slots, s));
   return launch_cast(n.cmp_n.out, featop_rows, n.bf, (size_t)N * n.F, s);
 }
 
@@ -660,7 +743,7 @@ static int encoder_bwd(Net& n, const void* obs, int N, const float* dfeat_rows, 
 // ---------------------------------------------------------------- forward / backward
 int net_forward(Net& n, int T, int E, const void* obs, const float* goal, const int32_t* prev_a,
                 const uint8_t* masks, const float* h0, const float* c0, const float* u,
-                int32_t* action, float* logp, cudaStream_t s) {
+                int32_t* action, float* logp, cudaStream_t s, bool infer) {
   const int N = T * E, Hd = n.H, G4 = 4 * Hd;
   if (N > n.NS || E > n.E) {
     set_error("forward: segment larger than the workspace");
@@ -670,7 +753,7 @@ int net_forward(Net& n, int T, int E, const void* obs, const float* goal, const 
   for (int c = 0; c < nch; ++c) {
     const int r0 = c * n.NC, rn = std::min(n.NC, N - r0);
     DDPPO_TRY(encoder_fwd(n, opoff(n, obs, (size_t)r0 * n.pix), rn,
-                          opoff(n, n.featop, (size_t)r0 * n.F), s));
+                          opoff(n, n.featop, (size_t)r0 * n.F), s, infer && n.f8 && rn <= n.E));
   }
   n.ev_valid_chunk = nch - 1;
   GemmDesc v;

@@ -22,6 +22,11 @@ struct ConvL {
   bool dgrad_as_conv = false;
   float* dwg = nullptr; // [cout, Kp] fp32 gradient in GEMM layout
   float* z = nullptr;   // [NC, Ho, Wo, cout] conv output (fp32)
+  // FP8 inference: E4M3 copy of wg with its per-tensor scale (device scalar) and absolute
+  // maximum (float bits); null where the input channels are not a multiple of 64
+  uint8_t* wg8 = nullptr;
+  float* w8_scale = nullptr;
+  unsigned* w8_amax = nullptr;
 };
 
 struct GNL {
@@ -31,6 +36,8 @@ struct GNL {
   float* rstd = nullptr;
   float* out = nullptr;   // [NC, HW, C] post-activation output (when materialised)
   __nv_bfloat16* out_bf = nullptr;  // its bf16 copy (BF16 form: the next conv's TMA operand)
+  uint8_t* out_f8 = nullptr;        // [E, HW, C] its E4M3 copy (FP8 inference)
+  int f8_slot = -1;                 // activation scale slot of out_f8
 };
 
 struct BlockL {
@@ -39,6 +46,8 @@ struct BlockL {
   bool down = false;
   float* y = nullptr;     // block output [NC, Ho, Wo, cout]
   __nv_bfloat16* y_bf = nullptr;  // its bf16 copy (BF16 form)
+  uint8_t* y_f8 = nullptr;        // [E, Ho, Wo, cout] its E4M3 copy (FP8 inference)
+  int y_slot = -1;
 };
 
 struct LstmL {
@@ -59,6 +68,14 @@ struct LstmL {
 struct Net {
   ddppo_ctx* x = nullptr;
   bool bf = false;
+  // FP8 inference (precision 2): the act-time encoder convolutions after the stem take
+  // E4M3 operands; training (evaluate, update) stays BF16
+  bool f8 = false;
+  uint8_t* pool_f8 = nullptr;  // [E, pooled HW, C] E4M3 copy of the stem output
+  int pool_slot = -1;
+  float* f8_scale = nullptr;   // [f8_slots] device: activation scales (delayed), weight scales
+  unsigned* f8_amax = nullptr; // [f8_slots] device: absolute maxima (float bits)
+  int f8_act_slots = 0, f8_slots = 0;
   int kind = 0, H = 0, L = 0, inh = 0, inw = 0;
   int F = 0, featC = 0, featHW = 0;
   int E = 0, T = 0, Emb = 0, NS = 0, NC = 0;

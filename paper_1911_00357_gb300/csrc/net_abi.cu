@@ -11,9 +11,11 @@
 #include "rl.cuh"
 
 namespace ddppo {
+// infer: an act-time pass (policy_act, the collect loop, the bootstrap value); under FP8
+// inference its encoder runs on E4M3 operands
 int net_forward(Net& n, int T, int E, const void* obs, const float* goal, const int32_t* prev_a,
                 const uint8_t* masks, const float* h0, const float* c0, const float* u,
-                int32_t* action, float* logp, cudaStream_t s);
+                int32_t* action, float* logp, cudaStream_t s, bool infer = false);
 int net_backward(Net& n, const float* dlogits, const float* dvalues, cudaStream_t s);
 int net_prep_weights(Net& n, cudaStream_t s);
 }  // namespace ddppo
@@ -85,7 +87,7 @@ static int act_impl(ddppo_ctx* x, const void* obs, const float* goal, const int3
                     float* logp, float* value, cudaStream_t s) {
   Net& n = *x->net;
   const int E = x->cfg.num_envs;
-  DDPPO_TRY(net_forward(n, 1, E, obs, goal, prev_a, masks, h, c, u, action, logp, s));
+  DDPPO_TRY(net_forward(n, 1, E, obs, goal, prev_a, masks, h, c, u, action, logp, s, true));
   DDPPO_CHECK_CUDA(cudaMemcpyAsync(value, n.values, (size_t)E * 4, cudaMemcpyDeviceToDevice, s));
   n.ev_valid = false;  // the act workspace is not kept for a backward pass
   return copy_state_out(n, E, h, c, s);
@@ -371,7 +373,7 @@ extern "C" int ddppo_collect(ddppo_ctx* x, const ddppo_rollout* ro, int32_t use_
       // autotuner sees the act shapes before they are frozen into the graph
       if (n.gws.tuner) {
         DDPPO_TRY(net_forward(n, 1, E, ro->obs, ro->goal, ro->prev_a, ro->masks, ro->h, ro->c,
-                              ro->uniforms, (int32_t*)n.perm, n.dvalues, s));
+                              ro->uniforms, (int32_t*)n.perm, n.dvalues, s, true));
         n.ev_valid = false;
       }
       if (n.graph_exec) { cudaGraphExecDestroy(n.graph_exec); n.graph_exec = nullptr; }
@@ -397,7 +399,8 @@ extern "C" int ddppo_collect(ddppo_ctx* x, const ddppo_rollout* ro, int32_t use_
   // bootstrap value V(o_T) with the state after step T-1; the state itself is not advanced
   const size_t oT = (size_t)T * E;
   DDPPO_TRY(net_forward(n, 1, E, (const char*)ro->obs + oT * ob, ro->goal + oT * 3,
-                        ro->prev_a + oT, ro->masks + oT, ro->h, ro->c, nullptr, nullptr, nullptr, s));
+                        ro->prev_a + oT, ro->masks + oT, ro->h, ro->c, nullptr, nullptr, nullptr, s,
+                        true));
   DDPPO_CHECK_CUDA(cudaMemcpyAsync(ro->values + oT, n.values, (size_t)E * 4,
                                    cudaMemcpyDeviceToDevice, s));
   n.ev_valid = false;
@@ -484,7 +487,7 @@ extern "C" int ddppo_count_kernels(ddppo_ctx* x, const ddppo_rollout* ro,
   const size_t oT = (size_t)T * E;
   if (rc == DDPPO_OK)
     rc = net_forward(n, 1, E, (const char*)ro->obs + oT * ob, ro->goal + oT * 3, ro->prev_a + oT,
-                     ro->masks + oT, ro->h, ro->c, nullptr, nullptr, nullptr, n.cap_stream);
+                     ro->masks + oT, ro->h, ro->c, nullptr, nullptr, nullptr, n.cap_stream, true);
   if (rc == DDPPO_OK)
     rc = launch_gae(ro->rewards, ro->dones, ro->values, T, E, gamma, lam, ro->adv, ro->ret,
                     n.cap_stream);
@@ -627,6 +630,57 @@ extern "C" int ddppo_conv2d(int32_t N, int32_t H, int32_t W, int32_t C, int32_t 
   d.M = N * c.Ho * c.Wo; d.N = Cout; d.K = k * k * C;
   d.conv = &c; d.A = x; d.lda = d.K; d.B = w; d.ldb = d.K;
   d.C = y; d.ldc = Cout; d.beta = beta;
+  return gemm(d, true, ws, (cudaStream_t)stream, nullptr);
+}
+
+// ---- E4M3 (FP8 inference) contractions and quantisation ----
+extern "C" int ddppo_quantize_e4m3(const void* x, int32_t x_bf16, int64_t n, void* q, float* scale,
+                                   void* stream) {
+  ARG(n >= 0, "quantize_e4m3: negative size");
+  ARG(x && q && scale, "quantize_e4m3: null argument");
+  int dev = 0;
+  DDPPO_CHECK_CUDA(cudaGetDevice(&dev));
+  ARG(dev < 64, "quantize_e4m3: device ordinal out of range");
+  static unsigned* amax[64] = {};
+  if (!amax[dev]) DDPPO_CHECK_CUDA(cudaMalloc(&amax[dev], sizeof(unsigned)));
+  cudaStream_t s = (cudaStream_t)stream;
+  DDPPO_CHECK_CUDA(cudaMemsetAsync(amax[dev], 0, sizeof(unsigned), s));
+  DDPPO_TRY(launch_amax(x, x_bf16 != 0, (size_t)n, amax[dev], s));
+  return launch_quant_e4m3(x, x_bf16 != 0, (size_t)n, amax[dev], scale, (uint8_t*)q, s);
+}
+
+extern "C" int ddppo_gemm_e4m3(int32_t M, int32_t N, int32_t K, const void* A, int32_t lda,
+                               const void* B, int32_t ldb, const float* scale_a,
+                               const float* scale_b, float* C, int32_t ldc, float beta,
+                               const float* bias, int32_t relu, int32_t* status, void* stream) {
+  ARG(M >= 0 && N >= 0 && K >= 1, "gemm_e4m3: bad sizes");
+  if (M == 0 || N == 0) return DDPPO_OK;
+  ARG(A && B && C, "gemm_e4m3: null argument");
+  ARG(lda >= K && ldb >= K && ldc >= N, "gemm_e4m3: leading dimension smaller than the row");
+  GemmWorkspace ws;
+  DDPPO_TRY(standalone_ws(&ws, status));
+  GemmDesc d;
+  d.M = M; d.N = N; d.K = K; d.A = A; d.lda = lda; d.B = B; d.ldb = ldb; d.C = C; d.ldc = ldc;
+  d.beta = beta; d.bias = bias; d.relu = relu;
+  d.fp8 = 1; d.scale_a = scale_a; d.scale_b = scale_b;
+  return gemm(d, true, ws, (cudaStream_t)stream, nullptr);
+}
+
+extern "C" int ddppo_conv2d_e4m3(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout,
+                                 int32_t k, int32_t stride, int32_t pad, const void* x,
+                                 const void* w, const float* scale_x, const float* scale_w,
+                                 float* y, float beta, int32_t* status, void* stream) {
+  ConvShape c;
+  DDPPO_TRY(conv_args(N, H, W, C, Cout, k, stride, pad, &c));
+  ARG(x && w && y, "conv2d_e4m3: null argument");
+  c.Cout = Cout;
+  GemmWorkspace ws;
+  DDPPO_TRY(standalone_ws(&ws, status));
+  GemmDesc d;
+  d.M = N * c.Ho * c.Wo; d.N = Cout; d.K = k * k * C;
+  d.conv = &c; d.A = x; d.lda = d.K; d.B = w; d.ldb = d.K;
+  d.C = y; d.ldc = Cout; d.beta = beta;
+  d.fp8 = 1; d.scale_a = scale_x; d.scale_b = scale_w;
   return gemm(d, true, ws, (cudaStream_t)stream, nullptr);
 }
 

@@ -46,6 +46,9 @@ struct GNApply {
   const float* zd; const float* mean_d; const float* rstd_d; const float* gamma_d; const float* beta_d;
   float* out; int relu;
   __nv_bfloat16* out_bf;  // optional bf16 copy of out (the next convolution's TMA operand)
+  // optional E4M3 copy of out for FP8 inference: e4m3(out / *f8_scale), saturating, and
+  // the largest |out| folded into *f8_amax (float bits; a max, so the order is irrelevant)
+  uint8_t* out_f8; const float* f8_scale; unsigned* f8_amax;
 };
 int launch_gn_apply(const GNApply& a, int N, int HW, int C, cudaStream_t s);
 // GroupNorm backward. g = dy, masked by (relu_y > 0) when relu_y is given (the ReLU that
@@ -169,5 +172,23 @@ int launch_add_vec(const float* a, const float* b, float* out, int n, cudaStream
 int launch_init_uniform(float* p, size_t n, float lo, float hi, uint64_t seed, uint64_t stream,
                         cudaStream_t s);
 int launch_fill(float* p, size_t n, float v, cudaStream_t s);
+
+// ---------------------------------------------------------------- E4M3 (fp8.cu)
+constexpr float kE4M3Max = 448.f;  // largest finite E4M3 value
+
+// x -> E4M3 code: round to nearest even, saturating to +-448
+__device__ __forceinline__ uint8_t e4m3_sat(float x) {
+  return (uint8_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+}
+
+// *amax = max(*amax, max |x|) over n values (fp32, or bf16 when x_bf16); *amax holds float
+// bits and must start at 0 (or a previous maximum)
+int launch_amax(const void* x, bool x_bf16, size_t n, unsigned* amax, cudaStream_t s);
+// per-tensor quantisation: scale = amax / 448 (1 when amax = 0), q = e4m3(x / scale)
+int launch_quant_e4m3(const void* x, bool x_bf16, size_t n, const unsigned* amax, float* scale,
+                      uint8_t* q, cudaStream_t s);
+// delayed activation scales: for every slot with amax > 0, scale = 2 amax / 448 (one binade
+// of headroom for the next pass); amax is reset to 0
+int launch_f8_scale_update(float* scale, unsigned* amax, int n, cudaStream_t s);
 
 }  // namespace ddppo

@@ -7,6 +7,7 @@
                 T=128, 2 epochs x 2 minibatches (the paper-shaped single-GPU run).
   mixed_1024  : 1024 envs on grids drawn from {64,128,256,512}^2, depth 128x128, BF16.
   wide_256    : 256 envs, 64-base encoder, depth 256x256 pooled.
+  wide_256_fp8: wide_256 with FP8 (E4M3, per-tensor scales) inference and BF16 training.
   scale_4096  : 4096 envs x T=128, 4 minibatches.
 """
 from __future__ import annotations
@@ -30,6 +31,10 @@ PRESETS = {
     "wide_256": dict(num_envs=256, gen_kind=1, grid_min=128, grid_max=128, cell_m=0.1,
                      depth_h=256, depth_w=256, pool2x2=1, net_kind=1, base_ch=64, hidden=512,
                      lstm_layers=2, rollout_T=128, minibatches=2, precision=1, encoder_chunk=4096),
+    "wide_256_fp8": dict(num_envs=256, gen_kind=1, grid_min=128, grid_max=128, cell_m=0.1,
+                         depth_h=256, depth_w=256, pool2x2=1, net_kind=1, base_ch=64, hidden=512,
+                         lstm_layers=2, rollout_T=128, minibatches=2, precision=2,
+                         encoder_chunk=4096),
     "scale_4096": dict(num_envs=4096, gen_kind=1, grid_min=128, grid_max=128, cell_m=0.1,
                        depth_h=256, depth_w=256, pool2x2=1, net_kind=1, base_ch=32, hidden=512,
                        lstm_layers=2, rollout_T=128, minibatches=4, precision=1),

@@ -21,7 +21,7 @@ class Worker:
         self.gamma, self.lam = gamma, lam
         E, T, L, H = self.E, self.T, self.L, self.H
         oh = cfg.depth_h >> cfg.pool2x2
-        od = torch.bfloat16 if cfg.precision == 1 else torch.float32
+        od = torch.bfloat16 if cfg.precision >= 1 else torch.float32
         dev = "cuda"
         z = lambda *s, dt=torch.float32: torch.zeros(*s, dtype=dt, device=dev)
         self.t = {

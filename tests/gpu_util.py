@@ -33,7 +33,7 @@ def obs_shape(cfg: B.Config, *lead):
 
 
 def obs_dtype(cfg: B.Config):
-    return torch.bfloat16 if cfg.precision == 1 else torch.float32
+    return torch.bfloat16 if cfg.precision >= 1 else torch.float32
 
 
 class Env:

@@ -102,7 +102,7 @@ def test_step_and_depth_parity(world):
                 # encoder input: pooled, normalised, cast
                 o_ref = OS.pool_obs(d_ref, pool, scfg.max_depth_m)
                 o = env.obs.float().cpu().numpy()[:, 0]
-                tol = (2.0 ** -8) * np.abs(o_ref) + 2e-5 if cfg.precision == 1 else 2e-5
+                tol = (2.0 ** -8) * np.abs(o_ref) + 2e-5 if cfg.precision >= 1 else 2e-5
                 ok = np.abs(o - o_ref) <= tol
                 assert ok.mean() >= 0.9999, (1 - ok.mean())
         assert bad_px <= max(0, int(1e-4 * tot_px)), (bad_px, tot_px)

@@ -1,0 +1,266 @@
+"""GPU parity of FP8 (E4M3) inference.
+
+Quantisation: the per-tensor scale is amax / 448, and every code equals torch's own
+float -> float8_e4m3fn conversion of x / scale (round to nearest even).
+
+E4M3 contractions (tcgen05 kind::f8f6f4, fp32 accumulation): compared with the float64
+product of exactly the E4M3 values the kernel reads, times the two per-tensor scales.
+The only difference is fp32 accumulation: within 4e-5 sqrt(K) of the scaled magnitude.
+
+FP8 act (precision 2: the act-time encoder convolutions after the stem on E4M3 operands):
+E4M3 keeps 3 mantissa bits (a relative rounding step up to 2^-4 per operand), which over
+the 17 quantised convolutions of the 64-base ResNet moves the LSTM state by up to ~0.3 of
+its scale against float64: that is the cost of E4M3 itself (a float64 evaluation with the
+same operands rounded to E4M3 shows it too). The test therefore pins the GPU to that
+emulation of the same E4M3 arithmetic (same scales, same delayed-scale sequence, bf16 FC and
+LSTM weights): logp and value within the BF16 form's 5e-2, the LSTM state within 0.1; and it
+bounds the error against float64 by twice the emulation's own plus 5e-2.
+"""
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as F
+
+from oracle import policy as OP
+from paper_1911_00357_gb300 import binding as B
+from paper_1911_00357_gb300.presets import make_config
+from tests import inputs as I
+from tests.gpu_util import net_config_from, obs_dtype
+
+pytestmark = pytest.mark.gpu
+E4 = torch.float8_e4m3fn
+
+
+def _e4m3(x):
+    """E4M3 values (as float8 tensor) of a float tensor, torch's rounding."""
+    return x.to(E4)
+
+
+@pytest.mark.parametrize("n,bf16", [(1, False), (4097, False), (100003, True), (65536, False)])
+def test_quantize_e4m3_matches_torch(n, bf16):
+    g = torch.Generator().manual_seed(n)
+    x = torch.randn(n, generator=g) * torch.exp(2 * torch.randn(n, generator=g))
+    if bf16:
+        x = x.to(torch.bfloat16)
+    xd = x.cuda()
+    q = torch.empty(n, dtype=torch.uint8, device="cuda")
+    sc = torch.zeros(1, device="cuda")
+    B.ddppo_quantize_e4m3(xd, q, sc)
+    torch.cuda.synchronize()
+    xf = x.float()
+    scale = xf.abs().max() / 448.0
+    assert sc.item() == scale.item()
+    ref = (xf / scale).to(E4).view(torch.uint8)
+    assert torch.equal(q.cpu(), ref)
+
+
+def test_quantize_e4m3_zero_tensor():
+    x = torch.zeros(1000, device="cuda")
+    q = torch.full((1000,), 7, dtype=torch.uint8, device="cuda")
+    sc = torch.zeros(1, device="cuda")
+    B.ddppo_quantize_e4m3(x, q, sc)
+    torch.cuda.synchronize()
+    assert sc.item() == 1.0 and int(q.max()) == 0
+
+
+GEMM_SHAPES = [
+    (300, 64, 256),     # ragged M, N tile 64
+    (128, 128, 512),
+    (1000, 256, 1024),  # several N tiles, split-K candidates
+    (77, 40, 96),       # ragged everything, K not a multiple of the 128-element K block
+    (40, 200, 128),     # M < 128 with N > M: computed transposed
+]
+
+
+@pytest.mark.parametrize("M,N,K", GEMM_SHAPES)
+def test_gemm_e4m3_parity(M, N, K):
+    g = torch.Generator().manual_seed(M * 7 + N + K)
+    A = _e4m3(torch.randn(M, K, generator=g))
+    Bm = _e4m3(torch.randn(N, K, generator=g))
+    sa = torch.tensor([0.5], device="cuda")
+    sb = torch.tensor([0.125], device="cuda")
+    bias = torch.randn(N, generator=g)
+    C0 = torch.randn(M, N, generator=g)
+    C = C0.cuda()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.ddppo_gemm_e4m3(A.cuda(), Bm.cuda(), C, sa, sb, beta=0.5, bias=bias.cuda(), relu=True, status=st)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    ref = 0.5 * 0.125 * (A.double() @ Bm.double().T) + 0.5 * C0.double() + bias.double()
+    ref = ref.clamp_min(0)
+    err = (C.cpu().double() - ref).abs().max().item()
+    assert err <= 4e-5 * np.sqrt(K) * 0.0625 * 4 + 1e-6, err
+
+
+def test_gemm_e4m3_rejects_odd_k():
+    A = torch.zeros(128, 33, dtype=torch.uint8, device="cuda")
+    Bm = torch.zeros(64, 33, dtype=torch.uint8, device="cuda")
+    C = torch.zeros(128, 64, device="cuda")
+    with pytest.raises(B.DDPPOError) as ei:
+        B.ddppo_gemm_e4m3(A, Bm, C)
+    assert ei.value.code == -2
+
+
+# (N, H, W, C, Cout, k, s, p): the 64-base encoder's layer shapes plus ragged cases
+CONV_SHAPES = [
+    (3, 32, 32, 64, 64, 3, 1, 1),     # first stage (64 channels = 32 byte pairs)
+    (2, 30, 30, 64, 64, 3, 1, 1),     # halo path only (no whole rows per 128-pixel tile)
+    (3, 15, 15, 64, 64, 3, 1, 1),     # halo, tiles straddle rows
+    (2, 16, 16, 128, 128, 3, 1, 1),   # 128 channels: 128-byte rows
+    (3, 16, 16, 64, 128, 3, 2, 1),    # stride 2
+    (4, 16, 16, 128, 256, 1, 2, 0),   # 1x1 stride-2 shortcut
+    (2, 8, 8, 512, 128, 3, 1, 1),     # compression conv shape
+]
+
+
+@pytest.mark.parametrize("N,H,W,C,Co,k,s,p", CONV_SHAPES)
+@pytest.mark.parametrize("beta", [0.0, 1.0])
+def test_conv2d_e4m3_parity(N, H, W, C, Co, k, s, p, beta):
+    g = torch.Generator().manual_seed(N * 131 + C * 7 + Co + k + s)
+    x = _e4m3(torch.relu(torch.randn(N, H, W, C, generator=g)) * 4)
+    wt = _e4m3(torch.randn(Co, C, k, k, generator=g) * 8)
+    wg = wt.float().permute(0, 2, 3, 1).contiguous().reshape(Co, k * k * C).to(E4)
+    sx = torch.tensor([0.25], device="cuda")
+    sw = torch.tensor([1.0 / 64], device="cuda")
+    Ho, Wo = (H + 2 * p - k) // s + 1, (W + 2 * p - k) // s + 1
+    y0 = torch.randn(N, Ho, Wo, Co, generator=g)
+    y = y0.cuda()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.ddppo_conv2d_e4m3(x.cuda(), wg.cuda(), y, k, s, p, sx, sw, beta=beta, status=st)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    ref = F.conv2d(x.double().permute(0, 3, 1, 2), wt.double(), stride=s, padding=p)
+    ref = ref.permute(0, 2, 3, 1) * (0.25 / 64) + beta * y0.double()
+    scale = max(ref.abs().max().item(), 1.0)
+    err = (y.cpu().double() - ref).abs().max().item()
+    assert err <= 4e-5 * np.sqrt(k * k * C) * scale, err
+
+
+def test_conv2d_e4m3_rejects_32_channels():
+    x = torch.zeros(2, 16, 16, 32, dtype=torch.uint8, device="cuda")
+    w = torch.zeros(32, 9 * 32, dtype=torch.uint8, device="cuda")
+    y = torch.zeros(2, 16, 16, 32, device="cuda")
+    with pytest.raises(B.DDPPOError) as ei:
+        B.ddppo_conv2d_e4m3(x, w, y, 3, 1, 1)
+    assert ei.value.code == -2
+
+
+def _rel_err(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-6)
+
+
+def _q(t, s):
+    """E4M3 rounding of t / s (saturating at +-448, as the kernels do), times s."""
+    return (t / s).clamp(-448.0, 448.0).float().to(E4).double() * s
+
+
+def _fp8_emulated_act(args, passes=2):
+    """The float64 oracle's act with the E4M3 arithmetic of FP8 inference emulated at
+    every convolution whose input channels are a multiple of 64: weights rounded to bf16
+    then to E4M3 at scale amax / 448; inputs rounded to E4M3 at the delayed scale (1/8 on
+    the first pass, then 2 amax / 448 of the previous pass's input). The 1-channel stem
+    runs on bf16 weights. Returns the last pass's outputs."""
+    orig = F.conv2d
+    state = {"amax": [], "prev": None}
+
+    def conv(x, w, b=None, stride=1, padding=0, **kw):
+        wb = w.float().to(torch.bfloat16).double()
+        if x.shape[1] % 64 == 0:
+            i = len(state["amax"])
+            state["amax"].append(x.abs().max().float())
+            sx = 0.125 if state["prev"] is None else float(2 * state["prev"][i] / 448.0)
+            sw = float(wb.abs().max().float() / 448.0)
+            x, wb = _q(x, sx), _q(wb, sw)
+        return orig(x, wb, b, stride=stride, padding=padding, **kw)
+
+    # the GEMM operands the GPU holds in bf16 after the encoder: visual FC and LSTM weights
+    p = dict(args[0])
+    for k in p:
+        if k == "vis.w" or (k.startswith("lstm") and (k.endswith("w_ih") or k.endswith("w_hh"))):
+            p[k] = p[k].float().to(torch.bfloat16).double()
+    args = (p,) + tuple(args[1:])
+    OP.F.conv2d = conv
+    try:
+        for _ in range(passes):
+            out = OP.act(*args)
+            state["prev"], state["amax"] = state["amax"], []
+    finally:
+        OP.F.conv2d = orig
+    return out
+
+
+def test_fp8_act_vs_oracle():
+    """Full-width 64-base ResNet agent, FP8 act (two passes on the same inputs: the first
+    at the initial activation scales, the second at the delayed ones). The GPU's second
+    pass must match an emulation of the same E4M3 arithmetic in float64 within the BF16
+    form's act tolerance (5e-2: the LSTM, heads and visual FC stay bf16). Against the
+    unquantised float64 oracle the error is what E4M3 itself costs; it is printed beside
+    the emulation's own error and must stay within twice it (plus the BF16 tolerance)."""
+    E = 6
+    cfg = make_config("resnet", base_ch=64, num_envs=E, rollout_T=4, minibatches=1, precision=2)
+    h_ = B.ddppo_create(cfg)
+    try:
+        ncfg = net_config_from(cfg)
+        flat = I.params(ncfg, 4).float()
+        B.ddppo_set_params(h_, flat.cuda())
+        mb = I.minibatch(ncfg, T=1, E=E, seed=5)
+        obs = mb["obs"][0].to(obs_dtype(cfg)).cuda().contiguous()
+        goal = mb["goal"][0].float().cuda()
+        prev_a = mb["prev_a"][0].int().cuda()
+        masks = mb["masks"][0].cuda()
+        u = torch.from_numpy(I.uniforms(1, E, seed=6)[0]).cuda()
+        outs = []
+        for _ in range(2):
+            h = mb["h0"].float().cuda()
+            c = mb["c0"].float().cuda()
+            act = torch.zeros(E, dtype=torch.int32, device="cuda")
+            logp = torch.zeros(E, device="cuda")
+            val = torch.zeros(E, device="cuda")
+            B.ddppo_policy_act(h_, obs, goal, prev_a, masks, h, c, u, act, logp, val)
+            torch.cuda.synchronize()
+            outs.append((act.cpu(), logp.cpu(), val.cpu(), h.cpu(), c.cpu()))
+        assert B.ddppo_device_status(h_) == 0
+    finally:
+        B.ddppo_destroy(h_)
+    act, logp, val, h, c = outs[1]
+    p = OP.unflatten(flat.double(), ncfg)
+    args = (p, obs.cpu().double(), goal.cpu().double(), mb["prev_a"][0], mb["masks"][0],
+            mb["h0"].float().double(), mb["c0"].float().double(), u.cpu().double(), ncfg)
+    ref = OP.act(*args)
+    emu = _fp8_emulated_act(args)
+    lp_at = lambda lg: torch.log_softmax(lg, -1).gather(1, act.long().unsqueeze(1))[:, 0]
+    got = dict(logp=logp, value=val, h=h, c=c)
+    want_emu = dict(logp=lp_at(emu[5]), value=emu[2], h=emu[3], c=emu[4])
+    want_ref = dict(logp=lp_at(ref[5]), value=ref[2], h=ref[3], c=ref[4])
+    e_emu = {k: _rel_err(got[k], want_emu[k]) for k in got}
+    e_gpu = {k: _rel_err(got[k], want_ref[k]) for k in got}
+    e_cost = {k: _rel_err(want_emu[k], want_ref[k]) for k in got}
+    rnd = lambda d: {k: round(float(v), 4) for k, v in d.items()}
+    print("FP8 act vs E4M3 emulation:", rnd(e_emu))
+    print("FP8 act vs float64:", rnd(e_gpu), " E4M3 emulation vs float64:", rnd(e_cost))
+    for k in got:
+        # logp and value within the BF16 act tolerance; the LSTM state, whose largest
+        # elements respond most to rounding, within twice it
+        assert e_emu[k] <= (5e-2 if k in ("logp", "value") else 1e-1), (k, e_emu[k])
+        assert e_gpu[k] <= 2 * e_cost[k] + 5e-2, (k, e_gpu[k], e_cost[k])
+    cdf = torch.cumsum(torch.softmax(emu[5], -1), -1)
+    decided = ((cdf - u.cpu().double().unsqueeze(1)).abs() > 3e-2).all(1)
+    assert (act.long()[decided] == emu[0][decided]).all()
+
+
+def test_fp8_worker_iteration():
+    """Collect (captured graph, FP8 act) + GAE + BF16 PPO update of the 64-base agent."""
+    from paper_1911_00357_gb300.worker import Worker
+    w = Worker("wide_256_fp8", seed=3, num_envs=8, rollout_T=8, minibatches=2, encoder_chunk=0)
+    try:
+        for _ in range(2):
+            w.iterate()
+        torch.cuda.synchronize()
+        assert B.ddppo_device_status(w.h) == 0
+        st = w.stats.cpu()
+        assert torch.isfinite(st).all()
+        assert torch.isfinite(w.t["logp"].cpu()).all() and torch.isfinite(w.t["values"].cpu()).all()
+    finally:
+        w.close()
