@@ -14,6 +14,8 @@ Encoders:
   kind 1 ("resnet18"): ResNet-18 BasicBlocks with base width c (c, 2c, 4c, 8c), stem
      7x7/2 + maxpool 3x3/2, GroupNorm (C/2 groups) in place of BatchNorm (App. "Visual
      Encoder"), then a 3x3 conv to 128 channels + GroupNorm + ReLU (128x4x4 = 2048-d).
+  kind 2 ("blind"): no visual input at all, the agent trained with only the GPS+Compass
+     sensor (Sec. 5): the LSTM input is [goal FC, action embedding].
 The 2x2 average pool of App. "Visual Encoder" is applied when the observation is
 produced (``oracle.sim.pool_obs``), so the encoder input is already [1, 128, 128].
 
@@ -34,7 +36,7 @@ NUM_ACTIONS = 4
 
 @dataclasses.dataclass
 class NetConfig:
-    net_kind: int = 0          # 0 nature, 1 resnet18
+    net_kind: int = 0          # 0 nature, 1 resnet18, 2 blind
     base_ch: int = 32
     hidden: int = 128
     lstm_layers: int = 1
@@ -62,6 +64,8 @@ def _conv_out(n, k, s, p):
 
 
 def feature_dim(cfg: NetConfig) -> int:
+    if cfg.net_kind == 2:
+        return 0
     if cfg.net_kind == 0:
         h = _conv_out(_conv_out(_conv_out(cfg.in_h, 8, 4, 0), 4, 2, 0), 3, 1, 0)
         w = _conv_out(_conv_out(_conv_out(cfg.in_w, 8, 4, 0), 4, 2, 0), 3, 1, 0)
@@ -79,7 +83,7 @@ def param_spec(cfg: NetConfig) -> list[tuple[str, tuple[int, ...]]]:
     if cfg.net_kind == 0:
         spec += [("c1.w", (32, 1, 8, 8)), ("c1.b", (32,)), ("c2.w", (64, 32, 4, 4)),
                  ("c2.b", (64,)), ("c3.w", (32, 64, 3, 3)), ("c3.b", (32,))]
-    else:
+    elif cfg.net_kind == 1:
         c = cfg.base_ch
         spec += [("stem.w", (c, 1, 7, 7)), ("stem.g", (c,)), ("stem.b", (c,))]
         for i, (cin, cout, s) in enumerate(_resnet_blocks(c)):
@@ -89,11 +93,13 @@ def param_spec(cfg: NetConfig) -> list[tuple[str, tuple[int, ...]]]:
                 spec += [(f"b{i}.d.w", (cout, cin, 1, 1)), (f"b{i}.nd.g", (cout,)), (f"b{i}.nd.b", (cout,))]
         spec += [("cmp.w", (128, 8 * c, 3, 3)), ("cmp.g", (128,)), ("cmp.b", (128,))]
     Hd = cfg.hidden
-    spec += [("vis.w", (Hd, feature_dim(cfg))), ("vis.b", (Hd,)),
-             ("goal.w", (cfg.goal_dim, 3)), ("goal.b", (cfg.goal_dim,)),
+    if cfg.net_kind != 2:
+        spec += [("vis.w", (Hd, feature_dim(cfg))), ("vis.b", (Hd,))]
+    spec += [("goal.w", (cfg.goal_dim, 3)), ("goal.b", (cfg.goal_dim,)),
              ("act.emb", (NUM_ACTIONS + 1, cfg.act_dim))]
+    vis = 0 if cfg.net_kind == 2 else Hd
     for l in range(cfg.lstm_layers):
-        In = Hd + cfg.goal_dim + cfg.act_dim if l == 0 else Hd
+        In = vis + cfg.goal_dim + cfg.act_dim if l == 0 else Hd
         spec += [(f"lstm{l}.w_ih", (4 * Hd, In)), (f"lstm{l}.w_hh", (4 * Hd, Hd)),
                  (f"lstm{l}.b_ih", (4 * Hd,)), (f"lstm{l}.b_hh", (4 * Hd,))]
     spec += [("actor.w", (NUM_ACTIONS, Hd)), ("actor.b", (NUM_ACTIONS,)),
@@ -166,9 +172,11 @@ def lstm_cell(x, h, c, w_ih, w_hh, b_ih, b_hh):
 
 def policy_inputs(p, obs, goal, prev_a, cfg):
     """Concatenated LSTM input for a batch of N frames."""
-    v = F.relu(encoder(p, obs, cfg) @ p["vis.w"].T + p["vis.b"])
     gvec = goal @ p["goal.w"].T + p["goal.b"]
     avec = p["act.emb"][prev_a.long()]
+    if cfg.net_kind == 2:
+        return torch.cat([gvec, avec], dim=1)
+    v = F.relu(encoder(p, obs, cfg) @ p["vis.w"].T + p["vis.b"])
     return torch.cat([v, gvec, avec], dim=1)
 
 

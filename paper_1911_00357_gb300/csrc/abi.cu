@@ -58,7 +58,7 @@ static int validate(const ddppo_config* c) {
   CFG_CHECK(c->pool2x2 == 0 || c->pool2x2 == 1, "pool2x2 must be 0 or 1");
   CFG_CHECK(c->max_depth_m > 0.f && c->ceil_h_m > c->cam_h_m && c->cam_h_m > 0.f,
             "camera must sit between floor and ceiling");
-  CFG_CHECK(c->net_kind == 0 || c->net_kind == 1, "net_kind must be 0 or 1");
+  CFG_CHECK(c->net_kind >= 0 && c->net_kind <= 2, "net_kind must be 0 (3-layer conv), 1 (ResNet) or 2 (blind)");
   CFG_CHECK(c->precision >= 0 && c->precision <= 2,
             "precision must be 0 (fp32), 1 (bf16) or 2 (fp8 inference, bf16 training)");
   CFG_CHECK(c->precision != 2 || (c->net_kind == 1 && c->base_ch % 64 == 0),
@@ -66,7 +66,7 @@ static int validate(const ddppo_config* c) {
   CFG_CHECK(c->lstm_layers >= 1 && c->lstm_layers <= 4, "lstm_layers must be in [1, 4]");
   CFG_CHECK(c->hidden >= 8 && c->hidden % 8 == 0 && c->hidden <= 2048,
             "hidden must be a multiple of 8 in [8, 2048]");
-  CFG_CHECK(c->net_kind == 0 || (c->base_ch >= 4 && c->base_ch % 4 == 0 && c->base_ch <= 128),
+  CFG_CHECK(c->net_kind != 1 || (c->base_ch >= 4 && c->base_ch % 4 == 0 && c->base_ch <= 128),
             "base_ch must be a multiple of 4 in [4, 128]");
   CFG_CHECK(c->rollout_T >= 1 && c->rollout_T <= 4096, "rollout_T must be in [1, 4096]");
   CFG_CHECK(c->minibatches >= 1 && c->num_envs % c->minibatches == 0,

@@ -81,6 +81,10 @@ static int build_layout(Net& n, Layout& lay) {
     for (auto& cv : n.nat) n.convs.push_back(&cv);
     n.featC = 32;
     n.featHW = n.nat[2].Ho * n.nat[2].Wo;
+  } else if (n.kind == 2) {
+    // blind agent (GPS+Compass only, Sec. 5): no visual encoder, no visual FC
+    n.featC = 0;
+    n.featHW = 0;
   } else {
     const int b = c.base_ch;
     set_conv(n.stem, 1, b, 7, 2, 3, false, n.inh, n.inw, lay);
@@ -116,13 +120,19 @@ static int build_layout(Net& n, Layout& lay) {
   }
   n.F = n.featC * n.featHW;
   const int Hd = n.H;
-  n.vis_w = lay.add((int64_t)Hd * n.F);
-  n.vis_b = lay.add(Hd);
+  if (n.F > 0) {
+    n.vis_w = lay.add((int64_t)Hd * n.F);
+    n.vis_b = lay.add(Hd);
+  }
   n.goal_w = lay.add(32 * 3);
   n.goal_b = lay.add(32);
   n.emb = lay.add(5 * 32);
-  n.In0 = Hd + 64;
-  n.InMax = n.In0;
+  // LSTM input [visual FC (H, when there is an encoder) | goal FC (32) | embedding (32)]
+  n.emb_col0 = n.F > 0 ? Hd : 0;
+  n.In0 = n.emb_col0 + 64;
+  // widest LSTM input (its gradient buffers): layer 0's, or H above it (the blind agent's
+  // first layer is narrower than the others)
+  n.InMax = std::max(n.In0, Hd);
   for (int l = 0; l < n.L; ++l) {
     LstmL& s = n.lstm[l];
     s.In = l == 0 ? n.In0 : Hd;
@@ -203,7 +213,7 @@ static int alloc_encoder(Net& n) {
   };
   if (n.kind == 0) {
     for (auto& c : n.nat) DDPPO_TRY(conv_bufs(c));
-  } else {
+  } else if (n.kind == 1) {
     DDPPO_TRY(conv_bufs(n.stem));
     // the stem's full-resolution activation is only stored when its pool is not fused
     DDPPO_TRY(gn_bufs(n.stem_n, n.stem.Ho * n.stem.Wo, n.stem.cout % 4 != 0));
@@ -270,7 +280,7 @@ static int init_params(Net& n, cudaStream_t s) {
   };
   if (n.kind == 0) {
     for (auto& c : n.nat) DDPPO_TRY(conv_init(c));
-  } else {
+  } else if (n.kind == 1) {
     DDPPO_TRY(conv_init(n.stem));
     DDPPO_TRY(gn_init(n.stem_n));
     for (auto& B : n.blocks) {
@@ -282,8 +292,10 @@ static int init_params(Net& n, cudaStream_t s) {
     DDPPO_TRY(gn_init(n.cmp_n));
   }
   const int Hd = n.H;
-  DDPPO_TRY(unif(n.vis_w, (int64_t)Hd * n.F, sqrtf(6.0f / n.F)));
-  DDPPO_TRY(launch_fill(n.params + n.vis_b, Hd, 0.f, s));
+  if (n.F > 0) {
+    DDPPO_TRY(unif(n.vis_w, (int64_t)Hd * n.F, sqrtf(6.0f / n.F)));
+    DDPPO_TRY(launch_fill(n.params + n.vis_b, Hd, 0.f, s));
+  }
   DDPPO_TRY(unif(n.goal_w, 96, sqrtf(3.0f / 3.0f)));
   DDPPO_TRY(launch_fill(n.params + n.goal_b, 32, 0.f, s));
   DDPPO_TRY(unif(n.emb, 160, sqrtf(3.0f)));
@@ -321,7 +333,8 @@ int net_prep_weights(Net& n, cudaStream_t s) {
       DDPPO_TRY(launch_quant_e4m3(c->wg, true, cnt, c->w8_amax, c->w8_scale, c->wg8, s));
     }
   }
-  DDPPO_TRY(launch_vis_w_prep(n.params + n.vis_w, n.H, n.featC, n.featHW, n.Wv, n.WvT, n.bf, s));
+  if (n.F > 0)
+    DDPPO_TRY(launch_vis_w_prep(n.params + n.vis_w, n.H, n.featC, n.featHW, n.Wv, n.WvT, n.bf, s));
   for (int l = 0; l < n.L; ++l) {
     LstmL& q = n.lstm[l];
     const int G4 = 4 * n.H;
@@ -749,21 +762,23 @@ int net_forward(Net& n, int T, int E, const void* obs, const float* goal, const 
     set_error("forward: segment larger than the workspace");
     return DDPPO_E_CONFIG;
   }
-  const int nch = (N + n.NC - 1) / n.NC;
-  for (int c = 0; c < nch; ++c) {
-    const int r0 = c * n.NC, rn = std::min(n.NC, N - r0);
-    DDPPO_TRY(encoder_fwd(n, opoff(n, obs, (size_t)r0 * n.pix), rn,
-                          opoff(n, n.featop, (size_t)r0 * n.F), s, infer && n.f8 && rn <= n.E));
+  if (n.F > 0) {
+    const int nch = (N + n.NC - 1) / n.NC;
+    for (int c = 0; c < nch; ++c) {
+      const int r0 = c * n.NC, rn = std::min(n.NC, N - r0);
+      DDPPO_TRY(encoder_fwd(n, opoff(n, obs, (size_t)r0 * n.pix), rn,
+                            opoff(n, n.featop, (size_t)r0 * n.F), s, infer && n.f8 && rn <= n.E));
+    }
+    n.ev_valid_chunk = nch - 1;
+    GemmDesc v;
+    v.M = N; v.N = Hd; v.K = n.F;
+    v.A = n.featop; v.lda = n.F; v.B = n.Wv; v.ldb = n.F;
+    v.C = n.x1; v.ldc = n.In0; v.c_bf16 = n.bf ? 1 : 0;
+    v.bias = n.params + n.vis_b; v.relu = 1;
+    DDPPO_TRY(G(n, v, s));
   }
-  n.ev_valid_chunk = nch - 1;
-  GemmDesc v;
-  v.M = N; v.N = Hd; v.K = n.F;
-  v.A = n.featop; v.lda = n.F; v.B = n.Wv; v.ldb = n.F;
-  v.C = n.x1; v.ldc = n.In0; v.c_bf16 = n.bf ? 1 : 0;
-  v.bias = n.params + n.vis_b; v.relu = 1;
-  DDPPO_TRY(G(n, v, s));
   DDPPO_TRY(launch_embed_fwd(N, goal, prev_a, n.params + n.goal_w, n.params + n.goal_b,
-                             n.params + n.emb, n.x1, n.In0, Hd, n.bf, s));
+                             n.params + n.emb, n.x1, n.In0, n.emb_col0, n.bf, s));
   for (int l = 0; l < n.L; ++l) {
     LstmL& q = n.lstm[l];
     GemmDesc gx;
@@ -871,9 +886,11 @@ int net_backward(Net& n, const float* dlogits, const float* dvalues, cudaStream_
     dabove = dX;
   }
   // concatenated LSTM input: [visual FC (H) | goal FC (32) | action embedding (32)]
+  DDPPO_TRY(launch_embed_bwd(N, n.ev_goal, n.ev_preva, dabove, n.In0, n.emb_col0,
+                             n.grad + n.goal_w, n.grad + n.goal_b, n.grad + n.emb, n.scratch,
+                             n.scratch_elems, s));
+  if (n.F == 0) return DDPPO_OK;  // blind agent: nothing below the LSTM input
   DDPPO_TRY(launch_vis_relu_bwd(N, Hd, dabove, n.In0, n.x1, n.In0, n.bf, n.dv32, n.dvop, s));
-  DDPPO_TRY(launch_embed_bwd(N, n.ev_goal, n.ev_preva, dabove, n.In0, Hd, n.grad + n.goal_w,
-                             n.grad + n.goal_b, n.grad + n.emb, n.scratch, n.scratch_elems, s));
   DDPPO_TRY(launch_colsum(n.dv32, N, Hd, Hd, n.grad + n.vis_b, false, s));
   GemmDesc wv;  // dWv[h, f] = sum_n dv[n, h] feat[n, f]
   wv.M = Hd; wv.N = n.F; wv.K = N;

@@ -80,6 +80,7 @@ struct Net {
   int F = 0, featC = 0, featHW = 0;
   int E = 0, T = 0, Emb = 0, NS = 0, NC = 0;
   int In0 = 0, InMax = 0;
+  int emb_col0 = 0;  // column of the goal FC in the LSTM input (after the visual FC, if any)
   size_t pix = 0;  // encoder input elements per image
   int64_t P = 0;
   float* params = nullptr;

@@ -9,6 +9,8 @@
   wide_256    : 256 envs, 64-base encoder, depth 256x256 pooled.
   wide_256_fp8: wide_256 with FP8 (E4M3, per-tensor scales) inference and BF16 training.
   scale_4096  : 4096 envs x T=128, 4 minibatches.
+  blind       : the resnet workload's worlds with the blind agent (GPS+Compass only, no
+                visual encoder; Sec. 5).
 """
 from __future__ import annotations
 
@@ -35,6 +37,9 @@ PRESETS = {
                          depth_h=256, depth_w=256, pool2x2=1, net_kind=1, base_ch=64, hidden=512,
                          lstm_layers=2, rollout_T=128, minibatches=2, precision=2,
                          encoder_chunk=4096),
+    "blind": dict(num_envs=64, gen_kind=1, grid_min=128, grid_max=128, cell_m=0.1, depth_h=256,
+                  depth_w=256, pool2x2=1, net_kind=2, hidden=512, lstm_layers=2, rollout_T=128,
+                  minibatches=2, precision=1),
     "scale_4096": dict(num_envs=4096, gen_kind=1, grid_min=128, grid_max=128, cell_m=0.1,
                        depth_h=256, depth_w=256, pool2x2=1, net_kind=1, base_ch=32, hidden=512,
                        lstm_layers=2, rollout_T=128, minibatches=4, precision=1),

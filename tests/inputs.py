@@ -24,6 +24,7 @@ NETS = {
     "resnet_b64": dict(net_kind=1, base_ch=64, hidden=512, lstm_layers=2, in_h=128, in_w=128),
     "tiny": dict(net_kind=0, base_ch=32, hidden=8, lstm_layers=2, in_h=36, in_w=36),
     "tiny_resnet": dict(net_kind=1, base_ch=8, hidden=16, lstm_layers=2, in_h=32, in_w=32),
+    "tiny_blind": dict(net_kind=2, base_ch=32, hidden=16, lstm_layers=2, in_h=32, in_w=32),
 }
 
 

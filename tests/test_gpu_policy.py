@@ -36,6 +36,9 @@ NETS = {
                          depth_w=128, pool2x2=0),
     "nature_full": dict(preset="nature_fp32"),
     "resnet_full": dict(preset="resnet"),
+    # the blind agent (GPS+Compass only): no encoder, no visual FC
+    "blind_small": dict(preset="nature_fp32", net_kind=2, hidden=16, lstm_layers=2),
+    "blind_full": dict(preset="resnet", net_kind=2),
 }
 
 
@@ -96,7 +99,8 @@ def _rel_close(a, b, rtol, name=""):
 
 @pytest.mark.parametrize("name,T,E,chunk", [("nature_small", 5, 3, 0), ("resnet_small", 4, 5, 0),
                                             ("nature_full", 3, 4, 0), ("resnet_full", 2, 3, 0),
-                                            ("resnet_small", 4, 5, 6), ("nature_small", 5, 3, 4)])
+                                            ("resnet_small", 4, 5, 6), ("nature_small", 5, 3, 4),
+                                            ("blind_small", 5, 3, 0), ("blind_full", 4, 6, 0)])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_evaluate_and_backward_parity(name, T, E, chunk, precision):
     """chunk > 0 runs the encoder in chunks of that many frames (ragged last chunk); the
@@ -149,16 +153,18 @@ def test_evaluate_and_backward_parity(name, T, E, chunk, precision):
         else:
             tol_enc, tol_med = (0.8, 0.45) if resnet else (0.1, 1.0)
             tol_rest = 0.25
-        worst = max(enc, key=enc.get)
-        assert enc[worst] <= tol_enc, "%s: relative L2 error %.3g > %.3g" % (worst, enc[worst], tol_enc)
-        assert np.median(list(enc.values())) <= tol_med
+        if enc:  # the blind agent has no encoder
+            worst = max(enc, key=enc.get)
+            assert enc[worst] <= tol_enc, "%s: relative L2 error %.3g > %.3g" % (worst, enc[worst], tol_enc)
+            assert np.median(list(enc.values())) <= tol_med
         worst = max(rest, key=rest.get)
         assert rest[worst] <= tol_rest, "%s: relative L2 error %.3g > %.3g" % (worst, rest[worst], tol_rest)
     finally:
         net.close()
 
 
-@pytest.mark.parametrize("name,E", [("nature_small", 7), ("resnet_full", 6)])
+@pytest.mark.parametrize("name,E", [("nature_small", 7), ("resnet_full", 6), ("blind_small", 7),
+                                    ("blind_full", 6)])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_act_parity(name, E, precision):
     cfg = _cfg(name, E, 4, precision)
