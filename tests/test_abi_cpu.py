@@ -41,6 +41,12 @@ def test_bad_configs_are_rejected_before_cuda():
         with pytest.raises(B.DDPPOError) as ei:
             B.ddppo_create(make_config("nature_fp32", **kw))
         assert ei.value.code == -2, kw
+    # FP8 inference needs the ResNet encoder at a base width that is a multiple of 64
+    for name, kw in [("resnet", dict(precision=2)), ("resnet", dict(precision=3)),
+                     ("blind", dict(precision=2)), ("resnet", dict(net_kind=3))]:
+        with pytest.raises(B.DDPPOError) as ei:
+            B.ddppo_create(make_config(name, **kw))
+        assert ei.value.code == -2, (name, kw)
 
 
 def test_null_arguments_are_rejected():
