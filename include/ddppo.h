@@ -74,7 +74,8 @@ typedef struct {
   float ceil_h_m;         /* ceiling height (2.5 m)                                          */
   float max_depth_m;      /* depth clip and normaliser (10 m)                                */
   /* agent network (App. "Agent Design") */
-  int32_t net_kind;       /* 0: 3-layer conv 32/64/32 (8/4/3); 1: ResNet-18-style + GN      */
+  int32_t net_kind;       /* 0: 3-layer conv 32/64/32 (8/4/3); 1: ResNet-18-style + GN;
+                             2: blind (GPS+Compass only, Sec. 5): no visual encoder or FC */
   int32_t base_ch;        /* ResNet base width (32 or 64)                                    */
   int32_t hidden;         /* LSTM hidden size and visual FC width (128 or 512)               */
   int32_t lstm_layers;    /* 1 or 2                                                          */
@@ -160,10 +161,11 @@ int ddppo_device_status(ddppo_ctx* ctx, int32_t* code_out, void* stream);
  *               (widths c,c,2c,2c,4c,4c,8c,8c; first of each width > c has stride 2):
  *               c1.w n1.g n1.b c2.w n2.g n2.b [d.w (1x1) nd.g nd.b if it changes shape];
  *               cmp.w [128,8c,3,3] cmp.g [128] cmp.b [128]
- *   then vis.w [H, F] vis.b [H] (F = flattened encoder output, C-major order),
- *   goal.w [32,3] goal.b [32], act.emb [5,32],
+ *   net_kind 2: nothing (no encoder)
+ *   then, except for net_kind 2, vis.w [H, F] vis.b [H] (F = flattened encoder output,
+ *   C-major order); then goal.w [32,3] goal.b [32], act.emb [5,32],
  *   per LSTM layer l: w_ih [4H, In_l] w_hh [4H, H] b_ih [4H] b_hh [4H]
- *               (In_0 = H + 64, In_l = H; gate order i, f, g, o),
+ *               (In_0 = H + 64, or 64 for net_kind 2; In_l = H; gate order i, f, g, o),
  *   actor.w [4,H] actor.b [4] critic.w [1,H] critic.b [1].
  * n_out: [host]. */
 int ddppo_num_params(const ddppo_ctx* ctx, int64_t* n_out);

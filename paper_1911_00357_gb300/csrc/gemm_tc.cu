@@ -1,4 +1,5 @@
-// BF16 GEMM on the 5th-generation tensor cores (sm_103a): C[M,N] (+)= A[M,K] B[N,K]^T.
+// BF16 (and E4M3) GEMM on the 5th-generation tensor cores (sm_103a):
+// C[M,N] (+)= A[M,K] B[N,K]^T.
 //
 //   * TMA (cp.async.bulk.tensor.2d) stages 128x64 A tiles and BNx64 B tiles into shared
 //     memory in the 128-byte swizzled K-major layout; out-of-range rows/columns are
@@ -6,7 +7,11 @@
 //   * A 4-stage ring of mbarriers: "full" (TMA -> MMA, transaction bytes) and "empty"
 //     (MMA -> TMA, signalled by tcgen05.commit when the MMAs reading a stage retire).
 //   * One thread issues tcgen05.mma.cta_group::1.kind::f16 (M=128, N=BN, K=16 per
-//     instruction) accumulating in fp32 in tensor memory (BN columns of TMEM).
+//     instruction) accumulating in fp32 in tensor memory (BN columns of TMEM); E4M3
+//     operands use kind::f8f6f4 (K=32) on the same byte layouts, with the two per-tensor
+//     scales applied in the epilogue.
+//   * Convolutions gather their operand tiles themselves: a 4-D TMA box per filter tap,
+//     or one halo box per tile read through row-shifted descriptors.
 //   * Epilogue: 4 warps each read their 32 TMEM lanes (rows) with tcgen05.ld.32x32b and
 //     apply beta/bias/ReLU, storing fp32 or bf16 -- or fp32 split-K partials that a
 //     fixed-order reduction combines.
