@@ -98,6 +98,8 @@ def lib():
         L.orc_batch_reset.argtypes = [P, ctypes.c_int, P, P, P]
         L.orc_batch_step.argtypes = [P, ctypes.c_int, P, P, P, P, P, P, P, P]
         L.orc_batch_render.argtypes = [P, ctypes.c_int, P, P, P, P]
+        L.orc_flee_rewards.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P, P]
+        L.orc_explore_rewards.argtypes = [P, ctypes.c_int, P]
     return _lib
 
 
@@ -170,6 +172,29 @@ def render_depth(cfg: SimConfig, grid: np.ndarray, state: np.ndarray) -> np.ndar
     assert grid.shape == (st[S_GRID], st[S_GRID])
     out = np.zeros((cfg.depth_h, cfg.depth_w), np.float64)
     lib().orc_render_depth(ctypes.byref(c), _p(grid), _p(st), _p(out))
+    return out
+
+
+def flee_rewards(grid: np.ndarray, cell_u: int, xy: np.ndarray) -> np.ndarray:
+    """Flee (Sec. 5 "Transfer Learning"): r_t = 5 (D_t - D_t-1), D_t = Geo(s_t, s_0) / Max(s_0).
+    xy int [T+1, 2] positions in u (xy[0] = the start); returns float32 [T]."""
+    grid = np.ascontiguousarray(grid, np.uint8)
+    xy = np.ascontiguousarray(xy, np.int32)
+    T = xy.shape[0] - 1
+    dist = np.zeros(grid.shape, np.int32)
+    out = np.zeros(max(T, 0), np.float32)
+    if lib().orc_flee_rewards(_p(grid), grid.shape[0], cell_u, _p(xy), T, _p(dist), _p(out)) != 0:
+        raise ValueError("start cell is a wall")
+    return out
+
+
+def explore_rewards(xy: np.ndarray) -> np.ndarray:
+    """Exploration (Sec. 5 "Transfer Learning"): r_t = 0.25 (|Visited_t| - |Visited_t-1|) over
+    1 m squares. xy int [T+1, 2] positions in u; returns float32 [T]."""
+    xy = np.ascontiguousarray(xy, np.int32)
+    T = xy.shape[0] - 1
+    out = np.zeros(max(T, 0), np.float32)
+    lib().orc_explore_rewards(_p(xy), T, _p(out))
     return out
 
 

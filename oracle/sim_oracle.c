@@ -326,6 +326,43 @@ int orc_step_env(const orc_cfg* c, int64_t env, uint8_t* grid, int32_t* dist, in
   return 0;
 }
 
+/* ---- transfer tasks (Sec. 5 "Transfer Learning"), as rewards of a trajectory ----
+ * xy: int32 [T+1, 2] agent positions in u, xy[0] the episode's start; rewards: [T].
+ *
+ * Flee: D_t = Geo(s_t, s_0) / Max(s_0), Geo the 4-connected unit-cost BFS distance from
+ * the start cell (the same geodesic as the PointGoal reward, from another source) and
+ * Max(s_0) the largest distance over the cells reachable from it; r_t = 5 (D_t - D_t-1).
+ * In cells the cell size cancels: r_t = 5 (d_t - d_t-1) / Max, two exact integers and
+ * one correctly rounded division (double, then float: innocuous for integers < 2^24).
+ * dist: scratch [g * g]. Returns -1 when the start cell is a wall (or out of memory). */
+int orc_flee_rewards(const uint8_t* grid, int g, int cs, const int32_t* xy, int T,
+                     int32_t* dist, float* rewards) {
+  int sx = xy[0] / cs, sy = xy[1] / cs;
+  if (grid[sy * g + sx]) return -1;
+  if (orc_bfs(grid, g, sx, sy, dist) != 0) return -1;
+  int32_t mx = 0;
+  for (int i = 0; i < g * g; ++i)
+    if (dist[i] > mx) mx = dist[i];
+  for (int t = 1; t <= T; ++t) {
+    int32_t d1 = dist[(xy[2 * t + 1] / cs) * g + xy[2 * t] / cs];
+    int32_t d0 = dist[(xy[2 * t - 1] / cs) * g + xy[2 * t - 2] / cs];
+    rewards[t - 1] = mx > 0 ? (float)((double)(5 * (d1 - d0)) / (double)mx) : 0.0f;
+  }
+  return 0;
+}
+
+/* Exploration: Visited_t = the distinct 1 m squares (floor(p / 10000 u) on each axis) of
+ * positions 0..t, the start included; r_t = 0.25 (|Visited_t| - |Visited_t-1|), exact in
+ * FP32. Brute force over the earlier positions. */
+void orc_explore_rewards(const int32_t* xy, int T, float* rewards) {
+  for (int t = 1; t <= T; ++t) {
+    int qx = xy[2 * t] / 10000, qy = xy[2 * t + 1] / 10000, seen = 0;
+    for (int k = 0; k < t && !seen; ++k)
+      seen = xy[2 * k] / 10000 == qx && xy[2 * k + 1] / 10000 == qy;
+    rewards[t - 1] = seen ? 0.0f : 0.25f;
+  }
+}
+
 /* ---- goal vector [r (m), cos(theta), sin(theta)]: the goal in the agent's
  * egocentric polar frame (App. "Goal encoder"); (r, 1, 0) when r = 0. ---- */
 void orc_goal_vector(const int32_t* st, double* out3) {

@@ -468,3 +468,91 @@ def test_env_permutation_is_permutation():
         p = S.env_permutation(0, 3, 1, E)
         assert sorted(p.tolist()) == list(range(E))
     assert not (S.env_permutation(0, 0, 0, 64) == np.arange(64)).all()
+
+
+# ---------------------------------------------------------------- transfer tasks (Sec. 5)
+def _border_room(g):
+    grid = np.zeros((g, g), np.uint8)
+    grid[0, :] = grid[-1, :] = grid[:, 0] = grid[:, -1] = 1
+    return grid
+
+
+def _walk(x0, y0, steps):
+    """Positions of a walk with axis-aligned unit moves of 2500 u: steps is a list of
+    (dx, dy) in {-1, 0, 1}^2 (0, 0 = a turn: the agent stays)."""
+    xy = [(x0, y0)]
+    for dx, dy in steps:
+        x, y = xy[-1]
+        xy.append((x + 2500 * dx, y + 2500 * dy))
+    return np.array(xy, np.int32)
+
+
+def test_flee_empty_room_closed_form():
+    # 16x16 room (free cells 1..14), 0.25 m cells, start at the centre of cell (3, 5):
+    # Geo = Manhattan distance in cells, Max = (14 - 3) + (14 - 5) = 20, so each cell
+    # walked away from the start earns 5 / 20 = 0.25, each one walked back -0.25, a turn 0.
+    g, cs = 16, 2500
+    grid = _border_room(g)
+    x0, y0 = 3 * cs + cs // 2, 5 * cs + cs // 2
+    steps = [(1, 0)] * 6 + [(0, 0)] * 3 + [(-1, 0)] * 8 + [(0, 1)] * 4
+    r = S.flee_rewards(grid, cs, _walk(x0, y0, steps))
+    want = [0.25] * 6 + [0.0] * 3 + [-0.25] * 6 + [0.25] * 2 + [0.25] * 4
+    assert r.tolist() == want
+    # the rewards telescope: sum = 5 D_T with D_T = (|x_T - 3| + |y_T - 5|) / 20
+    assert abs(float(r.astype(np.float64).sum()) - 5 * (2 + 4) / 20) < 1e-12
+
+
+def test_flee_geodesic_detour_against_networkx():
+    # a wall across the room with one gap: geodesic distances from the start and their
+    # maximum come from networkx's BFS on the free-cell graph
+    nx = pytest.importorskip("networkx")
+    g, cs = 12, 2500
+    grid = _border_room(g)
+    grid[6, 1:10] = 1                      # wall along row 6, gap at column 10
+    start = (2, 3)
+    G = nx.grid_2d_graph(g, g)
+    G.remove_nodes_from([(y, x) for y in range(g) for x in range(g) if grid[y, x]])
+    d = nx.single_source_shortest_path_length(G, (start[1], start[0]))
+    mx = max(d.values())
+    rng = np.random.default_rng(5)
+    cells = [start]
+    for _ in range(60):                    # a random walk over free cells
+        x, y = cells[-1]
+        opts = [(x + a, y + b) for a, b in ((1, 0), (-1, 0), (0, 1), (0, -1)) if not grid[y + b, x + a]]
+        cells.append(opts[rng.integers(len(opts))])
+    xy = np.array([(x * cs + 1250, y * cs + 1250) for x, y in cells], np.int32)
+    r = S.flee_rewards(grid, cs, xy)
+    for t in range(1, len(cells)):
+        dd = d[(cells[t][1], cells[t][0])] - d[(cells[t - 1][1], cells[t - 1][0])]
+        assert r[t - 1] == np.float32(5 * dd / mx)
+    assert mx > 2 * (g - 2)                # the detour is longer than any Manhattan path
+
+
+def test_flee_rejects_a_wall_start():
+    grid = _border_room(8)
+    with pytest.raises(ValueError):
+        S.flee_rewards(grid, 2500, np.array([[1250, 1250], [1250, 1250]], np.int32))
+
+
+def test_exploration_new_square_every_metre():
+    # start at (0.5 m, 0.5 m), heading +x in 0.25 m steps: x = 0.5 + 0.25 k enters the
+    # square of x = 1 m at k = 2, of 2 m at k = 6, of 3 m at k = 10; walking back over
+    # visited squares earns nothing; a step into y = 1 m is a new square again
+    steps = [(1, 0)] * 10 + [(-1, 0)] * 10 + [(0, 1)] * 2
+    r = S.explore_rewards(_walk(5000, 5000, steps))
+    want = np.zeros(22, np.float32)
+    want[[1, 5, 9, 21]] = 0.25
+    assert r.tolist() == want.tolist()
+    assert float(r.sum()) == 0.25 * (4 + 1 - 1)
+
+
+def test_exploration_total_counts_distinct_squares():
+    # over any trajectory the rewards add up to 0.25 (number of distinct squares - 1),
+    # and a trajectory confined to one square earns nothing
+    rng = np.random.default_rng(11)
+    xy = np.cumsum(rng.integers(-2500, 2501, size=(200, 2)), axis=0) + 50000
+    r = S.explore_rewards(xy.astype(np.int32))
+    squares = {(int(x) // 10000, int(y) // 10000) for x, y in xy}
+    assert float(r.astype(np.float64).sum()) == 0.25 * (len(squares) - 1)
+    still = np.tile(np.array([[12345, 61234]], np.int32), (9, 1)) + rng.integers(0, 5000, (9, 2)).astype(np.int32)
+    assert not S.explore_rewards(still).any()
