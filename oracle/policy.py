@@ -16,6 +16,14 @@ Encoders:
      Encoder"), then a 3x3 conv to 128 channels + GroupNorm + ReLU (128x4x4 = 2048-d).
   kind 2 ("blind"): no visual input at all, the agent trained with only the GPS+Compass
      sensor (Sec. 5): the LSTM input is [goal FC, action embedding].
+  kind 3 ("se_resnext"): SE-ResNeXt (App. "Visual Encoder": SE-ResNeXt50/101 with every
+     layer's channels halved, GroupNorm for BatchNorm, 1024x4x4 output). Bottleneck
+     blocks [3, 4, 6, 3] (50) or [3, 4, 23, 3] (101): 1x1 conv to the inner width 2c 2^i,
+     3x3 grouped conv (cardinality groups, stride here), 1x1 conv to 4c 2^i, each with
+     GroupNorm, ReLU after the first two; squeeze-excite on the branch (global mean, FC to
+     C/r + ReLU, FC back + sigmoid, channel scale) before the residual addition; 1x1 conv
+     + GroupNorm shortcut when the shape changes. Stem, max pool and the 3x3 compression
+     conv to 128 channels as in kind 1.
 The 2x2 average pool of App. "Visual Encoder" is applied when the observation is
 produced (``oracle.sim.pool_obs``), so the encoder input is already [1, 128, 128].
 
@@ -45,6 +53,10 @@ class NetConfig:
     goal_dim: int = 32
     act_dim: int = 32
     gn_eps: float = 1e-5
+    # kind 3 only
+    sx_blocks: tuple = (3, 4, 6, 3)   # bottleneck blocks per stage (50 layers)
+    cardinality: int = 32             # groups of the 3x3 convolution
+    se_reduction: int = 16            # squeeze-excite bottleneck ratio
 
 
 def _resnet_blocks(c):
@@ -56,6 +68,19 @@ def _resnet_blocks(c):
             s = 2 if (li > 0 and b == 0) else 1
             out.append((cin, w, s))
             cin = w
+    return out
+
+
+def _sx_blocks(cfg):
+    """(cin, inner, cout, stride) of the SE-ResNeXt bottleneck blocks."""
+    out = []
+    c = cfg.base_ch
+    cin = c
+    for i, n in enumerate(cfg.sx_blocks):
+        for b in range(n):
+            s = 2 if (i > 0 and b == 0) else 1
+            out.append((cin, 2 * c * 2 ** i, 4 * c * 2 ** i, s))
+            cin = 4 * c * 2 ** i
     return out
 
 
@@ -73,7 +98,9 @@ def feature_dim(cfg: NetConfig) -> int:
     h, w = cfg.in_h, cfg.in_w
     h, w = _conv_out(h, 7, 2, 3), _conv_out(w, 7, 2, 3)
     h, w = _conv_out(h, 3, 2, 1), _conv_out(w, 3, 2, 1)
-    for (_, _, s) in _resnet_blocks(cfg.base_ch):
+    strides = [s for (_, _, s) in _resnet_blocks(cfg.base_ch)] if cfg.net_kind == 1 else \
+        [s for (_, _, _, s) in _sx_blocks(cfg)]
+    for s in strides:
         h, w = _conv_out(h, 3, s, 1), _conv_out(w, 3, s, 1)
     return 128 * h * w
 
@@ -92,6 +119,20 @@ def param_spec(cfg: NetConfig) -> list[tuple[str, tuple[int, ...]]]:
             if s != 1 or cin != cout:
                 spec += [(f"b{i}.d.w", (cout, cin, 1, 1)), (f"b{i}.nd.g", (cout,)), (f"b{i}.nd.b", (cout,))]
         spec += [("cmp.w", (128, 8 * c, 3, 3)), ("cmp.g", (128,)), ("cmp.b", (128,))]
+    elif cfg.net_kind == 3:
+        c, G, r = cfg.base_ch, cfg.cardinality, cfg.se_reduction
+        spec += [("stem.w", (c, 1, 7, 7)), ("stem.g", (c,)), ("stem.b", (c,))]
+        for i, (cin, mid, cout, s) in enumerate(_sx_blocks(cfg)):
+            q = f"x{i}."
+            spec += [(q + "c1.w", (mid, cin, 1, 1)), (q + "n1.g", (mid,)), (q + "n1.b", (mid,)),
+                     (q + "c2.w", (mid, mid // G, 3, 3)), (q + "n2.g", (mid,)), (q + "n2.b", (mid,)),
+                     (q + "c3.w", (cout, mid, 1, 1)), (q + "n3.g", (cout,)), (q + "n3.b", (cout,)),
+                     (q + "se1.w", (cout // r, cout)), (q + "se1.b", (cout // r,)),
+                     (q + "se2.w", (cout, cout // r)), (q + "se2.b", (cout,))]
+            if s != 1 or cin != cout:
+                spec += [(q + "d.w", (cout, cin, 1, 1)), (q + "nd.g", (cout,)), (q + "nd.b", (cout,))]
+        last = _sx_blocks(cfg)[-1][2]
+        spec += [("cmp.w", (128, last, 3, 3)), ("cmp.g", (128,)), ("cmp.b", (128,))]
     Hd = cfg.hidden
     if cfg.net_kind != 2:
         spec += [("vis.w", (Hd, feature_dim(cfg))), ("vis.b", (Hd,))]
@@ -145,6 +186,11 @@ def encoder(p: dict, obs: torch.Tensor, cfg: NetConfig) -> torch.Tensor:
     e = cfg.gn_eps
     x = F.relu(_gn(F.conv2d(x, p["stem.w"], stride=2, padding=3), p["stem.g"], p["stem.b"], e))
     x = F.max_pool2d(x, 3, stride=2, padding=1)
+    if cfg.net_kind == 3:
+        for i, (_, _, _, s) in enumerate(_sx_blocks(cfg)):
+            x = sx_block(p, f"x{i}.", x, s, cfg)
+        x = F.relu(_gn(F.conv2d(x, p["cmp.w"], padding=1), p["cmp.g"], p["cmp.b"], e))
+        return x.flatten(1)
     for i, (cin, cout, s) in enumerate(_resnet_blocks(cfg.base_ch)):
         y = F.relu(_gn(F.conv2d(x, p[f"b{i}.c1.w"], stride=s, padding=1), p[f"b{i}.n1.g"], p[f"b{i}.n1.b"], e))
         y = _gn(F.conv2d(y, p[f"b{i}.c2.w"], stride=1, padding=1), p[f"b{i}.n2.g"], p[f"b{i}.n2.b"], e)
@@ -155,6 +201,29 @@ def encoder(p: dict, obs: torch.Tensor, cfg: NetConfig) -> torch.Tensor:
         x = F.relu(y + sc)
     x = F.relu(_gn(F.conv2d(x, p["cmp.w"], padding=1), p["cmp.g"], p["cmp.b"], e))
     return x.flatten(1)
+
+
+def squeeze_excite(p: dict, q: str, y: torch.Tensor) -> torch.Tensor:
+    """y * sigmoid(W2 relu(W1 mean_hw(y) + b1) + b2), per image and channel."""
+    z = y.mean(dim=(2, 3))
+    a = F.relu(z @ p[q + "se1.w"].T + p[q + "se1.b"])
+    w = torch.sigmoid(a @ p[q + "se2.w"].T + p[q + "se2.b"])
+    return y * w[:, :, None, None]
+
+
+def sx_block(p: dict, q: str, x: torch.Tensor, stride: int, cfg: NetConfig) -> torch.Tensor:
+    """One SE-ResNeXt bottleneck block (parameter prefix q)."""
+    e = cfg.gn_eps
+    y = F.relu(_gn(F.conv2d(x, p[q + "c1.w"]), p[q + "n1.g"], p[q + "n1.b"], e))
+    y = F.relu(_gn(F.conv2d(y, p[q + "c2.w"], stride=stride, padding=1, groups=cfg.cardinality),
+                   p[q + "n2.g"], p[q + "n2.b"], e))
+    y = _gn(F.conv2d(y, p[q + "c3.w"]), p[q + "n3.g"], p[q + "n3.b"], e)
+    y = squeeze_excite(p, q, y)
+    if q + "d.w" in p:
+        sc = _gn(F.conv2d(x, p[q + "d.w"], stride=stride), p[q + "nd.g"], p[q + "nd.b"], e)
+    else:
+        sc = x
+    return F.relu(y + sc)
 
 
 def lstm_cell(x, h, c, w_ih, w_hh, b_ih, b_hh):

@@ -25,6 +25,8 @@ NETS = {
     "tiny": dict(net_kind=0, base_ch=32, hidden=8, lstm_layers=2, in_h=36, in_w=36),
     "tiny_resnet": dict(net_kind=1, base_ch=8, hidden=16, lstm_layers=2, in_h=32, in_w=32),
     "tiny_blind": dict(net_kind=2, base_ch=32, hidden=16, lstm_layers=2, in_h=32, in_w=32),
+    "tiny_sx": dict(net_kind=3, base_ch=4, hidden=8, lstm_layers=1, in_h=32, in_w=32,
+                    sx_blocks=(1, 1, 1, 1), cardinality=2, se_reduction=4),
 }
 
 

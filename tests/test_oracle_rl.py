@@ -183,7 +183,7 @@ def _mb(cfg, T, E, seed):
     return I.minibatch(cfg, T=T, E=E, seed=seed)
 
 
-@pytest.mark.parametrize("net", ["tiny", "tiny_resnet", "tiny_blind"])
+@pytest.mark.parametrize("net", ["tiny", "tiny_resnet", "tiny_blind", "tiny_sx"])
 def test_ppo_gradient_matches_central_differences(net):
     cfg = I.net_config(net)
     hp = R.PPOHParams()
