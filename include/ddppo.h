@@ -371,6 +371,20 @@ int ddppo_conv2d_e4m3(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, 
                       const float* scale_x, const float* scale_w, float* y, float beta,
                       int32_t* status, void* stream);
 
+/* The paths and shared-memory staging geometry the tensor-core engine would use for a
+ * bf16 convolution of this shape and for its weight gradient. Host only: no CUDA call, no
+ * device needed. plan [host] int32 [18]:
+ *   [0] 4-D gather forward path usable; [1] halo forward path usable, then [2] anchor pitch
+ *   Wp = W + 2p, [3] padded height Hh, [4] images per 128-anchor tile (0: tiles within one
+ *   image), [5] tiles per image, [6] box rows per image, [7] anchor rows allocated per
+ *   ring stage, [8] anchor rows the box delivers, [9] tiles;
+ *   [10] 4-D gather weight gradient usable; [11] halo weight gradient usable, then [12]
+ *   rows per work unit RB, [13] pitch Wp, [14] input box rows, [15] dz box rows, [16] ring
+ *   depth, [17] shared memory bytes per CTA.
+ * E_ARG for invalid sizes or a null plan. */
+int ddppo_conv_plan(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, int32_t k,
+                    int32_t stride, int32_t pad, int32_t* plan);
+
 /* Whether ddppo_gemm with these operands runs on the tensor cores (1) or SIMT (0). */
 int ddppo_gemm_backend(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const void* A,
                        int32_t lda, const void* B, int32_t ldb, int32_t* tensor_cores);

@@ -116,6 +116,7 @@ _SIGS = {
     "ddppo_conv2d": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, F32, P, P],
     "ddppo_conv2d_wgrad": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, F32, P, P],
     "ddppo_quantize_e4m3": [P, I32, I64, P, P, P],
+    "ddppo_conv_plan": [I32, I32, I32, I32, I32, I32, I32, I32, P],
     "ddppo_gemm_e4m3": [I32, I32, I32, P, I32, P, I32, P, P, P, I32, F32, P, I32, P, P],
     "ddppo_conv2d_e4m3": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, P, P, F32, P, P],
 }
@@ -357,6 +358,15 @@ def ddppo_autotune_export(h) -> bytes:
 def ddppo_autotune_import(h, image: bytes) -> None:
     buf = ctypes.create_string_buffer(bytes(image), len(image))
     _check(lib().ddppo_autotune_import(h, buf, len(image)))
+
+
+def ddppo_conv_plan(N: int, H: int, W: int, C: int, Cout: int, k: int, stride: int,
+                    pad: int) -> list[int]:
+    """Paths and staging geometry of a bf16 convolution and its weight gradient (18 ints;
+    see the header). Host only: works without a GPU."""
+    plan = (ctypes.c_int32 * 18)()
+    _check(lib().ddppo_conv_plan(N, H, W, C, Cout, k, stride, pad, plan))
+    return list(plan)
 
 
 def ddppo_quantize_e4m3(x, q, scale):

@@ -94,6 +94,8 @@ int launch_splitk_reduce(int M, int N, int splits, const float* partial, float* 
 
 // tcgen05 path (gemm_tc.cu); returns DDPPO_E_CONFIG when the shape is not supported
 int gemm_tc(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s);
+// paths and staging geometry of a convolution (18 words; see gemm_tc.cu); host only
+void conv_plan(const ConvShape& c, int32_t* plan);
 bool gemm_tc_supported(const GemmDesc& d);
 // whether the implicit-im2col path covers this convolution (C % 32 == 0, output rows that
 // tile 128-pixel blocks, 16-byte aligned input)

@@ -1360,6 +1360,40 @@ bool conv_wgrad_halo_ok(const ConvShape& c, const void* x, const void* dz) {
   return encode_fn() && !((uintptr_t)x & 15) && !((uintptr_t)dz & 15) && wgrad_halo_geom(c, &g);
 }
 
+// The paths and staging geometry a convolution and its weight gradient take (host only,
+// no CUDA call): plan[0] 4-D gather forward path; plan[1] halo forward path, then its
+// pitch Wp, padded height Hh, images per tile ni (0: tiles within one image), tiles per
+// image tpi, box rows per image rows_box, rows allocated per ring stage, rows the box
+// delivers, tiles; plan[10] 4-D gather weight gradient; plan[11] halo weight gradient,
+// then unit rows RB, pitch Wp, input box rows, dz box rows, ring depth, shared memory
+// bytes. 18 words.
+void conv_plan(const ConvShape& c, int32_t* plan) {
+  for (int i = 0; i < 18; ++i) plan[i] = 0;
+  plan[0] = gather_ok(c) ? 1 : 0;
+  ConvA ca;
+  if (halo_geom(c, &ca)) {
+    const int rb = ca.cbw * 2;
+    plan[1] = 1;
+    plan[2] = ca.Wp; plan[3] = ca.Hh; plan[4] = ca.ni; plan[5] = ca.tpi;
+    plan[6] = ca.rows_box;
+    plan[7] = (int32_t)(ca.halo_bytes / rb);
+    plan[8] = (int32_t)(ca.box_bytes / rb);
+    plan[9] = ca.tiles_m;
+  }
+  int hi = 0, ni = 0;
+  plan[10] = ((c.C == 32 || (c.C > 0 && c.C % 64 == 0)) && c.k >= 1 && c.s >= 1 && c.s <= 8 &&
+              c.N >= 1 && convw_geom(c, &hi, &ni)) ? 1 : 0;
+  WgradHalo g;
+  if (wgrad_halo_geom(c, &g)) {
+    plan[11] = 1;
+    plan[12] = g.RB; plan[13] = g.Wp;
+    plan[14] = (int32_t)(g.x_bytes / (64u * g.Wp));
+    plan[15] = (int32_t)(g.dz_bytes / (64u * g.Wp));
+    plan[16] = g.stages;
+    plan[17] = (int32_t)g.smem;
+  }
+}
+
 int conv_wgrad_halo(const ConvShape& c, const void* x, const void* dz, float* dw, int ldw, float beta,
                     const GemmWorkspace& ws, cudaStream_t s) {
   WgradHalo g;

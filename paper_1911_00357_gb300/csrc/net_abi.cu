@@ -633,6 +633,16 @@ extern "C" int ddppo_conv2d(int32_t N, int32_t H, int32_t W, int32_t C, int32_t 
   return gemm(d, true, ws, (cudaStream_t)stream, nullptr);
 }
 
+extern "C" int ddppo_conv_plan(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout,
+                               int32_t k, int32_t stride, int32_t pad, int32_t* plan) {
+  ConvShape c;
+  DDPPO_TRY(conv_args(N, H, W, C, Cout, k, stride, pad, &c));
+  ARG(plan, "conv_plan: null argument");
+  c.Cout = Cout;
+  conv_plan(c, plan);
+  return DDPPO_OK;
+}
+
 // ---- E4M3 (FP8 inference) contractions and quantisation ----
 extern "C" int ddppo_quantize_e4m3(const void* x, int32_t x_bf16, int64_t n, void* q, float* scale,
                                    void* stream) {
