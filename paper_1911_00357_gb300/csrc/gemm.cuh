@@ -2,8 +2,9 @@
 //   C[M, N] = beta * C + sum_k A(m, k) B(n, k) (+ bias[N]) (ReLU)
 // A(m, k) = A[m * lda + k] (K-contiguous), or A[k * lda + m] when a_t ("MN-major": the
 // weight gradients read activations and output gradients as they are stored, [rows][C]).
-// B likewise with b_t. Operands are of the operand dtype (fp32 or bf16); C is fp32, or
-// bf16 when c_bf16 (then beta must be 0). Accumulation is fp32.
+// B likewise with b_t. Operands are of the operand dtype (fp32 or bf16; E4M3 with the
+// fp8 flag, K-major only); C is fp32, or bf16 when c_bf16 (then beta must be 0).
+// Accumulation is fp32.
 #pragma once
 
 #include "common.cuh"

@@ -1,5 +1,6 @@
 // Launchers of the network's non-GEMM kernels (nn_kernels.cu). Activations are NHWC
-// fp32; "T" buffers are GEMM operands in the precision's dtype (fp32 or bf16).
+// fp32; "T" buffers are GEMM operands in the precision's dtype (fp32 or bf16; FP8
+// inference adds E4M3 copies of the act-time convolution inputs).
 #pragma once
 
 #include "common.cuh"
