@@ -141,6 +141,11 @@ typedef struct {
  * Errors: E_ARG (null), E_CONFIG (unsupported shape), E_CUDA (allocation). */
 int ddppo_create(const ddppo_config* cfg, ddppo_ctx** out);
 
+/* The configuration checks of ddppo_create alone: host only, no CUDA call and no
+ * allocation. DDPPO_OK, or E_CONFIG with ddppo_last_error naming the first violated rule
+ * (E_ARG for a null cfg). */
+int ddppo_config_check(const ddppo_config* cfg);
+
 /* Free everything ddppo_create allocated. Synchronises the device. NULL is a no-op. */
 int ddppo_destroy(ddppo_ctx* ctx);
 

@@ -82,6 +82,7 @@ F32 = ctypes.c_float
 
 _SIGS = {
     "ddppo_create": [P, P],
+    "ddppo_config_check": [P],
     "ddppo_destroy": [P],
     "ddppo_device_status": [P, P, P],
     "ddppo_num_params": [P, P],
@@ -179,6 +180,11 @@ def ddppo_create(cfg: Config):
 
 def ddppo_destroy(h):
     _check(lib().ddppo_destroy(h))
+
+
+def ddppo_config_check(cfg) -> None:
+    """Raise DDPPOError when ddppo_create would reject cfg (host only, no GPU needed)."""
+    _check(lib().ddppo_config_check(ctypes.byref(cfg)))
 
 
 def ddppo_device_status(h) -> int:

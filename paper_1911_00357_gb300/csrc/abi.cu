@@ -125,6 +125,11 @@ void ctx_free_world(ddppo_ctx* x) {
 }
 }  // namespace ddppo
 
+extern "C" int ddppo_config_check(const ddppo_config* cfg) {
+  ARG_CHECK(cfg != nullptr, "ddppo_config_check: null argument");
+  return validate(cfg);
+}
+
 extern "C" int ddppo_create(const ddppo_config* cfg, ddppo_ctx** out) {
   ARG_CHECK(cfg != nullptr && out != nullptr, "ddppo_create: null argument");
   DDPPO_TRY(validate(cfg));

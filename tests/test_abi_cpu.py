@@ -60,6 +60,14 @@ def test_null_arguments_are_rejected():
     assert isinstance(L.ddppo_last_error(), bytes)
 
 
+def test_every_preset_passes_the_configuration_checks():
+    for name in PRESETS:
+        B.ddppo_config_check(make_config(name))
+    with pytest.raises(B.DDPPOError) as ei:
+        B.ddppo_config_check(make_config("wide_256_fp8", base_ch=32))
+    assert ei.value.code == -2 and "fp8" in str(ei.value)
+
+
 def test_presets_pass_validation_shapes():
     for name in PRESETS:
         cfg = make_config(name)
