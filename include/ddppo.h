@@ -141,8 +141,8 @@ typedef struct {
  * Errors: E_ARG (null), E_CONFIG (unsupported shape), E_CUDA (allocation). */
 int ddppo_create(const ddppo_config* cfg, ddppo_ctx** out);
 
-/* The configuration checks of ddppo_create alone: host only, no CUDA call and no
- * allocation. DDPPO_OK, or E_CONFIG with ddppo_last_error naming the first violated rule
+/* The configuration checks of ddppo_create alone (the world, agent and training
+ * settings of Sec. 4): host only, no CUDA call and no allocation. DDPPO_OK, or E_CONFIG with ddppo_last_error naming the first violated rule
  * (E_ARG for a null cfg). */
 int ddppo_config_check(const ddppo_config* cfg);
 
@@ -356,7 +356,8 @@ int ddppo_conv2d(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, int32
 int ddppo_conv2d_wgrad(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, int32_t k,
                        int32_t stride, int32_t pad, const void* x, const void* dy, float* dw,
                        float beta, int32_t* status, void* stream);
-/* E4M3 contractions (FP8 inference, config "Precision" of the paper-shaped workloads).
+/* E4M3 contractions: the encoder convolutions of Sec. 4 "Agent" / App. "Visual Encoder"
+ * at FP8 inference precision (E4M3 operands, per-tensor scales, fp32 accumulation).
  * ddppo_quantize_e4m3: per-tensor quantisation of n values x [dev] (fp32, or bf16 when
  * x_bf16): scale [dev] float = amax(|x|) / 448 (1 when every x is 0); q [dev] uint8 [n] =
  * e4m3(x / scale), rounded to nearest even, saturating at +-448.
@@ -377,7 +378,8 @@ int ddppo_conv2d_e4m3(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, 
                       int32_t* status, void* stream);
 
 /* The paths and shared-memory staging geometry the tensor-core engine would use for a
- * bf16 convolution of this shape and for its weight gradient. Host only: no CUDA call, no
+ * bf16 convolution of this shape (the encoder of Sec. 4 "Agent") and for its weight
+ * gradient. Host only: no CUDA call, no
  * device needed. plan [host] int32 [18]:
  *   [0] 4-D gather forward path usable; [1] halo forward path usable, then [2] anchor pitch
  *   Wp = W + 2p, [3] padded height Hh, [4] images per 128-anchor tile (0: tiles within one
