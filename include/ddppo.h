@@ -289,7 +289,9 @@ int ddppo_ppo_loss(int32_t n, const float* logits, const float* values, const in
  * is needed. n must be at most 1,048,576 (E_CONFIG otherwise). The first call on each
  * device looks up the array's device address; make it before any stream capture. Every
  * call shares the array, so calls that overlap on the GPU race. Each call overwrites the
- * partials it uses; nothing needs clearing between calls. */
+ * partials it uses; nothing needs clearing between calls. The looked-up address is kept
+ * for the life of the process: after a cudaDeviceReset of a device, do not call this
+ * entry point on that device again in the same process. */
 int ddppo_ppo_loss_static(int32_t n, const float* logits, const float* values,
                           const int32_t* actions, const float* logp_old, const float* adv,
                           const float* ret, float clip, float value_coef, float entropy_coef,

@@ -29,6 +29,17 @@ produced (``oracle.sim.pool_obs``), so the encoder input is already [1, 128, 128
 
 The flat parameter vector is the concatenation, in ``param_spec`` order, of each
 tensor in PyTorch's natural layout (conv [Cout, Cin, kh, kw], linear [out, in]).
+
+Pins (tests/test_oracle_rl.py, tests/test_oracle_sx.py, tests/test_oracle_pins_loss.py):
+  conv2d / _gn        loop definitions of convolution and GroupNorm (biased variance, C/2
+                      groups)
+  lstm_cell           torch.nn.LSTM on the same weights (gate order i, f, g, o)
+  feature_dim / encoder  128x4x4 = 2048 at 128x128 (App. "Visual Encoder"); SE-ResNeXt's
+                      1024x4x4 backbone, block counts, closed and open squeeze-excite gates
+  policy_inputs       concatenation order [visual, goal, action] on hand-set weights
+  sequence_forward    masks zero the state before the step (h0 has no effect at mask 0)
+  sample_action       inverse-CDF closed form
+  all of the above, through the PPO loss: central finite differences of the gradient
 """
 from __future__ import annotations
 

@@ -10,6 +10,19 @@ Loss (Eq. 2 plus the value and entropy terms the paper leaves unstated):
 with rho = exp(logpi - logpi_old); advantages are not normalised by default
 (Sec. 4 "Training"); the optional normalisation uses the mean and the
 (population) standard deviation over the whole rollout with eps 1e-5 added.
+
+Pins (independent of the formulas here; a plausible mistake fails the named test):
+  gae                 direct discounted sum at lambda = 1, TD error at lambda = 0, done cuts
+                      (tests/test_oracle_rl.py)
+  ppo_loss            value term alone = 0.5 c_v mean((R - V)^2) with its gradient; entropy
+                      ln 4 at uniform logits and the closed form at one dominant logit, with
+                      its sign; the clipped surrogate, clip fraction and approximate KL on
+                      hand-picked ratios (tests/test_oracle_pins_loss.py)
+  minibatch_loss_and_grad  central finite differences on four nets; -A grad log pi at
+                      theta_old; zero policy gradient when every sample is clipped
+  clip_grad_norm      3-4-5 closed form; below-threshold identity
+  adam_step           first two bias-corrected steps in closed form; a quadratic's minimum
+  ppo_update          one minibatch = one clipped Adam step on the permuted envs
 """
 from __future__ import annotations
 

@@ -3,6 +3,25 @@
 TEST INFRASTRUCTURE ONLY (tests, smoke check, CPU baseline). Each function
 states the passage of arXiv:1911.00357 it follows; the readings taken where
 the paper is silent are listed in the header comment of ``sim_oracle.c``.
+
+Pins (tests/test_oracle_sim.py unless noted):
+  counter_hash / splitmix64  SplitMix64's published outputs for state 0
+  fwd_table           closed forms at 0/30/60/90/180/270 deg, symmetries, length 2500 +- 1
+  gen_scene           border walls, Bernoulli density within 4 sigma, density 0 and 1,
+                      rooms connected with one-cell walls
+  bfs                 scipy Dijkstra, Floyd-Warshall on small grids, Manhattan on an empty grid
+  segment_blocked     exact rational Liang-Barsky clipping (Python fractions)
+  BatchSim.step       the hand-worked episode tests/golden/walk_9x9.txt (both terminal modes),
+                      SPL special cases, timeouts, motion invariants
+  render_depth / column_twall  empty-room closed forms (walls, floor, ceiling), a single
+                      wall cell, the clip at max_depth
+  goal_vector         3-4-5 triangle at two headings
+  flee_rewards / explore_rewards  empty-room closed forms, a networkx BFS around a wall
+                      gap, a straight walk's new squares
+  env_permutation     is a permutation; uniform over the 3! orders (chi-square,
+                      tests/test_oracle_pins_loss.py)
+  pool_obs            constant image, checkerboard, non-square ramp, odd values
+                      (tests/test_oracle_pins_loss.py)
 """
 from __future__ import annotations
 

@@ -14,7 +14,9 @@
 // current) and caches it; make that first call before any stream capture. All calls
 // share the array: calls that overlap on the GPU (different streams, or concurrent host
 // threads) race on it. Each call overwrites the partials it reads, so nothing has to be
-// cleared between calls.
+// cleared between calls. The cached address outlives a cudaDeviceReset, which makes it
+// stale: after a device reset, this entry point must not be called on that device again
+// in the same process.
 #include <mutex>
 
 #include "rl.cuh"

@@ -43,7 +43,9 @@ def _close(a, b, rtol=1e-5):
 
 
 def test_static_loss_matches_ppo_loss_two_calls_in_a_row():
-    for n, seed in ((300_001, 1), (4097, 2)):   # the larger first: its partials stay behind
+    # the limit (every one of the 4096 partial slots) first, then smaller sizes, so that
+    # partials of a larger call stay behind in the shared array
+    for n, seed in ((1_048_576, 3), (300_001, 1), (4097, 2)):
         args = _case(n, seed)
         ref = _run(B.ddppo_ppo_loss, n, args)
         got = _run(B.ddppo_ppo_loss_static, n, args)
