@@ -156,6 +156,15 @@ const char* ddppo_last_error(void);
  * with a device-to-host copy that synchronises `stream`. code_out: [host]. */
 int ddppo_device_status(ddppo_ctx* ctx, int32_t* code_out, void* stream);
 
+/* Cap on the level loop of the BFS geodesic field (Sec. 4 "Training": geodesic distance
+ * to the goal), for tests of the device-side failure path. cap = 0 (the default) allows
+ * G + 1 levels on a G-cell grid, more than any BFS needs; cap > 0 stops the loop after
+ * cap levels. A BFS that still had cells to reach then sets the sticky E_TIMEOUT status,
+ * leaves those cells unreachable (-1) and returns, so the launch completes and the
+ * context stays usable. Takes effect for launches enqueued afterwards (a collect graph
+ * keeps the value it was captured with). Host only. Errors: E_ARG (null, cap < 0). */
+int ddppo_set_bfs_level_cap(ddppo_ctx* ctx, int32_t cap);
+
 /* ---- parameters -------------------------------------------------------------- */
 
 /* Number of FP32 parameters. The flat layout is the concatenation of the

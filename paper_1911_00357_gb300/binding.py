@@ -85,6 +85,7 @@ _SIGS = {
     "ddppo_config_check": [P],
     "ddppo_destroy": [P],
     "ddppo_device_status": [P, P, P],
+    "ddppo_set_bfs_level_cap": [P, I32],
     "ddppo_num_params": [P, P],
     "ddppo_get_params": [P, P, I64, P],
     "ddppo_set_params": [P, P, I64, P],
@@ -191,6 +192,11 @@ def ddppo_device_status(h) -> int:
     code = ctypes.c_int32()
     _check(lib().ddppo_device_status(h, ctypes.byref(code), _s()))
     return code.value
+
+
+def ddppo_set_bfs_level_cap(h, cap: int) -> None:
+    """Cap the BFS level loop (0 restores the default); a test setting, see the header."""
+    _check(lib().ddppo_set_bfs_level_cap(h, cap))
 
 
 def ddppo_num_params(h) -> int:

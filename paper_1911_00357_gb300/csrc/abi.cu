@@ -209,6 +209,13 @@ extern "C" int ddppo_device_status(ddppo_ctx* x, int32_t* code_out, void* stream
   return DDPPO_OK;
 }
 
+extern "C" int ddppo_set_bfs_level_cap(ddppo_ctx* x, int32_t cap) {
+  ARG_CHECK(x, "set_bfs_level_cap: null ctx");
+  ARG_CHECK(cap >= 0, "set_bfs_level_cap: negative cap");
+  x->sp.bfs_level_cap = cap;
+  return DDPPO_OK;
+}
+
 // ---- environment ----
 extern "C" int ddppo_env_reset(ddppo_ctx* x, void* obs, float* goal, void* stream) {
   ARG_CHECK(x && obs && goal, "env_reset: null argument");

@@ -54,6 +54,7 @@ struct SimParams {
   uint64_t seed;
   int max_segs;
   int bf16_obs;
+  int bfs_level_cap;  // 0: none (G + 1 levels); > 0: cap the BFS level loop (tests)
 };
 
 // Every env owns two scene slots: the current episode's and the next one's, which the

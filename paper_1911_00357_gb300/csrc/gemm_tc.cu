@@ -18,7 +18,10 @@
 //   * Small-M problems (the per-step LSTM recurrences) are computed transposed (swap AB)
 //     so the 128-row MMA dimension covers the large side.
 // Every wait is bounded; a wait that runs out sets the sticky timeout flag and the CTA
-// drains and frees its tensor memory instead of hanging.
+// stops: its epilogue stores nothing, and before the tensor memory is freed the CTA waits
+// (again with a limit) for its own asynchronous work still in flight -- the TMA loads it
+// issued into stages the MMA thread never consumed, and the MMAs it issued (one final
+// tcgen05.commit covers all of them) -- so no copy or MMA lands in freed memory.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
@@ -46,6 +49,9 @@ struct TcSmem {
   uint64_t full[TC_STAGES];
   uint64_t empty[TC_STAGES];
   uint64_t done;
+  uint64_t drain;      // final commit of the MMA thread after an abort
+  uint32_t issued;     // ring stages whose TMA loads the producer issued
+  uint32_t consumed;   // ring stages the MMA thread waited for
   uint32_t tmem_base;
   int abort;
 };
@@ -85,6 +91,32 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   *abort = 1;
   if (err) atomicOr(err, 2);
   return false;
+}
+
+// the drain after an abort: poll until the phase completes or the limit runs out (the
+// abort flag is already set, so mbar_wait would return at once)
+__device__ __forceinline__ bool mbar_drain_wait(uint64_t* bar, uint32_t parity) {
+  for (uint32_t i = 0; i < TC_SPIN_LIMIT; ++i)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_addr(bar))
+      : "memory");
+}
+
+// After an abort (uniform once every role has left its loop): thread 0 waits for the
+// TMA loads of the stages issued but never consumed, stage it % stages completing phase
+// (it / stages) & 1 -- at most `stages` of them, since the producer waits for a stage's
+// release before refilling it -- and, in the halo mode, for the resident weights.
+__device__ __forceinline__ void drain_unconsumed(uint64_t* full, uint32_t consumed, uint32_t issued,
+                                                 int stages, uint64_t* weights) {
+  for (uint32_t it = consumed; it < issued; ++it)
+    mbar_drain_wait(&full[it % stages], (it / stages) & 1u);
+  if (weights) mbar_drain_wait(weights, 0u);
 }
 
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
@@ -275,6 +307,9 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
       mbar_init(&ctl.empty[s], 1);
     }
     mbar_init(&ctl.done, 1);  // halo mode: resident weights landed
+    mbar_init(&ctl.drain, 1);
+    ctl.issued = 0;
+    ctl.consumed = 0;
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
@@ -322,6 +357,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
           tma_load_4d(sA + hs * A_BYTES, &mapA, &ctl.full[hs], c0, -ca.p, ybase, img);
         }
       }
+      ctl.issued = hit;
     }
   } else if (warp == 1 && halo) {
     if (lane == 0) {
@@ -366,6 +402,11 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_addr(&acc_full[buf]))
             : "memory");
+      }
+      ctl.consumed = hit;
+      if (*abort) {
+        tc_commit(&ctl.drain);  // arrives once every MMA this thread issued has completed
+        mbar_drain_wait(&ctl.drain, 0u);
       }
     }
   } else if (warp == 0) {
@@ -437,6 +478,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
           }
         }
       }
+      ctl.issued = it;
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -484,6 +526,11 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
             "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                 smem_addr(&acc_full[buf]))
             : "memory");
+      }
+      ctl.consumed = it;
+      if (*abort) {
+        tc_commit(&ctl.drain);  // arrives once every MMA this thread issued has completed
+        mbar_drain_wait(&ctl.drain, 0u);
       }
     }
   } else {
@@ -638,6 +685,11 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (ctl.abort) {  // every role has left its loop: the flag no longer changes
+    if (threadIdx.x == 0)
+      drain_unconsumed(ctl.full, ctl.consumed, ctl.issued, stages, halo ? &ctl.done : nullptr);
+    __syncthreads();
+  }
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
@@ -1205,6 +1257,7 @@ __global__ void __launch_bounds__(WH_THREADS, 1)
   __shared__ uint64_t full[WH_STAGES], empty[WH_STAGES], done;
   __shared__ uint32_t tmem_base;
   __shared__ int abort_flag;
+  __shared__ uint32_t n_issued, n_consumed;  // ring stages loaded / waited for (drain)
   uint8_t* base = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
   uint8_t* sX = base;
   uint8_t* sD = base + stages * x_stride;
@@ -1217,6 +1270,8 @@ __global__ void __launch_bounds__(WH_THREADS, 1)
     }
     mbar_init(&done, 1);
     abort_flag = 0;
+    n_issued = 0;
+    n_consumed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -1242,6 +1297,7 @@ __global__ void __launch_bounds__(WH_THREADS, 1)
       tma_load_4d(sX + s * x_stride, &mapX, &full[s], 0, -1, y0 - 1, img);
       tma_load_4d(sD + s * dz_stride, &mapDZ, &full[s], 0, 0, y0, img);
     }
+    n_issued = it;
   } else if (warp == 1 && lane == 0) {
     const uint32_t idesc = f16_idesc(TC_BM, 32, 1, 1);
     uint32_t it = 0;
@@ -1273,6 +1329,10 @@ __global__ void __launch_bounds__(WH_THREADS, 1)
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
             smem_addr(&done))
         : "memory");
+    n_consumed = it;
+    // after an abort the epilogue no longer waits for `done`; this thread does, so that
+    // every MMA it issued has completed before the accumulators are freed
+    if (*abort) mbar_drain_wait(&done, 0u);
   }
   __syncwarp();
   // epilogue: warp w holds TMEM rows 32 w .. 32 w + 31 = tap kx = w, channel c = lane
@@ -1304,6 +1364,10 @@ __global__ void __launch_bounds__(WH_THREADS, 1)
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+  if (abort_flag) {  // uniform: no thread writes it after the barrier
+    if (threadIdx.x == 0) drain_unconsumed(full, n_consumed, n_issued, stages, nullptr);
+    __syncthreads();
+  }
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(128));

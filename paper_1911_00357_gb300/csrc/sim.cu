@@ -108,8 +108,11 @@ __device__ int block_exclusive_scan(int v, int* sh, int* total) {
 
 // ---- bit-parallel 4-connected BFS from cell `goal` over free bits Fw ----
 // One level per iteration: next = dilate(frontier) & free & ~visited, 32 cells per word.
+// The level loop is capped: at G + 1 levels (more than any BFS of a G-cell grid needs),
+// or at `level_cap` when that is positive (a test setting that makes the cap run out).
+// A run-out sets the sticky timeout flag and leaves the cells not reached at -1.
 __device__ void bfs_block(const uint32_t* __restrict__ Fw, uint32_t* Vw, uint32_t* A, uint32_t* B,
-                          int32_t* dist, int g, int goal, int32_t* err) {
+                          int32_t* dist, int g, int goal, int32_t* err, int level_cap) {
   const int tid = threadIdx.x, nt = blockDim.x;
   const int G = g * g, R = g >> 5, NW = G >> 5;
   for (int i = tid; i < G; i += nt) dist[i] = -1;
@@ -123,7 +126,8 @@ __device__ void bfs_block(const uint32_t* __restrict__ Fw, uint32_t* Vw, uint32_
   __syncthreads();
   int level = 0;
   bool finished = false;
-  for (int it = 0; it <= G; ++it) {
+  const int max_levels = level_cap > 0 && level_cap <= G ? level_cap : G + 1;
+  for (int it = 0; it < max_levels; ++it) {
     ++level;
     int any = 0;
     for (int w = tid; w < NW; w += nt) {
@@ -268,7 +272,7 @@ __device__ void gen_episode(const SimParams& p, const SimBuffers& b, int e, int6
     for (int a = 0; a < 64; ++a) {
       const int gi = (int)uni(chash(p.seed, e, episode, SM_GOAL, (uint64_t)a), (uint32_t)G);
       if (grid[gi]) continue;
-      bfs_block(Fw, Vw, A, B, dist, g, gi, b.err);
+      bfs_block(Fw, Vw, A, B, dist, g, gi, b.err, p.bfs_level_cap);
       const int chunk = (G + nt - 1) / nt;
       const int lo = min(G, tid * chunk), hi = min(G, lo + chunk);
       int cnt = 0;
@@ -474,8 +478,11 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 // Render env e with the whole block: TMA bulk copy of the bit-packed grid into smem (the
 // mbarrier `bar` completes phase `phase`), then one column ray per thread (looping when
 // the image is wider than the block), depth against the analytic planes, the optional
-// 2x2 pool, normalisation and cast; thread 0 writes the goal vector.
-__device__ void render_env_block(const SimParams& p, const SimBuffers& b, int e,
+// 2x2 pool, normalisation and cast; thread 0 writes the goal vector. Returns false (the
+// same for every thread) when the wait for the copy ran out: the timeout flag is set,
+// nothing is rendered, and the caller must not reuse `sbits` or `bar` -- the copy may
+// still land there.
+__device__ bool render_env_block(const SimParams& p, const SimBuffers& b, int e,
                                  void* __restrict__ obs, float* __restrict__ goal,
                                  float* __restrict__ depth_raw, uint32_t* sbits, uint64_t* mbar,
                                  uint32_t phase) {
@@ -504,7 +511,10 @@ __device__ void render_env_block(const SimParams& p, const SimBuffers& b, int e,
         : "r"(bar), "r"(phase)
         : "memory");
   }
-  if (!ok) set_err(b.err, ERRF_TIMEOUT);  // keep going: every later access stays in bounds
+  if (!__syncthreads_and(ok)) {
+    if (tid == 0) set_err(b.err, ERRF_TIMEOUT);
+    return false;
+  }
   const int cs = p.cell_u;
   const int k = st[ST_HEAD];
   const float c = c_cos[k], s = c_sin[k];
@@ -573,6 +583,7 @@ __device__ void render_env_block(const SimParams& p, const SimBuffers& b, int e,
       }
     }
   }
+  return true;
 }
 
 __global__ void render_kernel(SimParams p, SimBuffers b, void* __restrict__ obs,
@@ -621,7 +632,9 @@ __global__ void __launch_bounds__(RESET_THREADS)
       asm volatile("fence.proxy.async.global;" ::: "memory");
     }
     __syncthreads();
-    render_env_block(p, b, e, obs, goal, nullptr, smem, &mbar, phase);
+    // a copy that did not arrive may still land in smem: this CTA takes no further env
+    // (the others drain the work counter; the sticky flag reports the run-out)
+    if (!render_env_block(p, b, e, obs, goal, nullptr, smem, &mbar, phase)) break;
     phase ^= 1u;
     __syncthreads();  // smem is reused by the next env
   }
