@@ -267,6 +267,30 @@ int ddppo_policy_evaluate(ddppo_ctx* ctx, int32_t T, int32_t E, const void* obs,
 int ddppo_policy_backward(ddppo_ctx* ctx, const float* dlogits, const float* dvalues, float* grad,
                           void* stream);
 
+/* The visual encoder alone (App. "Visual Encoder"; the 3-layer conv, or the ResNet with
+ * GroupNorm and the compression layer): features feat [dev] [N, F] fp32 of obs [dev]
+ * [N, 1, h, w] (the precision's dtype), F = C x HW in channel-major order (feature
+ * c * HW + p, the column order of vis.w), the post-ReLU output of the last layer.
+ * 1 <= N <= rollout_T * num_envs / minibatches; larger N: E_CONFIG; the blind agent
+ * (net_kind 2): E_CONFIG. ddppo_encoder_backward: the hand-written backward of the last
+ * encoder_forward for dfeat [dev] [N, F] (same layout); grad [dev] [n_params] is
+ * overwritten, nonzero only in the encoder's tensors. Any other forward of the context
+ * in between (act, evaluate, collect, update, lstm_forward) invalidates it: E_STATE. */
+int ddppo_encoder_forward(ddppo_ctx* ctx, int32_t N, const void* obs, float* feat, void* stream);
+int ddppo_encoder_backward(ddppo_ctx* ctx, const float* dfeat, float* grad, void* stream);
+
+/* The LSTM layers alone over a [T, E] segment (App. "Navigation Policy"; gates i, f, g, o,
+ * state reset where masks == 0 before a step): in [dev] [T, E, In_0] fp32 (the layer-0
+ * input [visual FC | goal FC | action embedding], rounded to the operand dtype as the
+ * network does), masks [dev] [T, E], h0/c0 [dev] [L, E, H]; y [dev] [T, E, H] the top
+ * layer's output. ddppo_lstm_backward: back-propagation through time of the last
+ * lstm_forward for dy [dev] [T, E, H]; dx [dev] [T, E, In_0] (NULL ok) receives the
+ * input gradient; grad [dev] [n_params] is overwritten, nonzero only in the LSTM's
+ * tensors. Same workspace limits and invalidation as the encoder pair. */
+int ddppo_lstm_forward(ddppo_ctx* ctx, int32_t T, int32_t E, const float* in, const uint8_t* masks,
+                       const float* h0, const float* c0, float* y, void* stream);
+int ddppo_lstm_backward(ddppo_ctx* ctx, const float* dy, float* dx, float* grad, void* stream);
+
 /* ---- learning (Sec. 2 Eq. 1-2; Sec. 4 "Training") ----------------------------- */
 
 /* Generalised advantage estimation, one warp-level reverse scan per env:
@@ -324,6 +348,28 @@ int ddppo_ppo_update(ddppo_ctx* ctx, const ddppo_rollout* ro, const ddppo_ppo_hp
  * rollout pointers (the first call with new pointers captures and is not itself
  * capturable). */
 int ddppo_collect(ddppo_ctx* ctx, const ddppo_rollout* ro, int32_t use_graph, void* stream);
+
+/* ---- checkpoint / resume ---------------------------------------------------------- */
+
+/* Write / read a worker's whole learning state to / from the file `path` [host], so that
+ * a run can stop and resume bit-identically (the paper trains for days under a cluster
+ * scheduler that preempts and restarts jobs; Sec. 3, Sec. 4 "Training"). The file holds
+ * the configuration (ddppo_load rejects a file written by a worker with another one:
+ * E_CONFIG), the FP32 parameters, the Adam moments and step count, the world (both scene
+ * slots of every env with their grids, wall bits and BFS fields; agent states; prepared
+ * next episodes), FP8 inference's delayed activation scales and the GEMM autotuner's
+ * table. With a rollout view ro (NULL ok), it also holds the state the next
+ * ddppo_collect carries over: slot T of obs, goal, prev_a and masks, and the LSTM state
+ * ro->h, ro->c; a file written with ro must be loaded with ro (into any rollout view of
+ * the same shapes), and the next ddppo_collect then continues the saved run. Loaded
+ * without rollout state, the next ddppo_collect starts from env_reset. The update index
+ * (hparams) and the action uniforms stay with the caller. Both synchronise `stream`
+ * and are not capturable; save reads the state once every call enqueued on `stream`
+ * has finished. Errors: E_ARG (null argument, file cannot be opened or written),
+ * E_CONFIG (not a checkpoint of this library and configuration, a section of the wrong
+ * size, a truncated file), E_CUDA. */
+int ddppo_save(ddppo_ctx* ctx, const ddppo_rollout* ro, const char* path, void* stream);
+int ddppo_load(ddppo_ctx* ctx, const ddppo_rollout* ro, const char* path, void* stream);
 
 /* ---- contraction utility --------------------------------------------------------- */
 

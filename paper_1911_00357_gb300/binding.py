@@ -100,11 +100,17 @@ _SIGS = {
     "ddppo_policy_act": [P, P, P, P, P, P, P, P, P, P, P, P],
     "ddppo_policy_evaluate": [P, I32, I32, P, P, P, P, P, P, P, P, P],
     "ddppo_policy_backward": [P, P, P, P, P],
+    "ddppo_encoder_forward": [P, I32, P, P, P],
+    "ddppo_encoder_backward": [P, P, P, P],
+    "ddppo_lstm_forward": [P, I32, I32, P, P, P, P, P, P],
+    "ddppo_lstm_backward": [P, P, P, P, P],
     "ddppo_gae": [P, P, P, I32, I32, F32, F32, P, P, P],
     "ddppo_ppo_loss": [I32, P, P, P, P, P, P, F32, F32, F32, P, P, P, P],
     "ddppo_ppo_loss_static": [I32, P, P, P, P, P, P, F32, F32, F32, P, P, P, P],
     "ddppo_ppo_update": [P, P, P, P, P],
     "ddppo_collect": [P, P, I32, P],
+    "ddppo_save": [P, P, ctypes.c_char_p, P],
+    "ddppo_load": [P, P, ctypes.c_char_p, P],
     "ddppo_timing_enable": [P, I32],
     "ddppo_timing_read": [P, I32, P, P, P],
     "ddppo_count_kernels": [P, P, P, F32, F32, P],
@@ -263,6 +269,22 @@ def ddppo_policy_backward(h, dlogits, dvalues, grad):
     _check(lib().ddppo_policy_backward(h, _p(dlogits), _p(dvalues), _p(grad), _s()))
 
 
+def ddppo_encoder_forward(h, N, obs, feat):
+    _check(lib().ddppo_encoder_forward(h, N, _p(obs), _p(feat), _s()))
+
+
+def ddppo_encoder_backward(h, dfeat, grad):
+    _check(lib().ddppo_encoder_backward(h, _p(dfeat), _p(grad), _s()))
+
+
+def ddppo_lstm_forward(h, T, E, x, masks, h0, c0, y):
+    _check(lib().ddppo_lstm_forward(h, T, E, _p(x), _p(masks), _p(h0), _p(c0), _p(y), _s()))
+
+
+def ddppo_lstm_backward(h, dy, dx, grad):
+    _check(lib().ddppo_lstm_backward(h, _p(dy), _p(dx), _p(grad), _s()))
+
+
 def ddppo_gae(reward, done, value, T, E, gamma, lam, adv, ret):
     _check(lib().ddppo_gae(_p(reward), _p(done), _p(value), T, E, gamma, lam, _p(adv), _p(ret),
                            _s()))
@@ -288,6 +310,18 @@ def ddppo_ppo_update(h, ro: Rollout, hp: PPOHParams, stats=None):
 
 def ddppo_collect(h, ro: Rollout, use_graph: bool = True):
     _check(lib().ddppo_collect(h, ctypes.byref(ro), 1 if use_graph else 0, _s()))
+
+
+def ddppo_save(h, path: str, ro: Rollout | None = None):
+    """Checkpoint the worker (and, with ro, the rollout state the next collect carries)."""
+    _check(lib().ddppo_save(h, ctypes.byref(ro) if ro is not None else None,
+                            os.fsencode(path), _s()))
+
+
+def ddppo_load(h, path: str, ro: Rollout | None = None):
+    """Restore a checkpoint written by ddppo_save for a worker of the same configuration."""
+    _check(lib().ddppo_load(h, ctypes.byref(ro) if ro is not None else None,
+                            os.fsencode(path), _s()))
 
 
 def ddppo_timing_enable(h, on: bool):

@@ -169,6 +169,7 @@ static int alloc_f8(Net& n, int pool_hw) {
   n.f8_slots = slot + (int)wq.size();
   DDPPO_TRY(nalloc(n, &n.f8_scale, (size_t)n.f8_slots));
   DDPPO_TRY(nalloc(n, &n.f8_amax, (size_t)n.f8_slots));
+  DDPPO_TRY(nalloc(n, &n.f8_keep, 2 * (size_t)n.f8_act_slots));
   for (ConvL* c : wq) {
     DDPPO_TRY(nalloc(n, &c->wg8, (size_t)c->cout * c->Kp));
     c->w8_scale = n.f8_scale + slot;
@@ -754,31 +755,11 @@ static int encoder_bwd(Net& n, const void* obs, int N, const float* dfeat_rows, 
 }
 
 // ---------------------------------------------------------------- forward / backward
-int net_forward(Net& n, int T, int E, const void* obs, const float* goal, const int32_t* prev_a,
-                const uint8_t* masks, const float* h0, const float* c0, const float* u,
-                int32_t* action, float* logp, cudaStream_t s, bool infer) {
+// the LSTM layers over a [T, E] segment: layer 0 reads n.x1 (op dtype, [N, In0]); every
+// step's gates, cell and hidden state stay in the layer buffers for the backward
+static int lstm_forward(Net& n, int T, int E, const uint8_t* masks, const float* h0,
+                        const float* c0, cudaStream_t s) {
   const int N = T * E, Hd = n.H, G4 = 4 * Hd;
-  if (N > n.NS || E > n.E) {
-    set_error("forward: segment larger than the workspace");
-    return DDPPO_E_CONFIG;
-  }
-  if (n.F > 0) {
-    const int nch = (N + n.NC - 1) / n.NC;
-    for (int c = 0; c < nch; ++c) {
-      const int r0 = c * n.NC, rn = std::min(n.NC, N - r0);
-      DDPPO_TRY(encoder_fwd(n, opoff(n, obs, (size_t)r0 * n.pix), rn,
-                            opoff(n, n.featop, (size_t)r0 * n.F), s, infer && n.f8 && rn <= n.E));
-    }
-    n.ev_valid_chunk = nch - 1;
-    GemmDesc v;
-    v.M = N; v.N = Hd; v.K = n.F;
-    v.A = n.featop; v.lda = n.F; v.B = n.Wv; v.ldb = n.F;
-    v.C = n.x1; v.ldc = n.In0; v.c_bf16 = n.bf ? 1 : 0;
-    v.bias = n.params + n.vis_b; v.relu = 1;
-    DDPPO_TRY(G(n, v, s));
-  }
-  DDPPO_TRY(launch_embed_fwd(N, goal, prev_a, n.params + n.goal_w, n.params + n.goal_b,
-                             n.params + n.emb, n.x1, n.In0, n.emb_col0, n.bf, s));
   for (int l = 0; l < n.L; ++l) {
     LstmL& q = n.lstm[l];
     GemmDesc gx;
@@ -811,30 +792,17 @@ int net_forward(Net& n, int T, int E, const void* obs, const float* goal, const 
       DDPPO_TRY(launch_lstm_fwd(st, s));
     }
   }
-  Heads hd{};
-  hd.N = N; hd.H = Hd; hd.h = n.lstm[n.L - 1].h;
-  hd.Wa = n.params + n.actor_w; hd.ba = n.params + n.actor_b;
-  hd.Wv = n.params + n.critic_w; hd.bv = n.params + n.critic_b;
-  hd.logits = n.logits; hd.value = n.values;
-  hd.u = u; hd.action = action; hd.logp = logp;
-  DDPPO_TRY(launch_heads_fwd(hd, s));
-  n.ev_T = T; n.ev_E = E; n.ev_valid = true;
-  n.ev_obs = obs; n.ev_goal = goal; n.ev_preva = prev_a; n.ev_masks = masks;
-  n.ev_h0 = h0; n.ev_c0 = c0;
   return DDPPO_OK;
 }
 
-int net_backward(Net& n, const float* dlogits, const float* dvalues, cudaStream_t s) {
-  if (!n.ev_valid) {
-    set_error("policy_backward without a preceding evaluate");
-    return DDPPO_E_STATE;
-  }
-  const int T = n.ev_T, E = n.ev_E, N = T * E, Hd = n.H, G4 = 4 * Hd;
-  DDPPO_CHECK_CUDA(cudaMemsetAsync(n.grad, 0, n.P * sizeof(float), s));
-  DDPPO_TRY(launch_heads_bwd(N, Hd, n.lstm[n.L - 1].h, n.params + n.actor_w, n.params + n.critic_w,
-                             dlogits, dvalues, n.dh_top, n.grad + n.actor_w, n.grad + n.actor_b,
-                             n.grad + n.critic_w, n.grad + n.critic_b, n.scratch, n.scratch_elems, s));
-  const float* dabove = n.dh_top;
+// back-propagation through time over the last [T, E] forward of the LSTM layers: dtop
+// [N, H] is the gradient of the top layer's outputs; accumulates the LSTM parameter
+// gradients into n.grad and leaves the gradient of layer 0's input ([N, In0], fp32) in
+// *dx0
+static int lstm_backward(Net& n, int T, int E, const uint8_t* masks, const float* c0,
+                         const float* dtop, const float** dx0, cudaStream_t s) {
+  const int N = T * E, Hd = n.H, G4 = 4 * Hd;
+  const float* dabove = dtop;
   for (int l = n.L - 1; l >= 0; --l) {
     LstmL& q = n.lstm[l];
     DDPPO_CHECK_CUDA(cudaMemsetAsync(n.dc_carry, 0, (size_t)E * Hd * sizeof(float), s));
@@ -843,9 +811,9 @@ int net_backward(Net& n, const float* dlogits, const float* dvalues, cudaStream_
       b.E = E; b.H = Hd;
       b.gates = q.gates + (size_t)t * E * G4;
       b.c = q.c + (size_t)t * E * Hd;
-      b.c_prev = t == 0 ? n.ev_c0 + (size_t)l * E * Hd : q.c + (size_t)(t - 1) * E * Hd;
-      b.m = n.ev_masks + (size_t)t * E;
-      b.m_next = t + 1 < T ? n.ev_masks + (size_t)(t + 1) * E : nullptr;
+      b.c_prev = t == 0 ? c0 + (size_t)l * E * Hd : q.c + (size_t)(t - 1) * E * Hd;
+      b.m = masks + (size_t)t * E;
+      b.m_next = t + 1 < T ? masks + (size_t)(t + 1) * E : nullptr;
       b.dh_above = dabove + (size_t)t * E * Hd;
       b.dh_rec = t + 1 < T ? n.dh_rec : nullptr;
       b.dc_carry = n.dc_carry;
@@ -885,6 +853,82 @@ int net_backward(Net& n, const float* dlogits, const float* dvalues, cudaStream_
     DDPPO_TRY(launch_colsum(n.dg32, N, G4, G4, n.grad + q.bhh, false, s));
     dabove = dX;
   }
+  *dx0 = dabove;
+  return DDPPO_OK;
+}
+
+// encoder backward over N frames of obs given n.dfeat (NHWC-flattened feature rows, fp32):
+// last chunk first (its activations are still resident), the others recomputed; the
+// convolution weight gradients land in n.grad
+static int encoder_backward(Net& n, const void* obs, int N, cudaStream_t s) {
+  const int nch = (N + n.NC - 1) / n.NC;
+  for (int c = nch - 1; c >= 0; --c) {
+    const int r0 = c * n.NC, rn = std::min(n.NC, N - r0);
+    const void* obs_c = opoff(n, obs, (size_t)r0 * n.pix);
+    if (c != n.ev_valid_chunk) {
+      DDPPO_TRY(encoder_fwd(n, obs_c, rn, n.featT, s));  // feature rows are not needed again
+      n.ev_valid_chunk = c;
+    }
+    DDPPO_TRY(encoder_bwd(n, obs_c, rn, n.dfeat + (size_t)r0 * n.F, c == nch - 1, s));
+  }
+  for (ConvL* c : n.convs)
+    DDPPO_TRY(launch_conv_w_grad(c->dwg, c->cout, c->cin, c->k, c->Kp, n.grad + c->w_off, s));
+  return DDPPO_OK;
+}
+
+int net_forward(Net& n, int T, int E, const void* obs, const float* goal, const int32_t* prev_a,
+                const uint8_t* masks, const float* h0, const float* c0, const float* u,
+                int32_t* action, float* logp, cudaStream_t s, bool infer) {
+  const int N = T * E, Hd = n.H;
+  if (N > n.NS || E > n.E) {
+    set_error("forward: segment larger than the workspace");
+    return DDPPO_E_CONFIG;
+  }
+  n.enc_valid = false;
+  n.lstm_valid = false;
+  if (n.F > 0) {
+    const int nch = (N + n.NC - 1) / n.NC;
+    for (int c = 0; c < nch; ++c) {
+      const int r0 = c * n.NC, rn = std::min(n.NC, N - r0);
+      DDPPO_TRY(encoder_fwd(n, opoff(n, obs, (size_t)r0 * n.pix), rn,
+                            opoff(n, n.featop, (size_t)r0 * n.F), s, infer && n.f8 && rn <= n.E));
+    }
+    n.ev_valid_chunk = nch - 1;
+    GemmDesc v;
+    v.M = N; v.N = Hd; v.K = n.F;
+    v.A = n.featop; v.lda = n.F; v.B = n.Wv; v.ldb = n.F;
+    v.C = n.x1; v.ldc = n.In0; v.c_bf16 = n.bf ? 1 : 0;
+    v.bias = n.params + n.vis_b; v.relu = 1;
+    DDPPO_TRY(G(n, v, s));
+  }
+  DDPPO_TRY(launch_embed_fwd(N, goal, prev_a, n.params + n.goal_w, n.params + n.goal_b,
+                             n.params + n.emb, n.x1, n.In0, n.emb_col0, n.bf, s));
+  DDPPO_TRY(lstm_forward(n, T, E, masks, h0, c0, s));
+  Heads hd{};
+  hd.N = N; hd.H = Hd; hd.h = n.lstm[n.L - 1].h;
+  hd.Wa = n.params + n.actor_w; hd.ba = n.params + n.actor_b;
+  hd.Wv = n.params + n.critic_w; hd.bv = n.params + n.critic_b;
+  hd.logits = n.logits; hd.value = n.values;
+  hd.u = u; hd.action = action; hd.logp = logp;
+  DDPPO_TRY(launch_heads_fwd(hd, s));
+  n.ev_T = T; n.ev_E = E; n.ev_valid = true;
+  n.ev_obs = obs; n.ev_goal = goal; n.ev_preva = prev_a; n.ev_masks = masks;
+  n.ev_h0 = h0; n.ev_c0 = c0;
+  return DDPPO_OK;
+}
+
+int net_backward(Net& n, const float* dlogits, const float* dvalues, cudaStream_t s) {
+  if (!n.ev_valid) {
+    set_error("policy_backward without a preceding evaluate");
+    return DDPPO_E_STATE;
+  }
+  const int T = n.ev_T, E = n.ev_E, N = T * E, Hd = n.H;
+  DDPPO_CHECK_CUDA(cudaMemsetAsync(n.grad, 0, n.P * sizeof(float), s));
+  DDPPO_TRY(launch_heads_bwd(N, Hd, n.lstm[n.L - 1].h, n.params + n.actor_w, n.params + n.critic_w,
+                             dlogits, dvalues, n.dh_top, n.grad + n.actor_w, n.grad + n.actor_b,
+                             n.grad + n.critic_w, n.grad + n.critic_b, n.scratch, n.scratch_elems, s));
+  const float* dabove = nullptr;
+  DDPPO_TRY(lstm_backward(n, T, E, n.ev_masks, n.ev_c0, n.dh_top, &dabove, s));
   // concatenated LSTM input: [visual FC (H) | goal FC (32) | action embedding (32)]
   DDPPO_TRY(launch_embed_bwd(N, n.ev_goal, n.ev_preva, dabove, n.In0, n.emb_col0,
                              n.grad + n.goal_w, n.grad + n.goal_b, n.grad + n.emb, n.scratch,
@@ -903,19 +947,104 @@ int net_backward(Net& n, const float* dlogits, const float* dvalues, cudaStream_
   df.A = n.dvop; df.lda = Hd; df.B = n.WvT; df.ldb = Hd;
   df.C = n.dfeat; df.ldc = n.F;
   DDPPO_TRY(G(n, df, s));
-  // encoder, last chunk first (its activations are still resident)
-  const int nch = (N + n.NC - 1) / n.NC;
-  for (int c = nch - 1; c >= 0; --c) {
-    const int r0 = c * n.NC, rn = std::min(n.NC, N - r0);
-    const void* obs_c = opoff(n, n.ev_obs, (size_t)r0 * n.pix);
-    if (c != n.ev_valid_chunk) {
-      DDPPO_TRY(encoder_fwd(n, obs_c, rn, n.featT, s));  // feature rows are not needed again
-      n.ev_valid_chunk = c;
-    }
-    DDPPO_TRY(encoder_bwd(n, obs_c, rn, n.dfeat + (size_t)r0 * n.F, c == nch - 1, s));
+  DDPPO_TRY(encoder_backward(n, n.ev_obs, N, s));
+  return DDPPO_OK;
+}
+
+
+// ---------------------------------------------------------------- stand-alone pieces
+// Encoder features leave and enter the library in the parameter layout's order (channel-
+// major: f = c * HW + p, the order vis.w's columns use); inside they are NHWC rows.
+__global__ void feat_layout_kernel(const float* __restrict__ in, float* __restrict__ out, int N,
+                                   int HW, int C, int to_cmajor) {
+  const size_t total = (size_t)N * HW * C;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const size_t img = i / ((size_t)HW * C);
+    const int r = (int)(i - img * HW * C), p = r / C, c = r - p * C;
+    const size_t cm = img * HW * C + (size_t)c * HW + p;
+    if (to_cmajor) out[cm] = in[i];
+    else out[i] = in[cm];
   }
-  for (ConvL* c : n.convs)
-    DDPPO_TRY(launch_conv_w_grad(c->dwg, c->cout, c->cin, c->k, c->Kp, n.grad + c->w_off, s));
+}
+
+static int feat_layout(const Net& n, const float* in, float* out, int N, bool to_cmajor,
+                       cudaStream_t s) {
+  const size_t total = (size_t)N * n.F;
+  if (!total) return DDPPO_OK;
+  const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
+  feat_layout_kernel<<<blocks, 256, 0, s>>>(in, out, N, n.featHW, n.featC, to_cmajor ? 1 : 0);
+  DDPPO_CHECK_LAUNCH();
+  return DDPPO_OK;
+}
+
+int net_encoder_forward(Net& n, int N, const void* obs, float* feat, cudaStream_t s) {
+  if (n.F == 0) {
+    set_error("encoder_forward: the blind agent has no visual encoder");
+    return DDPPO_E_CONFIG;
+  }
+  if (N < 1 || N > n.NS) {
+    set_error("encoder_forward: N must be in [1, rollout_T * num_envs / minibatches]");
+    return DDPPO_E_CONFIG;
+  }
+  const int nch = (N + n.NC - 1) / n.NC;
+  for (int c = 0; c < nch; ++c) {
+    const int r0 = c * n.NC, rn = std::min(n.NC, N - r0);
+    DDPPO_TRY(encoder_fwd(n, opoff(n, obs, (size_t)r0 * n.pix), rn,
+                          opoff(n, n.featop, (size_t)r0 * n.F), s));
+    // the chunk's fp32 features: the post-ReLU output of the last layer
+    const float* out = n.kind == 0 ? n.nat[2].z : n.cmp_n.out;
+    DDPPO_TRY(feat_layout(n, out, feat + (size_t)r0 * n.F, rn, true, s));
+  }
+  n.ev_valid_chunk = nch - 1;
+  n.ev_valid = false;
+  n.lstm_valid = false;
+  n.enc_valid = true;
+  n.enc_obs = obs;
+  n.enc_N = N;
+  return DDPPO_OK;
+}
+
+int net_encoder_backward(Net& n, const float* dfeat, cudaStream_t s) {
+  if (!n.enc_valid) {
+    set_error("encoder_backward without a preceding encoder_forward");
+    return DDPPO_E_STATE;
+  }
+  DDPPO_CHECK_CUDA(cudaMemsetAsync(n.grad, 0, n.P * sizeof(float), s));
+  DDPPO_TRY(feat_layout(n, dfeat, n.dfeat, n.enc_N, false, s));
+  return encoder_backward(n, n.enc_obs, n.enc_N, s);
+}
+
+int net_lstm_forward(Net& n, int T, int E, const float* x, const uint8_t* masks, const float* h0,
+                     const float* c0, float* y, cudaStream_t s) {
+  const int N = T * E;
+  if (T < 1 || E < 1 || N > n.NS || E > n.E) {
+    set_error("lstm_forward: segment larger than the workspace");
+    return DDPPO_E_CONFIG;
+  }
+  DDPPO_TRY(launch_cast(x, n.x1, n.bf, (size_t)N * n.In0, s));
+  DDPPO_TRY(lstm_forward(n, T, E, masks, h0, c0, s));
+  DDPPO_CHECK_CUDA(cudaMemcpyAsync(y, n.lstm[n.L - 1].h, (size_t)N * n.H * sizeof(float),
+                                   cudaMemcpyDeviceToDevice, s));
+  n.ev_valid = false;
+  n.enc_valid = false;
+  n.lstm_valid = true;
+  n.ls_T = T; n.ls_E = E; n.ls_masks = masks; n.ls_c0 = c0;
+  return DDPPO_OK;
+}
+
+int net_lstm_backward(Net& n, const float* dy, float* dx, cudaStream_t s) {
+  if (!n.lstm_valid) {
+    set_error("lstm_backward without a preceding lstm_forward");
+    return DDPPO_E_STATE;
+  }
+  const int N = n.ls_T * n.ls_E;
+  DDPPO_CHECK_CUDA(cudaMemsetAsync(n.grad, 0, n.P * sizeof(float), s));
+  const float* dx0 = nullptr;
+  DDPPO_TRY(lstm_backward(n, n.ls_T, n.ls_E, n.ls_masks, n.ls_c0, dy, &dx0, s));
+  if (dx)
+    DDPPO_CHECK_CUDA(cudaMemcpyAsync(dx, dx0, (size_t)N * n.In0 * sizeof(float),
+                                     cudaMemcpyDeviceToDevice, s));
   return DDPPO_OK;
 }
 

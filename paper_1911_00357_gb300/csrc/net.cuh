@@ -75,6 +75,7 @@ struct Net {
   int pool_slot = -1;
   float* f8_scale = nullptr;   // [f8_slots] device: activation scales (delayed), weight scales
   unsigned* f8_amax = nullptr; // [f8_slots] device: absolute maxima (float bits)
+  float* f8_keep = nullptr;    // [2 f8_act_slots] activation scales / maxima kept aside
   int f8_act_slots = 0, f8_slots = 0;
   int kind = 0, H = 0, L = 0, inh = 0, inw = 0;
   int F = 0, featC = 0, featHW = 0;
@@ -145,6 +146,11 @@ struct Net {
   const void* ev_obs = nullptr; const float* ev_goal = nullptr; const int32_t* ev_preva = nullptr;
   const uint8_t* ev_masks = nullptr; const float* ev_h0 = nullptr; const float* ev_c0 = nullptr;
   int ev_valid_chunk = -1;
+  // last stand-alone encoder / LSTM forward (read again by their backward)
+  bool enc_valid = false, lstm_valid = false;
+  const void* enc_obs = nullptr; int enc_N = 0;
+  int ls_T = 0, ls_E = 0;
+  const uint8_t* ls_masks = nullptr; const float* ls_c0 = nullptr;
 
   // collect graph
   bool collect_started = false;

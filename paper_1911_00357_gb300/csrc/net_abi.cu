@@ -18,6 +18,11 @@ int net_forward(Net& n, int T, int E, const void* obs, const float* goal, const 
                 int32_t* action, float* logp, cudaStream_t s, bool infer = false);
 int net_backward(Net& n, const float* dlogits, const float* dvalues, cudaStream_t s);
 int net_prep_weights(Net& n, cudaStream_t s);
+int net_encoder_forward(Net& n, int N, const void* obs, float* feat, cudaStream_t s);
+int net_encoder_backward(Net& n, const float* dfeat, cudaStream_t s);
+int net_lstm_forward(Net& n, int T, int E, const float* x, const uint8_t* masks, const float* h0,
+                     const float* c0, float* y, cudaStream_t s);
+int net_lstm_backward(Net& n, const float* dy, float* dx, cudaStream_t s);
 }  // namespace ddppo
 
 using namespace ddppo;
@@ -129,6 +134,38 @@ extern "C" int ddppo_policy_backward(ddppo_ctx* x, const float* dlogits, const f
   cudaStream_t s = (cudaStream_t)stream;
   DDPPO_TRY(net_backward(n, dlogits, dvalues, s));
   DDPPO_CHECK_CUDA(cudaMemcpyAsync(grad, n.grad, n.P * 4, cudaMemcpyDeviceToDevice, s));
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_encoder_forward(ddppo_ctx* x, int32_t N, const void* obs, float* feat,
+                                     void* stream) {
+  ARG(x && x->net && obs && feat, "encoder_forward: null argument");
+  return net_encoder_forward(*x->net, N, obs, feat, (cudaStream_t)stream);
+}
+
+extern "C" int ddppo_encoder_backward(ddppo_ctx* x, const float* dfeat, float* grad, void* stream) {
+  ARG(x && x->net && dfeat && grad, "encoder_backward: null argument");
+  Net& n = *x->net;
+  cudaStream_t s = (cudaStream_t)stream;
+  DDPPO_TRY(net_encoder_backward(n, dfeat, s));
+  DDPPO_CHECK_CUDA(cudaMemcpyAsync(grad, n.grad, (size_t)n.P * 4, cudaMemcpyDeviceToDevice, s));
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_lstm_forward(ddppo_ctx* x, int32_t T, int32_t E, const float* in,
+                                  const uint8_t* masks, const float* h0, const float* c0, float* y,
+                                  void* stream) {
+  ARG(x && x->net && in && masks && h0 && c0 && y, "lstm_forward: null argument");
+  return net_lstm_forward(*x->net, T, E, in, masks, h0, c0, y, (cudaStream_t)stream);
+}
+
+extern "C" int ddppo_lstm_backward(ddppo_ctx* x, const float* dy, float* dx, float* grad,
+                                   void* stream) {
+  ARG(x && x->net && dy && grad, "lstm_backward: null argument");
+  Net& n = *x->net;
+  cudaStream_t s = (cudaStream_t)stream;
+  DDPPO_TRY(net_lstm_backward(n, dy, dx, s));
+  DDPPO_CHECK_CUDA(cudaMemcpyAsync(grad, n.grad, (size_t)n.P * 4, cudaMemcpyDeviceToDevice, s));
   return DDPPO_OK;
 }
 
@@ -372,9 +409,22 @@ extern "C" int ddppo_collect(ddppo_ctx* x, const ddppo_rollout* ro, int32_t use_
       // one act step outside the capture (state into scratch buffers) so that the GEMM
       // autotuner sees the act shapes before they are frozen into the graph
       if (n.gws.tuner) {
+        // the pass leaves no trace: FP8 inference's delayed activation scales are put back
+        // (a resumed run, whose first collect captures again, then matches an unbroken one)
+        const size_t fa = (size_t)n.f8_act_slots * 4;
+        if (n.f8) {
+          DDPPO_CHECK_CUDA(cudaMemcpyAsync(n.f8_keep, n.f8_scale, fa, cudaMemcpyDeviceToDevice, s));
+          DDPPO_CHECK_CUDA(cudaMemcpyAsync(n.f8_keep + n.f8_act_slots, n.f8_amax, fa,
+                                           cudaMemcpyDeviceToDevice, s));
+        }
         DDPPO_TRY(net_forward(n, 1, E, ro->obs, ro->goal, ro->prev_a, ro->masks, ro->h, ro->c,
                               ro->uniforms, (int32_t*)n.perm, n.dvalues, s, true));
         n.ev_valid = false;
+        if (n.f8) {
+          DDPPO_CHECK_CUDA(cudaMemcpyAsync(n.f8_scale, n.f8_keep, fa, cudaMemcpyDeviceToDevice, s));
+          DDPPO_CHECK_CUDA(cudaMemcpyAsync(n.f8_amax, n.f8_keep + n.f8_act_slots, fa,
+                                           cudaMemcpyDeviceToDevice, s));
+        }
       }
       if (n.graph_exec) { cudaGraphExecDestroy(n.graph_exec); n.graph_exec = nullptr; }
       DDPPO_CHECK_CUDA(cudaStreamSynchronize(s));

@@ -69,6 +69,20 @@ class Worker:
         B.ddppo_ppo_update(self.h, self.view, self.hp, self.stats)
         self.updates += 1
 
+    def save(self, path: str):
+        """Checkpoint the worker: the library's state (parameters, Adam, world, tuning
+        table, the rollout state carried into the next collect) in `path`, and the loop's
+        own counters (updates done, position in the uniform pool) in `path` + ".loop"."""
+        B.ddppo_save(self.h, path, self.view)
+        with open(path + ".loop", "w") as f:
+            f.write("%d %d\n" % (self.updates, self._k))
+
+    def load(self, path: str):
+        """Resume from a checkpoint of a worker with the same preset, seed and overrides."""
+        B.ddppo_load(self.h, path, self.view)
+        with open(path + ".loop") as f:
+            self.updates, self._k = (int(v) for v in f.read().split())
+
     def time_e2e(self, steps: int):
         """Steps through the public API with host buffers: each step copies its action
         uniforms host->device (pinned) and reads the PPO statistics, rewards and done flags
