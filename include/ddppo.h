@@ -89,6 +89,16 @@ typedef struct {
   int32_t minibatches;    /* PPO minibatches per epoch (E must divide evenly)                */
   int32_t encoder_chunk;  /* max frames per encoder pass in the update (0: min(all, 8192));
                              larger minibatches run in chunks, recomputed for the backward */
+  /* task (Sec. 5 "Transfer Learning"): the reward env_step returns. Motion, episodes (stop
+     or max_steps) and observations are the same for every task.
+       0 PointGoal: -delta geodesic to the goal - 0.01 per step, terminal bonus (Sec. 4);
+       1 Flee: r_t = 5 (D_t - D_t-1), D_t = Geo(s_t, s_0) / Max(s_0): the BFS geodesic from
+         the episode's start cell, Max(s_0) the largest one reachable from it;
+       2 Exploration: r_t = 0.25 (|Visited_t| - |Visited_t-1|), Visited_t the distinct
+         squares of side explore_m (the paper's 1 m cubes, on the floor) occupied so far,
+         the start's included. */
+  int32_t task;
+  float explore_m;        /* Exploration square side in metres (1.0)                        */
   uint64_t seed;          /* seeds the world (counter hash) and the initial weights          */
 } ddppo_config;
 

@@ -118,7 +118,7 @@ def lib():
         L.orc_batch_step.argtypes = [P, ctypes.c_int, P, P, P, P, P, P, P, P]
         L.orc_batch_render.argtypes = [P, ctypes.c_int, P, P, P, P]
         L.orc_flee_rewards.argtypes = [P, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P, P]
-        L.orc_explore_rewards.argtypes = [P, ctypes.c_int, P]
+        L.orc_explore_rewards.argtypes = [P, ctypes.c_int, ctypes.c_int, P]
     return _lib
 
 
@@ -207,13 +207,14 @@ def flee_rewards(grid: np.ndarray, cell_u: int, xy: np.ndarray) -> np.ndarray:
     return out
 
 
-def explore_rewards(xy: np.ndarray) -> np.ndarray:
+def explore_rewards(xy: np.ndarray, square_u: int = 10000) -> np.ndarray:
     """Exploration (Sec. 5 "Transfer Learning"): r_t = 0.25 (|Visited_t| - |Visited_t-1|) over
-    1 m squares. xy int [T+1, 2] positions in u; returns float32 [T]."""
+    squares of side square_u (1 m by default). xy int [T+1, 2] positions in u; returns
+    float32 [T]."""
     xy = np.ascontiguousarray(xy, np.int32)
     T = xy.shape[0] - 1
     out = np.zeros(max(T, 0), np.float32)
-    lib().orc_explore_rewards(_p(xy), T, _p(out))
+    lib().orc_explore_rewards(_p(xy), T, int(square_u), _p(out))
     return out
 
 

@@ -351,14 +351,15 @@ int orc_flee_rewards(const uint8_t* grid, int g, int cs, const int32_t* xy, int 
   return 0;
 }
 
-/* Exploration: Visited_t = the distinct 1 m squares (floor(p / 10000 u) on each axis) of
- * positions 0..t, the start included; r_t = 0.25 (|Visited_t| - |Visited_t-1|), exact in
- * FP32. Brute force over the earlier positions. */
-void orc_explore_rewards(const int32_t* xy, int T, float* rewards) {
+/* Exploration: Visited_t = the distinct squares of side sq u (the paper's 1 m cubes:
+ * sq = 10000; floor(p / sq) on each axis) of positions 0..t, the start included;
+ * r_t = 0.25 (|Visited_t| - |Visited_t-1|), exact in FP32. Brute force over the earlier
+ * positions. */
+void orc_explore_rewards(const int32_t* xy, int T, int sq, float* rewards) {
   for (int t = 1; t <= T; ++t) {
-    int qx = xy[2 * t] / 10000, qy = xy[2 * t + 1] / 10000, seen = 0;
+    int qx = xy[2 * t] / sq, qy = xy[2 * t + 1] / sq, seen = 0;
     for (int k = 0; k < t && !seen; ++k)
-      seen = xy[2 * k] / 10000 == qx && xy[2 * k + 1] / 10000 == qy;
+      seen = xy[2 * k] / sq == qx && xy[2 * k + 1] / sq == qy;
     rewards[t - 1] = seen ? 0.0f : 0.25f;
   }
 }

@@ -32,17 +32,22 @@ from . import binding as B
 
 
 class _Sync:
-    """Pushes a parameter tensor into a worker when it is not the one last pushed."""
+    """Pushes a parameter tensor into a worker when it is not the one last pushed. The last
+    pushed tensor is held, so that no new tensor can reuse its memory and pass for it."""
 
     def __init__(self):
         self._last = {}
 
     def __call__(self, h, params: torch.Tensor):
-        key = (params.data_ptr(), params._version)
         hk = h.value if hasattr(h, "value") else int(h)
-        if self._last.get(hk) != key:
+        last = self._last.get(hk)
+        if last is None or last[0] is not params or last[1] != params._version:
             B.ddppo_set_params(h, params.detach())
-            self._last[hk] = key
+            self._last[hk] = (params, params._version)
+
+    def forget(self, h):
+        """Drop the record of a worker (call before destroying it)."""
+        self._last.pop(h.value if hasattr(h, "value") else int(h), None)
 
 
 sync_params = _Sync()

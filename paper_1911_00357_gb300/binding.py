@@ -42,6 +42,7 @@ class Config(ctypes.Structure):
         ("hidden", ctypes.c_int32), ("lstm_layers", ctypes.c_int32),
         ("precision", ctypes.c_int32), ("rollout_T", ctypes.c_int32),
         ("minibatches", ctypes.c_int32), ("encoder_chunk", ctypes.c_int32),
+        ("task", ctypes.c_int32), ("explore_m", ctypes.c_float),
         ("seed", ctypes.c_uint64),
     ]
 

@@ -72,6 +72,9 @@ static int validate(const ddppo_config* c) {
   CFG_CHECK(c->minibatches >= 1 && c->num_envs % c->minibatches == 0,
             "minibatches must divide num_envs");
   CFG_CHECK(c->encoder_chunk >= 0, "encoder_chunk must be >= 0");
+  CFG_CHECK(c->task >= 0 && c->task <= 2, "task must be 0 (PointGoal), 1 (Flee) or 2 (Exploration)");
+  CFG_CHECK(c->task != 2 || (c->explore_m >= c->cell_m && c->explore_m <= 100.f),
+            "explore_m must be in [cell_m, 100]");
   return DDPPO_OK;
 }
 
@@ -104,6 +107,13 @@ static SimParams make_sim_params(const ddppo_config* c) {
                    ? (c->grid_max - 2) * (c->grid_max - 2) / (c->min_room * c->min_room) + 1
                    : 0;
   p.bf16_obs = c->precision >= 1;
+  p.task = c->task;
+  if (c->task == 2) {
+    p.explore_u = (int)llround((double)c->explore_m * 10000.0);
+    // squares per side: positions lie in [0, grid_max * cell_u)
+    p.vis_side = (c->grid_max * p.cell_u + p.explore_u - 1) / p.explore_u;
+    p.vis_words = (p.vis_side * p.vis_side + 31) / 32;
+  }
   return p;
 }
 
@@ -119,6 +129,7 @@ void ctx_free_world(ddppo_ctx* x) {
   cudaFree(x->sb.grids); cudaFree(x->sb.bits); cudaFree(x->sb.dists); cudaFree(x->sb.states);
   cudaFree(x->sb.pend); cudaFree(x->sb.slot); cudaFree(x->sb.ready);
   cudaFree(x->sb.segs); cudaFree(x->sb.need); cudaFree(x->sb.err); cudaFree(x->sb.work);
+  cudaFree(x->sb.tmax); cudaFree(x->sb.visited);
   if (x->ev_fork) cudaEventDestroy(x->ev_fork);
   if (x->ev_join) cudaEventDestroy(x->ev_join);
   if (x->side) cudaStreamDestroy(x->side);
@@ -158,6 +169,8 @@ extern "C" int ddppo_create(const ddppo_config* cfg, ddppo_ctx** out) {
       set_error("stream/event creation failed"); rc = DDPPO_E_CUDA; break;
     }
     if ((rc = dmalloc(&x->sb.segs, E * (size_t)x->sp.max_segs)) != DDPPO_OK) break;
+    if ((rc = dmalloc(&x->sb.tmax, cfg->task == 1 ? 2 * E : 0)) != DDPPO_OK) break;
+    if ((rc = dmalloc(&x->sb.visited, E * (size_t)x->sp.vis_words)) != DDPPO_OK) break;
     if ((rc = dmalloc(&x->sb.need, E)) != DDPPO_OK) break;
     if ((rc = dmalloc(&x->sb.err, 1)) != DDPPO_OK) break;
     if ((rc = dmalloc(&x->sb.work, 4)) != DDPPO_OK) break;

@@ -7,7 +7,8 @@
 // one:
 //   - the FP32 parameters, both Adam moments and the Adam step count;
 //   - the world: both scene slots of every env (grid, wall bits, BFS field), the agent
-//     states, the prepared next episodes (start state, slot index, ready flag);
+//     states, the prepared next episodes (start state, slot index, ready flag), and the
+//     transfer tasks' per-episode state (Flee's Max(s_0), Exploration's visited squares);
 //   - the delayed activation scales of FP8 inference;
 //   - the GEMM autotuner's table (a re-tuned table could choose split-K for a shape the
 //     saved run reduced in one pass, which changes the bits of the sums);
@@ -37,7 +38,8 @@ constexpr uint32_t kVersion = 1;
 enum : uint32_t {
   SEC_PARAMS = 1, SEC_ADAM_M, SEC_ADAM_V, SEC_ADAM_T, SEC_GRIDS, SEC_BITS, SEC_DISTS,
   SEC_STATES, SEC_PEND, SEC_SLOT, SEC_READY, SEC_FLAGS, SEC_F8_SCALE, SEC_F8_AMAX, SEC_TUNER,
-  SEC_RO_OBS, SEC_RO_GOAL, SEC_RO_PREVA, SEC_RO_MASKS, SEC_RO_H, SEC_RO_C, SEC_END = 0xFFFFFFFFu
+  SEC_RO_OBS, SEC_RO_GOAL, SEC_RO_PREVA, SEC_RO_MASKS, SEC_RO_H, SEC_RO_C, SEC_TMAX, SEC_VISITED,
+  SEC_END = 0xFFFFFFFFu
 };
 
 struct File {
@@ -135,6 +137,8 @@ extern "C" int ddppo_save(ddppo_ctx* x, const ddppo_rollout* ro, const char* pat
   DDPPO_TRY(put(f, SEC_PEND, x->sb.pend, z.E * ST_N * 4, true, s));
   DDPPO_TRY(put(f, SEC_SLOT, x->sb.slot, z.E, true, s));
   DDPPO_TRY(put(f, SEC_READY, x->sb.ready, z.E, true, s));
+  DDPPO_TRY(put(f, SEC_TMAX, x->sb.tmax, x->cfg.task == 1 ? 2 * z.E * 4 : 0, true, s));
+  DDPPO_TRY(put(f, SEC_VISITED, x->sb.visited, z.E * (size_t)x->sp.vis_words * 4, true, s));
   const int32_t flags[2] = {x->env_ready ? 1 : 0, n.collect_started ? 1 : 0};
   DDPPO_TRY(put(f, SEC_FLAGS, flags, sizeof(flags), false, s));
   DDPPO_TRY(put(f, SEC_F8_SCALE, n.f8_scale, (size_t)n.f8_slots * 4, true, s));
@@ -192,6 +196,8 @@ extern "C" int ddppo_load(ddppo_ctx* x, const ddppo_rollout* ro, const char* pat
   DDPPO_TRY(get(f, SEC_PEND, x->sb.pend, z.E * ST_N * 4, true, s));
   DDPPO_TRY(get(f, SEC_SLOT, x->sb.slot, z.E, true, s));
   DDPPO_TRY(get(f, SEC_READY, x->sb.ready, z.E, true, s));
+  DDPPO_TRY(get(f, SEC_TMAX, x->sb.tmax, x->cfg.task == 1 ? 2 * z.E * 4 : 0, true, s));
+  DDPPO_TRY(get(f, SEC_VISITED, x->sb.visited, z.E * (size_t)x->sp.vis_words * 4, true, s));
   int32_t flags[2] = {0, 0};
   DDPPO_TRY(get(f, SEC_FLAGS, flags, sizeof(flags), false, s));
   // the GEMM-layout (and E4M3) weight copies follow the loaded parameters; the FP8

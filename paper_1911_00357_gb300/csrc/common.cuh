@@ -31,6 +31,7 @@ void set_error(const std::string& msg);
 
 // sticky device error word: bit flags
 enum : int32_t { ERRF_BOUNDS = 1, ERRF_TIMEOUT = 2, ERRF_RESET = 4 };
+enum : int { TASK_POINTGOAL = 0, TASK_FLEE = 1, TASK_EXPLORE = 2 };
 
 // agent state slots (int32), same meaning as ddppo_env_state
 enum {
@@ -55,6 +56,9 @@ struct SimParams {
   int max_segs;
   int bf16_obs;
   int bfs_level_cap;  // 0: none (G + 1 levels); > 0: cap the BFS level loop (tests)
+  int task;           // 0 PointGoal, 1 Flee, 2 Exploration (the reward of env_step)
+  int explore_u;      // Exploration square side (u)
+  int vis_side, vis_words;  // Exploration squares per side, bitmap words per env
 };
 
 // Every env owns two scene slots: the current episode's and the next one's, which the
@@ -71,6 +75,8 @@ struct SimBuffers {
   uint8_t* need;      // [E] reset request
   int32_t* err;       // [1] sticky
   int32_t* work;      // [4] env-step and prefetch work counters + CTAs finished (self re-arming)
+  int32_t* tmax;      // [2, E] Flee: Max(s_0) (cells) of the episode in each scene slot
+  uint32_t* visited;  // [E, vis_words] Exploration: squares visited in the current episode
 };
 
 // host-side launchers (sim.cu)

@@ -305,6 +305,25 @@ __device__ void gen_episode(const SimParams& p, const SimBuffers& b, int e, int6
         st[ST_GRID] = g;
         st[ST_COLLIDED] = 0;
       }
+      if (p.task == TASK_FLEE) {
+        // Flee measures geodesics from the start: the slot's field becomes the BFS from
+        // the start cell (the goal field was needed only to draw the start), and Max(s_0)
+        // is its largest entry
+        const int si = s_sel;
+        __syncthreads();  // thread 0 has read the goal field for the start state
+        bfs_block(Fw, Vw, A, B, dist, g, si, b.err, p.bfs_level_cap);
+        __shared__ int s_mx;
+        if (tid == 0) s_mx = 0;
+        __syncthreads();
+        int mx = 0;
+        for (int i = tid; i < G; i += nt) mx = max(mx, dist[i]);
+        atomicMax(&s_mx, mx);
+        __syncthreads();
+        if (tid == 0) {
+          b.tmax[si_] = s_mx;
+          st[ST_GEO_PREV] = 0;
+        }
+      }
       return;
     }
   }
@@ -316,6 +335,20 @@ __device__ void gen_episode(const SimParams& p, const SimBuffers& b, int e, int6
     st[ST_PATH] = 0; st[ST_GEO_START] = 0; st[ST_GEO_PREV] = 0; st[ST_GOAL_X] = st[ST_X];
     st[ST_GOAL_Y] = st[ST_Y]; st[ST_EPISODE] = (int32_t)episode; st[ST_GRID] = g; st[ST_COLLIDED] = 0;
   }
+}
+
+// Exploration: the visited squares of env e's new episode are its start square alone
+__device__ void explore_begin(const SimParams& p, const SimBuffers& b, int e) {
+  if (p.task != TASK_EXPLORE) return;  // uniform over the block
+  uint32_t* vw = b.visited + (size_t)e * p.vis_words;
+  for (int w = threadIdx.x; w < p.vis_words; w += blockDim.x) vw[w] = 0u;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int32_t* st = b.states + (size_t)ST_N * e;
+    const int sq = (st[ST_Y] / p.explore_u) * p.vis_side + st[ST_X] / p.explore_u;
+    vw[sq >> 5] |= 1u << (sq & 31);
+  }
+  __syncthreads();
 }
 
 // the episode that follows env e's current one: the prepared slot when ready, else
@@ -337,6 +370,7 @@ __device__ void next_episode(const SimParams& p, const SimBuffers& b, int e, uin
     b.ready[e] = 0;
   }
   __syncthreads();
+  explore_begin(p, b, e);
 }
 
 __global__ void __launch_bounds__(RESET_THREADS) reset_kernel(SimParams p, SimBuffers b, int all) {
@@ -351,6 +385,7 @@ __global__ void __launch_bounds__(RESET_THREADS) reset_kernel(SimParams p, SimBu
       b.slot[e] = 0;
       b.ready[e] = 0;
     }
+    explore_begin(p, b, e);
   } else {
     next_episode(p, b, e, smem);
   }
@@ -434,6 +469,18 @@ __device__ int step_env(const SimParams& p, const SimBuffers& b, int e,
   else set_err(b.err, ERRF_BOUNDS);
   const int32_t geo_new = dcell * cs;
   int64_t r = (int64_t)st[ST_GEO_PREV] - geo_new - 100;
+  float task_r = 0.0f;
+  if (p.task == TASK_FLEE) {
+    // 5 (D_t - D_t-1) with D = Geo(s, s_0) / Max(s_0): in cells, one rounded division
+    const int32_t d0 = st[ST_GEO_PREV] / cs, mx = b.tmax[ci];
+    task_r = mx > 0 ? (float)((double)(5 * (dcell - d0)) / (double)mx) : 0.0f;
+  } else if (p.task == TASK_EXPLORE) {
+    uint32_t* vw = b.visited + (size_t)e * p.vis_words;
+    const int sq = (y / p.explore_u) * p.vis_side + x / p.explore_u;
+    const uint32_t bit = 1u << (sq & 31);
+    task_r = (vw[sq >> 5] & bit) ? 0.0f : 0.25f;
+    vw[sq >> 5] |= bit;
+  }
   const int64_t l = st[ST_GEO_START], pl = path, m = l > pl ? l : pl;
   if (success) {
     if (p.terminal_mode == 0) r += 25000;
@@ -442,7 +489,7 @@ __device__ int step_env(const SimParams& p, const SimBuffers& b, int e,
   if (!finished && steps >= p.max_steps) finished = 1;
   st[ST_X] = x; st[ST_Y] = y; st[ST_HEAD] = k; st[ST_STEPS] = steps; st[ST_PATH] = path;
   st[ST_GEO_PREV] = geo_new; st[ST_COLLIDED] = collided;
-  reward[e] = (float)r / 10000.0f;
+  reward[e] = p.task == TASK_POINTGOAL ? (float)r / 10000.0f : task_r;
   done[e] = (uint8_t)finished;
   b.need[e] = (uint8_t)finished;
   if (info) {

@@ -20,7 +20,7 @@ _BASE = dict(num_envs=16, gen_kind=0, grid_min=32, grid_max=32, cell_m=0.25, wal
              door_m=0.8, min_room=8, max_steps=500, terminal_mode=0, depth_h=64, depth_w=64,
              pool2x2=0, cam_h_m=0.88, ceil_h_m=2.5, max_depth_m=10.0, net_kind=0, base_ch=32,
              hidden=128, lstm_layers=1, precision=0, rollout_T=32, minibatches=2,
-             encoder_chunk=0, seed=0)
+             encoder_chunk=0, task=0, explore_m=1.0, seed=0)
 
 PRESETS = {
     "nature_fp32": dict(),

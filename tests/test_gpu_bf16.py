@@ -2,13 +2,22 @@
 
 The BF16 form rounds the operands of every contraction, and the output gradients that
 feed the backward contractions, to bfloat16 (8 significant bits); everything else is
-fp32. Against the plain float64 oracle that costs a few percent, much more in the
-encoder gradient, where ReLU masks and max-pool choices amplify it. So the GPU is pinned
-to tests/bf16_emu.py: the oracle's network with exactly those roundings, in float64.
-What remains between the GPU and the emulation is fp32 accumulation and the rare
-decision it flips; the bounds below are stated per quantity. Against float64 the GPU
-must stay within twice the emulation's own distance plus 1e-2 (the error the bf16
-roundings themselves cost), which catches a rounding added or dropped in the wrong place.
+fp32. tests/bf16_emu.py is the oracle's network with exactly those roundings, in
+float64. Against it:
+
+  - the 3-layer conv agent and the blind agent: the GPU reproduces the emulation to fp32
+    accuracy (outputs within 1e-5, gradients within 1e-5 / 3e-4 relative L2), so any
+    rounding added, dropped or moved in the contraction, FC, LSTM or head paths fails;
+  - the GroupNorm ResNet-18: a deep stack of bf16 roundings is a chaotic function of
+    fp32-level noise. Perturbing the emulation's parameters by one fp32 unit roundoff
+    (2^-24, relative) moves its logits by ~2e-3 and its encoder gradients by up to ~0.3
+    relative L2: every bf16 rounding an fp32 difference flips injects a 2^-9 jump, and
+    after a few layers the roundings of two computations that differ at fp32 level are
+    independent. No implementation can be closer to the emulation than that floor. The
+    test measures the floor (the emulation against itself under 2^-24 and 2^-22
+    perturbations) and bounds the GPU's distance to the emulation by twice it.
+Against float64 the GPU must stay within twice the emulation's own distance (the cost of
+the bf16 roundings) plus 1e-2.
 
 Checked: evaluate + backward on small and full-width nets (logits, values and every
 parameter tensor's gradient), and a whole ddppo_ppo_update (2 epochs x 2 minibatches of
@@ -29,11 +38,11 @@ from tests.test_gpu_policy import Net, _cfg, _dev_inputs, _rollout_tensors, _vie
 pytestmark = pytest.mark.gpu
 DT = torch.float64
 
-# GPU vs emulation
-TOL_OUT = 2e-3      # logits and values, relative to the tensor's largest magnitude
-TOL_GRAD = 2e-2     # relative L2 of every non-encoder parameter gradient
-TOL_GRAD_ENC = 5e-2  # relative L2 of every encoder parameter gradient (max over tensors)
-TOL_GRAD_ENC_MED = 1e-2  # ... and their median
+# non-chaotic nets (3-layer conv, blind): GPU vs emulation
+TOL_OUT = 1e-5       # logits and values, relative to the tensor's largest magnitude
+TOL_GRAD = 1e-5      # relative L2 of every non-encoder parameter gradient
+TOL_GRAD_ENC = 3e-4  # relative L2 of every encoder parameter gradient
+CHAOS_EPS = (2.0 ** -24, 2.0 ** -22)
 
 
 def _rel(a, b):
@@ -109,13 +118,31 @@ def test_bf16_evaluate_backward_vs_emulation(name, T, E, chunk):
         fmt = lambda d: {k: "%.2g" % v for k, v in d.items()}
         print("\n%s GPU vs emulation: out %s\n  encoder %s\n  rest %s" % (name, fmt(err), fmt(enc), fmt(rest)))
         print("  emulation vs float64 (bf16 cost): %s" % fmt(cost))
-        assert err["logits"] <= TOL_OUT and err["values"] <= TOL_OUT, err
-        worst = max(rest, key=rest.get)
-        assert rest[worst] <= TOL_GRAD, (worst, rest[worst])
-        if enc:
-            worst = max(enc, key=enc.get)
-            assert enc[worst] <= TOL_GRAD_ENC, (worst, enc[worst])
-            assert np.median(list(enc.values())) <= TOL_GRAD_ENC_MED
+        if net.ncfg.net_kind == 1:
+            # the chaos floor: the emulation against itself under fp32-level perturbations
+            floor = {}
+            for i, eps in enumerate(CHAOS_EPS):
+                noise = torch.randn(f64.shape, generator=torch.Generator().manual_seed(40 + i), dtype=DT)
+                lg_p, v_p, g_p = _forward_grad(EMU.sequence_forward, f64 * (1 + eps * noise), ref,
+                                               net.ncfg, dl.double(), dv.double())
+                gq = _per_tensor(net.ncfg, g_p)
+                cand = {"logits": _rel(lg_p, lg_e), "values": _rel(v_p, v_e)}
+                cand.update({k: _rel_l2(gq[k], ge[k]) for k in list(enc) + list(rest)})
+                floor = {k: max(floor.get(k, 0.0), v) for k, v in cand.items()}
+            print("  chaos floor (emulation vs itself): %s" % fmt(floor))
+            for k in ("logits", "values"):
+                assert err[k] <= 2 * floor[k] + 1e-4, (k, err[k], floor[k])
+            for grp in (enc, rest):
+                fl = [floor[k] for k in grp]
+                assert max(grp.values()) <= 2 * max(fl) + 1e-3, (max(grp.values()), max(fl))
+                assert np.median(list(grp.values())) <= 2 * np.median(fl) + 1e-3
+        else:
+            assert err["logits"] <= TOL_OUT and err["values"] <= TOL_OUT, err
+            worst = max(rest, key=rest.get)
+            assert rest[worst] <= TOL_GRAD, (worst, rest[worst])
+            if enc:
+                worst = max(enc, key=enc.get)
+                assert enc[worst] <= TOL_GRAD_ENC, (worst, enc[worst])
         for k in gpu64:
             assert gpu64[k] <= 2 * cost[k] + 1e-2, (k, gpu64[k], cost[k])
     finally:
@@ -125,11 +152,13 @@ def test_bf16_evaluate_backward_vs_emulation(name, T, E, chunk):
 @pytest.mark.parametrize("name,T,E", [("nature_small", 8, 4), ("resnet_small", 8, 4),
                                       ("resnet_full", 8, 4)])
 def test_bf16_ppo_update_vs_emulation(name, T, E):
-    """The whole BF16 update against oracle.rl.ppo_update through the emulation: every
-    parameter's change (Adam moves each coordinate by about lr per step) within 5% of
-    lr x steps, the per-minibatch loss within 1e-3 of its magnitude and the gradient norm
-    (before clipping) within 2%. The float64 update without the bf16 roundings is printed
-    beside it: its distance to the emulation is what the roundings cost."""
+    """The whole BF16 update against oracle.rl.ppo_update through the emulation.
+    3-layer conv agent: every parameter's change (Adam moves each coordinate by about lr
+    per step) within 5% of lr x steps, the per-minibatch loss within 1e-4 of its
+    magnitude, the gradient norm (before clipping) within 1e-3. ResNet agents (chaotic in
+    BF16, see above): the parameter change vector, the losses and the gradient norms
+    within twice the emulation's own distance to the float64 update (the bf16 cost) plus
+    a small absolute term."""
     mb = 2
     cfg = _cfg(name, E, T, 1, mb=mb)
     net = Net(cfg, seed=7)
@@ -158,17 +187,28 @@ def test_bf16_ppo_update_vs_emulation(name, T, E):
         unit = hp.lr * st_e
         e_par = (d_gpu - d_emu).abs().max().item() / unit
         c_par = (d_emu - d_64).abs().max().item() / unit
+        e_l2 = _rel_l2(d_gpu, d_emu)
+        c_l2 = _rel_l2(d_emu, d_64)
         s = stats.cpu().double()
-        e_loss = max(abs(s[k, 0].item() - st["loss"].item()) / max(1.0, abs(st["loss"].item()))
-                     for k, st in enumerate(sts_e))
+        rl = lambda a, b: abs(a - b) / max(1.0, abs(b))
+        e_loss = max(rl(s[k, 0].item(), st["loss"].item()) for k, st in enumerate(sts_e))
+        c_loss = max(rl(a["loss"].item(), b["loss"].item()) for a, b in zip(sts_e, sts_r))
         e_gn = max(abs(s[k, 6].item() - st["grad_norm"].item()) / st["grad_norm"].item()
                    for k, st in enumerate(sts_e))
         c_gn = max(abs(a["grad_norm"].item() - b["grad_norm"].item()) / b["grad_norm"].item()
                    for a, b in zip(sts_e, sts_r))
-        print("\n%s BF16 update vs emulation: param change %.3g of lr*steps, loss %.2g, grad norm %.2g;"
-              " emulation vs float64: param %.3g, grad norm %.2g" % (name, e_par, e_loss, e_gn, c_par, c_gn))
-        assert e_par <= 0.05, e_par
-        assert e_loss <= 1e-3, e_loss
-        assert e_gn <= 2e-2, e_gn
+        print("\n%s BF16 update vs emulation: param change max %.3g of lr*steps, rel L2 %.3g, loss "
+              "%.2g, grad norm %.2g; emulation vs float64: max %.3g, rel L2 %.3g, loss %.2g, grad "
+              "norm %.2g" % (name, e_par, e_l2, e_loss, e_gn, c_par, c_l2, c_loss, c_gn))
+        if net.ncfg.net_kind == 1:
+            assert e_l2 <= 2 * c_l2 + 1e-2, (e_l2, c_l2)
+            assert e_loss <= 2 * c_loss + 1e-4, (e_loss, c_loss)
+            assert e_gn <= 2 * c_gn + 1e-3, (e_gn, c_gn)
+        else:
+            assert e_par <= 0.05, e_par
+            assert e_loss <= 1e-4, e_loss
+            assert e_gn <= 1e-3, e_gn
+        # and against float64 itself: within twice the bf16 cost
+        assert _rel_l2(d_gpu, d_64) <= 2 * c_l2 + 1e-2
     finally:
         net.close()

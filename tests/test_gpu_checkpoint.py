@@ -90,8 +90,8 @@ def test_load_rejects_other_configuration_and_truncated_files(tmp_path):
     same = Worker("nature_fp32", seed=1, num_envs=4, rollout_T=4, minibatches=2)
     try:
         with pytest.raises(B.DDPPOError) as ei:
-            B.ddppo_load(same.h, path)  # written with rollout state
-        assert ei.value.code == -2
+            B.ddppo_load(same.h, path)  # written with rollout state: the view is required
+        assert ei.value.code == -1
         cut = str(tmp_path / "cut.bin")
         with open(path, "rb") as f:
             data = f.read()

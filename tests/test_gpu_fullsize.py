@@ -7,9 +7,11 @@ GAE, 2 x 2 PPO update). Checked on outputs the oracle can compute one by one:
   * the whole trajectory: the oracle world re-stepped with the collected actions gives
     bit-identical rewards and dones for every (t, env);
   * the observation of sampled frames: oracle depth, pooled and normalised;
-  * the policy on sampled envs: the oracle's float64 forward over each env's full
-    128-step sequence reproduces the stored log-probabilities (within 5e-2) and values
-    (within 0.1 of their largest magnitude): the BF16 bounds;
+  * the policy on sampled envs: over each env's full 128-step sequence, the stored
+    log-probabilities and values are within twice the distance of a float64 emulation of
+    the BF16 roundings (tests/bf16_emu.py) to the float64 oracle, plus 1e-2: the BF16
+    ResNet is chaotic at fp32 noise level, so its distance to float64 is set by the bf16
+    roundings themselves, which the emulation measures;
   * GAE on the stored rewards/values: float64 recursion within 1e-5 relative.
 """
 import numpy as np
@@ -21,6 +23,7 @@ from oracle import rl as OR
 from oracle import sim as OS
 from paper_1911_00357_gb300 import binding as B
 from paper_1911_00357_gb300.worker import Worker
+from tests import bf16_emu as EMU
 from tests.gpu_util import net_config_from, sim_config_from
 
 pytestmark = pytest.mark.gpu
@@ -58,17 +61,25 @@ def test_full_size_sampled_parity():
         ncfg = net_config_from(cfg)
         p = OP.unflatten(flat.cpu().double(), ncfg)
         envs = [0, 37]
-        with torch.no_grad():
-            lg, v, _, _ = OP.sequence_forward(
-                p, t["obs"][:T, envs].double(), t["goal"][:T, envs].double(), t["prev_a"][:T, envs],
+        args = (p, t["obs"][:T, envs].double(), t["goal"][:T, envs].double(), t["prev_a"][:T, envs],
                 t["masks"][:T, envs], t["h0"][:, envs].double(), t["c0"][:, envs].double(), ncfg)
-            lp = torch.log_softmax(lg, -1).gather(2, t["actions"][:, envs].long().unsqueeze(2))[..., 0]
-        err_lp = (lp - t["logp"][:, envs].double()).abs().max().item()
-        err_v = (v - t["values"][:T, envs].double()).abs().max().item() / max(v.abs().max().item(), 1e-3)
-        # BF16 GEMM operands: a few percent of the output scale (the critic's outputs are
-        # small at initialisation, so the value bound is relative to their largest magnitude)
-        assert err_lp <= 5e-2 * max(1.0, lp.abs().max().item()), err_lp
-        assert err_v <= 1e-1, err_v
+        act = t["actions"][:, envs].long().unsqueeze(2)
+        with torch.no_grad():
+            lg, v, _, _ = OP.sequence_forward(*args)
+            lg_e, v_e, _, _ = EMU.sequence_forward(*args)
+        lp = torch.log_softmax(lg, -1).gather(2, act)[..., 0]
+        lp_e = torch.log_softmax(lg_e, -1).gather(2, act)[..., 0]
+        lp_g, v_g = t["logp"][:, envs].double(), t["values"][:T, envs].double()
+        scale_lp = max(1.0, lp.abs().max().item())
+        scale_v = max(v.abs().max().item(), 1e-3)
+        err_lp = (lp_g - lp).abs().max().item() / scale_lp
+        err_v = (v_g - v).abs().max().item() / scale_v
+        cost_lp = (lp_e - lp).abs().max().item() / scale_lp
+        cost_v = (v_e - v).abs().max().item() / scale_v
+        print("full size: logp err %.3g (bf16 emulation %.3g), value err %.3g (emulation %.3g)"
+              % (err_lp, cost_lp, err_v, cost_v))
+        assert err_lp <= 2 * cost_lp + 1e-2, (err_lp, cost_lp)
+        assert err_v <= 2 * cost_v + 1e-2, (err_v, cost_v)
         # 4. GAE of this rollout
         A_ref, R_ref = OR.gae(t["rewards"].numpy(), t["dones"].numpy(), t["values"].numpy(), 0.99, 0.95)
         assert np.all(np.abs(t["adv"].numpy() - A_ref) <= 1e-5 * np.maximum(1.0, np.abs(A_ref)))

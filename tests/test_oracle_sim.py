@@ -556,3 +556,14 @@ def test_exploration_total_counts_distinct_squares():
     assert float(r.astype(np.float64).sum()) == 0.25 * (len(squares) - 1)
     still = np.tile(np.array([[12345, 61234]], np.int32), (9, 1)) + rng.integers(0, 5000, (9, 2)).astype(np.int32)
     assert not S.explore_rewards(still).any()
+
+
+def test_exploration_square_side_is_a_parameter():
+    # 0.5 m squares: from x = 0.125 m in 0.25 m steps the walk enters a new square every
+    # second step (x = 0.625, 1.125, ... m); the total still counts distinct squares
+    steps = [(1, 0)] * 8
+    r = S.explore_rewards(_walk(1250, 1250, steps), square_u=5000)
+    want = np.zeros(8, np.float32)
+    want[[1, 3, 5, 7]] = 0.25
+    assert r.tolist() == want.tolist()
+    assert S.explore_rewards(_walk(1250, 1250, steps)).tolist() == [0, 0, 0, 0.25, 0, 0, 0, 0.25]
