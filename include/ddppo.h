@@ -359,6 +359,47 @@ int ddppo_ppo_update(ddppo_ctx* ctx, const ddppo_rollout* ro, const ddppo_ppo_hp
  * capturable). */
 int ddppo_collect(ddppo_ctx* ctx, const ddppo_rollout* ro, int32_t use_graph, void* stream);
 
+/* ---- DD-PPO workers: step-wise collection with preemption, exchanged gradients ----- */
+
+/* The collection stage one step at a time, for workers whose collection can be preempted
+ * (Sec. 3: once p% of the workers have finished their rollout, the stragglers' collection
+ * ends early, but not before one quarter of the rollout length). collect_begin is
+ * ddppo_collect's prologue: slot 0 <- the previous collection's last slot (slot T, or
+ * T_valid after a preempted one; the first call resets the world), h0/c0 <- h/c.
+ * collect_step(t), for t = 0, 1, ... in order (t < rollout_T): act on slot t, env_step,
+ * slot t + 1 (the next episodes prepared on the side stream meanwhile). collect_end
+ * writes the bootstrap value of slot T_valid, T_valid = the steps taken (>= 1); a
+ * following ddppo_collect or collect_begin continues from that slot. Launches directly
+ * (no graph). The results of begin + rollout_T steps + end equal ddppo_collect's.
+ * Errors: E_ARG (null argument or buffer), E_STATE (steps out of order, T_valid wrong). */
+int ddppo_collect_begin(ddppo_ctx* ctx, const ddppo_rollout* ro, void* stream);
+int ddppo_collect_step(ddppo_ctx* ctx, const ddppo_rollout* ro, int32_t t, void* stream);
+int ddppo_collect_end(ddppo_ctx* ctx, const ddppo_rollout* ro, int32_t T_valid, void* stream);
+
+/* The update one minibatch at a time, for workers that exchange gradients (Eq. 4:
+ * theta <- ParamUpdate(theta, AllReduce(grad_1, ..., grad_N)), the mean over workers).
+ * ddppo_ppo_grad: the gradient of minibatch k (0 <= k < minibatches) of epoch `epoch` of
+ * an update with hp->update_index -- the same envs, replay, loss and hand-written
+ * backward as ddppo_ppo_update -- over the first T_valid steps of the rollout (a
+ * preempted worker's shorter rollout; its loss is the mean over its own samples, so every
+ * worker weighs equally, as Sec. 3 states). grad [dev] [n_params] receives the unclipped
+ * gradient; stats [dev] [DDPPO_NSTATS] (NULL ok) the loss statistics. ro->adv/ret must
+ * hold GAE over the same T_valid steps (ddppo_gae with T = T_valid).
+ * ddppo_apply_grad: ParamUpdate with grad [dev] [n_params] times `scale` (1/N for a sum
+ * over N workers): global-norm clip, one Adam step (the worker's step count + 1), the
+ * GEMM-layout weights refreshed; stats [dev] (NULL ok) receives the norm in slot 6.
+ * Calling ppo_grad and apply_grad (scale 1) for every epoch and minibatch in order gives
+ * ddppo_ppo_update's parameters bit for bit.
+ * ddppo_grad_mean: out [dev] [len] = (1/n) sum_r bufs[r] [dev] [len], summed in the order
+ * r = 0 .. n-1 (deterministic): the AllReduce of workers that share a GPU; bufs [host]
+ * holds n <= 64 device pointers. Errors: E_ARG, E_CONFIG (shapes), E_CUDA. */
+int ddppo_ppo_grad(ddppo_ctx* ctx, const ddppo_rollout* ro, const ddppo_ppo_hparams* hp,
+                   int32_t T_valid, int32_t epoch, int32_t k, float* grad, float* stats,
+                   void* stream);
+int ddppo_apply_grad(ddppo_ctx* ctx, const float* grad, float scale, const ddppo_ppo_hparams* hp,
+                     float* stats, void* stream);
+int ddppo_grad_mean(int32_t n, const float* const* bufs, int64_t len, float* out, void* stream);
+
 /* ---- checkpoint / resume ---------------------------------------------------------- */
 
 /* Write / read a worker's whole learning state to / from the file `path` [host], so that

@@ -23,6 +23,9 @@ Pins (independent of the formulas here; a plausible mistake fails the named test
   clip_grad_norm      3-4-5 closed form; below-threshold identity
   adam_step           first two bias-corrected steps in closed form; a quadratic's minimum
   ppo_update          one minibatch = one clipped Adam step on the permuted envs
+  dd_ppo_update       one worker = ppo_update; the mean of equal-sized workers' gradients =
+                      the gradient of the loss over the union of their minibatches
+                      (tests/test_oracle_pins_loss.py)
 """
 from __future__ import annotations
 
@@ -153,3 +156,50 @@ def ppo_update(flat, m, v, step, ro, ncfg, hp: PPOHParams, seed: int, update: in
             flat, m, v = adam_step(flat.detach(), g, m, v, step, hp)
             all_stats.append(stats)
     return flat, m, v, step, all_stats
+
+
+def dd_ppo_update(flat, m, v, step, rollouts, ncfg, hp: PPOHParams, seeds, update: int,
+                  T_valid=None):
+    """DD-PPO's update across N workers (Sec. 3, Eq. 4): at every minibatch step each worker
+    n computes the PPO gradient of its own minibatch (its own envs, permuted by its own
+    seed), the gradients are averaged (AllReduce with the mean), and every worker applies
+    the same clipped Adam step, so all parameter copies stay equal.
+
+    rollouts: one dict per worker as for ppo_update; seeds: the workers' seeds; T_valid:
+    per worker, the steps of its rollout that count (a preempted straggler's shorter
+    rollout: its loss is the mean over its own samples, each worker weighing equally).
+    Returns (flat, m, v, step, per-step list of per-worker stats, per-step mean gradients).
+    """
+    N = len(rollouts)
+    Tv = [ro["actions"].shape[0] for ro in rollouts] if T_valid is None else list(T_valid)
+    all_stats, grads_out = [], []
+    for e in range(hp.epochs):
+        perms = [torch.from_numpy(S.env_permutation(seeds[n], update, e, rollouts[n]["actions"].shape[1])
+                                  .astype(np.int64)) for n in range(N)]
+        for k in range(hp.minibatches):
+            grads, stats = [], []
+            for n, ro in enumerate(rollouts):
+                E = ro["actions"].shape[1]
+                Emb = E // hp.minibatches
+                idx = perms[n][k * Emb:(k + 1) * Emb]
+                T = Tv[n]
+                adv = ro["adv"][:T]
+                if hp.norm_adv:
+                    adv = (adv - adv.mean()) / (adv.std(unbiased=False) + 1e-5)
+                mb = {key: ro[key][:T, idx] for key in ("obs", "goal", "prev_a", "masks", "actions",
+                                                        "logp_old", "ret")}
+                mb["adv"] = adv[:, idx]
+                mb["h0"] = ro["h0"][:, idx]
+                mb["c0"] = ro["c0"][:, idx]
+                _, st, g = minibatch_loss_and_grad(flat, mb, ncfg, hp)
+                grads.append(g)
+                stats.append(st)
+            g = sum(grads) / N                 # AllReduce(mean)
+            grads_out.append(g)
+            g, gn = clip_grad_norm(g, hp.max_grad_norm)
+            for st in stats:
+                st["grad_norm"] = gn
+            step += 1
+            flat, m, v = adam_step(flat.detach(), g, m, v, step, hp)
+            all_stats.append(stats)
+    return flat, m, v, step, all_stats, grads_out

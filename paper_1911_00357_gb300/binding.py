@@ -110,6 +110,12 @@ _SIGS = {
     "ddppo_ppo_loss_static": [I32, P, P, P, P, P, P, F32, F32, F32, P, P, P, P],
     "ddppo_ppo_update": [P, P, P, P, P],
     "ddppo_collect": [P, P, I32, P],
+    "ddppo_collect_begin": [P, P, P],
+    "ddppo_collect_step": [P, P, I32, P],
+    "ddppo_collect_end": [P, P, I32, P],
+    "ddppo_ppo_grad": [P, P, P, I32, I32, I32, P, P, P],
+    "ddppo_apply_grad": [P, P, F32, P, P, P],
+    "ddppo_grad_mean": [I32, P, I64, P, P],
     "ddppo_save": [P, P, ctypes.c_char_p, P],
     "ddppo_load": [P, P, ctypes.c_char_p, P],
     "ddppo_timing_enable": [P, I32],
@@ -311,6 +317,34 @@ def ddppo_ppo_update(h, ro: Rollout, hp: PPOHParams, stats=None):
 
 def ddppo_collect(h, ro: Rollout, use_graph: bool = True):
     _check(lib().ddppo_collect(h, ctypes.byref(ro), 1 if use_graph else 0, _s()))
+
+
+def ddppo_collect_begin(h, ro: Rollout, stream=None):
+    _check(lib().ddppo_collect_begin(h, ctypes.byref(ro), _s(stream)))
+
+
+def ddppo_collect_step(h, ro: Rollout, t: int, stream=None):
+    _check(lib().ddppo_collect_step(h, ctypes.byref(ro), t, _s(stream)))
+
+
+def ddppo_collect_end(h, ro: Rollout, T_valid: int, stream=None):
+    _check(lib().ddppo_collect_end(h, ctypes.byref(ro), T_valid, _s(stream)))
+
+
+def ddppo_ppo_grad(h, ro: Rollout, hp: PPOHParams, T_valid: int, epoch: int, k: int, grad,
+                   stats=None, stream=None):
+    _check(lib().ddppo_ppo_grad(h, ctypes.byref(ro), ctypes.byref(hp), T_valid, epoch, k, _p(grad),
+                                _p(stats), _s(stream)))
+
+
+def ddppo_apply_grad(h, grad, scale: float, hp: PPOHParams, stats=None, stream=None):
+    _check(lib().ddppo_apply_grad(h, _p(grad), scale, ctypes.byref(hp), _p(stats), _s(stream)))
+
+
+def ddppo_grad_mean(bufs, out, stream=None):
+    """out = mean of the equally sized CUDA tensors in bufs (fixed summation order)."""
+    arr = (ctypes.c_void_p * len(bufs))(*[b.data_ptr() for b in bufs])
+    _check(lib().ddppo_grad_mean(len(bufs), arr, out.numel(), _p(out), _s(stream)))
 
 
 def ddppo_save(h, path: str, ro: Rollout | None = None):

@@ -139,7 +139,7 @@ extern "C" int ddppo_save(ddppo_ctx* x, const ddppo_rollout* ro, const char* pat
   DDPPO_TRY(put(f, SEC_READY, x->sb.ready, z.E, true, s));
   DDPPO_TRY(put(f, SEC_TMAX, x->sb.tmax, x->cfg.task == 1 ? 2 * z.E * 4 : 0, true, s));
   DDPPO_TRY(put(f, SEC_VISITED, x->sb.visited, z.E * (size_t)x->sp.vis_words * 4, true, s));
-  const int32_t flags[2] = {x->env_ready ? 1 : 0, n.collect_started ? 1 : 0};
+  const int32_t flags[3] = {x->env_ready ? 1 : 0, n.collect_started ? 1 : 0, n.T_last};
   DDPPO_TRY(put(f, SEC_FLAGS, flags, sizeof(flags), false, s));
   DDPPO_TRY(put(f, SEC_F8_SCALE, n.f8_scale, (size_t)n.f8_slots * 4, true, s));
   DDPPO_TRY(put(f, SEC_F8_AMAX, n.f8_amax, (size_t)n.f8_slots * 4, true, s));
@@ -198,7 +198,7 @@ extern "C" int ddppo_load(ddppo_ctx* x, const ddppo_rollout* ro, const char* pat
   DDPPO_TRY(get(f, SEC_READY, x->sb.ready, z.E, true, s));
   DDPPO_TRY(get(f, SEC_TMAX, x->sb.tmax, x->cfg.task == 1 ? 2 * z.E * 4 : 0, true, s));
   DDPPO_TRY(get(f, SEC_VISITED, x->sb.visited, z.E * (size_t)x->sp.vis_words * 4, true, s));
-  int32_t flags[2] = {0, 0};
+  int32_t flags[3] = {0, 0, 0};
   DDPPO_TRY(get(f, SEC_FLAGS, flags, sizeof(flags), false, s));
   // the GEMM-layout (and E4M3) weight copies follow the loaded parameters; the FP8
   // activation scales are restored after, since the weight preparation leaves them alone
@@ -234,6 +234,7 @@ extern "C" int ddppo_load(ddppo_ctx* x, const ddppo_rollout* ro, const char* pat
   n.adam_t = adam_t;
   x->env_ready = flags[0] != 0;
   n.collect_started = flags[1] != 0 && has_ro;
+  n.T_last = flags[2];
   n.ev_valid = false;
   return DDPPO_OK;
 }

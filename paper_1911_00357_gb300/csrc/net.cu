@@ -361,6 +361,7 @@ int net_create(ddppo_ctx* x) {
   n.L = c.lstm_layers;
   n.E = c.num_envs;
   n.T = c.rollout_T;
+  n.T_last = c.rollout_T;
   n.Emb = c.num_envs / c.minibatches;
   n.NS = std::max(n.T * n.Emb, n.E);
   // encoder pass size: the whole minibatch when it fits the automatic cap (8192 frames,

@@ -154,6 +154,8 @@ struct Net {
 
   // collect graph
   bool collect_started = false;
+  int T_last = 0;      // valid steps of the last collection (its last slot is carried over)
+  int step_next = -1;  // step-wise collection: the next step index (-1: none begun)
   cudaGraphExec_t graph_exec = nullptr;
   ddppo_rollout graph_ro{};
   // captured PPO update: replayed while its rollout view, statistics buffer and

@@ -233,6 +233,112 @@ static int update_body(ddppo_ctx* x, const ddppo_rollout* ro, const ddppo_ppo_hp
   return DDPPO_OK;
 }
 
+// ---- the update one minibatch at a time (gradients exchanged between workers, Eq. 4) ----
+__global__ void scale_copy_kernel(const float* __restrict__ g, float scale, float* __restrict__ out,
+                                  size_t n) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x)
+    out[i] = scale * g[i];
+}
+
+extern "C" int ddppo_ppo_grad(ddppo_ctx* x, const ddppo_rollout* ro, const ddppo_ppo_hparams* hp,
+                              int32_t T_valid, int32_t epoch, int32_t k, float* grad, float* stats,
+                              void* stream) {
+  ARG(x && x->net && ro && hp && grad, "ppo_grad: null argument");
+  ARG(ro->obs && ro->goal && ro->prev_a && ro->masks && ro->actions && ro->logp && ro->adv &&
+          ro->ret && ro->h0 && ro->c0,
+      "ppo_grad: rollout view has a null buffer");
+  Net& n = *x->net;
+  const ddppo_config& c = x->cfg;
+  if (hp->minibatches != c.minibatches || epoch < 0 || epoch >= hp->epochs || k < 0 ||
+      k >= hp->minibatches || T_valid < 1 || T_valid > c.rollout_T) {
+    set_error("ppo_grad: minibatches must equal the config's, 0 <= epoch < epochs, "
+              "0 <= k < minibatches, 1 <= T_valid <= rollout_T");
+    return DDPPO_E_CONFIG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int E = c.num_envs, Emb = n.Emb, L = n.L, Hd = n.H, T = T_valid;
+  set_steps_kernel<<<1, 1, 0, s>>>(n.d_steps, hp->update_index, n.adam_t);
+  DDPPO_CHECK_LAUNCH();
+  const float* adv = ro->adv;
+  if (hp->norm_adv) {
+    DDPPO_TRY(launch_normalize_adv(ro->adv, n.adv_norm, (size_t)T * E, n.scal, n.scratch,
+                                   n.scratch_elems, s));
+    adv = n.adv_norm;
+  }
+  DDPPO_TRY(launch_permutation(c.seed, n.d_steps, epoch, E, n.perm, s));
+  const int32_t* idx = n.perm + (size_t)k * Emb;
+  DDPPO_TRY(launch_gather_rows(ro->obs, n.obs_mb, idx, T, E, Emb, n.pix * op_bytes(n), s));
+  DDPPO_TRY(launch_gather_rows(ro->goal, n.goal_mb, idx, T, E, Emb, 12, s));
+  DDPPO_TRY(launch_gather_rows(ro->prev_a, n.preva_mb, idx, T, E, Emb, 4, s));
+  DDPPO_TRY(launch_gather_rows(ro->masks, n.masks_mb, idx, T, E, Emb, 1, s));
+  DDPPO_TRY(launch_gather_rows(ro->actions, n.act_mb, idx, T, E, Emb, 4, s));
+  DDPPO_TRY(launch_gather_rows(ro->logp, n.logp_mb, idx, T, E, Emb, 4, s));
+  DDPPO_TRY(launch_gather_rows(adv, n.adv_mb, idx, T, E, Emb, 4, s));
+  DDPPO_TRY(launch_gather_rows(ro->ret, n.ret_mb, idx, T, E, Emb, 4, s));
+  DDPPO_TRY(launch_gather_rows(ro->h0, n.h0_mb, idx, L, E, Emb, (size_t)Hd * 4, s));
+  DDPPO_TRY(launch_gather_rows(ro->c0, n.c0_mb, idx, L, E, Emb, (size_t)Hd * 4, s));
+  DDPPO_TRY(net_forward(n, T, Emb, n.obs_mb, n.goal_mb, n.preva_mb, n.masks_mb, n.h0_mb, n.c0_mb,
+                        nullptr, nullptr, nullptr, s));
+  float* st = stats ? stats : n.stats_tmp;
+  DDPPO_TRY(launch_ppo_loss(T * Emb, n.logits, n.values, n.act_mb, n.logp_mb, n.adv_mb, n.ret_mb,
+                            hp->clip, hp->value_coef, hp->entropy_coef, st, n.dlogits, n.dvalues,
+                            n.scratch, n.scratch_elems, s));
+  DDPPO_TRY(net_backward(n, n.dlogits, n.dvalues, s));
+  DDPPO_CHECK_CUDA(cudaMemcpyAsync(grad, n.grad, (size_t)n.P * 4, cudaMemcpyDeviceToDevice, s));
+  n.ev_valid = false;
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_apply_grad(ddppo_ctx* x, const float* grad, float scale,
+                                const ddppo_ppo_hparams* hp, float* stats, void* stream) {
+  ARG(x && x->net && grad && hp, "apply_grad: null argument");
+  Net& n = *x->net;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t P = (size_t)n.P;
+  scale_copy_kernel<<<(unsigned)std::min<size_t>((P + 255) / 256, 4096), 256, 0, s>>>(grad, scale,
+                                                                                     n.grad, P);
+  DDPPO_CHECK_LAUNCH();
+  DDPPO_TRY(launch_grad_norm(n.grad, P, n.norm, n.scratch, n.scratch_elems, s));
+  if (stats) DDPPO_TRY(launch_copy_scalar(stats + 6, n.norm, s));
+  set_steps_kernel<<<1, 1, 0, s>>>(n.d_steps, hp->update_index, n.adam_t);
+  DDPPO_CHECK_LAUNCH();
+  DDPPO_TRY(launch_adam(n.params, n.grad, n.adam_m, n.adam_v, P,
+                        hp->max_grad_norm > 0.f ? n.norm : nullptr, hp->max_grad_norm, hp->lr,
+                        hp->beta1, hp->beta2, hp->adam_eps, n.d_steps + 1, 1, s));
+  DDPPO_TRY(net_prep_weights(n, s));
+  n.adam_t += 1;
+  return DDPPO_OK;
+}
+
+constexpr int kMeanMax = 64;
+struct MeanArgs {
+  const float* p[kMeanMax];
+};
+__global__ void grad_mean_kernel(MeanArgs a, int nb, size_t len, float* __restrict__ out) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (size_t)gridDim.x * blockDim.x) {
+    float acc = 0.f;
+    for (int r = 0; r < nb; ++r) acc += a.p[r][i];  // fixed order: worker 0 first
+    out[i] = acc / (float)nb;
+  }
+}
+
+extern "C" int ddppo_grad_mean(int32_t n, const float* const* bufs, int64_t len, float* out,
+                               void* stream) {
+  ARG(n >= 1 && n <= kMeanMax && len >= 0 && bufs && out, "grad_mean: bad arguments");
+  if (len == 0) return DDPPO_OK;
+  MeanArgs a{};
+  for (int r = 0; r < n; ++r) {
+    ARG(bufs[r] != nullptr, "grad_mean: null buffer");
+    a.p[r] = bufs[r];
+  }
+  grad_mean_kernel<<<(unsigned)std::min<int64_t>((len + 255) / 256, 4096), 256, 0,
+                     (cudaStream_t)stream>>>(a, n, (size_t)len, out);
+  DDPPO_CHECK_LAUNCH();
+  return DDPPO_OK;
+}
+
 static bool same_hparams(const ddppo_ppo_hparams& a, const ddppo_ppo_hparams& b) {
   ddppo_ppo_hparams x = a, y = b;
   x.update_index = 0;
@@ -372,27 +478,22 @@ static int collect_body(ddppo_ctx* x, const ddppo_rollout* ro, cudaStream_t s) {
   return DDPPO_OK;
 }
 
-extern "C" int ddppo_collect(ddppo_ctx* x, const ddppo_rollout* ro, int32_t use_graph,
-                             void* stream) {
-  ARG(x && x->net && ro, "collect: null argument");
-  ARG(ro->obs && ro->goal && ro->prev_a && ro->masks && ro->actions && ro->logp && ro->values &&
-          ro->rewards && ro->dones && ro->h0 && ro->c0 && ro->h && ro->c && ro->uniforms,
-      "collect: rollout view has a null buffer");
+// prologue of a collection: slot 0 is the previous rollout's last slot (slot T, or the
+// preempted length of a step-wise collection; first call: reset everything), h0/c0 <- h/c
+static int collect_prologue(ddppo_ctx* x, const ddppo_rollout* ro, cudaStream_t s) {
   Net& n = *x->net;
-  cudaStream_t s = (cudaStream_t)stream;
-  const int E = x->cfg.num_envs, T = x->cfg.rollout_T, L = n.L, Hd = n.H;
+  const int E = x->cfg.num_envs, L = n.L, Hd = n.H;
   const size_t ob = n.pix * op_bytes(n);
   const size_t st_bytes = (size_t)L * E * Hd * 4;
-  // prologue: slot 0 is the previous rollout's slot T (first call: reset everything)
   if (!n.collect_started || !x->env_ready) {
-    DDPPO_TRY(ddppo_env_reset(x, ro->obs, ro->goal, stream));
+    DDPPO_TRY(ddppo_env_reset(x, ro->obs, ro->goal, s));
     start_slot_kernel<<<(E + 127) / 128, 128, 0, s>>>(E, ro->prev_a, ro->masks);
     DDPPO_CHECK_LAUNCH();
     DDPPO_CHECK_CUDA(cudaMemsetAsync(ro->h, 0, st_bytes, s));
     DDPPO_CHECK_CUDA(cudaMemsetAsync(ro->c, 0, st_bytes, s));
     n.collect_started = true;
   } else {
-    const size_t oT = (size_t)T * E;
+    const size_t oT = (size_t)n.T_last * E;
     DDPPO_CHECK_CUDA(cudaMemcpyAsync(ro->obs, (const char*)ro->obs + oT * ob, (size_t)E * ob,
                                      cudaMemcpyDeviceToDevice, s));
     DDPPO_CHECK_CUDA(cudaMemcpyAsync(ro->goal, ro->goal + oT * 3, (size_t)E * 12,
@@ -404,6 +505,90 @@ extern "C" int ddppo_collect(ddppo_ctx* x, const ddppo_rollout* ro, int32_t use_
   }
   DDPPO_CHECK_CUDA(cudaMemcpyAsync(ro->h0, ro->h, st_bytes, cudaMemcpyDeviceToDevice, s));
   DDPPO_CHECK_CUDA(cudaMemcpyAsync(ro->c0, ro->c, st_bytes, cudaMemcpyDeviceToDevice, s));
+  return DDPPO_OK;
+}
+
+// bootstrap value V(o_Tv) with the state after step Tv - 1; the state itself is not advanced
+static int collect_bootstrap(ddppo_ctx* x, const ddppo_rollout* ro, int Tv, cudaStream_t s) {
+  Net& n = *x->net;
+  const int E = x->cfg.num_envs;
+  const size_t ob = n.pix * op_bytes(n);
+  const size_t oT = (size_t)Tv * E;
+  DDPPO_TRY(net_forward(n, 1, E, (const char*)ro->obs + oT * ob, ro->goal + oT * 3,
+                        ro->prev_a + oT, ro->masks + oT, ro->h, ro->c, nullptr, nullptr, nullptr, s,
+                        true));
+  DDPPO_CHECK_CUDA(cudaMemcpyAsync(ro->values + oT, n.values, (size_t)E * 4,
+                                   cudaMemcpyDeviceToDevice, s));
+  n.ev_valid = false;
+  n.T_last = Tv;
+  return DDPPO_OK;
+}
+
+static bool collect_view_ok(const ddppo_rollout* ro) {
+  return ro->obs && ro->goal && ro->prev_a && ro->masks && ro->actions && ro->logp && ro->values &&
+         ro->rewards && ro->dones && ro->h0 && ro->c0 && ro->h && ro->c && ro->uniforms;
+}
+
+extern "C" int ddppo_collect_begin(ddppo_ctx* x, const ddppo_rollout* ro, void* stream) {
+  ARG(x && x->net && ro && collect_view_ok(ro), "collect_begin: null argument or buffer");
+  DDPPO_TRY(collect_prologue(x, ro, (cudaStream_t)stream));
+  x->net->step_next = 0;
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_collect_step(ddppo_ctx* x, const ddppo_rollout* ro, int32_t t, void* stream) {
+  ARG(x && x->net && ro && collect_view_ok(ro), "collect_step: null argument or buffer");
+  Net& n = *x->net;
+  const int E = x->cfg.num_envs;
+  if (t != n.step_next || t < 0 || t >= x->cfg.rollout_T) {
+    set_error("collect_step: steps must follow collect_begin in order, t < rollout_T");
+    return DDPPO_E_STATE;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t ob = n.pix * op_bytes(n);
+  // the next episodes are prepared on the side stream while the policy acts, and joined
+  // before the env step: the same overlap as a whole collection
+  DDPPO_CHECK_CUDA(cudaEventRecord(x->ev_fork, s));
+  DDPPO_CHECK_CUDA(cudaStreamWaitEvent(x->side, x->ev_fork, 0));
+  DDPPO_TRY(launch_env_prefetch(x->sp, x->sb, x->prefetch_grid, x->side));
+  DDPPO_CHECK_CUDA(cudaEventRecord(x->ev_join, x->side));
+  const size_t o = (size_t)t * E, o1 = (size_t)(t + 1) * E;
+  DDPPO_TRY(act_impl(x, (const char*)ro->obs + o * ob, ro->goal + o * 3, ro->prev_a + o,
+                     ro->masks + o, ro->h, ro->c, ro->uniforms + o, ro->actions + o, ro->logp + o,
+                     ro->values + o, s));
+  DDPPO_CHECK_CUDA(cudaStreamWaitEvent(s, x->ev_join, 0));
+  DDPPO_TRY(ddppo_env_step(x, ro->actions + o, (char*)ro->obs + o1 * ob, ro->goal + o1 * 3,
+                           ro->rewards + o, ro->dones + o, ro->info ? ro->info + o * 4 : nullptr, s));
+  post_step_kernel<<<(E + 127) / 128, 128, 0, s>>>(E, ro->actions + o, ro->dones + o,
+                                                   ro->prev_a + o1, ro->masks + o1);
+  DDPPO_CHECK_LAUNCH();
+  n.step_next = t + 1;
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_collect_end(ddppo_ctx* x, const ddppo_rollout* ro, int32_t T_valid,
+                                 void* stream) {
+  ARG(x && x->net && ro && collect_view_ok(ro), "collect_end: null argument or buffer");
+  Net& n = *x->net;
+  if (T_valid < 1 || T_valid != n.step_next) {
+    set_error("collect_end: T_valid must equal the number of steps taken (>= 1)");
+    return DDPPO_E_STATE;
+  }
+  n.step_next = -1;
+  return collect_bootstrap(x, ro, T_valid, (cudaStream_t)stream);
+}
+
+extern "C" int ddppo_collect(ddppo_ctx* x, const ddppo_rollout* ro, int32_t use_graph,
+                             void* stream) {
+  ARG(x && x->net && ro, "collect: null argument");
+  ARG(ro->obs && ro->goal && ro->prev_a && ro->masks && ro->actions && ro->logp && ro->values &&
+          ro->rewards && ro->dones && ro->h0 && ro->c0 && ro->h && ro->c && ro->uniforms,
+      "collect: rollout view has a null buffer");
+  Net& n = *x->net;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int E = x->cfg.num_envs, T = x->cfg.rollout_T;
+  const size_t ob = n.pix * op_bytes(n);
+  DDPPO_TRY(collect_prologue(x, ro, s));
   if (use_graph) {
     if (!n.graph_exec || memcmp(&n.graph_ro, ro, sizeof(*ro)) != 0) {
       // one act step outside the capture (state into scratch buffers) so that the GEMM
@@ -446,15 +631,7 @@ extern "C" int ddppo_collect(ddppo_ctx* x, const ddppo_rollout* ro, int32_t use_
   } else {
     DDPPO_TRY(collect_body(x, ro, s));
   }
-  // bootstrap value V(o_T) with the state after step T-1; the state itself is not advanced
-  const size_t oT = (size_t)T * E;
-  DDPPO_TRY(net_forward(n, 1, E, (const char*)ro->obs + oT * ob, ro->goal + oT * 3,
-                        ro->prev_a + oT, ro->masks + oT, ro->h, ro->c, nullptr, nullptr, nullptr, s,
-                        true));
-  DDPPO_CHECK_CUDA(cudaMemcpyAsync(ro->values + oT, n.values, (size_t)E * 4,
-                                   cudaMemcpyDeviceToDevice, s));
-  n.ev_valid = false;
-  return DDPPO_OK;
+  return collect_bootstrap(x, ro, T, s);
 }
 
 // ---- timing ----

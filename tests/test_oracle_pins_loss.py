@@ -213,3 +213,63 @@ def test_policy_inputs_concatenate_visual_goal_action_in_that_order():
     H = cfg.hidden
     assert x.shape == (2, H + 64)
     assert (x[:, :H] == 3).all() and (x[:, H:H + 32] == 1).all() and (x[:, H + 32:] == 2).all()
+
+
+# ---------------------------------------------------------------- DD-PPO's gradient AllReduce
+def _rollout(cfg, T, E, seed):
+    from tests import inputs as I
+    return I.minibatch(cfg, T=T, E=E, seed=seed)
+
+
+def test_dd_update_with_one_worker_is_ppo_update():
+    from tests import inputs as I
+    cfg = I.net_config("tiny")
+    hp = R.PPOHParams(epochs=2, minibatches=2)
+    flat = I.params(cfg, seed=21)
+    ro = _rollout(cfg, 3, 4, 22)
+    z = torch.zeros_like(flat)
+    f1, m1, v1, s1, _ = R.ppo_update(flat, z, z.clone(), 0, ro, cfg, hp, seed=5, update=2)
+    f2, m2, v2, s2, _, _ = R.dd_ppo_update(flat, z, z.clone(), 0, [ro], cfg, hp, [5], update=2)
+    assert s1 == s2 == 4
+    assert torch.equal(f1, f2) and torch.equal(m1, m2) and torch.equal(v1, v2)
+
+
+def test_dd_mean_gradient_is_the_gradient_of_the_union_minibatch():
+    """Eq. 4 with equal minibatch sizes: the mean of the workers' mean losses is the mean
+    loss over the union of their samples, so the averaged gradient equals the gradient of
+    one minibatch holding both workers' sequences (a second restatement, through
+    minibatch_loss_and_grad on concatenated inputs, not through the averaging code)."""
+    from tests import inputs as I
+    cfg = I.net_config("tiny")
+    hp = R.PPOHParams(epochs=1, minibatches=1)
+    flat = I.params(cfg, seed=23)
+    ros = [_rollout(cfg, 3, 2, 24), _rollout(cfg, 3, 2, 25)]
+    z = torch.zeros_like(flat)
+    _, _, _, _, _, grads = R.dd_ppo_update(flat, z, z.clone(), 0, ros, cfg, hp, [7, 8], update=0)
+    union = {}
+    for key in ("obs", "goal", "prev_a", "masks", "actions", "logp_old", "adv", "ret"):
+        union[key] = torch.cat([ros[0][key], ros[1][key]], dim=1)
+    for key in ("h0", "c0"):
+        union[key] = torch.cat([ros[0][key], ros[1][key]], dim=1)
+    _, _, g_union = R.minibatch_loss_and_grad(flat, union, cfg, hp)
+    # one minibatch per epoch: every env of each worker, in any order (the loss is a mean)
+    assert torch.allclose(grads[0], g_union, rtol=1e-10, atol=1e-13)
+
+
+def test_dd_short_rollout_weighs_its_worker_equally():
+    """A preempted worker (T_valid < T) contributes the mean over its own samples with the
+    same weight 1/N as a full one (Sec. 3): the averaged gradient is the plain mean of the
+    two workers' gradients, each over its own steps."""
+    from tests import inputs as I
+    cfg = I.net_config("tiny")
+    hp = R.PPOHParams(epochs=1, minibatches=1)
+    flat = I.params(cfg, seed=26)
+    ros = [_rollout(cfg, 4, 2, 27), _rollout(cfg, 4, 2, 28)]
+    z = torch.zeros_like(flat)
+    _, _, _, _, _, grads = R.dd_ppo_update(flat, z, z.clone(), 0, ros, cfg, hp, [1, 2], update=0,
+                                           T_valid=[4, 2])
+    mb1 = {k: ros[1][k][:2] for k in ("obs", "goal", "prev_a", "masks", "actions", "logp_old", "adv", "ret")}
+    mb1["h0"], mb1["c0"] = ros[1]["h0"], ros[1]["c0"]
+    _, _, g0 = R.minibatch_loss_and_grad(flat, ros[0], cfg, hp)
+    _, _, g1 = R.minibatch_loss_and_grad(flat, mb1, cfg, hp)
+    assert torch.allclose(grads[0], 0.5 * (g0 + g1), rtol=1e-10, atol=1e-13)
