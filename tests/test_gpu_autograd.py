@@ -98,7 +98,9 @@ def test_encoder_function(name):
         # the GroupNorm ResNet is piecewise smooth (ReLU, max pool): differences over a finite
         # step carry its kinks, in float64 as well; the FP32 forward's differences must track
         # the oracle's, and the gradient the differences within the kink error
-        for fd, gv, fd64 in _directional_fd(loss_of, net.flat32, g, mask, loss64, rel=2e-4):
+        # (a step of 2e-5 of the parameter norm keeps the kinks' share of the difference small)
+        rel = 2e-5 if name == "resnet_full" else 2e-4
+        for fd, gv, fd64 in _directional_fd(loss_of, net.flat32, g, mask, loss64, rel=rel):
             assert abs(fd - fd64) <= 1e-2 * abs(fd64) + 1e-6, (fd, fd64)
             assert abs(fd - gv) <= 5e-2 * abs(gv) + 1e-6, (fd, gv)
     finally:
@@ -203,7 +205,8 @@ def test_policy_and_ppo_loss_functions(name):
                 return float(loss_fn(theta.cuda()))
         mask = torch.ones(net.P, dtype=torch.bool)
         tol = 5e-2 if name == "resnet_full" else 2e-2
-        for fd, gv, _ in _directional_fd(loss_of, net.flat32, g, mask, rel=2e-4):
+        rel = 2e-5 if name == "resnet_full" else 2e-4
+        for fd, gv, _ in _directional_fd(loss_of, net.flat32, g, mask, rel=rel):
             assert abs(fd - gv) <= tol * abs(gv) + 1e-6, (fd, gv)
     finally:
         AG.sync_params.forget(net.h)
