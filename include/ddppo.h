@@ -75,8 +75,13 @@ typedef struct {
   float max_depth_m;      /* depth clip and normaliser (10 m)                                */
   /* agent network (App. "Agent Design") */
   int32_t net_kind;       /* 0: 3-layer conv 32/64/32 (8/4/3); 1: ResNet-18-style + GN;
-                             2: blind (GPS+Compass only, Sec. 5): no visual encoder or FC */
-  int32_t base_ch;        /* ResNet base width (32 or 64)                                    */
+                             2: blind (GPS+Compass only, Sec. 5): no visual encoder or FC;
+                             3 / 4: SE-ResNeXt50 / 101 with every layer's channels halved
+                             and GroupNorm (App. "Visual Encoder"; Tab. 1): bottlenecks
+                             [3,4,6,3] / [3,4,23,3] of inner width 2 base 2^i (grouped 3x3,
+                             32 groups, carrying the stride) and output 4 base 2^i,
+                             squeeze-excite with reduction 16; 1024 x 4 x 4 at base 32    */
+  int32_t base_ch;        /* ResNet base width (32 or 64); SE-ResNeXt: 16 or 32            */
   int32_t hidden;         /* LSTM hidden size and visual FC width (128 or 512)               */
   int32_t lstm_layers;    /* 1 or 2                                                          */
   int32_t precision;      /* 0: FP32 everywhere; 1: BF16 GEMM operands, FP32 accumulate;
@@ -87,7 +92,8 @@ typedef struct {
   /* rollout / update shapes, used to size the workspace at creation */
   int32_t rollout_T;      /* T: frames per env per rollout (128)                             */
   int32_t minibatches;    /* PPO minibatches per epoch (E must divide evenly)                */
-  int32_t encoder_chunk;  /* max frames per encoder pass in the update (0: min(all, 8192));
+  int32_t encoder_chunk;  /* max frames per encoder pass in the update (0: min(all, 8192),
+                             1024 for the SE-ResNeXt);
                              larger minibatches run in chunks, recomputed for the backward */
   /* task (Sec. 5 "Transfer Learning"): the reward env_step returns. Motion, episodes (stop
      or max_steps) and observations are the same for every task.
@@ -186,6 +192,10 @@ int ddppo_set_bfs_level_cap(ddppo_ctx* ctx, int32_t cap);
  *               c1.w n1.g n1.b c2.w n2.g n2.b [d.w (1x1) nd.g nd.b if it changes shape];
  *               cmp.w [128,8c,3,3] cmp.g [128] cmp.b [128]
  *   net_kind 2: nothing (no encoder)
+ *   net_kind 3, 4: stem.w stem.g stem.b; for each bottleneck: c1.w [mid,cin,1,1] n1.g n1.b
+ *               c2.w [mid,mid/32,3,3] n2.g n2.b c3.w [out,mid,1,1] n3.g n3.b se1.w [out/16,out]
+ *               se1.b se2.w [out,out/16] se2.b [d.w [out,cin,1,1] nd.g nd.b if it changes
+ *               shape]; cmp.w [128,last,3,3] cmp.g cmp.b
  *   then, except for net_kind 2, vis.w [H, F] vis.b [H] (F = flattened encoder output,
  *   C-major order); then goal.w [32,3] goal.b [32], act.emb [5,32],
  *   per LSTM layer l: w_ih [4H, In_l] w_hh [4H, H] b_ih [4H] b_hh [4H]

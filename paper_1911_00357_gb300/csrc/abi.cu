@@ -58,7 +58,11 @@ static int validate(const ddppo_config* c) {
   CFG_CHECK(c->pool2x2 == 0 || c->pool2x2 == 1, "pool2x2 must be 0 or 1");
   CFG_CHECK(c->max_depth_m > 0.f && c->ceil_h_m > c->cam_h_m && c->cam_h_m > 0.f,
             "camera must sit between floor and ceiling");
-  CFG_CHECK(c->net_kind >= 0 && c->net_kind <= 2, "net_kind must be 0 (3-layer conv), 1 (ResNet) or 2 (blind)");
+  CFG_CHECK(c->net_kind >= 0 && c->net_kind <= 4,
+            "net_kind must be 0 (3-layer conv), 1 (ResNet), 2 (blind), 3 (SE-ResNeXt50) or 4 "
+            "(SE-ResNeXt101)");
+  CFG_CHECK(c->net_kind < 3 || c->base_ch == 16 || c->base_ch == 32,
+            "SE-ResNeXt base_ch must be 16 or 32 (32 groups of at most 16 channels)");
   CFG_CHECK(c->precision >= 0 && c->precision <= 2,
             "precision must be 0 (fp32), 1 (bf16) or 2 (fp8 inference, bf16 training)");
   CFG_CHECK(c->precision != 2 || (c->net_kind == 1 && c->base_ch % 64 == 0),

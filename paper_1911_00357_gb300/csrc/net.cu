@@ -85,6 +85,54 @@ static int build_layout(Net& n, Layout& lay) {
     // blind agent (GPS+Compass only, Sec. 5): no visual encoder, no visual FC
     n.featC = 0;
     n.featHW = 0;
+  } else if (n.kind >= 3) {
+    // SE-ResNeXt50 (kind 3) / 101 (kind 4) with every layer's channels halved: stem and
+    // max pool as the ResNet's; bottlenecks [3, 4, 6, 3] / [3, 4, 23, 3] of inner width
+    // 2b 2^i (grouped 3x3 with 32 groups, the stride here) and output 4b 2^i; squeeze-
+    // excite with reduction 16; then the 3x3 compression to 128 channels
+    const int b = c.base_ch;
+    set_conv(n.stem, 1, b, 7, 2, 3, false, n.inh, n.inw, lay);
+    set_gn(n.stem_n, b, lay);
+    n.convs.push_back(&n.stem);
+    int H = (n.stem.Ho - 1) / 2 + 1, W = (n.stem.Wo - 1) / 2 + 1;
+    int cin = b;
+    const int counts[2][4] = {{3, 4, 6, 3}, {3, 4, 23, 3}};
+    const int* cnt = counts[n.kind == 3 ? 0 : 1];
+    n.sx.resize(cnt[0] + cnt[1] + cnt[2] + cnt[3]);
+    for (int i = 0, bi = 0; i < 4; ++i)
+      for (int r = 0; r < cnt[i]; ++r, ++bi) {
+        SxL& X = n.sx[bi];
+        const int mid = (2 * b) << i, cout = (4 * b) << i, st = (i > 0 && r == 0) ? 2 : 1;
+        set_conv(X.c1, cin, mid, 1, 1, 0, false, H, W, lay);
+        set_gn(X.n1, mid, lay);
+        GConvL& g = X.c2;
+        g.C = mid; g.cpg = mid / 32; g.s = st; g.H = H; g.W = W;
+        g.Ho = conv_out(H, 3, st, 1); g.Wo = conv_out(W, 3, st, 1);
+        g.w_off = lay.add((int64_t)mid * g.cpg * 9);
+        set_gn(X.n2, mid, lay);
+        set_conv(X.c3, mid, cout, 1, 1, 0, false, g.Ho, g.Wo, lay);
+        set_gn(X.n3, cout, lay);
+        X.C = cout; X.Cr = cout / 16; X.HW = g.Ho * g.Wo;
+        X.se1_w = lay.add((int64_t)X.Cr * cout);
+        X.se1_b = lay.add(X.Cr);
+        X.se2_w = lay.add((int64_t)cout * X.Cr);
+        X.se2_b = lay.add(cout);
+        X.down = st != 1 || cin != cout;
+        if (X.down) {
+          set_conv(X.d, cin, cout, 1, st, 0, false, H, W, lay);
+          set_gn(X.nd, cout, lay);
+          n.convs.push_back(&X.d);
+        }
+        n.convs.push_back(&X.c1);
+        n.convs.push_back(&X.c3);
+        H = g.Ho; W = g.Wo; cin = cout;
+      }
+    if (H < 1 || W < 1) { set_error("depth too small for the SE-ResNeXt encoder"); return DDPPO_E_CONFIG; }
+    set_conv(n.cmp, cin, 128, 3, 1, 1, false, H, W, lay);
+    set_gn(n.cmp_n, 128, lay);
+    n.convs.push_back(&n.cmp);
+    n.featC = 128;
+    n.featHW = n.cmp.Ho * n.cmp.Wo;
   } else {
     const int b = c.base_ch;
     set_conv(n.stem, 1, b, 7, 2, 3, false, n.inh, n.inw, lay);
@@ -214,7 +262,7 @@ static int alloc_encoder(Net& n) {
   };
   if (n.kind == 0) {
     for (auto& c : n.nat) DDPPO_TRY(conv_bufs(c));
-  } else if (n.kind == 1) {
+  } else if (n.kind == 1 || n.kind >= 3) {
     DDPPO_TRY(conv_bufs(n.stem));
     // the stem's full-resolution activation is only stored when its pool is not fused
     DDPPO_TRY(gn_bufs(n.stem_n, n.stem.Ho * n.stem.Wo, n.stem.cout % 4 != 0));
@@ -222,7 +270,47 @@ static int alloc_encoder(Net& n) {
     DDPPO_TRY(nalloc(n, &n.pool, NC * ph * pw * n.stem.cout));
     if (n.bf) DDPPO_TRY(nalloc(n, &n.pool_bf, NC * ph * pw * n.stem.cout));
     DDPPO_TRY(nalloc(n, &n.pool_arg, NC * ph * pw * n.stem.cout));
+    int maxC = 0, maxCr = 0;
+    for (SxL& X : n.sx) {
+      const int HWi = X.c1.H * X.c1.W;
+      DDPPO_TRY(conv_bufs(X.c1));
+      DDPPO_TRY(conv_bufs(X.c3));
+      DDPPO_TRY(gn_bufs(X.n1, HWi, true));
+      DDPPO_TRY(gn_bufs(X.n2, X.HW, true));
+      DDPPO_TRY(gn_bufs(X.n3, X.HW, false));
+      if (X.down) {
+        DDPPO_TRY(conv_bufs(X.d));
+        DDPPO_TRY(gn_bufs(X.nd, X.HW, false));
+        DDPPO_TRY(nalloc(n, &X.sc, NC * X.HW * X.C));
+      }
+      const GConvL& g = X.c2;
+      DDPPO_TRY(nalloc_op(n, &X.c2.wg, (size_t)g.C * g.cpg * 9));
+      DDPPO_TRY(nalloc(n, &X.c2.z, NC * X.HW * g.C));
+      if (n.bf) {
+        DDPPO_TRY(nalloc(n, &X.n1.out_bf, NC * HWi * g.C));
+        DDPPO_TRY(nalloc(n, &X.n2.out_bf, NC * X.HW * g.C));
+        DDPPO_TRY(nalloc(n, &X.y_bf, NC * X.HW * X.C));
+      }
+      DDPPO_TRY(nalloc(n, &X.u, NC * X.HW * X.C));
+      DDPPO_TRY(nalloc(n, &X.y, NC * X.HW * X.C));
+      DDPPO_TRY(nalloc(n, &X.m, NC * X.C));
+      DDPPO_TRY(nalloc(n, &X.a, NC * X.Cr));
+      DDPPO_TRY(nalloc(n, &X.gate, NC * X.C));
+      GConv gc{(int)NC, g.H, g.W, g.C, g.cpg, g.s, g.Ho, g.Wo};
+      n.gw_part_elems = std::max(n.gw_part_elems,
+                                 (size_t)gconv_wgrad_chunks(gc, n.gws.num_sms) * g.C * g.cpg * 9);
+      maxC = std::max(maxC, X.C);
+      maxCr = std::max(maxCr, X.Cr);
+    }
+    if (!n.sx.empty()) {
+      DDPPO_TRY(nalloc(n, &n.gw_part, n.gw_part_elems));
+      DDPPO_TRY(nalloc(n, &n.se_dg, NC * maxC));
+      DDPPO_TRY(nalloc(n, &n.se_dq, NC * maxC));
+      DDPPO_TRY(nalloc(n, &n.se_dm, NC * maxC));
+      DDPPO_TRY(nalloc(n, &n.se_dh, NC * maxCr));
+    }
     for (auto& B : n.blocks) {
+      if (n.kind != 1) break;
       DDPPO_TRY(conv_bufs(B.c1));
       DDPPO_TRY(conv_bufs(B.c2));
       DDPPO_TRY(gn_bufs(B.n1, B.c1.Ho * B.c1.Wo, true));
@@ -250,7 +338,7 @@ static int alloc_encoder(Net& n) {
   const int C = std::max(n.max_gnC, 64);
   DDPPO_TRY(nalloc(n, &n.gnp_g, NC * C));
   DDPPO_TRY(nalloc(n, &n.gnp_b, NC * C));
-  if (n.kind == 1) {
+  if (n.kind == 1 || n.kind >= 3) {
     n.gnw.max_images = (int)NC;
     n.gnw.part_elems = gn_part_elems((int)NC, C);
     DDPPO_TRY(nalloc(n, &n.gnw.part, n.gnw.part_elems));
@@ -291,6 +379,23 @@ static int init_params(Net& n, cudaStream_t s) {
     }
     DDPPO_TRY(conv_init(n.cmp));
     DDPPO_TRY(gn_init(n.cmp_n));
+  } else if (n.kind >= 3) {
+    DDPPO_TRY(conv_init(n.stem));
+    DDPPO_TRY(gn_init(n.stem_n));
+    for (SxL& X : n.sx) {
+      DDPPO_TRY(conv_init(X.c1)); DDPPO_TRY(gn_init(X.n1));
+      const int fan = X.c2.cpg * 9;
+      DDPPO_TRY(unif(X.c2.w_off, (int64_t)X.c2.C * fan, sqrtf(6.0f / fan)));
+      DDPPO_TRY(gn_init(X.n2));
+      DDPPO_TRY(conv_init(X.c3)); DDPPO_TRY(gn_init(X.n3));
+      DDPPO_TRY(unif(X.se1_w, (int64_t)X.Cr * X.C, sqrtf(6.0f / X.C)));
+      DDPPO_TRY(launch_fill(n.params + X.se1_b, X.Cr, 0.f, s));
+      DDPPO_TRY(unif(X.se2_w, (int64_t)X.C * X.Cr, sqrtf(6.0f / X.Cr)));
+      DDPPO_TRY(launch_fill(n.params + X.se2_b, X.C, 0.f, s));
+      if (X.down) { DDPPO_TRY(conv_init(X.d)); DDPPO_TRY(gn_init(X.nd)); }
+    }
+    DDPPO_TRY(conv_init(n.cmp));
+    DDPPO_TRY(gn_init(n.cmp_n));
   }
   const int Hd = n.H;
   if (n.F > 0) {
@@ -323,6 +428,8 @@ int net_prep_weights(Net& n, cudaStream_t s) {
     if (c->dgrad_as_conv)
       DDPPO_TRY(launch_conv_w_flip(n.params + c->w_off, c->cout, c->cin, c->k, c->wgR, n.bf, s));
   }
+  for (SxL& X : n.sx)
+    DDPPO_TRY(launch_gconv_w_prep(n.params + X.c2.w_off, X.c2.C, X.c2.cpg, X.c2.wg, n.bf, s));
   if (n.f8) {
     // per-tensor E4M3 weights from the bf16 GEMM layout
     const int na = n.f8_act_slots;
@@ -366,7 +473,9 @@ int net_create(ddppo_ctx* x) {
   n.NS = std::max(n.T * n.Emb, n.E);
   // encoder pass size: the whole minibatch when it fits the automatic cap (8192 frames,
   // ~30 GB of activations for the 32-base ResNet), else chunks with recomputation
-  n.NC = c.encoder_chunk > 0 ? std::min(c.encoder_chunk, n.NS) : std::min(n.NS, 8192);
+  // (the SE-ResNeXt keeps ~20 MB of activations per 128x128 frame: 1024 frames per pass)
+  const int auto_chunk = c.net_kind >= 3 ? 1024 : 8192;
+  n.NC = c.encoder_chunk > 0 ? std::min(c.encoder_chunk, n.NS) : std::min(n.NS, auto_chunk);
   n.NC = std::max(n.NC, n.E);  // an act step always fits one chunk
   n.NC = std::min(n.NC, n.NS);
   Layout lay;
@@ -617,6 +726,78 @@ static int gn_bwd(Net& n, GNL& g, const float* dy, const float* z, int N, int HW
   return DDPPO_OK;
 }
 
+static GConv gconv_of(const GConvL& g, int N) {
+  GConv c;
+  c.N = N; c.H = g.H; c.W = g.W; c.C = g.C; c.cpg = g.cpg; c.s = g.s; c.Ho = g.Ho; c.Wo = g.Wo;
+  return c;
+}
+
+static SeArgs se_args(Net& n, SxL& X, int N) {
+  SeArgs e{};
+  e.N = N; e.HW = X.HW; e.C = X.C; e.Cr = X.Cr;
+  e.u = X.u;
+  e.W1 = n.params + X.se1_w; e.b1 = n.params + X.se1_b;
+  e.W2 = n.params + X.se2_w; e.b2 = n.params + X.se2_b;
+  e.m = X.m; e.a = X.a; e.gate = X.gate;
+  e.y = X.y; e.y_bf = n.bf ? X.y_bf : nullptr;
+  e.dg = n.se_dg; e.dq = n.se_dq; e.dh = n.se_dh; e.dm = n.se_dm;
+  e.gW1 = n.grad + X.se1_w; e.gb1 = n.grad + X.se1_b;
+  e.gW2 = n.grad + X.se2_w; e.gb2 = n.grad + X.se2_b;
+  return e;
+}
+
+// SE-ResNeXt bottleneck forward: x (fp32) and its bf16 copy (BF16 form) -> X.y (+ X.y_bf)
+static int sx_block_fwd(Net& n, SxL& X, int N, const float* x, const __nv_bfloat16* x_bf,
+                        cudaStream_t s) {
+  const int HWi = X.c1.H * X.c1.W;
+  DDPPO_TRY(conv_fwd(n, X.c1, x, false, N, X.c1.z, false, s, x_bf));
+  DDPPO_TRY(gn_fwd(n, X.n1, X.c1.z, N, HWi, X.n1.out, true, nullptr, nullptr, nullptr, s,
+                   X.n1.out_bf));
+  const void* g_in = n.bf ? (const void*)X.n1.out_bf : (const void*)X.n1.out;
+  DDPPO_TRY(launch_gconv_fwd(gconv_of(X.c2, N), g_in, X.c2.wg, X.c2.z, n.bf, s));
+  DDPPO_TRY(gn_fwd(n, X.n2, X.c2.z, N, X.HW, X.n2.out, true, nullptr, nullptr, nullptr, s,
+                   X.n2.out_bf));
+  DDPPO_TRY(conv_fwd(n, X.c3, X.n2.out, false, N, X.c3.z, false, s, X.n2.out_bf));
+  DDPPO_TRY(gn_fwd(n, X.n3, X.c3.z, N, X.HW, X.u, false, nullptr, nullptr, nullptr, s));
+  const float* sc = x;
+  if (X.down) {
+    DDPPO_TRY(conv_fwd(n, X.d, x, false, N, X.d.z, false, s, x_bf));
+    DDPPO_TRY(gn_fwd(n, X.nd, X.d.z, N, X.HW, X.sc, false, nullptr, nullptr, nullptr, s));
+    sc = X.sc;
+  }
+  SeArgs e = se_args(n, X, N);
+  e.sc = sc;
+  return launch_se_fwd(e, s);
+}
+
+// its backward: gcur holds the gradient of X.y and receives that of the block input x;
+// gA, gB are scratch of the same size (the three buffers may be rotated: gcur is updated)
+static int sx_block_bwd(Net& n, SxL& X, int N, const float* x, const __nv_bfloat16* x_bf,
+                        bool first, float*& gcur, float*& gA, float*& gB, cudaStream_t s) {
+  const int HWi = X.c1.H * X.c1.W;
+  SeArgs e = se_args(n, X, N);
+  // gcur <- gradient through the output ReLU (the shortcut's); gA <- the branch's (du)
+  DDPPO_TRY(launch_se_bwd(e, gcur, gcur, gA, !first, s));
+  DDPPO_TRY(gn_bwd(n, X.n3, gA, X.c3.z, N, X.HW, first, s));
+  DDPPO_TRY(conv_bwd(n, X.c3, X.n2.out, false, N, n.dzop, gB, false, first, s, X.n2.out_bf));
+  DDPPO_TRY(gn_bwd(n, X.n2, gB, X.c2.z, N, X.HW, first, s, X.n2.out));
+  const GConv gc = gconv_of(X.c2, N);
+  const void* g_in = n.bf ? (const void*)X.n1.out_bf : (const void*)X.n1.out;
+  DDPPO_TRY(launch_gconv_wgrad(gc, g_in, n.dzop, n.gw_part, n.gw_part_elems, n.gws.num_sms,
+                               n.grad + X.c2.w_off, first ? 0.f : 1.f, n.bf, s));
+  DDPPO_TRY(launch_gconv_dgrad(gc, n.dzop, X.c2.wg, gA, false, n.bf, s));
+  DDPPO_TRY(gn_bwd(n, X.n1, gA, X.c1.z, N, HWi, first, s, X.n1.out));
+  if (X.down) {
+    DDPPO_TRY(conv_bwd(n, X.c1, x, false, N, n.dzop, gB, false, first, s, x_bf));
+    DDPPO_TRY(gn_bwd(n, X.nd, gcur, X.d.z, N, X.HW, first, s));
+    DDPPO_TRY(conv_bwd(n, X.d, x, false, N, n.dzop, gB, true, first, s, x_bf));
+    float* t = gcur; gcur = gB; gB = t;
+  } else {
+    DDPPO_TRY(conv_bwd(n, X.c1, x, false, N, n.dzop, gcur, true, first, s, x_bf));
+  }
+  return DDPPO_OK;
+}
+
 // forward of one chunk of N images: obs (op dtype) -> featop rows (op dtype). f8: the
 // act-time pass of FP8 inference (N <= E): every convolution after the stem reads E4M3
 // copies of its input and weights; the activation scales advance once per pass
@@ -654,6 +835,13 @@ static int encoder_fwd(Net& n, const void* obs, int N, void* featop_rows, cudaSt
   }
   const float* cur = n.pool;
   const __nv_bfloat16* cur_bf = f8 ? nullptr : n.pool_bf;
+  if (!n.sx.empty()) {
+    for (SxL& X : n.sx) DDPPO_TRY(sx_block_fwd(n, X, N, cur, cur_bf, s));
+    const SxL& L = n.sx.back();
+    DDPPO_TRY(conv_fwd(n, n.cmp, L.y, false, N, n.cmp.z, false, s, L.y_bf));
+    DDPPO_TRY(gn_fwd(n, n.cmp_n, n.cmp.z, N, n.featHW, n.cmp_n.out, true, nullptr, nullptr, nullptr, s));
+    return launch_cast(n.cmp_n.out, featop_rows, n.bf, (size_t)N * n.F, s);
+  }
   const uint8_t* cur_f8 = f8 ? n.pool_f8 : nullptr;
   const float* cur_sc = f8 ? n.f8_scale + n.pool_slot : nullptr;
   for (auto& B : n.blocks) {
@@ -705,13 +893,19 @@ static int encoder_bwd(Net& n, const void* obs, int N, const float* dfeat_rows, 
   }
   // compression conv
   DDPPO_TRY(gn_bwd(n, n.cmp_n, dfeat_rows, n.cmp.z, N, n.featHW, first, s, n.cmp_n.out));
-  DDPPO_TRY(conv_bwd(n, n.cmp, n.blocks[7].y, false, N, n.dzop, n.g1, false, first, s,
-                     n.blocks[7].y_bf));
+  const float* last_y = n.sx.empty() ? n.blocks[7].y : n.sx.back().y;
+  const __nv_bfloat16* last_bf = n.sx.empty() ? n.blocks[7].y_bf : n.sx.back().y_bf;
+  DDPPO_TRY(conv_bwd(n, n.cmp, last_y, false, N, n.dzop, n.g1, false, first, s, last_bf));
   // residual blocks, last to first. gcur: gradient of the block output (before its ReLU)
   float* gcur = n.g1;
   float* gA = n.g0;
   float* gB = n.g2;
-  for (int bi = 7; bi >= 0; --bi) {
+  for (int bi = (int)n.sx.size() - 1; bi >= 0; --bi) {
+    const float* xin = bi > 0 ? n.sx[bi - 1].y : n.pool;
+    const __nv_bfloat16* xin_bf = bi > 0 ? n.sx[bi - 1].y_bf : n.pool_bf;
+    DDPPO_TRY(sx_block_bwd(n, n.sx[bi], N, xin, xin_bf, first, gcur, gA, gB, s));
+  }
+  for (int bi = n.sx.empty() ? 7 : -1; bi >= 0; --bi) {
     BlockL& B = n.blocks[bi];
     const int HW = B.c1.Ho * B.c1.Wo;
     const float* xin = bi > 0 ? n.blocks[bi - 1].y : n.pool;

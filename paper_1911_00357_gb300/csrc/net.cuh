@@ -50,6 +50,32 @@ struct BlockL {
   int y_slot = -1;
 };
 
+// grouped 3x3 convolution of an SE-ResNeXt bottleneck (cpg = C / 32 channels per group)
+struct GConvL {
+  int C = 0, cpg = 0, s = 1, H = 0, W = 0, Ho = 0, Wo = 0;
+  int64_t w_off = -1;    // canonical [C, cpg, 3, 3] in the flat parameters
+  void* wg = nullptr;    // [C][3][3][cpg] op dtype
+  float* z = nullptr;    // [NC, Ho, Wo, C] output (fp32)
+};
+
+// SE-ResNeXt bottleneck (App. "Visual Encoder"): 1x1 conv -> GN -> ReLU -> grouped 3x3
+// -> GN -> ReLU -> 1x1 conv -> GN (u) -> squeeze-excite -> + shortcut -> ReLU
+struct SxL {
+  ConvL c1, c3, d;
+  GConvL c2;
+  GNL n1, n2, n3, nd;
+  bool down = false;
+  int C = 0, Cr = 0, HW = 0;  // output channels, squeeze width (C / 16), output pixels
+  int64_t se1_w = -1, se1_b = -1, se2_w = -1, se2_b = -1;
+  float* u = nullptr;     // [NC, HW, C] the branch before the excitation
+  float* sc = nullptr;    // [NC, HW, C] the normalised 1x1 shortcut (when down)
+  float* m = nullptr;     // [NC, C] squeeze means
+  float* a = nullptr;     // [NC, Cr] squeeze FC output (after ReLU)
+  float* gate = nullptr;  // [NC, C] excitation gates
+  float* y = nullptr;     // [NC, HW, C] block output
+  __nv_bfloat16* y_bf = nullptr;  // its bf16 copy (BF16 form)
+};
+
 struct LstmL {
   int In = 0;
   int64_t wih = -1, whh = -1, bih = -1, bhh = -1;
@@ -98,6 +124,9 @@ struct Net {
   __nv_bfloat16* pool_bf = nullptr;
   uint8_t* pool_arg = nullptr;
   BlockL blocks[8];
+  std::vector<SxL> sx;                  // SE-ResNeXt bottlenecks (net_kind 3, 4)
+  float* gw_part = nullptr; size_t gw_part_elems = 0;  // grouped-conv weight-gradient partials
+  float* se_dg = nullptr; float* se_dq = nullptr; float* se_dh = nullptr; float* se_dm = nullptr;
   ConvL cmp;
   GNL cmp_n;
   std::vector<ConvL*> convs;

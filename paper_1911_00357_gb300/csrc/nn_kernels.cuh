@@ -80,6 +80,39 @@ int launch_relu_bwd(const float* dy, const float* y, size_t n, float* dz32, void
 // dz += dy * (y > 0)   (used where a ReLU output feeds two consumers)
 int launch_add(float* dst, const float* src, size_t n, cudaStream_t s);
 
+// ---- SE-ResNeXt pieces (sx.cu) ----
+// grouped 3x3 convolution, padding 1, stride s; input [N, H, W, C], output [N, Ho, Wo, C],
+// cpg = C / groups channels per group; weights [C][3][3][cpg] in the operand dtype
+struct GConv {
+  int N, H, W, C, cpg, s, Ho, Wo;
+};
+int launch_gconv_fwd(const GConv& g, const void* x, const void* w, float* z, bool bf, cudaStream_t s);
+int launch_gconv_dgrad(const GConv& g, const void* dz, const void* w, float* dx, bool accumulate,
+                       bool bf, cudaStream_t s);
+// dw canonical [C][cpg][3][3] fp32 = beta dw + the weight gradient; part: scratch of at
+// least gconv_wgrad_chunks() * C * cpg * 9 floats
+int gconv_wgrad_chunks(const GConv& g, int num_sms);
+int launch_gconv_wgrad(const GConv& g, const void* x, const void* dz, float* part, size_t part_elems,
+                       int num_sms, float* dw, float beta, bool bf, cudaStream_t s);
+int launch_gconv_w_prep(const float* w, int C, int cpg, void* out, bool bf, cudaStream_t s);
+// squeeze-excite of a branch u [N, HW, C] with shortcut sc (null: none) into y (+ y_bf):
+//   m = mean_hw u, a = relu(W1 m + b1) [N, Cr], gate = sigmoid(W2 a + b2), y = relu(u gate + sc)
+// backward (launch_se_bwd): from gy (the gradient of y): gpre = gy (y > 0) (the shortcut's
+// gradient; gpre may be gy), du (the branch's), and the FC parameter gradients
+// gW1/gb1/gW2/gb2 (+= when accumulate); dg, dq, dh, dm are [N, C] / [N, Cr] scratch
+struct SeArgs {
+  int N, HW, C, Cr;
+  const float* u; const float* sc;
+  const float* W1; const float* b1; const float* W2; const float* b2;
+  float* m; float* a; float* gate;
+  float* y; __nv_bfloat16* y_bf;
+  float* dg; float* dq; float* dh; float* dm;
+  float* gW1; float* gb1; float* gW2; float* gb2;
+};
+int launch_se_fwd(const SeArgs& e, cudaStream_t s);
+int launch_se_bwd(const SeArgs& e, const float* gy, float* gpre, float* du, bool accumulate,
+                  cudaStream_t s);
+
 int launch_maxpool_fwd(const float* x, int N, int H, int W, int C, float* y, uint8_t* arg,
                        __nv_bfloat16* y_bf, cudaStream_t s);
 int launch_maxpool_bwd(const float* dy, const uint8_t* arg, int N, int H, int W, int C, float* dx,

@@ -79,31 +79,31 @@ class _Linear(torch.autograd.Function):
 
 
 class _Conv(torch.autograd.Function):
-    """y = conv(R(x), R(w)); backward from R(dy)."""
+    """y = conv(R(x), R(w)) (optionally grouped); backward from R(dy)."""
 
     @staticmethod
-    def forward(ctx, x, w, stride, padding):
+    def forward(ctx, x, w, stride, padding, groups):
         xr, wr = R(x), R(w)
         ctx.save_for_backward(xr, wr)
-        ctx.cfg = (stride, padding, x.shape, w.shape)
-        return F.conv2d(xr, wr, stride=stride, padding=padding)
+        ctx.cfg = (stride, padding, groups, x.shape, w.shape)
+        return F.conv2d(xr, wr, stride=stride, padding=padding, groups=groups)
 
     @staticmethod
     def backward(ctx, g):
         xr, wr = ctx.saved_tensors
-        stride, padding, xs, ws = ctx.cfg
+        stride, padding, groups, xs, ws = ctx.cfg
         gr = R(g)
-        dx = torch.nn.grad.conv2d_input(xs, wr, gr, stride=stride, padding=padding)
-        dw = torch.nn.grad.conv2d_weight(xr, ws, gr, stride=stride, padding=padding)
-        return dx, dw, None, None
+        dx = torch.nn.grad.conv2d_input(xs, wr, gr, stride=stride, padding=padding, groups=groups)
+        dw = torch.nn.grad.conv2d_weight(xr, ws, gr, stride=stride, padding=padding, groups=groups)
+        return dx, dw, None, None, None
 
 
 def linear(A, W):
     return _Linear.apply(A, W)
 
 
-def conv(x, w, stride=1, padding=0):
-    return _Conv.apply(x, w, stride, padding)
+def conv(x, w, stride=1, padding=0, groups=1):
+    return _Conv.apply(x, w, stride, padding, groups)
 
 
 def store(x):
@@ -125,6 +125,23 @@ def encoder(p, obs, cfg):
     e = cfg.gn_eps
     x = F.relu(_gn(conv(x, p["stem.w"], 2, 3), p["stem.g"], p["stem.b"], e))
     x = F.max_pool2d(x, 3, stride=2, padding=1)
+    if cfg.net_kind == 3:
+        # SE-ResNeXt: the three convolutions read bf16 copies; the squeeze-excite FCs, the
+        # GroupNorms and the shortcut stay fp32
+        for i, (_, _, _, s) in enumerate(OP._sx_blocks(cfg)):
+            q = f"x{i}."
+            y = F.relu(_gn(conv(x, p[q + "c1.w"]), p[q + "n1.g"], p[q + "n1.b"], e))
+            y = F.relu(_gn(conv(y, p[q + "c2.w"], s, 1, cfg.cardinality), p[q + "n2.g"],
+                           p[q + "n2.b"], e))
+            y = _gn(conv(y, p[q + "c3.w"]), p[q + "n3.g"], p[q + "n3.b"], e)
+            y = OP.squeeze_excite(p, q, y)
+            if q + "d.w" in p:
+                sc = _gn(conv(x, p[q + "d.w"], s), p[q + "nd.g"], p[q + "nd.b"], e)
+            else:
+                sc = x
+            x = F.relu(y + sc)
+        x = F.relu(_gn(conv(x, p["cmp.w"], 1, 1), p["cmp.g"], p["cmp.b"], e))
+        return x.flatten(1)
     for i, (cin, cout, s) in enumerate(OP._resnet_blocks(cfg.base_ch)):
         q = f"b{i}."
         y = F.relu(_gn(conv(x, p[q + "c1.w"], s, 1), p[q + "n1.g"], p[q + "n1.b"], e))

@@ -23,8 +23,11 @@ def sim_config_from(cfg: B.Config) -> OS.SimConfig:
 
 def net_config_from(cfg: B.Config) -> OP.NetConfig:
     h = cfg.depth_h >> cfg.pool2x2
-    return OP.NetConfig(net_kind=cfg.net_kind, base_ch=cfg.base_ch, hidden=cfg.hidden,
-                        lstm_layers=cfg.lstm_layers, in_h=h, in_w=h)
+    kw = dict(net_kind=cfg.net_kind, base_ch=cfg.base_ch, hidden=cfg.hidden,
+              lstm_layers=cfg.lstm_layers, in_h=h, in_w=h)
+    if cfg.net_kind == 4:  # SE-ResNeXt101: the oracle's SE-ResNeXt with [3, 4, 23, 3] blocks
+        kw.update(net_kind=3, sx_blocks=(3, 4, 23, 3))
+    return OP.NetConfig(**kw)
 
 
 def obs_shape(cfg: B.Config, *lead):

@@ -43,7 +43,10 @@ def test_bad_configs_are_rejected_before_cuda():
         assert ei.value.code == -2, kw
     # FP8 inference needs the ResNet encoder at a base width that is a multiple of 64
     for name, kw in [("resnet", dict(precision=2)), ("resnet", dict(precision=3)),
-                     ("blind", dict(precision=2)), ("resnet", dict(net_kind=3))]:
+                     ("blind", dict(precision=2)), ("resnet", dict(net_kind=5)),
+                     ("resnet", dict(net_kind=3, base_ch=64)), ("resnet", dict(net_kind=4, base_ch=8)),
+                     ("wide_256_fp8", dict(net_kind=3)), ("resnet", dict(task=3)),
+                     ("resnet", dict(task=2, explore_m=0.05))]:
         with pytest.raises(B.DDPPOError) as ei:
             B.ddppo_create(make_config(name, **kw))
         assert ei.value.code == -2, (name, kw)
@@ -63,6 +66,10 @@ def test_null_arguments_are_rejected():
 def test_every_preset_passes_the_configuration_checks():
     for name in PRESETS:
         B.ddppo_config_check(make_config(name))
+    for kind in (3, 4):  # the SE-ResNeXt encoders at the paper's halved widths
+        B.ddppo_config_check(make_config("resnet", net_kind=kind, base_ch=32))
+    for task in (1, 2):
+        B.ddppo_config_check(make_config("resnet", task=task))
     with pytest.raises(B.DDPPOError) as ei:
         B.ddppo_config_check(make_config("wide_256_fp8", base_ch=32))
     assert ei.value.code == -2 and "fp8" in str(ei.value)

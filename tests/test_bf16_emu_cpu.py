@@ -22,7 +22,7 @@ def _grads(fwd, cfg, flat, mb):
     return lg.detach(), v.detach(), h.detach(), gr
 
 
-@pytest.mark.parametrize("net", ["tiny", "tiny_resnet", "tiny_blind"])
+@pytest.mark.parametrize("net", ["tiny", "tiny_resnet", "tiny_blind", "tiny_sx"])
 def test_emulation_without_rounding_is_the_oracle(net):
     cfg = I.net_config(net)
     flat = I.params(cfg, seed=1)

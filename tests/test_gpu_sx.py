@@ -1,0 +1,206 @@
+"""GPU parity of the SE-ResNeXt encoders (App. "Visual Encoder"; Tab. 1: SE-ResNeXt50 and
+SE-ResNeXt101 with every layer's channels halved and GroupNorm) against the oracle.
+
+The CUDA path: 1x1 convolutions on the contraction engine, the grouped 3x3 convolution
+(32 groups of 1-16 channels) and squeeze-excite as their own kernels, GroupNorm as in the
+ResNet. Checked, on 128x128 inputs (1024 x 4 x 4 backbone output at base 32):
+  * FP32 form: logits and values within 1e-4 of the float64 oracle's scale; the
+    gradients of the LSTM, heads and FCs within 1e-3 relative L2; the encoder's
+    within 5e-2 (max) / 1e-2 (median) -- like the ResNet's, its gradient runs through
+    ReLU masks and max-pool choices that flip under fp32 rounding;
+  * the act step (sampled actions where the CDF margin is decided, log-probabilities,
+    values, LSTM state), and a 2 x 2 PPO update (parameter change within 2% of
+    lr x steps of the oracle's);
+  * BF16 form against the float64 emulation of its roundings (tests/bf16_emu.py),
+    bounded by the emulation's own chaos floor as for the ResNet;
+  * worker iterations (collect + GAE + update) of SE-ResNeXt50 and SE-ResNeXt101.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import policy as OP
+from oracle import rl as OR
+from paper_1911_00357_gb300 import binding as B
+from paper_1911_00357_gb300.presets import make_config
+from paper_1911_00357_gb300.worker import Worker
+from tests import bf16_emu as EMU
+from tests import inputs as I
+from tests.test_gpu_bf16 import CHAOS_EPS, HEAD_PREFIX, _forward_grad, _per_tensor, _rel, _rel_l2
+from tests.test_gpu_policy import Net, _dev_inputs, _rollout_tensors, _view
+
+pytestmark = pytest.mark.gpu
+DT = torch.float64
+
+
+def _sx_cfg(kind, base, E, T, precision, mb=1, **kw):
+    d = dict(net_kind=kind, base_ch=base, depth_h=128, depth_w=128, pool2x2=0, hidden=32,
+             lstm_layers=1, num_envs=E, rollout_T=T, minibatches=mb, precision=precision)
+    d.update(kw)
+    return make_config("resnet", **d)
+
+
+def _eval_backward(net, cfg, T, E):
+    mb = I.minibatch(net.ncfg, T=T, E=E, seed=2)
+    dev, ref = _dev_inputs(cfg, mb)
+    logits = torch.zeros(T, E, 4, device="cuda")
+    values = torch.zeros(T, E, device="cuda")
+    B.ddppo_policy_evaluate(net.h, T, E, dev["obs"], dev["goal"], dev["prev_a"], dev["masks"],
+                            dev["h0"], dev["c0"], logits, values)
+    g = torch.Generator().manual_seed(3)
+    dl = torch.randn(T, E, 4, generator=g, dtype=DT).float()
+    dv = torch.randn(T, E, generator=g, dtype=DT).float()
+    grad = torch.zeros(net.P, device="cuda")
+    B.ddppo_policy_backward(net.h, dl.cuda(), dv.cuda(), grad)
+    torch.cuda.synchronize()
+    assert B.ddppo_device_status(net.h) == 0
+    return ref, logits.cpu(), values.cpu(), grad.cpu().double(), dl.double(), dv.double()
+
+
+@pytest.mark.parametrize("kind,base,T,E", [(3, 16, 2, 2), (3, 32, 2, 2)])
+def test_sx_fp32_evaluate_and_backward(kind, base, T, E):
+    cfg = _sx_cfg(kind, base, E, T, 0)
+    net = Net(cfg, seed=1)
+    try:
+        ref, lg, vv, gg, dl, dv = _eval_backward(net, cfg, T, E)
+        lg_r, v_r, g_r = _forward_grad(OP.sequence_forward, net.flat64(), ref, net.ncfg, dl, dv)
+        assert _rel(lg, lg_r) <= 1e-4 and _rel(vv, v_r) <= 1e-4, (_rel(lg, lg_r), _rel(vv, v_r))
+        gp, gr = _per_tensor(net.ncfg, gg), _per_tensor(net.ncfg, g_r)
+        enc, rest = {}, {}
+        for k in gr:
+            if torch.linalg.vector_norm(gr[k]).item() < 1e-8:
+                continue
+            (rest if k.startswith(HEAD_PREFIX) else enc)[k] = _rel_l2(gp[k], gr[k])
+        print("\nSE-ResNeXt%d base %d FP32 gradient errors: encoder max %.3g median %.3g, rest max %.3g"
+              % (50 if kind == 3 else 101, base, max(enc.values()), np.median(list(enc.values())),
+                 max(rest.values())))
+        assert max(rest.values()) <= 1e-3, max(rest, key=rest.get)
+        assert max(enc.values()) <= 5e-2, max(enc, key=enc.get)
+        assert np.median(list(enc.values())) <= 1e-2
+    finally:
+        net.close()
+
+
+def test_sx_act_parity():
+    E = 5
+    cfg = _sx_cfg(3, 32, E, 2, 0)
+    net = Net(cfg, seed=4)
+    try:
+        mb = I.minibatch(net.ncfg, T=1, E=E, seed=5)
+        dev, ref = _dev_inputs(cfg, mb)
+        u = torch.from_numpy(I.uniforms(1, E, seed=6)[0]).cuda()
+        h, c = dev["h0"].clone(), dev["c0"].clone()
+        act = torch.zeros(E, dtype=torch.int32, device="cuda")
+        logp = torch.zeros(E, device="cuda")
+        val = torch.zeros(E, device="cuda")
+        B.ddppo_policy_act(net.h, dev["obs"][0], dev["goal"][0], dev["prev_a"][0], dev["masks"][0],
+                           h, c, u, act, logp, val)
+        torch.cuda.synchronize()
+        p = OP.unflatten(net.flat64(), net.ncfg)
+        a_r, _, v_r, h_r, c_r, lg_r = OP.act(p, ref["obs"][0], ref["goal"][0], ref["prev_a"][0],
+                                             ref["masks"][0], ref["h0"], ref["c0"],
+                                             u.cpu().double(), net.ncfg)
+        cdf = torch.cumsum(torch.softmax(lg_r, -1), -1)
+        decided = ((cdf - u.cpu().double().unsqueeze(1)).abs() > 1e-4).all(1)
+        assert (act.cpu().long()[decided] == a_r[decided]).all()
+        lp_at = torch.log_softmax(lg_r, -1).gather(1, act.cpu().long().unsqueeze(1))[:, 0]
+        assert _rel(logp.cpu(), lp_at) <= 1e-4 and _rel(val.cpu(), v_r) <= 1e-4
+        assert _rel(h.cpu(), h_r) <= 1e-4 and _rel(c.cpu(), c_r) <= 1e-4
+    finally:
+        net.close()
+
+
+def test_sx_fp32_ppo_update():
+    T, E, mb = 3, 4, 2
+    cfg = _sx_cfg(3, 16, E, T, 0, mb=mb)
+    net = Net(cfg, seed=7)
+    try:
+        ro_t, ref = _rollout_tensors(cfg, net, T, E, seed=8)
+        hpb = B.default_hparams(minibatches=mb, update_index=1)
+        stats = torch.zeros(2 * mb, 8, device="cuda")
+        B.ddppo_ppo_update(net.h, _view(ro_t), hpb, stats)
+        out = torch.zeros(net.P, device="cuda")
+        B.ddppo_get_params(net.h, out)
+        torch.cuda.synchronize()
+        assert B.ddppo_device_status(net.h) == 0
+        hp = OR.PPOHParams(minibatches=mb)
+        ro = {k: ref[k] for k in ("obs", "goal", "prev_a", "masks", "actions", "logp_old", "adv",
+                                   "ret", "h0", "c0")}
+        f0 = net.flat64()
+        z = torch.zeros_like(f0)
+        f2, _, _, st2, sts = OR.ppo_update(f0, z, z.clone(), 0, ro, net.ncfg, hp, seed=cfg.seed,
+                                           update=1)
+        err = ((out.cpu().double() - f0) - (f2 - f0)).abs().max().item()
+        assert err <= 0.02 * hp.lr * st2, err
+        s = stats.cpu().double()
+        for k, st in enumerate(sts):
+            assert abs(s[k, 0].item() - st["loss"].item()) <= 1e-4 * max(1.0, abs(st["loss"].item()))
+    finally:
+        net.close()
+
+
+@pytest.mark.parametrize("base", [16, 32])
+def test_sx_bf16_vs_emulation(base):
+    T, E = 2, 2
+    cfg = _sx_cfg(3, base, E, T, 1)
+    net = Net(cfg, seed=1)
+    try:
+        ref, lg, vv, gg, dl, dv = _eval_backward(net, cfg, T, E)
+        f64 = net.flat64()
+        lg_e, v_e, g_e = _forward_grad(EMU.sequence_forward, f64, ref, net.ncfg, dl, dv)
+        lg_r, v_r, g_r = _forward_grad(OP.sequence_forward, f64, ref, net.ncfg, dl, dv)
+        names = [k for k, _ in OP.param_spec(net.ncfg)]
+        enc = [k for k in names if not k.startswith(HEAD_PREFIX)]
+        rest = [k for k in names if k.startswith(HEAD_PREFIX)]
+
+        def pooled(g):
+            q = _per_tensor(net.ncfg, g)
+            return torch.cat([q[k] for k in enc]), torch.cat([q[k] for k in rest])
+        pe, pr = pooled(g_e)
+        pge, pgr = pooled(gg)
+        got = {"logits": _rel(lg, lg_e), "values": _rel(vv, v_e), "encoder": _rel_l2(pge, pe),
+               "rest": _rel_l2(pgr, pr)}
+        floor = {k: 0.0 for k in got}
+        for i, eps in enumerate(CHAOS_EPS + (2.0 ** -23,)):
+            noise = torch.randn(f64.shape, generator=torch.Generator().manual_seed(40 + i), dtype=DT)
+            lg_p, v_p, g_p = _forward_grad(EMU.sequence_forward, f64 * (1 + eps * noise), ref,
+                                           net.ncfg, dl, dv)
+            qe, qr = pooled(g_p)
+            cand = {"logits": _rel(lg_p, lg_e), "values": _rel(v_p, v_e),
+                    "encoder": _rel_l2(qe, pe), "rest": _rel_l2(qr, pr)}
+            floor = {k: max(floor[k], cand[k]) for k in floor}
+        qr64e, qr64r = pooled(g_r)
+        cost = {"logits": _rel(lg_e, lg_r), "values": _rel(v_e, v_r), "encoder": _rel_l2(pe, qr64e),
+                "rest": _rel_l2(pr, qr64r)}
+        gpu64 = {"logits": _rel(lg, lg_r), "values": _rel(vv, v_r), "encoder": _rel_l2(pge, qr64e),
+                 "rest": _rel_l2(pgr, qr64r)}
+        fmt = lambda d: {k: "%.3g" % v for k, v in d.items()}
+        print("\nSE-ResNeXt50 base %d BF16 vs emulation %s; chaos floor %s; bf16 cost %s"
+              % (base, fmt(got), fmt(floor), fmt(cost)))
+        for k in got:
+            assert got[k] <= 2.5 * floor[k] + 1e-4, (k, got[k], floor[k])
+            assert gpu64[k] <= 2 * cost[k] + 1e-2, (k, gpu64[k], cost[k])
+    finally:
+        net.close()
+
+
+@pytest.mark.parametrize("kind", [3, 4])
+def test_sx_worker_iterations(kind):
+    w = Worker("resnet", seed=2, net_kind=kind, base_ch=32, num_envs=4, rollout_T=8, minibatches=2,
+               max_steps=12)
+    try:
+        before = torch.zeros(B.ddppo_num_params(w.h), device="cuda")
+        B.ddppo_get_params(w.h, before)
+        for _ in range(2):
+            w.iterate()
+        after = torch.zeros_like(before)
+        B.ddppo_get_params(w.h, after)
+        torch.cuda.synchronize()
+        assert B.ddppo_device_status(w.h) == 0
+        assert torch.isfinite(after).all() and (after - before).abs().max().item() > 0
+        assert torch.isfinite(w.stats).all()
+        ncfg = OP.NetConfig(net_kind=3, base_ch=32, hidden=512, lstm_layers=2, in_h=128, in_w=128,
+                            sx_blocks=(3, 4, 6, 3) if kind == 3 else (3, 4, 23, 3))
+        assert before.numel() == OP.num_params(ncfg)
+    finally:
+        w.close()
