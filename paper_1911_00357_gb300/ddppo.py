@@ -106,7 +106,7 @@ class VirtualWorkers:
     heterogeneous workload: some workers' scenes cost more to simulate)."""
 
     def __init__(self, preset: str, n: int, p: float = 1.0, seed: int = 0, grid_sides=None,
-                 hparams: dict | None = None, **overrides):
+                 hparams: dict | None = None, tune: bool = False, **overrides):
         self.n = n
         self.workers = []
         for w in range(n):
@@ -117,9 +117,23 @@ class VirtualWorkers:
         w0 = self.workers[0]
         self.T = w0.T
         self.P = B.ddppo_num_params(w0.h)
+        if tune and w0.cfg.precision >= 1:
+            # the GEMM autotuner times its candidates on worker 0 alone (every worker has
+            # the same network shapes), then the table is frozen and shared: preempted
+            # rollouts' new shapes take the fixed heuristic instead of timing trials
+            # disturbed by the other workers' streams
+            w0.iterate()
+            table = B.ddppo_autotune_export(w0.h)
+            for w in self.workers:
+                if w is not w0:
+                    B.ddppo_autotune_import(w.h, table)
+                B.ddppo_autotune(w.h, False)
+        else:
+            for w in self.workers:
+                B.ddppo_autotune(w.h, False)
         flat = torch.empty(self.P, device="cuda")
         B.ddppo_get_params(w0.h, flat)
-        for w in self.workers[1:]:
+        for w in self.workers:
             B.ddppo_set_params(w.h, flat)
         torch.cuda.synchronize()
         self.streams = [torch.cuda.Stream() for _ in range(n)]
@@ -133,6 +147,10 @@ class VirtualWorkers:
     def close(self):
         for w in self.workers:
             w.close()
+
+    def set_threshold(self, p: float):
+        """Change the preemption threshold (the next collection uses it)."""
+        self.counter = PreemptionCounter(self.n, p, self.T)
 
     def collect(self) -> list[int]:
         """Every worker collects on its own stream, at most one step in flight each; the

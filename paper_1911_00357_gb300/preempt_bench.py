@@ -39,23 +39,25 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     args = ap.parse_args()
     sides = [args.sides[w % len(args.sides)] for w in range(args.workers)]
-    for p in args.p:
-        vw = VirtualWorkers(args.preset, args.workers, p=p, seed=args.seed, grid_sides=sides,
-                            num_envs=args.envs, rollout_T=args.T, minibatches=2,
-                            encoder_chunk=args.chunk)
-        try:
+    vw = VirtualWorkers(args.preset, args.workers, seed=args.seed, grid_sides=sides,
+                        num_envs=args.envs, rollout_T=args.T, minibatches=2,
+                        encoder_chunk=args.chunk, tune=True)
+    try:
+        for p in args.p:
+            vw.set_threshold(p)
             r = timed_iterations(vw, args.iters, args.warmup)
             tv = [sum(x) / len(x) for x in zip(*r["T_valid"])]
             print(json.dumps({
                 "p": p, "workers": args.workers, "envs_per_worker": args.envs, "T": args.T,
-                "grid_sides": sides, "frames_per_s": round(r["frames_per_s"], 1),
+                "preset": args.preset, "grid_sides": sides,
+                "frames_per_s": round(r["frames_per_s"], 1),
                 "s_per_iter": round(r["s_per_iter"], 4),
                 "mean_T_valid_per_worker": [round(x, 1) for x in tv],
                 "device_status": max(abs(B.ddppo_device_status(w.h)) for w in vw.workers),
             }), flush=True)
-        finally:
-            vw.close()
-            torch.cuda.synchronize()
+    finally:
+        vw.close()
+        torch.cuda.synchronize()
 
 
 if __name__ == "__main__":
