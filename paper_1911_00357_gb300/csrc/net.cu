@@ -558,6 +558,7 @@ int net_create(ddppo_ctx* x) {
   DDPPO_CHECK_CUDA(cudaMemset(n.stats_tmp, 0, 8 * 64 * 4));
   DDPPO_CHECK_CUDA(cudaStreamCreateWithFlags(&n.cap_stream, cudaStreamNonBlocking));
   DDPPO_TRY(nalloc(n, &n.d_steps, 2));
+  DDPPO_TRY(nalloc(n, &n.lstm_bar, 4));
   DDPPO_CHECK_CUDA(cudaMemset(n.d_steps, 0, 2 * sizeof(int64_t)));
   DDPPO_CHECK_CUDA(cudaEventCreateWithFlags(&n.ev_a, cudaEventDisableTiming));
   DDPPO_CHECK_CUDA(cudaEventCreateWithFlags(&n.ev_b, cudaEventDisableTiming));
@@ -955,6 +956,7 @@ static int encoder_bwd(Net& n, const void* obs, int N, const float* dfeat_rows, 
 static int lstm_forward(Net& n, int T, int E, const uint8_t* masks, const float* h0,
                         const float* c0, cudaStream_t s) {
   const int N = T * E, Hd = n.H, G4 = 4 * Hd;
+  const bool seq = n.lstm_seq_on && lstm_seq_supported(Hd, E, n.gws.num_sms);
   for (int l = 0; l < n.L; ++l) {
     LstmL& q = n.lstm[l];
     GemmDesc gx;
@@ -963,6 +965,17 @@ static int lstm_forward(Net& n, int T, int E, const uint8_t* masks, const float*
     gx.B = q.Wih; gx.ldb = q.In;
     gx.C = n.gx; gx.ldc = G4; gx.bias = q.bsum;
     DDPPO_TRY(G(n, gx, s));
+    if (seq) {
+      // the whole recurrence of the layer in one launch
+      LstmSeq a{};
+      a.T = T; a.E = E; a.H = Hd;
+      a.gx = n.gx; a.m = masks; a.h0 = h0 + (size_t)l * E * Hd; a.c0 = c0 + (size_t)l * E * Hd;
+      a.Whh = q.Whh;
+      a.gates = q.gates; a.c = q.c; a.h = q.h; a.y_op = q.y; a.hm = q.hm;
+      a.bar = n.lstm_bar; a.err = n.gws.err; a.op_bf16 = n.bf ? 1 : 0;
+      DDPPO_TRY(launch_lstm_seq_fwd(a, n.gws.num_sms, s));
+      continue;
+    }
     DDPPO_TRY(launch_mask_state(h0 + (size_t)l * E * Hd, masks, E, Hd, q.hm, n.bf, s));
     for (int t = 0; t < T; ++t) {
       GemmDesc gh;
@@ -997,11 +1010,21 @@ static int lstm_forward(Net& n, int T, int E, const uint8_t* masks, const float*
 static int lstm_backward(Net& n, int T, int E, const uint8_t* masks, const float* c0,
                          const float* dtop, const float** dx0, cudaStream_t s) {
   const int N = T * E, Hd = n.H, G4 = 4 * Hd;
+  const bool seq = n.lstm_seq_on && lstm_seq_supported(Hd, E, n.gws.num_sms);
   const float* dabove = dtop;
   for (int l = n.L - 1; l >= 0; --l) {
     LstmL& q = n.lstm[l];
-    DDPPO_CHECK_CUDA(cudaMemsetAsync(n.dc_carry, 0, (size_t)E * Hd * sizeof(float), s));
-    for (int t = T - 1; t >= 0; --t) {
+    if (seq) {
+      LstmSeq a{};
+      a.T = T; a.E = E; a.H = Hd;
+      a.m = masks; a.c0 = c0 + (size_t)l * E * Hd; a.Whh = q.Whh;
+      a.gates = q.gates; a.c = q.c;
+      a.dh_above = dabove; a.dg32 = n.dg32; a.dg_op = n.dgop;
+      a.bar = n.lstm_bar; a.err = n.gws.err; a.op_bf16 = n.bf ? 1 : 0;
+      DDPPO_TRY(launch_lstm_seq_bwd(a, n.gws.num_sms, s));
+    }
+    if (!seq) DDPPO_CHECK_CUDA(cudaMemsetAsync(n.dc_carry, 0, (size_t)E * Hd * sizeof(float), s));
+    for (int t = seq ? -1 : T - 1; t >= 0; --t) {
       LstmBack b;
       b.E = E; b.H = Hd;
       b.gates = q.gates + (size_t)t * E * G4;

@@ -795,6 +795,12 @@ extern "C" int ddppo_update_graph(ddppo_ctx* x, int32_t on) {
   return DDPPO_OK;
 }
 
+extern "C" int ddppo_lstm_whole_segment(ddppo_ctx* x, int32_t on) {
+  ARG(x && x->net, "lstm_whole_segment: null ctx");
+  x->net->lstm_seq_on = on != 0;
+  return DDPPO_OK;
+}
+
 extern "C" int ddppo_autotune(ddppo_ctx* x, int32_t on, int64_t* tuned_shapes) {
   ARG(x && x->net, "autotune: null ctx");
   tc_tuner_enable(x->net->gws.tuner, on != 0);

@@ -156,6 +156,24 @@ struct LstmBack {
 };
 int launch_lstm_bwd(const LstmBack& a, cudaStream_t s);
 
+// The whole T-step recurrence of one LSTM layer (forward) or its back-propagation through
+// time (backward) in one cooperative launch (lstm_seq.cu). Forward: gx [T, E, 4H] (input
+// projection + biases), masks [T, E], h0 / c0 [E, H] -> gates [T, E, 4H], c, h [T, E, H],
+// y_op [T, E, H] (op dtype, may be null), hm [T, E, H] (op dtype: the masked state entering
+// each step, slot 0 included). Backward: gates, c, c0, masks, dh_above [T, E, H] ->
+// dg32 / dg_op [T, E, 4H]. Whh [4H, H] op dtype. bar: one device counter (zeroed by the
+// launcher); err: the sticky status word (timeout flag on a run-out barrier wait).
+struct LstmSeq {
+  int T, E, H;
+  const float* gx; const uint8_t* m; const float* h0; const float* c0; const void* Whh;
+  float* gates; float* c; float* h; void* y_op; void* hm;
+  const float* dh_above; float* dg32; void* dg_op;
+  unsigned* bar; int32_t* err; int op_bf16;
+};
+bool lstm_seq_supported(int H, int E, int num_sms);
+int launch_lstm_seq_fwd(const LstmSeq& a, int num_sms, cudaStream_t s);
+int launch_lstm_seq_bwd(const LstmSeq& a, int num_sms, cudaStream_t s);
+
 // heads: logits = h Wa^T + ba, value = h wv + bv (canonical fp32 weights)
 struct Heads {
   int N, H;
