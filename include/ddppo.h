@@ -495,6 +495,30 @@ int ddppo_conv2d_e4m3(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, 
                       const float* scale_x, const float* scale_w, float* y, float beta,
                       int32_t* status, void* stream);
 
+/* GroupNorm of the encoder (App. "Visual Encoder": GroupNorm in place of BatchNorm; C/2
+ * groups of 2 channels, eps 1e-5): out = act(gn(z) gamma + beta + resid) over NHWC z [dev]
+ * fp32 [N, HW, C]; gamma, beta [dev] [C]; resid [dev] [N, HW, C] or NULL; relu 0/1; mean,
+ * rstd [dev] [N, C/2] receive the group statistics. N <= 8192, C even <= 1024 (E_ARG
+ * otherwise). The first call per device allocates a scratch (not capturable). */
+int ddppo_group_norm(int32_t N, int32_t HW, int32_t C, const float* z, const float* gamma,
+                     const float* beta, const float* resid, int32_t relu, float* out, float* mean,
+                     float* rstd, void* stream);
+
+/* The SE-ResNeXt bottleneck's own kernels (App. "Visual Encoder"; ResNeXt's grouped
+ * convolution; squeeze-and-excitation), stand-alone, fp32 NHWC:
+ * ddppo_grouped_conv3x3: z [dev] [N, Ho, Wo, C] = the 3x3 convolution, padding 1, of x
+ * [dev] [N, H, W, C] with `groups` groups, weights w [dev] [C, C/groups, 3, 3] (PyTorch's
+ * grouped layout); C / groups <= 16, C <= 1024, stride 1 or 2 (E_ARG otherwise); the first
+ * call per device allocates a weight scratch (not capturable).
+ * ddppo_squeeze_excite: for u [dev] [N, HW, C]: m = mean_hw u [N, C], a = relu(W1 m + b1)
+ * [N, Cr], gate = sigmoid(W2 a + b2) [N, C], y = relu(u gate + sc) [N, HW, C] (sc [dev] or
+ * NULL); W1 [Cr, C], b1 [Cr], W2 [C, Cr], b2 [C]; every output [dev]. */
+int ddppo_grouped_conv3x3(int32_t N, int32_t H, int32_t W, int32_t C, int32_t groups, int32_t stride,
+                          const float* x, const float* w, float* z, void* stream);
+int ddppo_squeeze_excite(int32_t N, int32_t HW, int32_t C, int32_t Cr, const float* u,
+                         const float* sc, const float* W1, const float* b1, const float* W2,
+                         const float* b2, float* m, float* a, float* gate, float* y, void* stream);
+
 /* The paths and shared-memory staging geometry the tensor-core engine would use for a
  * bf16 convolution of this shape (the encoder of Sec. 4 "Agent") and for its weight
  * gradient. Host only: no CUDA call, no

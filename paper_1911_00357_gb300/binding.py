@@ -133,6 +133,9 @@ _SIGS = {
     "ddppo_conv2d_wgrad": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, F32, P, P],
     "ddppo_quantize_e4m3": [P, I32, I64, P, P, P],
     "ddppo_conv_plan": [I32, I32, I32, I32, I32, I32, I32, I32, P],
+    "ddppo_group_norm": [I32, I32, I32, P, P, P, P, I32, P, P, P, P],
+    "ddppo_grouped_conv3x3": [I32, I32, I32, I32, I32, I32, P, P, P, P],
+    "ddppo_squeeze_excite": [I32, I32, I32, I32, P, P, P, P, P, P, P, P, P, P, P],
     "ddppo_gemm_e4m3": [I32, I32, I32, P, I32, P, I32, P, P, P, I32, F32, P, I32, P, P],
     "ddppo_conv2d_e4m3": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, P, P, F32, P, P],
 }
@@ -499,3 +502,23 @@ def ddppo_conv2d(x, w, y, k: int, stride: int, pad: int, beta: float = 0.0, stat
     N, H, W, C = x.shape
     _check(lib().ddppo_conv2d(N, H, W, C, w.shape[0], k, stride, pad, _p(x), _p(w), _p(y),
                               beta, _p(status), _s()))
+
+
+def ddppo_group_norm(z, gamma, beta, out, mean, rstd, resid=None, relu=False):
+    """out = act(GroupNorm(z) + resid), C/2 groups; z, out, resid fp32 [N, HW, C]."""
+    N, HW, C = z.shape
+    _check(lib().ddppo_group_norm(N, HW, C, _p(z), _p(gamma), _p(beta), _p(resid), 1 if relu else 0,
+                                  _p(out), _p(mean), _p(rstd), _s()))
+
+
+def ddppo_grouped_conv3x3(x, w, z, groups: int, stride: int):
+    """z = grouped 3x3 convolution (padding 1) of NHWC fp32 x with w [C, C/groups, 3, 3]."""
+    N, H, W, C = x.shape
+    _check(lib().ddppo_grouped_conv3x3(N, H, W, C, groups, stride, _p(x), _p(w), _p(z), _s()))
+
+
+def ddppo_squeeze_excite(u, W1, b1, W2, b2, m, a, gate, y, sc=None):
+    """Squeeze-excite of u [N, HW, C] (fp32) with the shortcut sc; see the header."""
+    N, HW, C = u.shape
+    _check(lib().ddppo_squeeze_excite(N, HW, C, W1.shape[0], _p(u), _p(sc), _p(W1), _p(b1), _p(W2),
+                                      _p(b2), _p(m), _p(a), _p(gate), _p(y), _s()))

@@ -820,6 +820,68 @@ extern "C" int ddppo_autotune_import(ddppo_ctx* x, const void* buf, size_t size)
   return tc_tuner_import(x->net->gws.tuner, buf, size);
 }
 
+// ---- stand-alone GroupNorm (C/2 groups, the encoder's normalisation) ----
+extern "C" int ddppo_group_norm(int32_t N, int32_t HW, int32_t C, const float* z, const float* gamma,
+                                const float* beta, const float* resid, int32_t relu, float* out,
+                                float* mean, float* rstd, void* stream) {
+  ARG(N >= 1 && N <= 8192 && HW >= 1 && C >= 2 && C <= 1024 && C % 2 == 0,
+      "group_norm: N in [1, 8192], C even in [2, 1024]");
+  ARG(z && gamma && beta && out && mean && rstd, "group_norm: null argument");
+  int dev = 0;
+  DDPPO_CHECK_CUDA(cudaGetDevice(&dev));
+  ARG(dev < 64, "group_norm: device ordinal out of range");
+  static GnScratch ws[64];
+  if (!ws[dev].part) {
+    GnScratch w;
+    w.max_images = 8192;
+    w.part_elems = gn_part_elems(w.max_images, 1024);
+    DDPPO_CHECK_CUDA(cudaMalloc(&w.part, w.part_elems * sizeof(float)));
+    DDPPO_CHECK_CUDA(cudaMalloc(&w.cnt, (size_t)w.max_images * sizeof(int)));
+    DDPPO_CHECK_CUDA(cudaMemset(w.cnt, 0, (size_t)w.max_images * sizeof(int)));
+    ws[dev] = w;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  DDPPO_TRY(launch_gn_stats(z, N, HW, C, 1e-5f, mean, rstd, ws[dev], s));
+  GNApply a{};
+  a.z = z; a.mean = mean; a.rstd = rstd; a.gamma = gamma; a.beta = beta;
+  a.resid = resid; a.out = out; a.relu = relu ? 1 : 0;
+  return launch_gn_apply(a, N, HW, C, s);
+}
+
+// ---- stand-alone SE-ResNeXt pieces: grouped 3x3 convolution and squeeze-excite ----
+extern "C" int ddppo_grouped_conv3x3(int32_t N, int32_t H, int32_t W, int32_t C, int32_t groups,
+                                     int32_t stride, const float* x, const float* w, float* z,
+                                     void* stream) {
+  ARG(N >= 1 && H >= 1 && W >= 1 && groups >= 1 && C % groups == 0 && C / groups <= 16 &&
+          (stride == 1 || stride == 2) && C <= 1024,
+      "grouped_conv3x3: bad sizes (C / groups <= 16, C <= 1024, stride 1 or 2)");
+  ARG(x && w && z, "grouped_conv3x3: null argument");
+  int dev = 0;
+  DDPPO_CHECK_CUDA(cudaGetDevice(&dev));
+  ARG(dev < 64, "grouped_conv3x3: device ordinal out of range");
+  static float* wbuf[64] = {};
+  if (!wbuf[dev]) DDPPO_CHECK_CUDA(cudaMalloc(&wbuf[dev], (size_t)1024 * 16 * 9 * sizeof(float)));
+  cudaStream_t s = (cudaStream_t)stream;
+  GConv g;
+  g.N = N; g.H = H; g.W = W; g.C = C; g.cpg = C / groups; g.s = stride;
+  g.Ho = (H + 2 - 3) / stride + 1; g.Wo = (W + 2 - 3) / stride + 1;
+  DDPPO_TRY(launch_gconv_w_prep(w, C, g.cpg, wbuf[dev], false, s));
+  return launch_gconv_fwd(g, x, wbuf[dev], z, false, s);
+}
+
+extern "C" int ddppo_squeeze_excite(int32_t N, int32_t HW, int32_t C, int32_t Cr, const float* u,
+                                    const float* sc, const float* W1, const float* b1,
+                                    const float* W2, const float* b2, float* m, float* a,
+                                    float* gate, float* y, void* stream) {
+  ARG(N >= 1 && HW >= 1 && C >= 1 && Cr >= 1 && C <= 4096, "squeeze_excite: bad sizes");
+  ARG(u && W1 && b1 && W2 && b2 && m && a && gate && y, "squeeze_excite: null argument");
+  SeArgs e{};
+  e.N = N; e.HW = HW; e.C = C; e.Cr = Cr;
+  e.u = u; e.sc = sc; e.W1 = W1; e.b1 = b1; e.W2 = W2; e.b2 = b2;
+  e.m = m; e.a = a; e.gate = gate; e.y = y;
+  return launch_se_fwd(e, (cudaStream_t)stream);
+}
+
 // ---- stand-alone convolution on the implicit-im2col tensor-core path ----
 static int standalone_ws(GemmWorkspace* ws, int32_t* status) {
   int dev = 0;

@@ -204,3 +204,62 @@ def test_sx_worker_iterations(kind):
         assert before.numel() == OP.num_params(ncfg)
     finally:
         w.close()
+
+
+# ---------------------------------------------------------------- the kernels on their own
+@pytest.mark.parametrize("N,H,W,C,G,s", [(2, 8, 8, 32, 32, 1), (3, 9, 7, 64, 32, 2), (2, 16, 16, 128, 32, 1),
+                                         (1, 8, 8, 512, 32, 2), (2, 5, 6, 12, 3, 1)])
+def test_grouped_conv3x3_matches_float64(N, H, W, C, G, s):
+    g = torch.Generator().manual_seed(C + s)
+    x = torch.randn(N, H, W, C, generator=g)
+    w = torch.randn(C, C // G, 3, 3, generator=g)
+    Ho, Wo = (H - 1) // s + 1, (W - 1) // s + 1
+    z = torch.zeros(N, Ho, Wo, C, device="cuda")
+    B.ddppo_grouped_conv3x3(x.cuda(), w.cuda(), z, G, s)
+    torch.cuda.synchronize()
+    ref = torch.nn.functional.conv2d(x.double().permute(0, 3, 1, 2), w.double(), stride=s, padding=1,
+                                     groups=G).permute(0, 2, 3, 1)
+    err = (z.cpu().double() - ref).abs().max().item()
+    assert err <= 1e-5 * max(1.0, ref.abs().max().item()), err
+
+
+@pytest.mark.parametrize("N,HW,C,shortcut", [(3, 16, 128, True), (2, 64, 64, False), (4, 1, 1024, True)])
+def test_squeeze_excite_matches_float64(N, HW, C, shortcut):
+    g = torch.Generator().manual_seed(N * HW + C)
+    Cr = C // 16
+    u = torch.randn(N, HW, C, generator=g)
+    sc = torch.randn(N, HW, C, generator=g) if shortcut else None
+    W1, b1 = torch.randn(Cr, C, generator=g) / C ** 0.5, torch.randn(Cr, generator=g) * 0.1
+    W2, b2 = torch.randn(C, Cr, generator=g) / Cr ** 0.5, torch.randn(C, generator=g) * 0.1
+    m = torch.zeros(N, C, device="cuda")
+    a = torch.zeros(N, Cr, device="cuda")
+    gate = torch.zeros(N, C, device="cuda")
+    y = torch.zeros(N, HW, C, device="cuda")
+    B.ddppo_squeeze_excite(u.cuda(), W1.cuda(), b1.cuda(), W2.cuda(), b2.cuda(), m, a, gate, y,
+                           sc.cuda() if shortcut else None)
+    torch.cuda.synchronize()
+    p = {"q.se1.w": W1.double(), "q.se1.b": b1.double(), "q.se2.w": W2.double(), "q.se2.b": b2.double()}
+    ref = OP.squeeze_excite(p, "q.", u.double().permute(0, 2, 1).reshape(N, C, HW, 1))
+    ref = ref.reshape(N, C, HW).permute(0, 2, 1)
+    if shortcut:
+        ref = ref + sc.double()
+    ref = torch.relu(ref)
+    assert (y.cpu().double() - ref).abs().max().item() <= 1e-5 * max(1.0, ref.abs().max().item())
+    assert torch.allclose(m.cpu().double(), u.double().mean(1), atol=1e-5)
+
+
+def test_group_norm_entry_matches_float64():
+    g = torch.Generator().manual_seed(4)
+    N, HW, C = 3, 16, 1024
+    z = torch.randn(N, HW, C, generator=g) * 2 + 0.5
+    gam, bet = 1 + 0.1 * torch.randn(C, generator=g), 0.1 * torch.randn(C, generator=g)
+    res = torch.randn(N, HW, C, generator=g)
+    out = torch.zeros(N, HW, C, device="cuda")
+    mean = torch.zeros(N, C // 2, device="cuda")
+    rstd = torch.zeros(N, C // 2, device="cuda")
+    B.ddppo_group_norm(z.cuda(), gam.cuda(), bet.cuda(), out, mean, rstd, resid=res.cuda(), relu=True)
+    torch.cuda.synchronize()
+    ref = torch.nn.functional.group_norm(z.double().permute(0, 2, 1), C // 2, gam.double(), bet.double(),
+                                         1e-5).permute(0, 2, 1)
+    ref = torch.relu(ref + res.double())
+    assert (out.cpu().double() - ref).abs().max().item() <= 1e-4
