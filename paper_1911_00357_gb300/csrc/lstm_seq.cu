@@ -31,7 +31,7 @@ namespace {
 constexpr int LS_THREADS = 256;
 constexpr int LS_KPER = 32;     // recurrent weights per thread (registers)
 constexpr int LS_ET_FWD = 32;   // envs per staged tile (forward)
-constexpr int LS_ET_BWD = 8;    // envs per staged tile (backward: rows of 4H)
+constexpr int LS_ET_BWD = 16;   // envs per staged tile (backward: rows of 4H)
 constexpr int LS_MAX_E = 64;
 constexpr unsigned LS_SPIN_LIMIT = 1u << 22;
 
@@ -50,6 +50,53 @@ __device__ __forceinline__ void st_opv(void* p, size_t i, float v, int bf) {
   else ((float*)p)[i] = v;
 }
 __device__ __forceinline__ float sigm(float x) { return 1.f / (1.f + expf(-x)); }
+
+// dst[0, n) (fp32, shared) <- src[off, off + n) (operand dtype, global, read through L2);
+// n and off multiples of 8. 16-byte loads, eight in flight per thread: the staging is one
+// or two L2 round trips rather than one per element.
+__device__ __forceinline__ void stage_flat(float* dst, const void* src, size_t off, int n, int bf) {
+  constexpr int UNR = 8;
+  if (bf) {
+    const uint4* sv = reinterpret_cast<const uint4*>((const __nv_bfloat16*)src + off);
+    const int nv = n >> 3;
+    for (int i0 = threadIdx.x; i0 < nv; i0 += blockDim.x * UNR) {
+      uint4 v[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const int j = i0 + u * blockDim.x;
+        if (j < nv) v[u] = __ldcg(sv + j);
+      }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const int j = i0 + u * blockDim.x;
+        if (j >= nv) break;
+        const uint32_t w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+        float4* d = reinterpret_cast<float4*>(dst + (size_t)j * 8);
+        d[0] = make_float4(__uint_as_float(w[0] << 16), __uint_as_float(w[0] & 0xffff0000u),
+                           __uint_as_float(w[1] << 16), __uint_as_float(w[1] & 0xffff0000u));
+        d[1] = make_float4(__uint_as_float(w[2] << 16), __uint_as_float(w[2] & 0xffff0000u),
+                           __uint_as_float(w[3] << 16), __uint_as_float(w[3] & 0xffff0000u));
+      }
+    }
+  } else {
+    const float4* sv = reinterpret_cast<const float4*>((const float*)src + off);
+    const int nv = n >> 2;
+    for (int i0 = threadIdx.x; i0 < nv; i0 += blockDim.x * UNR) {
+      float4 v[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const int j = i0 + u * blockDim.x;
+        if (j < nv) v[u] = __ldcg(sv + j);
+      }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const int j = i0 + u * blockDim.x;
+        if (j >= nv) break;
+        reinterpret_cast<float4*>(dst)[j] = v[u];
+      }
+    }
+  }
+}
 
 // grid-wide barrier number `round` (0, 1, ...): every CTA adds one arrival and waits for
 // (round + 1) * gridDim.x; false when the wait ran out (timeout flag set)
@@ -101,15 +148,13 @@ __global__ void __launch_bounds__(LS_THREADS, 1) lstm_seq_fwd_kernel(LstmSeq a) 
     for (int e0 = 0; e0 < E; e0 += ET) {
       const int ne = min(ET, E - e0);
       // stage the masked previous state of the tile (operand dtype values)
-      for (int i = tid; i < ne * H; i += LS_THREADS) {
-        const int e = i / H, k = i - e * H;
-        float v;
-        if (t == 0) {
-          v = a.m[e0 + e] ? round_op(a.h0[(size_t)(e0 + e) * H + k], bf) : 0.f;
-        } else {
-          v = ld_op_cg(a.hm, ((size_t)t * E + e0 + e) * H + k, bf);
+      if (t == 0) {
+        for (int i = tid; i < ne * H; i += LS_THREADS) {
+          const int e = i / H, k = i - e * H;
+          hs[i] = a.m[e0 + e] ? round_op(a.h0[(size_t)(e0 + e) * H + k], bf) : 0.f;
         }
-        hs[i] = v;
+      } else {
+        stage_flat(hs, a.hm, ((size_t)t * E + e0) * H, ne * H, bf);
       }
       __syncthreads();
       for (int e = 0; e < ne; ++e) {
@@ -212,10 +257,7 @@ __global__ void __launch_bounds__(LS_THREADS, 1) lstm_seq_bwd_kernel(LstmSeq a) 
     // phase B: dh_rec[e][u] = sum_j R(dz_t)[e][j] W_hh[j][u] for this CTA's units
     for (int e0 = 0; e0 < E; e0 += ET) {
       const int ne = min(ET, E - e0);
-      for (int i = tid; i < ne * G4; i += LS_THREADS) {
-        const int e = i / G4, j = i - e * G4;
-        dgs[i] = ld_op_cg(a.dg_op, ((size_t)t * E + e0 + e) * G4 + j, bf);
-      }
+      stage_flat(dgs, a.dg_op, ((size_t)t * E + e0) * G4, ne * G4, bf);
       __syncthreads();
       for (int e = 0; e < ne; ++e) {
         const float* de = dgs + (size_t)e * G4 + jc;

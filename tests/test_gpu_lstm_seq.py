@@ -19,6 +19,16 @@ from tests.test_gpu_policy import Net, _cfg, _dev_inputs, _rollout_tensors, _vie
 pytestmark = pytest.mark.gpu
 
 
+def _cfg2(name, E, T, precision, mb=1):
+    # hidden sizes whose units split unevenly over the SMs (U = 2 units per CTA for H = 32)
+    extra = {"nature_h32": dict(hidden=32), "nature_h64": dict(hidden=64)}
+    if name in extra:
+        from paper_1911_00357_gb300.presets import make_config
+        return make_config("nature_fp32", num_envs=E, rollout_T=T, minibatches=mb,
+                           precision=precision, lstm_layers=2, **extra[name])
+    return _cfg(name, E, T, precision, mb=mb)
+
+
 def _run(net, cfg, T, E, whole):
     B.ddppo_lstm_whole_segment(net.h, whole)
     mb = I.minibatch(net.ncfg, T=T, E=E, seed=2)
@@ -46,10 +56,11 @@ def _run(net, cfg, T, E, whole):
 
 
 @pytest.mark.parametrize("name,T,E,precision", [("nature_small", 7, 5, 0), ("resnet_small", 6, 4, 0),
+                                                ("nature_h32", 5, 3, 0), ("nature_h64", 5, 64, 0),
                                                 ("blind_full", 9, 6, 0), ("nature_full", 8, 33, 0),
                                                 ("blind_full", 9, 6, 1), ("resnet_full", 4, 3, 1)])
 def test_whole_segment_matches_step_by_step(name, T, E, precision):
-    cfg = _cfg(name, E, T, precision)
+    cfg = _cfg2(name, E, T, precision)
     net = Net(cfg, seed=1)
     try:
         a = _run(net, cfg, T, E, True)

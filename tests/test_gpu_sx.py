@@ -57,11 +57,13 @@ def _eval_backward(net, cfg, T, E):
     return ref, logits.cpu(), values.cpu(), grad.cpu().double(), dl.double(), dv.double()
 
 
-@pytest.mark.parametrize("kind,base,T,E", [(3, 16, 2, 2), (3, 32, 2, 2)])
-def test_sx_fp32_evaluate_and_backward(kind, base, T, E):
+@pytest.mark.parametrize("kind,base,T,E,whole", [(3, 16, 2, 2, True), (3, 32, 2, 2, True),
+                                                  (3, 16, 2, 2, False)])
+def test_sx_fp32_evaluate_and_backward(kind, base, T, E, whole):
     cfg = _sx_cfg(kind, base, E, T, 0)
     net = Net(cfg, seed=1)
     try:
+        B.ddppo_lstm_whole_segment(net.h, whole)
         ref, lg, vv, gg, dl, dv = _eval_backward(net, cfg, T, E)
         lg_r, v_r, g_r = _forward_grad(OP.sequence_forward, net.flat64(), ref, net.ncfg, dl, dv)
         assert _rel(lg, lg_r) <= 1e-4 and _rel(vv, v_r) <= 1e-4, (_rel(lg, lg_r), _rel(vv, v_r))
