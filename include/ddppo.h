@@ -546,13 +546,15 @@ int ddppo_gemm_backend(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const v
 int ddppo_update_graph(ddppo_ctx* ctx, int32_t on);
 
 /* The LSTM recurrence (App. "Agent Design"; Sec. 4 "Training": BPTT over the rollout):
- * on = 1 (the default) runs each layer's whole T-step forward, and its back-propagation
- * through time, as one cooperative launch (the recurrent weights held in registers
- * across the SMs, one grid barrier per step) wherever the shape allows (at most 64 envs
- * per segment, hidden sizes whose 4H gate rows split over the SMs); on = 0 launches a
- * recurrent contraction and a cell kernel per step. Both compute the same arithmetic;
- * the contraction's fp32 summation order differs. Applies to launches enqueued afterwards
- * (a captured graph keeps the mode it was captured with). Host only. */
+ * on = 0 (the default) launches a recurrent contraction and a cell kernel per step;
+ * on = 1 runs each layer's whole T-step forward, and its back-propagation through time,
+ * as one cooperative launch (the recurrent weights held in registers across the SMs, one
+ * grid barrier per step) wherever the shape allows (at most 64 envs per segment, hidden
+ * sizes whose 4H gate rows split over the SMs). Both compute the same arithmetic; the
+ * contraction's fp32 summation order differs. The whole-segment form is slower at the
+ * default sizes (its per-step contraction is bound by shared-memory loads: one FMA per
+ * loaded state value), hence off by default. Applies to launches enqueued afterwards (a
+ * captured graph keeps the mode it was captured with). Host only. */
 int ddppo_lstm_whole_segment(ddppo_ctx* ctx, int32_t on);
 
 /* Tile-shape autotuner of the tensor-core GEMM (precision 1): on by default. The first

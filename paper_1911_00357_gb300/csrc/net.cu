@@ -837,7 +837,11 @@ static int encoder_fwd(Net& n, const void* obs, int N, void* featop_rows, cudaSt
   const float* cur = n.pool;
   const __nv_bfloat16* cur_bf = f8 ? nullptr : n.pool_bf;
   if (!n.sx.empty()) {
-    for (SxL& X : n.sx) DDPPO_TRY(sx_block_fwd(n, X, N, cur, cur_bf, s));
+    for (SxL& X : n.sx) {
+      DDPPO_TRY(sx_block_fwd(n, X, N, cur, cur_bf, s));
+      cur = X.y;
+      cur_bf = n.bf ? X.y_bf : nullptr;
+    }
     const SxL& L = n.sx.back();
     DDPPO_TRY(conv_fwd(n, n.cmp, L.y, false, N, n.cmp.z, false, s, L.y_bf));
     DDPPO_TRY(gn_fwd(n, n.cmp_n, n.cmp.z, N, n.featHW, n.cmp_n.out, true, nullptr, nullptr, nullptr, s));

@@ -204,7 +204,7 @@ struct Net {
   bool upd_graph_on = true;      // caller's choice (ddppo_update_graph)
   int64_t* d_steps = nullptr;    // [2] device: update index, Adam steps before this update
   unsigned* lstm_bar = nullptr;  // grid-barrier counter of the whole-segment LSTM kernels
-  bool lstm_seq_on = true;       // whole-segment LSTM recurrence where the shape allows
+  bool lstm_seq_on = false;      // whole-segment LSTM recurrence where the shape allows
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   uint8_t* post_done = nullptr;

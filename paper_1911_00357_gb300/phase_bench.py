@@ -27,12 +27,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--precision", type=int, default=None, help="override the preset's precision")
-    ap.add_argument("--lstm-step", action="store_true",
-                    help="step-by-step LSTM recurrence instead of the whole-segment kernels")
+    ap.add_argument("--lstm-whole", action="store_true",
+                    help="whole-segment LSTM kernels instead of the step-by-step recurrence")
     args = ap.parse_args()
     w = Worker(args.preset, seed=args.seed, precision=args.precision)
-    if args.lstm_step:
-        B.ddppo_lstm_whole_segment(w.h, False)
+    if args.lstm_whole:
+        B.ddppo_lstm_whole_segment(w.h, True)
     try:
         for _ in range(args.warmup):
             w.iterate()
@@ -60,7 +60,7 @@ def main():
         frames = w.E * w.T
         print(json.dumps({
             "preset": args.preset, "precision": w.cfg.precision, "num_envs": w.E, "rollout_T": w.T,
-            "seed": args.seed, "lstm": "step" if args.lstm_step else "whole-segment",
+            "seed": args.seed, "lstm": "whole-segment" if args.lstm_whole else "step",
             "collect_ms": round(c, 2), "update_ms": round(u, 2),
             "act_frames_per_s": round(frames / c * 1e3, 1),
             "frames_per_s": round(frames / (c + u) * 1e3, 1),

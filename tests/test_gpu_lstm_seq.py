@@ -4,7 +4,7 @@ contraction and a cell kernel per step). Both compute the same arithmetic; only 
 recurrent contraction's fp32 summation order differs, so results agree to fp32 accuracy:
 logits, values, LSTM states and every gradient tensor within 1e-5 relative (1e-4 for the
 gradients, which sum over the segment), and a whole 2 x 2 PPO update within 2% of
-lr x steps per coordinate. The float64 oracle parity of the default (whole-segment) path
+lr x steps per coordinate. The float64 oracle parity of the default (step-by-step) path
 is covered by the policy and update parity tests.
 """
 import numpy as np
