@@ -503,6 +503,15 @@ int ddppo_conv2d_e4m3(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, 
 int ddppo_group_norm(int32_t N, int32_t HW, int32_t C, const float* z, const float* gamma,
                      const float* beta, const float* resid, int32_t relu, float* out, float* mean,
                      float* rstd, void* stream);
+/* How the encoder's forward GroupNorms run: on = 1 (the default) computes the statistics
+ * and normalises in one cooperative launch wherever every block fits on the GPU at once
+ * (the images' blocks meet at a bounded per-image barrier; z is read from HBM once);
+ * otherwise, and with on = 0, a statistics launch then a normalise launch. Both give the
+ * same statistics for the same split of an image over blocks; the one-launch form may use
+ * fewer blocks per image, which changes only the fp32 summation order. ddppo_group_norm
+ * takes the one-launch form when it fits. Applies to launches enqueued afterwards. Host
+ * only. */
+int ddppo_group_norm_one_launch(ddppo_ctx* ctx, int32_t on);
 
 /* The SE-ResNeXt bottleneck's own kernels (App. "Visual Encoder"; ResNeXt's grouped
  * convolution; squeeze-and-excitation), stand-alone, fp32 NHWC:

@@ -126,6 +126,7 @@ _SIGS = {
     "ddppo_timing_launches": [P, I32, P, P, P, I64, P],
     "ddppo_autotune": [P, I32, P],
     "ddppo_lstm_whole_segment": [P, I32],
+    "ddppo_group_norm_one_launch": [P, I32],
     "ddppo_update_graph": [P, I32],
     "ddppo_autotune_export": [P, P, ctypes.c_size_t, P],
     "ddppo_autotune_import": [P, P, ctypes.c_size_t],
@@ -427,6 +428,10 @@ def ddppo_update_graph(h, on: bool = True) -> None:
 
 def ddppo_lstm_whole_segment(h, on: bool = True) -> None:
     _check(lib().ddppo_lstm_whole_segment(h, 1 if on else 0))
+
+
+def ddppo_group_norm_one_launch(h, on: bool = True) -> None:
+    _check(lib().ddppo_group_norm_one_launch(h, 1 if on else 0))
 
 
 def ddppo_autotune(h, on: bool = True) -> int:

@@ -115,18 +115,13 @@ __device__ __forceinline__ bool last_of_image(int* cnt, int S, int* flag) {
 }
 
 // ---- statistics: shifted sums about the image's first pixel, combined in double ----
+// the block's per-channel (sum d, sum d^2), d = z - z[first pixel], over its pixel rows
+// [pb, pe) of image zi, written to pp[2c], pp[2c + 1]
 template <int V>
-__global__ void __launch_bounds__(kThreads) gn_stats_kernel(const float* __restrict__ z, int HW, int C,
-                                                            int S, float eps, float* __restrict__ part,
-                                                            int* __restrict__ cnt, float* __restrict__ mean,
-                                                            float* __restrict__ rstd) {
-  extern __shared__ float sh[];
-  __shared__ int flag;
+__device__ __forceinline__ void block_shifted_sums(const float* __restrict__ zi, int pb, int pe, int C,
+                                                   float* sh, float* pp) {
   const int R = C / V, P = blockDim.x / R;
-  const int n = blockIdx.y, sb = blockIdx.x;
   const int cv = threadIdx.x % R, pr = threadIdx.x / R, c0 = cv * V;
-  const int chunk = (HW + S - 1) / S, pb = sb * chunk, pe = min(HW, pb + chunk);
-  const float* zi = z + (size_t)n * HW * C;
   float K[V], s1[V], s2[V];
   ldv<V>(zi + c0, K);
 #pragma unroll
@@ -142,11 +137,14 @@ __global__ void __launch_bounds__(kThreads) gn_stats_kernel(const float* __restr
       s2[v] += d * d;
     }
   }
-  float* pp = part + ((size_t)n * S + sb) * C * 2;
   block_pair_sums<V>(s1, s2, sh, C, pp);
-  if (!last_of_image(cnt + n, S, &flag)) return;
-  // the image's S x C x 2 partials, staged in shared memory with all loads in flight
-  const float* pim = part + (size_t)n * S * C * 2;
+}
+
+// the image's group means and 1 / sqrt(var + eps) from its S x C x 2 partials, read
+// through L2 into sh and combined in block order (double); results to mean[g], rstd[g]
+__device__ __forceinline__ void combine_groups(const float* pim, const float* __restrict__ zi, int S,
+                                               int C, int HW, float eps, float* sh, float* mean,
+                                               float* rstd) {
   for (int i = threadIdx.x; i < S * C * 2; i += blockDim.x) sh[i] = __ldcg(pim + i);
   __syncthreads();
   const int G = C / 2;
@@ -166,13 +164,71 @@ __global__ void __launch_bounds__(kThreads) gn_stats_kernel(const float* __restr
     const double dm = m[0] - m[1];
     double var = (M2[0] + M2[1] + 0.5 * HW * dm * dm) / (2.0 * HW);
     if (var < 0.0) var = 0.0;
-    mean[(size_t)n * G + g] = (float)(0.5 * (m[0] + m[1]));
-    rstd[(size_t)n * G + g] = 1.0f / sqrtf((float)var + eps);
+    mean[g] = (float)(0.5 * (m[0] + m[1]));
+    rstd[g] = 1.0f / sqrtf((float)var + eps);
   }
+}
+
+template <int V>
+__global__ void __launch_bounds__(kThreads) gn_stats_kernel(const float* __restrict__ z, int HW, int C,
+                                                            int S, float eps, float* __restrict__ part,
+                                                            int* __restrict__ cnt, float* __restrict__ mean,
+                                                            float* __restrict__ rstd) {
+  extern __shared__ float sh[];
+  __shared__ int flag;
+  const int n = blockIdx.y, sb = blockIdx.x;
+  const int chunk = (HW + S - 1) / S, pb = sb * chunk, pe = min(HW, pb + chunk);
+  const float* zi = z + (size_t)n * HW * C;
+  block_shifted_sums<V>(zi, pb, pe, C, sh, part + ((size_t)n * S + sb) * C * 2);
+  if (!last_of_image(cnt + n, S, &flag)) return;
+  const int G = C / 2;
+  combine_groups(part + (size_t)n * S * C * 2, zi, S, C, HW, eps, sh, mean + (size_t)n * G,
+                 rstd + (size_t)n * G);
   if (threadIdx.x == 0) cnt[n] = 0;  // re-arm for the next launch on this stream
 }
 
 // ---- out = act(gn(z) + res) ----
+// one vector of V channels at element offset o (channel c0) of image n; mu/rs (and mud/rsd)
+// point at the group statistics of channel c0 (group c0 / 2); returns max |out| (E4M3 copy)
+template <int V>
+__device__ __forceinline__ float apply_vec(const GNApply& a, size_t o, int c0, const float* mu,
+                                           const float* rs, const float* mud, const float* rsd,
+                                           float f8s) {
+  float x[V], gm[V], bt[V];
+  ldv<V>(a.z + o, x);
+  ldv<V>(a.gamma + c0, gm);
+  ldv<V>(a.beta + c0, bt);
+#pragma unroll
+  for (int v = 0; v < V; ++v) x[v] = (x[v] - mu[v / 2]) * rs[v / 2] * gm[v] + bt[v];
+  if (a.resid) {
+    float r[V];
+    ldv<V>(a.resid + o, r);
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] += r[v];
+  }
+  if (a.zd) {
+    float d[V], gd[V], bd[V];
+    ldv<V>(a.zd + o, d);
+    ldv<V>(a.gamma_d + c0, gd);
+    ldv<V>(a.beta_d + c0, bd);
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] += (d[v] - mud[v / 2]) * rsd[v / 2] * gd[v] + bd[v];
+  }
+  if (a.relu) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) x[v] = fmaxf(x[v], 0.f);
+  }
+  if (a.out) stv<V>(a.out + o, x);
+  if (a.out_bf) stv_bf<V>(a.out_bf + o, x);
+  float f8m = 0.f;
+  if (a.out_f8) {
+    stv_e4m3<V>(a.out_f8 + o, x, f8s);
+#pragma unroll
+    for (int v = 0; v < V; ++v) f8m = fmaxf(f8m, fabsf(x[v]));
+  }
+  return f8m;
+}
+
 template <int V>
 __global__ void __launch_bounds__(kThreads) gn_apply_kernel(GNApply a, int HW, int C) {
   const int R = C / V, G = C / 2;
@@ -182,44 +238,93 @@ __global__ void __launch_bounds__(kThreads) gn_apply_kernel(GNApply a, int HW, i
   const float f8s = a.out_f8 ? *a.f8_scale : 1.f;
   float f8m = 0.f;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per; i += gridDim.x * blockDim.x) {
-    const int cv = i % R, c0 = cv * V;
-    const size_t o = ib + (size_t)i * V;
-    float x[V], gm[V], bt[V];
-    ldv<V>(a.z + o, x);
-    ldv<V>(a.gamma + c0, gm);
-    ldv<V>(a.beta + c0, bt);
-    const float* mu = a.mean + (size_t)n * G + c0 / 2;
-    const float* rs = a.rstd + (size_t)n * G + c0 / 2;
-#pragma unroll
-    for (int v = 0; v < V; ++v) x[v] = (x[v] - mu[v / 2]) * rs[v / 2] * gm[v] + bt[v];
-    if (a.resid) {
-      float r[V];
-      ldv<V>(a.resid + o, r);
-#pragma unroll
-      for (int v = 0; v < V; ++v) x[v] += r[v];
+    const int c0 = (i % R) * V;
+    const size_t gq = (size_t)n * G + c0 / 2;
+    const float* mud = a.zd ? a.mean_d + gq : nullptr;
+    const float* rsd = a.zd ? a.rstd_d + gq : nullptr;
+    f8m = fmaxf(f8m, apply_vec<V>(a, ib + (size_t)i * V, c0, a.mean + gq, a.rstd + gq, mud, rsd, f8s));
+  }
+  if (a.out_f8) block_amax(f8m, a.f8_amax);
+}
+
+// ---- statistics and normalisation in one launch ----
+// Every block of the (S, N) grid is resident (cooperative launch). Each block sums its
+// pixel rows as the statistics kernel does (z, and zd when present); the S blocks of an
+// image then meet at a per-image barrier: an arrival counter, and a departure counter
+// whose last increment re-arms both for the next launch. The wait is bounded: on a
+// run-out the sticky timeout flag is set and the block returns without writing. After
+// the barrier each block combines the image's partials in block order exactly as the
+// statistics kernel's last block does (so the statistics are bit-identical for the same
+// S), block 0 of the image stores them for the backward, and every block normalises the
+// rows it just summed (still in L2): z is read from HBM once, and one launch replaces two.
+constexpr unsigned GN_SPIN_LIMIT = 1u << 22;
+
+__device__ __forceinline__ bool image_barrier(int* arrive, int* depart, int S, int32_t* err,
+                                              int* s_ok) {
+  __threadfence();  // this thread's partial sums are visible device-wide before the arrival
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    atomicAdd(arrive, 1);
+    int ok = 0;
+    for (unsigned i = 0; i < GN_SPIN_LIMIT; ++i) {
+      if (*(volatile int*)arrive >= S) { ok = 1; break; }
+      if (err && (*(volatile int32_t*)err & ERRF_TIMEOUT)) break;
+      __nanosleep(64);
     }
-    if (a.zd) {
-      float d[V], gd[V], bd[V];
-      ldv<V>(a.zd + o, d);
-      ldv<V>(a.gamma_d + c0, gd);
-      ldv<V>(a.beta_d + c0, bd);
-      const float* mud = a.mean_d + (size_t)n * G + c0 / 2;
-      const float* rsd = a.rstd_d + (size_t)n * G + c0 / 2;
-#pragma unroll
-      for (int v = 0; v < V; ++v) x[v] += (d[v] - mud[v / 2]) * rsd[v / 2] * gd[v] + bd[v];
+    if (!ok && err) atomicOr(err, ERRF_TIMEOUT);
+    __threadfence();
+    // every block has stopped reading `arrive` once the departures reach S
+    if (atomicAdd(depart, 1) == S - 1) {
+      atomicExch(arrive, 0);
+      atomicExch(depart, 0);
     }
-    if (a.relu) {
-#pragma unroll
-      for (int v = 0; v < V; ++v) x[v] = fmaxf(x[v], 0.f);
-    }
-    if (a.out) stv<V>(a.out + o, x);
-    if (a.out_bf) stv_bf<V>(a.out_bf + o, x);
-    if (a.out_f8) {
-      stv_e4m3<V>(a.out_f8 + o, x, f8s);
-#pragma unroll
-      for (int v = 0; v < V; ++v) f8m = fmaxf(f8m, fabsf(x[v]));
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
+}
+
+template <int V>
+__global__ void __launch_bounds__(kThreads) gn_fused_kernel(GNApply a, int HW, int C, int S, float eps,
+                                                            float* __restrict__ part,
+                                                            float* __restrict__ part_d, int* arrive,
+                                                            int* depart, int32_t* err) {
+  extern __shared__ float sh[];
+  __shared__ int s_ok;
+  const int n = blockIdx.y, sb = blockIdx.x, G = C / 2;
+  const int chunk = (HW + S - 1) / S, pb = sb * chunk, pe = min(HW, pb + chunk);
+  const size_t ib = (size_t)n * HW * C;
+  float* st = sh + max((int)blockDim.x * 2 * V, S * C * 2);  // [4][G]: mean, rstd, mean_d, rstd_d
+  block_shifted_sums<V>(a.z + ib, pb, pe, C, sh, part + ((size_t)n * S + sb) * C * 2);
+  if (a.zd) {
+    __syncthreads();
+    block_shifted_sums<V>(a.zd + ib, pb, pe, C, sh, part_d + ((size_t)n * S + sb) * C * 2);
+  }
+  if (!image_barrier(arrive + n, depart + n, S, err, &s_ok)) return;
+  combine_groups(part + (size_t)n * S * C * 2, a.z + ib, S, C, HW, eps, sh, st, st + G);
+  if (a.zd) {
+    __syncthreads();
+    combine_groups(part_d + (size_t)n * S * C * 2, a.zd + ib, S, C, HW, eps, sh, st + 2 * G,
+                   st + 3 * G);
+  }
+  __syncthreads();
+  if (sb == 0) {
+    for (int g = threadIdx.x; g < G; g += blockDim.x) {
+      const_cast<float*>(a.mean)[(size_t)n * G + g] = st[g];
+      const_cast<float*>(a.rstd)[(size_t)n * G + g] = st[G + g];
+      if (a.zd) {
+        const_cast<float*>(a.mean_d)[(size_t)n * G + g] = st[2 * G + g];
+        const_cast<float*>(a.rstd_d)[(size_t)n * G + g] = st[3 * G + g];
+      }
     }
   }
+  const int R = C / V, P = blockDim.x / R;
+  const int cv = threadIdx.x % R, pr = threadIdx.x / R, c0 = cv * V;
+  const float f8s = a.out_f8 ? *a.f8_scale : 1.f;
+  float f8m = 0.f;
+  for (int p = pb + pr; p < pe; p += P)
+    f8m = fmaxf(f8m, apply_vec<V>(a, ib + (size_t)p * C + c0, c0, st + c0 / 2, st + G + c0 / 2,
+                                  st + 2 * G + c0 / 2, st + 3 * G + c0 / 2, f8s));
   if (a.out_f8) block_amax(f8m, a.f8_amax);
 }
 
@@ -395,6 +500,45 @@ int launch_gn_stats(const float* z, int N, int HW, int C, float eps, float* mean
   if (V == 4) gn_stats_kernel<4><<<grid, th, smem, s>>>(z, HW, C, S, eps, w.part, w.cnt, mean, rstd);
   else gn_stats_kernel<2><<<grid, th, smem, s>>>(z, HW, C, S, eps, w.part, w.cnt, mean, rstd);
   DDPPO_CHECK_LAUNCH();
+  return DDPPO_OK;
+}
+
+int launch_gn_fused(const GNApply& a, int N, int HW, int C, float eps, const GnScratch& w,
+                    int32_t* err, cudaStream_t s, bool* launched) {
+  *launched = false;
+  if (!N || !HW) { *launched = true; return DDPPO_OK; }
+  if (!w.cnt2 || !gn_shape_ok(C) || N > w.max_images || N > 65535) return DDPPO_OK;
+  const int V = C % 4 == 0 ? 4 : 2;
+  const int th = threads_for(C, V);
+  const int sms = num_sms_cached();
+  void (*kern)(GNApply, int, int, int, float, float*, float*, int*, int*, int32_t*) =
+      V == 4 ? gn_fused_kernel<4> : gn_fused_kernel<2>;
+  const int nt = a.zd ? 2 : 1;
+  int S = gn_split(N, HW, C, w);
+  auto smem_of = [&](int S_) {
+    return ((size_t)std::max(th * 2 * V, S_ * C * 2) + 2 * (size_t)C) * sizeof(float);
+  };
+  // every block resident at once, and the partials of z (and zd) in the scratch
+  for (; S >= 1; --S) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, th, smem_of(S)) != cudaSuccess)
+      return DDPPO_OK;
+    if ((long)S * N <= (long)occ * sms && (size_t)nt * N * S * C * 2 <= w.part_elems) break;
+  }
+  if (S < 1) return DDPPO_OK;  // too many images for one resident wave: two launches instead
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(S, N);
+  cfg.blockDim = dim3(th);
+  cfg.dynamicSmemBytes = smem_of(S);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  float* part_d = w.part + (size_t)N * S * C * 2;
+  DDPPO_CHECK_CUDA(cudaLaunchKernelEx(&cfg, kern, a, HW, C, S, eps, w.part, part_d, w.cnt, w.cnt2, err));
+  *launched = true;
   return DDPPO_OK;
 }
 

@@ -344,6 +344,8 @@ static int alloc_encoder(Net& n) {
     DDPPO_TRY(nalloc(n, &n.gnw.part, n.gnw.part_elems));
     DDPPO_TRY(nalloc(n, &n.gnw.cnt, NC));
     DDPPO_CHECK_CUDA(cudaMemset(n.gnw.cnt, 0, NC * sizeof(int)));
+    DDPPO_TRY(nalloc(n, &n.gnw.cnt2, NC));
+    DDPPO_CHECK_CUDA(cudaMemset(n.gnw.cnt2, 0, NC * sizeof(int)));
     DDPPO_TRY(nalloc(n, &n.gn_m1, NC * C / 2));
     DDPPO_TRY(nalloc(n, &n.gn_m2, NC * C / 2));
   }
@@ -690,13 +692,11 @@ static int gn_fwd(Net& n, GNL& g, const float* z, int N, int HW, float* out, boo
                   const float* resid, const GNL* gd, const float* zd, cudaStream_t s,
                   __nv_bfloat16* out_bf = nullptr, uint8_t* out_f8 = nullptr, int f8_slot = -1) {
   const float eps = 1e-5f;
-  DDPPO_TRY(launch_gn_stats(z, N, HW, g.C, eps, g.mean, g.rstd, n.gnw, s));
   GNApply a{};
   a.z = z; a.mean = g.mean; a.rstd = g.rstd;
   a.gamma = n.params + g.g_off; a.beta = n.params + g.b_off;
   a.resid = resid;
   if (gd) {
-    DDPPO_TRY(launch_gn_stats(zd, N, HW, gd->C, eps, gd->mean, gd->rstd, n.gnw, s));
     a.zd = zd; a.mean_d = gd->mean; a.rstd_d = gd->rstd;
     a.gamma_d = n.params + gd->g_off; a.beta_d = n.params + gd->b_off;
   }
@@ -708,6 +708,14 @@ static int gn_fwd(Net& n, GNL& g, const float* z, int N, int HW, float* out, boo
     a.f8_amax = n.f8_amax + f8_slot;
   }
   a.relu = relu ? 1 : 0;
+  if (n.gn_fused_on) {
+    // statistics and normalisation in one launch when the grid fits one resident wave
+    bool done = false;
+    DDPPO_TRY(launch_gn_fused(a, N, HW, g.C, eps, n.gnw, n.gws.err, s, &done));
+    if (done) return DDPPO_OK;
+  }
+  DDPPO_TRY(launch_gn_stats(z, N, HW, g.C, eps, g.mean, g.rstd, n.gnw, s));
+  if (gd) DDPPO_TRY(launch_gn_stats(zd, N, HW, gd->C, eps, gd->mean, gd->rstd, n.gnw, s));
   return launch_gn_apply(a, N, HW, g.C, s);
 }
 

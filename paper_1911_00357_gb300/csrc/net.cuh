@@ -205,6 +205,7 @@ struct Net {
   int64_t* d_steps = nullptr;    // [2] device: update index, Adam steps before this update
   unsigned* lstm_bar = nullptr;  // grid-barrier counter of the whole-segment LSTM kernels
   bool lstm_seq_on = false;      // whole-segment LSTM recurrence where the shape allows
+  bool gn_fused_on = true;       // GroupNorm statistics + normalisation in one launch
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   uint8_t* post_done = nullptr;

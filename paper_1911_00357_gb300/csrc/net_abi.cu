@@ -838,14 +838,25 @@ extern "C" int ddppo_group_norm(int32_t N, int32_t HW, int32_t C, const float* z
     DDPPO_CHECK_CUDA(cudaMalloc(&w.part, w.part_elems * sizeof(float)));
     DDPPO_CHECK_CUDA(cudaMalloc(&w.cnt, (size_t)w.max_images * sizeof(int)));
     DDPPO_CHECK_CUDA(cudaMemset(w.cnt, 0, (size_t)w.max_images * sizeof(int)));
+    DDPPO_CHECK_CUDA(cudaMalloc(&w.cnt2, (size_t)w.max_images * sizeof(int)));
+    DDPPO_CHECK_CUDA(cudaMemset(w.cnt2, 0, (size_t)w.max_images * sizeof(int)));
     ws[dev] = w;
   }
   cudaStream_t s = (cudaStream_t)stream;
-  DDPPO_TRY(launch_gn_stats(z, N, HW, C, 1e-5f, mean, rstd, ws[dev], s));
   GNApply a{};
   a.z = z; a.mean = mean; a.rstd = rstd; a.gamma = gamma; a.beta = beta;
   a.resid = resid; a.out = out; a.relu = relu ? 1 : 0;
+  bool done = false;
+  DDPPO_TRY(launch_gn_fused(a, N, HW, C, 1e-5f, ws[dev], nullptr, s, &done));
+  if (done) return DDPPO_OK;
+  DDPPO_TRY(launch_gn_stats(z, N, HW, C, 1e-5f, mean, rstd, ws[dev], s));
   return launch_gn_apply(a, N, HW, C, s);
+}
+
+extern "C" int ddppo_group_norm_one_launch(ddppo_ctx* x, int32_t on) {
+  ARG(x && x->net, "group_norm_one_launch: null ctx");
+  x->net->gn_fused_on = on != 0;
+  return DDPPO_OK;
 }
 
 // ---- stand-alone SE-ResNeXt pieces: grouped 3x3 convolution and squeeze-excite ----

@@ -33,6 +33,7 @@ struct GnScratch {
   float* part = nullptr;  // gn_part_elems(max_images, max_C) floats
   size_t part_elems = 0;
   int* cnt = nullptr;     // [max_images], zeroed once
+  int* cnt2 = nullptr;    // [max_images], zeroed once (the one-launch form's departures)
   int max_images = 0;
 };
 size_t gn_part_elems(int max_images, int max_C);
@@ -52,6 +53,13 @@ struct GNApply {
   uint8_t* out_f8; const float* f8_scale; unsigned* f8_amax;
 };
 int launch_gn_apply(const GNApply& a, int N, int HW, int C, cudaStream_t s);
+// statistics and normalisation in one cooperative launch: a.mean/a.rstd (and a.mean_d /
+// a.rstd_d with zd) receive the statistics, out as launch_gn_apply. Sets *launched = false,
+// launching nothing, when the grid cannot be resident at once (many images) or w has no
+// departure counters; the caller then runs launch_gn_stats + launch_gn_apply. err: the
+// sticky status word (timeout flag on a barrier run-out).
+int launch_gn_fused(const GNApply& a, int N, int HW, int C, float eps, const GnScratch& w,
+                    int32_t* err, cudaStream_t s, bool* launched);
 // GroupNorm backward. g = dy, masked by (relu_y > 0) when relu_y is given (the ReLU that
 // followed the normalisation); g_out (optional, with relu_y) receives g.
 //   dz = rstd (g gamma - m1 - xhat m2), m1 / m2 the group means of gamma g and gamma g xhat;

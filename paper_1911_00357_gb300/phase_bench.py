@@ -29,10 +29,14 @@ def main():
     ap.add_argument("--precision", type=int, default=None, help="override the preset's precision")
     ap.add_argument("--lstm-whole", action="store_true",
                     help="whole-segment LSTM kernels instead of the step-by-step recurrence")
+    ap.add_argument("--gn-two-launch", action="store_true",
+                    help="GroupNorm statistics and normalisation as two launches")
     args = ap.parse_args()
     w = Worker(args.preset, seed=args.seed, precision=args.precision)
     if args.lstm_whole:
         B.ddppo_lstm_whole_segment(w.h, True)
+    if args.gn_two_launch:
+        B.ddppo_group_norm_one_launch(w.h, False)
     try:
         for _ in range(args.warmup):
             w.iterate()
@@ -61,6 +65,7 @@ def main():
         print(json.dumps({
             "preset": args.preset, "precision": w.cfg.precision, "num_envs": w.E, "rollout_T": w.T,
             "seed": args.seed, "lstm": "whole-segment" if args.lstm_whole else "step",
+            "group_norm": "two launches" if args.gn_two_launch else "one launch",
             "collect_ms": round(c, 2), "update_ms": round(u, 2),
             "act_frames_per_s": round(frames / c * 1e3, 1),
             "frames_per_s": round(frames / (c + u) * 1e3, 1),

@@ -250,9 +250,11 @@ def test_squeeze_excite_matches_float64(N, HW, C, shortcut):
     assert torch.allclose(m.cpu().double(), u.double().mean(1), atol=1e-5)
 
 
-def test_group_norm_entry_matches_float64():
+@pytest.mark.parametrize("N,HW,C", [(3, 16, 1024), (64, 4096, 32), (5, 37, 6), (2000, 16, 64)])
+def test_group_norm_entry_matches_float64(N, HW, C):
+    # one launch (the first three: every block resident at once) and two launches (2000
+    # images do not fit one resident wave); C = 6 takes the two-channel vectors
     g = torch.Generator().manual_seed(4)
-    N, HW, C = 3, 16, 1024
     z = torch.randn(N, HW, C, generator=g) * 2 + 0.5
     gam, bet = 1 + 0.1 * torch.randn(C, generator=g), 0.1 * torch.randn(C, generator=g)
     res = torch.randn(N, HW, C, generator=g)
@@ -265,3 +267,8 @@ def test_group_norm_entry_matches_float64():
                                          1e-5).permute(0, 2, 1)
     ref = torch.relu(ref + res.double())
     assert (out.cpu().double() - ref).abs().max().item() <= 1e-4
+    zg = z.double().reshape(N, HW, C // 2, 2)
+    m64 = zg.mean(dim=(1, 3))
+    r64 = 1.0 / torch.sqrt(zg.var(dim=(1, 3), unbiased=False) + 1e-5)
+    assert (mean.cpu().double() - m64).abs().max().item() <= 1e-5
+    assert ((rstd.cpu().double() - r64).abs() / r64).max().item() <= 1e-5
