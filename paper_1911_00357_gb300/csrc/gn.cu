@@ -485,6 +485,32 @@ size_t gn_part_elems(int max_images, int max_C) {
   return (size_t)(max_images + 8 * num_sms_cached() + 64) * max_C * 2;
 }
 
+// dynamic shared memory of the one-launch kernel for S blocks per image
+static size_t fused_smem(int S, int C, int V) {
+  const int th = threads_for(C, V);
+  return ((size_t)std::max(th * 2 * V, S * C * 2) + 2 * (size_t)C) * sizeof(float);
+}
+
+// blocks per image of the one-launch form: gn_split's choice, lowered until all S x N
+// blocks are resident at once; 0 when even S = 1 is not (the two-launch form then keeps
+// gn_split's choice). The statistics launch of the two-launch form uses the same S, so
+// the two forms give bit-identical statistics.
+static int gn_split_one_launch(int N, int HW, int C, const GnScratch& w) {
+  if (!w.cnt2) return 0;
+  const int V = C % 4 == 0 ? 4 : 2;
+  void (*kern)(GNApply, int, int, int, float, float*, float*, int*, int*, int32_t*) =
+      V == 4 ? gn_fused_kernel<4> : gn_fused_kernel<2>;
+  const int th = threads_for(C, V);
+  const int sms = num_sms_cached();
+  for (int S = gn_split(N, HW, C, w); S >= 1; --S) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, th, fused_smem(S, C, V)) != cudaSuccess)
+      return 0;
+    if ((long)S * N <= (long)occ * sms) return S;
+  }
+  return 0;
+}
+
 int launch_gn_stats(const float* z, int N, int HW, int C, float eps, float* mean, float* rstd,
                     const GnScratch& w, cudaStream_t s) {
   if (!N || !HW) return DDPPO_OK;
@@ -493,7 +519,8 @@ int launch_gn_stats(const float* z, int N, int HW, int C, float eps, float* mean
     return DDPPO_E_CONFIG;
   }
   const int V = C % 4 == 0 ? 4 : 2;
-  const int S = gn_split(N, HW, C, w);
+  const int S1 = gn_split_one_launch(N, HW, C, w);
+  const int S = S1 ? S1 : gn_split(N, HW, C, w);
   const int th = threads_for(C, V);
   const size_t smem = std::max((size_t)th * 2 * V, (size_t)S * C * 2) * sizeof(float);
   const dim3 grid(S, N);
@@ -510,26 +537,17 @@ int launch_gn_fused(const GNApply& a, int N, int HW, int C, float eps, const GnS
   if (!w.cnt2 || !gn_shape_ok(C) || N > w.max_images || N > 65535) return DDPPO_OK;
   const int V = C % 4 == 0 ? 4 : 2;
   const int th = threads_for(C, V);
-  const int sms = num_sms_cached();
   void (*kern)(GNApply, int, int, int, float, float*, float*, int*, int*, int32_t*) =
       V == 4 ? gn_fused_kernel<4> : gn_fused_kernel<2>;
   const int nt = a.zd ? 2 : 1;
-  int S = gn_split(N, HW, C, w);
-  auto smem_of = [&](int S_) {
-    return ((size_t)std::max(th * 2 * V, S_ * C * 2) + 2 * (size_t)C) * sizeof(float);
-  };
-  // every block resident at once, and the partials of z (and zd) in the scratch
-  for (; S >= 1; --S) {
-    int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, th, smem_of(S)) != cudaSuccess)
-      return DDPPO_OK;
-    if ((long)S * N <= (long)occ * sms && (size_t)nt * N * S * C * 2 <= w.part_elems) break;
-  }
-  if (S < 1) return DDPPO_OK;  // too many images for one resident wave: two launches instead
+  // every block resident at once, and the partials of z (and zd) in the scratch;
+  // otherwise two launches
+  const int S = gn_split_one_launch(N, HW, C, w);
+  if (S < 1 || (size_t)nt * N * S * C * 2 > w.part_elems) return DDPPO_OK;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(S, N);
   cfg.blockDim = dim3(th);
-  cfg.dynamicSmemBytes = smem_of(S);
+  cfg.dynamicSmemBytes = fused_smem(S, C, V);
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;
