@@ -85,12 +85,37 @@ __global__ void __launch_bounds__(256) ppo_loss_kernel(int n, const float* __res
   block_partials<5>(acc, part);
 }
 
-__global__ void ppo_loss_final(int nb, int n, const float* part, float cv, float ce,
-                               float* stats) {
+// the sum over nb blocks of NV partials each (part[b * NV + k]) by one block of kFinal
+// threads, in a fixed order: thread i adds partials i, i + kFinal, ... in turn, then a fixed
+// halving tree over the threads. Every thread reads its partials before the first barrier.
+constexpr int kFinal = 256;
+template <int NV>
+__device__ void final_sums(const float* part, int nb, float (&out)[NV]) {
+  __shared__ float sh[NV][kFinal];
+  float acc[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) acc[k] = 0.f;
+  for (int b = threadIdx.x; b < nb; b += kFinal)
+#pragma unroll
+    for (int k = 0; k < NV; ++k) acc[k] += part[b * NV + k];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] = acc[k];
+  __syncthreads();
+  for (int w = kFinal / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) sh[k][threadIdx.x] += sh[k][threadIdx.x + w];
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < NV; ++k) out[k] = sh[k][0];
+}
+
+__global__ void __launch_bounds__(kFinal) ppo_loss_final(int nb, int n, const float* part, float cv,
+                                                        float ce, float* stats) {
+  float s[5];
+  final_sums<5>(part, nb, s);  // part may alias stats: all reads precede the writes below
   if (threadIdx.x != 0) return;
-  float s[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-  for (int b = 0; b < nb; ++b)
-    for (int k = 0; k < 5; ++k) s[k] += part[b * 5 + k];  // read all partials before writing
   const float inv = 1.0f / (float)n;
   const float pol = s[0] * inv, vl = s[1] * inv, ent = s[2] * inv;
   stats[0] = pol + cv * vl - ce * ent;
@@ -116,7 +141,7 @@ int launch_ppo_loss(int n, const float* logits, const float* values, const int32
   ppo_loss_kernel<<<nb, 256, 0, s>>>(n, logits, values, actions, logp_old, adv, ret, clip, cv, ce,
                                      dlogits, dvalues, part);
   DDPPO_CHECK_LAUNCH();
-  ppo_loss_final<<<1, 32, 0, s>>>(nb, n, part, cv, ce, stats);
+  ppo_loss_final<<<1, kFinal, 0, s>>>(nb, n, part, cv, ce, stats);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -129,7 +154,7 @@ int launch_ppo_loss_blocks(int n, const float* logits, const float* values, cons
   ppo_loss_kernel<<<nb, 256, 0, s>>>(n, logits, values, actions, logp_old, adv, ret, clip, cv, ce,
                                      dlogits, dvalues, part);
   DDPPO_CHECK_LAUNCH();
-  ppo_loss_final<<<1, 32, 0, s>>>(nb, n, part, cv, ce, stats);
+  ppo_loss_final<<<1, kFinal, 0, s>>>(nb, n, part, cv, ce, stats);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -145,10 +170,12 @@ __global__ void __launch_bounds__(256) sumsq_partial(const float* __restrict__ x
   }
   block_partials<1>(v, part);
 }
-__global__ void sum_final(int nb, const float* __restrict__ part, float* out, int mode, float scale) {
+__global__ void __launch_bounds__(kFinal) sum_final(int nb, const float* __restrict__ part, float* out,
+                                                   int mode, float scale) {
+  float t[1];
+  final_sums<1>(part, nb, t);
   if (threadIdx.x != 0) return;
-  float s = 0.f;
-  for (int b = 0; b < nb; ++b) s += part[b];  // fixed order
+  const float s = t[0];
   if (mode == 0) out[0] = sqrtf(s);          // L2 norm
   else if (mode == 1) out[0] = s * scale;    // mean
   else out[0] = sqrtf(s * scale);            // population std
@@ -167,7 +194,7 @@ int launch_grad_norm(const float* g, size_t n, float* norm_out, float* part, siz
   if ((size_t)nb > part_elems) { set_error("grad_norm: scratch too small"); return DDPPO_E_CONFIG; }
   sumsq_partial<<<nb, 256, 0, s>>>(g, n, part, 1, nullptr);
   DDPPO_CHECK_LAUNCH();
-  sum_final<<<1, 32, 0, s>>>(nb, part, norm_out, 0, 1.f);
+  sum_final<<<1, kFinal, 0, s>>>(nb, part, norm_out, 0, 1.f);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -252,11 +279,11 @@ int launch_normalize_adv(const float* adv, float* out, size_t n, float* scal2, f
   if ((size_t)nb > part_elems) { set_error("normalize: scratch too small"); return DDPPO_E_CONFIG; }
   sumsq_partial<<<nb, 256, 0, s>>>(adv, n, part, 0, nullptr);
   DDPPO_CHECK_LAUNCH();
-  sum_final<<<1, 32, 0, s>>>(nb, part, scal2, 1, 1.0f / (float)n);
+  sum_final<<<1, kFinal, 0, s>>>(nb, part, scal2, 1, 1.0f / (float)n);
   DDPPO_CHECK_LAUNCH();
   sumsq_partial<<<nb, 256, 0, s>>>(adv, n, part, 1, scal2);
   DDPPO_CHECK_LAUNCH();
-  sum_final<<<1, 32, 0, s>>>(nb, part, scal2 + 1, 2, 1.0f / (float)n);
+  sum_final<<<1, kFinal, 0, s>>>(nb, part, scal2 + 1, 2, 1.0f / (float)n);
   DDPPO_CHECK_LAUNCH();
   normalize_kernel<<<reduce_blocks(n), 256, 0, s>>>(adv, out, n, scal2, scal2 + 1);
   DDPPO_CHECK_LAUNCH();

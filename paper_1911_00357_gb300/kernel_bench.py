@@ -19,7 +19,8 @@ Algorithmic bytes per unit (each operand read once, each result written once):
               then normalise), so 2/3 (3/4 with a residual) is its ceiling
   env_step    84 B of state, action and outputs per env plus the observation written
               (depth H x W in the operand dtype); the step is bound by the ray cast's ALU
-              work, so the HBM fraction is reported for completeness
+              work, so the HBM fraction is reported for completeness. The next episodes are
+              prepared (untimed) before each timed step, as in the collect loop
 
 Each line is one JSON object; `frac` is achieved / peak, the peak being the measured copy
 bandwidth passed in (the GB/s of a plain device copy on this GPU model). A measurement
@@ -43,11 +44,15 @@ class _Timer:
         self.reps = reps
         self.flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
 
-    def __call__(self, fn) -> float:
+    def __call__(self, fn, pre=None) -> float:
         s = torch.cuda.current_stream()
+        if pre:
+            pre()
         fn()  # warm-up (first-call allocations, lookups)
         times = []
         for _ in range(self.reps):
+            if pre:
+                pre()  # untimed set-up on the same stream
             self.flush.fill_(1.0)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
@@ -136,8 +141,11 @@ def bench_worker_kernels(tm, peak, presets):
             acts = torch.randint(0, 4, (E,), device="cuda", dtype=torch.int32)
             ob = t["obs"][0]
             obs_bytes = ob[0].numel() * ob.element_size()
+            # the next episode of every env prepared beforehand (untimed), as the collect
+            # loop does on its side stream: the step adopts it instead of generating one
             ms = tm(lambda: B.ddppo_env_step(w.h, acts, t["obs"][1], t["goal"][1], t["rewards"][0],
-                                             t["dones"][0]))
+                                             t["dones"][0]),
+                    pre=lambda: B.ddppo_env_prefetch(w.h))
             _line("env_step", f"{preset}: {E} envs, obs {tuple(ob.shape[1:])} {ob.dtype}", E,
                   "envs", 84 + obs_bytes, ms, peak, bound="alu (ray cast)",
                   env_steps_per_s=round(E / (ms * 1e-3), 1))
