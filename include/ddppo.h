@@ -554,17 +554,20 @@ int ddppo_gemm_backend(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const v
  * are bit-identical either way. */
 int ddppo_update_graph(ddppo_ctx* ctx, int32_t on);
 
-/* The LSTM recurrence (App. "Agent Design"; Sec. 4 "Training": BPTT over the rollout):
- * on = 0 (the default) launches a recurrent contraction and a cell kernel per step;
- * on = 1 runs each layer's whole T-step forward, and its back-propagation through time,
- * as one cooperative launch (the recurrent weights held in registers across the SMs, one
- * grid barrier per step) wherever the shape allows (at most 64 envs per segment, hidden
- * sizes whose 4H gate rows split over the SMs). Both compute the same arithmetic; the
- * contraction's fp32 summation order differs. The whole-segment form is slower at the
- * default sizes (its per-step contraction is bound by shared-memory loads: one FMA per
- * loaded state value), hence off by default. Applies to launches enqueued afterwards (a
- * captured graph keeps the mode it was captured with). Host only. */
-int ddppo_lstm_whole_segment(ddppo_ctx* ctx, int32_t on);
+/* The LSTM recurrence (App. "Agent Design"; Sec. 4 "Training": BPTT over the rollout).
+ * mode 2 (the default): in the BF16 forms the forward of each layer runs all T steps in
+ * one launch on the tensor cores (tcgen05, M = 128 gate rows per CTA, the CTA's rows of
+ * W_hh resident in shared memory, the cell update fused into the TMEM epilogue, one
+ * bounded grid barrier per step) wherever the shape allows (H a multiple of 64, at most
+ * 128 envs per segment, 64 when H = 512); the backward, the FP32 form and other shapes
+ * run step by step. mode 0: a recurrent contraction and a cell kernel per step, forward
+ * and backward. mode 1: forward and backward as one cooperative launch per layer on the
+ * CUDA cores (recurrent weights in registers; at most 64 envs per segment); slower than
+ * mode 0 at the default sizes (its per-step contraction is bound by shared-memory loads).
+ * All modes compute the same arithmetic; only the recurrent contraction's fp32 summation
+ * order differs. Applies to launches enqueued afterwards (a captured graph keeps the mode
+ * it was captured with). E_ARG for another mode. Host only. */
+int ddppo_lstm_whole_segment(ddppo_ctx* ctx, int32_t mode);
 
 /* Tile-shape autotuner of the tensor-core GEMM (precision 1): on by default. The first
  * time a contraction shape is seen outside a stream capture, each candidate (N tile 64 or

@@ -426,8 +426,10 @@ def ddppo_update_graph(h, on: bool = True) -> None:
     _check(lib().ddppo_update_graph(h, 1 if on else 0))
 
 
-def ddppo_lstm_whole_segment(h, on: bool = True) -> None:
-    _check(lib().ddppo_lstm_whole_segment(h, 1 if on else 0))
+def ddppo_lstm_whole_segment(h, mode: int = 1) -> None:
+    """LSTM recurrence mode: 0 step by step, 1 whole segment on CUDA cores, 2 tcgen05
+    forward (the default); a bool selects 1 (True) or 0 (False)."""
+    _check(lib().ddppo_lstm_whole_segment(h, int(mode)))
 
 
 def ddppo_group_norm_one_launch(h, on: bool = True) -> None:

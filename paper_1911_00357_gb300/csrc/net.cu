@@ -968,7 +968,8 @@ static int encoder_bwd(Net& n, const void* obs, int N, const float* dfeat_rows, 
 static int lstm_forward(Net& n, int T, int E, const uint8_t* masks, const float* h0,
                         const float* c0, cudaStream_t s) {
   const int N = T * E, Hd = n.H, G4 = 4 * Hd;
-  const bool seq = n.lstm_seq_on && lstm_seq_supported(Hd, E, n.gws.num_sms);
+  const bool seq = n.lstm_mode == 1 && lstm_seq_supported(Hd, E, n.gws.num_sms);
+  const bool tc = n.lstm_mode == 2 && n.bf && lstm_tc_supported(Hd, E, n.gws.num_sms);
   for (int l = 0; l < n.L; ++l) {
     LstmL& q = n.lstm[l];
     GemmDesc gx;
@@ -986,6 +987,18 @@ static int lstm_forward(Net& n, int T, int E, const uint8_t* masks, const float*
       a.gates = q.gates; a.c = q.c; a.h = q.h; a.y_op = q.y; a.hm = q.hm;
       a.bar = n.lstm_bar; a.err = n.gws.err; a.op_bf16 = n.bf ? 1 : 0;
       DDPPO_TRY(launch_lstm_seq_fwd(a, n.gws.num_sms, s));
+      continue;
+    }
+    if (tc) {
+      DDPPO_TRY(launch_mask_state(h0 + (size_t)l * E * Hd, masks, E, Hd, q.hm, true, s));
+      LstmTc a{};
+      a.T = T; a.E = E; a.H = Hd;
+      a.gx = n.gx; a.m = masks; a.c0 = c0 + (size_t)l * E * Hd;
+      a.Whh = (const __nv_bfloat16*)q.Whh;
+      a.gates = q.gates; a.c = q.c; a.h = q.h;
+      a.y_op = (__nv_bfloat16*)q.y; a.hm = (__nv_bfloat16*)q.hm;
+      a.bar = n.lstm_bar; a.err = n.gws.err;
+      DDPPO_TRY(launch_lstm_tc_fwd(a, n.gws.num_sms, s));
       continue;
     }
     DDPPO_TRY(launch_mask_state(h0 + (size_t)l * E * Hd, masks, E, Hd, q.hm, n.bf, s));
@@ -1022,7 +1035,7 @@ static int lstm_forward(Net& n, int T, int E, const uint8_t* masks, const float*
 static int lstm_backward(Net& n, int T, int E, const uint8_t* masks, const float* c0,
                          const float* dtop, const float** dx0, cudaStream_t s) {
   const int N = T * E, Hd = n.H, G4 = 4 * Hd;
-  const bool seq = n.lstm_seq_on && lstm_seq_supported(Hd, E, n.gws.num_sms);
+  const bool seq = n.lstm_mode == 1 && lstm_seq_supported(Hd, E, n.gws.num_sms);
   const float* dabove = dtop;
   for (int l = n.L - 1; l >= 0; --l) {
     LstmL& q = n.lstm[l];

@@ -204,7 +204,9 @@ struct Net {
   bool upd_graph_on = true;      // caller's choice (ddppo_update_graph)
   int64_t* d_steps = nullptr;    // [2] device: update index, Adam steps before this update
   unsigned* lstm_bar = nullptr;  // grid-barrier counter of the whole-segment LSTM kernels
-  bool lstm_seq_on = false;      // whole-segment LSTM recurrence where the shape allows
+  // LSTM recurrence: 0 step by step; 1 whole segment on CUDA cores (forward and
+  // backward); 2 forward on tcgen05 (whole segment, BF16), backward step by step
+  int lstm_mode = 2;
   bool gn_fused_on = true;       // GroupNorm statistics + normalisation in one launch
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;

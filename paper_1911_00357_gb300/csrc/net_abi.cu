@@ -795,9 +795,10 @@ extern "C" int ddppo_update_graph(ddppo_ctx* x, int32_t on) {
   return DDPPO_OK;
 }
 
-extern "C" int ddppo_lstm_whole_segment(ddppo_ctx* x, int32_t on) {
+extern "C" int ddppo_lstm_whole_segment(ddppo_ctx* x, int32_t mode) {
   ARG(x && x->net, "lstm_whole_segment: null ctx");
-  x->net->lstm_seq_on = on != 0;
+  ARG(mode >= 0 && mode <= 2, "lstm_whole_segment: mode must be 0, 1 or 2");
+  x->net->lstm_mode = mode;
   return DDPPO_OK;
 }
 

@@ -179,6 +179,17 @@ struct LstmSeq {
   unsigned* bar; int32_t* err; int op_bf16;
 };
 bool lstm_seq_supported(int H, int E, int num_sms);
+
+// the forward recurrence on tcgen05 (lstm_tc.cu): BF16 operands, [T, E, *] layouts as the
+// step-by-step path; hm[0] (the masked initial state) must be written beforehand
+struct LstmTc {
+  int T, E, H;
+  const float* gx; const uint8_t* m; const float* c0; const __nv_bfloat16* Whh;
+  float* gates; float* c; float* h; __nv_bfloat16* y_op; __nv_bfloat16* hm;
+  unsigned* bar; int32_t* err;
+};
+bool lstm_tc_supported(int H, int E, int num_sms);
+int launch_lstm_tc_fwd(const LstmTc& a, int num_sms, cudaStream_t s);
 int launch_lstm_seq_fwd(const LstmSeq& a, int num_sms, cudaStream_t s);
 int launch_lstm_seq_bwd(const LstmSeq& a, int num_sms, cudaStream_t s);
 

@@ -15,8 +15,11 @@ Algorithmic bytes per unit (each operand read once, each result written once):
               scaling, global-norm clip, Adam, GEMM-layout weight refresh), so the
               fraction charges the other passes to Adam's bytes
   group_norm  12 B per element with a residual (z, residual read; output written), 8 without
-              (App. "Visual Encoder": GroupNorm); the kernel reads z twice (statistics,
-              then normalise), so 2/3 (3/4 with a residual) is its ceiling
+              (App. "Visual Encoder": GroupNorm). z is read twice (statistics, then
+              normalise): the one-launch form re-reads each block's rows right after summing
+              them (an L2 hit when the batch fits L2); the two-launch form, taken when the
+              grid cannot be resident at once, reads z from HBM twice (ceiling 2/3, or 3/4
+              with a residual)
   env_step    84 B of state, action and outputs per env plus the observation written
               (depth H x W in the operand dtype); the step is bound by the ray cast's ALU
               work, so the HBM fraction is reported for completeness. The next episodes are

@@ -27,14 +27,14 @@ def main():
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--precision", type=int, default=None, help="override the preset's precision")
-    ap.add_argument("--lstm-whole", action="store_true",
-                    help="whole-segment LSTM kernels instead of the step-by-step recurrence")
+    ap.add_argument("--lstm-mode", type=int, default=2, choices=[0, 1, 2],
+                    help="LSTM recurrence: 0 step by step, 1 whole segment on CUDA cores, "
+                         "2 tcgen05 forward (default)")
     ap.add_argument("--gn-two-launch", action="store_true",
                     help="GroupNorm statistics and normalisation as two launches")
     args = ap.parse_args()
     w = Worker(args.preset, seed=args.seed, precision=args.precision)
-    if args.lstm_whole:
-        B.ddppo_lstm_whole_segment(w.h, True)
+    B.ddppo_lstm_whole_segment(w.h, args.lstm_mode)
     if args.gn_two_launch:
         B.ddppo_group_norm_one_launch(w.h, False)
     try:
@@ -64,7 +64,7 @@ def main():
         frames = w.E * w.T
         print(json.dumps({
             "preset": args.preset, "precision": w.cfg.precision, "num_envs": w.E, "rollout_T": w.T,
-            "seed": args.seed, "lstm": "whole-segment" if args.lstm_whole else "step",
+            "seed": args.seed, "lstm_mode": args.lstm_mode,
             "group_norm": "two launches" if args.gn_two_launch else "one launch",
             "collect_ms": round(c, 2), "update_ms": round(u, 2),
             "act_frames_per_s": round(frames / c * 1e3, 1),

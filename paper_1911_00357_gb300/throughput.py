@@ -39,11 +39,10 @@ def ci95(xs):
     return mean, _T95.get(n - 1, 1.96) * math.sqrt(var / n)
 
 
-def run_seed(preset, seed, iters, last, precision=None, lstm_whole=False):
+def run_seed(preset, seed, iters, last, precision=None, lstm_mode=2):
     w = Worker(preset, seed=seed, precision=precision)
     try:
-        if lstm_whole:
-            B.ddppo_lstm_whole_segment(w.h, True)
+        B.ddppo_lstm_whole_segment(w.h, lstm_mode)
         s = torch.cuda.current_stream()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(iters + 1)]
         torch.cuda.synchronize()
@@ -66,7 +65,7 @@ def main():
     ap.add_argument("--seeds", type=int, nargs="+", default=[0, 1, 2])
     ap.add_argument("--iters", type=int, default=10)
     ap.add_argument("--last", type=int, default=5)
-    ap.add_argument("--lstm-whole", action="store_true")
+    ap.add_argument("--lstm-mode", type=int, default=2, choices=[0, 1, 2])
     args = ap.parse_args()
     if not 1 <= args.last <= args.iters:
         ap.error("need 1 <= last <= iters")
@@ -74,7 +73,7 @@ def main():
     prec = None
     for seed in args.seeds:
         fps, ms_it, prec, status = run_seed(args.preset, seed, args.iters, args.last,
-                                            args.precision, args.lstm_whole)
+                                            args.precision, args.lstm_mode)
         rates.append(fps)
         print(json.dumps({"preset": args.preset, "precision": prec, "seed": seed,
                           "frames_per_s": round(fps, 1), "ms_per_iter": round(ms_it, 2),

@@ -1,11 +1,16 @@
-"""The whole-segment LSTM kernels (one cooperative launch per layer for the T-step forward
-and for its back-propagation through time) against the step-by-step path (a recurrent
-contraction and a cell kernel per step). Both compute the same arithmetic; only the
-recurrent contraction's fp32 summation order differs, so results agree to fp32 accuracy:
-logits, values, LSTM states and every gradient tensor within 1e-5 relative (1e-4 for the
-gradients, which sum over the segment), and a whole 2 x 2 PPO update within 2% of
-lr x steps per coordinate. The float64 oracle parity of the default (step-by-step) path
-is covered by the policy and update parity tests.
+"""The whole-segment LSTM forms against the step-by-step path (mode 0: a recurrent
+contraction and a cell kernel per step):
+  mode 1, one cooperative launch per layer on the CUDA cores for the T-step forward and
+  its back-propagation through time;
+  mode 2 (the default), the forward on tcgen05 (one launch per layer, W_hh rows resident
+  in shared memory, the cell update in the TMEM epilogue), backward step by step.
+All compute the same arithmetic; only the recurrent contraction's fp32 summation order
+differs, so in FP32 results agree to fp32 accuracy: logits, values, LSTM states and every
+gradient tensor within 1e-5 relative (1e-4 for the gradients, which sum over the segment),
+and a whole 2 x 2 PPO update within 2% of lr x steps per coordinate. With BF16 operands a
+summation difference can flip a bf16 rounding of the recurrent state (a 2^-9 step), so the
+bound there is a few bf16 units (2e-2). The float64 oracle parity of the default path is
+covered by the policy, BF16-emulation and update parity tests.
 """
 import numpy as np
 import pytest
@@ -21,7 +26,8 @@ pytestmark = pytest.mark.gpu
 
 def _cfg2(name, E, T, precision, mb=1):
     # hidden sizes whose units split unevenly over the SMs (U = 2 units per CTA for H = 32)
-    extra = {"nature_h32": dict(hidden=32), "nature_h64": dict(hidden=64)}
+    extra = {"nature_h32": dict(hidden=32), "nature_h64": dict(hidden=64),
+             "nature_h192": dict(hidden=192)}
     if name in extra:
         from paper_1911_00357_gb300.presets import make_config
         return make_config("nature_fp32", num_envs=E, rollout_T=T, minibatches=mb,
@@ -29,8 +35,8 @@ def _cfg2(name, E, T, precision, mb=1):
     return _cfg(name, E, T, precision, mb=mb)
 
 
-def _run(net, cfg, T, E, whole):
-    B.ddppo_lstm_whole_segment(net.h, whole)
+def _run(net, cfg, T, E, mode):
+    B.ddppo_lstm_whole_segment(net.h, mode)
     mb = I.minibatch(net.ncfg, T=T, E=E, seed=2)
     dev, _ = _dev_inputs(cfg, mb)
     logits = torch.zeros(T, E, 4, device="cuda")
@@ -55,16 +61,20 @@ def _run(net, cfg, T, E, whole):
     return [x.cpu().double() for x in (logits, values, grad, h, c, logp, val)]
 
 
-@pytest.mark.parametrize("name,T,E,precision", [("nature_small", 7, 5, 0), ("resnet_small", 6, 4, 0),
-                                                ("nature_h32", 5, 3, 0), ("nature_h64", 5, 64, 0),
-                                                ("blind_full", 9, 6, 0), ("nature_full", 8, 33, 0),
-                                                ("blind_full", 9, 6, 1), ("resnet_full", 4, 3, 1)])
-def test_whole_segment_matches_step_by_step(name, T, E, precision):
+@pytest.mark.parametrize("mode,name,T,E,precision", [
+    (1, "nature_small", 7, 5, 0), (1, "resnet_small", 6, 4, 0), (1, "nature_h32", 5, 3, 0),
+    (1, "nature_h64", 5, 64, 0), (1, "blind_full", 9, 6, 0), (1, "nature_full", 8, 33, 0),
+    (1, "blind_full", 9, 6, 1), (1, "resnet_full", 4, 3, 1),
+    # tcgen05 forward: N = 32 / 64 / 128 env columns, H = 64 .. 512 (2 .. 16 CTAs)
+    (2, "resnet_full", 4, 3, 1), (2, "blind_full", 9, 6, 1), (2, "blind_full", 5, 64, 1),
+    (2, "nature_full", 8, 33, 1), (2, "nature_h64", 5, 100, 1), (2, "nature_h192", 3, 17, 1),
+    (2, "nature_full", 1, 128, 1)])
+def test_whole_segment_matches_step_by_step(mode, name, T, E, precision):
     cfg = _cfg2(name, E, T, precision)
     net = Net(cfg, seed=1)
     try:
-        a = _run(net, cfg, T, E, True)
-        b = _run(net, cfg, T, E, False)
+        a = _run(net, cfg, T, E, mode)
+        b = _run(net, cfg, T, E, 0)
         names = ["logits", "values", "grad", "h", "c", "logp", "value"]
         tol = {"grad": 1e-4}
         for nm, x, y in zip(names, a, b):
@@ -107,3 +117,27 @@ def test_whole_segment_update_matches_step_by_step():
             net.close()
     (a, f0), (b, _) = outs
     assert ((a - f0) - (b - f0)).abs().max().item() <= 0.02 * 2.5e-4 * 4
+
+
+def test_tc_forward_update_matches_step_by_step():
+    """A whole BF16 2 x 2 PPO update with the tcgen05 forward (mode 2) against mode 0: the
+    parameter change agrees within 5% in relative L2 (BF16 operands; see the module note)."""
+    T, E, mb = 8, 6, 2
+    outs = []
+    for mode in (2, 0):
+        cfg = _cfg2("nature_h64", E, T, 1, mb=mb)
+        net = Net(cfg, seed=7)
+        try:
+            B.ddppo_lstm_whole_segment(net.h, mode)
+            ro_t, _ = _rollout_tensors(cfg, net, T, E, seed=8)
+            B.ddppo_ppo_update(net.h, _view(ro_t), B.default_hparams(minibatches=mb, update_index=3))
+            out = torch.zeros(net.P, device="cuda")
+            B.ddppo_get_params(net.h, out)
+            torch.cuda.synchronize()
+            assert B.ddppo_device_status(net.h) == 0
+            outs.append((out.cpu().double(), net.flat64()))
+        finally:
+            net.close()
+    (a, f0), (b, _) = outs
+    da, db = a - f0, b - f0
+    assert torch.linalg.vector_norm(da - db).item() <= 0.05 * torch.linalg.vector_norm(db).item()
