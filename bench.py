@@ -27,6 +27,21 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = "pointnav_resnet18b32_lstm2x512_E64_T128_rooms128"
+
+# the oracle's sample of each named workload for the reference arm: (workload name, sample
+# envs, sample frames, SimConfig fields, NetConfig fields, 2x2 pool, minibatches)
+ORACLE_SAMPLES = {
+    "resnet": (WORKLOAD, 4, 16, {}, {}, True, 2),
+    "nature": ("pointnav_nature_cnn_lstm128_E16_T32_bernoulli32", 4, 32,
+               dict(gen_kind=0, grid_min=32, grid_max=32, cell_m=0.25, depth_h=64, depth_w=64),
+               dict(net_kind=0, hidden=128, lstm_layers=1, in_h=64, in_w=64), False, 2),
+    "mixed": ("pointnav_resnet18b32_lstm2x512_E1024_T128_mixed64-512", 4, 16,
+              dict(grid_min=64, grid_max=512, depth_h=128, depth_w=128), {}, False, 2),
+    "wide": ("pointnav_resnet18b64_lstm2x512_E256_T128_rooms128", 4, 16, {}, dict(base_ch=64),
+             True, 2),
+    "scale": ("pointnav_resnet18b32_lstm2x512_E4096_T128_rooms128_4mb", 4, 16, {}, {}, True, 4),
+    "blind": ("pointnav_blind_lstm2x512_E64_T128_rooms128", 4, 16, {}, dict(net_kind=2), True, 2),
+}
 METRIC = "experience frames/sec (sim+act+learn) on 1 GB300, BF16 batched vs plain FP32"
 UNIT = "frames/s"
 
@@ -259,7 +274,8 @@ def run_reference(args):
         return
     from oracle import loop as OL
     import torch
-    r = OL.OracleLoop(num_envs=4, T=16, seed=3)
+    name, e, t, sim, net, pool, mb = ORACLE_SAMPLES[args.workload]
+    r = OL.OracleLoop(num_envs=e, T=t, seed=3, minibatches=mb, sim=sim, net=net, pool=pool)
     for _ in range(args.warmup):
         r.iterate()
     t0 = time.perf_counter()
@@ -268,12 +284,13 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     frames = r.E * r.T * args.steps
     v = frames / dt
-    sample = ("float64 oracle, each step = 1 iteration of 4 envs x 16 frames of the same workload "
-              "(ResNet-18/32 + 2x512 LSTM, 128x128 rooms, 256x256 depth, 2x2 PPO)")
+    sample = ("float64 oracle, each step = 1 iteration of %d envs x %d frames of the workload's "
+              "worlds and network, %d epochs x %d minibatches" % (e, t, 2, mb))
+    WL = name
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1e3 * dt / args.steps, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample": sample},
+            "data": "synthetic", "config": {"workload": WL, "sample": sample},
             "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": torch.get_num_threads(),
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -289,7 +306,10 @@ def main():
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
     ap.add_argument("--skip-fp32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-steps", type=int, default=1)
+    ap.add_argument("--cpu-sample-steps", type=int, default=6,
+                    help="oracle iterations timed for cpu_baseline (about 10-20 s of host work)")
+    ap.add_argument("--workload", default="resnet", choices=sorted(ORACLE_SAMPLES),
+                    help="reference arm only: the workload whose oracle sample is timed")
     ap.add_argument("--rollout-T", type=int, default=None,
                     help="shorter rollout for profiler launch lists (not a bench value)")
     ap.add_argument("--profile", action="store_true",

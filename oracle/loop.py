@@ -32,14 +32,22 @@ def init_params(cfg: P.NetConfig, seed: int) -> torch.Tensor:
 
 
 class OracleLoop:
-    """ResNet-18-style (32 base) agent with a 2-layer 512 LSTM on 128x128 rooms grids at
-    0.1 m with 256x256 depth pooled to 128x128 (the paper-shaped single-GPU workload)."""
+    """By default the ResNet-18-style (32 base) agent with a 2-layer 512 LSTM on 128x128
+    rooms grids at 0.1 m with 256x256 depth pooled to 128x128 (the paper-shaped
+    single-GPU workload). sim / net: SimConfig / NetConfig fields that replace those
+    defaults (another workload); pool: the 2x2 average pool of the depth image."""
 
-    def __init__(self, num_envs: int = 4, T: int = 16, seed: int = 0, minibatches: int = 2):
+    def __init__(self, num_envs: int = 4, T: int = 16, seed: int = 0, minibatches: int = 2,
+                 sim: dict | None = None, net: dict | None = None, pool: bool = True):
         self.E, self.T = num_envs, T
-        self.scfg = S.SimConfig(num_envs=num_envs, gen_kind=1, grid_min=128, grid_max=128,
-                                cell_m=0.1, depth_h=256, depth_w=256, seed=seed)
-        self.ncfg = P.NetConfig(net_kind=1, base_ch=32, hidden=512, lstm_layers=2, in_h=128, in_w=128)
+        skw = dict(num_envs=num_envs, gen_kind=1, grid_min=128, grid_max=128, cell_m=0.1,
+                   depth_h=256, depth_w=256, seed=seed)
+        skw.update(sim or {})
+        self.scfg = S.SimConfig(**skw)
+        nkw = dict(net_kind=1, base_ch=32, hidden=512, lstm_layers=2, in_h=128, in_w=128)
+        nkw.update(net or {})
+        self.ncfg = P.NetConfig(**nkw)
+        self.pool = pool
         self.hp = R.PPOHParams(minibatches=minibatches)
         self.seed = seed
         self.sim = S.BatchSim(self.scfg)
@@ -53,7 +61,7 @@ class OracleLoop:
         self.h = torch.zeros(L, num_envs, H, dtype=DT)
         self.c = torch.zeros(L, num_envs, H, dtype=DT)
         depth, goal = self.sim.render()
-        self.obs = torch.from_numpy(S.pool_obs(depth, True, self.scfg.max_depth_m)).unsqueeze(1)
+        self.obs = torch.from_numpy(S.pool_obs(depth, self.pool, self.scfg.max_depth_m)).unsqueeze(1)
         self.goal = torch.from_numpy(goal)
         self.prev_a = torch.full((num_envs,), 4, dtype=torch.int32)
         self.masks = torch.zeros(num_envs, dtype=torch.uint8)
@@ -78,7 +86,7 @@ class OracleLoop:
                 rewards.append(r)
                 dones.append(d)
                 depth, goal = self.sim.render()
-                self.obs = torch.from_numpy(S.pool_obs(depth, True, self.scfg.max_depth_m)).unsqueeze(1)
+                self.obs = torch.from_numpy(S.pool_obs(depth, self.pool, self.scfg.max_depth_m)).unsqueeze(1)
                 self.goal = torch.from_numpy(goal)
                 dt = torch.from_numpy(d.astype(np.int32))
                 self.prev_a = torch.where(dt == 1, torch.full_like(a, 4), a).to(torch.int32)

@@ -97,12 +97,25 @@ __global__ void __launch_bounds__(LT_THREADS, 1) lstm_tc_fwd_kernel(LstmTc a) {
                  "r"((uint32_t)NP));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
-  // resident A: row r = 4 uu + q  <-  W_hh row q H + u0 + uu
-  for (int i = threadIdx.x; i < 128 * (H / 8); i += LT_THREADS) {
-    const int r = i / (H / 8), kc = i - r * (H / 8);
-    const int q = r & 3, uu = r >> 2;
-    const uint4 v = __ldg(reinterpret_cast<const uint4*>(a.Whh + ((size_t)q * H + u0 + uu) * H) + kc);
-    *reinterpret_cast<uint4*>(sA + (size_t)(kc >> 3) * 128 * 128 + sw128_off(r, kc & 7)) = v;
+  // resident A: row r = 4 uu + q  <-  W_hh row q H + u0 + uu (eight 16-byte loads in flight
+  // per thread)
+  for (int i0 = threadIdx.x; i0 < 128 * (H / 8); i0 += LT_THREADS * 8) {
+    uint4 v[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = i0 + j * LT_THREADS;
+      const int r = i / (H / 8), kc = i - r * (H / 8);
+      const int q = r & 3, uu = r >> 2;
+      if (i < 128 * (H / 8))
+        v[j] = __ldg(reinterpret_cast<const uint4*>(a.Whh + ((size_t)q * H + u0 + uu) * H) + kc);
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int i = i0 + j * LT_THREADS;
+      if (i >= 128 * (H / 8)) break;
+      const int r = i / (H / 8), kc = i - r * (H / 8);
+      *reinterpret_cast<uint4*>(sA + (size_t)(kc >> 3) * 128 * 128 + sw128_off(r, kc & 7)) = v[j];
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();

@@ -206,7 +206,7 @@ struct Net {
   unsigned* lstm_bar = nullptr;  // grid-barrier counter of the whole-segment LSTM kernels
   // LSTM recurrence: 0 step by step; 1 whole segment on CUDA cores (forward and
   // backward); 2 forward on tcgen05 (whole segment, BF16), backward step by step
-  int lstm_mode = 2;
+  int lstm_mode = 0;
   bool gn_fused_on = true;       // GroupNorm statistics + normalisation in one launch
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
