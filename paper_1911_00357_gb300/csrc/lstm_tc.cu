@@ -127,6 +127,22 @@ __global__ void __launch_bounds__(LT_THREADS, 1) lstm_tc_fwd_kernel(LstmTc a) {
   const int k = lane & 7, eo = lane >> 3;
   const int u = u0 + 8 * warp + k;
   float cst[NCH][8];
+  // the input projection of the next step does not depend on the recurrence: it is loaded
+  // into registers before the step's barrier, off the critical path
+  float zg[NCH][8][4];
+  auto load_gx = [&](int t) {
+    const float* gx_t = a.gx + (size_t)t * E * G4;
+#pragma unroll
+    for (int ch = 0; ch < NCH; ++ch)
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int e = ch * 32 + eo + 4 * i;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          zg[ch][i][q] = e < E ? gx_t[(size_t)e * G4 + (size_t)q * H + u] : 0.f;
+      }
+  };
+  load_gx(0);
   bool failed = false;
   uint32_t issued = 0;  // MMA batches committed (for the drain after a run-out)
   for (int t = 0; t < a.T && !failed; ++t) {
@@ -170,7 +186,6 @@ __global__ void __launch_bounds__(LT_THREADS, 1) lstm_tc_fwd_kernel(LstmTc a) {
     // (uniform: a thread whose wait ran out makes the whole CTA stop)
     const bool ok = __syncthreads_and(mbar_wait(&mma_bar, (uint32_t)(t & 1), abort, a.err) ? 1 : 0) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const float* gx_t = a.gx + (size_t)t * E * G4;
     const uint8_t* m_t = a.m + (size_t)t * E;
     const uint8_t* m_n = t + 1 < a.T ? a.m + (size_t)(t + 1) * E : nullptr;
 #pragma unroll
@@ -192,22 +207,14 @@ __global__ void __launch_bounds__(LT_THREADS, 1) lstm_tc_fwd_kernel(LstmTc a) {
       for (int j = 0; j < 32; ++j) ztw[lane * LT_PITCH + j] = __uint_as_float(r[j]);
       __syncwarp();
       // 4. the cells (unit u, env e = 32 ch + eo + 4 i)
-      float zg[8][4];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int el = eo + 4 * i, e = ch * 32 + el;
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-          zg[i][q] = e < E ? gx_t[(size_t)e * G4 + (size_t)q * H + u] : 0.f;
-      }
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int el = eo + 4 * i, e = ch * 32 + el;
         if (e >= E) continue;
-        const float zi = zg[i][0] + ztw[(4 * k + 0) * LT_PITCH + el];
-        const float zf = zg[i][1] + ztw[(4 * k + 1) * LT_PITCH + el];
-        const float zq = zg[i][2] + ztw[(4 * k + 2) * LT_PITCH + el];
-        const float zo = zg[i][3] + ztw[(4 * k + 3) * LT_PITCH + el];
+        const float zi = zg[ch][i][0] + ztw[(4 * k + 0) * LT_PITCH + el];
+        const float zf = zg[ch][i][1] + ztw[(4 * k + 1) * LT_PITCH + el];
+        const float zq = zg[ch][i][2] + ztw[(4 * k + 2) * LT_PITCH + el];
+        const float zo = zg[ch][i][3] + ztw[(4 * k + 3) * LT_PITCH + el];
         const float ig = lt_sigm(zi), fg = lt_sigm(zf), gg = tanhf(zq), og = lt_sigm(zo);
         const size_t idx = (size_t)e * H + u;
         const float cprev = t == 0 ? a.c0[idx] : cst[ch][i];
@@ -231,6 +238,7 @@ __global__ void __launch_bounds__(LT_THREADS, 1) lstm_tc_fwd_kernel(LstmTc a) {
     // the accumulator is rewritten by the next step's MMAs
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     if (!ok) { failed = true; break; }
+    if (t + 1 < a.T) load_gx(t + 1);
     // 5. every CTA's state for step t + 1 is written before anyone stages it
     if (t + 1 < a.T && !lt_grid_barrier(a.bar, (unsigned)t, a.err, &s_ok)) failed = true;
   }

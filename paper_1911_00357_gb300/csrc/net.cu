@@ -969,7 +969,8 @@ static int lstm_forward(Net& n, int T, int E, const uint8_t* masks, const float*
                         const float* c0, cudaStream_t s) {
   const int N = T * E, Hd = n.H, G4 = 4 * Hd;
   const bool seq = n.lstm_mode == 1 && lstm_seq_supported(Hd, E, n.gws.num_sms);
-  const bool tc = n.lstm_mode == 2 && n.bf && lstm_tc_supported(Hd, E, n.gws.num_sms);
+  // (a single step -- the act path -- gains nothing from the resident weights: step path)
+  const bool tc = n.lstm_mode == 2 && n.bf && T > 1 && lstm_tc_supported(Hd, E, n.gws.num_sms);
   for (int l = 0; l < n.L; ++l) {
     LstmL& q = n.lstm[l];
     GemmDesc gx;
