@@ -13,9 +13,11 @@
 //      layout, env rows padded with zeros to N = 32, 64 or 128;
 //   2. one thread issues the H / 16 MMAs (M = 128, N, K = 16) into an fp32 TMEM
 //      accumulator and commits them to an mbarrier;
-//   3. each warp reads its 32 TMEM lanes (rows). Row r holds gate r % 4 of unit r / 4, so a
-//      warp holds all four gates of 8 units; a per-warp shared-memory transpose hands each
-//      lane 8 (unit, env) cells, whose cell state c stays in registers across the steps;
+//   3. 16 warps read the accumulator: warp w takes TMEM lanes (rows) 32 (w % 4) .. + 31 and
+//      columns 8 (w / 4) .. + 7 of every 32-column chunk. Row r holds gate r % 4 of unit
+//      r / 4, so a warp holds all four gates of 8 units; a per-warp shared-memory transpose
+//      hands each lane 2 (unit, env) cells per chunk, whose cell state c stays in registers
+//      across the steps;
 //   4. the lane adds gx, applies the gate nonlinearities and the cell update (the same
 //      arithmetic as the step-by-step cell kernel), and writes the gates, c, h, the
 //      layer output and the masked state entering the next step;
@@ -32,9 +34,9 @@ namespace ddppo {
 
 namespace {
 
-constexpr int LT_THREADS = 128;  // 4 warps: one per 32 TMEM lanes
+constexpr int LT_THREADS = 512;  // 16 warps: 4 per 32 TMEM lanes, each 8 columns of a chunk
 constexpr int LT_UNITS = 32;     // hidden units per CTA (128 gate rows)
-constexpr int LT_PITCH = 33;     // floats per row of the per-warp transpose tile
+constexpr int LT_PITCH = 9;      // floats per row of the per-warp transpose tile (8 columns)
 
 __device__ __forceinline__ float lt_sigm(float x) { return 1.0f / (1.0f + expf(-x)); }
 
@@ -82,8 +84,9 @@ __global__ void __launch_bounds__(LT_THREADS, 1) lstm_tc_fwd_kernel(LstmTc a) {
   uint8_t* base = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = base;                                 // KA atoms of 128 rows x 128 B
   uint8_t* sB = sA + (size_t)KA * 128 * 128;          // KA atoms of NP rows x 128 B
-  float* zt = (float*)(sB + (size_t)KA * NP * 128);   // [4 warps][32][LT_PITCH]
+  float* zt = (float*)(sB + (size_t)KA * NP * 128);   // [16 warps][32][LT_PITCH]
   float* ztw = zt + warp * 32 * LT_PITCH;
+  const int qd = warp & 3, cg = warp >> 2;  // TMEM lane quadrant, 8-column group
   volatile int* abort = &abort_flag;
 
   if (threadIdx.x == 0) {
@@ -123,20 +126,21 @@ __global__ void __launch_bounds__(LT_THREADS, 1) lstm_tc_fwd_kernel(LstmTc a) {
   const uint32_t tmem = tmem_base;
   const uint32_t idesc = f16_idesc(128, NP, 0, 0);
 
-  // this lane's cells: unit k of the warp's 8, envs eo + 4 i of every 32-env chunk
+  // this lane's cells: unit k of the warp's 8, envs 8 cg + eo + 4 i (i = 0, 1) of every
+  // 32-env chunk
   const int k = lane & 7, eo = lane >> 3;
-  const int u = u0 + 8 * warp + k;
-  float cst[NCH][8];
+  const int u = u0 + 8 * qd + k;
+  float cst[NCH][2];
   // the input projection of the next step does not depend on the recurrence: it is loaded
   // into registers before the step's barrier, off the critical path
-  float zg[NCH][8][4];
+  float zg[NCH][2][4];
   auto load_gx = [&](int t) {
     const float* gx_t = a.gx + (size_t)t * E * G4;
 #pragma unroll
     for (int ch = 0; ch < NCH; ++ch)
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int e = ch * 32 + eo + 4 * i;
+      for (int i = 0; i < 2; ++i) {
+        const int e = ch * 32 + 8 * cg + eo + 4 * i;
 #pragma unroll
         for (int q = 0; q < 4; ++q)
           zg[ch][i][q] = e < E ? gx_t[(size_t)e * G4 + (size_t)q * H + u] : 0.f;
@@ -191,25 +195,21 @@ __global__ void __launch_bounds__(LT_THREADS, 1) lstm_tc_fwd_kernel(LstmTc a) {
 #pragma unroll
     for (int ch = 0; ch < NCH; ++ch) {
       if (!ok) break;
-      uint32_t r[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(ch * 32);
+      uint32_t r[8];
+      const uint32_t taddr = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(ch * 32 + cg * 8);
       asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-          "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
           : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-            "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-            "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-            "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-            "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            "=r"(r[7])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int j = 0; j < 32; ++j) ztw[lane * LT_PITCH + j] = __uint_as_float(r[j]);
+      for (int j = 0; j < 8; ++j) ztw[lane * LT_PITCH + j] = __uint_as_float(r[j]);
       __syncwarp();
-      // 4. the cells (unit u, env e = 32 ch + eo + 4 i)
+      // 4. the cells (unit u, env e = 32 ch + 8 cg + eo + 4 i)
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int el = eo + 4 * i, e = ch * 32 + el;
+      for (int i = 0; i < 2; ++i) {
+        const int el = eo + 4 * i, e = ch * 32 + 8 * cg + el;
         if (e >= E) continue;
         const float zi = zg[ch][i][0] + ztw[(4 * k + 0) * LT_PITCH + el];
         const float zf = zg[ch][i][1] + ztw[(4 * k + 1) * LT_PITCH + el];
@@ -260,7 +260,7 @@ static int lt_nch(int E) { return E <= 32 ? 1 : E <= 64 ? 2 : E <= 128 ? 4 : 0; 
 
 static size_t lt_smem(int H, int E) {
   const int np = 32 * lt_nch(E);
-  return 1024 + (size_t)(128 + np) * H * 2 + (size_t)4 * 32 * LT_PITCH * sizeof(float);
+  return 1024 + (size_t)(128 + np) * H * 2 + (size_t)(LT_THREADS / 32) * 32 * LT_PITCH * sizeof(float);
 }
 
 bool lstm_tc_supported(int H, int E, int num_sms) {
