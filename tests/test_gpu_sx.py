@@ -57,28 +57,50 @@ def _eval_backward(net, cfg, T, E):
     return ref, logits.cpu(), values.cpu(), grad.cpu().double(), dl.double(), dv.double()
 
 
+# parameter perturbations at fp32 scale for the kink floor (see the evaluate test below)
+KINK_EPS = (2.0 ** -24, 2.0 ** -23)
+
+
+def _pooled_enc_rest(ncfg, g):
+    t = _per_tensor(ncfg, g)
+    enc = torch.cat([v.flatten() for k, v in t.items() if not k.startswith(HEAD_PREFIX)])
+    rest = torch.cat([v.flatten() for k, v in t.items() if k.startswith(HEAD_PREFIX)])
+    return enc, rest
+
+
 @pytest.mark.parametrize("kind,base,T,E,whole", [(3, 16, 2, 2, True), (3, 32, 2, 2, True),
                                                   (3, 16, 2, 2, False)])
 def test_sx_fp32_evaluate_and_backward(kind, base, T, E, whole):
+    """FP32 logits and values within 1e-4 of the float64 oracle; gradients pooled over the
+    encoder (and over the rest of the network) within 2.5 times the oracle's own kink
+    floor plus 1e-4: the change of the float64 gradient when the parameters move by one
+    fp32 rounding (relative 2^-24 and 2^-23 Gaussian perturbations). ReLU and max-pool
+    kinks make a deep encoder's gradient sensitive at that scale: for the 32-base
+    SE-ResNeXt50 on these inputs the oracle's own gradient moves by up to ~1e-2 per
+    tensor, for the 16-base one by ~1e-7, and the GPU sits at about twice that floor."""
     cfg = _sx_cfg(kind, base, E, T, 0)
     net = Net(cfg, seed=1)
     try:
         B.ddppo_lstm_whole_segment(net.h, whole)
         ref, lg, vv, gg, dl, dv = _eval_backward(net, cfg, T, E)
-        lg_r, v_r, g_r = _forward_grad(OP.sequence_forward, net.flat64(), ref, net.ncfg, dl, dv)
+        f64 = net.flat64()
+        lg_r, v_r, g_r = _forward_grad(OP.sequence_forward, f64, ref, net.ncfg, dl, dv)
         assert _rel(lg, lg_r) <= 1e-4 and _rel(vv, v_r) <= 1e-4, (_rel(lg, lg_r), _rel(vv, v_r))
-        gp, gr = _per_tensor(net.ncfg, gg), _per_tensor(net.ncfg, g_r)
-        enc, rest = {}, {}
-        for k in gr:
-            if torch.linalg.vector_norm(gr[k]).item() < 1e-8:
-                continue
-            (rest if k.startswith(HEAD_PREFIX) else enc)[k] = _rel_l2(gp[k], gr[k])
-        print("\nSE-ResNeXt%d base %d FP32 gradient errors: encoder max %.3g median %.3g, rest max %.3g"
-              % (50 if kind == 3 else 101, base, max(enc.values()), np.median(list(enc.values())),
-                 max(rest.values())))
-        assert max(rest.values()) <= 1e-3, max(rest, key=rest.get)
-        assert max(enc.values()) <= 5e-2, max(enc, key=enc.get)
-        assert np.median(list(enc.values())) <= 1e-2
+        pe, pr = _pooled_enc_rest(net.ncfg, g_r)
+        ge, gr_ = _pooled_enc_rest(net.ncfg, gg)
+        got = {"encoder": _rel_l2(ge, pe), "rest": _rel_l2(gr_, pr)}
+        floor = {"encoder": 0.0, "rest": 0.0}
+        for i, eps in enumerate(KINK_EPS):
+            noise = torch.randn(f64.shape, generator=torch.Generator().manual_seed(60 + i), dtype=DT)
+            _, _, g_p = _forward_grad(OP.sequence_forward, f64 * (1 + eps * noise), ref, net.ncfg,
+                                      dl, dv)
+            qe, qr = _pooled_enc_rest(net.ncfg, g_p)
+            floor = {"encoder": max(floor["encoder"], _rel_l2(qe, pe)),
+                     "rest": max(floor["rest"], _rel_l2(qr, pr))}
+        print("\nSE-ResNeXt%d base %d FP32 pooled gradient errors %s, kink floor %s"
+              % (50 if kind == 3 else 101, base, got, floor))
+        for k in got:
+            assert got[k] <= 2.5 * floor[k] + 1e-4, (k, got[k], floor[k])
     finally:
         net.close()
 
@@ -133,7 +155,15 @@ def test_sx_fp32_ppo_update():
         f2, _, _, st2, sts = OR.ppo_update(f0, z, z.clone(), 0, ro, net.ncfg, hp, seed=cfg.seed,
                                            update=1)
         err = ((out.cpu().double() - f0) - (f2 - f0)).abs().max().item()
-        assert err <= 0.02 * hp.lr * st2, err
+        # the oracle's own kink floor: its update from parameters moved by one fp32 rounding
+        # (Adam turns a gradient coordinate that flips at a ReLU kink into a whole step)
+        noise = torch.randn(f0.shape, generator=torch.Generator().manual_seed(61), dtype=f0.dtype)
+        fp = f0 * (1 + 2.0 ** -24 * noise)
+        f3, _, _, _, _ = OR.ppo_update(fp, z, z.clone(), 0, ro, net.ncfg, hp, seed=cfg.seed, update=1)
+        floor = ((f3 - fp) - (f2 - f0)).abs().max().item()
+        print("\nSE-ResNeXt50 FP32 update: max parameter-change error %.3g, oracle kink floor %.3g"
+              % (err, floor))
+        assert err <= 2.5 * floor + 0.02 * hp.lr * st2, (err, floor)
         s = stats.cpu().double()
         for k, st in enumerate(sts):
             assert abs(s[k, 0].item() - st["loss"].item()) <= 1e-4 * max(1.0, abs(st["loss"].item()))
