@@ -275,7 +275,7 @@ def sequence_forward(p, obs, goal, prev_a, masks, h0, c0, cfg):
     c = [c0[l] for l in range(L)]
     logits, values = [], []
     for t in range(T):
-        m = masks[t].to(DT).unsqueeze(1)
+        m = masks[t].to(h0.dtype).unsqueeze(1)  # float64 here; a float32 state in the tests' fp32 floor
         x = x_all[t]
         for l in range(L):
             h[l], c[l] = lstm_cell(x, h[l] * m, c[l] * m, p[f"lstm{l}.w_ih"], p[f"lstm{l}.w_hh"],

@@ -72,12 +72,13 @@ def _pooled_enc_rest(ncfg, g):
                                                   (3, 16, 2, 2, False)])
 def test_sx_fp32_evaluate_and_backward(kind, base, T, E, whole):
     """FP32 logits and values within 1e-4 of the float64 oracle; gradients pooled over the
-    encoder (and over the rest of the network) within 2.5 times the oracle's own kink
-    floor plus 1e-4: the change of the float64 gradient when the parameters move by one
-    fp32 rounding (relative 2^-24 and 2^-23 Gaussian perturbations). ReLU and max-pool
-    kinks make a deep encoder's gradient sensitive at that scale: for the 32-base
-    SE-ResNeXt50 on these inputs the oracle's own gradient moves by up to ~1e-2 per
-    tensor, for the 16-base one by ~1e-7, and the GPU sits at about twice that floor."""
+    encoder (and over the rest of the network) within 2.5 times the kink floor plus 1e-4.
+    The floor is the larger of (a) the change of the oracle's float64 gradient when the
+    parameters move by one fp32 rounding (relative 2^-24 and 2^-23 Gaussian
+    perturbations) and (b) the distance to float64 of the same oracle evaluated in plain
+    float32 on the CPU. ReLU and max-pool kinks make a deep encoder's gradient sensitive
+    at that scale: for the 32-base SE-ResNeXt50 on these inputs a float32 evaluation is
+    7.8e-3 from float64 (the GPU 6.0e-3), for the 16-base one 7.4e-6 (the GPU 7.7e-6)."""
     cfg = _sx_cfg(kind, base, E, T, 0)
     net = Net(cfg, seed=1)
     try:
@@ -97,6 +98,14 @@ def test_sx_fp32_evaluate_and_backward(kind, base, T, E, whole):
             qe, qr = _pooled_enc_rest(net.ncfg, g_p)
             floor = {"encoder": max(floor["encoder"], _rel_l2(qe, pe)),
                      "rest": max(floor["rest"], _rel_l2(qr, pr))}
+        # (b) the same network in plain float32 (the oracle's ops on float32 tensors)
+        ref32 = {k: (v.float() if torch.is_tensor(v) and v.is_floating_point() else v)
+                 for k, v in ref.items()}
+        _, _, g32 = _forward_grad(OP.sequence_forward, f64.float(), ref32, net.ncfg, dl.float(),
+                                  dv.float())
+        qe, qr = _pooled_enc_rest(net.ncfg, g32.double())
+        floor = {"encoder": max(floor["encoder"], _rel_l2(qe, pe)),
+                 "rest": max(floor["rest"], _rel_l2(qr, pr))}
         print("\nSE-ResNeXt%d base %d FP32 pooled gradient errors %s, kink floor %s"
               % (50 if kind == 3 else 101, base, got, floor))
         for k in got:
@@ -159,14 +168,18 @@ def test_sx_fp32_ppo_update():
         # (Adam turns a gradient coordinate that flips at a ReLU kink into a whole step)
         noise = torch.randn(f0.shape, generator=torch.Generator().manual_seed(61), dtype=f0.dtype)
         fp = f0 * (1 + 2.0 ** -24 * noise)
-        f3, _, _, _, _ = OR.ppo_update(fp, z, z.clone(), 0, ro, net.ncfg, hp, seed=cfg.seed, update=1)
+        f3, _, _, _, sts3 = OR.ppo_update(fp, z, z.clone(), 0, ro, net.ncfg, hp, seed=cfg.seed,
+                                          update=1)
         floor = ((f3 - fp) - (f2 - f0)).abs().max().item()
         print("\nSE-ResNeXt50 FP32 update: max parameter-change error %.3g, oracle kink floor %.3g"
               % (err, floor))
         assert err <= 2.5 * floor + 0.02 * hp.lr * st2, (err, floor)
         s = stats.cpu().double()
         for k, st in enumerate(sts):
-            assert abs(s[k, 0].item() - st["loss"].item()) <= 1e-4 * max(1.0, abs(st["loss"].item()))
+            # the first minibatch's loss sees the initial parameters (fp32 accuracy); later
+            # ones see parameters after Adam steps, bounded like the parameters
+            lf = abs(sts3[k]["loss"].item() - st["loss"].item())
+            assert abs(s[k, 0].item() - st["loss"].item()) <= 2.5 * lf + 1e-4 * max(1.0, abs(st["loss"].item()))
     finally:
         net.close()
 
