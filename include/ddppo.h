@@ -457,8 +457,11 @@ int ddppo_gemm(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const void* A, 
  * x [dev] NHWC bf16 [N, H, W, C]; w [dev] bf16 [Cout, k*k*C] with K ordered (ky, kx, c);
  * y [dev] fp32 NHWC [N, Ho, Wo, Cout] (read when beta != 0). Requires C % 32 == 0 and an
  * output width dividing 128 (whole output rows per 128-pixel tile), or stride 1, odd k,
- * p = k / 2, C == 32, Cout <= 128 and W + 2p <= 256; E_CONFIG otherwise. status as for
- * ddppo_gemm. The first call per device allocates a split-K workspace. */
+ * p = k / 2, C == 32, Cout <= 128 and W + 2p <= 256, or -- the encoder's stem -- C == 1,
+ * k * k <= 64 and Cout 16, 32 or 64 (each 128-pixel tile's patches gathered by the CTA
+ * into shared memory, the weights resident; at most 2^30 output pixels); E_CONFIG
+ * otherwise. status as for ddppo_gemm. The first call per device allocates a split-K
+ * workspace. */
 int ddppo_conv2d(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, int32_t k,
                  int32_t stride, int32_t pad, const void* x, const void* w, float* y,
                  float beta, int32_t* status, void* stream);

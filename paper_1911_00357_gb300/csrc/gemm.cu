@@ -1,6 +1,7 @@
 // SIMT GEMM (the plain FP32 form, and the fallback shape path of the BF16 form) with
 // deterministic split-K, plus the dispatcher that routes bf16 operands to tcgen05.
 #include "gemm.cuh"
+#include "nn_kernels.cuh"
 
 namespace ddppo {
 
@@ -168,6 +169,14 @@ static int gemm_fp8(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s) 
   return gemm_tc(p, ws, s);
 }
 
+// the single-channel convolution kernel covers this contraction: an implicit convolution
+// of a 1-channel input into fp32 rows of Cout (no bias, ReLU or bf16 output)
+static bool conv_c1_ok(const GemmDesc& d) {
+  return d.conv && d.conv->C == 1 && conv_c1_tc_supported(d.conv->k, d.conv->Cout) &&
+         d.N == d.conv->Cout && d.ldc == d.N && !d.c_bf16 && !d.bias && !d.relu && !d.fp8 &&
+         d.ldb >= d.conv->k * d.conv->k;
+}
+
 int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t s,
          KernelTimer* timer) {
   if (d.M <= 0 || d.N <= 0) return DDPPO_OK;
@@ -183,7 +192,7 @@ int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t 
     set_error("gemm: bf16 output cannot accumulate");
     return DDPPO_E_CONFIG;
   }
-  if (d.conv && !d.fp8 && !(op_bf16 && gemm_conv_supported(*d.conv, d.A))) {
+  if (d.conv && !d.fp8 && !(op_bf16 && (gemm_conv_supported(*d.conv, d.A) || conv_c1_ok(d)))) {
     set_error("gemm: implicit convolution not supported for this shape");
     return DDPPO_E_CONFIG;
   }
@@ -208,6 +217,19 @@ int gemm(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, cudaStream_t 
   int rc;
   if (d.fp8) {
     rc = gemm_fp8(d, ws, s);
+    if (ws.tc && ws.tc->on) {
+      ws.tc->launches += 1;
+      ws.tc->flops += 2.0 * d.M * d.N * d.K;
+    }
+  } else if (op_bf16 && conv_c1_ok(d)) {
+    // a single-channel convolution (the stem): patches gathered in shared memory
+    const ConvShape& c = *d.conv;
+    ConvC1 a{};
+    a.N = c.N; a.H = c.H; a.W = c.W; a.k = c.k; a.s = c.s; a.p = c.p; a.Ho = c.Ho; a.Wo = c.Wo;
+    a.Cout = c.Cout; a.ldw = d.ldb;
+    a.x = (const __nv_bfloat16*)d.A; a.w = (const __nv_bfloat16*)d.B; a.y = (float*)d.C;
+    a.beta = d.beta; a.err = ws.err;
+    rc = launch_conv_c1_tc(a, ws.num_sms, s);
     if (ws.tc && ws.tc->on) {
       ws.tc->launches += 1;
       ws.tc->flops += 2.0 * d.M * d.N * d.K;

@@ -927,7 +927,9 @@ extern "C" int ddppo_conv2d(int32_t N, int32_t H, int32_t W, int32_t C, int32_t 
   DDPPO_TRY(conv_args(N, H, W, C, Cout, k, stride, pad, &c));
   ARG(x && w && y, "conv2d: null argument");
   c.Cout = Cout;
-  if (!gemm_conv_supported(c, x)) {
+  // one input channel (the encoder's stem): the contraction gathers its patches itself
+  const bool c1 = C == 1 && conv_c1_tc_supported(k, Cout);
+  if (!c1 && !gemm_conv_supported(c, x)) {
     set_error("conv2d: shape not covered by the implicit-im2col path");
     return DDPPO_E_CONFIG;
   }

@@ -189,6 +189,16 @@ struct LstmTc {
   unsigned* bar; int32_t* err;
 };
 bool lstm_tc_supported(int H, int E, int num_sms);
+
+// single-channel convolution on tcgen05 (conv_c1_tc.cu): y [N, Ho, Wo, Cout] fp32
+// (= beta y + conv) of x [N, H, W] bf16 with w [Cout, ldw] bf16 (taps (ky, kx) in its
+// first k^2 columns); k^2 <= 64, Cout 16 / 32 / 64
+struct ConvC1 {
+  int N, H, W, k, s, p, Ho, Wo, Cout, ldw;
+  const __nv_bfloat16* x; const __nv_bfloat16* w; float* y; float beta; int32_t* err;
+};
+bool conv_c1_tc_supported(int k, int Cout);
+int launch_conv_c1_tc(const ConvC1& a, int num_sms, cudaStream_t s);
 int launch_lstm_tc_fwd(const LstmTc& a, int num_sms, cudaStream_t s);
 int launch_lstm_seq_fwd(const LstmSeq& a, int num_sms, cudaStream_t s);
 int launch_lstm_seq_bwd(const LstmSeq& a, int num_sms, cudaStream_t s);

@@ -37,6 +37,12 @@ SHAPES = [
     (3, 9, 9, 32, 64, 1, 1, 0),       # 1x1 filter
     (3, 8, 16, 64, 32, 3, 1, 1),      # 64 channels: 4-D gather path
     (2, 16, 16, 64, 64, 5, 1, 2),     # 5x5, 64 channels: 4-D gather path
+    # one input channel (the stem): patches gathered in shared memory, no im2col matrix
+    (3, 128, 128, 1, 32, 7, 2, 3),    # the bench's stem (64x64 outputs, 32 tiles per image)
+    (2, 64, 64, 1, 16, 7, 2, 3),      # 16 output channels
+    (3, 30, 22, 1, 64, 7, 2, 3),      # 64 output channels, ragged last tile
+    (2, 9, 9, 1, 32, 3, 1, 1),        # 3x3 / stride 1: a tile spans images
+    (1, 17, 13, 1, 32, 8, 3, 2),      # k^2 = 64: every tap column used
 ]
 
 
@@ -65,6 +71,7 @@ BETA_SHAPES = [
     (5, 5, 5, 32, 32, 3, 1, 1),       # halo, two images per tile
     (2, 30, 30, 32, 32, 3, 1, 1),     # halo only (no whole rows per 128-pixel tile)
     (3, 16, 16, 64, 64, 3, 1, 1),     # 4-D gather path
+    (2, 40, 40, 1, 32, 7, 2, 3),      # one input channel
 ]
 
 
