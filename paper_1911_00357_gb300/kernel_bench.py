@@ -25,6 +25,12 @@ Algorithmic bytes per unit (each operand read once, each result written once):
               work, so the HBM fraction is reported for completeness. The next episodes are
               prepared (untimed) before each timed step, as in the collect loop
 
+  lstm        the 2-layer 512 LSTM forward over T = 128 steps of 32 envs (one update
+              minibatch of the ResNet workload, BF16) in each recurrence mode: 0 step by
+              step, 1 whole segment on CUDA cores, 2 whole segment on tcgen05 (times only)
+
+    python -m paper_1911_00357_gb300.kernel_bench --only lstm group_norm
+
 Each line is one JSON object; `frac` is achieved / peak, the peak being the measured copy
 bandwidth passed in (the GB/s of a plain device copy on this GPU model). A measurement
 tool; the headline number is bench.py's.
@@ -157,18 +163,53 @@ def bench_worker_kernels(tm, peak, presets):
             w.close()
 
 
+def bench_lstm(tm, peak):
+    from .presets import make_config
+    T, E = 128, 32
+    cfg = make_config("resnet", num_envs=64, rollout_T=T, precision=1)
+    h = B.ddppo_create(cfg)
+    try:
+        P = B.ddppo_num_params(h)
+        g = torch.Generator(device="cuda").manual_seed(5)
+        B.ddppo_set_params(h, torch.randn(P, device="cuda", generator=g) * 0.02)
+        x = torch.randn(T, E, cfg.hidden + 64, device="cuda", generator=g)
+        m = torch.ones(T, E, dtype=torch.uint8, device="cuda")
+        h0 = torch.zeros(cfg.lstm_layers, E, cfg.hidden, device="cuda")
+        c0 = torch.zeros_like(h0)
+        y = torch.zeros(T, E, cfg.hidden, device="cuda")
+        for mode in (0, 1, 2):
+            B.ddppo_lstm_whole_segment(h, mode)
+            ms = tm(lambda: B.ddppo_lstm_forward(h, T, E, x, m, h0, c0, y))
+            print(json.dumps({"kernel": "lstm_forward", "mode": mode, "workload":
+                              "2 layers x 512, T 128 x E 32, BF16", "ms": round(ms, 4),
+                              "us_per_step_and_layer": round(1e3 * ms / (T * cfg.lstm_layers), 2)}),
+                  flush=True)
+        assert B.ddppo_device_status(h) == 0
+    finally:
+        B.ddppo_destroy(h)
+
+
+BENCHES = {"gae": bench_gae, "ppo_loss": bench_loss, "group_norm": bench_group_norm,
+           "lstm": bench_lstm}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--reps", type=int, default=15)
+    ap.add_argument("--only", nargs="+", default=None,
+                    choices=sorted(BENCHES) + ["adam_env_step"],
+                    help="run these benches only (adam_env_step: the worker-based ones)")
     ap.add_argument("--peak-gbs", type=float, default=6783.8,
                     help="measured device-copy bandwidth (GB/s) used as the roofline peak")
     ap.add_argument("--presets", nargs="+", default=["resnet", "wide_256", "mixed_1024"])
     args = ap.parse_args()
     tm = _Timer(args.reps)
-    bench_gae(tm, args.peak_gbs)
-    bench_loss(tm, args.peak_gbs)
-    bench_group_norm(tm, args.peak_gbs)
-    bench_worker_kernels(tm, args.peak_gbs, args.presets)
+    only = args.only or (sorted(BENCHES) + ["adam_env_step"])
+    for name in ("gae", "ppo_loss", "group_norm", "lstm"):
+        if name in only:
+            BENCHES[name](tm, args.peak_gbs)
+    if "adam_env_step" in only:
+        bench_worker_kernels(tm, args.peak_gbs, args.presets)
 
 
 if __name__ == "__main__":
