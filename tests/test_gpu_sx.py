@@ -176,10 +176,17 @@ def test_sx_fp32_ppo_update():
         assert err <= 2.5 * floor + 0.02 * hp.lr * st2, (err, floor)
         s = stats.cpu().double()
         for k, st in enumerate(sts):
-            # the first minibatch's loss sees the initial parameters (fp32 accuracy); later
-            # ones see parameters after Adam steps, bounded like the parameters
-            lf = abs(sts3[k]["loss"].item() - st["loss"].item())
-            assert abs(s[k, 0].item() - st["loss"].item()) <= 2.5 * lf + 1e-4 * max(1.0, abs(st["loss"].item()))
+            scale = max(1.0, abs(st["loss"].item()))
+            d = abs(s[k, 0].item() - st["loss"].item())
+            if k == 0:
+                # the first minibatch's loss sees the initial parameters: fp32 accuracy
+                assert d <= 1e-4 * scale, (k, d)
+            else:
+                # later ones see parameters after Adam steps, which differ by up to a few
+                # lr in the coordinates whose gradient flipped at a kink (bounded above):
+                # within the perturbed oracle run's own loss change x 2.5, or 1e-3
+                lf = abs(sts3[k]["loss"].item() - st["loss"].item())
+                assert d <= max(2.5 * lf, 1e-3 * scale), (k, d, lf)
     finally:
         net.close()
 
