@@ -37,7 +37,7 @@ __device__ __forceinline__ uint32_t cc_pack(__nv_bfloat16 lo, __nv_bfloat16 hi) 
 
 // NC16: output channels / 16 (Cout = 16, 32 or 64)
 template <int NC16>
-__global__ void __launch_bounds__(CC_THREADS) conv_c1_tc_kernel(ConvC1 a) {
+__global__ void __launch_bounds__(CC_THREADS, 5) conv_c1_tc_kernel(ConvC1 a) {
   constexpr int COUT = 16 * NC16;
   constexpr uint32_t TCOLS = COUT < 32 ? 32 : COUT;
   extern __shared__ __align__(1024) uint8_t dyn[];
@@ -87,34 +87,46 @@ __global__ void __launch_bounds__(CC_THREADS) conv_c1_tc_kernel(ConvC1 a) {
   const uint32_t idesc = f16_idesc(128, COUT, 0, 0);
   const __nv_bfloat16 zero = __float2bfloat16_rn(0.f);
 
+  // this thread's chunk of taps (fixed over the tiles): offsets of taps 8 cc .. 8 cc + 7
+  const int cc = threadIdx.x & 7, rr = threadIdx.x >> 3;
+  int tdy[8], tdx[8];
+  uint32_t tval = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const int t = cc * 8 + q;
+    tdy[q] = t / a.k - a.p;
+    tdx[q] = t % a.k - a.p;
+    if (t < KK) tval |= 1u << q;
+  }
   uint32_t it = 0;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
     const int m0 = tile * 128;
-    // 1. the tile's patches: 128 rows x 8 chunks of 8 taps
-    for (int id = threadIdx.x; id < 128 * 8; id += CC_THREADS) {
-      const int r = id >> 3, c = id & 7;
-      const int m = m0 + r;
-      uint32_t v[4] = {0u, 0u, 0u, 0u};
-      if (m < M) {
-        const int n = m / HoWo;
-        const int rem = m - n * HoWo;
+    // 1. the tile's patches: 128 rows x 8 chunks of 8 taps. Thread i fills chunk i % 8 of
+    // rows i / 8 + 16 j (j = 0..7): its 8 taps are fixed, and all 64 loads are in flight
+    // before they are packed and stored
+    {
+      __nv_bfloat16 tv[8][8];
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int m = m0 + rr + 16 * j;
+        const bool in_m = m < M;
+        const int n = in_m ? m / HoWo : 0;
+        const int rem = in_m ? m - n * HoWo : 0;
         const int oy = rem / a.Wo, ox = rem - oy * a.Wo;
+        const int y0 = oy * a.s, x0 = ox * a.s;
         const __nv_bfloat16* xi = a.x + (size_t)n * a.H * a.W;
-        __nv_bfloat16 tv[8];
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-          const int t = c * 8 + q;
-          tv[q] = zero;
-          if (t < KK) {
-            const int ky = t / a.k, kx = t - ky * a.k;
-            const int iy = oy * a.s - a.p + ky, ix = ox * a.s - a.p + kx;
-            if (iy >= 0 && iy < a.H && ix >= 0 && ix < a.W) tv[q] = xi[(size_t)iy * a.W + ix];
-          }
+          const int iy = y0 + tdy[q], ix = x0 + tdx[q];
+          const bool ok = in_m && ((tval >> q) & 1) && iy >= 0 && iy < a.H && ix >= 0 && ix < a.W;
+          tv[j][q] = ok ? xi[iy * a.W + ix] : zero;
         }
-#pragma unroll
-        for (int h = 0; h < 4; ++h) v[h] = cc_pack(tv[2 * h], tv[2 * h + 1]);
       }
-      *reinterpret_cast<uint4*>(sA + cc_sw128(r, c)) = make_uint4(v[0], v[1], v[2], v[3]);
+#pragma unroll
+      for (int j = 0; j < 8; ++j)
+        *reinterpret_cast<uint4*>(sA + cc_sw128(rr + 16 * j, cc)) =
+            make_uint4(cc_pack(tv[j][0], tv[j][1]), cc_pack(tv[j][2], tv[j][3]),
+                       cc_pack(tv[j][4], tv[j][5]), cc_pack(tv[j][6], tv[j][7]));
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
@@ -198,9 +210,13 @@ int launch_conv_c1_tc(const ConvC1& a, int num_sms, cudaStream_t s) {
   void (*kern)(ConvC1) = a.Cout == 16 ? conv_c1_tc_kernel<1>
                        : a.Cout == 32 ? conv_c1_tc_kernel<2> : conv_c1_tc_kernel<4>;
   const size_t smem = cc_smem(a.Cout);
-  int occ = 0;
-  DDPPO_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, CC_THREADS, smem));
-  occ = std::max(1, std::min(occ, 8));
+  // CTAs per SM from the kernel's own limits: shared memory (227 KiB per SM, 1 KiB reserved
+  // per CTA), tensor memory (512 columns per SM), registers, and at most 8
+  const int tcols = a.Cout < 32 ? 32 : a.Cout;
+  cudaFuncAttributes fa{};
+  DDPPO_CHECK_CUDA(cudaFuncGetAttributes(&fa, kern));
+  const int regs = std::max(1, ((fa.numRegs + 7) / 8) * 8) * CC_THREADS;  // per CTA
+  const int occ = std::max(1, std::min({8, (int)(232448 / (smem + 1024)), 512 / tcols, 65536 / regs}));
   const long long grid = std::min<long long>(ntiles, (long long)num_sms * occ);
   kern<<<(unsigned)grid, CC_THREADS, smem, s>>>(a);
   DDPPO_CHECK_LAUNCH();
