@@ -627,13 +627,6 @@ static int conv_fwd(Net& n, ConvL& c, const void* in, bool in_bf16, int N, float
     d.A = in_bf; d.lda = d.K;
     return G(n, d, s);
   }
-  if (n.bf && in_bf16 && c.cin == 1 && !bias_relu && n.stem_tc_on &&
-      conv_c1_tc_supported(c.k, c.cout)) {
-    // the stem: the contraction gathers its patches in shared memory (no im2col matrix)
-    d.conv = &cs;
-    d.A = in; d.lda = d.K;
-    return G(n, d, s);
-  }
   const ConvGeom g = geom(c, N);
   DDPPO_TRY(launch_im2col(g, in, in_bf16, n.col, n.bf, false, s));
   d.A = n.col; d.lda = c.Kp;

@@ -208,7 +208,6 @@ struct Net {
   // backward); 2 forward on tcgen05 (whole segment, BF16), backward step by step
   int lstm_mode = 0;
   bool gn_fused_on = true;       // GroupNorm statistics + normalisation in one launch
-  bool stem_tc_on = true;        // single-channel stem convolution without im2col (BF16)
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev_a = nullptr, ev_b = nullptr;
   uint8_t* post_done = nullptr;
