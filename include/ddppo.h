@@ -506,14 +506,14 @@ int ddppo_conv2d_e4m3(int32_t N, int32_t H, int32_t W, int32_t C, int32_t Cout, 
 int ddppo_group_norm(int32_t N, int32_t HW, int32_t C, const float* z, const float* gamma,
                      const float* beta, const float* resid, int32_t relu, float* out, float* mean,
                      float* rstd, void* stream);
-/* How the encoder's forward GroupNorms run: on = 1 (the default) computes the statistics
- * and normalises in one cooperative launch wherever every block fits on the GPU at once
- * (the images' blocks meet at a bounded per-image barrier; z is read from HBM once);
- * otherwise, and with on = 0, a statistics launch then a normalise launch. Both give the
- * same statistics for the same split of an image over blocks; the one-launch form may use
- * fewer blocks per image, which changes only the fp32 summation order. ddppo_group_norm
- * takes the one-launch form when it fits. Applies to launches enqueued afterwards. Host
- * only. */
+/* How the encoder's forward GroupNorms run. An image of at most 32K elements is summed by
+ * one block, then normalised by a second launch that spreads it over many blocks. A larger
+ * image is split over S blocks: with on = 1 (the default) the statistics and the
+ * normalisation run in one cooperative launch wherever every block fits on the GPU at once
+ * (the image's blocks meet at a bounded per-image barrier, then normalise the rows they
+ * summed), otherwise, and with on = 0, as a statistics launch then a normalise launch.
+ * Both forms use the same S, so their results are bit-identical. ddppo_group_norm follows
+ * the same rules. Applies to launches enqueued afterwards. Host only. */
 int ddppo_group_norm_one_launch(ddppo_ctx* ctx, int32_t on);
 
 /* The SE-ResNeXt bottleneck's own kernels (App. "Visual Encoder"; ResNeXt's grouped

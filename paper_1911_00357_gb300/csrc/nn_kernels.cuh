@@ -55,9 +55,10 @@ struct GNApply {
 int launch_gn_apply(const GNApply& a, int N, int HW, int C, cudaStream_t s);
 // statistics and normalisation in one cooperative launch: a.mean/a.rstd (and a.mean_d /
 // a.rstd_d with zd) receive the statistics, out as launch_gn_apply. Sets *launched = false,
-// launching nothing, when the grid cannot be resident at once (many images) or w has no
-// departure counters; the caller then runs launch_gn_stats + launch_gn_apply. err: the
-// sticky status word (timeout flag on a barrier run-out).
+// launching nothing, when an image takes one block (small images: the two launches are
+// faster), when the grid cannot be resident at once (many images) or w has no departure
+// counters; the caller then runs launch_gn_stats + launch_gn_apply. err: the sticky status
+// word (timeout flag on a barrier run-out).
 int launch_gn_fused(const GNApply& a, int N, int HW, int C, float eps, const GnScratch& w,
                     int32_t* err, cudaStream_t s, bool* launched);
 // GroupNorm backward. g = dy, masked by (relu_y > 0) when relu_y is given (the ReLU that
