@@ -537,26 +537,29 @@ __global__ void maxpool_bwd4_kernel(const float* __restrict__ dy, const uint8_t*
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per; i += gridDim.x * blockDim.x) {
     const int c4 = i % C4, pix = i / C4;
     const int ix = pix % W, iy = pix / W;
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    for (int ky = 0; ky < 3; ++ky) {
-      const int ty = iy + 1 - ky;
-      if (ty < 0 || (ty & 1)) continue;
-      const int oy = ty >> 1;
-      if (oy >= Ho) continue;
-      for (int kx = 0; kx < 3; ++kx) {
-        const int tx = ix + 1 - kx;
-        if (tx < 0 || (tx & 1)) continue;
-        const int ox = tx >> 1;
-        if (ox >= Wo) continue;
-        const size_t o = ob + ((size_t)oy * Wo + ox) * C + c4 * 4;
-        const uchar4 a4 = *reinterpret_cast<const uchar4*>(arg + o);
-        const float4 d4 = *reinterpret_cast<const float4*>(dy + o);
-        const int t = ky * 3 + kx;
-        if (a4.x == t) acc[0] += d4.x;
-        if (a4.y == t) acc[1] += d4.y;
-        if (a4.z == t) acc[2] += d4.z;
-        if (a4.w == t) acc[3] += d4.w;
+    // the (at most 2 x 2) windows covering this pixel: every load issued before any is used,
+    // then the contributions added in (ky, kx) order
+    uchar4 a4[9];
+    float4 d4[9];
+    bool cov[9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int ty = iy + 1 - t / 3, tx = ix + 1 - t % 3;
+      cov[t] = ty >= 0 && !(ty & 1) && (ty >> 1) < Ho && tx >= 0 && !(tx & 1) && (tx >> 1) < Wo;
+      if (cov[t]) {
+        const size_t o = ob + ((size_t)(ty >> 1) * Wo + (tx >> 1)) * C + c4 * 4;
+        a4[t] = *reinterpret_cast<const uchar4*>(arg + o);
+        d4[t] = *reinterpret_cast<const float4*>(dy + o);
       }
+    }
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      if (!cov[t]) continue;
+      if (a4[t].x == t) acc[0] += d4[t].x;
+      if (a4[t].y == t) acc[1] += d4[t].y;
+      if (a4[t].z == t) acc[2] += d4[t].z;
+      if (a4[t].w == t) acc[3] += d4[t].w;
     }
     *reinterpret_cast<float4*>(dx + (size_t)n * per * 4 + (size_t)i * 4) =
         make_float4(acc[0], acc[1], acc[2], acc[3]);
