@@ -620,25 +620,21 @@ __global__ void __launch_bounds__(kThreads) gn_relu_maxpool_kernel(GNApply a, in
       mu[v] = a.mean[(size_t)n * G + (c0 + v) / 2];
       rs[v] = a.rstd[(size_t)n * G + (c0 + v) / 2];
     }
-    // the 3x3 window: every in-image tap's load issued before any is used, then the taps
-    // compared in (ky, kx) order (the first strict maximum wins)
-    float x[9][4];
-    bool in[9];
-#pragma unroll
-    for (int t = 0; t < 9; ++t) {
-      const int iy = oy * 2 - 1 + t / 3, ix = ox * 2 - 1 + t % 3;
-      in[t] = iy >= 0 && iy < H && ix >= 0 && ix < W;
-      if (in[t]) ldv<4>(zi + ((size_t)iy * W + ix) * C + c0, x[t]);
-    }
     float best[4] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY};
     int bi[4] = {0, 0, 0, 0};
+    for (int ky = 0; ky < 3; ++ky) {
+      const int iy = oy * 2 - 1 + ky;
+      if (iy < 0 || iy >= H) continue;
+      for (int kx = 0; kx < 3; ++kx) {
+        const int ix = ox * 2 - 1 + kx;
+        if (ix < 0 || ix >= W) continue;
+        float x[4];
+        ldv<4>(zi + ((size_t)iy * W + ix) * C + c0, x);
 #pragma unroll
-    for (int t = 0; t < 9; ++t) {
-      if (!in[t]) continue;
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        const float y = fmaxf((x[t][v] - mu[v]) * rs[v] * gm[v] + bt[v], 0.f);
-        if (y > best[v]) { best[v] = y; bi[v] = t; }
+        for (int v = 0; v < 4; ++v) {
+          const float y = fmaxf((x[v] - mu[v]) * rs[v] * gm[v] + bt[v], 0.f);
+          if (y > best[v]) { best[v] = y; bi[v] = ky * 3 + kx; }
+        }
       }
     }
     const size_t o = (size_t)n * per * 4 + (size_t)i * 4;

@@ -217,16 +217,31 @@ int launch_im2col(const ConvGeom& g, const void* x, bool x_bf16, void* col, bool
   if (total == 0) return DDPPO_OK;
   if (!transposed && g.C == 1 && g.k == 7 && g.s == 2 && g.p == 3 && g.Kp == 56 &&
       ((uintptr_t)col & 15) == 0 && g.N <= 65535 && g.W <= 900) {
-    constexpr int RB = 4;
-    const dim3 gb((unsigned)((g.Ho + RB - 1) / RB), (unsigned)g.N);
-    const size_t smem = (size_t)((RB - 1) * 2 + 7) * (g.W + 6) * sizeof(float);
+    // 16 output rows per block where the staged input rows fit the default shared memory
+    // (fewer, longer blocks: the staging and its barrier are amortised), else 4
+    if (g.W <= 256) {
+      constexpr int RB = 16;
+      const dim3 gb((unsigned)((g.Ho + RB - 1) / RB), (unsigned)g.N);
+      const size_t smem = (size_t)((RB - 1) * 2 + 7) * (g.W + 6) * sizeof(float);
 #define STEM_CASE(TI, TO) \
-    im2col_stem_kernel<TI, TO, 7, 2, 3, RB><<<gb, 256, smem, s>>>(g, (const TI*)x, (TO*)col);
-    if (x_bf16 && op_bf16) { STEM_CASE(__nv_bfloat16, __nv_bfloat16) }
-    else if (x_bf16) { STEM_CASE(__nv_bfloat16, float) }
-    else if (op_bf16) { STEM_CASE(float, __nv_bfloat16) }
-    else { STEM_CASE(float, float) }
+      im2col_stem_kernel<TI, TO, 7, 2, 3, RB><<<gb, 256, smem, s>>>(g, (const TI*)x, (TO*)col);
+      if (x_bf16 && op_bf16) { STEM_CASE(__nv_bfloat16, __nv_bfloat16) }
+      else if (x_bf16) { STEM_CASE(__nv_bfloat16, float) }
+      else if (op_bf16) { STEM_CASE(float, __nv_bfloat16) }
+      else { STEM_CASE(float, float) }
 #undef STEM_CASE
+    } else {
+      constexpr int RB = 4;
+      const dim3 gb((unsigned)((g.Ho + RB - 1) / RB), (unsigned)g.N);
+      const size_t smem = (size_t)((RB - 1) * 2 + 7) * (g.W + 6) * sizeof(float);
+#define STEM_CASE(TI, TO) \
+      im2col_stem_kernel<TI, TO, 7, 2, 3, RB><<<gb, 256, smem, s>>>(g, (const TI*)x, (TO*)col);
+      if (x_bf16 && op_bf16) { STEM_CASE(__nv_bfloat16, __nv_bfloat16) }
+      else if (x_bf16) { STEM_CASE(__nv_bfloat16, float) }
+      else if (op_bf16) { STEM_CASE(float, __nv_bfloat16) }
+      else { STEM_CASE(float, float) }
+#undef STEM_CASE
+    }
     DDPPO_CHECK_LAUNCH();
     return DDPPO_OK;
   }
@@ -537,29 +552,33 @@ __global__ void maxpool_bwd4_kernel(const float* __restrict__ dy, const uint8_t*
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < per; i += gridDim.x * blockDim.x) {
     const int c4 = i % C4, pix = i / C4;
     const int ix = pix % W, iy = pix / W;
-    // the (at most 2 x 2) windows covering this pixel: every load issued before any is used,
-    // then the contributions added in (ky, kx) order
-    uchar4 a4[9];
-    float4 d4[9];
-    bool cov[9];
+    // the (at most 2 x 2) windows covering this pixel: filter row ky covers it when
+    // iy + 1 - ky is even and in range, i.e. ky = (iy + 1) & 1 and that + 2 (the same for
+    // kx); the four candidate loads are issued first, then added in (ky, kx) order
+    const int ky0 = (iy + 1) & 1, kx0 = (ix + 1) & 1;
+    uchar4 a4[4];
+    float4 d4[4];
+    bool cov[4];
 #pragma unroll
-    for (int t = 0; t < 9; ++t) {
-      const int ty = iy + 1 - t / 3, tx = ix + 1 - t % 3;
-      cov[t] = ty >= 0 && !(ty & 1) && (ty >> 1) < Ho && tx >= 0 && !(tx & 1) && (tx >> 1) < Wo;
-      if (cov[t]) {
+    for (int j = 0; j < 4; ++j) {
+      const int ky = ky0 + 2 * (j >> 1), kx = kx0 + 2 * (j & 1);
+      const int ty = iy + 1 - ky, tx = ix + 1 - kx;
+      cov[j] = ky <= 2 && kx <= 2 && ty >= 0 && (ty >> 1) < Ho && tx >= 0 && (tx >> 1) < Wo;
+      if (cov[j]) {
         const size_t o = ob + ((size_t)(ty >> 1) * Wo + (tx >> 1)) * C + c4 * 4;
-        a4[t] = *reinterpret_cast<const uchar4*>(arg + o);
-        d4[t] = *reinterpret_cast<const float4*>(dy + o);
+        a4[j] = *reinterpret_cast<const uchar4*>(arg + o);
+        d4[j] = *reinterpret_cast<const float4*>(dy + o);
       }
     }
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-    for (int t = 0; t < 9; ++t) {
-      if (!cov[t]) continue;
-      if (a4[t].x == t) acc[0] += d4[t].x;
-      if (a4[t].y == t) acc[1] += d4[t].y;
-      if (a4[t].z == t) acc[2] += d4[t].z;
-      if (a4[t].w == t) acc[3] += d4[t].w;
+    for (int j = 0; j < 4; ++j) {
+      if (!cov[j]) continue;
+      const int t = (ky0 + 2 * (j >> 1)) * 3 + kx0 + 2 * (j & 1);
+      if (a4[j].x == t) acc[0] += d4[j].x;
+      if (a4[j].y == t) acc[1] += d4[j].y;
+      if (a4[j].z == t) acc[2] += d4[j].z;
+      if (a4[j].w == t) acc[3] += d4[j].w;
     }
     *reinterpret_cast<float4*>(dx + (size_t)n * per * 4 + (size_t)i * 4) =
         make_float4(acc[0], acc[1], acc[2], acc[3]);
