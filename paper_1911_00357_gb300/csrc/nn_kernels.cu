@@ -217,31 +217,16 @@ int launch_im2col(const ConvGeom& g, const void* x, bool x_bf16, void* col, bool
   if (total == 0) return DDPPO_OK;
   if (!transposed && g.C == 1 && g.k == 7 && g.s == 2 && g.p == 3 && g.Kp == 56 &&
       ((uintptr_t)col & 15) == 0 && g.N <= 65535 && g.W <= 900) {
-    // 16 output rows per block where the staged input rows fit the default shared memory
-    // (fewer, longer blocks: the staging and its barrier are amortised), else 4
-    if (g.W <= 256) {
-      constexpr int RB = 16;
-      const dim3 gb((unsigned)((g.Ho + RB - 1) / RB), (unsigned)g.N);
-      const size_t smem = (size_t)((RB - 1) * 2 + 7) * (g.W + 6) * sizeof(float);
+    constexpr int RB = 4;  // 16 rows per block measured slower at the 64-image act batch
+    const dim3 gb((unsigned)((g.Ho + RB - 1) / RB), (unsigned)g.N);
+    const size_t smem = (size_t)((RB - 1) * 2 + 7) * (g.W + 6) * sizeof(float);
 #define STEM_CASE(TI, TO) \
-      im2col_stem_kernel<TI, TO, 7, 2, 3, RB><<<gb, 256, smem, s>>>(g, (const TI*)x, (TO*)col);
-      if (x_bf16 && op_bf16) { STEM_CASE(__nv_bfloat16, __nv_bfloat16) }
-      else if (x_bf16) { STEM_CASE(__nv_bfloat16, float) }
-      else if (op_bf16) { STEM_CASE(float, __nv_bfloat16) }
-      else { STEM_CASE(float, float) }
+    im2col_stem_kernel<TI, TO, 7, 2, 3, RB><<<gb, 256, smem, s>>>(g, (const TI*)x, (TO*)col);
+    if (x_bf16 && op_bf16) { STEM_CASE(__nv_bfloat16, __nv_bfloat16) }
+    else if (x_bf16) { STEM_CASE(__nv_bfloat16, float) }
+    else if (op_bf16) { STEM_CASE(float, __nv_bfloat16) }
+    else { STEM_CASE(float, float) }
 #undef STEM_CASE
-    } else {
-      constexpr int RB = 4;
-      const dim3 gb((unsigned)((g.Ho + RB - 1) / RB), (unsigned)g.N);
-      const size_t smem = (size_t)((RB - 1) * 2 + 7) * (g.W + 6) * sizeof(float);
-#define STEM_CASE(TI, TO) \
-      im2col_stem_kernel<TI, TO, 7, 2, 3, RB><<<gb, 256, smem, s>>>(g, (const TI*)x, (TO*)col);
-      if (x_bf16 && op_bf16) { STEM_CASE(__nv_bfloat16, __nv_bfloat16) }
-      else if (x_bf16) { STEM_CASE(__nv_bfloat16, float) }
-      else if (op_bf16) { STEM_CASE(float, __nv_bfloat16) }
-      else { STEM_CASE(float, float) }
-#undef STEM_CASE
-    }
     DDPPO_CHECK_LAUNCH();
     return DDPPO_OK;
   }
