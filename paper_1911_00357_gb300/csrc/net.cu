@@ -730,8 +730,8 @@ static int gn_bwd(Net& n, GNL& g, const float* dy, const float* z, int N, int HW
   b.dzop = n.dzop; b.op_bf16 = n.bf;
   b.dgamma_part = n.gnp_g; b.dbeta_part = n.gnp_b;
   DDPPO_TRY(launch_gn_bwd(b, N, HW, g.C, n.gnw, s));
-  DDPPO_TRY(launch_colsum(n.gnp_g, N, g.C, g.C, n.grad + g.g_off, !first, s));
-  DDPPO_TRY(launch_colsum(n.gnp_b, N, g.C, g.C, n.grad + g.b_off, !first, s));
+  DDPPO_TRY(launch_colsum2(n.gnp_g, n.gnp_b, N, g.C, g.C, n.grad + g.g_off, n.grad + g.b_off,
+                           !first, s));
   return DDPPO_OK;
 }
 
@@ -952,8 +952,8 @@ static int encoder_bwd(Net& n, const void* obs, int N, const float* dfeat_rows, 
     b.dzop = n.dzop; b.op_bf16 = n.bf;
     b.dgamma_part = n.gnp_g; b.dbeta_part = n.gnp_b;
     DDPPO_TRY(launch_gn_bwd(b, N, st.Ho * st.Wo, st.cout, n.gnw, s));
-    DDPPO_TRY(launch_colsum(n.gnp_g, N, st.cout, st.cout, n.grad + n.stem_n.g_off, !first, s));
-    DDPPO_TRY(launch_colsum(n.gnp_b, N, st.cout, st.cout, n.grad + n.stem_n.b_off, !first, s));
+    DDPPO_TRY(launch_colsum2(n.gnp_g, n.gnp_b, N, st.cout, st.cout, n.grad + n.stem_n.g_off,
+                             n.grad + n.stem_n.b_off, !first, s));
   } else {
     DDPPO_TRY(launch_maxpool_bwd(gcur, n.pool_arg, N, st.Ho, st.Wo, st.cout, gA, s));
     DDPPO_TRY(gn_bwd(n, n.stem_n, gA, st.z, N, st.Ho * st.Wo, first, s, n.stem_n.out));
@@ -1093,8 +1093,7 @@ static int lstm_backward(Net& n, int T, int E, const uint8_t* masks, const float
     wh.A = n.dgop; wh.lda = G4; wh.a_t = 1; wh.B = q.hm; wh.ldb = Hd; wh.b_t = 1;
     wh.C = n.grad + q.whh; wh.ldc = Hd;
     DDPPO_TRY(G(n, wh, s));
-    DDPPO_TRY(launch_colsum(n.dg32, N, G4, G4, n.grad + q.bih, false, s));
-    DDPPO_TRY(launch_colsum(n.dg32, N, G4, G4, n.grad + q.bhh, false, s));
+    DDPPO_TRY(launch_colsum2(n.dg32, n.dg32, N, G4, G4, n.grad + q.bih, n.grad + q.bhh, false, s));
     dabove = dX;
   }
   *dx0 = dabove;

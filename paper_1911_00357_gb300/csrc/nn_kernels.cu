@@ -587,25 +587,43 @@ int launch_maxpool_bwd(const float* dy, const uint8_t* arg, int N, int H, int W,
 
 // ---------------------------------------------------------------- column sums
 // block (32, 8): column c = blockIdx.x*32 + tx; row lanes ty; fixed-order combine.
-__global__ void colsum_kernel(const float* __restrict__ in, int R, int Cc, int ld,
-                              float* __restrict__ out, int accumulate) {
-  __shared__ float sh[8][33];
+// out[c] (+)= sum over rows r of in[r * ld + c]. Block (32, 32): column c = blockIdx.x * 32
+// + tx; row lane ty sums rows ty, ty + 32, ... (eight loads in flight); then a fixed-order
+// combine over the 32 lanes. Two arrays of the same shape in one launch (blockIdx.y).
+__global__ void __launch_bounds__(1024) colsum_kernel(const float* __restrict__ in0,
+                                                      const float* __restrict__ in1, int R,
+                                                      int Cc, int ld, float* __restrict__ out0,
+                                                      float* __restrict__ out1, int accumulate) {
+  __shared__ float sh[32][33];
+  const float* in = blockIdx.y ? in1 : in0;
+  float* out = blockIdx.y ? out1 : out0;
   const int c = blockIdx.x * 32 + threadIdx.x;
   float s = 0.f;
-  if (c < Cc)
-    for (int r = threadIdx.y; r < R; r += 8) s += in[(size_t)r * ld + c];
+  if (c < Cc) {
+#pragma unroll 8
+    for (int r = threadIdx.y; r < R; r += 32) s += in[(size_t)r * ld + c];
+  }
   sh[threadIdx.y][threadIdx.x] = s;
   __syncthreads();
   if (threadIdx.y == 0 && c < Cc) {
     float t = 0.f;
-    for (int k = 0; k < 8; ++k) t += sh[k][threadIdx.x];
+    for (int k = 0; k < 32; ++k) t += sh[k][threadIdx.x];
     out[c] = accumulate ? out[c] + t : t;
   }
 }
 int launch_colsum(const float* in, int R, int Cc, int ld, float* out, bool accumulate,
                   cudaStream_t s) {
   if (Cc == 0) return DDPPO_OK;
-  colsum_kernel<<<(Cc + 31) / 32, dim3(32, 8), 0, s>>>(in, R, Cc, ld, out, accumulate ? 1 : 0);
+  colsum_kernel<<<dim3((Cc + 31) / 32, 1), dim3(32, 32), 0, s>>>(in, in, R, Cc, ld, out, out,
+                                                                 accumulate ? 1 : 0);
+  DDPPO_CHECK_LAUNCH();
+  return DDPPO_OK;
+}
+int launch_colsum2(const float* in0, const float* in1, int R, int Cc, int ld, float* out0,
+                   float* out1, bool accumulate, cudaStream_t s) {
+  if (Cc == 0) return DDPPO_OK;
+  colsum_kernel<<<dim3((Cc + 31) / 32, 2), dim3(32, 32), 0, s>>>(in0, in1, R, Cc, ld, out0, out1,
+                                                                 accumulate ? 1 : 0);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }

@@ -130,6 +130,9 @@ int launch_maxpool_bwd(const float* dy, const uint8_t* arg, int N, int H, int W,
 // out[c] (+)= sum_r in[r * ld + c], fixed summation order
 int launch_colsum(const float* in, int R, int Cc, int ld, float* out, bool accumulate,
                   cudaStream_t s);
+// the column sums of two arrays of the same shape in one launch
+int launch_colsum2(const float* in0, const float* in1, int R, int Cc, int ld, float* out0,
+                   float* out1, bool accumulate, cudaStream_t s);
 
 // LSTM cell (gate order i, f, g, o). Step t of a [T, E] segment.
 struct LstmStep {
