@@ -348,7 +348,7 @@ __global__ void __launch_bounds__(kThreads) gn_bwd_reduce_kernel(GNBack b, int H
     rs[v] = b.rstd[(size_t)n * G + (c0 + v) / 2];
     sg[v] = sgx[v] = 0.f;
   }
-#pragma unroll 4
+#pragma unroll 8
   for (int p = pb + pr; p < pe; p += P) {
     const size_t o = ib + (size_t)p * C + c0;
     float d[V], x[V];

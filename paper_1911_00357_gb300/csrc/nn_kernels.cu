@@ -854,34 +854,43 @@ int launch_embed_fwd(int N, const float* goal, const int32_t* prev_a, const floa
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
-// thread per output weight: gWg[j, i] (96), gbg[j] (32), gEmb[a, j] (160); fixed n order
-__global__ void embed_bwd_kernel(int N, const float* __restrict__ goal,
-                                 const int32_t* __restrict__ prev_a, const float* __restrict__ dx,
-                                 int lddx, int col0, float* gWg, float* gbg, float* gEmb) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+// warp per output weight: gWg[j, i] (96), gbg[j] (32), gEmb[a, j] (160). Lane l sums rows
+// l, l + 32, ... (eight loads in flight); a fixed xor tree combines the lanes.
+__global__ void __launch_bounds__(256) embed_bwd_kernel(int N, const float* __restrict__ goal,
+                                                        const int32_t* __restrict__ prev_a,
+                                                        const float* __restrict__ dx, int lddx,
+                                                        int col0, float* gWg, float* gbg,
+                                                        float* gEmb) {
+  const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (t >= 96 + 32 + 160) return;
   float s = 0.f;
   if (t < 96) {
     const int j = t / 3, i = t % 3;
-    for (int n = 0; n < N; ++n) s += dx[(size_t)n * lddx + col0 + j] * goal[3 * n + i];
-    gWg[t] = s;
+#pragma unroll 8
+    for (int n = lane; n < N; n += 32) s += dx[(size_t)n * lddx + col0 + j] * goal[3 * n + i];
   } else if (t < 128) {
     const int j = t - 96;
-    for (int n = 0; n < N; ++n) s += dx[(size_t)n * lddx + col0 + j];
-    gbg[j] = s;
+#pragma unroll 8
+    for (int n = lane; n < N; n += 32) s += dx[(size_t)n * lddx + col0 + j];
   } else {
     const int a = (t - 128) / 32, j = (t - 128) % 32;
-    for (int n = 0; n < N; ++n) {
+#pragma unroll 8
+    for (int n = lane; n < N; n += 32) {
       int pa = prev_a[n];
       pa = pa < 0 ? 0 : (pa > 4 ? 4 : pa);
       if (pa == a) s += dx[(size_t)n * lddx + col0 + 32 + j];
     }
-    gEmb[a * 32 + j] = s;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane != 0) return;
+  if (t < 96) gWg[t] = s;
+  else if (t < 128) gbg[t - 96] = s;
+  else gEmb[t - 128] = s;
 }
 int launch_embed_bwd(int N, const float* goal, const int32_t* prev_a, const float* dx, int lddx,
                      int col0, float* gWg, float* gbg, float* gEmb, float*, size_t, cudaStream_t s) {
-  embed_bwd_kernel<<<nblk(288, 64), 64, 0, s>>>(N, goal, prev_a, dx, lddx, col0, gWg, gbg, gEmb);
+  embed_bwd_kernel<<<(288 + 7) / 8, 256, 0, s>>>(N, goal, prev_a, dx, lddx, col0, gWg, gbg, gEmb);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
