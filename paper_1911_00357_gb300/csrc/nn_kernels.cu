@@ -800,6 +800,7 @@ __global__ void heads_wgrad_final(int H, int nch, const float* __restrict__ part
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= 5 * H) return;
   float s = 0.f;
+#pragma unroll 8
   for (int c = 0; c < nch; ++c) s += part[(size_t)c * 5 * H + idx];
   const int q = idx / H, k = idx % H;
   if (q < 4) gWa[q * H + k] = s;
