@@ -328,6 +328,67 @@ __global__ void __launch_bounds__(kThreads) gn_fused_kernel(GNApply a, int HW, i
   if (a.out_f8) block_amax(f8m, a.f8_amax);
 }
 
+// ---- one block per image: statistics and normalisation without any grid barrier ----
+// The block sums the whole image (the statistics kernel's S = 1 arithmetic), combines in
+// shared memory, and normalises the image it just read (an L2 hit). An ordinary launch:
+// nothing waits on another block, so it needs no co-residency.
+__device__ __forceinline__ void combine_groups_one(const float* p, const float* __restrict__ zi,
+                                                   int C, int HW, float eps, float* mean,
+                                                   float* rstd) {
+  const int G = C / 2;
+  const double inv = 1.0 / HW;
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    double m[2], M2[2];
+    for (int j = 0; j < 2; ++j) {
+      const int c = 2 * g + j;
+      const double a = 0.0 + (double)p[c * 2], b = 0.0 + (double)p[c * 2 + 1];
+      m[j] = (double)zi[c] + a * inv;
+      M2[j] = b - a * a * inv;
+    }
+    const double dm = m[0] - m[1];
+    double var = (M2[0] + M2[1] + 0.5 * HW * dm * dm) / (2.0 * HW);
+    if (var < 0.0) var = 0.0;
+    mean[g] = (float)(0.5 * (m[0] + m[1]));
+    rstd[g] = 1.0f / sqrtf((float)var + eps);
+  }
+}
+
+template <int V>
+__global__ void __launch_bounds__(kThreads) gn_image_kernel(GNApply a, int HW, int C, float eps) {
+  extern __shared__ float sh[];
+  const int n = blockIdx.x, G = C / 2;
+  const size_t ib = (size_t)n * HW * C;
+  float* pz = sh + (int)blockDim.x * 2 * V;  // [C][2] partial sums of z, then of zd
+  float* pd = pz + 2 * C;
+  float* st = pd + 2 * C;                    // [4][G]: mean, rstd, mean_d, rstd_d
+  block_shifted_sums<V>(a.z + ib, 0, HW, C, sh, pz);
+  if (a.zd) {
+    __syncthreads();
+    block_shifted_sums<V>(a.zd + ib, 0, HW, C, sh, pd);
+  }
+  __syncthreads();
+  combine_groups_one(pz, a.z + ib, C, HW, eps, st, st + G);
+  if (a.zd) combine_groups_one(pd, a.zd + ib, C, HW, eps, st + 2 * G, st + 3 * G);
+  __syncthreads();
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    const_cast<float*>(a.mean)[(size_t)n * G + g] = st[g];
+    const_cast<float*>(a.rstd)[(size_t)n * G + g] = st[G + g];
+    if (a.zd) {
+      const_cast<float*>(a.mean_d)[(size_t)n * G + g] = st[2 * G + g];
+      const_cast<float*>(a.rstd_d)[(size_t)n * G + g] = st[3 * G + g];
+    }
+  }
+  const int R = C / V, P = blockDim.x / R;
+  const int cv = threadIdx.x % R, pr = threadIdx.x / R, c0 = cv * V;
+  const float f8s = a.out_f8 ? *a.f8_scale : 1.f;
+  float f8m = 0.f;
+#pragma unroll 4
+  for (int p = pr; p < HW; p += P)
+    f8m = fmaxf(f8m, apply_vec<V>(a, ib + (size_t)p * C + c0, c0, st + c0 / 2, st + G + c0 / 2,
+                                  st + 2 * G + c0 / 2, st + 3 * G + c0 / 2, f8s));
+  if (a.out_f8) block_amax(f8m, a.f8_amax);
+}
+
 // ---- backward reductions: g = dy (masked by relu_y > 0), xhat = (z - mu) rstd;
 //      per image and channel sum(g) and sum(g xhat); group means of gamma-weighted sums ----
 template <int V>
@@ -543,10 +604,19 @@ int launch_gn_fused(const GNApply& a, int N, int HW, int C, float eps, const GnS
   void (*kern)(GNApply, int, int, int, float, float*, float*, int*, int*, int32_t*) =
       V == 4 ? gn_fused_kernel<4> : gn_fused_kernel<2>;
   const int nt = a.zd ? 2 : 1;
-  // one block per image: the statistics launch needs no barrier and the normalise launch
-  // spreads each image over many blocks, which measured faster than one launch whose
-  // single block per image also normalises it
-  if (gn_split(N, HW, C, w) == 1) return DDPPO_OK;
+  if (gn_split(N, HW, C, w) == 1) {
+    // one block per image. With many images (at least 4 per SM: the update's minibatches)
+    // one launch, whose blocks normalise the image they just summed (re-read from L2);
+    // with few (the 64-image act batch) the statistics launch then a normalise launch that
+    // spreads each image over many blocks, which measured faster there
+    if (N < 4 * num_sms_cached()) return DDPPO_OK;
+    const size_t smem = ((size_t)th * 2 * V + 6 * (size_t)C) * sizeof(float);
+    if (V == 4) gn_image_kernel<4><<<N, th, smem, s>>>(a, HW, C, eps);
+    else gn_image_kernel<2><<<N, th, smem, s>>>(a, HW, C, eps);
+    DDPPO_CHECK_LAUNCH();
+    *launched = true;
+    return DDPPO_OK;
+  }
   // every block resident at once, and the partials of z (and zd) in the scratch;
   // otherwise two launches
   const int S = gn_split_one_launch(N, HW, C, w);
