@@ -507,7 +507,9 @@ int ddppo_group_norm(int32_t N, int32_t HW, int32_t C, const float* z, const flo
                      const float* beta, const float* resid, int32_t relu, float* out, float* mean,
                      float* rstd, void* stream);
 /* How the encoder's forward GroupNorms run. An image of at most 32K elements is summed by
- * one block, then normalised by a second launch that spreads it over many blocks. A larger
+ * one block: with at least 4 images per SM the same block then normalises it (one launch,
+ * the image re-read from L2); with fewer, a second launch normalises it, spread over many
+ * blocks. A larger
  * image is split over S blocks: with on = 1 (the default) the statistics and the
  * normalisation run in one cooperative launch wherever every block fits on the GPU at once
  * (the image's blocks meet at a bounded per-image barrier, then normalise the rows they
