@@ -501,6 +501,93 @@ __global__ void __launch_bounds__(kThreads) gn_bwd_apply_kernel(GNBack b, int HW
   }
 }
 
+// ---- backward, one block per image: the reduction (the reduce kernel's S = 1 arithmetic),
+//      the group means in shared memory, then the input gradient of the image just read ----
+template <int V>
+__global__ void __launch_bounds__(kThreads) gn_bwd_image_kernel(GNBack b, int HW, int C) {
+  extern __shared__ float sh[];
+  const int R = C / V, P = blockDim.x / R, G = C / 2;
+  const int n = blockIdx.x;
+  const int cv = threadIdx.x % R, pr = threadIdx.x / R, c0 = cv * V;
+  const size_t ib = (size_t)n * HW * C;
+  float* part = sh + blockDim.x * 2 * V;  // [C][2]: sum g, sum g xhat
+  float* m12 = part + 2 * C;              // [2][G]: m1, m2
+  float mu[V], rs[V], sg[V], sgx[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    mu[v] = b.mean[(size_t)n * G + (c0 + v) / 2];
+    rs[v] = b.rstd[(size_t)n * G + (c0 + v) / 2];
+    sg[v] = sgx[v] = 0.f;
+  }
+#pragma unroll 8
+  for (int p = pr; p < HW; p += P) {
+    const size_t o = ib + (size_t)p * C + c0;
+    float d[V], x[V];
+    ldv<V>(b.z + o, x);
+    ldv<V>(b.dy + o, d);
+    if (b.relu_from_z) {
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        if (!((x[v] - mu[v]) * rs[v] * b.gamma[c0 + v] + b.beta[c0 + v] > 0.f)) d[v] = 0.f;
+    }
+    if (b.relu_y) {
+      float y[V];
+      ldv<V>(b.relu_y + o, y);
+#pragma unroll
+      for (int v = 0; v < V; ++v) d[v] = y[v] > 0.f ? d[v] : 0.f;
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      sg[v] += d[v];
+      sgx[v] += d[v] * ((x[v] - mu[v]) * rs[v]);
+    }
+  }
+  block_pair_sums<V>(sg, sgx, sh, C, part);
+  __syncthreads();
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    b.dbeta_part[(size_t)n * C + c] = 0.f + part[2 * c];
+    b.dgamma_part[(size_t)n * C + c] = 0.f + part[2 * c + 1];
+  }
+  const float inv = 1.0f / (float)(2 * HW);
+  for (int g = threadIdx.x; g < G; g += blockDim.x) {
+    const float g0 = b.gamma[2 * g], g1 = b.gamma[2 * g + 1];
+    const float t0 = 0.f + part[4 * g], t1 = 0.f + part[4 * g + 1];
+    const float t2 = 0.f + part[4 * g + 2], t3 = 0.f + part[4 * g + 3];
+    m12[g] = (t0 * g0 + t2 * g1) * inv;
+    m12[G + g] = (t1 * g0 + t3 * g1) * inv;
+  }
+  __syncthreads();
+  float gm[V];
+  ldv<V>(b.gamma + c0, gm);
+#pragma unroll 4
+  for (int p = pr; p < HW; p += P) {
+    const size_t o = ib + (size_t)p * C + c0;
+    float d[V], x[V], r[V];
+    ldv<V>(b.z + o, x);
+    ldv<V>(b.dy + o, d);
+    if (b.relu_from_z) {
+#pragma unroll
+      for (int v = 0; v < V; ++v)
+        if (!((x[v] - mu[v]) * rs[v] * gm[v] + b.beta[c0 + v] > 0.f)) d[v] = 0.f;
+    }
+    if (b.relu_y) {
+      float y[V];
+      ldv<V>(b.relu_y + o, y);
+#pragma unroll
+      for (int v = 0; v < V; ++v) d[v] = y[v] > 0.f ? d[v] : 0.f;
+      if (b.g_out) stv<V>(b.g_out + o, d);
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int g = (c0 + v) / 2;
+      const float xh = (x[v] - mu[v]) * rs[v];
+      r[v] = rs[v] * (d[v] * gm[v] - m12[g] - xh * m12[G + g]);
+    }
+    if (b.dz32) stv<V>(b.dz32 + o, r);
+    if (b.dzop) stv_op<V>(b.dzop, o, r, b.op_bf16);
+  }
+}
+
 int num_sms_cached() {
   static int sms = 0;
   if (!sms) {
@@ -657,6 +744,14 @@ int launch_gn_bwd(const GNBack& b, int N, int HW, int C, const GnScratch& w, cud
   const int V = C % 4 == 0 ? 4 : 2;
   const int S = gn_split(N, HW, C, w);
   const int th = threads_for(C, V);
+  if (S == 1 && N >= 4 * num_sms_cached()) {
+    // many small images: one block per image, reduction and input gradient in one launch
+    const size_t smem1 = ((size_t)th * 2 * V + 3 * (size_t)C) * sizeof(float);
+    if (V == 4) gn_bwd_image_kernel<4><<<N, th, smem1, s>>>(b, HW, C);
+    else gn_bwd_image_kernel<2><<<N, th, smem1, s>>>(b, HW, C);
+    DDPPO_CHECK_LAUNCH();
+    return DDPPO_OK;
+  }
   const size_t smem = std::max((size_t)th * 2 * V, (size_t)(S + 1) * C * 2) * sizeof(float);
   const dim3 grid(S, N);
   if (V == 4) gn_bwd_reduce_kernel<4><<<grid, th, smem, s>>>(b, HW, C, S, w.part, w.cnt);
