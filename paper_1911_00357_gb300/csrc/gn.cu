@@ -604,8 +604,9 @@ bool gn_shape_ok(int C) { return C >= 2 && C % 2 == 0 && C / (C % 4 == 0 ? 4 : 2
 // blocks per image: enough for ~8 blocks per SM overall, at least one pixel pass each
 int gn_split(int N, int HW, int C, const GnScratch& w) {
   // images of at most 32K elements (128 KB): one block each -- a block sums such an image
-  // faster than S blocks combine their partials (measured: the 64-image act batch)
-  if ((long)HW * C <= 32768) return 1;
+  // faster than S blocks combine their partials (measured: the 64-image act batch); and any
+  // image size once there are at least 4 images per SM (one block each already fills the GPU)
+  if ((long)HW * C <= 32768 || N >= 4 * num_sms_cached()) return 1;
   const int V = C % 4 == 0 ? 4 : 2;
   const int P = rows_per_pass(C, V);
   const int want = (8 * num_sms_cached() + N - 1) / N;
