@@ -50,8 +50,6 @@ __global__ void __launch_bounds__(SM_WARPS * 32)
     for (int j = 0; j < 4; ++j)
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
-  // unrolled so that several K steps' fragment loads are in flight before their MMAs
-#pragma unroll 4
   for (int ks = kb; ks < ke; ++ks) {
     const int k0 = ks * 16 + 2 * t;
     uint32_t a[MT][4], b[4][2];
