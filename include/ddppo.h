@@ -560,19 +560,31 @@ int ddppo_gemm_backend(int32_t M, int32_t N, int32_t K, int32_t op_bf16, const v
 int ddppo_update_graph(ddppo_ctx* ctx, int32_t on);
 
 /* The LSTM recurrence (App. "Agent Design"; Sec. 4 "Training": BPTT over the rollout).
- * mode 2 (the default): in the BF16 forms the forward of each layer runs all T steps in
+ * mode 2: in the BF16 forms the forward of each layer runs all T steps in
  * one launch on the tensor cores (tcgen05, M = 128 gate rows per CTA, the CTA's rows of
  * W_hh resident in shared memory, the cell update fused into the TMEM epilogue, one
  * bounded grid barrier per step) wherever the shape allows (H a multiple of 64, at most
  * 128 envs per segment, 64 when H = 512); the backward, the FP32 form and other shapes
- * run step by step. mode 0: a recurrent contraction and a cell kernel per step, forward
- * and backward. mode 1: forward and backward as one cooperative launch per layer on the
+ * run step by step. mode 0 (the default): a recurrent contraction and a cell kernel per
+ * step, forward and backward. mode 1: forward and backward as one cooperative launch per layer on the
  * CUDA cores (recurrent weights in registers; at most 64 envs per segment); slower than
  * mode 0 at the default sizes (its per-step contraction is bound by shared-memory loads).
  * All modes compute the same arithmetic; only the recurrent contraction's fp32 summation
  * order differs. Applies to launches enqueued afterwards (a captured graph keeps the mode
  * it was captured with). E_ARG for another mode. Host only. */
 int ddppo_lstm_whole_segment(ddppo_ctx* ctx, int32_t mode);
+
+/* Launch overlap (process-wide; not a method step): every kernel of the library is
+ * launched with programmatic dependent launch, so its blocks become resident and run their
+ * prologue (barrier set-up, tensor-memory allocation) while the previous kernel in the
+ * stream finishes; each kernel waits for that kernel's completion before it reads or
+ * writes global memory, so results are bit-identical either way. on = 0 launches with
+ * plain stream order. The initial state is on unless the environment variable
+ * DDPPO_LAUNCH_OVERLAP is "0". Applies to launches enqueued afterwards; a graph captured
+ * earlier (collect, update) keeps the form it was captured with. Host only. */
+int ddppo_set_launch_overlap(int32_t on);
+/* on [host]: the current state (1 on, 0 off). */
+int ddppo_launch_overlap(int32_t* on);
 
 /* Tile-shape autotuner of the tensor-core GEMM (precision 1): on by default. The first
  * time a contraction shape is seen outside a stream capture, each candidate (N tile 64 or

@@ -128,6 +128,8 @@ _SIGS = {
     "ddppo_lstm_whole_segment": [P, I32],
     "ddppo_group_norm_one_launch": [P, I32],
     "ddppo_update_graph": [P, I32],
+    "ddppo_set_launch_overlap": [I32],
+    "ddppo_launch_overlap": [P],
     "ddppo_autotune_export": [P, P, ctypes.c_size_t, P],
     "ddppo_autotune_import": [P, P, ctypes.c_size_t],
     "ddppo_conv2d": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, F32, P, P],
@@ -427,9 +429,19 @@ def ddppo_update_graph(h, on: bool = True) -> None:
 
 
 def ddppo_lstm_whole_segment(h, mode: int = 1) -> None:
-    """LSTM recurrence mode: 0 step by step, 1 whole segment on CUDA cores, 2 tcgen05
-    forward (the default); a bool selects 1 (True) or 0 (False)."""
+    """LSTM recurrence mode: 0 step by step (the default), 1 whole segment on CUDA cores,
+    2 tcgen05 forward; a bool selects 1 (True) or 0 (False)."""
     _check(lib().ddppo_lstm_whole_segment(h, int(mode)))
+
+
+def ddppo_set_launch_overlap(on: bool = True) -> None:
+    _check(lib().ddppo_set_launch_overlap(1 if on else 0))
+
+
+def ddppo_launch_overlap() -> bool:
+    v = ctypes.c_int32()
+    _check(lib().ddppo_launch_overlap(ctypes.byref(v)))
+    return bool(v.value)
 
 
 def ddppo_group_norm_one_launch(h, on: bool = True) -> None:

@@ -7,6 +7,9 @@
 #include <mutex>
 #include <string>
 
+#include <atomic>
+#include <cstdlib>
+
 #include "net.cuh"
 
 namespace ddppo {
@@ -34,6 +37,34 @@ using namespace ddppo;
   } while (0)
 
 extern "C" const char* ddppo_last_error(void) { return g_last_error.c_str(); }
+
+namespace ddppo {
+// launch overlap (programmatic dependent launch): on unless DDPPO_LAUNCH_OVERLAP=0
+static std::atomic<int> g_pdl{-1};
+bool pdl_enabled() {
+  int v = g_pdl.load(std::memory_order_relaxed);
+  if (v < 0) {
+    const char* e = getenv("DDPPO_LAUNCH_OVERLAP");
+    v = (e && e[0] == '0') ? 0 : 1;
+    g_pdl.store(v, std::memory_order_relaxed);
+  }
+  return v != 0;
+}
+}  // namespace ddppo
+
+extern "C" int ddppo_set_launch_overlap(int32_t on) {
+  ddppo::g_pdl.store(on ? 1 : 0, std::memory_order_relaxed);
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_launch_overlap(int32_t* on) {
+  if (!on) {
+    ddppo::set_error("launch_overlap: null argument");
+    return DDPPO_E_ARG;
+  }
+  *on = ddppo::pdl_enabled() ? 1 : 0;
+  return DDPPO_OK;
+}
 
 static bool pow2_multiple(int a, int b) {
   if (a <= 0 || b < a || b % a) return false;

@@ -29,6 +29,40 @@ void set_error(const std::string& msg);
     if (_rc != DDPPO_OK) return _rc; \
   } while (0)
 
+// ---- programmatic dependent launch ----
+// Every kernel of the library is launched through launch_k with the programmatic
+// stream-serialization attribute: its blocks may become resident while the previous kernel
+// in the stream is still running, which hides the launch gap and the block prologue.
+// DDPPO_PDL_ENTRY() therefore comes before a kernel's first global-memory access (read or
+// write): griddepcontrol.wait returns once the previous kernel has completed and its
+// writes are visible (a no-op without a programmatic predecessor). The launch_dependents
+// after it lets the next kernel's blocks become resident; since a block triggers only after
+// its own wait has returned, at most one kernel waits ahead of the running one, and
+// kernels that allocate tensor memory do so before the trigger, so a waiting kernel never
+// holds columns a running one still needs.
+#define DDPPO_PDL_ENTRY() \
+  asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory")
+
+// process-wide switch (ddppo_set_launch_overlap); graphs captured before a change keep the
+// form they were captured with
+bool pdl_enabled();
+
+template <typename... P, typename... A>
+inline void launch_k(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     A&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  (void)cudaLaunchKernelEx(&cfg, kern, static_cast<A&&>(args)...);  // checked by the caller
+}
+
 // sticky device error word: bit flags
 enum : int32_t { ERRF_BOUNDS = 1, ERRF_TIMEOUT = 2, ERRF_RESET = 4 };
 enum : int { TASK_POINTGOAL = 0, TASK_FLEE = 1, TASK_EXPLORE = 2 };

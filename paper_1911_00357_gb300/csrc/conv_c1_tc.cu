@@ -67,6 +67,8 @@ __global__ void __launch_bounds__(CC_THREADS, 5) conv_c1_tc_kernel(ConvC1 a) {
                  "r"(TCOLS));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  __syncthreads();    // the allocation is done before any thread of the block triggers
+  DDPPO_PDL_ENTRY();
   // resident weights: row co = w[co, 0 .. k^2), zero up to 64 taps
   for (int i = threadIdx.x; i < COUT * 8; i += CC_THREADS) {
     const int co = i >> 3, c = i & 7;
@@ -218,7 +220,7 @@ int launch_conv_c1_tc(const ConvC1& a, int num_sms, cudaStream_t s) {
   const int regs = std::max(1, ((fa.numRegs + 7) / 8) * 8) * CC_THREADS;  // per CTA
   const int occ = std::max(1, std::min({8, (int)(232448 / (smem + 1024)), 512 / tcols, 65536 / regs}));
   const long long grid = std::min<long long>(ntiles, (long long)num_sms * occ);
-  kern<<<(unsigned)grid, CC_THREADS, smem, s>>>(a);
+  ::ddppo::launch_k(kern, (unsigned)grid, CC_THREADS, smem, s, a);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }

@@ -21,6 +21,7 @@ __device__ __forceinline__ float ld_any(const void* x, size_t i) {
 template <bool BF>
 __global__ void __launch_bounds__(kQThreads) amax_kernel(const void* __restrict__ x, size_t n,
                                                          unsigned* __restrict__ amax) {
+  DDPPO_PDL_ENTRY();
   __shared__ float wmax[kQThreads / 32];
   float m = 0.f;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -42,6 +43,7 @@ __global__ void __launch_bounds__(kQThreads) quant_kernel(const void* __restrict
                                                           const unsigned* __restrict__ amax,
                                                           float* __restrict__ scale,
                                                           uint8_t* __restrict__ q) {
+  DDPPO_PDL_ENTRY();
   const float a = __uint_as_float(*amax);
   const float sc = a > 0.f ? a / kE4M3Max : 1.f;
   if (blockIdx.x == 0 && threadIdx.x == 0) *scale = sc;
@@ -51,6 +53,7 @@ __global__ void __launch_bounds__(kQThreads) quant_kernel(const void* __restrict
 }
 
 __global__ void f8_scale_update_kernel(float* __restrict__ scale, unsigned* __restrict__ amax, int n) {
+  DDPPO_PDL_ENTRY();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const float a = __uint_as_float(amax[i]);
@@ -67,23 +70,23 @@ unsigned qgrid(size_t n) {
 
 int launch_amax(const void* x, bool x_bf16, size_t n, unsigned* amax, cudaStream_t s) {
   if (!n) return DDPPO_OK;
-  if (x_bf16) amax_kernel<true><<<qgrid(n), kQThreads, 0, s>>>(x, n, amax);
-  else amax_kernel<false><<<qgrid(n), kQThreads, 0, s>>>(x, n, amax);
+  if (x_bf16) ::ddppo::launch_k(amax_kernel<true>, qgrid(n), kQThreads, 0, s, x, n, amax);
+  else ::ddppo::launch_k(amax_kernel<false>, qgrid(n), kQThreads, 0, s, x, n, amax);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
 
 int launch_quant_e4m3(const void* x, bool x_bf16, size_t n, const unsigned* amax, float* scale,
                       uint8_t* q, cudaStream_t s) {
-  if (x_bf16) quant_kernel<true><<<qgrid(n), kQThreads, 0, s>>>(x, n, amax, scale, q);
-  else quant_kernel<false><<<qgrid(n), kQThreads, 0, s>>>(x, n, amax, scale, q);
+  if (x_bf16) ::ddppo::launch_k(quant_kernel<true>, qgrid(n), kQThreads, 0, s, x, n, amax, scale, q);
+  else ::ddppo::launch_k(quant_kernel<false>, qgrid(n), kQThreads, 0, s, x, n, amax, scale, q);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
 
 int launch_f8_scale_update(float* scale, unsigned* amax, int n, cudaStream_t s) {
   if (n <= 0) return DDPPO_OK;
-  f8_scale_update_kernel<<<(n + 127) / 128, 128, 0, s>>>(scale, amax, n);
+  ::ddppo::launch_k(f8_scale_update_kernel, (n + 127) / 128, 128, 0, s, scale, amax, n);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }

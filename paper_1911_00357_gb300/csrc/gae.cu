@@ -15,6 +15,7 @@ __global__ void __launch_bounds__(1024) gae_kernel(const float* __restrict__ r,
                                                    const float* __restrict__ v, int T, int E,
                                                    float gamma, float lam, float* __restrict__ adv,
                                                    float* __restrict__ ret) {
+  DDPPO_PDL_ENTRY();
   extern __shared__ float sh[];
   float* sdelta = sh;           // [T][32]
   float* sc = sh + T * 32;      // [T][32]
@@ -80,7 +81,7 @@ int launch_gae(const float* r, const uint8_t* d, const float* v, int T, int E, f
     DDPPO_CHECK_CUDA(cudaFuncSetAttribute(gae_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)smem));
   if (E == 0 || T == 0) return DDPPO_OK;
-  gae_kernel<<<(E + 31) / 32, 1024, smem, s>>>(r, d, v, T, E, gamma, lam, adv, ret);
+  ::ddppo::launch_k(gae_kernel, (E + 31) / 32, 1024, smem, s, r, d, v, T, E, gamma, lam, adv, ret);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }

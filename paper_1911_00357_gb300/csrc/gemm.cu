@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(int M, int N, int K, con
                                                         int relu, int kchunk,
                                                         float* __restrict__ partial, int a_t,
                                                         int b_t) {
+  DDPPO_PDL_ENTRY();
   __shared__ float As[SB_K][SB_M + 4];
   __shared__ float Bs[SB_K][SB_N + 4];
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
@@ -83,6 +84,7 @@ __global__ void __launch_bounds__(256) gemm_simt_kernel(int M, int N, int K, con
 __global__ void splitk_reduce_kernel(int M, int N, int splits, const float* __restrict__ partial,
                                      float* __restrict__ C, int ldc, int c_bf16, float beta,
                                      const float* __restrict__ bias, int relu) {
+  DDPPO_PDL_ENTRY();
   const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (size_t)M * N) return;
   const int m = (int)(idx / N), n = (int)(idx % N);
@@ -114,11 +116,11 @@ static int gemm_simt(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, c
   float* partial = splits > 1 ? ws.partial : nullptr;
   dim3 grid(gm, gn, splits);
   if (op_bf16)
-    gemm_simt_kernel<__nv_bfloat16><<<grid, 256, 0, s>>>(
+    ::ddppo::launch_k(gemm_simt_kernel<__nv_bfloat16>, grid, 256, 0, s,
         d.M, d.N, d.K, (const __nv_bfloat16*)d.A, d.lda, (const __nv_bfloat16*)d.B, d.ldb,
         (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu, kchunk, partial, d.a_t, d.b_t);
   else
-    gemm_simt_kernel<float><<<grid, 256, 0, s>>>(d.M, d.N, d.K, (const float*)d.A, d.lda,
+    ::ddppo::launch_k(gemm_simt_kernel<float>, grid, 256, 0, s, d.M, d.N, d.K, (const float*)d.A, d.lda,
                                                  (const float*)d.B, d.ldb, (float*)d.C, d.ldc,
                                                  d.c_bf16, d.beta, d.bias, d.relu, kchunk, partial,
                                                  d.a_t, d.b_t);
@@ -132,7 +134,7 @@ static int gemm_simt(const GemmDesc& d, bool op_bf16, const GemmWorkspace& ws, c
 int launch_splitk_reduce(int M, int N, int splits, const float* partial, float* C, int ldc,
                          int c_bf16, float beta, const float* bias, int relu, cudaStream_t s) {
   const size_t n = (size_t)M * N;
-  splitk_reduce_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(M, N, splits, partial, C, ldc,
+  ::ddppo::launch_k(splitk_reduce_kernel, (unsigned)((n + 255) / 256), 256, 0, s, M, N, splits, partial, C, ldc,
                                                                    c_bf16, beta, bias, relu);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;

@@ -35,6 +35,7 @@ __global__ void __launch_bounds__(SM_WARPS * 32)
     gemm_small_kernel(int M, int N, int K, const __nv_bfloat16* __restrict__ A, int lda,
                       const __nv_bfloat16* __restrict__ B, int ldb, float* __restrict__ C, int ldc,
                       int c_bf16, float beta, const float* __restrict__ bias, int relu) {
+  DDPPO_PDL_ENTRY();
   extern __shared__ float red[];  // [SM_WARPS][16 MT][SM_NB]
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, t = lane & 3;
@@ -113,7 +114,7 @@ int launch_small(const GemmDesc& d, cudaStream_t s) {
     attr_done[dev] = true;
   }
   const unsigned grid = (unsigned)((d.N + SM_NB - 1) / SM_NB);
-  gemm_small_kernel<MT><<<grid, SM_WARPS * 32, smem, s>>>(
+  ::ddppo::launch_k(gemm_small_kernel<MT>, grid, SM_WARPS * 32, smem, s,
       d.M, d.N, d.K, (const __nv_bfloat16*)d.A, d.lda, (const __nv_bfloat16*)d.B, d.ldb,
       (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu);
   DDPPO_CHECK_LAUNCH();

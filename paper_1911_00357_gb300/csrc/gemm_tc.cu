@@ -230,6 +230,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  DDPPO_PDL_ENTRY();  // after the barrier set-up and the tensor-memory allocation
   const uint32_t tmem = ctl.tmem_base;
 
   if (warp == 0 && halo) {
@@ -952,7 +953,7 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
   const int stages = cfg.stages;
   const int ntiles = gm * gn * splits;
   const int grid = min(ntiles, ws.num_sms * per_sm);
-  gemm_tc_kernel<BN><<<grid, TC_PTHREADS, smem, s>>>(
+  ::ddppo::launch_k(gemm_tc_kernel<BN>, grid, TC_PTHREADS, smem, s,
       ma, mb, M, N, K, kchunk, (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu, trans,
       partial, ws.err, a_mn, b_mn, stages, gm, gn, splits, ca, d.fp8, d.scale_a, d.scale_b);
   DDPPO_CHECK_LAUNCH();
@@ -1187,6 +1188,7 @@ __global__ void __launch_bounds__(WH_THREADS, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  DDPPO_PDL_ENTRY();  // after the barrier set-up and the tensor-memory allocation
   const uint32_t tmem = tmem_base;
   const int kq = RB * Wp / 16;
   const bool has_work = (int)blockIdx.x < nunits;
@@ -1281,6 +1283,7 @@ __global__ void __launch_bounds__(WH_THREADS, 1)
 // dw[co, (ky*3 + kx)*32 + c] = beta dw + sum over CTAs (in order) of part[cta][ky][kx][c][co]
 __global__ void wgrad_halo_reduce_kernel(const float* __restrict__ part, int nctas, float* __restrict__ dw,
                                          int ldw, float beta) {
+  DDPPO_PDL_ENTRY();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= 32 * 288) return;
   const int co = i / 288, kk = i - co * 288;
@@ -1404,11 +1407,11 @@ int conv_wgrad_halo(const ConvShape& c, const void* x, const void* dz, float* dw
                                           (int)TC_SMEM_MAX));
     attr_done[dev] = true;
   }
-  wgrad_halo_kernel<<<grid, WH_THREADS, g.smem, s>>>(mx, md, Wp, RB, nrb, nunits, g.x_bytes,
+  ::ddppo::launch_k(wgrad_halo_kernel, grid, WH_THREADS, g.smem, s, mx, md, Wp, RB, nrb, nunits, g.x_bytes,
                                                      g.dz_bytes, g.x_stride, g.dz_stride, g.stages,
                                                      ws.partial, ws.err);
   DDPPO_CHECK_LAUNCH();
-  wgrad_halo_reduce_kernel<<<(32 * 288 + 255) / 256, 256, 0, s>>>(ws.partial, grid, dw, ldw, beta);
+  ::ddppo::launch_k(wgrad_halo_reduce_kernel, (32 * 288 + 255) / 256, 256, 0, s, ws.partial, grid, dw, ldw, beta);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }

@@ -174,6 +174,7 @@ __global__ void __launch_bounds__(kThreads) gn_stats_kernel(const float* __restr
                                                             int S, float eps, float* __restrict__ part,
                                                             int* __restrict__ cnt, float* __restrict__ mean,
                                                             float* __restrict__ rstd) {
+  DDPPO_PDL_ENTRY();
   extern __shared__ float sh[];
   __shared__ int flag;
   const int n = blockIdx.y, sb = blockIdx.x;
@@ -231,6 +232,7 @@ __device__ __forceinline__ float apply_vec(const GNApply& a, size_t o, int c0, c
 
 template <int V>
 __global__ void __launch_bounds__(kThreads) gn_apply_kernel(GNApply a, int HW, int C) {
+  DDPPO_PDL_ENTRY();
   const int R = C / V, G = C / 2;
   const int n = blockIdx.y;
   const int per = HW * R;
@@ -289,6 +291,7 @@ __global__ void __launch_bounds__(kThreads) gn_fused_kernel(GNApply a, int HW, i
                                                             float* __restrict__ part,
                                                             float* __restrict__ part_d, int* arrive,
                                                             int* depart, int32_t* err) {
+  DDPPO_PDL_ENTRY();
   extern __shared__ float sh[];
   __shared__ int s_ok;
   const int n = blockIdx.y, sb = blockIdx.x, G = C / 2;
@@ -355,6 +358,7 @@ __device__ __forceinline__ void combine_groups_one(const float* p, const float* 
 
 template <int V>
 __global__ void __launch_bounds__(kThreads) gn_image_kernel(GNApply a, int HW, int C, float eps) {
+  DDPPO_PDL_ENTRY();
   extern __shared__ float sh[];
   const int n = blockIdx.x, G = C / 2;
   const size_t ib = (size_t)n * HW * C;
@@ -395,6 +399,7 @@ template <int V>
 __global__ void __launch_bounds__(kThreads) gn_bwd_reduce_kernel(GNBack b, int HW, int C, int S,
                                                                  float* __restrict__ part,
                                                                  int* __restrict__ cnt) {
+  DDPPO_PDL_ENTRY();
   extern __shared__ float sh[];
   __shared__ int flag;
   const int R = C / V, P = blockDim.x / R, G = C / 2;
@@ -464,6 +469,7 @@ __global__ void __launch_bounds__(kThreads) gn_bwd_reduce_kernel(GNBack b, int H
 // ---- dz = rstd (g gamma - m1 - xhat m2); optionally g itself (the masked gradient) ----
 template <int V>
 __global__ void __launch_bounds__(kThreads) gn_bwd_apply_kernel(GNBack b, int HW, int C) {
+  DDPPO_PDL_ENTRY();
   const int R = C / V, G = C / 2;
   const int n = blockIdx.y;
   const int per = HW * R;
@@ -505,6 +511,7 @@ __global__ void __launch_bounds__(kThreads) gn_bwd_apply_kernel(GNBack b, int HW
 //      the group means in shared memory, then the input gradient of the image just read ----
 template <int V>
 __global__ void __launch_bounds__(kThreads) gn_bwd_image_kernel(GNBack b, int HW, int C) {
+  DDPPO_PDL_ENTRY();
   extern __shared__ float sh[];
   const int R = C / V, P = blockDim.x / R, G = C / 2;
   const int n = blockIdx.x;
@@ -676,8 +683,8 @@ int launch_gn_stats(const float* z, int N, int HW, int C, float eps, float* mean
   const int th = threads_for(C, V);
   const size_t smem = std::max((size_t)th * 2 * V, (size_t)S * C * 2) * sizeof(float);
   const dim3 grid(S, N);
-  if (V == 4) gn_stats_kernel<4><<<grid, th, smem, s>>>(z, HW, C, S, eps, w.part, w.cnt, mean, rstd);
-  else gn_stats_kernel<2><<<grid, th, smem, s>>>(z, HW, C, S, eps, w.part, w.cnt, mean, rstd);
+  if (V == 4) ::ddppo::launch_k(gn_stats_kernel<4>, grid, th, smem, s, z, HW, C, S, eps, w.part, w.cnt, mean, rstd);
+  else ::ddppo::launch_k(gn_stats_kernel<2>, grid, th, smem, s, z, HW, C, S, eps, w.part, w.cnt, mean, rstd);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -699,8 +706,8 @@ int launch_gn_fused(const GNApply& a, int N, int HW, int C, float eps, const GnS
     // spreads each image over many blocks, which measured faster there
     if (N < 4 * num_sms_cached()) return DDPPO_OK;
     const size_t smem = ((size_t)th * 2 * V + 6 * (size_t)C) * sizeof(float);
-    if (V == 4) gn_image_kernel<4><<<N, th, smem, s>>>(a, HW, C, eps);
-    else gn_image_kernel<2><<<N, th, smem, s>>>(a, HW, C, eps);
+    if (V == 4) ::ddppo::launch_k(gn_image_kernel<4>, N, th, smem, s, a, HW, C, eps);
+    else ::ddppo::launch_k(gn_image_kernel<2>, N, th, smem, s, a, HW, C, eps);
     DDPPO_CHECK_LAUNCH();
     *launched = true;
     return DDPPO_OK;
@@ -730,8 +737,8 @@ int launch_gn_apply(const GNApply& a, int N, int HW, int C, cudaStream_t s) {
   if (!gn_shape_ok(C) || N > 65535) { set_error("gn: unsupported shape"); return DDPPO_E_CONFIG; }
   const int V = C % 4 == 0 ? 4 : 2;
   const dim3 grid(apply_blocks(N, HW, C, V), N);
-  if (V == 4) gn_apply_kernel<4><<<grid, kThreads, 0, s>>>(a, HW, C);
-  else gn_apply_kernel<2><<<grid, kThreads, 0, s>>>(a, HW, C);
+  if (V == 4) ::ddppo::launch_k(gn_apply_kernel<4>, grid, kThreads, 0, s, a, HW, C);
+  else ::ddppo::launch_k(gn_apply_kernel<2>, grid, kThreads, 0, s, a, HW, C);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -748,19 +755,19 @@ int launch_gn_bwd(const GNBack& b, int N, int HW, int C, const GnScratch& w, cud
   if (S == 1 && N >= 4 * num_sms_cached()) {
     // many small images: one block per image, reduction and input gradient in one launch
     const size_t smem1 = ((size_t)th * 2 * V + 3 * (size_t)C) * sizeof(float);
-    if (V == 4) gn_bwd_image_kernel<4><<<N, th, smem1, s>>>(b, HW, C);
-    else gn_bwd_image_kernel<2><<<N, th, smem1, s>>>(b, HW, C);
+    if (V == 4) ::ddppo::launch_k(gn_bwd_image_kernel<4>, N, th, smem1, s, b, HW, C);
+    else ::ddppo::launch_k(gn_bwd_image_kernel<2>, N, th, smem1, s, b, HW, C);
     DDPPO_CHECK_LAUNCH();
     return DDPPO_OK;
   }
   const size_t smem = std::max((size_t)th * 2 * V, (size_t)(S + 1) * C * 2) * sizeof(float);
   const dim3 grid(S, N);
-  if (V == 4) gn_bwd_reduce_kernel<4><<<grid, th, smem, s>>>(b, HW, C, S, w.part, w.cnt);
-  else gn_bwd_reduce_kernel<2><<<grid, th, smem, s>>>(b, HW, C, S, w.part, w.cnt);
+  if (V == 4) ::ddppo::launch_k(gn_bwd_reduce_kernel<4>, grid, th, smem, s, b, HW, C, S, w.part, w.cnt);
+  else ::ddppo::launch_k(gn_bwd_reduce_kernel<2>, grid, th, smem, s, b, HW, C, S, w.part, w.cnt);
   DDPPO_CHECK_LAUNCH();
   const dim3 ga(apply_blocks(N, HW, C, V), N);
-  if (V == 4) gn_bwd_apply_kernel<4><<<ga, kThreads, 0, s>>>(b, HW, C);
-  else gn_bwd_apply_kernel<2><<<ga, kThreads, 0, s>>>(b, HW, C);
+  if (V == 4) ::ddppo::launch_k(gn_bwd_apply_kernel<4>, ga, kThreads, 0, s, b, HW, C);
+  else ::ddppo::launch_k(gn_bwd_apply_kernel<2>, ga, kThreads, 0, s, b, HW, C);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -770,6 +777,7 @@ __global__ void __launch_bounds__(kThreads) gn_relu_maxpool_kernel(GNApply a, in
                                                                    float* __restrict__ pool,
                                                                    __nv_bfloat16* __restrict__ pool_bf,
                                                                    uint8_t* __restrict__ arg) {
+  DDPPO_PDL_ENTRY();
   const int Hq = (H - 1) / 2 + 1, Wq = (W - 1) / 2 + 1, C4 = C / 4, G = C / 2;
   const int n = blockIdx.y, per = Hq * Wq * C4;
   const float* zi = a.z + (size_t)n * H * W * C;
@@ -828,7 +836,7 @@ int launch_gn_relu_maxpool(const GNApply& a, int N, int H, int W, int C, float* 
   const dim3 gb((unsigned)std::max<long>(1, std::min<long>((per + kThreads - 1) / kThreads,
                                                            (8l * num_sms_cached() + N - 1) / N)),
                 N);
-  gn_relu_maxpool_kernel<<<gb, kThreads, 0, s>>>(a, H, W, C, pool, pool_bf, arg);
+  ::ddppo::launch_k(gn_relu_maxpool_kernel, gb, kThreads, 0, s, a, H, W, C, pool, pool_bf, arg);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }

@@ -124,6 +124,7 @@ __device__ bool grid_barrier(unsigned* bar, unsigned round, int32_t* err, int* s
 
 // rows of a CTA: r = q * U + uu (gate q, unit u0 + uu) -> W_hh row q * H + u0 + uu
 __global__ void __launch_bounds__(LS_THREADS, 1) lstm_seq_fwd_kernel(LstmSeq a) {
+  DDPPO_PDL_ENTRY();
   extern __shared__ float sh[];
   __shared__ int s_ok;
   const int H = a.H, U = H / gridDim.x, R4 = 4 * U, u0 = blockIdx.x * U;
@@ -206,6 +207,7 @@ __global__ void __launch_bounds__(LS_THREADS, 1) lstm_seq_fwd_kernel(LstmSeq a) 
 // columns of a CTA: its units u0 .. u0 + U - 1 of W_hh [4H, H]; thread (uu, jc) holds
 // W_hh[j][u0 + uu] for j = jj * JC + jc
 __global__ void __launch_bounds__(LS_THREADS, 1) lstm_seq_bwd_kernel(LstmSeq a) {
+  DDPPO_PDL_ENTRY();
   extern __shared__ float sh[];
   __shared__ int s_ok;
   const int H = a.H, U = H / gridDim.x, u0 = blockIdx.x * U, G4 = 4 * H;

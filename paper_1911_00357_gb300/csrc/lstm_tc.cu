@@ -100,6 +100,8 @@ __global__ void __launch_bounds__(LT_THREADS, 1) lstm_tc_fwd_kernel(LstmTc a) {
                  "r"((uint32_t)NP));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
+  __syncthreads();    // the allocation is done before any thread of the block triggers
+  DDPPO_PDL_ENTRY();
   // resident A: row r = 4 uu + q  <-  W_hh row q H + u0 + uu (eight 16-byte loads in flight
   // per thread)
   for (int i0 = threadIdx.x; i0 < 128 * (H / 8); i0 += LT_THREADS * 8) {

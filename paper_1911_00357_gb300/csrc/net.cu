@@ -1200,6 +1200,7 @@ int net_backward(Net& n, const float* dlogits, const float* dvalues, cudaStream_
 // major: f = c * HW + p, the order vis.w's columns use); inside they are NHWC rows.
 __global__ void feat_layout_kernel(const float* __restrict__ in, float* __restrict__ out, int N,
                                    int HW, int C, int to_cmajor) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)N * HW * C;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -1216,7 +1217,7 @@ static int feat_layout(const Net& n, const float* in, float* out, int N, bool to
   const size_t total = (size_t)N * n.F;
   if (!total) return DDPPO_OK;
   const int blocks = (int)std::min<size_t>((total + 255) / 256, 4096);
-  feat_layout_kernel<<<blocks, 256, 0, s>>>(in, out, N, n.featHW, n.featC, to_cmajor ? 1 : 0);
+  ::ddppo::launch_k(feat_layout_kernel, blocks, 256, 0, s, in, out, N, n.featHW, n.featC, to_cmajor ? 1 : 0);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }

@@ -182,6 +182,7 @@ extern "C" int ddppo_ppo_loss(int32_t n, const float* logits, const float* value
 }
 
 __global__ void set_steps_kernel(int64_t* d, int64_t update_index, int64_t adam_t) {
+  DDPPO_PDL_ENTRY();
   d[0] = update_index;
   d[1] = adam_t;
 }
@@ -236,6 +237,7 @@ static int update_body(ddppo_ctx* x, const ddppo_rollout* ro, const ddppo_ppo_hp
 // ---- the update one minibatch at a time (gradients exchanged between workers, Eq. 4) ----
 __global__ void scale_copy_kernel(const float* __restrict__ g, float scale, float* __restrict__ out,
                                   size_t n) {
+  DDPPO_PDL_ENTRY();
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (size_t)gridDim.x * blockDim.x)
     out[i] = scale * g[i];
@@ -258,7 +260,7 @@ extern "C" int ddppo_ppo_grad(ddppo_ctx* x, const ddppo_rollout* ro, const ddppo
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int E = c.num_envs, Emb = n.Emb, L = n.L, Hd = n.H, T = T_valid;
-  set_steps_kernel<<<1, 1, 0, s>>>(n.d_steps, hp->update_index, n.adam_t);
+  ::ddppo::launch_k(set_steps_kernel, 1, 1, 0, s, n.d_steps, hp->update_index, n.adam_t);
   DDPPO_CHECK_LAUNCH();
   const float* adv = ro->adv;
   if (hp->norm_adv) {
@@ -296,12 +298,12 @@ extern "C" int ddppo_apply_grad(ddppo_ctx* x, const float* grad, float scale,
   Net& n = *x->net;
   cudaStream_t s = (cudaStream_t)stream;
   const size_t P = (size_t)n.P;
-  scale_copy_kernel<<<(unsigned)std::min<size_t>((P + 255) / 256, 4096), 256, 0, s>>>(grad, scale,
+  ::ddppo::launch_k(scale_copy_kernel, (unsigned)std::min<size_t>((P + 255) / 256, 4096), 256, 0, s, grad, scale,
                                                                                      n.grad, P);
   DDPPO_CHECK_LAUNCH();
   DDPPO_TRY(launch_grad_norm(n.grad, P, n.norm, n.scratch, n.scratch_elems, s));
   if (stats) DDPPO_TRY(launch_copy_scalar(stats + 6, n.norm, s));
-  set_steps_kernel<<<1, 1, 0, s>>>(n.d_steps, hp->update_index, n.adam_t);
+  ::ddppo::launch_k(set_steps_kernel, 1, 1, 0, s, n.d_steps, hp->update_index, n.adam_t);
   DDPPO_CHECK_LAUNCH();
   DDPPO_TRY(launch_adam(n.params, n.grad, n.adam_m, n.adam_v, P,
                         hp->max_grad_norm > 0.f ? n.norm : nullptr, hp->max_grad_norm, hp->lr,
@@ -316,6 +318,7 @@ struct MeanArgs {
   const float* p[kMeanMax];
 };
 __global__ void grad_mean_kernel(MeanArgs a, int nb, size_t len, float* __restrict__ out) {
+  DDPPO_PDL_ENTRY();
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < len;
        i += (size_t)gridDim.x * blockDim.x) {
     float acc = 0.f;
@@ -333,8 +336,7 @@ extern "C" int ddppo_grad_mean(int32_t n, const float* const* bufs, int64_t len,
     ARG(bufs[r] != nullptr, "grad_mean: null buffer");
     a.p[r] = bufs[r];
   }
-  grad_mean_kernel<<<(unsigned)std::min<int64_t>((len + 255) / 256, 4096), 256, 0,
-                     (cudaStream_t)stream>>>(a, n, (size_t)len, out);
+  ::ddppo::launch_k(grad_mean_kernel, (unsigned)std::min<int64_t>((len + 255) / 256, 4096), 256, 0, (cudaStream_t)stream, a, n, (size_t)len, out);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -361,7 +363,7 @@ extern "C" int ddppo_ppo_update(ddppo_ctx* x, const ddppo_rollout* ro, const ddp
   cudaStream_t s = (cudaStream_t)stream;
   // this update's index and the Adam steps taken so far, as device scalars (kernel
   // arguments: valid inside a caller's capture too)
-  set_steps_kernel<<<1, 1, 0, s>>>(n.d_steps, hp->update_index, n.adam_t);
+  ::ddppo::launch_k(set_steps_kernel, 1, 1, 0, s, n.d_steps, hp->update_index, n.adam_t);
   DDPPO_CHECK_LAUNCH();
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   DDPPO_CHECK_CUDA(cudaStreamIsCapturing(s, &cs));
@@ -431,12 +433,14 @@ extern "C" int ddppo_ppo_update(ddppo_ctx* x, const ddppo_rollout* ro, const ddp
 // ---- collection ----
 __global__ void post_step_kernel(int E, const int32_t* __restrict__ a, const uint8_t* __restrict__ d,
                                  int32_t* __restrict__ prev_a, uint8_t* __restrict__ masks) {
+  DDPPO_PDL_ENTRY();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   prev_a[e] = d[e] ? 4 : a[e];
   masks[e] = d[e] ? 0 : 1;
 }
 __global__ void start_slot_kernel(int E, int32_t* prev_a, uint8_t* masks) {
+  DDPPO_PDL_ENTRY();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= E) return;
   prev_a[e] = 4;
@@ -470,7 +474,7 @@ static int collect_body(ddppo_ctx* x, const ddppo_rollout* ro, cudaStream_t s) {
     const size_t o1 = (size_t)(t + 1) * E;
     DDPPO_TRY(ddppo_env_step(x, ro->actions + o, (char*)ro->obs + o1 * ob, ro->goal + o1 * 3,
                              ro->rewards + o, ro->dones + o, ro->info ? ro->info + o * 4 : nullptr, s));
-    post_step_kernel<<<(E + 127) / 128, 128, 0, s>>>(E, ro->actions + o, ro->dones + o,
+    ::ddppo::launch_k(post_step_kernel, (E + 127) / 128, 128, 0, s, E, ro->actions + o, ro->dones + o,
                                                      ro->prev_a + o1, ro->masks + o1);
     DDPPO_CHECK_LAUNCH();
     if (t + 1 < T) DDPPO_TRY(fork_prefetch());
@@ -487,7 +491,7 @@ static int collect_prologue(ddppo_ctx* x, const ddppo_rollout* ro, cudaStream_t 
   const size_t st_bytes = (size_t)L * E * Hd * 4;
   if (!n.collect_started || !x->env_ready) {
     DDPPO_TRY(ddppo_env_reset(x, ro->obs, ro->goal, s));
-    start_slot_kernel<<<(E + 127) / 128, 128, 0, s>>>(E, ro->prev_a, ro->masks);
+    ::ddppo::launch_k(start_slot_kernel, (E + 127) / 128, 128, 0, s, E, ro->prev_a, ro->masks);
     DDPPO_CHECK_LAUNCH();
     DDPPO_CHECK_CUDA(cudaMemsetAsync(ro->h, 0, st_bytes, s));
     DDPPO_CHECK_CUDA(cudaMemsetAsync(ro->c, 0, st_bytes, s));
@@ -559,7 +563,7 @@ extern "C" int ddppo_collect_step(ddppo_ctx* x, const ddppo_rollout* ro, int32_t
   DDPPO_CHECK_CUDA(cudaStreamWaitEvent(s, x->ev_join, 0));
   DDPPO_TRY(ddppo_env_step(x, ro->actions + o, (char*)ro->obs + o1 * ob, ro->goal + o1 * 3,
                            ro->rewards + o, ro->dones + o, ro->info ? ro->info + o * 4 : nullptr, s));
-  post_step_kernel<<<(E + 127) / 128, 128, 0, s>>>(E, ro->actions + o, ro->dones + o,
+  ::ddppo::launch_k(post_step_kernel, (E + 127) / 128, 128, 0, s, E, ro->actions + o, ro->dones + o,
                                                    ro->prev_a + o1, ro->masks + o1);
   DDPPO_CHECK_LAUNCH();
   n.step_next = t + 1;

@@ -31,6 +31,7 @@ __device__ __forceinline__ float ld_any(const void* p, size_t i, bool bf) {
 // ---------------------------------------------------------------- im2col / col2im
 template <typename Ti, typename To>
 __global__ void im2col_kernel(ConvGeom g, const Ti* __restrict__ x, To* __restrict__ col) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)g.N * g.Ho * g.Wo * g.Kp;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -51,6 +52,7 @@ __global__ void im2col_kernel(ConvGeom g, const Ti* __restrict__ x, To* __restri
 // colT[kk, m]
 template <typename Ti, typename To>
 __global__ void im2colT_kernel(ConvGeom g, const Ti* __restrict__ x, To* __restrict__ colT) {
+  DDPPO_PDL_ENTRY();
   const size_t M = (size_t)g.N * g.Ho * g.Wo;
   const size_t total = M * g.Kp;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -82,6 +84,7 @@ static unsigned grid_for(size_t total) {
 // consecutive threads touch consecutive bytes.
 template <typename Ti, typename To>
 __global__ void im2col_vec_kernel(ConvGeom g, const Ti* __restrict__ x, To* __restrict__ col) {
+  DDPPO_PDL_ENTRY();
   const int C8 = g.C >> 3, taps = g.k * g.k;
   const size_t total = (size_t)g.N * g.Ho * g.Wo * taps * C8;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -128,6 +131,7 @@ __global__ void im2col_vec_kernel(ConvGeom g, const Ti* __restrict__ x, To* __re
 // threads write adjacent rows, so a warp writes one contiguous stretch of the col matrix.
 template <typename Ti, typename To>
 __global__ void im2col_c1_kernel(ConvGeom g, const Ti* __restrict__ x, To* __restrict__ col) {
+  DDPPO_PDL_ENTRY();
   const int nck = g.Kp / 8;                     // 8-tap chunks per row
   const int per_img = g.Ho * g.Wo * nck;        // chunks of one image
   const int n = blockIdx.y;
@@ -171,6 +175,7 @@ __global__ void im2col_c1_kernel(ConvGeom g, const Ti* __restrict__ x, To* __res
 template <typename Ti, typename To, int KS, int S, int P, int RB>
 __global__ void __launch_bounds__(256) im2col_stem_kernel(ConvGeom g, const Ti* __restrict__ x,
                                                           To* __restrict__ col) {
+  DDPPO_PDL_ENTRY();
   constexpr int KK = KS * KS, KP = (KK + 7) / 8 * 8, NCK = KP / 8, ROWS = (RB - 1) * S + KS;
   extern __shared__ float tile[];  // [ROWS][W + 2P]
   const int n = blockIdx.y, oy0 = blockIdx.x * RB;
@@ -221,7 +226,7 @@ int launch_im2col(const ConvGeom& g, const void* x, bool x_bf16, void* col, bool
     const dim3 gb((unsigned)((g.Ho + RB - 1) / RB), (unsigned)g.N);
     const size_t smem = (size_t)((RB - 1) * 2 + 7) * (g.W + 6) * sizeof(float);
 #define STEM_CASE(TI, TO) \
-    im2col_stem_kernel<TI, TO, 7, 2, 3, RB><<<gb, 256, smem, s>>>(g, (const TI*)x, (TO*)col);
+    ::ddppo::launch_k(im2col_stem_kernel<TI, TO, 7, 2, 3, RB>, gb, 256, smem, s, g, (const TI*)x, (TO*)col);
     if (x_bf16 && op_bf16) { STEM_CASE(__nv_bfloat16, __nv_bfloat16) }
     else if (x_bf16) { STEM_CASE(__nv_bfloat16, float) }
     else if (op_bf16) { STEM_CASE(float, __nv_bfloat16) }
@@ -236,13 +241,13 @@ int launch_im2col(const ConvGeom& g, const void* x, bool x_bf16, void* col, bool
     const dim3 gb((unsigned)std::max<long>(1, std::min<long>((per + 255) / 256,
                                                              (8l * 152 + g.N - 1) / g.N)), g.N);
     if (x_bf16 && op_bf16)
-      im2col_c1_kernel<__nv_bfloat16, __nv_bfloat16><<<gb, 256, 0, s>>>(g, (const __nv_bfloat16*)x, (__nv_bfloat16*)col);
+      ::ddppo::launch_k(im2col_c1_kernel<__nv_bfloat16, __nv_bfloat16>, gb, 256, 0, s, g, (const __nv_bfloat16*)x, (__nv_bfloat16*)col);
     else if (x_bf16)
-      im2col_c1_kernel<__nv_bfloat16, float><<<gb, 256, 0, s>>>(g, (const __nv_bfloat16*)x, (float*)col);
+      ::ddppo::launch_k(im2col_c1_kernel<__nv_bfloat16, float>, gb, 256, 0, s, g, (const __nv_bfloat16*)x, (float*)col);
     else if (op_bf16)
-      im2col_c1_kernel<float, __nv_bfloat16><<<gb, 256, 0, s>>>(g, (const float*)x, (__nv_bfloat16*)col);
+      ::ddppo::launch_k(im2col_c1_kernel<float, __nv_bfloat16>, gb, 256, 0, s, g, (const float*)x, (__nv_bfloat16*)col);
     else
-      im2col_c1_kernel<float, float><<<gb, 256, 0, s>>>(g, (const float*)x, (float*)col);
+      ::ddppo::launch_k(im2col_c1_kernel<float, float>, gb, 256, 0, s, g, (const float*)x, (float*)col);
     DDPPO_CHECK_LAUNCH();
     return DDPPO_OK;
   }
@@ -250,9 +255,9 @@ int launch_im2col(const ConvGeom& g, const void* x, bool x_bf16, void* col, bool
                    ((uintptr_t)x & 15) == 0 && ((uintptr_t)col & 15) == 0;
   const unsigned gb = grid_for(vec ? total / 8 : total);
 #define IM2COL_CASE(TI, TO)                                                                   \
-  if (vec) im2col_vec_kernel<TI, TO><<<gb, 256, 0, s>>>(g, (const TI*)x, (TO*)col);           \
-  else if (transposed) im2colT_kernel<TI, TO><<<gb, 256, 0, s>>>(g, (const TI*)x, (TO*)col);  \
-  else im2col_kernel<TI, TO><<<gb, 256, 0, s>>>(g, (const TI*)x, (TO*)col);
+  if (vec) ::ddppo::launch_k(im2col_vec_kernel<TI, TO>, gb, 256, 0, s, g, (const TI*)x, (TO*)col);           \
+  else if (transposed) ::ddppo::launch_k(im2colT_kernel<TI, TO>, gb, 256, 0, s, g, (const TI*)x, (TO*)col);  \
+  else ::ddppo::launch_k(im2col_kernel<TI, TO>, gb, 256, 0, s, g, (const TI*)x, (TO*)col);
   if (x_bf16 && op_bf16) { IM2COL_CASE(__nv_bfloat16, __nv_bfloat16) }
   else if (x_bf16) { IM2COL_CASE(__nv_bfloat16, float) }
   else if (op_bf16) { IM2COL_CASE(float, __nv_bfloat16) }
@@ -264,6 +269,7 @@ int launch_im2col(const ConvGeom& g, const void* x, bool x_bf16, void* col, bool
 
 __global__ void col2im_kernel(ConvGeom g, const float* __restrict__ dcol, float* __restrict__ dx,
                               int accumulate) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)g.N * g.H * g.W * g.C;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -292,6 +298,7 @@ __global__ void col2im_kernel(ConvGeom g, const float* __restrict__ dcol, float*
 // vectorised col2im for C % 8 == 0: one thread per (pixel, 8-channel group)
 __global__ void col2im_vec_kernel(ConvGeom g, const float* __restrict__ dcol, float* __restrict__ dx,
                                   int accumulate) {
+  DDPPO_PDL_ENTRY();
   const int C8 = g.C >> 3;
   const size_t total = (size_t)g.N * g.H * g.W * C8;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -332,9 +339,9 @@ int launch_col2im(const ConvGeom& g, const float* dcol, float* dx, bool accumula
   const size_t total = (size_t)g.N * g.H * g.W * g.C;
   if (total == 0) return DDPPO_OK;
   if (g.C % 8 == 0 && g.Kp % 4 == 0 && ((uintptr_t)dcol & 15) == 0 && ((uintptr_t)dx & 15) == 0)
-    col2im_vec_kernel<<<grid_for(total / 8), 256, 0, s>>>(g, dcol, dx, accumulate ? 1 : 0);
+    ::ddppo::launch_k(col2im_vec_kernel, grid_for(total / 8), 256, 0, s, g, dcol, dx, accumulate ? 1 : 0);
   else
-    col2im_kernel<<<grid_for(total), 256, 0, s>>>(g, dcol, dx, accumulate ? 1 : 0);
+    ::ddppo::launch_k(col2im_kernel, grid_for(total), 256, 0, s, g, dcol, dx, accumulate ? 1 : 0);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -343,6 +350,7 @@ int launch_col2im(const ConvGeom& g, const float* dcol, float* dx, bool accumula
 template <typename Ti, typename To>
 __global__ void transpose_kernel(const Ti* __restrict__ in, To* __restrict__ out, int R, int Cc,
                                  int ld_in) {
+  DDPPO_PDL_ENTRY();
   __shared__ float tile[32][33];
   const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;  // rows on x: R can be in the millions
   for (int j = threadIdx.y; j < 32; j += blockDim.y) {
@@ -361,24 +369,25 @@ int launch_transpose(const void* in, bool in_bf16, void* out, bool out_bf16, int
   if (R == 0 || Cc == 0) return DDPPO_OK;
   dim3 grid((R + 31) / 32, (Cc + 31) / 32), blk(32, 8);
   if (in_bf16 && out_bf16)
-    transpose_kernel<__nv_bfloat16, __nv_bfloat16><<<grid, blk, 0, s>>>((const __nv_bfloat16*)in, (__nv_bfloat16*)out, R, Cc, ld_in);
+    ::ddppo::launch_k(transpose_kernel<__nv_bfloat16, __nv_bfloat16>, grid, blk, 0, s, (const __nv_bfloat16*)in, (__nv_bfloat16*)out, R, Cc, ld_in);
   else if (in_bf16)
-    transpose_kernel<__nv_bfloat16, float><<<grid, blk, 0, s>>>((const __nv_bfloat16*)in, (float*)out, R, Cc, ld_in);
+    ::ddppo::launch_k(transpose_kernel<__nv_bfloat16, float>, grid, blk, 0, s, (const __nv_bfloat16*)in, (float*)out, R, Cc, ld_in);
   else if (out_bf16)
-    transpose_kernel<float, __nv_bfloat16><<<grid, blk, 0, s>>>((const float*)in, (__nv_bfloat16*)out, R, Cc, ld_in);
+    ::ddppo::launch_k(transpose_kernel<float, __nv_bfloat16>, grid, blk, 0, s, (const float*)in, (__nv_bfloat16*)out, R, Cc, ld_in);
   else
-    transpose_kernel<float, float><<<grid, blk, 0, s>>>((const float*)in, (float*)out, R, Cc, ld_in);
+    ::ddppo::launch_k(transpose_kernel<float, float>, grid, blk, 0, s, (const float*)in, (float*)out, R, Cc, ld_in);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
 
 __global__ void cast_kernel(const float* __restrict__ in, void* out, int bf, size_t n) {
+  DDPPO_PDL_ENTRY();
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     st_op(out, i, in[i], bf);
 }
 int launch_cast(const float* in, void* out, bool out_bf16, size_t n, cudaStream_t s) {
   if (!n) return DDPPO_OK;
-  cast_kernel<<<grid_for(n), 256, 0, s>>>(in, out, out_bf16 ? 1 : 0, n);
+  ::ddppo::launch_k(cast_kernel, grid_for(n), 256, 0, s, in, out, out_bf16 ? 1 : 0, n);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -399,6 +408,7 @@ __device__ __forceinline__ float warp_sum(float v) {
 // ---------------------------------------------------------------- ReLU backward, add
 __global__ void relu_bwd_kernel(const float* dy, const float* __restrict__ y, size_t n, float* dz32,
                                 void* dzop, int bf) {
+  DDPPO_PDL_ENTRY();
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const float v = y[i] > 0.f ? dy[i] : 0.f;
     if (dz32) dz32[i] = v;
@@ -408,17 +418,18 @@ __global__ void relu_bwd_kernel(const float* dy, const float* __restrict__ y, si
 int launch_relu_bwd(const float* dy, const float* y, size_t n, float* dz32, void* dzop, bool op_bf16,
                     cudaStream_t s) {
   if (!n) return DDPPO_OK;
-  relu_bwd_kernel<<<grid_for(n), 256, 0, s>>>(dy, y, n, dz32, dzop, op_bf16 ? 1 : 0);
+  ::ddppo::launch_k(relu_bwd_kernel, grid_for(n), 256, 0, s, dy, y, n, dz32, dzop, op_bf16 ? 1 : 0);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
 __global__ void add_kernel(float* dst, const float* __restrict__ src, size_t n) {
+  DDPPO_PDL_ENTRY();
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     dst[i] += src[i];
 }
 int launch_add(float* dst, const float* src, size_t n, cudaStream_t s) {
   if (!n) return DDPPO_OK;
-  add_kernel<<<grid_for(n), 256, 0, s>>>(dst, src, n);
+  ::ddppo::launch_k(add_kernel, grid_for(n), 256, 0, s, dst, src, n);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -427,6 +438,7 @@ int launch_add(float* dst, const float* src, size_t n, cudaStream_t s) {
 __global__ void maxpool_fwd_kernel(const float* __restrict__ x, int N, int H, int W, int C,
                                    float* __restrict__ y, uint8_t* __restrict__ arg,
                                    __nv_bfloat16* __restrict__ y_bf) {
+  DDPPO_PDL_ENTRY();
   const int Ho = (H + 2 - 3) / 2 + 1, Wo = (W + 2 - 3) / 2 + 1;
   const size_t total = (size_t)N * Ho * Wo * C;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -455,6 +467,7 @@ __global__ void maxpool_fwd_kernel(const float* __restrict__ x, int N, int H, in
 __global__ void maxpool_fwd4_kernel(const float* __restrict__ x, int H, int W, int C,
                                     float* __restrict__ y, uint8_t* __restrict__ arg,
                                     __nv_bfloat16* __restrict__ y_bf) {
+  DDPPO_PDL_ENTRY();
   const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1, C4 = C / 4;
   const int n = blockIdx.y, per = Ho * Wo * C4;
   const float* xi = x + (size_t)n * H * W * C;
@@ -495,15 +508,16 @@ int launch_maxpool_fwd(const float* x, int N, int H, int W, int C, float* y, uin
   if (C % 4 == 0 && N <= 65535 && (int64_t)Ho * Wo * C < (1ll << 31)) {
     const long per = (long)Ho * Wo * (C / 4);
     const dim3 gb((unsigned)std::max<long>(1, std::min<long>((per + 255) / 256, (8l * 152 + N - 1) / N)), N);
-    maxpool_fwd4_kernel<<<gb, 256, 0, s>>>(x, H, W, C, y, arg, y_bf);
+    ::ddppo::launch_k(maxpool_fwd4_kernel, gb, 256, 0, s, x, H, W, C, y, arg, y_bf);
   } else {
-    maxpool_fwd_kernel<<<grid_for(total), 256, 0, s>>>(x, N, H, W, C, y, arg, y_bf);
+    ::ddppo::launch_k(maxpool_fwd_kernel, grid_for(total), 256, 0, s, x, N, H, W, C, y, arg, y_bf);
   }
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
 __global__ void maxpool_bwd_kernel(const float* __restrict__ dy, const uint8_t* __restrict__ arg,
                                    int N, int H, int W, int C, float* __restrict__ dx) {
+  DDPPO_PDL_ENTRY();
   const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1;
   const size_t total = (size_t)N * H * W * C;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -531,6 +545,7 @@ __global__ void maxpool_bwd_kernel(const float* __restrict__ dy, const uint8_t* 
 }
 __global__ void maxpool_bwd4_kernel(const float* __restrict__ dy, const uint8_t* __restrict__ arg,
                                     int H, int W, int C, float* __restrict__ dx) {
+  DDPPO_PDL_ENTRY();
   const int Ho = (H - 1) / 2 + 1, Wo = (W - 1) / 2 + 1, C4 = C / 4;
   const int n = blockIdx.y, per = H * W * C4;
   const size_t ob = (size_t)n * Ho * Wo * C;
@@ -577,9 +592,9 @@ int launch_maxpool_bwd(const float* dy, const uint8_t* arg, int N, int H, int W,
   if (C % 4 == 0 && N <= 65535 && (int64_t)H * W * C < (1ll << 31)) {
     const long per = (long)H * W * (C / 4);
     const dim3 gb((unsigned)std::max<long>(1, std::min<long>((per + 255) / 256, (8l * 152 + N - 1) / N)), N);
-    maxpool_bwd4_kernel<<<gb, 256, 0, s>>>(dy, arg, H, W, C, dx);
+    ::ddppo::launch_k(maxpool_bwd4_kernel, gb, 256, 0, s, dy, arg, H, W, C, dx);
   } else {
-    maxpool_bwd_kernel<<<grid_for(total), 256, 0, s>>>(dy, arg, N, H, W, C, dx);
+    ::ddppo::launch_k(maxpool_bwd_kernel, grid_for(total), 256, 0, s, dy, arg, N, H, W, C, dx);
   }
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
@@ -594,6 +609,7 @@ __global__ void __launch_bounds__(1024) colsum_kernel(const float* __restrict__ 
                                                       const float* __restrict__ in1, int R,
                                                       int Cc, int ld, float* __restrict__ out0,
                                                       float* __restrict__ out1, int accumulate) {
+  DDPPO_PDL_ENTRY();
   __shared__ float sh[32][33];
   const float* in = blockIdx.y ? in1 : in0;
   float* out = blockIdx.y ? out1 : out0;
@@ -614,7 +630,7 @@ __global__ void __launch_bounds__(1024) colsum_kernel(const float* __restrict__ 
 int launch_colsum(const float* in, int R, int Cc, int ld, float* out, bool accumulate,
                   cudaStream_t s) {
   if (Cc == 0) return DDPPO_OK;
-  colsum_kernel<<<dim3((Cc + 31) / 32, 1), dim3(32, 32), 0, s>>>(in, in, R, Cc, ld, out, out,
+  ::ddppo::launch_k(colsum_kernel, dim3((Cc + 31) / 32, 1), dim3(32, 32), 0, s, in, in, R, Cc, ld, out, out,
                                                                  accumulate ? 1 : 0);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
@@ -622,7 +638,7 @@ int launch_colsum(const float* in, int R, int Cc, int ld, float* out, bool accum
 int launch_colsum2(const float* in0, const float* in1, int R, int Cc, int ld, float* out0,
                    float* out1, bool accumulate, cudaStream_t s) {
   if (Cc == 0) return DDPPO_OK;
-  colsum_kernel<<<dim3((Cc + 31) / 32, 2), dim3(32, 32), 0, s>>>(in0, in1, R, Cc, ld, out0, out1,
+  ::ddppo::launch_k(colsum_kernel, dim3((Cc + 31) / 32, 2), dim3(32, 32), 0, s, in0, in1, R, Cc, ld, out0, out1,
                                                                  accumulate ? 1 : 0);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
@@ -632,6 +648,7 @@ int launch_colsum2(const float* in0, const float* in1, int R, int Cc, int ld, fl
 __device__ __forceinline__ float sigm(float x) { return 1.0f / (1.0f + expf(-x)); }
 
 __global__ void lstm_fwd_kernel(LstmStep a) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)a.E * a.H;
   const int bf = a.op_bf16 ? 1 : 0;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -657,12 +674,13 @@ __global__ void lstm_fwd_kernel(LstmStep a) {
 int launch_lstm_fwd(const LstmStep& a, cudaStream_t s) {
   const size_t total = (size_t)a.E * a.H;
   if (!total) return DDPPO_OK;
-  lstm_fwd_kernel<<<grid_for(total), 256, 0, s>>>(a);
+  ::ddppo::launch_k(lstm_fwd_kernel, grid_for(total), 256, 0, s, a);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
 __global__ void mask_state_kernel(const float* __restrict__ h0, const uint8_t* __restrict__ m,
                                   int E, int H, void* hm, int bf) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)E * H;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x)
@@ -672,7 +690,7 @@ int launch_mask_state(const float* h0, const uint8_t* m, int E, int H, void* hm,
                       cudaStream_t s) {
   const size_t total = (size_t)E * H;
   if (!total) return DDPPO_OK;
-  mask_state_kernel<<<grid_for(total), 256, 0, s>>>(h0, m, E, H, hm, op_bf16 ? 1 : 0);
+  ::ddppo::launch_k(mask_state_kernel, grid_for(total), 256, 0, s, h0, m, E, H, hm, op_bf16 ? 1 : 0);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -682,6 +700,7 @@ int launch_mask_state(const float* h0, const uint8_t* m, int E, int H, void* hm,
 //   dz_i = dc g i(1-i), dz_f = dc c_prev_m f(1-f), dz_g = dc i (1-g^2), dz_o = dh tanh(c) o(1-o)
 //   dc_carry <- dc f  (the caller's next step applies m_t)
 __global__ void lstm_bwd_kernel(LstmBack a) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)a.E * a.H;
   const int bf = a.op_bf16 ? 1 : 0;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -714,7 +733,7 @@ __global__ void lstm_bwd_kernel(LstmBack a) {
 int launch_lstm_bwd(const LstmBack& a, cudaStream_t s) {
   const size_t total = (size_t)a.E * a.H;
   if (!total) return DDPPO_OK;
-  lstm_bwd_kernel<<<grid_for(total), 256, 0, s>>>(a);
+  ::ddppo::launch_k(lstm_bwd_kernel, grid_for(total), 256, 0, s, a);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -722,6 +741,7 @@ int launch_lstm_bwd(const LstmBack& a, cudaStream_t s) {
 // ---------------------------------------------------------------- heads
 // one warp per sample
 __global__ void heads_fwd_kernel(Heads a) {
+  DDPPO_PDL_ENTRY();
   const int n = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (n >= a.N) return;
   const float* h = a.h + (size_t)n * a.H;
@@ -759,7 +779,7 @@ __global__ void heads_fwd_kernel(Heads a) {
 }
 int launch_heads_fwd(const Heads& a, cudaStream_t s) {
   if (!a.N) return DDPPO_OK;
-  heads_fwd_kernel<<<nblk((size_t)a.N * 32, 256), 256, 0, s>>>(a);
+  ::ddppo::launch_k(heads_fwd_kernel, nblk((size_t)a.N * 32, 256), 256, 0, s, a);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -767,6 +787,7 @@ int launch_heads_fwd(const Heads& a, cudaStream_t s) {
 __global__ void heads_dh_kernel(int N, int H, const float* __restrict__ Wa,
                                 const float* __restrict__ Wv, const float* __restrict__ dl,
                                 const float* __restrict__ dv, float* __restrict__ dh) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)N * H;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -781,6 +802,7 @@ __global__ void heads_dh_kernel(int N, int H, const float* __restrict__ Wa,
 __global__ void heads_wgrad_partial(int N, int H, int chunk, const float* __restrict__ h,
                                     const float* __restrict__ dl, const float* __restrict__ dv,
                                     float* __restrict__ part) {
+  DDPPO_PDL_ENTRY();
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   const int ch = blockIdx.y;
   if (k >= H) return;
@@ -797,6 +819,7 @@ __global__ void heads_wgrad_partial(int N, int H, int chunk, const float* __rest
 }
 __global__ void heads_wgrad_final(int H, int nch, const float* __restrict__ part, float* gWa,
                                   float* gWv) {
+  DDPPO_PDL_ENTRY();
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= 5 * H) return;
   float s = 0.f;
@@ -810,15 +833,15 @@ int launch_heads_bwd(int N, int H, const float* h, const float* Wa, const float*
                      const float* dlogits, const float* dvalue, float* dh, float* gWa, float* gba,
                      float* gWv, float* gbv, float* scratch, size_t scratch_elems, cudaStream_t s) {
   if (!N) return DDPPO_OK;
-  heads_dh_kernel<<<grid_for((size_t)N * H), 256, 0, s>>>(N, H, Wa, Wv, dlogits, dvalue, dh);
+  ::ddppo::launch_k(heads_dh_kernel, grid_for((size_t)N * H), 256, 0, s, N, H, Wa, Wv, dlogits, dvalue, dh);
   DDPPO_CHECK_LAUNCH();
   int nch = (int)min((size_t)((N + 63) / 64), scratch_elems / (5 * (size_t)H));
   if (nch < 1) { set_error("heads_bwd: scratch too small"); return DDPPO_E_CONFIG; }
   const int chunk = (N + nch - 1) / nch;
   nch = (N + chunk - 1) / chunk;
-  heads_wgrad_partial<<<dim3((H + 127) / 128, nch), 128, 0, s>>>(N, H, chunk, h, dlogits, dvalue, scratch);
+  ::ddppo::launch_k(heads_wgrad_partial, dim3((H + 127) / 128, nch), 128, 0, s, N, H, chunk, h, dlogits, dvalue, scratch);
   DDPPO_CHECK_LAUNCH();
-  heads_wgrad_final<<<nblk(5 * (size_t)H, 256), 256, 0, s>>>(H, nch, scratch, gWa, gWv);
+  ::ddppo::launch_k(heads_wgrad_final, nblk(5 * (size_t)H, 256), 256, 0, s, H, nch, scratch, gWa, gWv);
   DDPPO_CHECK_LAUNCH();
   DDPPO_TRY(launch_colsum(dlogits, N, 4, 4, gba, false, s));
   DDPPO_TRY(launch_colsum(dvalue, N, 1, 1, gbv, false, s));
@@ -830,6 +853,7 @@ __global__ void embed_fwd_kernel(int N, const float* __restrict__ goal,
                                  const int32_t* __restrict__ prev_a, const float* __restrict__ Wg,
                                  const float* __restrict__ bg, const float* __restrict__ Emb,
                                  void* x, int ldx, int col0, int bf) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)N * 64;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -850,7 +874,7 @@ int launch_embed_fwd(int N, const float* goal, const int32_t* prev_a, const floa
                      const float* bg, const float* Emb, void* x, int ldx, int col0, bool op_bf16,
                      cudaStream_t s) {
   if (!N) return DDPPO_OK;
-  embed_fwd_kernel<<<grid_for((size_t)N * 64), 256, 0, s>>>(N, goal, prev_a, Wg, bg, Emb, x, ldx,
+  ::ddppo::launch_k(embed_fwd_kernel, grid_for((size_t)N * 64), 256, 0, s, N, goal, prev_a, Wg, bg, Emb, x, ldx,
                                                             col0, op_bf16 ? 1 : 0);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
@@ -862,6 +886,7 @@ __global__ void __launch_bounds__(256) embed_bwd_kernel(int N, const float* __re
                                                         const float* __restrict__ dx, int lddx,
                                                         int col0, float* gWg, float* gbg,
                                                         float* gEmb) {
+  DDPPO_PDL_ENTRY();
   const int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (t >= 96 + 32 + 160) return;
   float s = 0.f;
@@ -891,13 +916,14 @@ __global__ void __launch_bounds__(256) embed_bwd_kernel(int N, const float* __re
 }
 int launch_embed_bwd(int N, const float* goal, const int32_t* prev_a, const float* dx, int lddx,
                      int col0, float* gWg, float* gbg, float* gEmb, float*, size_t, cudaStream_t s) {
-  embed_bwd_kernel<<<(288 + 7) / 8, 256, 0, s>>>(N, goal, prev_a, dx, lddx, col0, gWg, gbg, gEmb);
+  ::ddppo::launch_k(embed_bwd_kernel, (288 + 7) / 8, 256, 0, s, N, goal, prev_a, dx, lddx, col0, gWg, gbg, gEmb);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
 
 __global__ void vis_relu_bwd_kernel(int N, int H, const float* __restrict__ dx, int lddx,
                                     const void* x, int ldx, int bf, float* dv32, void* dvop) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)N * H;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -911,7 +937,7 @@ __global__ void vis_relu_bwd_kernel(int N, int H, const float* __restrict__ dx, 
 int launch_vis_relu_bwd(int N, int H, const float* dx, int lddx, const void* x, int ldx,
                         bool op_bf16, float* dv32, void* dvop, cudaStream_t s) {
   if (!N) return DDPPO_OK;
-  vis_relu_bwd_kernel<<<grid_for((size_t)N * H), 256, 0, s>>>(N, H, dx, lddx, x, ldx,
+  ::ddppo::launch_k(vis_relu_bwd_kernel, grid_for((size_t)N * H), 256, 0, s, N, H, dx, lddx, x, ldx,
                                                               op_bf16 ? 1 : 0, dv32, dvop);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
@@ -921,6 +947,7 @@ int launch_vis_relu_bwd(int N, int H, const float* dx, int lddx, const void* x, 
 __global__ void gather_rows_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
                                    const int32_t* __restrict__ idx, int T, int Ein, int Eout,
                                    size_t words) {  // rows of `words` 4-byte words
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)T * Eout * words;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -933,6 +960,7 @@ __global__ void gather_rows_kernel(const uint8_t* __restrict__ in, uint8_t* __re
 __global__ void gather_rows_bytes_kernel(const uint8_t* __restrict__ in, uint8_t* __restrict__ out,
                                          const int32_t* __restrict__ idx, int T, int Ein, int Eout,
                                          size_t bytes) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)T * Eout * bytes;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -947,10 +975,10 @@ int launch_gather_rows(const void* in, void* out, const int32_t* idx, int T, int
   const size_t total = (size_t)T * Eout * bytes;
   if (!total) return DDPPO_OK;
   if (bytes % 4 == 0 && ((uintptr_t)in & 3) == 0 && ((uintptr_t)out & 3) == 0)
-    gather_rows_kernel<<<grid_for(total / 4), 256, 0, s>>>((const uint8_t*)in, (uint8_t*)out, idx,
+    ::ddppo::launch_k(gather_rows_kernel, grid_for(total / 4), 256, 0, s, (const uint8_t*)in, (uint8_t*)out, idx,
                                                            T, Ein, Eout, bytes / 4);
   else
-    gather_rows_bytes_kernel<<<grid_for(total), 256, 0, s>>>((const uint8_t*)in, (uint8_t*)out, idx,
+    ::ddppo::launch_k(gather_rows_bytes_kernel, grid_for(total), 256, 0, s, (const uint8_t*)in, (uint8_t*)out, idx,
                                                              T, Ein, Eout, bytes);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
@@ -960,6 +988,7 @@ int launch_gather_rows(const void* in, void* out, const int32_t* idx, int T, int
 // canonical w[co, ci, ky, kx] -> wg[co, (ky*k + kx)*cin + ci] and wgT[(..), co]; pad zero
 __global__ void conv_w_prep_kernel(const float* __restrict__ w, int cout, int cin, int k, int Kp,
                                    void* wg, void* wgT, int bf) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)cout * Kp;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -975,13 +1004,14 @@ __global__ void conv_w_prep_kernel(const float* __restrict__ w, int cout, int ci
 }
 int launch_conv_w_prep(const float* w, int cout, int cin, int k, int Kp, void* wg, void* wgT,
                        bool op_bf16, cudaStream_t s) {
-  conv_w_prep_kernel<<<grid_for((size_t)cout * Kp), 256, 0, s>>>(w, cout, cin, k, Kp, wg, wgT,
+  ::ddppo::launch_k(conv_w_prep_kernel, grid_for((size_t)cout * Kp), 256, 0, s, w, cout, cin, k, Kp, wg, wgT,
                                                                  op_bf16 ? 1 : 0);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
 __global__ void conv_w_flip_kernel(const float* __restrict__ w, int cout, int cin, int k, void* wr,
                                    int bf) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)cin * k * k * cout;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -994,13 +1024,14 @@ __global__ void conv_w_flip_kernel(const float* __restrict__ w, int cout, int ci
 }
 int launch_conv_w_flip(const float* w, int cout, int cin, int k, void* wr, bool op_bf16,
                        cudaStream_t s) {
-  conv_w_flip_kernel<<<grid_for((size_t)cin * k * k * cout), 256, 0, s>>>(w, cout, cin, k, wr,
+  ::ddppo::launch_k(conv_w_flip_kernel, grid_for((size_t)cin * k * k * cout), 256, 0, s, w, cout, cin, k, wr,
                                                                           op_bf16 ? 1 : 0);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
 __global__ void conv_w_grad_kernel(const float* __restrict__ dwg, int cout, int cin, int k, int Kp,
                                    float* __restrict__ dw) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)cout * cin * k * k;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -1011,12 +1042,13 @@ __global__ void conv_w_grad_kernel(const float* __restrict__ dwg, int cout, int 
 }
 int launch_conv_w_grad(const float* dwg, int cout, int cin, int k, int Kp, float* dw,
                        cudaStream_t s) {
-  conv_w_grad_kernel<<<grid_for((size_t)cout * cin * k * k), 256, 0, s>>>(dwg, cout, cin, k, Kp, dw);
+  ::ddppo::launch_k(conv_w_grad_kernel, grid_for((size_t)cout * cin * k * k), 256, 0, s, dwg, cout, cin, k, Kp, dw);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
 __global__ void vis_w_prep_kernel(const float* __restrict__ w, int H, int C, int HW, void* wg,
                                   void* wgT, int bf) {
+  DDPPO_PDL_ENTRY();
   const int F = C * HW;
   const size_t total = (size_t)H * F;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -1030,12 +1062,13 @@ __global__ void vis_w_prep_kernel(const float* __restrict__ w, int H, int C, int
 }
 int launch_vis_w_prep(const float* w, int H, int C, int HW, void* wg, void* wgT, bool op_bf16,
                       cudaStream_t s) {
-  vis_w_prep_kernel<<<grid_for((size_t)H * C * HW), 256, 0, s>>>(w, H, C, HW, wg, wgT, op_bf16 ? 1 : 0);
+  ::ddppo::launch_k(vis_w_prep_kernel, grid_for((size_t)H * C * HW), 256, 0, s, w, H, C, HW, wg, wgT, op_bf16 ? 1 : 0);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
 __global__ void vis_w_grad_kernel(const float* __restrict__ dwg, int H, int C, int HW,
                                   float* __restrict__ dw) {
+  DDPPO_PDL_ENTRY();
   const int F = C * HW;
   const size_t total = (size_t)H * F;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -1046,17 +1079,18 @@ __global__ void vis_w_grad_kernel(const float* __restrict__ dwg, int H, int C, i
   }
 }
 int launch_vis_w_grad(const float* dwg, int H, int C, int HW, float* dw, cudaStream_t s) {
-  vis_w_grad_kernel<<<grid_for((size_t)H * C * HW), 256, 0, s>>>(dwg, H, C, HW, dw);
+  ::ddppo::launch_k(vis_w_grad_kernel, grid_for((size_t)H * C * HW), 256, 0, s, dwg, H, C, HW, dw);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
 __global__ void add_vec_kernel(const float* a, const float* b, float* out, int n) {
+  DDPPO_PDL_ENTRY();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) out[i] = a[i] + b[i];
 }
 int launch_add_vec(const float* a, const float* b, float* out, int n, cudaStream_t s) {
   if (!n) return DDPPO_OK;
-  add_vec_kernel<<<nblk(n, 256), 256, 0, s>>>(a, b, out, n);
+  ::ddppo::launch_k(add_vec_kernel, nblk(n, 256), 256, 0, s, a, b, out, n);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -1070,6 +1104,7 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
 }
 __global__ void init_uniform_kernel(float* p, size_t n, float lo, float hi, uint64_t seed,
                                     uint64_t stream) {
+  DDPPO_PDL_ENTRY();
   const uint64_t key = mix64(mix64(seed) + 0xD1B54A32D192ED03ull * (stream + 1));
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
     const float u = (float)(mix64(key + i) >> 40) * (1.0f / 16777216.0f);
@@ -1079,17 +1114,18 @@ __global__ void init_uniform_kernel(float* p, size_t n, float lo, float hi, uint
 int launch_init_uniform(float* p, size_t n, float lo, float hi, uint64_t seed, uint64_t stream,
                         cudaStream_t s) {
   if (!n) return DDPPO_OK;
-  init_uniform_kernel<<<grid_for(n), 256, 0, s>>>(p, n, lo, hi, seed, stream);
+  ::ddppo::launch_k(init_uniform_kernel, grid_for(n), 256, 0, s, p, n, lo, hi, seed, stream);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
 __global__ void fill_kernel(float* p, size_t n, float v) {
+  DDPPO_PDL_ENTRY();
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     p[i] = v;
 }
 int launch_fill(float* p, size_t n, float v, cudaStream_t s) {
   if (!n) return DDPPO_OK;
-  fill_kernel<<<grid_for(n), 256, 0, s>>>(p, n, v);
+  ::ddppo::launch_k(fill_kernel, grid_for(n), 256, 0, s, p, n, v);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }

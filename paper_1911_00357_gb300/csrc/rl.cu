@@ -44,6 +44,7 @@ __global__ void __launch_bounds__(256) ppo_loss_kernel(int n, const float* __res
                                                        const float* __restrict__ ret, float clip,
                                                        float cv, float ce, float* dlogits,
                                                        float* dvalues, float* part) {
+  DDPPO_PDL_ENTRY();
   float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     float lg[4];
@@ -113,6 +114,7 @@ __device__ void final_sums(const float* part, int nb, float (&out)[NV]) {
 
 __global__ void __launch_bounds__(kFinal) ppo_loss_final(int nb, int n, const float* part, float cv,
                                                         float ce, float* stats) {
+  DDPPO_PDL_ENTRY();
   float s[5];
   final_sums<5>(part, nb, s);  // part may alias stats: all reads precede the writes below
   if (threadIdx.x != 0) return;
@@ -138,10 +140,10 @@ int launch_ppo_loss(int n, const float* logits, const float* values, const int32
   if (nb > 1024) nb = 1024;
   if (!part) part = stats;
   else if ((size_t)nb * 5 > part_elems) { set_error("ppo_loss: scratch too small"); return DDPPO_E_CONFIG; }
-  ppo_loss_kernel<<<nb, 256, 0, s>>>(n, logits, values, actions, logp_old, adv, ret, clip, cv, ce,
+  ::ddppo::launch_k(ppo_loss_kernel, nb, 256, 0, s, n, logits, values, actions, logp_old, adv, ret, clip, cv, ce,
                                      dlogits, dvalues, part);
   DDPPO_CHECK_LAUNCH();
-  ppo_loss_final<<<1, kFinal, 0, s>>>(nb, n, part, cv, ce, stats);
+  ::ddppo::launch_k(ppo_loss_final, 1, kFinal, 0, s, nb, n, part, cv, ce, stats);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -151,10 +153,10 @@ int launch_ppo_loss_blocks(int n, const float* logits, const float* values, cons
                            float cv, float ce, float* stats, float* dlogits, float* dvalues,
                            float* part, int nb, cudaStream_t s) {
   if (n <= 0) return DDPPO_OK;
-  ppo_loss_kernel<<<nb, 256, 0, s>>>(n, logits, values, actions, logp_old, adv, ret, clip, cv, ce,
+  ::ddppo::launch_k(ppo_loss_kernel, nb, 256, 0, s, n, logits, values, actions, logp_old, adv, ret, clip, cv, ce,
                                      dlogits, dvalues, part);
   DDPPO_CHECK_LAUNCH();
-  ppo_loss_final<<<1, kFinal, 0, s>>>(nb, n, part, cv, ce, stats);
+  ::ddppo::launch_k(ppo_loss_final, 1, kFinal, 0, s, nb, n, part, cv, ce, stats);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -162,6 +164,7 @@ int launch_ppo_loss_blocks(int n, const float* logits, const float* values, cons
 // ---- sum of squares / sums, two-stage ----
 __global__ void __launch_bounds__(256) sumsq_partial(const float* __restrict__ x, size_t n,
                                                      float* part, int square, const float* shift) {
+  DDPPO_PDL_ENTRY();
   float v[1] = {0.f};
   const float mu = shift ? shift[0] : 0.f;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
@@ -172,6 +175,7 @@ __global__ void __launch_bounds__(256) sumsq_partial(const float* __restrict__ x
 }
 __global__ void __launch_bounds__(kFinal) sum_final(int nb, const float* __restrict__ part, float* out,
                                                    int mode, float scale) {
+  DDPPO_PDL_ENTRY();
   float t[1];
   final_sums<1>(part, nb, t);
   if (threadIdx.x != 0) return;
@@ -192,9 +196,9 @@ int launch_grad_norm(const float* g, size_t n, float* norm_out, float* part, siz
                      cudaStream_t s) {
   const int nb = reduce_blocks(n);
   if ((size_t)nb > part_elems) { set_error("grad_norm: scratch too small"); return DDPPO_E_CONFIG; }
-  sumsq_partial<<<nb, 256, 0, s>>>(g, n, part, 1, nullptr);
+  ::ddppo::launch_k(sumsq_partial, nb, 256, 0, s, g, n, part, 1, nullptr);
   DDPPO_CHECK_LAUNCH();
-  sum_final<<<1, kFinal, 0, s>>>(nb, part, norm_out, 0, 1.f);
+  ::ddppo::launch_k(sum_final, 1, kFinal, 0, s, nb, part, norm_out, 0, 1.f);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -204,6 +208,7 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
                             float* __restrict__ v, size_t n, const float* __restrict__ norm,
                             float max_norm, float lr, float b1, float b2, float eps,
                             const int64_t* __restrict__ t_dev, int t_off) {
+  DDPPO_PDL_ENTRY();
   __shared__ float s_bc[2];
   if (threadIdx.x == 0) {
     const double t = (double)(*t_dev + t_off);
@@ -229,7 +234,7 @@ int launch_adam(float* p, const float* g, float* m, float* v, size_t n, const fl
                 int t_off, cudaStream_t s) {
   size_t b = (n + 255) / 256;
   if (b > 152 * 16) b = 152 * 16;
-  adam_kernel<<<(unsigned)b, 256, 0, s>>>(p, g, m, v, n, norm, max_norm, lr, b1, b2, eps, t_dev,
+  ::ddppo::launch_k(adam_kernel, (unsigned)b, 256, 0, s, p, g, m, v, n, norm, max_norm, lr, b1, b2, eps, t_dev,
                                           t_off);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
@@ -244,6 +249,7 @@ __device__ __forceinline__ uint64_t sm64r(uint64_t z) {
 }
 __global__ void perm_kernel(uint64_t seed, const int64_t* __restrict__ update_dev, int64_t epoch,
                             int E, int32_t* perm) {
+  DDPPO_PDL_ENTRY();
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const int64_t update = *update_dev;
   for (int i = 0; i < E; ++i) perm[i] = i;
@@ -261,7 +267,7 @@ __global__ void perm_kernel(uint64_t seed, const int64_t* __restrict__ update_de
 }
 int launch_permutation(uint64_t seed, const int64_t* update_dev, int64_t epoch, int E,
                        int32_t* perm, cudaStream_t s) {
-  perm_kernel<<<1, 32, 0, s>>>(seed, update_dev, epoch, E, perm);
+  ::ddppo::launch_k(perm_kernel, 1, 32, 0, s, seed, update_dev, epoch, E, perm);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -269,6 +275,7 @@ int launch_permutation(uint64_t seed, const int64_t* update_dev, int64_t epoch, 
 // ---- advantage normalisation: (A - mean) / (std + 1e-5), population std ----
 __global__ void normalize_kernel(const float* __restrict__ x, float* __restrict__ y, size_t n,
                                  const float* __restrict__ mean, const float* __restrict__ sd) {
+  DDPPO_PDL_ENTRY();
   const float mu = mean[0], inv = 1.0f / (sd[0] + 1e-5f);
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     y[i] = (x[i] - mu) * inv;
@@ -277,22 +284,23 @@ int launch_normalize_adv(const float* adv, float* out, size_t n, float* scal2, f
                          size_t part_elems, cudaStream_t s) {
   const int nb = reduce_blocks(n);
   if ((size_t)nb > part_elems) { set_error("normalize: scratch too small"); return DDPPO_E_CONFIG; }
-  sumsq_partial<<<nb, 256, 0, s>>>(adv, n, part, 0, nullptr);
+  ::ddppo::launch_k(sumsq_partial, nb, 256, 0, s, adv, n, part, 0, nullptr);
   DDPPO_CHECK_LAUNCH();
-  sum_final<<<1, kFinal, 0, s>>>(nb, part, scal2, 1, 1.0f / (float)n);
+  ::ddppo::launch_k(sum_final, 1, kFinal, 0, s, nb, part, scal2, 1, 1.0f / (float)n);
   DDPPO_CHECK_LAUNCH();
-  sumsq_partial<<<nb, 256, 0, s>>>(adv, n, part, 1, scal2);
+  ::ddppo::launch_k(sumsq_partial, nb, 256, 0, s, adv, n, part, 1, scal2);
   DDPPO_CHECK_LAUNCH();
-  sum_final<<<1, kFinal, 0, s>>>(nb, part, scal2 + 1, 2, 1.0f / (float)n);
+  ::ddppo::launch_k(sum_final, 1, kFinal, 0, s, nb, part, scal2 + 1, 2, 1.0f / (float)n);
   DDPPO_CHECK_LAUNCH();
-  normalize_kernel<<<reduce_blocks(n), 256, 0, s>>>(adv, out, n, scal2, scal2 + 1);
+  ::ddppo::launch_k(normalize_kernel, reduce_blocks(n), 256, 0, s, adv, out, n, scal2, scal2 + 1);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
 
-__global__ void put_scalar_kernel(float* dst, const float* src) { dst[0] = src[0]; }
+__global__ void put_scalar_kernel(float* dst, const float* src) {
+  DDPPO_PDL_ENTRY(); dst[0] = src[0]; }
 int launch_copy_scalar(float* dst, const float* src, cudaStream_t s) {
-  put_scalar_kernel<<<1, 1, 0, s>>>(dst, src);
+  ::ddppo::launch_k(put_scalar_kernel, 1, 1, 0, s, dst, src);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }

@@ -374,6 +374,7 @@ __device__ void next_episode(const SimParams& p, const SimBuffers& b, int e, uin
 }
 
 __global__ void __launch_bounds__(RESET_THREADS) reset_kernel(SimParams p, SimBuffers b, int all) {
+  DDPPO_PDL_ENTRY();
   const int e = blockIdx.x;
   if (e >= p.E) return;
   if (!all && !b.need[e]) return;
@@ -392,7 +393,7 @@ __global__ void __launch_bounds__(RESET_THREADS) reset_kernel(SimParams p, SimBu
 }
 
 int launch_reset(const SimParams& p, const SimBuffers& b, bool all, cudaStream_t s) {
-  reset_kernel<<<p.E, RESET_THREADS, reset_smem_bytes(p), s>>>(p, b, all ? 1 : 0);
+  ::ddppo::launch_k(reset_kernel, p.E, RESET_THREADS, reset_smem_bytes(p), s, p, b, all ? 1 : 0);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -504,6 +505,7 @@ __device__ int step_env(const SimParams& p, const SimBuffers& b, int e,
 __global__ void step_kernel(SimParams p, SimBuffers b, const int32_t* __restrict__ actions,
                             float* __restrict__ reward, uint8_t* __restrict__ done,
                             float* __restrict__ info) {
+  DDPPO_PDL_ENTRY();
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= p.E) return;
   step_env(p, b, e, actions, reward, done, info);
@@ -512,7 +514,7 @@ __global__ void step_kernel(SimParams p, SimBuffers b, const int32_t* __restrict
 int launch_step(const SimParams& p, const SimBuffers& b, const int32_t* actions, float* reward,
                 uint8_t* done, float* info, cudaStream_t s) {
   const int th = 128;
-  step_kernel<<<(p.E + th - 1) / th, th, 0, s>>>(p, b, actions, reward, done, info);
+  ::ddppo::launch_k(step_kernel, (p.E + th - 1) / th, th, 0, s, p, b, actions, reward, done, info);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -635,6 +637,7 @@ __device__ bool render_env_block(const SimParams& p, const SimBuffers& b, int e,
 
 __global__ void render_kernel(SimParams p, SimBuffers b, void* __restrict__ obs,
                               float* __restrict__ goal, float* __restrict__ depth_raw) {
+  DDPPO_PDL_ENTRY();
   extern __shared__ __align__(128) uint32_t sbits[];
   __shared__ __align__(8) uint64_t mbar;
   if (threadIdx.x == 0) {
@@ -655,6 +658,7 @@ __global__ void __launch_bounds__(RESET_THREADS)
                                void* __restrict__ obs, float* __restrict__ goal,
                                float* __restrict__ reward, uint8_t* __restrict__ done,
                                float* __restrict__ info) {
+  DDPPO_PDL_ENTRY();
   extern __shared__ __align__(128) uint32_t smem[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ int s_env, s_fin;
@@ -699,6 +703,7 @@ __global__ void __launch_bounds__(RESET_THREADS)
 // next episode of every env whose other slot is not ready. Runs beside the policy's
 // forward pass; the next env step adopts the prepared slot instead of generating it.
 __global__ void __launch_bounds__(RESET_THREADS) env_prefetch_kernel(SimParams p, SimBuffers b) {
+  DDPPO_PDL_ENTRY();
   extern __shared__ __align__(128) uint32_t smem[];
   __shared__ int s_env;
   const int tid = threadIdx.x;
@@ -726,13 +731,14 @@ __global__ void __launch_bounds__(RESET_THREADS) env_prefetch_kernel(SimParams p
 }
 
 int launch_env_prefetch(const SimParams& p, const SimBuffers& b, int grid, cudaStream_t s) {
-  env_prefetch_kernel<<<grid, RESET_THREADS, reset_smem_bytes(p), s>>>(p, b);
+  ::ddppo::launch_k(env_prefetch_kernel, grid, RESET_THREADS, reset_smem_bytes(p), s, p, b);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
 
 __global__ void copy_current_kernel(SimParams p, SimBuffers b, uint8_t* __restrict__ grids,
                                     int32_t* __restrict__ dists) {
+  DDPPO_PDL_ENTRY();
   const int e = blockIdx.y;
   const size_t GM = (size_t)p.grid_max * p.grid_max, ci = cur_index(p, b, e);
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < GM;
@@ -747,7 +753,7 @@ int launch_copy_current(const SimParams& p, const SimBuffers& b, uint8_t* grids,
   if (p.E > 65535) { set_error("env_grids: too many envs"); return DDPPO_E_CONFIG; }
   const size_t GM = (size_t)p.grid_max * p.grid_max;
   const unsigned bx = (unsigned)std::min<size_t>((GM + 255) / 256, 64);
-  copy_current_kernel<<<dim3(bx, p.E), 256, 0, s>>>(p, b, grids, dists);
+  ::ddppo::launch_k(copy_current_kernel, dim3(bx, p.E), 256, 0, s, p, b, grids, dists);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -756,7 +762,7 @@ int launch_env_step(const SimParams& p, const SimBuffers& b, int grid, const int
                     void* obs, float* goal, float* reward, uint8_t* done, float* info,
                     cudaStream_t s) {
   const size_t smem = max(reset_smem_bytes(p), (size_t)p.grid_max * p.grid_max / 8);
-  env_step_persistent_kernel<<<grid, RESET_THREADS, smem, s>>>(p, b, actions, obs, goal, reward,
+  ::ddppo::launch_k(env_step_persistent_kernel, grid, RESET_THREADS, smem, s, p, b, actions, obs, goal, reward,
                                                                done, info);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
@@ -765,7 +771,7 @@ int launch_env_step(const SimParams& p, const SimBuffers& b, int grid, const int
 int launch_render(const SimParams& p, const SimBuffers& b, void* obs, float* goal, float* depth_raw,
                   cudaStream_t s) {
   const size_t smem = (size_t)p.grid_max * p.grid_max / 8;
-  render_kernel<<<p.E, p.W, smem, s>>>(p, b, obs, goal, depth_raw);
+  ::ddppo::launch_k(render_kernel, p.E, p.W, smem, s, p, b, obs, goal, depth_raw);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }

@@ -36,6 +36,7 @@ template <> __device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloa
 template <typename T>
 __global__ void gconv_fwd_kernel(GConv g, const T* __restrict__ x, const T* __restrict__ w,
                                  float* __restrict__ z) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)g.N * g.Ho * g.Wo * g.C;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -63,6 +64,7 @@ __global__ void gconv_fwd_kernel(GConv g, const T* __restrict__ x, const T* __re
 template <typename T>
 __global__ void gconv_dgrad_kernel(GConv g, const T* __restrict__ dz, const T* __restrict__ w,
                                    float* __restrict__ dx, int accumulate) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)g.N * g.H * g.W * g.C;
   for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (size_t)gridDim.x * blockDim.x) {
@@ -100,6 +102,7 @@ template <typename T>
 __global__ void __launch_bounds__(GW_THREADS)
     gconv_wgrad_kernel(GConv g, const T* __restrict__ x, const T* __restrict__ dz, int pix_per_chunk,
                        float* __restrict__ part) {
+  DDPPO_PDL_ENTRY();
   extern __shared__ float sh[];
   const int cpg = g.cpg, gi = blockIdx.x, chunk = blockIdx.y;
   float* sdz = sh;                         // [GW_PIX][cpg]
@@ -155,6 +158,7 @@ __global__ void __launch_bounds__(GW_THREADS)
 // dw[i] (= beta dw + sum over chunks in order), i over C * cpg * 9 canonical weights
 __global__ void gconv_wgrad_reduce_kernel(const float* __restrict__ part, int chunks, size_t nwt,
                                           float* __restrict__ dw, float beta) {
+  DDPPO_PDL_ENTRY();
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < nwt;
        i += (size_t)gridDim.x * blockDim.x) {
     float v = 0.f;
@@ -165,6 +169,7 @@ __global__ void gconv_wgrad_reduce_kernel(const float* __restrict__ part, int ch
 
 // canonical [C][cpg][3][3] fp32 -> [C][3][3][cpg] operand dtype
 __global__ void gconv_w_prep_kernel(const float* __restrict__ w, int C, int cpg, void* out, int bf) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)C * cpg * 9;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -187,10 +192,10 @@ int launch_gconv_fwd(const GConv& g, const void* x, const void* w, float* z, boo
   const size_t total = (size_t)g.N * g.Ho * g.Wo * g.C;
   if (!total) return DDPPO_OK;
   if (bf)
-    gconv_fwd_kernel<<<sx_blocks(total, 256), 256, 0, s>>>(g, (const __nv_bfloat16*)x,
+    ::ddppo::launch_k(gconv_fwd_kernel<__nv_bfloat16>, sx_blocks(total, 256), 256, 0, s, g, (const __nv_bfloat16*)x,
                                                            (const __nv_bfloat16*)w, z);
   else
-    gconv_fwd_kernel<<<sx_blocks(total, 256), 256, 0, s>>>(g, (const float*)x, (const float*)w, z);
+    ::ddppo::launch_k(gconv_fwd_kernel<float>, sx_blocks(total, 256), 256, 0, s, g, (const float*)x, (const float*)w, z);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -200,10 +205,10 @@ int launch_gconv_dgrad(const GConv& g, const void* dz, const void* w, float* dx,
   const size_t total = (size_t)g.N * g.H * g.W * g.C;
   if (!total) return DDPPO_OK;
   if (bf)
-    gconv_dgrad_kernel<<<sx_blocks(total, 256), 256, 0, s>>>(
+    ::ddppo::launch_k(gconv_dgrad_kernel<__nv_bfloat16>, sx_blocks(total, 256), 256, 0, s,
         g, (const __nv_bfloat16*)dz, (const __nv_bfloat16*)w, dx, accumulate ? 1 : 0);
   else
-    gconv_dgrad_kernel<<<sx_blocks(total, 256), 256, 0, s>>>(g, (const float*)dz, (const float*)w,
+    ::ddppo::launch_k(gconv_dgrad_kernel<float>, sx_blocks(total, 256), 256, 0, s, g, (const float*)dz, (const float*)w,
                                                              dx, accumulate ? 1 : 0);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
@@ -226,19 +231,19 @@ int launch_gconv_wgrad(const GConv& g, const void* x, const void* dz, float* par
   const dim3 grid(g.C / g.cpg, chunks);
   const size_t smem = (size_t)GW_PIX * 10 * g.cpg * sizeof(float);
   if (bf)
-    gconv_wgrad_kernel<<<grid, GW_THREADS, smem, s>>>(g, (const __nv_bfloat16*)x,
+    ::ddppo::launch_k(gconv_wgrad_kernel<__nv_bfloat16>, grid, GW_THREADS, smem, s, g, (const __nv_bfloat16*)x,
                                                       (const __nv_bfloat16*)dz, ppc, part);
   else
-    gconv_wgrad_kernel<<<grid, GW_THREADS, smem, s>>>(g, (const float*)x, (const float*)dz, ppc, part);
+    ::ddppo::launch_k(gconv_wgrad_kernel<float>, grid, GW_THREADS, smem, s, g, (const float*)x, (const float*)dz, ppc, part);
   DDPPO_CHECK_LAUNCH();
-  gconv_wgrad_reduce_kernel<<<sx_blocks(nwt, 256), 256, 0, s>>>(part, chunks, nwt, dw, beta);
+  ::ddppo::launch_k(gconv_wgrad_reduce_kernel, sx_blocks(nwt, 256), 256, 0, s, part, chunks, nwt, dw, beta);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
 
 int launch_gconv_w_prep(const float* w, int C, int cpg, void* out, bool bf, cudaStream_t s) {
   const size_t total = (size_t)C * cpg * 9;
-  gconv_w_prep_kernel<<<sx_blocks(total, 256), 256, 0, s>>>(w, C, cpg, out, bf ? 1 : 0);
+  ::ddppo::launch_k(gconv_w_prep_kernel, sx_blocks(total, 256), 256, 0, s, w, C, cpg, out, bf ? 1 : 0);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -247,6 +252,7 @@ int launch_gconv_w_prep(const float* w, int C, int cpg, void* out, bool bf, cuda
 // m[n, c] = mean over the HW pixels of u[n, :, c]
 __global__ void se_squeeze_kernel(const float* __restrict__ u, int N, int HW, int C,
                                   float* __restrict__ m) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)N * C;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -270,6 +276,7 @@ __global__ void se_fc_fwd_kernel(const float* __restrict__ m, const float* __res
                                  const float* __restrict__ b1, const float* __restrict__ W2,
                                  const float* __restrict__ b2, int C, int Cr, float* __restrict__ a,
                                  float* __restrict__ gate) {
+  DDPPO_PDL_ENTRY();
   extern __shared__ float sm[];
   float* sm_m = sm;       // [C]
   float* sm_a = sm + C;   // [Cr]
@@ -298,6 +305,7 @@ __global__ void se_fc_fwd_kernel(const float* __restrict__ m, const float* __res
 __global__ void se_apply_kernel(const float* __restrict__ u, const float* __restrict__ gate,
                                 const float* __restrict__ sc, int N, int HW, int C,
                                 float* __restrict__ y, __nv_bfloat16* __restrict__ y_bf) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)N * HW * C;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -315,6 +323,7 @@ __global__ void se_apply_kernel(const float* __restrict__ u, const float* __rest
 __global__ void se_bwd_reduce_kernel(const float* gy, const float* __restrict__ y,
                                      const float* __restrict__ u, int N, int HW, int C, float* gpre,
                                      float* __restrict__ dg) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)N * C;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -336,6 +345,7 @@ __global__ void se_fc_bwd_kernel(const float* __restrict__ dg, const float* __re
                                  const float* __restrict__ a, const float* __restrict__ W1,
                                  const float* __restrict__ W2, int C, int Cr, float* __restrict__ dq,
                                  float* __restrict__ dh, float* __restrict__ dm) {
+  DDPPO_PDL_ENTRY();
   extern __shared__ float sm[];
   float* sm_q = sm;       // [C]
   float* sm_h = sm + C;   // [Cr]
@@ -369,6 +379,7 @@ __global__ void se_fc_bwd_kernel(const float* __restrict__ dg, const float* __re
 __global__ void se_du_kernel(const float* __restrict__ gpre, const float* __restrict__ gate,
                              const float* __restrict__ dm, int N, int HW, int C,
                              float* __restrict__ du) {
+  DDPPO_PDL_ENTRY();
   const size_t total = (size_t)N * HW * C;
   const float inv = 1.f / (float)HW;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
@@ -386,6 +397,7 @@ __global__ void se_wgrad_kernel(const float* __restrict__ dq, const float* __res
                                 const float* __restrict__ a, const float* __restrict__ m, int N,
                                 int C, int Cr, float* __restrict__ gW1, float* __restrict__ gb1,
                                 float* __restrict__ gW2, float* __restrict__ gb2, int accumulate) {
+  DDPPO_PDL_ENTRY();
   const size_t n1 = (size_t)Cr * C, n2 = n1 + Cr, n3 = n2 + (size_t)C * Cr, total = n3 + C;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (size_t)gridDim.x * blockDim.x) {
@@ -415,12 +427,12 @@ __global__ void se_wgrad_kernel(const float* __restrict__ dq, const float* __res
 
 int launch_se_fwd(const SeArgs& e, cudaStream_t s) {
   const size_t NC = (size_t)e.N * e.C, tot = NC * e.HW;
-  se_squeeze_kernel<<<sx_blocks(NC, 256), 256, 0, s>>>(e.u, e.N, e.HW, e.C, e.m);
+  ::ddppo::launch_k(se_squeeze_kernel, sx_blocks(NC, 256), 256, 0, s, e.u, e.N, e.HW, e.C, e.m);
   DDPPO_CHECK_LAUNCH();
-  se_fc_fwd_kernel<<<e.N, 256, (size_t)(e.C + e.Cr) * 4, s>>>(e.m, e.W1, e.b1, e.W2, e.b2, e.C, e.Cr,
+  ::ddppo::launch_k(se_fc_fwd_kernel, e.N, 256, (size_t)(e.C + e.Cr) * 4, s, e.m, e.W1, e.b1, e.W2, e.b2, e.C, e.Cr,
                                                              e.a, e.gate);
   DDPPO_CHECK_LAUNCH();
-  se_apply_kernel<<<sx_blocks(tot, 256), 256, 0, s>>>(e.u, e.gate, e.sc, e.N, e.HW, e.C, e.y, e.y_bf);
+  ::ddppo::launch_k(se_apply_kernel, sx_blocks(tot, 256), 256, 0, s, e.u, e.gate, e.sc, e.N, e.HW, e.C, e.y, e.y_bf);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;
 }
@@ -428,15 +440,15 @@ int launch_se_fwd(const SeArgs& e, cudaStream_t s) {
 int launch_se_bwd(const SeArgs& e, const float* gy, float* gpre, float* du, bool accumulate,
                   cudaStream_t s) {
   const size_t NC = (size_t)e.N * e.C, tot = NC * e.HW;
-  se_bwd_reduce_kernel<<<sx_blocks(NC, 256), 256, 0, s>>>(gy, e.y, e.u, e.N, e.HW, e.C, gpre, e.dg);
+  ::ddppo::launch_k(se_bwd_reduce_kernel, sx_blocks(NC, 256), 256, 0, s, gy, e.y, e.u, e.N, e.HW, e.C, gpre, e.dg);
   DDPPO_CHECK_LAUNCH();
-  se_fc_bwd_kernel<<<e.N, 256, (size_t)(e.C + e.Cr) * 4, s>>>(e.dg, e.gate, e.a, e.W1, e.W2, e.C,
+  ::ddppo::launch_k(se_fc_bwd_kernel, e.N, 256, (size_t)(e.C + e.Cr) * 4, s, e.dg, e.gate, e.a, e.W1, e.W2, e.C,
                                                              e.Cr, e.dq, e.dh, e.dm);
   DDPPO_CHECK_LAUNCH();
-  se_du_kernel<<<sx_blocks(tot, 256), 256, 0, s>>>(gpre, e.gate, e.dm, e.N, e.HW, e.C, du);
+  ::ddppo::launch_k(se_du_kernel, sx_blocks(tot, 256), 256, 0, s, gpre, e.gate, e.dm, e.N, e.HW, e.C, du);
   DDPPO_CHECK_LAUNCH();
   const size_t np = (size_t)e.Cr * e.C * 2 + e.Cr + e.C;
-  se_wgrad_kernel<<<sx_blocks(np, 256), 256, 0, s>>>(e.dq, e.dh, e.a, e.m, e.N, e.C, e.Cr, e.gW1,
+  ::ddppo::launch_k(se_wgrad_kernel, sx_blocks(np, 256), 256, 0, s, e.dq, e.dh, e.a, e.m, e.N, e.C, e.Cr, e.gW1,
                                                      e.gb1, e.gW2, e.gb2, accumulate ? 1 : 0);
   DDPPO_CHECK_LAUNCH();
   return DDPPO_OK;

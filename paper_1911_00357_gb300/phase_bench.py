@@ -27,12 +27,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=2)
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--precision", type=int, default=None, help="override the preset's precision")
-    ap.add_argument("--lstm-mode", type=int, default=2, choices=[0, 1, 2],
-                    help="LSTM recurrence: 0 step by step, 1 whole segment on CUDA cores, "
-                         "2 tcgen05 forward (default)")
+    ap.add_argument("--lstm-mode", type=int, default=0, choices=[0, 1, 2],
+                    help="LSTM recurrence: 0 step by step (default), 1 whole segment on CUDA "
+                         "cores, 2 tcgen05 forward")
     ap.add_argument("--gn-two-launch", action="store_true",
                     help="GroupNorm statistics and normalisation as two launches")
+    ap.add_argument("--no-launch-overlap", action="store_true",
+                    help="plain stream order instead of programmatic dependent launch")
     args = ap.parse_args()
+    B.ddppo_set_launch_overlap(not args.no_launch_overlap)
     w = Worker(args.preset, seed=args.seed, precision=args.precision)
     B.ddppo_lstm_whole_segment(w.h, args.lstm_mode)
     if args.gn_two_launch:
@@ -66,6 +69,7 @@ def main():
             "preset": args.preset, "precision": w.cfg.precision, "num_envs": w.E, "rollout_T": w.T,
             "seed": args.seed, "lstm_mode": args.lstm_mode,
             "group_norm": "two launches" if args.gn_two_launch else "one launch",
+            "launch_overlap": not args.no_launch_overlap,
             "collect_ms": round(c, 2), "update_ms": round(u, 2),
             "act_frames_per_s": round(frames / c * 1e3, 1),
             "frames_per_s": round(frames / (c + u) * 1e3, 1),
