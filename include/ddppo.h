@@ -537,10 +537,13 @@ int ddppo_squeeze_excite(int32_t N, int32_t HW, int32_t C, int32_t Cr, const flo
  * bf16 convolution of this shape (the encoder of Sec. 4 "Agent") and for its weight
  * gradient. Host only: no CUDA call, no
  * device needed. plan [host] int32 [18]:
- *   [0] 4-D gather forward path usable; [1] halo forward path usable, then [2] anchor pitch
- *   Wp = W + 2p, [3] padded height Hh, [4] images per 128-anchor tile (0: tiles within one
- *   image), [5] tiles per image, [6] box rows per image, [7] anchor rows allocated per
- *   ring stage, [8] anchor rows the box delivers, [9] tiles;
+ *   [0] 4-D gather forward path usable; [1] halo forward path usable (1: anchor halo, 2:
+ *   row halo -- 3x3 filters, W in {8, 16, 32}, H >= 128 / W, Cout <= 32: whole image rows
+ *   per tile, the three column taps in one MMA, the default path for such shapes), then
+ *   [2] anchor pitch Wp = W + 2p (row halo: W), [3] padded height Hh (row halo: H), [4]
+ *   images per 128-anchor tile (0: tiles within one image), [5] tiles per image, [6] box
+ *   rows per image, [7] anchor rows allocated per ring stage, [8] anchor rows the box
+ *   delivers, [9] tiles;
  *   [10] 4-D gather weight gradient usable; [11] halo weight gradient usable, then [12]
  *   rows per work unit RB, [13] pitch Wp, [14] input box rows, [15] dz box rows, [16] ring
  *   depth, [17] shared memory bytes per CTA.

@@ -11,7 +11,9 @@
 //     operands use kind::f8f6f4 (K=32) on the same byte layouts, with the two per-tensor
 //     scales applied in the epilogue.
 //   * Convolutions gather their operand tiles themselves: a 4-D TMA box per filter tap,
-//     or one halo box per tile read through row-shifted descriptors.
+//     or one halo box per tile read through row-shifted descriptors (for 3x3 filters on
+//     images at most 32 wide: whole image rows per tile, the three column taps as one
+//     N = 3 x 32 MMA per filter row, combined in the epilogue by lane shuffles).
 //   * Epilogue: 4 warps each read their 32 TMEM lanes (rows) with tcgen05.ld.32x32b and
 //     apply beta/bias/ReLU, storing fp32 or bf16 -- or fp32 split-K partials that a
 //     fixed-order reduction combines.
@@ -112,6 +114,14 @@ __device__ __forceinline__ uint64_t sw64_desc(uint32_t saddr) {
 //         tile's output rows plus the filter's halo, rows of pitch Wp = W + 2p) is staged,
 //         and every filter tap reads it as a row-shifted view. Tile rows are "anchors" on
 //         the Wp-pitch grid; anchors outside the image are computed and discarded.
+// on = 4: row halo (3x3 stride-1 'same' convolution of 32 channels, W in {8, 16, 32}, at
+//         most 32 output channels): a tile is R = 128 / W whole image rows; its box holds
+//         those rows and the rows above and below (W columns from x = 0, pitch W, so each
+//         filter row ky is the box shifted by ky W rows -- a whole number of 512-byte
+//         swizzle atoms). One MMA per (ky, 16-channel step) multiplies by the three column
+//         taps at once (N = 96: B rows (kx, co)), giving D_kx at every pixel; the epilogue
+//         forms out(x) = D_1(x) + D_0(x - 1) + D_2(x + 1) with the neighbours' values taken
+//         by lane shuffles (a row never crosses a warp) and zero at the image's edges.
 struct ConvA {
   int on = 0;
   int C = 0, cbw = 64;       // input channels, channels per K-block (64 or 32)
@@ -124,6 +134,7 @@ struct ConvA {
   int ni = 0;                // images per tile (small images), or 0: tiles within one image
   int tpi = 1;               // tiles per image when ni == 0
   int rows_box = 1;          // rows of the halo box (per image)
+  int R = 0;                 // row halo: image rows per tile
   int tiles_m = 1;
   uint32_t halo_bytes = 0;   // stride of the two halo stages in shared memory
   uint32_t box_bytes = 0;    // bytes one halo box delivers
@@ -132,7 +143,12 @@ struct ConvA {
 // output row of anchor r of halo-mode tile tm, or -1 when the anchor is not an output pixel
 __device__ __forceinline__ long long halo_out_row(const ConvA& ca, int tm, int r) {
   int img, y, x;
-  if (ca.ni) {
+  if (ca.on == 4) {
+    img = tm / ca.tpi;
+    const int rr = r / ca.W;
+    x = r - rr * ca.W;
+    y = (tm - img * ca.tpi) * ca.R + rr;
+  } else if (ca.ni) {
     const int per = ca.Hh * ca.Wp;
     const int i = r / per, rem = r - i * per;
     if (i >= ca.ni) return -1;
@@ -173,6 +189,20 @@ __device__ __forceinline__ uint64_t sw128_mn_desc(uint32_t saddr) {
   return d;
 }
 
+// 32 accumulator columns of this warp's 32 TMEM lanes -> registers (waits for the load)
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+      "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+        "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+        "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 // Persistent, warp-specialised kernel. Warp 0 streams (tile, k-block) stages through the
 // shared-memory ring with TMA; warp 1 issues the MMAs of a tile into one of two TMEM
 // accumulators; warps 2..5 drain the other accumulator (tcgen05.ld -> smem transpose ->
@@ -195,7 +225,11 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
   __shared__ float epi_stage[4][32 * TC_EPI_PITCH];
   // stage sizes follow the K extent of one ring slot (32 channels for narrow convolutions);
   // the halo mode has a ring of `stages` halo boxes (A) and all the weights resident (B)
-  const bool halo = ca.on == 3;
+  const bool halo = ca.on >= 3;
+  const bool rowh = BN == 32 && ca.on == 4;  // the row halo has one 32-column N tile
+  // accumulator columns: BN per buffer, or 96 (three column taps x 32) in the row halo,
+  // spaced 128 apart
+  const uint32_t acc_stride = rowh ? 128u : (uint32_t)BN, tcols = 2u * acc_stride;
   const int kslot = (ca.on == 1 || halo) ? ca.cbw : TC_BK;
   const uint32_t A_BYTES = halo ? ca.halo_bytes : TC_BM * kslot * 2, B_BYTES = BN * kslot * 2;
   uint8_t* base = (uint8_t*)(((uintptr_t)dyn + 1023) & ~(uintptr_t)1023);
@@ -224,7 +258,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_addr(&ctl.tmem_base)),
-                 "r"(2 * BN));
+                 "r"(tcols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -246,8 +280,12 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
       uint32_t hit = 0;
       for (int t = blockIdx.x; t < ntiles && !*abort; t += gridDim.x) {
         const int tm = t % tiles_m, z = t / (tiles_m * tiles_n);
-        int img, ybase;
-        if (ca.ni) {
+        int img, ybase, xbase = -ca.p;
+        if (rowh) {
+          img = tm / ca.tpi;
+          ybase = (tm - img * ca.tpi) * ca.R - 1;
+          xbase = 0;
+        } else if (ca.ni) {
           img = tm * ca.ni;
           ybase = -ca.p;
         } else {
@@ -259,7 +297,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
           const int hs = hit % stages;
           if (!mbar_wait(&ctl.empty[hs], ((hit / stages) & 1u) ^ 1u, abort, err)) break;
           mbar_expect_tx(&ctl.full[hs], ca.box_bytes);
-          tma_load_4d(sA + hs * A_BYTES, &mapA, &ctl.full[hs], c0, -ca.p, ybase, img);
+          tma_load_4d(sA + hs * A_BYTES, &mapA, &ctl.full[hs], c0, xbase, ybase, img);
         }
       }
       ctl.issued = hit;
@@ -267,7 +305,8 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
   } else if (warp == 1 && halo) {
     if (lane == 0) {
       // halo MMA issuer: tap (ky, kx) reads the staged box from row off + ky Wp + kx on
-      const uint32_t idesc = fp8 ? f8_idesc(TC_BM, BN) : f16_idesc(TC_BM, BN, 0, 0);
+      const int NM = rowh ? 96 : BN;  // MMA N: the row halo's three column taps x 32
+      const uint32_t idesc = fp8 ? f8_idesc(TC_BM, NM) : f16_idesc(TC_BM, NM, 0, 0);
       const int nkk = ca.k * ca.k, ncb = ca.C / ca.cbw, rb = ca.cbw * 2;
       const uint32_t wbox = (uint32_t)BN * ca.cbw * 2;
       const bool wok = mbar_wait(&ctl.done, 0u, abort, err);
@@ -278,7 +317,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
         const uint32_t buf = ti & 1u, bph = (ti >> 1) & 1u;
         if (!mbar_wait(&acc_empty[buf], bph ^ 1u, abort, err)) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t dacc = tmem + buf * BN;
+        const uint32_t dacc = tmem + buf * acc_stride;
         uint32_t acc = 0;
         const int cb_end = min(ca.C, z * kchunk + kchunk);
         for (int c0 = z * kchunk; c0 < cb_end; c0 += ca.cbw, ++hit) {
@@ -287,7 +326,19 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t h0 = smem_addr(sA + hs * A_BYTES);
           const int cb = c0 / ca.cbw;
-          for (int tap = 0; tap < nkk; ++tap) {
+          if (rowh) {
+            // filter row ky: the box from row ky W on; B = the weights of taps (ky, 0..2),
+            // resident one after another (96 rows of 64 bytes)
+            for (int ky = 0; ky < 3; ++ky) {
+              const uint32_t arow = h0 + (uint32_t)(ky * ca.W) * (uint32_t)rb;
+              const uint32_t b0 = smem_addr(sB + (ky * 3 * ncb + cb) * wbox);
+              for (int kq = 0; kq < ca.cbw / 16; ++kq) {
+                tc_mma(dacc, sw64_desc(arow + kq * 32), sw64_desc(b0 + kq * 32), idesc, acc, fp8);
+                acc = 1u;
+              }
+            }
+          }
+          for (int tap = 0; tap < (rowh ? 0 : nkk); ++tap) {
             const int ky = tap / ca.k, kx = tap - ky * ca.k;
             const uint32_t arow = h0 + (uint32_t)(off + ky * ca.Wp + kx) * rb;
             const uint32_t b0 = smem_addr(sB + (tap * ncb + cb) * wbox);
@@ -456,21 +507,36 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
       // halo mode: output row of this lane's tile row, computed once per tile and handed to
       // the row loop by shuffles
       const long long my_orow = halo ? halo_out_row(ca, tm, q * 32 + lane) : 0;
+      const int px = rowh ? (q * 32 + lane) % ca.W : 0;  // row halo: this lane's image column
 #pragma unroll 1
       for (int c0 = 0; c0 < BN; c0 += 32) {
         if (n0 + c0 >= N) break;  // columns past N: nothing to read or store
         uint32_t r[32];
-        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * BN + (uint32_t)c0;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-            "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-              "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-              "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-              "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + buf * acc_stride + (uint32_t)c0;
+        if (rowh) {
+          // out(x) = D_1(x) + D_0(x - 1) + D_2(x + 1), in that order; the neighbours' values
+          // come from lanes -1 / +1 of the same image row, zero past the row's ends
+          float o[32];
+          tmem_ld32(taddr + 32u, r);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) o[j] = __uint_as_float(r[j]);
+          tmem_ld32(taddr, r);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float v = __shfl_up_sync(0xffffffffu, __uint_as_float(r[j]), 1);
+            if (px > 0) o[j] += v;
+          }
+          tmem_ld32(taddr + 64u, r);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            const float v = __shfl_down_sync(0xffffffffu, __uint_as_float(r[j]), 1);
+            if (px < ca.W - 1) o[j] += v;
+          }
+#pragma unroll
+          for (int j = 0; j < 32; ++j) r[j] = __float_as_uint(o[j]);
+        } else {
+          tmem_ld32(taddr, r);
+        }
         if (!ok) continue;
         if (trans_out) {
           if (row >= M) continue;
@@ -597,7 +663,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
   }
   if (warp == 0) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tcols));
   }
 }
 
@@ -676,6 +742,22 @@ static bool halo_geom(const ConvShape& c, ConvA* ca) {
   if (!bn) return false;
   const size_t wbytes = (size_t)bn * c.k * c.k * c.C * 2;
   if (wbytes > TC_HALO_WEIGHTS_MAX) return false;
+  if (c.k == 3 && bn == 32 && (c.W == 8 || c.W == 16 || c.W == 32) && c.H >= TC_BM / c.W) {
+    // row halo: R whole rows per tile, the box R + 2 rows of W pixels (64 bytes each)
+    const int R = TC_BM / c.W;
+    const uint32_t box = (uint32_t)((R + 2) * c.W * 64);
+    if (ca) {
+      ca->on = 4;
+      ca->C = 32; ca->cbw = 32; ca->k = 3; ca->s = 1; ca->p = 1;
+      ca->Ho = c.Ho; ca->Wo = c.Wo;
+      ca->N = c.N; ca->H = c.H; ca->W = c.W; ca->Wp = c.W; ca->Hh = c.H;
+      ca->ni = 0; ca->tpi = (c.H + R - 1) / R; ca->rows_box = R + 2; ca->R = R;
+      ca->tiles_m = c.N * ca->tpi;
+      ca->halo_bytes = (box + 1023) / 1024 * 1024;
+      ca->box_bytes = box;
+    }
+    return true;
+  }
   const int Wp = c.W + 2 * c.p, Hh = c.H + 2 * c.p, per = Hh * Wp;
   const int cbw = c.C == 32 ? 32 : 64, rb = cbw * 2;
   int ni, tpi, rows_box, rows_need;
@@ -715,7 +797,8 @@ static size_t halo_smem(const ConvA& ca, int bn, int stages) {
 }
 
 // NHWC bf16 input as [C, W, H, N]; one box = the halo of a tile: cbw channels x Wp columns
-// (from x = -p) x rows_box rows x (ni or 1) images, zero outside the image
+// (from x = -p; the row halo: W columns from x = 0) x rows_box rows x (ni or 1) images,
+// zero outside the image
 static bool make_halo_map(CUtensorMap* m, const void* x, const ConvShape& c, const ConvA& ca) {
   auto fn = encode_fn();
   if (!fn) return false;
@@ -922,7 +1005,7 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
                                           (int)TC_SMEM_MAX));
     attr_done[dev] = true;
   }
-  const bool halo = ca.on == 3;
+  const bool halo = ca.on >= 3;
   const int gm = halo ? ca.tiles_m : (M + TC_BM - 1) / TC_BM, gn = (N + BN - 1) / BN;
   const int tiles = gm * gn;
   // split-K: over K elements, or over channel blocks in the halo mode (every block runs all
@@ -1094,9 +1177,9 @@ static TcCfg tune(const GemmDesc& d, const GemmWorkspace& ws, TcTuner& t, cudaSt
 int gemm_tc(const GemmDesc& d, const GemmWorkspace& ws, cudaStream_t s) {
   const bool swap = d.convw || (!d.conv && d.M < TC_BM && d.N > d.M);
   TcCfg cfg = default_cfg(swap ? d.M : d.N, kslot_of(d));
-  if (d.conv && !gather_ok(*d.conv) && halo_geom(*d.conv, nullptr)) {
-    ConvA ca;
-    halo_geom(*d.conv, &ca);
+  ConvA hca;
+  if (d.conv && halo_geom(*d.conv, &hca) && (hca.on == 4 || !gather_ok(*d.conv))) {
+    const ConvA& ca = hca;
     cfg.halo = 1;
     cfg.bn = halo_bn(d.conv->Cout);
     cfg.stages = 2;  // halo boxes in flight: as many as fit two CTAs per SM, else 2
@@ -1344,7 +1427,7 @@ void conv_plan(const ConvShape& c, int32_t* plan) {
   ConvA ca;
   if (halo_geom(c, &ca)) {
     const int rb = ca.cbw * 2;
-    plan[1] = 1;
+    plan[1] = ca.on == 4 ? 2 : 1;
     plan[2] = ca.Wp; plan[3] = ca.Hh; plan[4] = ca.ni; plan[5] = ca.tpi;
     plan[6] = ca.rows_box;
     plan[7] = (int32_t)(ca.halo_bytes / rb);

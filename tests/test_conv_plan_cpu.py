@@ -35,6 +35,9 @@ def test_halo_forward_reads_stay_in_the_staged_box(N, H, W, k, Cout):
         assert Cout * k * k * 32 * 2 > 96 * 1024 or W + 2 * p > 256 or H > 200
         return
     Wp, Hh, ni, tpi, rows_box, alloc, delivered, tiles = plan[2:10]
+    if plan[1] == 2:
+        _check_row_halo(N, H, W, k, Cout, plan)
+        return
     assert Wp == W + 2 * p and Hh == H + 2 * p
     assert delivered == rows_box * Wp * (ni if ni else 1)
     assert tiles == ((N + ni - 1) // ni if ni else N * tpi)
@@ -58,6 +61,46 @@ def test_halo_forward_reads_stay_in_the_staged_box(N, H, W, k, Cout):
             assert last < alloc, (tm, m, last, alloc)
             if valid:
                 assert last < delivered, (tm, m, last, delivered)
+
+
+def _check_row_halo(N, H, W, k, Cout, plan):
+    # whole image rows per tile: R = 128 / W rows, the box R + 2 rows of W pixels starting
+    # one row above the tile; filter row ky reads box pixels m + ky W for tile pixel m, and
+    # the column taps are neighbours in the same image row (the epilogue's lane shuffles)
+    Wp, Hh, ni, tpi, rows_box, alloc, delivered, tiles = plan[2:10]
+    assert k == 3 and W in (8, 16, 32) and Cout <= 32
+    R = TC_BM // W
+    assert H >= R and Wp == W and Hh == H and ni == 0
+    assert rows_box == R + 2 and tpi == (H + R - 1) // R and tiles == N * tpi
+    assert delivered == (R + 2) * W and alloc >= delivered and (alloc * 64) % 1024 == 0
+    for m in range(TC_BM):
+        rr, x = divmod(m, W)
+        for ky in range(3):
+            rd = m + ky * W                  # box pixel this lane's row of the MMA reads
+            assert rd < delivered
+            assert rd // W == rr + ky and rd % W == x  # image row y + ky - 1, same column
+        # a lane's image row lies within its warp: the shuffles never cross warps
+        assert (m // 32) == ((m - x) // 32) == ((m - x + W - 1) // 32)
+    # each filter row's view starts on a 512-byte (8-row) swizzle atom
+    assert all((ky * W * 64) % 512 == 0 for ky in range(3))
+
+
+@pytest.mark.parametrize("N,H,W", [(1, 4, 32), (3, 32, 32), (2, 35, 32), (2, 16, 16), (3, 20, 8),
+                                   (1, 16, 8)])
+def test_row_halo_geometry(N, H, W):
+    plan = B.ddppo_conv_plan(N, H, W, 32, 32, 3, 1, 1)
+    assert plan[1] == 2
+    _check_row_halo(N, H, W, 3, 32, plan)
+
+
+def test_row_halo_is_declined_where_it_does_not_apply():
+    for N, H, W, Cout, k in [(2, 2, 32, 32, 3),     # fewer rows than one tile
+                             (2, 30, 30, 32, 3),    # width 30
+                             (2, 32, 32, 64, 3),    # 64 output channels
+                             (2, 32, 32, 32, 5),    # 5x5 filter
+                             (2, 64, 64, 32, 3)]:   # a row wider than a warp
+        plan = B.ddppo_conv_plan(N, H, W, 32, Cout, k, 1, k // 2)
+        assert plan[1] != 2, (N, H, W, Cout, k)
 
 
 def _wgrad_shapes():
@@ -92,7 +135,7 @@ def test_workload_shapes_take_the_halo_paths():
     # the 64x64 input variants: forward, input gradient and weight gradient on the halo path
     for H in (32, 64):
         plan = B.ddppo_conv_plan(4096, H, H, 32, 32, 3, 1, 1)
-        assert plan[1] == 1 and plan[11] == 1
+        assert plan[1] == (2 if H == 32 else 1) and plan[11] == 1
     assert B.ddppo_conv_plan(64, 32, 32, 32, 64, 3, 1, 1)[1] == 1
 
 

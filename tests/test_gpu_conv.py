@@ -35,6 +35,12 @@ SHAPES = [
     (3, 12, 20, 32, 32, 3, 1, 1),     # non-square
     (2, 16, 16, 32, 32, 5, 1, 2),     # 5x5 filter, halo of two
     (3, 9, 9, 32, 64, 1, 1, 0),       # 1x1 filter
+    # 3x3 filters on rows of 8, 16 or 32 pixels take the row halo: whole rows per tile,
+    # the three column taps in one N = 96 MMA, combined by lane shuffles
+    (2, 16, 16, 32, 32, 3, 1, 1),     # 8 rows per tile
+    (3, 20, 8, 32, 16, 3, 1, 1),      # 16 rows per tile, the last one ragged; Cout 16
+    (2, 35, 32, 32, 32, 3, 1, 1),     # 4 rows per tile, 35 rows: ragged last tile
+    (5, 8, 16, 32, 24, 3, 1, 1),      # one tile per image, Cout 24
     (3, 8, 16, 64, 32, 3, 1, 1),      # 64 channels: 4-D gather path
     (2, 16, 16, 64, 64, 5, 1, 2),     # 5x5, 64 channels: 4-D gather path
     # one input channel (the stem): patches gathered in shared memory, no im2col matrix
@@ -70,6 +76,8 @@ BETA_SHAPES = [
     (3, 15, 15, 32, 32, 3, 1, 1),     # halo, tiles straddle rows
     (5, 5, 5, 32, 32, 3, 1, 1),       # halo, two images per tile
     (2, 30, 30, 32, 32, 3, 1, 1),     # halo only (no whole rows per 128-pixel tile)
+    (3, 32, 32, 32, 32, 3, 1, 1),     # row halo
+    (2, 20, 8, 32, 16, 3, 1, 1),      # row halo, ragged last tile, Cout 16
     (3, 16, 16, 64, 64, 3, 1, 1),     # 4-D gather path
     (2, 40, 40, 1, 32, 7, 2, 3),      # one input channel
 ]

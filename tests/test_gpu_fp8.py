@@ -106,6 +106,8 @@ CONV_SHAPES = [
     (3, 32, 32, 64, 64, 3, 1, 1),     # first stage (64 channels = 32 byte pairs)
     (2, 30, 30, 64, 64, 3, 1, 1),     # halo path only (no whole rows per 128-pixel tile)
     (3, 15, 15, 64, 64, 3, 1, 1),     # halo, tiles straddle rows
+    (2, 16, 16, 64, 32, 3, 1, 1),     # row halo (32 outputs, rows of 16): one N = 96 MMA per
+                                      # filter row on the 64-byte rows of 64 E4M3 channels
     (2, 16, 16, 128, 128, 3, 1, 1),   # 128 channels: 128-byte rows
     (3, 16, 16, 64, 128, 3, 2, 1),    # stride 2
     (4, 16, 16, 128, 256, 1, 2, 0),   # 1x1 stride-2 shortcut
