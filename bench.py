@@ -110,9 +110,9 @@ class ClockSampler:
 
 # DRAM traffic of the update's contractions over their algorithmic bytes, from one ncu
 # capture of the same step at T = 16 (dram__bytes_read.sum + dram__bytes_write.sum over the
-# update's contraction launches: 11,437 MB against 15,690 MB algorithmic); the full-size
+# update's contraction launches: 10,399 MB against 15,690 MB algorithmic); the full-size
 # traffic is reported as this fraction of the live algorithmic bytes
-GEMM_TRAFFIC_OVER_ALGORITHMIC = 11437.0 / 15690.0
+GEMM_TRAFFIC_OVER_ALGORITHMIC = 10399.0 / 15690.0
 
 
 def _dist():
@@ -246,7 +246,8 @@ def run_gpu(args):
                      "algorithmic_bytes_per_launch": round(sum(l_by) / max(len(l_by), 1)),
                      "traffic": round(GEMM_TRAFFIC_OVER_ALGORITHMIC * sum(l_by) / max(len(l_by), 1)),
                      "traffic_source": "dram bytes per launch, the T = 16 ncu capture's traffic / "
-                                       "algorithmic ratio (0.73) times this run's algorithmic bytes"},
+                                       "algorithmic ratio (%.3f) times this run's algorithmic "
+                                       "bytes" % GEMM_TRAFFIC_OVER_ALGORITHMIC},
         "raycast": {"launches": r_n, "avg_launch_us": round(1e3 * r_ms / max(r_n, 1), 2),
                 "kernel": "env_step render (TMA-staged DDA ray cast, 64 x 256x256 -> 128x128 bf16)",
                     "out_GBps": round(r_bytes / (r_ms / 1e3) / 1e9, 2) if r_ms > 0 else None},

@@ -589,6 +589,19 @@ int ddppo_set_launch_overlap(int32_t on);
 /* on [host]: the current state (1 on, 0 off). */
 int ddppo_launch_overlap(int32_t* on);
 
+/* Tensor-store epilogue (process-wide; not a method step): a tensor-core contraction tile
+ * whose rows are whole rows of the output (plain GEMM, convolution tiles, the row halo),
+ * with nothing accumulated into C and no split-K, hands its result to one tensor copy
+ * (cp.async.bulk.tensor) per 32 x 32 block from shared memory instead of transposing it
+ * and storing it row by row. The values are formed identically (scale, bias, ReLU, output
+ * type), so results are bit-identical either way. on = 0 keeps the per-row stores. The
+ * initial state is on unless the environment variable DDPPO_TMA_EPILOGUE is "0". Applies
+ * to launches enqueued afterwards; a captured graph keeps the form it was captured with.
+ * Host only. */
+int ddppo_set_tma_epilogue(int32_t on);
+/* on [host]: the current state (1 on, 0 off). */
+int ddppo_tma_epilogue(int32_t* on);
+
 /* Tile-shape autotuner of the tensor-core GEMM (precision 1): on by default. The first
  * time a contraction shape is seen outside a stream capture, each candidate (N tile 64 or
  * 128, ring depth 2-4, split-K or not) runs on a scratch output and the fastest is kept;

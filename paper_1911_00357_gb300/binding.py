@@ -130,6 +130,8 @@ _SIGS = {
     "ddppo_update_graph": [P, I32],
     "ddppo_set_launch_overlap": [I32],
     "ddppo_launch_overlap": [P],
+    "ddppo_set_tma_epilogue": [I32],
+    "ddppo_tma_epilogue": [P],
     "ddppo_autotune_export": [P, P, ctypes.c_size_t, P],
     "ddppo_autotune_import": [P, P, ctypes.c_size_t],
     "ddppo_conv2d": [I32, I32, I32, I32, I32, I32, I32, I32, P, P, P, F32, P, P],
@@ -441,6 +443,16 @@ def ddppo_set_launch_overlap(on: bool = True) -> None:
 def ddppo_launch_overlap() -> bool:
     v = ctypes.c_int32()
     _check(lib().ddppo_launch_overlap(ctypes.byref(v)))
+    return bool(v.value)
+
+
+def ddppo_set_tma_epilogue(on: bool = True) -> None:
+    _check(lib().ddppo_set_tma_epilogue(1 if on else 0))
+
+
+def ddppo_tma_epilogue() -> bool:
+    v = ctypes.c_int32()
+    _check(lib().ddppo_tma_epilogue(ctypes.byref(v)))
     return bool(v.value)
 
 

@@ -50,7 +50,32 @@ bool pdl_enabled() {
   }
   return v != 0;
 }
+// tensor-store epilogue of the tcgen05 GEMM: on unless DDPPO_TMA_EPILOGUE=0
+static std::atomic<int> g_tma_epi{-1};
+bool tma_epilogue_enabled() {
+  int v = g_tma_epi.load(std::memory_order_relaxed);
+  if (v < 0) {
+    const char* e = getenv("DDPPO_TMA_EPILOGUE");
+    v = (e && e[0] == '0') ? 0 : 1;
+    g_tma_epi.store(v, std::memory_order_relaxed);
+  }
+  return v != 0;
+}
 }  // namespace ddppo
+
+extern "C" int ddppo_set_tma_epilogue(int32_t on) {
+  ddppo::g_tma_epi.store(on ? 1 : 0, std::memory_order_relaxed);
+  return DDPPO_OK;
+}
+
+extern "C" int ddppo_tma_epilogue(int32_t* on) {
+  if (!on) {
+    ddppo::set_error("tma_epilogue: null argument");
+    return DDPPO_E_ARG;
+  }
+  *on = ddppo::tma_epilogue_enabled() ? 1 : 0;
+  return DDPPO_OK;
+}
 
 extern "C" int ddppo_set_launch_overlap(int32_t on) {
   ddppo::g_pdl.store(on ? 1 : 0, std::memory_order_relaxed);

@@ -46,6 +46,10 @@ void set_error(const std::string& msg);
 // process-wide switch (ddppo_set_launch_overlap); graphs captured before a change keep the
 // form they were captured with
 bool pdl_enabled();
+// process-wide switch (ddppo_set_tma_epilogue): tensor-core GEMM tiles whose rows are whole
+// output rows leave through a tensor store from shared memory (on) or through the
+// transpose and per-row stores (off); bit-identical results either way
+bool tma_epilogue_enabled();
 
 template <typename... P, typename... A>
 inline void launch_k(void (*kern)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,

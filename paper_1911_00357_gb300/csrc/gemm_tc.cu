@@ -29,6 +29,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -40,7 +41,11 @@
 namespace ddppo {
 
 constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 16;  // TC_STAGES: deepest ring
-constexpr int TC_EPI_PITCH = 33;  // floats per staged row (bank-conflict-free transpose)
+// epilogue staging: 32 x 32 floats per epilogue warp, 1024-byte aligned. The transpose
+// path stores element (row i, column j) at i * 32 + (j ^ i) (conflict-free both ways); the
+// tensor-store path writes 128-byte rows whose 16-byte chunks sit at chunk ^ (row & 7) --
+// the layout a SWIZZLE_128B tensor copy reads (SWIZZLE_64B for bf16 rows of 64 bytes).
+constexpr int TC_EPI_FLOATS = 32 * 32;
 // dynamic part; the static part (barriers, 17 KiB epilogue staging) makes up the rest of
 // the 227 KiB opt-in limit
 constexpr size_t TC_SMEM_MAX = 205 * 1024;
@@ -203,6 +208,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+// tensor store of one 32 x 32 block of the output from shared memory (bulk async group of
+// the issuing thread); rows and columns outside the tensor are not written
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   (uint64_t)map),
+               "r"(smem_addr(src)), "r"(x), "r"(y)
+               : "memory");
+}
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int x, int y,
+                                             int z) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                   (uint64_t)map),
+               "r"(smem_addr(src)), "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+__device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
+  const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
 // Persistent, warp-specialised kernel. Warp 0 streams (tile, k-block) stages through the
 // shared-memory ring with TMA; warp 1 issues the MMAs of a tile into one of two TMEM
 // accumulators; warps 2..5 drain the other accumulator (tcgen05.ld -> smem transpose ->
@@ -217,12 +242,13 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
                    float beta, const float* __restrict__ bias, int relu, int trans_out,
                    float* __restrict__ partial, int32_t* err, int a_mn, int b_mn, int stages,
                    int tiles_m, int tiles_n, int splits, ConvA ca, int fp8,
-                   const float* __restrict__ scale_a, const float* __restrict__ scale_b) {
+                   const float* __restrict__ scale_a, const float* __restrict__ scale_b,
+                   const __grid_constant__ CUtensorMap mapC, int tma_out_req) {
   extern __shared__ __align__(1024) uint8_t dyn[];
   __shared__ TcSmem ctl;
   __shared__ uint64_t acc_full[2], acc_empty[2];
   // epilogue staging, one 32 x 32 block per epilogue warp (static: known to be shared memory)
-  __shared__ float epi_stage[4][32 * TC_EPI_PITCH];
+  __shared__ __align__(1024) float epi_stage[4][TC_EPI_FLOATS];
   // stage sizes follow the K extent of one ring slot (32 channels for narrow convolutions);
   // the halo mode has a ring of `stages` halo boxes (A) and all the weights resident (B)
   const bool halo = ca.on >= 3;
@@ -493,6 +519,8 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
     // epilogue warps 2..5: warp w reads TMEM lanes 32 (w % 4) .. +31
     const int q = warp & 3;
     float* stage_out = epi_stage[q];
+    // the tensor store reads the staging block through the swizzle of its 1024-byte atom
+    const int tma_out = (smem_addr(&epi_stage[0][0]) & 1023u) ? 0 : tma_out_req;
     const int Mo = trans_out ? N : M, No = trans_out ? M : N;
     // per-tensor scales of E4M3 operands (exactly 1 otherwise)
     const float alpha = (scale_a ? *scale_a : 1.f) * (scale_b ? *scale_b : 1.f);
@@ -538,6 +566,54 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
           tmem_ld32(taddr, r);
         }
         if (!ok) continue;
+        if (tma_out) {
+          // tensor-store path (rows of the tile are consecutive output rows, beta = 0, no
+          // split-K): this lane's row of 32 values, formed exactly as the transpose path
+          // below forms them (scale, + bias, ReLU, then the output type), written to the
+          // staging block in the swizzled layout and stored by one tensor copy
+          const float bl = bias ? bias[min(n0 + c0 + lane, N - 1)] : 0.f;
+          float x[32];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) {
+            float v = __uint_as_float(r[j]);
+            if (fp8) v *= alpha;
+            v += __shfl_sync(0xffffffffu, bl, j);
+            if (relu) v = fmaxf(v, 0.f);
+            x[j] = v;
+          }
+          // the previous tensor store from this block has finished reading it
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+          __syncwarp();
+          char* sb = reinterpret_cast<char*>(stage_out);
+          if (tma_out == 1) {
+            // fp32: 128-byte rows, 16-byte chunk c of row l at chunk c ^ (l & 7)
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+              *reinterpret_cast<float4*>(sb + lane * 128 + ((c ^ (lane & 7)) << 4)) =
+                  make_float4(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+          } else {
+            // bf16: 64-byte rows, 16-byte chunk c of row l at chunk c ^ ((l >> 1) & 3)
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              *reinterpret_cast<uint4*>(sb + lane * 64 + ((c ^ ((lane >> 1) & 3)) << 4)) =
+                  make_uint4(bf16x2_bits(x[8 * c], x[8 * c + 1]), bf16x2_bits(x[8 * c + 2], x[8 * c + 3]),
+                             bf16x2_bits(x[8 * c + 4], x[8 * c + 5]), bf16x2_bits(x[8 * c + 6], x[8 * c + 7]));
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) {
+            if (rowh) {
+              // [images, H W, N]: the warp's 32 rows are pixels of one image from
+              // y0 W + 32 q on; pixels past the image's last one are not written
+              const int img = tm / ca.tpi;
+              tma_store_3d(&mapC, sb, n0 + c0, (tm - img * ca.tpi) * ca.R * ca.W + q * 32, img);
+            } else {
+              tma_store_2d(&mapC, sb, n0 + c0, m0 + q * 32);
+            }
+            asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+          }
+          continue;
+        }
         if (trans_out) {
           if (row >= M) continue;
 #pragma unroll
@@ -561,10 +637,10 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
         // transpose through shared memory: lane l then owns column c0 + l of the 32 rows,
         // so every store instruction writes 32 consecutive values of one row
 #pragma unroll
-        for (int j = 0; j < 32; ++j) stage_out[lane * TC_EPI_PITCH + j] = __uint_as_float(r[j]);
+        for (int j = 0; j < 32; ++j) stage_out[lane * 32 + (j ^ lane)] = __uint_as_float(r[j]);
         if (fp8) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) stage_out[lane * TC_EPI_PITCH + j] *= alpha;
+          for (int j = 0; j < 32; ++j) stage_out[lane * 32 + (j ^ lane)] *= alpha;
         }
         __syncwarp();
         const int col = n0 + c0 + lane;
@@ -577,7 +653,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
             long long orows[8];
 #pragma unroll
             for (int k = 0; k < 8; ++k) {
-              v[k] = stage_out[(i0 + k) * TC_EPI_PITCH + lane];
+              v[k] = stage_out[(i0 + k) * 32 + (lane ^ (i0 + k))];
               orows[k] = __shfl_sync(0xffffffffu, my_orow, i0 + k);
             }
             if (!cin) continue;
@@ -615,7 +691,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
         for (int i0 = 0; i0 < 32; i0 += 8) {
           float v[8];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) v[k] = stage_out[(i0 + k) * TC_EPI_PITCH + lane];
+          for (int k = 0; k < 8; ++k) v[k] = stage_out[(i0 + k) * 32 + (lane ^ (i0 + k))];
           if (!cin || i0 >= nrows) continue;
           if (partial) {
             float* pz = partial + ((size_t)z * Mo + m0 + q * 32 + i0) * No + col;
@@ -653,6 +729,8 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
       }
       if (!ok) break;
     }
+    // every tensor store of this warp has completed before the kernel ends
+    if (tma_out && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -707,6 +785,33 @@ static bool make_map_sw(CUtensorMap* m, const void* ptr, int rows, int cols, int
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(ptr), dims, strides, box,
             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The output C as a tensor-store target: fp32 rows (SWIZZLE_128B) or bf16 rows
+// (SWIZZLE_64B), boxes of 32 rows x 32 columns. hw > 0: as a 3-D tensor [rows / hw, hw,
+// cols] (the row halo stores per image, so a ragged last tile stops at the image's last
+// pixel). False when the layout does not allow it (the transpose path stores instead).
+static bool make_out_map(CUtensorMap* m, void* C, int rows, int cols, int ldc, int bf16, int hw) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const size_t es = bf16 ? 2 : 4;
+  if (((uintptr_t)C & 15) || ((size_t)ldc * es) % 16 || cols < 32 || rows < 32) return false;
+  const CUtensorMapDataType dt = bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+  const CUtensorMapSwizzle sw = bf16 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_128B;
+  cuuint32_t estr[3] = {1, 1, 1};
+  if (hw > 0) {
+    if (hw < 32 || rows % hw) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)hw, (cuuint64_t)(rows / hw)};
+    cuuint64_t strides[2] = {(cuuint64_t)ldc * es, (cuuint64_t)hw * ldc * es};
+    cuuint32_t box[3] = {32u, 32u, 1u};
+    return fn(m, dt, 3, C, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+              CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  }
+  cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ldc * es};
+  cuuint32_t box[2] = {32u, 32u};
+  return fn(m, dt, 2, C, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, sw,
+            CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // NHWC bf16 input as a 4-D tensor [C, W, H, N]; one box = the cbw channels of the
@@ -1036,9 +1141,19 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
   const int stages = cfg.stages;
   const int ntiles = gm * gn * splits;
   const int grid = min(ntiles, ws.num_sms * per_sm);
+  // tensor-store epilogue: whole output rows per tile row (plain, 4-D gather and row-halo
+  // tiles), nothing accumulated into C, no split-K partials
+  CUtensorMap mc;
+  memset(&mc, 0, sizeof(mc));
+  int tma_out = 0;
+  if (tma_epilogue_enabled() && !partial && !trans && d.beta == 0.f &&
+      (ca.on == 0 || ca.on == 1 || ca.on == 4) &&
+      make_out_map(&mc, d.C, M, N, d.ldc, d.c_bf16, ca.on == 4 ? ca.H * ca.W : 0))
+    tma_out = d.c_bf16 ? 2 : 1;
   ::ddppo::launch_k(gemm_tc_kernel<BN>, grid, TC_PTHREADS, smem, s,
       ma, mb, M, N, K, kchunk, (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu, trans,
-      partial, ws.err, a_mn, b_mn, stages, gm, gn, splits, ca, d.fp8, d.scale_a, d.scale_b);
+      partial, ws.err, a_mn, b_mn, stages, gm, gn, splits, ca, d.fp8, d.scale_a, d.scale_b, mc,
+      tma_out);
   DDPPO_CHECK_LAUNCH();
   if (partial)
     DDPPO_TRY(launch_splitk_reduce(d.M, d.N, splits, partial, (float*)d.C, d.ldc, d.c_bf16, d.beta,
