@@ -89,6 +89,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       : "memory");
 }
 
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int x,
+                                            int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, "
+      "%4, %5}], [%2];" ::"r"(smem_addr(dst)),
+      "l"((uint64_t)map), "r"(smem_addr(bar)), "r"(x), "r"(y), "r"(z)
+      : "memory");
+}
+
 __device__ __forceinline__ void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
                                             int c1, int c2, int c3) {
   asm volatile(
@@ -247,6 +256,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
   extern __shared__ __align__(1024) uint8_t dyn[];
   __shared__ TcSmem ctl;
   __shared__ uint64_t acc_full[2], acc_empty[2];
+  __shared__ uint64_t epi_bar[4];  // tensor loads of C blocks (beta != 0), one per epilogue warp
   // epilogue staging, one 32 x 32 block per epilogue warp (static: known to be shared memory)
   __shared__ __align__(1024) float epi_stage[4][TC_EPI_FLOATS];
   // stage sizes follow the K extent of one ring slot (32 channels for narrow convolutions);
@@ -278,6 +288,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
     }
+    for (int b = 0; b < 4; ++b) mbar_init(&epi_bar[b], 1);
     ctl.abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -521,6 +532,8 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
     float* stage_out = epi_stage[q];
     // the tensor store reads the staging block through the swizzle of its 1024-byte atom
     const int tma_out = (smem_addr(&epi_stage[0][0]) & 1023u) ? 0 : tma_out_req;
+    uint32_t epi_ph = 0;     // phase of this warp's C-load barrier
+    bool c_pending = false;  // a C load whose wait ran out (drained at the end)
     const int Mo = trans_out ? N : M, No = trans_out ? M : N;
     // per-tensor scales of E4M3 operands (exactly 1 otherwise)
     const float alpha = (scale_a ? *scale_a : 1.f) * (scale_b ? *scale_b : 1.f);
@@ -567,25 +580,54 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
         }
         if (!ok) continue;
         if (tma_out) {
-          // tensor-store path (rows of the tile are consecutive output rows, beta = 0, no
-          // split-K): this lane's row of 32 values, formed exactly as the transpose path
-          // below forms them (scale, + bias, ReLU, then the output type), written to the
-          // staging block in the swizzled layout and stored by one tensor copy
-          const float bl = bias ? bias[min(n0 + c0 + lane, N - 1)] : 0.f;
+          // tensor-store path (rows of the tile are consecutive output rows, no transposed
+          // output): this lane's row of 32 values, formed exactly as the transpose path
+          // below forms them -- scale; then for C: + beta C (one fused multiply-add, C read
+          // by a tensor load of the same block), + bias, ReLU, output type; split-K
+          // partials stay raw -- written to the staging block in the swizzled layout and
+          // stored by one tensor copy
+          if (c_pending) continue;  // a C load ran out of time: this CTA stores nothing more
+          char* sb = reinterpret_cast<char*>(stage_out);
+          const bool part = tma_out == 3;
+          const int img = rowh ? tm / ca.tpi : 0;
+          const int ty = rowh ? (tm - img * ca.tpi) * ca.R * ca.W + q * 32 : m0 + q * 32;
+          // the previous tensor store from this block has finished reading it
+          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+          __syncwarp();
+          float cv[32];
+          if (beta != 0.f && !part) {
+            if (lane == 0) {
+              mbar_expect_tx(&epi_bar[q], 4096u);  // fp32 output (the host's condition)
+              if (rowh) tma_load_3d(sb, &mapC, &epi_bar[q], n0 + c0, ty, img);
+              else tma_load_2d(sb, &mapC, &epi_bar[q], n0 + c0, ty);
+            }
+            const bool got = __all_sync(0xffffffffu, mbar_wait(&epi_bar[q], epi_ph, abort, err));
+            epi_ph ^= 1u;
+            if (!got) {
+              c_pending = true;  // drained before the kernel ends
+              continue;
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              const float4 t = *reinterpret_cast<const float4*>(sb + lane * 128 + ((c ^ (lane & 7)) << 4));
+              cv[4 * c] = t.x; cv[4 * c + 1] = t.y; cv[4 * c + 2] = t.z; cv[4 * c + 3] = t.w;
+            }
+            __syncwarp();  // every lane has read its row before the block is rewritten
+          }
+          const float bl = (bias && !part) ? bias[min(n0 + c0 + lane, N - 1)] : 0.f;
           float x[32];
 #pragma unroll
           for (int j = 0; j < 32; ++j) {
             float v = __uint_as_float(r[j]);
             if (fp8) v *= alpha;
-            v += __shfl_sync(0xffffffffu, bl, j);
-            if (relu) v = fmaxf(v, 0.f);
+            if (!part) {
+              if (beta != 0.f) v = __fmaf_rn(beta, cv[j], v);
+              v += __shfl_sync(0xffffffffu, bl, j);
+              if (relu) v = fmaxf(v, 0.f);
+            }
             x[j] = v;
           }
-          // the previous tensor store from this block has finished reading it
-          if (lane == 0) asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
-          __syncwarp();
-          char* sb = reinterpret_cast<char*>(stage_out);
-          if (tma_out == 1) {
+          if (tma_out != 2) {
             // fp32: 128-byte rows, 16-byte chunk c of row l at chunk c ^ (l & 7)
 #pragma unroll
             for (int c = 0; c < 8; ++c)
@@ -602,14 +644,12 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
           if (lane == 0) {
-            if (rowh) {
-              // [images, H W, N]: the warp's 32 rows are pixels of one image from
-              // y0 W + 32 q on; pixels past the image's last one are not written
-              const int img = tm / ca.tpi;
-              tma_store_3d(&mapC, sb, n0 + c0, (tm - img * ca.tpi) * ca.R * ca.W + q * 32, img);
-            } else {
-              tma_store_2d(&mapC, sb, n0 + c0, m0 + q * 32);
-            }
+            // row halo: [images, H W, N], the warp's 32 rows are pixels of one image from
+            // y0 W + 32 q on (pixels past the image's last one are not written); split-K
+            // partials: [splits, M, N]; otherwise [M, N]
+            if (rowh) tma_store_3d(&mapC, sb, n0 + c0, ty, img);
+            else if (part) tma_store_3d(&mapC, sb, n0 + c0, ty, z);
+            else tma_store_2d(&mapC, sb, n0 + c0, ty);
             asm volatile("cp.async.bulk.commit_group;" ::: "memory");
           }
           continue;
@@ -626,7 +666,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
               continue;
             }
             const size_t o = (size_t)col * ldc + row;
-            if (beta != 0.f) v += beta * C[o];
+            if (beta != 0.f) v = __fmaf_rn(beta, C[o], v);
             if (bias) v += bias[row];
             if (relu) v = fmaxf(v, 0.f);
             if (c_bf16) ((__nv_bfloat16*)C)[o] = __float2bfloat16_rn(v);
@@ -674,7 +714,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
                 continue;
               }
               const size_t o = (size_t)orow * ldc + col;
-              if (beta != 0.f) x += beta * cv[k];
+              if (beta != 0.f) x = __fmaf_rn(beta, cv[k], x);
               x += bv;
               if (relu) x = fmaxf(x, 0.f);
               if (c_bf16) ((__nv_bfloat16*)C)[o] = __float2bfloat16_rn(x);
@@ -706,7 +746,7 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
 #pragma unroll
             for (int k = 0; k < 8; ++k) cv[k] = i0 + k < nrows ? C[o0 + (size_t)k * ldc] : 0.f;
 #pragma unroll
-            for (int k = 0; k < 8; ++k) v[k] += beta * cv[k];
+            for (int k = 0; k < 8; ++k) v[k] = __fmaf_rn(beta, cv[k], v[k]);
           }
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
@@ -729,8 +769,10 @@ __global__ void __launch_bounds__(TC_PTHREADS, 2)
       }
       if (!ok) break;
     }
-    // every tensor store of this warp has completed before the kernel ends
+    // every tensor store of this warp has completed before the kernel ends, and a C load
+    // whose wait ran out has landed before the shared memory is released
     if (tma_out && lane == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    if (c_pending) mbar_drain_wait(&epi_bar[q], epi_ph ^ 1u);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -1142,14 +1184,18 @@ static int launch_tc(const CUtensorMap& ma, const CUtensorMap& mb, int M, int N,
   const int ntiles = gm * gn * splits;
   const int grid = min(ntiles, ws.num_sms * per_sm);
   // tensor-store epilogue: whole output rows per tile row (plain, 4-D gather and row-halo
-  // tiles), nothing accumulated into C, no split-K partials
+  // tiles), into C (beta C read by a tensor load of each block) or into split-K partials
   CUtensorMap mc;
   memset(&mc, 0, sizeof(mc));
   int tma_out = 0;
-  if (tma_epilogue_enabled() && !partial && !trans && d.beta == 0.f &&
-      (ca.on == 0 || ca.on == 1 || ca.on == 4) &&
-      make_out_map(&mc, d.C, M, N, d.ldc, d.c_bf16, ca.on == 4 ? ca.H * ca.W : 0))
-    tma_out = d.c_bf16 ? 2 : 1;
+  if (tma_epilogue_enabled() && !trans && (ca.on == 0 || ca.on == 1 || ca.on == 4)) {
+    if (partial) {
+      if (ca.on != 4 && make_out_map(&mc, partial, splits * M, N, N, 0, M)) tma_out = 3;
+    } else if ((d.beta == 0.f || !d.c_bf16) &&  // C is read back (beta != 0) in fp32 only
+               make_out_map(&mc, d.C, M, N, d.ldc, d.c_bf16, ca.on == 4 ? ca.H * ca.W : 0)) {
+      tma_out = d.c_bf16 ? 2 : 1;
+    }
+  }
   ::ddppo::launch_k(gemm_tc_kernel<BN>, grid, TC_PTHREADS, smem, s,
       ma, mb, M, N, K, kchunk, (float*)d.C, d.ldc, d.c_bf16, d.beta, d.bias, d.relu, trans,
       partial, ws.err, a_mn, b_mn, stages, gm, gn, splits, ca, d.fp8, d.scale_a, d.scale_b, mc,

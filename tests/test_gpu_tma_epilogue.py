@@ -1,10 +1,12 @@
 """The tensor-store epilogue of the tcgen05 GEMM changes how a tile's result leaves the SM
 (one tensor copy per 32 x 32 block from swizzled shared memory, instead of a transpose and
 one store per row), never the values: each output is formed by the same operations in the
-same order (scale, + bias, ReLU, output type). With the epilogue on and off, plain
-contractions (fp32 and bf16 outputs, bias and ReLU, ragged M and N), convolutions on the
-4-D gather and the row halo (ragged last tiles, Cout below 32), and whole rollout-then-
-update iterations (captured collect and update graphs) are bit-identical."""
+same order (scale, + beta C as one fused multiply-add with C read by a tensor load, + bias,
+ReLU, output type; split-K partials raw). With the epilogue on and off, plain contractions
+(fp32 and bf16 outputs, beta, bias and ReLU, ragged M and N, split-K partials),
+convolutions on the 4-D gather and the row halo (ragged last tiles, Cout below 32, beta),
+and whole rollout-then-update iterations (captured collect and update graphs) are
+bit-identical."""
 import numpy as np
 import pytest
 import torch
@@ -27,28 +29,33 @@ def _both(fn):
     return a, b
 
 
-# (M, N, K, c dtype, bias, relu): tiles of 128 rows; N tiles of 64 / 128 with 32-column
-# store blocks; ragged M and N (the stores stop at the tensor's edge)
+# (M, N, K, c dtype, beta, bias, relu): tiles of 128 rows; N tiles of 64 / 128 with
+# 32-column store blocks; ragged M and N (the stores stop at the tensor's edge); K >= 512
+# with few tiles takes split-K (partials through the tensor store, then the reduction)
 GEMMS = [
-    (4096, 64, 288, torch.float32, False, False),
-    (1000, 300, 520, torch.float32, True, True),
-    (8192, 512, 2048, torch.bfloat16, True, True),
-    (777, 96, 64, torch.bfloat16, False, True),
-    (300, 40, 128, torch.float32, True, False),
-    (129, 33, 72, torch.float32, False, False),
+    (4096, 64, 288, torch.float32, 0.0, False, False),
+    (4096, 64, 288, torch.float32, 1.0, False, False),
+    (1000, 300, 520, torch.float32, 0.0, True, True),
+    (1000, 300, 520, torch.float32, 0.5, True, True),
+    (8192, 512, 2048, torch.bfloat16, 0.0, True, True),
+    (777, 96, 64, torch.bfloat16, 0.0, False, True),
+    (300, 40, 128, torch.float32, -0.75, True, False),
+    (129, 33, 72, torch.float32, 0.0, False, False),
+    (2000, 128, 1024, torch.float32, 1.0, False, True),
 ]
 
 
-@pytest.mark.parametrize("M,N,K,cdt,bias,relu", GEMMS)
-def test_gemm_epilogues_bit_identical(M, N, K, cdt, bias, relu):
+@pytest.mark.parametrize("M,N,K,cdt,beta,bias,relu", GEMMS)
+def test_gemm_epilogues_bit_identical(M, N, K, cdt, beta, bias, relu):
     g = torch.Generator(device="cuda").manual_seed(M + 3 * N + 7 * K)
     A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
     Bm = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
     bv = torch.randn(N, device="cuda", generator=g) if bias else None
+    C0 = torch.randn(M, N, device="cuda", generator=g)
 
     def run():
-        C = torch.full((M, N), float("nan"), device="cuda").to(cdt)
-        B.ddppo_gemm(A, Bm, C, bias=bv, relu=relu)
+        C = C0.clone() if beta else torch.full((M, N), float("nan"), device="cuda").to(cdt)
+        B.ddppo_gemm(A, Bm, C, beta=beta, bias=bv, relu=relu)
         torch.cuda.synchronize()
         return C.cpu()
 
@@ -56,6 +63,8 @@ def test_gemm_epilogues_bit_identical(M, N, K, cdt, bias, relu):
     assert torch.equal(a.view(torch.int16) if cdt == torch.bfloat16 else a.view(torch.int32),
                        b.view(torch.int16) if cdt == torch.bfloat16 else b.view(torch.int32))
     ref = A.double().cpu() @ Bm.double().cpu().T
+    if beta:
+        ref = ref + beta * C0.double().cpu()
     if bias:
         ref = ref + bv.double().cpu()
     if relu:
@@ -76,17 +85,20 @@ CONVS = [
 ]
 
 
+@pytest.mark.parametrize("beta", [0.0, 1.0])
 @pytest.mark.parametrize("N,H,W,C,Co,k,s,p", CONVS)
-def test_conv_epilogues_bit_identical(N, H, W, C, Co, k, s, p):
+def test_conv_epilogues_bit_identical(N, H, W, C, Co, k, s, p, beta):
     g = torch.Generator(device="cuda").manual_seed(N * 131 + C * 7 + Co + k + s)
     x = torch.randn(N, H, W, C, device="cuda", generator=g).to(torch.bfloat16)
     wg = (torch.randn(Co, k * k * C, device="cuda", generator=g) / np.sqrt(C * k * k)).to(torch.bfloat16)
     Ho, Wo = (H + 2 * p - k) // s + 1, (W + 2 * p - k) // s + 1
 
+    y0 = torch.randn(N, Ho, Wo, Co, device="cuda", generator=g)
+
     def run():
-        y = torch.full((N, Ho, Wo, Co), float("nan"), device="cuda")
+        y = y0.clone() if beta else torch.full((N, Ho, Wo, Co), float("nan"), device="cuda")
         st = torch.zeros(1, dtype=torch.int32, device="cuda")
-        B.ddppo_conv2d(x, wg, y, k, s, p, status=st)
+        B.ddppo_conv2d(x, wg, y, k, s, p, beta=beta, status=st)
         torch.cuda.synchronize()
         assert st.item() == 0
         return y.cpu()
