@@ -1,6 +1,7 @@
 """Compile ``sim_oracle.c`` into ``oracle/_build/libddppo_oracle.so`` with gcc.
 
-Test infrastructure: building the checker is not using it.
+Test infrastructure: the library is compiled with the package so that the tests and the
+benchmark's oracle leg can load it; nothing on the CUDA path loads or calls it.
 """
 import os
 import subprocess
