@@ -16,7 +16,10 @@
 //     N = 3 x 32 MMA per filter row, combined in the epilogue by lane shuffles).
 //   * Epilogue: 4 warps each read their 32 TMEM lanes (rows) with tcgen05.ld.32x32b and
 //     apply beta/bias/ReLU, storing fp32 or bf16 -- or fp32 split-K partials that a
-//     fixed-order reduction combines.
+//     fixed-order reduction combines. Where the tile's rows are whole output rows, each
+//     warp stages its 32 x 32 block in the swizzle a tensor copy reads and issues one
+//     cp.async.bulk.tensor store (C for beta != 0 comes in by a tensor load); otherwise
+//     it transposes through shared memory and stores row by row.
 //   * Small-M problems (the per-step LSTM recurrences) are computed transposed (swap AB)
 //     so the 128-row MMA dimension covers the large side.
 // Every wait is bounded; a wait that runs out sets the sticky timeout flag and the CTA
@@ -46,8 +49,8 @@ constexpr int TC_BM = 128, TC_BK = 64, TC_STAGES = 16;  // TC_STAGES: deepest ri
 // tensor-store path writes 128-byte rows whose 16-byte chunks sit at chunk ^ (row & 7) --
 // the layout a SWIZZLE_128B tensor copy reads (SWIZZLE_64B for bf16 rows of 64 bytes).
 constexpr int TC_EPI_FLOATS = 32 * 32;
-// dynamic part; the static part (barriers, 17 KiB epilogue staging) makes up the rest of
-// the 227 KiB opt-in limit
+// dynamic part; the static part (barriers, 16 KiB epilogue staging: 17 KiB in all) makes up
+// the rest of the 227 KiB opt-in limit
 constexpr size_t TC_SMEM_MAX = 205 * 1024;
 constexpr size_t TC_SMEM_TWO_PER_SM = 94 * 1024;  // dynamic bytes that still fit two CTAs per SM
 
@@ -239,8 +242,9 @@ __device__ __forceinline__ uint32_t bf16x2_bits(float a, float b) {
 
 // Persistent, warp-specialised kernel. Warp 0 streams (tile, k-block) stages through the
 // shared-memory ring with TMA; warp 1 issues the MMAs of a tile into one of two TMEM
-// accumulators; warps 2..5 drain the other accumulator (tcgen05.ld -> smem transpose ->
-// coalesced stores), so one tile's epilogue overlaps the next tile's loads and MMAs.
+// accumulators; warps 2..5 drain the other accumulator (tcgen05.ld -> a tensor store from
+// swizzled shared memory, or a shared-memory transpose and coalesced row stores), so one
+// tile's epilogue overlaps the next tile's loads and MMAs.
 // Tiles are (m, n, split) triples walked with stride gridDim.x.
 constexpr int TC_PTHREADS = 192;
 
